@@ -1,0 +1,150 @@
+"""Exact-arithmetic replays of BiCG and GPBiCG (Fig. 5) on tiny systems.
+
+Independent of the oracle's C code: every operation is a rational operation
+rounded by tests/exact.py's round-to-nearest-even.  The op order is the one
+both implementations follow (each printed product and sum rounded, left to
+right), and dot products are exact sums rounded once.
+"""
+from fractions import Fraction
+
+import exact
+
+
+def _dot(x, y, p):
+    return exact.exact_sum([a.q * b.q for a, b in zip(x, y)], p)
+
+
+def _spmv(rows, x, p, mode):
+    out = []
+    for entries in rows:  # entries: list of (col, Val) in column order
+        if mode == 0:
+            y = exact.Val(Fraction(0))
+            for c, a in entries:
+                if a.q == 0 or x[c].q == 0:
+                    continue
+                y = exact.radd(y, exact.rmul(a, x[c], p), p)
+        else:
+            y = exact.exact_sum([a.q * x[c].q for c, a in entries], p)
+        out.append(y)
+    return out
+
+
+def _threshold(rr0, rtol, atol, p):
+    rt = exact.Val(Fraction(rtol))
+    at = exact.Val(Fraction(atol))
+    T = exact.rmul(rt, rt, p)
+    A = exact.rmul(at, at, p)
+    return exact.radd(exact.rmul(T, rr0, p), A, p)
+
+
+def _residual(rows, b, x, p):
+    return [exact.exact_sum([b[i].q] + [-a.q * x[c].q for c, a in rows[i]], p)
+            for i in range(len(b))]
+
+
+def gpbicg(rows, b, x, p, mode, rtol, maxit):
+    """Returns (x, iterations, status, [(r_i, r_i)])."""
+    R = exact.rmul
+    A_ = exact.radd
+    S_ = exact.rsub
+    D = exact.rdiv
+    n = len(b)
+    Z = exact.Val(Fraction(0))
+    r = _residual(rows, b, x, p)
+    rt = list(r)
+    rr0 = _dot(r, r, p)
+    thr = _threshold(rr0, rtol, 0.0, p)
+    hist = []
+    if rr0.q <= thr.q:
+        return x, 0, "ok", hist
+    rho = _dot(rt, r, p)
+    u = [Z] * n
+    z = [Z] * n
+    s = [Z] * n
+    pv = q = t = v = w = y = None
+    beta = eta = Z
+    zeta = alpha = rho_prev = None
+    for i in range(1, maxit + 1):
+        if rho.q == 0:
+            return x, i - 1, "breakdown", hist
+        if i == 1:
+            pv = list(r)
+            q = _spmv(rows, pv, p, mode)
+            d = _dot(rt, q, p)
+            alpha = D(rho, d, p)
+            aq = [R(alpha, qk, p) for qk in q]
+            t = [S_(rk, a, p) for rk, a in zip(r, aq)]
+            y = [S_(a, rk, p) for rk, a in zip(r, aq)]
+            v = _spmv(rows, t, p, mode)
+            mu5 = _dot(v, v, p)
+            zeta = D(_dot(v, t, p), mu5, p) if mu5.q != 0 else Z
+            eta = Z
+        else:
+            beta = R(D(rho, rho_prev, p), D(alpha, zeta, p), p)
+            w = [A_(vk, R(beta, qk, p), p) for vk, qk in zip(v, q)]
+            pv = [A_(rk, R(beta, S_(pk, uk, p), p), p) for rk, pk, uk in zip(r, pv, u)]
+            q = _spmv(rows, pv, p, mode)
+            alpha = D(rho, _dot(rt, q, p), p)
+            s = [S_(tk, rk, p) for tk, rk in zip(t, r)]
+            t = [S_(rk, R(alpha, qk, p), p) for rk, qk in zip(r, q)]
+            v = _spmv(rows, t, p, mode)
+            y = [S_(sk, R(alpha, S_(wk, qk, p), p), p) for sk, wk, qk in zip(s, w, q)]
+            mu1, mu2, mu3 = _dot(y, y, p), _dot(v, t, p), _dot(y, t, p)
+            mu4, mu5 = _dot(v, y, p), _dot(v, v, p)
+            tau = S_(R(mu5, mu1, p), R(mu4, mu4, p), p)
+            if tau.q == 0:
+                zeta = eta = Z
+            else:
+                zeta = D(S_(R(mu1, mu2, p), R(mu3, mu4, p), p), tau, p)
+                eta = D(S_(R(mu5, mu3, p), R(mu4, mu2, p), p), tau, p)
+        u = [A_(R(zeta, qk, p), R(eta, A_(sk, R(beta, uk, p), p), p), p)
+             for qk, sk, uk in zip(q, s, u)]
+        z = [S_(A_(R(zeta, rk, p), R(eta, zk, p), p), R(alpha, uk, p), p)
+             for rk, zk, uk in zip(r, z, u)]
+        x = [A_(A_(xk, R(alpha, pk, p), p), zk, p) for xk, pk, zk in zip(x, pv, z)]
+        r = [S_(S_(tk, R(eta, yk, p), p), R(zeta, vk, p), p) for tk, yk, vk in zip(t, y, v)]
+        rr = _dot(r, r, p)
+        hist.append(rr)
+        rho_prev, rho = rho, _dot(rt, r, p)
+        if rr.q <= thr.q:
+            return x, i, "ok", hist
+        if zeta.q == 0:
+            return x, i, "breakdown", hist
+    return x, maxit, "noconv", hist
+
+
+def bicg(rows, rows_t, b, x, p, mode, rtol, maxit):
+    R = exact.rmul
+    A_ = exact.radd
+    S_ = exact.rsub
+    D = exact.rdiv
+    r = _residual(rows, b, x, p)
+    rt = list(r)
+    rr0 = _dot(r, r, p)
+    thr = _threshold(rr0, rtol, 0.0, p)
+    hist = []
+    if rr0.q <= thr.q:
+        return x, 0, "ok", hist
+    rho = _dot(rt, r, p)
+    pv = pt = rho_prev = None
+    for i in range(1, maxit + 1):
+        if rho.q == 0:
+            return x, i - 1, "breakdown", hist
+        if i == 1:
+            pv, pt = list(r), list(rt)
+        else:
+            beta = D(rho, rho_prev, p)
+            pv = [A_(rk, R(beta, pk, p), p) for rk, pk in zip(r, pv)]
+            pt = [A_(rk, R(beta, pk, p), p) for rk, pk in zip(rt, pt)]
+        z = _spmv(rows, pv, p, mode)
+        zt = _spmv(rows_t, pt, p, mode)
+        alpha = D(rho, _dot(pt, z, p), p)
+        x = [A_(xk, R(alpha, pk, p), p) for xk, pk in zip(x, pv)]
+        r = [S_(rk, R(alpha, zk, p), p) for rk, zk in zip(r, z)]
+        rt = [S_(rk, R(alpha, zk, p), p) for rk, zk in zip(rt, zt)]
+        rr = _dot(r, r, p)
+        hist.append(rr)
+        rho_prev, rho = rho, _dot(rt, r, p)
+        if rr.q <= thr.q:
+            return x, i, "ok", hist
+    return x, maxit, "noconv", hist
