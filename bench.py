@@ -1,0 +1,438 @@
+#!/usr/bin/env python
+"""Benchmark: p-bit CSR SpMV throughput (Gnnz/s) against its roofline.
+
+Workload (the SpMV throughput sweep): a synthetic n = 10^6 nonsymmetric
+sparse matrix, seed 1, lognormal row lengths (mean 16, max 256), columns in
+a +-5000 band around the diagonal with 10 % uniform far entries, values with
+random sign, mantissa in [1, 2) and exponent in [-40, 40], 1 % exact zeros;
+x with no zeros.  One step = y = A x in ORDERED and EXACT mode at p = 128,
+256, 512 and 1024 bits (8 products over 4 resident matrices).  The matrices
+(>= 448 MB each) are larger than L2, so no flush is needed between steps.
+
+value      = stored nonzeros processed per second over the timed steps
+             (all ranks), in Gnnz/s.
+e2e        = the same metric through the public API with x copied from
+             pinned host memory and y copied back every product.
+roofline   = the dominant product (largest share of the step): algorithmic
+             bytes (values, column indices, row pointers, x once, y once) at
+             the measured HBM peak vs its 32x32->64 multiply count at the
+             integer-multiply peak; the slower of the two is the bound.
+cpu_baseline = the oracle (plain C, one thread) on a bounded row sample.
+
+--impl reference times the oracle alone (the CPU reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MODES = (("ordered", 0), ("exact", 1))
+METRIC = "p-bit CSR SpMV Gnnz/s vs roofline"
+CONFIG_NAME = "spmv_sweep_n1e6_lognormal16_band5000_p128-1024"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=("native", "reference"))
+    ap.add_argument("--precs", default="128,256,512,1024")
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="oracle time budget of the CPU baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-solver", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def algorithmic(n, nnz, products, p):
+    """Bytes and 32x32->64 multiplies of one y = A x."""
+    L = p // 64
+    nbytes = nnz * (8 * L + 12) + n * 8 + 2 * n * (8 * L + 8)
+    imads = products * (p // 32) ** 2
+    return nbytes, imads
+
+
+class ClockSampler:
+    """nvidia-smi sampled every 50 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu=timestamp,{self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "50"], stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        self.t0 = time.time()
+
+    def stop(self):
+        self.t1 = time.time()
+        if self.proc is not None:
+            time.sleep(0.12)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [ln.strip().split(", ") for ln in self.file if ln.count(",") >= 9]
+        os.unlink(self.file.name)
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            try:
+                sm.append(float(r[2]))
+                mx = float(r[3])
+            except ValueError:
+                continue
+            for name, v in zip(names, r[6:10]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(rowptr, colidx, values, xs, precs, budget_s):
+    """Times the oracle on leading row ranges of every (p, mode), about
+    budget_s seconds in total; returns (nnz, seconds, description)."""
+    import oracle
+    from paper_1411_2377_gb300 import synth
+
+    per = budget_s / (len(precs) * len(MODES))
+    tot_nnz, tot_t, parts = 0, 0.0, []
+    for p in precs:
+        vrec = values[p]
+        xr = synth.planes_to_records(xs[p])
+        for name, m in MODES:
+            rows = 64
+            while True:  # calibrate on a small range, then size the sample
+                e = int(rowptr[rows])
+                t0 = time.perf_counter()
+                _sample(oracle, p, m, rowptr, colidx, vrec, xr, rows)
+                dt = time.perf_counter() - t0
+                if dt > 0.05 or rows >= len(rowptr) - 1:
+                    break
+                rows = min(rows * 4, len(rowptr) - 1)
+            rate = e / max(dt, 1e-9)
+            want = int(rate * per)
+            rows2 = int(np.searchsorted(rowptr, want))
+            rows2 = max(1, min(rows2, len(rowptr) - 1))
+            t0 = time.perf_counter()
+            _sample(oracle, p, m, rowptr, colidx, vrec, xr, rows2)
+            dt = time.perf_counter() - t0
+            nn = int(rowptr[rows2])
+            tot_nnz += nn
+            tot_t += dt
+            parts.append(f"p{p}/{name}:{rows2}rows/{nn}nnz")
+    return tot_nnz, tot_t, "oracle, 1 thread, leading rows of the workload: " + ", ".join(parts)
+
+
+def _sample(oracle, p, mode, rowptr, colidx, vrec, xr, rows):
+    e = int(rowptr[rows])
+    rp = np.concatenate([rowptr[: rows + 1], np.full(len(rowptr) - rows - 1, e, np.int64)])
+    L1 = p // 64 + 1
+    vals = np.ascontiguousarray(vrec[:, :e].T)
+    assert vals.shape == (e, L1)
+    y, st = oracle.spmv(p, mode, rp, colidx[:e], vals, xr, rows=(0, rows))
+    assert st == oracle.OK
+
+
+def build_workload(n, precs, on_gpu=True):
+    from paper_1411_2377_gb300 import synth
+
+    t0 = time.time()
+    rowptr, colidx = synth.spmv_pattern(n)
+    values, xs = {}, {}
+    for p in precs:
+        values[p], xs[p] = synth.spmv_values(p, len(colidx), n)
+    return rowptr, colidx, values, xs, time.time() - t0
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    from oracle.build import build_oracle
+
+    build_oracle()
+    precs = [int(p) for p in args.precs.split(",")]
+    rowptr, colidx, values, xs, _ = build_workload(args.n, precs)
+    per_step = max(0.5, min(12.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_sample(rowptr, colidx, values, xs, precs, per_step / 4)
+    nnz_tot, t_tot, desc = 0, 0.0, ""
+    for _ in range(args.steps):
+        nn, dt, desc = oracle_sample(rowptr, colidx, values, xs, precs, per_step)
+        nnz_tot += nn
+        t_tot += dt
+    value = nnz_tot / t_tot / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Gnnz/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_tot / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64 limbs (p-bit RN)", "data": "synthetic",
+        "config": {"workload": CONFIG_NAME, "n": args.n, "precs": precs,
+                   "modes": [m for m, _ in MODES]},
+        "cpu_baseline": {"value": value, "unit": "Gnnz/s", "cores": 1, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": "Gnnz/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_native(args):
+    import torch
+
+    world, rank, local = dist_setup(args)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1411_2377_gb300 as mpk
+    from paper_1411_2377_gb300 import _lib
+
+    lib = _lib.load()
+    precs = [int(p) for p in args.precs.split(",")]
+    n = args.n
+    rowptr, colidx, values, xs, gen_s = build_workload(n, precs)
+    nnz = len(colidx)
+    mats, xv, yv, products = {}, {}, {}, {}
+    for p in precs:
+        heads = values[p][0].view(np.int64) >> 1
+        products[p] = int(np.count_nonzero(heads != mpk.EXP_ZERO))
+        mats[p] = mpk.CSR(rowptr, colidx, values[p], p)
+        xv[p] = mpk.Vec.from_planes(xs[p], p)
+        yv[p] = mpk.Vec.empty(n, p)
+    slots = {p: mats[p].info()["slots"] for p in precs}
+    stream = torch.cuda.current_stream()
+    sptr = ctypes.c_void_p(stream.cuda_stream)
+
+    def step(events=None):
+        for p in precs:
+            A, x, y = mats[p], xv[p].c(), yv[p].c()
+            for name, m in MODES:
+                if events is not None:
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                st = lib.mp_spmv(A.h, x, y, m, sptr)
+                if st:
+                    raise mpk.MPError(st, "mp_spmv")
+                if events is not None:
+                    e1.record(stream)
+                    events[(p, name)].append((e0, e1))
+
+    for _ in range(args.warmup):
+        step()
+    mpk.check()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    events = {(p, name): [] for p in precs for name, _ in MODES}
+    sampler = ClockSampler(local if "CUDA_VISIBLE_DEVICES" not in os.environ else
+                           os.environ["CUDA_VISIBLE_DEVICES"].split(",")[local])
+    barrier()
+    sampler.start()
+    mpk.launch_count(reset=True)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step(events)
+    t1.record(stream)
+    barrier()
+    launches = mpk.launch_count(reset=True)
+    clocks = sampler.stop()
+    mpk.check()
+    total_ms = t0.elapsed_time(t1)
+    if world > 1:
+        import torch.distributed as dist
+
+        tt = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    units = args.steps * nnz * len(precs) * len(MODES) * world
+    value = units / (total_ms * 1e-3) / 1e9
+
+    peaks, peak_src = measured_peaks()
+    props = torch.cuda.get_device_properties(local)
+    sms = props.multi_processor_count
+    max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    # 64 32-bit IMAD results per clock per SM (CUDA C Programming Guide
+    # throughput table); a 32x32->64 IMAD.WIDE yields two of them.
+    imad_peak = sms * 32 * max_mhz * 1e6
+    probe = mpk.imad_probe()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+
+    kernels = []
+    for p in precs:
+        for name, _ in MODES:
+            ts = [a.elapsed_time(b) for a, b in events[(p, name)]]
+            avg_ms = sum(ts) / len(ts)
+            nbytes, imads = algorithmic(n, nnz, products[p], p)
+            t_hbm = nbytes / (hbm * 1e9)
+            t_alu = imads / imad_peak
+            bound = "alu" if t_alu > t_hbm else "hbm"
+            if bound == "hbm":
+                achieved, peak, unit = nbytes / (avg_ms * 1e-3) / 1e9, hbm, "GB/s"
+            else:
+                achieved, peak, unit = imads / (avg_ms * 1e-3) / 1e12, imad_peak / 1e12, "TIMAD/s"
+            kernels.append({"p": p, "mode": name, "ms": avg_ms,
+                            "gnnz_s": nnz / (avg_ms * 1e-3) / 1e9, "bound": bound,
+                            "achieved": achieved, "peak": peak, "unit": unit,
+                            "frac": achieved / peak, "bytes": nbytes, "imads": imads,
+                            "share": sum(ts) / total_ms})
+    dom = max(kernels, key=lambda k: k["ms"])
+    roofline = {"bound": dom["bound"], "achieved": dom["achieved"], "peak": dom["peak"],
+                "unit": dom["unit"], "frac": dom["frac"], "traffic": None,
+                "kernel": f"spmv_{dom['mode']}_kernel<p={dom['p']}>",
+                "peak_source": (f"{peak_src} hbm_gbs" if dom["bound"] == "hbm" else
+                                f"derived: {sms} SMs x 32 IMAD.WIDE/clk x {max_mhz:.0f} MHz")}
+
+    e2e = None
+    if not args.no_e2e:
+        hx = {p: xv[p].t.cpu().pin_memory() for p in precs}
+        hy = {p: torch.empty_like(yv[p].t, device="cpu").pin_memory() for p in precs}
+        h2d = sum(hx[p].numel() * 8 for p in precs) * len(MODES)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            for p in precs:
+                for name, _ in MODES:
+                    xv[p].t.copy_(hx[p], non_blocking=True)
+                    mpk.spmv(mats[p], xv[p], yv[p], mode=name, sync=False)
+                    hy[p].copy_(yv[p].t, non_blocking=True)
+        e1.record(stream)
+        barrier()
+        mpk.check()
+        ms = e0.elapsed_time(e1)
+        e2e = {"value": units / (ms * 1e-3) / 1e9, "unit": "Gnnz/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": h2d}
+
+    solver = None
+    if not args.no_solver and rank == 0:
+        solver = solver_bench(mpk)
+
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        from oracle.build import build_oracle
+
+        build_oracle()
+        nn, dt, desc = oracle_sample(rowptr, colidx, values, xs, precs, args.cpu_seconds)
+        cpu = {"value": nn / dt / 1e9, "unit": "Gnnz/s", "cores": 1, "kind": "oracle",
+               "sample": desc}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "Gnnz/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u64 limbs (p-bit RN)", "data": "synthetic",
+            "config": {"workload": CONFIG_NAME, "n": n, "nnz": nnz, "precs": precs,
+                       "modes": [m for m, _ in MODES], "slots": slots,
+                       "l2": "inputs larger than L2 (matrices >= 448 MB), no flush",
+                       "parallelism": f"replicas x{world}", "generate_s": round(gen_s, 1)},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clocks, "imad_probe_per_s": probe, "kernels": kernels, "solver": solver,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def solver_bench(mpk):
+    """GPBiCG and BiCG at 128 bits on the 64x64 convection-diffusion system,
+    b = A*ones, to relative residual 1e-30 (iterations, time on the stream)."""
+    from paper_1411_2377_gb300 import synth
+
+    p = 128
+    rowptr, colidx, v64 = synth.stencil2d(64, seed=0)
+    n = len(rowptr) - 1
+    A = mpk.CSR(rowptr, colidx, v64, p, transpose=True)
+    ones = mpk.Vec.from_f64(np.ones(n), p)
+    b = mpk.spmv(A, ones, mode="exact")
+    out = {"workload": "stencil2d_64x64_p128_rtol1e-30"}
+    for name, fn in (("gpbicg", mpk.gpbicg), ("bicg", mpk.bicg)):
+        fn(A, b, rtol=1e-30, maxit=2000, poll_every=32)  # warm-up
+        x, info = fn(A, b, rtol=1e-30, maxit=2000, poll_every=32)
+        err = float((x.to_f64() - 1).abs().max())
+        out[name] = {"iters": info["iters"], "status": info["status"], "ms": round(info["ms"], 3),
+                     "relres": info["relres"], "max_abs_err": err}
+    A.close()
+    return out
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,211 @@
+/* mpkrylov.h -- C ABI of the GB300 (sm_103a) multiple-precision sparse Krylov
+ * library: p-bit CSR sparse matrix-vector products y = A x and y = A^T x,
+ * exact dot products, axpy, and the BiCG and GPBiCG solvers built on them.
+ *
+ * The operations are those of Kouya, "A Highly Efficient Implementation of
+ * Multiple Precision Sparse Matrix-Vector Multiplication and Its Application
+ * to Product-type Krylov Subspace Methods": a CSR matrix whose entries carry
+ * `prec` bits (Section 2, the mpfrsmatrix structure), its SpMV (Section 3),
+ * and BiCG / GPBiCG with the SpMV in place of the matrix products (Section 4,
+ * Fig. 5), stopped by the residual rule of Section 4.
+ *
+ * Number format.  A value is (-1)^s * M * 2^(e-p) with 2^(p-1) <= M < 2^p
+ * (MPFR's 0.1xxx_2 * 2^e convention, Section 2), or a signed zero
+ * (e == MP_EXP_ZERO, M = 0).  p is one of 128, 256, 512, 1024.  Every
+ * operation rounds to nearest, ties to even (MPFR's RN); NaN, infinities and
+ * the other rounding modes are not represented.  Nonzero exponents must
+ * satisfy |e| < 2^60.
+ *
+ * Memory layout ("planes").  A vector of n values with L = p/64 is L+1
+ * planes of uint64 words: plane 0 holds the head words e*2 + s (as int64
+ * bit patterns), plane k (1 <= k <= L) holds mantissa limb k-1, least
+ * significant first.  Plane k starts ld words after plane k-1.  A scalar
+ * is a vector with n = 1.
+ *
+ * Conventions.  Every function returns an mp_status and never aborts.
+ * Device pointers are CUDA device memory of the current device; the library
+ * never frees memory it did not allocate.  `stream` is a cudaStream_t (NULL =
+ * the legacy default stream).  Work is enqueued asynchronously on the stream;
+ * argument errors are returned immediately, while data-dependent errors found
+ * by kernels (an exact sum whose exponent span exceeds MP_SPAN_CAP, a zero
+ * divisor) are recorded in a per-device status word read by mp_check().
+ * Calls that share an mp_csr handle or the per-device status word must be
+ * ordered on one stream.  There is no CPU fallback: without a usable GPU
+ * every compute call returns MP_ERR_CUDA.
+ */
+#ifndef MPKRYLOV_H
+#define MPKRYLOV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MP_OK = 0,
+  MP_ERR_ARG = 1,       /* invalid argument; mp_last_error() has the details */
+  MP_ERR_PREC = 2,      /* prec_bits not in {128, 256, 512, 1024}             */
+  MP_ERR_ALLOC = 3,     /* device or host allocation failed                    */
+  MP_ERR_CUDA = 4,      /* a CUDA call failed (no device, launch error, ...)   */
+  MP_ERR_SPAN = 5,      /* exact sum with exponent span > MP_SPAN_CAP          */
+  MP_ERR_BREAKDOWN = 6, /* Krylov breakdown (Fig. 5 "exits")                   */
+  MP_ERR_NOCONV = 7,    /* maxit reached (the paper's "NC", Tables 1-2)        */
+  MP_ERR_TIMEOUT = 8,   /* a bounded device wait gave up                       */
+  MP_ERR_DIVZERO = 9    /* elementwise division by zero                        */
+} mp_status;
+
+typedef enum {
+  MP_ORDERED = 0, /* each product and each sum rounded, in CSR column order   */
+  MP_EXACT = 1    /* each row summed exactly, rounded once                     */
+} mp_mode;
+
+typedef enum { MP_OP_MUL = 0, MP_OP_ADD = 1, MP_OP_SUB = 2, MP_OP_DIV = 3 } mp_op;
+
+#define MP_EXP_ZERO (-(INT64_C(1) << 61))
+/* Largest exponent span (max minus min term exponent e_a + e_x) of an exact
+ * sum (MP_EXACT rows, dot products, residuals). */
+#define MP_SPAN_CAP 16384
+
+/* mp_csr_create flags */
+#define MP_CSR_TRANSPOSE 1 /* also build A^T (needed by mp_spmv_t and mp_bicg) */
+
+typedef struct mp_csr_s* mp_csr; /* opaque; owns its device storage */
+
+typedef struct {
+  int64_t n;          /* number of values                          */
+  int32_t prec_bits;  /* p                                          */
+  int64_t ld;         /* words between consecutive planes, >= n     */
+  uint64_t* data;     /* device pointer to plane 0 (caller-owned)   */
+} mp_vec;
+
+/* ---- matrices ----------------------------------------------------------- */
+
+/* Builds a device matrix from a host CSR matrix (Section 2's sparse storage:
+ * per-row column indices and the nonzero values at precision prec_bits).
+ *   n        rows = columns, 0 <= n < 2^31
+ *   rowptr   host, n+1 entries, rowptr[0] = 0, nondecreasing
+ *   colidx   host, rowptr[n] entries in [0, n); a row may list its columns
+ *            in any order but not twice (the ORDERED sum runs in ascending
+ *            column order)
+ *   values   host planes, (L+1) * rowptr[n] words: plane k at values + k*nnz
+ *   flags    MP_CSR_TRANSPOSE to build A^T as well
+ * The host arrays are copied; the caller may free them on return.  The
+ * device copy is a sliced, row-length-sorted layout of the same rows (see
+ * mp_csr_info).  Returns MP_ERR_ARG for a malformed matrix or value, with the
+ * offending row in mp_last_error(). */
+mp_status mp_csr_create(int64_t n, const int64_t* rowptr, const int32_t* colidx,
+                        const uint64_t* values, int32_t prec_bits, int32_t flags,
+                        void* stream, mp_csr* out);
+
+/* As mp_csr_create with double-precision host values, each converted exactly
+ * to prec_bits (53 <= p; Section 4 converts the UF matrices this way).
+ * NaN or infinite values give MP_ERR_ARG. */
+mp_status mp_csr_create_f64(int64_t n, const int64_t* rowptr, const int32_t* colidx,
+                            const double* values, int32_t prec_bits, int32_t flags,
+                            void* stream, mp_csr* out);
+
+/* Frees the matrix (waits for work queued on it to finish). */
+mp_status mp_csr_destroy(mp_csr A);
+
+/* Sizes of a matrix: rows, stored entries, precision, slots of the sliced
+ * layout (stored entries plus padding) and device bytes held. Any pointer
+ * may be NULL. */
+mp_status mp_csr_info(mp_csr A, int64_t* n, int64_t* nnz, int32_t* prec_bits,
+                      int64_t* slots, int64_t* device_bytes);
+
+/* ---- products ------------------------------------------------------------ */
+
+/* y = A x (Section 3's SpMV).  MP_ORDERED: y_i = +0, then for each stored
+ * a_ik in ascending column order with a_ik != 0 and x_k != 0 (the zero fast
+ * path of Section 2), y_i = RN(y_i + RN(a_ik * x_k)).  MP_EXACT: y_i =
+ * RN(sum_k a_ik x_k) with the sum formed exactly (zero terms skipped, an
+ * exact zero is +0); a row whose term exponents span more than MP_SPAN_CAP
+ * bits becomes +0 and records MP_ERR_SPAN.  x, y: n values at the matrix
+ * precision, distinct storage. */
+mp_status mp_spmv(mp_csr A, mp_vec x, mp_vec y, mp_mode mode, void* stream);
+
+/* y = A^T x (BiCG's shadow product, Fig. 5); row j of A^T lists the rows i
+ * of A with a stored a_ij in ascending i, which is the ORDERED order.
+ * Requires MP_CSR_TRANSPOSE at creation. */
+mp_status mp_spmv_t(mp_csr A, mp_vec x, mp_vec y, mp_mode mode, void* stream);
+
+/* r_i = RN(b_i - sum_k a_ik x_k), summed exactly and rounded once (the
+ * initial residual r0 = b - A x0 of Fig. 5). */
+mp_status mp_residual(mp_csr A, mp_vec b, mp_vec x, mp_vec r, void* stream);
+
+/* ---- vectors ------------------------------------------------------------- */
+
+/* out = RN(sum_i x_i y_i) formed exactly and rounded once (the inner
+ * products of Fig. 5); zero pairs are skipped, an exact zero is +0.  out is
+ * a device scalar (n = 1).  Uses a per-device scratch buffer allocated on
+ * first use. */
+mp_status mp_dot(mp_vec x, mp_vec y, mp_vec out, void* stream);
+
+/* y_i = RN(y_i + RN(alpha * x_i)); alpha a device scalar. */
+mp_status mp_axpy(mp_vec alpha, mp_vec x, mp_vec y, void* stream);
+
+/* out_i = RN(a_i op b_i) for op in mp_op.  A zero divisor gives +0 and
+ * records MP_ERR_DIVZERO.  out may alias a or b. */
+mp_status mp_ewise(int32_t op, mp_vec a, mp_vec b, mp_vec out, void* stream);
+
+/* Exact conversion of n device doubles into a vector (53 <= p). */
+mp_status mp_vec_from_f64(const double* d, mp_vec out, void* stream);
+
+/* Nearest double of each value (reporting only). */
+mp_status mp_vec_to_f64(mp_vec a, double* d, void* stream);
+
+/* ---- solvers (Fig. 5, left preconditioner K = I) ------------------------- */
+
+typedef struct {
+  double rtol;       /* stop when (r,r) <= RN(RN(rtol^2)*(r0,r0)) + RN(atol^2) */
+  double atol;
+  int64_t maxit;     /* iteration limit ("NC" beyond it)                        */
+  int32_t mode;      /* mp_mode used for the SpMVs                              */
+  int32_t poll_every;/* iterations between host checks of the device flags (>=1)*/
+  mp_vec history;    /* optional (data may be NULL): entry i-1 receives (r_i,r_i) */
+} mp_solve_opts;
+
+typedef struct {
+  int64_t iters;  /* completed iterations                                   */
+  int32_t status; /* MP_OK (converged), MP_ERR_NOCONV or MP_ERR_BREAKDOWN   */
+  double relres;  /* sqrt((r,r)/(r0,r0)) of the last iterate, as a double    */
+  double ms;      /* wall time of the solve on the stream                    */
+} mp_solve_info;
+
+/* BiCG (Fig. 5 left).  x holds x0 on entry and the last iterate on return.
+ * The iteration runs on the device; the host reads a few status bytes every
+ * poll_every iterations.  Returns info->status.  Needs MP_CSR_TRANSPOSE. */
+mp_status mp_bicg(mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* opts,
+                  mp_solve_info* info, void* stream);
+
+/* GPBiCG (Fig. 5 right, Zhang's method: z = zeta r + eta z - alpha u and
+ * r = t - eta y - zeta A t). */
+mp_status mp_gpbicg(mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* opts,
+                    mp_solve_info* info, void* stream);
+
+/* ---- status -------------------------------------------------------------- */
+
+/* Waits for `stream`, then returns and clears the device-side status word of
+ * the current device (MP_OK if no kernel recorded an error). */
+mp_status mp_check(void* stream);
+
+const char* mp_status_string(mp_status s);
+
+/* Details of the last error returned on the calling thread. */
+const char* mp_last_error(void);
+
+/* Kernels launched by this library on the calling thread since the counter
+ * was last reset (reset = 1 clears it after reading). */
+int64_t mp_launch_count(int32_t reset);
+
+/* Throughput probe of the 32x32->64-bit multiply-add that the p-bit products
+ * are made of: runs a dependency-free IMAD.WIDE.U32 loop on every SM and
+ * returns the products per second through *rate.  Used for the roofline of
+ * the integer-bound kernels. */
+mp_status mp_imad_probe(double* rate, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,267 @@
+"""paper_1411_2377_gb300 -- p-bit CSR SpMV, exact dot products and the BiCG /
+GPBiCG solvers of Kouya's multiple-precision sparse Krylov paper, on GB300.
+
+The compute path is the native library libmpkrylov.so (hand-written sm_103a
+CUDA behind a C ABI, include/mpkrylov.h); this module only marshals
+arguments.  PyTorch provides device memory and the current stream.
+
+Vectors (:class:`Vec`) hold p-bit values as ``L+1`` planes of 64-bit words
+(``L = p // 64``) in a ``torch.int64`` CUDA tensor of shape ``(L+1, n)``:
+plane 0 the head words ``exp*2 + sign``, planes 1..L the mantissa limbs,
+least significant first.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import (EXP_ZERO, MP_EXACT, MP_OP_ADD, MP_OP_DIV, MP_OP_MUL, MP_OP_SUB,  # noqa: F401
+                   MP_ORDERED, SPAN_CAP)
+
+__all__ = ["MPError", "Vec", "CSR", "spmv", "spmv_t", "residual", "dot", "axpy", "ewise",
+           "bicg", "gpbicg", "check", "launch_count", "imad_probe", "MODES"]
+
+MODES = {"ordered": MP_ORDERED, "exact": MP_EXACT, MP_ORDERED: MP_ORDERED, MP_EXACT: MP_EXACT}
+
+
+class MPError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        lib = _lib.load()
+        msg = lib.mp_status_string(status).decode()
+        detail = lib.mp_last_error().decode()
+        super().__init__(f"{where}: {msg} ({detail})")
+        self.status = status
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ok(status: int, where: str):
+    if status != 0:
+        raise MPError(status, where)
+
+
+def check(stream=None):
+    """Waits for the stream and raises if a kernel recorded an error."""
+    _ok(_lib.load().mp_check(_stream(stream)), "device status")
+
+
+def launch_count(reset: bool = False) -> int:
+    return int(_lib.load().mp_launch_count(1 if reset else 0))
+
+
+def imad_probe(stream=None) -> float:
+    """32x32->64 multiply-adds per second measured on the current GPU."""
+    rate = ctypes.c_double(0.0)
+    _ok(_lib.load().mp_imad_probe(ctypes.byref(rate), _stream(stream)), "mp_imad_probe")
+    return rate.value
+
+
+class Vec:
+    """n p-bit values on the GPU (planes of a (L+1, n) int64 tensor)."""
+
+    def __init__(self, tensor, prec: int):
+        torch = _torch()
+        L = prec // 64
+        assert tensor.dtype == torch.int64 and tensor.dim() == 2 and tensor.shape[0] == L + 1
+        assert tensor.is_cuda and tensor.stride(1) == 1
+        self.t = tensor
+        self.prec = prec
+
+    @property
+    def n(self) -> int:
+        return int(self.t.shape[1])
+
+    def c(self) -> _lib.MpVec:
+        ld = self.t.stride(0) if self.n > 0 else max(self.n, 1)
+        return _lib.MpVec(self.n, self.prec, max(ld, self.n), self.t.data_ptr())
+
+    @classmethod
+    def empty(cls, n: int, prec: int, device="cuda"):
+        torch = _torch()
+        return cls(torch.empty((prec // 64 + 1, n), dtype=torch.int64, device=device), prec)
+
+    @classmethod
+    def zeros(cls, n: int, prec: int, device="cuda"):
+        v = cls.empty(n, prec, device)
+        v.t.zero_()
+        v.t[0].fill_(EXP_ZERO * 2)
+        return v
+
+    @classmethod
+    def from_planes(cls, planes: np.ndarray, prec: int, device="cuda"):
+        torch = _torch()
+        a = np.ascontiguousarray(planes, dtype=np.uint64).view(np.int64)
+        return cls(torch.from_numpy(a).to(device), prec)
+
+    @classmethod
+    def from_f64(cls, d, prec: int, stream=None):
+        """Exact conversion of doubles (a CUDA float64 tensor or array)."""
+        torch = _torch()
+        d = torch.as_tensor(d, dtype=torch.float64).to("cuda").contiguous()
+        v = cls.empty(d.numel(), prec)
+        _ok(_lib.load().mp_vec_from_f64(ctypes.c_void_p(d.data_ptr()), v.c(), _stream(stream)),
+            "mp_vec_from_f64")
+        check(stream)
+        return v
+
+    def to_f64(self, stream=None):
+        torch = _torch()
+        d = torch.empty(self.n, dtype=torch.float64, device=self.t.device)
+        _ok(_lib.load().mp_vec_to_f64(self.c(), ctypes.c_void_p(d.data_ptr()), _stream(stream)),
+            "mp_vec_to_f64")
+        return d
+
+    def planes(self) -> np.ndarray:
+        """(L+1, n) uint64 planes on the host."""
+        return self.t.cpu().numpy().view(np.uint64)
+
+    def records(self) -> np.ndarray:
+        """(n, L+1) uint64 records (value-major) on the host."""
+        return np.ascontiguousarray(self.planes().T)
+
+    def clone(self):
+        return Vec(self.t.clone(), self.prec)
+
+
+class CSR:
+    """A p-bit CSR matrix resident on the GPU (Section 2's sparse storage)."""
+
+    def __init__(self, rowptr, colidx, values, prec: int, transpose: bool = False, stream=None):
+        """values: (L+1, nnz) uint64 planes, or float64 values (converted
+        exactly to p bits)."""
+        lib = _lib.load()
+        rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+        colidx = np.ascontiguousarray(colidx, dtype=np.int32)
+        n = rowptr.shape[0] - 1
+        handle = ctypes.c_void_p()
+        flags = _lib.MP_CSR_TRANSPOSE if transpose else 0
+        values = np.asarray(values)
+        if values.dtype == np.float64:
+            vals = np.ascontiguousarray(values)
+            st = lib.mp_csr_create_f64(n, rowptr.ctypes.data, colidx.ctypes.data,
+                                       vals.ctypes.data, prec, flags, _stream(stream),
+                                       ctypes.byref(handle))
+        else:
+            vals = np.ascontiguousarray(values, dtype=np.uint64)
+            assert vals.shape == (prec // 64 + 1, colidx.shape[0]), vals.shape
+            st = lib.mp_csr_create(n, rowptr.ctypes.data, colidx.ctypes.data, vals.ctypes.data,
+                                   prec, flags, _stream(stream), ctypes.byref(handle))
+        _ok(st, "mp_csr_create")
+        self.h = handle
+        self.n = n
+        self.nnz = int(rowptr[-1])
+        self.prec = prec
+        self.transpose = transpose
+
+    def info(self) -> dict:
+        n, nnz, slots, nbytes = (ctypes.c_int64() for _ in range(4))
+        p = ctypes.c_int32()
+        _ok(_lib.load().mp_csr_info(self.h, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(p),
+                                    ctypes.byref(slots), ctypes.byref(nbytes)), "mp_csr_info")
+        return {"n": n.value, "nnz": nnz.value, "prec": p.value, "slots": slots.value,
+                "device_bytes": nbytes.value}
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            _lib.load().mp_csr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def spmv(A: CSR, x: Vec, y: Vec | None = None, mode="ordered", stream=None, sync=True) -> Vec:
+    """y = A x (Section 3)."""
+    y = y if y is not None else Vec.empty(A.n, A.prec)
+    _ok(_lib.load().mp_spmv(A.h, x.c(), y.c(), MODES[mode], _stream(stream)), "mp_spmv")
+    if sync:
+        check(stream)
+    return y
+
+
+def spmv_t(A: CSR, x: Vec, y: Vec | None = None, mode="ordered", stream=None, sync=True) -> Vec:
+    """y = A^T x (needs ``transpose=True`` at creation)."""
+    y = y if y is not None else Vec.empty(A.n, A.prec)
+    _ok(_lib.load().mp_spmv_t(A.h, x.c(), y.c(), MODES[mode], _stream(stream)), "mp_spmv_t")
+    if sync:
+        check(stream)
+    return y
+
+
+def residual(A: CSR, b: Vec, x: Vec, r: Vec | None = None, stream=None, sync=True) -> Vec:
+    """r = RN(b - A x), each row summed exactly."""
+    r = r if r is not None else Vec.empty(A.n, A.prec)
+    _ok(_lib.load().mp_residual(A.h, b.c(), x.c(), r.c(), _stream(stream)), "mp_residual")
+    if sync:
+        check(stream)
+    return r
+
+
+def dot(x: Vec, y: Vec, out: Vec | None = None, stream=None, sync=True) -> Vec:
+    """RN(sum x_i y_i), exact sum rounded once; returns a 1-element Vec."""
+    out = out if out is not None else Vec.empty(1, x.prec)
+    _ok(_lib.load().mp_dot(x.c(), y.c(), out.c(), _stream(stream)), "mp_dot")
+    if sync:
+        check(stream)
+    return out
+
+
+def axpy(alpha: Vec, x: Vec, y: Vec, stream=None, sync=True) -> Vec:
+    """y <- RN(y + RN(alpha x)) in place."""
+    _ok(_lib.load().mp_axpy(alpha.c(), x.c(), y.c(), _stream(stream)), "mp_axpy")
+    if sync:
+        check(stream)
+    return y
+
+
+def ewise(op: int, a: Vec, b: Vec, out: Vec | None = None, stream=None, sync=True) -> Vec:
+    out = out if out is not None else Vec.empty(a.n, a.prec)
+    _ok(_lib.load().mp_ewise(op, a.c(), b.c(), out.c(), _stream(stream)), "mp_ewise")
+    if sync:
+        check(stream)
+    return out
+
+
+def _solve(fn, name, A, b, x0, rtol, atol, maxit, mode, poll_every, history, stream):
+    x = x0.clone() if x0 is not None else Vec.zeros(A.n, A.prec)
+    hist = Vec.empty(max(maxit, 1), A.prec) if history else None
+    opts = _lib.MpSolveOpts(float(rtol), float(atol), int(maxit), MODES[mode], int(poll_every),
+                            hist.c() if hist is not None else _lib.MpVec(0, A.prec, 1, None))
+    info = _lib.MpSolveInfo()
+    st = fn(A.h, b.c(), x.c(), ctypes.byref(opts), ctypes.byref(info), _stream(stream))
+    if st not in (0, _lib.MP_ERR_NOCONV, _lib.MP_ERR_BREAKDOWN):
+        raise MPError(st, name)
+    res = {"iters": int(info.iters), "status": int(info.status), "relres": float(info.relres),
+           "ms": float(info.ms)}
+    if hist is not None:
+        res["history"] = Vec(hist.t[:, : max(int(info.iters), 0)].contiguous(), A.prec)
+    return x, res
+
+
+def bicg(A: CSR, b: Vec, x0: Vec | None = None, rtol=1e-30, atol=0.0, maxit=1000,
+         mode="ordered", poll_every=8, history=False, stream=None):
+    """BiCG (Fig. 5 left, K = I).  Returns (x, info dict)."""
+    return _solve(_lib.load().mp_bicg, "mp_bicg", A, b, x0, rtol, atol, maxit, mode,
+                  poll_every, history, stream)
+
+
+def gpbicg(A: CSR, b: Vec, x0: Vec | None = None, rtol=1e-30, atol=0.0, maxit=1000,
+           mode="ordered", poll_every=8, history=False, stream=None):
+    """GPBiCG (Fig. 5 right).  Returns (x, info dict)."""
+    return _solve(_lib.load().mp_gpbicg, "mp_gpbicg", A, b, x0, rtol, atol, maxit, mode,
+                  poll_every, history, stream)

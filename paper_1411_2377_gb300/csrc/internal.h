@@ -1,0 +1,103 @@
+// internal.h -- host-side internals shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <type_traits>
+
+#include "mpkrylov.h"
+
+namespace mpk {
+
+// Sliced, row-length-sorted layout of a CSR matrix (SELL-32-sigma).  Rows are
+// sorted by length (descending, ties by row index) inside windows of
+// kSigma rows and packed 32 per chunk; chunk c holds its rows' entries
+// column-major, slot chunk_off[c] + j*32 + lane for the j-th entry of the
+// lane's row, so that a warp reading entry j of 32 rows touches 32
+// consecutive slots.  Each row keeps its CSR column order.
+constexpr int kSigma = 4096;
+
+struct Sell {
+  int64_t n = 0, nnz = 0, nslots = 0, nchunks = 0;
+  int64_t* chunk_off = nullptr;  // [nchunks + 1]
+  int32_t* row_of = nullptr;     // [nchunks * 32], original row or -1
+  int32_t* row_len = nullptr;    // [nchunks * 32]
+  int32_t* col = nullptr;        // [nslots]
+  uint64_t* val = nullptr;       // [(L+1) * nslots], plane-major
+};
+
+}  // namespace mpk
+
+struct mp_csr_s {
+  int64_t n = 0, nnz = 0;
+  int32_t prec = 0;
+  int device = 0;
+  bool has_t = false;
+  mpk::Sell A, AT;
+  int32_t* ovf = nullptr;  // [n + 1]: overflow-row count then rows (EXACT wide path)
+  int64_t bytes = 0;
+};
+
+namespace mpk {
+
+// ---- errors -------------------------------------------------------------
+mp_status set_error(mp_status s, const char* fmt, ...);
+mp_status cuda_error(cudaError_t e, const char* where);
+#define MPK_CUDA(call)                                              \
+  do {                                                              \
+    cudaError_t e_ = (call);                                        \
+    if (e_ != cudaSuccess) return ::mpk::cuda_error(e_, #call);     \
+  } while (0)
+
+// ---- device status word and launch accounting ---------------------------
+int* status_word();  // device address of the current device's status word
+void count_launch(int k = 1);
+mp_status launch_check(const char* what);  // cudaGetLastError after a launch
+
+// ---- precision ------------------------------------------------------------
+inline bool prec_ok(int p) { return p == 128 || p == 256 || p == 512 || p == 1024; }
+inline int planes_of(int p) { return p / 64 + 1; }
+
+mp_status check_vec(const mp_vec& v, int64_t n, int prec, const char* name);
+
+// Calls f(std::integral_constant<int, W>{}) with W = p/32 words.
+template <class F>
+mp_status dispatch_w(int p, F&& f) {
+  switch (p) {
+    case 128: return f(std::integral_constant<int, 4>{});
+    case 256: return f(std::integral_constant<int, 8>{});
+    case 512: return f(std::integral_constant<int, 16>{});
+    case 1024: return f(std::integral_constant<int, 32>{});
+    default: return set_error(MP_ERR_PREC, "precision %d not in {128,256,512,1024}", p);
+  }
+}
+
+// ---- scratch ---------------------------------------------------------------
+// Per-device scratch of the standalone dot product (grown on demand).
+void* dot_scratch(size_t bytes);
+
+// ---- kernels exported across translation units ----------------------------
+// Exact dot products: k pairs (x[j], y[j]) of length n -> out[j] (device
+// scalars, plane-major with ld 1 each, may point into a larger buffer).
+struct DotArgs {
+  int k = 0;
+  int64_t n = 0;
+  const uint64_t* x[5] = {};
+  const uint64_t* y[5] = {};
+  int64_t ldx[5] = {}, ldy[5] = {};
+  uint64_t* out[5] = {};  // plane-major scalars with ld = out_ld[j]
+  int64_t out_ld[5] = {};
+};
+size_t dot_scratch_bytes(int prec, int k);
+mp_status launch_dot(int prec, const DotArgs& a, void* scratch, const int* gate,
+                     cudaStream_t st);
+
+// SpMV / residual on a sliced matrix.  resid_b != nullptr computes
+// r = RN(b - A x) (EXACT only).  gate: device flag; when nonzero at run time
+// the kernels return without work (used by the solvers after convergence).
+mp_status launch_spmv(const mp_csr_s* M, const Sell& S, int mode, const uint64_t* x, int64_t ldx,
+                      uint64_t* y, int64_t ldy, const uint64_t* resid_b, int64_t ldb,
+                      const int* gate, cudaStream_t st);
+
+}  // namespace mpk

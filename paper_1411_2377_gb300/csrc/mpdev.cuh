@@ -1,0 +1,528 @@
+// mpdev.cuh -- device-side p-bit floating-point arithmetic for sm_103a.
+//
+// A value is (-1)^s * M * 2^(e-p) with 2^(p-1) <= M < 2^p (the MPFR convention
+// 0.1xxx_2 * 2^e of the paper's Section 2), or a signed zero (e == EXP_ZERO).
+// In registers the mantissa is W = p/32 little-endian 32-bit words; in memory a
+// vector is plane-major: plane 0 holds head words e*2 + s, planes 1..L (L = W/2)
+// the 64-bit limbs, least significant first.
+//
+// Every operation rounds to nearest with ties to even (MPFR's RN).  All loops
+// over words have compile-time trip counts and are fully unrolled so the words
+// stay in registers; variable shifts are done by log-depth barrel stages of
+// predicated selects plus one funnel shift.
+#pragma once
+#include <cstdint>
+
+namespace mpk {
+
+constexpr int64_t EXP_ZERO = -(int64_t(1) << 61);
+constexpr int SPAN_CAP = 16384;  // largest exponent span an exact sum accepts
+
+template <int W>
+struct Num {
+  uint32_t m[W];
+  int64_t e;
+  uint32_t s;
+};
+
+__device__ __forceinline__ bool zero_e(int64_t e) { return e == EXP_ZERO; }
+
+__device__ __forceinline__ void unpack_head(uint64_t h, int64_t& e, uint32_t& s) {
+  const int64_t v = (int64_t)h;
+  s = (uint32_t)(v & 1);
+  e = v >> 1;  // arithmetic shift
+}
+
+__device__ __forceinline__ uint64_t pack_head(int64_t e, uint32_t s) {
+  return (uint64_t)(e * 2 + (int64_t)s);
+}
+
+template <int W>
+__device__ __forceinline__ void set_zero(Num<W>& r, uint32_t s) {
+#pragma unroll
+  for (int k = 0; k < W; ++k) r.m[k] = 0u;
+  r.e = EXP_ZERO;
+  r.s = s;
+}
+
+// ---------------------------------------------------------------------------
+// Memory <-> registers (plane-major vectors)
+// ---------------------------------------------------------------------------
+
+template <int W>
+__device__ __forceinline__ void load_limbs(uint32_t (&m)[W], const uint64_t* __restrict__ base,
+                                           int64_t ld, int64_t i) {
+#pragma unroll
+  for (int k = 0; k < W / 2; ++k) {
+    const uint64_t l = __ldg(base + (int64_t)(k + 1) * ld + i);
+    m[2 * k] = (uint32_t)l;
+    m[2 * k + 1] = (uint32_t)(l >> 32);
+  }
+}
+
+template <int W>
+__device__ __forceinline__ void load(Num<W>& a, const uint64_t* __restrict__ base, int64_t ld,
+                                     int64_t i) {
+  unpack_head(__ldg(base + i), a.e, a.s);
+  load_limbs<W>(a.m, base, ld, i);
+}
+
+template <int W>
+__device__ __forceinline__ void store(const Num<W>& a, uint64_t* __restrict__ base, int64_t ld,
+                                      int64_t i) {
+  base[i] = pack_head(a.e, a.s);
+#pragma unroll
+  for (int k = 0; k < W / 2; ++k)
+    base[(int64_t)(k + 1) * ld + i] = (uint64_t)a.m[2 * k] | ((uint64_t)a.m[2 * k + 1] << 32);
+}
+
+// ---------------------------------------------------------------------------
+// Word-array helpers
+// ---------------------------------------------------------------------------
+
+// m += inc (inc in {0,1}); a carry out of the top means M reached 2^p, which is
+// renormalised to 2^(p-1) with the exponent raised by one.
+template <int W>
+__device__ __forceinline__ void round_increment(uint32_t (&m)[W], int64_t& e, uint32_t inc) {
+  uint32_t c = inc;
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    const uint32_t t = m[k] + c;
+    c = (t < c) ? 1u : 0u;
+    m[k] = t;
+  }
+  if (c) {
+    m[W - 1] = 0x80000000u;
+    e += 1;
+  }
+}
+
+// Right shift of N words by sh bits (0 <= sh < 32*N + 32); returns the OR of
+// all bits shifted out (the sticky information).
+template <int N, int NS>
+__device__ __forceinline__ uint32_t shift_right_sticky(uint32_t (&x)[N], uint32_t sh) {
+  uint32_t sticky = 0u;
+  const uint32_t ws = sh >> 5, bs = sh & 31u;
+#pragma unroll
+  for (int st = 0; st < NS; ++st) {
+    const int b = 1 << st;
+    const bool on = (ws >> st) & 1u;
+    uint32_t lost = 0u;
+#pragma unroll
+    for (int k = 0; k < b && k < N; ++k) lost |= x[k];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const uint32_t src = (k + b < N) ? x[k + b] : 0u;
+      x[k] = on ? src : x[k];
+    }
+    sticky |= on ? lost : 0u;
+  }
+  sticky |= (bs != 0u) ? (x[0] << (32u - bs)) : 0u;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const uint32_t hi = (k + 1 < N) ? x[k + 1] : 0u;
+    x[k] = __funnelshift_r(x[k], hi, bs);
+  }
+  return sticky;
+}
+
+// Left shift of N words by sh bits (0 <= sh < 32*N), zeros shifted in.
+template <int N, int NS>
+__device__ __forceinline__ void shift_left(uint32_t (&x)[N], uint32_t sh) {
+  const uint32_t ws = sh >> 5, bs = sh & 31u;
+#pragma unroll
+  for (int st = 0; st < NS; ++st) {
+    const int b = 1 << st;
+    const bool on = (ws >> st) & 1u;
+#pragma unroll
+    for (int k = N - 1; k >= 0; --k) {
+      const uint32_t src = (k - b >= 0) ? x[k - b] : 0u;
+      x[k] = on ? src : x[k];
+    }
+  }
+#pragma unroll
+  for (int k = N - 1; k >= 0; --k) {
+    const uint32_t lo = (k > 0) ? x[k - 1] : 0u;
+    x[k] = __funnelshift_l(lo, x[k], bs);
+  }
+}
+
+template <int N>
+__device__ __forceinline__ uint32_t count_leading_zeros(const uint32_t (&x)[N]) {
+  uint32_t lz = 0u;
+  bool found = false;
+#pragma unroll
+  for (int k = N - 1; k >= 0; --k) {
+    const bool nz = x[k] != 0u;
+    lz += found ? 0u : (nz ? (uint32_t)__clz(x[k]) : 32u);
+    found = found || nz;
+  }
+  return lz;
+}
+
+// Stage count of a barrel shifter for word shifts 0..maxw.
+__host__ __device__ constexpr int stages_for(int maxw) {
+  return maxw <= 0 ? 0 : (maxw < 2 ? 1 : 1 + stages_for(maxw / 2));
+}
+
+// r[0..2W) = a * b, schoolbook over 32-bit words (IMAD.WIDE.U32 products).
+template <int W>
+__device__ __forceinline__ void mul_full(const uint32_t (&a)[W], const uint32_t (&b)[W],
+                                         uint32_t (&r)[2 * W]) {
+#pragma unroll
+  for (int k = 0; k < 2 * W; ++k) r[k] = 0u;
+#pragma unroll
+  for (int i = 0; i < W; ++i) {
+    uint32_t carry = 0u;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      const uint64_t t = (uint64_t)a[i] * b[j] + r[i + j] + carry;
+      r[i + j] = (uint32_t)t;
+      carry = (uint32_t)(t >> 32);
+    }
+    r[i + W] = carry;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Correctly rounded operations
+// ---------------------------------------------------------------------------
+
+// r = RN(a*b).  The exact product Ma*Mb has 2p or 2p-1 bits; keep the top p
+// bits, round with the next bit and the OR of the rest.
+template <int W>
+__device__ __forceinline__ void mul_rn(const Num<W>& a, const Num<W>& b, Num<W>& r) {
+  const uint32_t s = a.s ^ b.s;
+  if (zero_e(a.e) || zero_e(b.e)) {
+    set_zero(r, s);
+    return;
+  }
+  uint32_t P[2 * W];
+  mul_full<W>(a.m, b.m, P);
+  const uint32_t sh = 1u - (P[2 * W - 1] >> 31);  // 1 when the product has 2p-1 bits
+#pragma unroll
+  for (int k = 0; k < W; ++k) r.m[k] = __funnelshift_l(P[W + k - 1], P[W + k], sh);
+  const uint32_t g = P[W - 1] << sh;
+  uint32_t st = g << 1;
+#pragma unroll
+  for (int k = 0; k < W - 1; ++k) st |= P[k];
+  r.e = a.e + b.e - (int64_t)sh;
+  r.s = s;
+  round_increment<W>(r.m, r.e, (g >> 31) & ((st != 0u) | (r.m[0] & 1u)));
+}
+
+// r = RN(a+b) with the IEEE/MPFR signed-zero rules of round-to-nearest:
+// (+0)+(-0) = +0, (-0)+(-0) = -0, x + (+-0) = x, exact cancellation = +0.
+template <int W>
+__device__ __forceinline__ void add_rn(const Num<W>& a_, const Num<W>& b_, Num<W>& r) {
+  const bool az = zero_e(a_.e), bz = zero_e(b_.e);
+  if (az | bz) {
+    if (az & bz) {
+      set_zero(r, a_.s & b_.s);
+    } else {
+      r = az ? b_ : a_;
+    }
+    return;
+  }
+  const bool sw = b_.e > a_.e;
+  uint32_t X[W + 1], Y[W + 1];
+  X[0] = 0u;
+  Y[0] = 0u;
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    X[k + 1] = sw ? b_.m[k] : a_.m[k];
+    Y[k + 1] = sw ? a_.m[k] : b_.m[k];
+  }
+  int64_t e = sw ? b_.e : a_.e;
+  uint32_t s = sw ? b_.s : a_.s;
+  const uint32_t ys = sw ? a_.s : b_.s;
+  const int64_t d = sw ? (b_.e - a_.e) : (a_.e - b_.e);
+  if (d >= (int64_t)(32 * W + 2)) {
+    // |smaller| < ulp(larger)/4: the larger operand is the rounded sum.
+#pragma unroll
+    for (int k = 0; k < W; ++k) r.m[k] = X[k + 1];
+    r.e = e;
+    r.s = s;
+    return;
+  }
+  // Y = (Msmall * 2^32) >> d inside a (W+1)-word frame whose low word guards
+  // the kept bits; bits below the frame collapse into `sticky`.
+  uint32_t sticky = shift_right_sticky<W + 1, stages_for(W)>(Y, (uint32_t)d);
+  if (s == ys) {
+    uint32_t c = 0u;
+#pragma unroll
+    for (int k = 0; k <= W; ++k) {
+      const uint64_t t = (uint64_t)X[k] + Y[k] + c;
+      X[k] = (uint32_t)t;
+      c = (uint32_t)(t >> 32);
+    }
+    if (c) {  // carry out: one more bit, shift right by one
+      sticky |= X[0] & 1u;
+#pragma unroll
+      for (int k = 0; k < W; ++k) X[k] = __funnelshift_r(X[k], X[k + 1], 1);
+      X[W] = (X[W] >> 1) | 0x80000000u;
+      e += 1;
+    }
+  } else {
+    if (d == 0) {
+      int cmp = 0;
+#pragma unroll
+      for (int k = W; k >= 1; --k) cmp = (cmp != 0) ? cmp : ((X[k] > Y[k]) ? 1 : ((X[k] < Y[k]) ? -1 : 0));
+      if (cmp == 0) {
+        set_zero(r, 0u);
+        return;
+      }
+      if (cmp < 0) {
+#pragma unroll
+        for (int k = 1; k <= W; ++k) {
+          const uint32_t t = X[k];
+          X[k] = Y[k];
+          Y[k] = t;
+        }
+        s = ys;
+      }
+    }
+    // X - Y - sticky: the true subtrahend exceeds Y by less than one guard ulp
+    // when bits were lost, so this is the floor of the exact difference.
+    uint32_t bw = sticky;
+#pragma unroll
+    for (int k = 0; k <= W; ++k) {
+      const uint64_t t = (uint64_t)X[k] - Y[k] - bw;
+      X[k] = (uint32_t)t;
+      bw = (uint32_t)(t >> 63);
+    }
+    const uint32_t lz = count_leading_zeros<W + 1>(X);
+    shift_left<W + 1, stages_for(W)>(X, lz);
+    e -= (int64_t)lz;
+  }
+  const uint32_t rb = X[0] >> 31;
+  const uint32_t st = (X[0] << 1) | sticky;
+#pragma unroll
+  for (int k = 0; k < W; ++k) r.m[k] = X[k + 1];
+  r.e = e;
+  r.s = s;
+  round_increment<W>(r.m, r.e, rb & ((st != 0u) | (r.m[0] & 1u)));
+}
+
+template <int W>
+__device__ __forceinline__ void neg(Num<W>& a) {
+  a.s ^= 1u;
+}
+
+template <int W>
+__device__ __forceinline__ void sub_rn(const Num<W>& a, const Num<W>& b, Num<W>& r) {
+  Num<W> nb = b;
+  nb.s ^= 1u;
+  add_rn<W>(a, nb, r);
+}
+
+// r = RN(a/b) for b != 0 (callers test b first).  Knuth's algorithm D in base
+// 2^32 divides N = Ma * 2^(32(W+1)) by Mb (normalised: top bit set), giving a
+// (W+2)-word quotient Q of 32W+32 or 32W+33 bits and a remainder R; the kept
+// p bits, the next bit of Q and sticky = (rest of Q or R nonzero) round it.
+template <int W>
+__device__ __forceinline__ void div_rn(const Num<W>& a, const Num<W>& b, Num<W>& r) {
+  const uint32_t s = a.s ^ b.s;
+  if (zero_e(a.e)) {
+    set_zero(r, s);
+    return;
+  }
+  uint32_t u[2 * W + 2];
+#pragma unroll
+  for (int k = 0; k <= W; ++k) u[k] = 0u;
+#pragma unroll
+  for (int k = 0; k < W; ++k) u[W + 1 + k] = a.m[k];
+  u[2 * W + 1] = 0u;
+  uint32_t q[W + 2];
+  const uint64_t vt = b.m[W - 1], vt2 = b.m[W - 2];
+#pragma unroll
+  for (int j = W + 1; j >= 0; --j) {
+    const uint64_t num = ((uint64_t)u[j + W] << 32) | u[j + W - 1];
+    uint64_t qhat = num / vt;
+    uint64_t rhat = num - qhat * vt;
+    const uint64_t u2 = (j + W - 2 >= 0) ? u[j + W - 2] : 0u;
+    while ((qhat >> 32) != 0u || qhat * vt2 > ((rhat << 32) | u2)) {
+      qhat -= 1u;
+      rhat += vt;
+      if ((rhat >> 32) != 0u) break;
+    }
+    uint64_t carry = 0u;
+    uint32_t bw = 0u;
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+      const uint64_t pr = qhat * b.m[i] + carry;
+      carry = pr >> 32;
+      const uint64_t t = (uint64_t)u[i + j] - (uint32_t)pr - bw;
+      u[i + j] = (uint32_t)t;
+      bw = (uint32_t)(t >> 63);
+    }
+    const uint64_t t = (uint64_t)u[j + W] - carry - bw;
+    u[j + W] = (uint32_t)t;
+    q[j] = (uint32_t)qhat;
+    if ((t >> 63) != 0u) {  // qhat was one too large: add the divisor back
+      q[j] -= 1u;
+      uint32_t c = 0u;
+#pragma unroll
+      for (int i = 0; i < W; ++i) {
+        const uint64_t s2 = (uint64_t)u[i + j] + b.m[i] + c;
+        u[i + j] = (uint32_t)s2;
+        c = (uint32_t)(s2 >> 32);
+      }
+      u[j + W] += c;
+    }
+  }
+  uint32_t rem = 0u;
+#pragma unroll
+  for (int k = 0; k < W; ++k) rem |= u[k];
+  const uint32_t top = q[W + 1] & 1u;  // Q has 32W+33 bits
+  // keep bits [32+top, 32W+32+top) of Q
+#pragma unroll
+  for (int k = 0; k < W; ++k) r.m[k] = __funnelshift_r(q[k + 1], q[k + 2], top);
+  const uint32_t g = top ? (q[1] << 31) | (q[0] >> 1) : q[0];
+  const uint32_t rb = g >> 31;
+  const uint32_t st = (g << 1) | (top ? (q[0] & 1u) : 0u) | rem;
+  r.e = a.e - b.e + (int64_t)top;
+  r.s = s;
+  round_increment<W>(r.m, r.e, rb & ((st != 0u) | (r.m[0] & 1u)));
+}
+
+// -1, 0, 1 (zeros of either sign compare equal).
+template <int W>
+__device__ __forceinline__ int cmp(const Num<W>& a, const Num<W>& b) {
+  const int sa = zero_e(a.e) ? 0 : (a.s ? -1 : 1);
+  const int sb = zero_e(b.e) ? 0 : (b.s ? -1 : 1);
+  if (sa != sb) return sa < sb ? -1 : 1;
+  if (sa == 0) return 0;
+  int mag = 0;
+  if (a.e != b.e) {
+    mag = a.e > b.e ? 1 : -1;
+  } else {
+#pragma unroll
+    for (int k = W - 1; k >= 0; --k)
+      mag = (mag != 0) ? mag : ((a.m[k] > b.m[k]) ? 1 : ((a.m[k] < b.m[k]) ? -1 : 0));
+  }
+  return sa > 0 ? mag : -mag;
+}
+
+// Exact conversion of an IEEE double (53 <= p).
+template <int W>
+__device__ __forceinline__ void from_f64(double d, Num<W>& r) {
+  const uint64_t bits = (uint64_t)__double_as_longlong(d);
+  const uint32_t s = (uint32_t)(bits >> 63);
+  const int be = (int)((bits >> 52) & 0x7ffu);
+  const uint64_t f = bits & ((uint64_t(1) << 52) - 1u);
+  set_zero(r, s);
+  if (be == 0 && f == 0u) return;
+  uint64_t top;
+  int64_t e;
+  if (be == 0) {  // subnormal: f * 2^-1074
+    const int lz = __clzll((long long)f);
+    top = f << lz;
+    e = (int64_t)(64 - lz) - 1074;
+  } else {
+    top = ((uint64_t(1) << 52) | f) << 11;
+    e = (int64_t)be - 1022;
+  }
+  r.m[W - 1] = (uint32_t)(top >> 32);
+  r.m[W - 2] = (uint32_t)top;
+  r.e = e;
+}
+
+// Nearest double (for reporting; huge exponents saturate).
+template <int W>
+__device__ __forceinline__ double to_f64(const Num<W>& a) {
+  if (zero_e(a.e)) return a.s ? -0.0 : 0.0;
+  const uint64_t t = ((uint64_t)a.m[W - 1] << 32) | a.m[W - 2];
+  uint32_t rest = 0u;
+#pragma unroll
+  for (int k = 0; k < W - 2; ++k) rest |= a.m[k];
+  uint64_t q = t >> 11;
+  const uint32_t rb = (uint32_t)(t >> 10) & 1u;
+  const bool st = ((t & 0x3ffu) != 0u) || rest != 0u;
+  if (rb && (st || (q & 1u))) q += 1u;
+  const int64_t e = a.e < -4000 ? -4000 : (a.e > 4000 ? 4000 : a.e);
+  const double v = ldexp((double)q, (int)e - 53);
+  return a.s ? -v : v;
+}
+
+// ---------------------------------------------------------------------------
+// Exact sums: 64-bit signed digit counters over 32-bit digits
+// ---------------------------------------------------------------------------
+// A term P * 2^(E - 2p) (P the exact 2W-word product) enters an accumulator
+// whose digit 0 has weight 2^(Emin - 2p) as P * 2^(E - Emin): 2W+1 digits
+// starting at digit (E - Emin) / 32 after a funnel shift by (E - Emin) % 32.
+// Counters absorb signed 32-bit digits without carries; carries are resolved
+// once, when the sum is rounded.
+
+template <int W>
+__device__ __forceinline__ void shifted_digits(const uint32_t (&P)[2 * W], uint32_t bs,
+                                               uint32_t (&D)[2 * W + 1]) {
+#pragma unroll
+  for (int k = 0; k <= 2 * W; ++k) {
+    const uint32_t lo = (k > 0) ? P[k - 1] : 0u;
+    const uint32_t hi = (k < 2 * W) ? P[k] : 0u;
+    D[k] = __funnelshift_l(lo, hi, bs);
+  }
+}
+
+// Resolve carries of nd signed digit counters c[d*stride] into 32-bit words
+// (stored back into the counters' slots), returning 1 when the total is
+// negative.  The counters are then the two's complement words of the sum.
+__device__ __forceinline__ uint32_t resolve_digits(int64_t* c, int stride, int nd) {
+  int64_t carry = 0;
+  for (int d = 0; d < nd; ++d) {
+    const int64_t t = c[d * stride] + carry;
+    c[d * stride] = (int64_t)(uint32_t)t;
+    carry = t >> 32;
+  }
+  return carry < 0 ? 1u : 0u;
+}
+
+// Negate the nd two's complement words in place (magnitude of a negative sum).
+__device__ __forceinline__ void negate_words(int64_t* c, int stride, int nd) {
+  uint32_t carry = 1u;
+  for (int d = 0; d < nd; ++d) {
+    const uint64_t t = (uint64_t)(uint32_t)~(uint32_t)c[d * stride] + carry;
+    c[d * stride] = (int64_t)(uint32_t)t;
+    carry = (uint32_t)(t >> 32);
+  }
+}
+
+// r = RN( (-1)^neg * S * 2^k ) for the natural S held in nd 32-bit words
+// c[d*stride]; S == 0 gives +0.
+template <int W>
+__device__ __forceinline__ void round_words(const int64_t* c, int stride, int nd, int64_t k,
+                                            uint32_t neg, Num<W>& r) {
+  int t = nd - 1;
+  while (t >= 0 && (uint32_t)c[t * stride] == 0u) --t;
+  if (t < 0) {
+    set_zero(r, 0u);
+    return;
+  }
+  const int64_t nb = 32 * (int64_t)t + (32 - __clz((uint32_t)c[t * stride]));
+  const int64_t pos = nb - 32 * W;  // lowest kept bit (negative: exact)
+  auto word = [&](int64_t i) -> uint32_t {
+    return (i >= 0 && i < nd) ? (uint32_t)c[i * stride] : 0u;
+  };
+  auto bits32 = [&](int64_t at) -> uint32_t {  // bits [at, at+32)
+    const int64_t q = (at >= 0) ? at / 32 : -((-at + 31) / 32);
+    const uint32_t sh = (uint32_t)(at - 32 * q);
+    return __funnelshift_r(word(q), word(q + 1), sh);
+  };
+#pragma unroll
+  for (int j = 0; j < W; ++j) r.m[j] = bits32(pos + 32 * j);
+  uint32_t rb = 0u, st = 0u;
+  if (pos > 0) {
+    rb = (bits32(pos - 1) & 1u);
+    const int64_t below = pos - 1;  // bits [0, below) form the sticky
+    const int64_t fw = below / 32;
+    for (int64_t i = 0; i < fw; ++i) st |= word(i);
+    const uint32_t rem = (uint32_t)(below - 32 * fw);
+    if (rem) st |= word(fw) << (32u - rem);
+  }
+  r.e = nb + k;
+  r.s = neg;
+  round_increment<W>(r.m, r.e, rb & ((st != 0u) | (r.m[0] & 1u)));
+}
+
+}  // namespace mpk

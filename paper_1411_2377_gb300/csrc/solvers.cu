@@ -1,0 +1,736 @@
+// solvers.cu -- device-resident BiCG and GPBiCG (Fig. 5, K = I).
+//
+// Every step of an iteration is a kernel on the caller's stream: the SpMVs,
+// the exact dot products (fused where they share operands), one-thread
+// scalar kernels for the recurrences' coefficients (p-bit divisions
+// included), and fused vector updates that evaluate the figure's formulas
+// with each product and sum rounded, left to right.  A device state word
+// ("done") gates every kernel: once a scalar kernel decides convergence,
+// breakdown or the iteration limit, later launches return at once, so the
+// host can run several iterations between polls and the result does not
+// depend on the poll interval.  From the second iteration on, one iteration
+// is captured once as a CUDA graph and replayed.
+//
+// Readings of Fig. 5 (shared with the oracle):
+//  * GPBiCG uses z = zeta r + eta z - alpha u and r = t - eta y - zeta A t
+//    (Zhang's method); the printed "zeta z" and "zeta u" break r = b - A x.
+//  * At i = 1 the general u/z/x/r updates run with u = z = s = 0 and
+//    beta = eta = +0; y = alpha q - r and zeta = mu2/mu5.
+//  * A zero divisor of zeta/eta (mu5 at i = 1, tau later) gives
+//    zeta = eta = +0; a zero (r~, q) or (p~, z) is a breakdown.
+//  * The stopping rule (r,r) <= RN(RN(rtol^2)(r0,r0)) + RN(atol^2) is checked
+//    once r_i is formed; GPBiCG then exits on zeta = 0.  Reaching maxit wins
+//    over a zero rho found for the next iteration.
+//  * BiCG: z~ = A^T p~ and p~_i = r~_{i-1} + beta p~_{i-1}.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+#include "mpdev.cuh"
+
+namespace mpk {
+mp_status init_dot_scratch(void* scratch, cudaStream_t st);
+
+namespace {
+
+struct SState {
+  int done;    // gate for every kernel of the solve
+  int status;  // MP_OK, MP_ERR_BREAKDOWN, MP_ERR_NOCONV
+  long long iters;
+  long long maxit;
+};
+
+enum Scal {
+  RHO, RHO_NEW, RHO_PREV, ALPHA, BETA, ZETA, ETA, DEN, MU1, MU2, MU3, MU4, MU5, RR, RR0, THR,
+  NSCAL
+};
+
+template <int W>
+__device__ __forceinline__ void ld_s(Num<W>& a, const uint64_t* S, int j) {
+  load<W>(a, S + (size_t)j * (W / 2 + 1), 1, 0);
+}
+template <int W>
+__device__ __forceinline__ void st_s(const Num<W>& a, uint64_t* S, int j) {
+  store<W>(a, S + (size_t)j * (W / 2 + 1), 1, 0);
+}
+
+__device__ __forceinline__ void finish(SState* st, int status) {
+  st->status = status;
+  st->done = 1;
+}
+
+// ---------------------------------------------------------------------------
+// Scalar kernels (one thread)
+// ---------------------------------------------------------------------------
+
+// thr = RN(RN(T*(r0,r0)) + A) with T = RN(rtol^2), A = RN(atol^2); exits
+// before the first iteration when (r0,r0) <= thr or rho = 0.
+template <int W>
+__global__ void sc_setup(SState* st, uint64_t* S, double rtol, double atol) {
+  Num<W> rt, at, T, A, t, thr, rr0, rho, z;
+  from_f64<W>(rtol, rt);
+  from_f64<W>(atol, at);
+  mul_rn<W>(rt, rt, T);
+  mul_rn<W>(at, at, A);
+  ld_s<W>(rr0, S, RR0);
+  mul_rn<W>(T, rr0, t);
+  add_rn<W>(t, A, thr);
+  st_s<W>(thr, S, THR);
+  set_zero(z, 0u);
+  st_s<W>(z, S, BETA);
+  st_s<W>(z, S, ETA);
+  st_s<W>(z, S, ZETA);
+  ld_s<W>(rho, S, RHO);
+  st->iters = 0;
+  st->status = MP_OK;
+  st->done = 0;
+  if (cmp<W>(rr0, thr) <= 0) {
+    finish(st, MP_OK);
+  } else if (st->maxit <= 0) {
+    finish(st, MP_ERR_NOCONV);
+  } else if (zero_e(rho.e)) {
+    finish(st, MP_ERR_BREAKDOWN);
+  }
+}
+
+// alpha = RN(rho / DEN); DEN = 0 is a breakdown.
+template <int W>
+__global__ void sc_alpha(SState* st, uint64_t* S) {
+  if (st->done) return;
+  Num<W> rho, d, a;
+  ld_s<W>(d, S, DEN);
+  if (zero_e(d.e)) {
+    finish(st, MP_ERR_BREAKDOWN);
+    return;
+  }
+  ld_s<W>(rho, S, RHO);
+  div_rn<W>(rho, d, a);
+  st_s<W>(a, S, ALPHA);
+}
+
+// GPBiCG i = 1: zeta = mu2/mu5 (mu5 = 0 -> 0), eta = 0.
+template <int W>
+__global__ void sc_zeta1(SState* st, uint64_t* S) {
+  if (st->done) return;
+  Num<W> m2, m5, z;
+  ld_s<W>(m2, S, MU2);
+  ld_s<W>(m5, S, MU5);
+  if (zero_e(m5.e))
+    set_zero(z, 0u);
+  else
+    div_rn<W>(m2, m5, z);
+  st_s<W>(z, S, ZETA);
+  set_zero(z, 0u);
+  st_s<W>(z, S, ETA);
+}
+
+// tau = mu5 mu1 - mu4 mu4; zeta = (mu1 mu2 - mu3 mu4)/tau;
+// eta = (mu5 mu3 - mu4 mu2)/tau; tau = 0 -> zeta = eta = 0.
+template <int W>
+__global__ void sc_zeta(SState* st, uint64_t* S) {
+  if (st->done) return;
+  Num<W> m1, m2, m3, m4, m5, a, b, c, tau, z;
+  ld_s<W>(m1, S, MU1);
+  ld_s<W>(m4, S, MU4);
+  ld_s<W>(m5, S, MU5);
+  mul_rn<W>(m5, m1, a);
+  mul_rn<W>(m4, m4, b);
+  sub_rn<W>(a, b, tau);
+  if (zero_e(tau.e)) {
+    set_zero(z, 0u);
+    st_s<W>(z, S, ZETA);
+    st_s<W>(z, S, ETA);
+    return;
+  }
+  ld_s<W>(m2, S, MU2);
+  ld_s<W>(m3, S, MU3);
+  mul_rn<W>(m1, m2, a);
+  mul_rn<W>(m3, m4, b);
+  sub_rn<W>(a, b, c);
+  div_rn<W>(c, tau, z);
+  st_s<W>(z, S, ZETA);
+  mul_rn<W>(m5, m3, a);
+  mul_rn<W>(m4, m2, b);
+  sub_rn<W>(a, b, c);
+  div_rn<W>(c, tau, z);
+  st_s<W>(z, S, ETA);
+}
+
+// GPBiCG: beta = RN(RN(rho/rho_prev) * RN(alpha/zeta)); BiCG: rho/rho_prev.
+template <int W, bool GP>
+__global__ void sc_beta(SState* st, uint64_t* S) {
+  if (st->done) return;
+  Num<W> rho, rp, q1, a, z, q2, b;
+  ld_s<W>(rho, S, RHO);
+  ld_s<W>(rp, S, RHO_PREV);
+  div_rn<W>(rho, rp, q1);
+  if (GP) {
+    ld_s<W>(a, S, ALPHA);
+    ld_s<W>(z, S, ZETA);
+    div_rn<W>(a, z, q2);
+    mul_rn<W>(q1, q2, b);
+    st_s<W>(b, S, BETA);
+  } else {
+    st_s<W>(q1, S, BETA);
+  }
+}
+
+// End of an iteration: count it, record (r,r), shift rho, decide the exit.
+template <int W, bool GP>
+__global__ void sc_check(SState* st, uint64_t* S, uint64_t* hist, int64_t hist_ld,
+                         int64_t hist_n) {
+  if (st->done) return;
+  Num<W> rr, thr, rho, rn, z;
+  st->iters += 1;
+  ld_s<W>(rr, S, RR);
+  if (hist && st->iters <= hist_n) store<W>(rr, hist, hist_ld, st->iters - 1);
+  ld_s<W>(rho, S, RHO);
+  ld_s<W>(rn, S, RHO_NEW);
+  st_s<W>(rho, S, RHO_PREV);
+  st_s<W>(rn, S, RHO);
+  ld_s<W>(thr, S, THR);
+  ld_s<W>(z, S, ZETA);
+  if (cmp<W>(rr, thr) <= 0) {
+    finish(st, MP_OK);
+  } else if (GP && zero_e(z.e)) {
+    finish(st, MP_ERR_BREAKDOWN);
+  } else if (st->iters >= st->maxit) {
+    finish(st, MP_ERR_NOCONV);
+  } else if (zero_e(rn.e)) {
+    finish(st, MP_ERR_BREAKDOWN);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Vector kernels (gated)
+// ---------------------------------------------------------------------------
+
+struct Vecs {
+  uint64_t* v[12];
+  int64_t ld;
+  int64_t n;
+};
+
+#define GRID_LOOP(i, n) \
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+template <int W>
+__global__ void set_zero_kernel(uint64_t* a, int64_t ld, int64_t n) {
+  GRID_LOOP(i, n) {
+    Num<W> z;
+    set_zero(z, 0u);
+    store<W>(z, a, ld, i);
+  }
+}
+
+template <int W>
+__global__ void copy_kernel(const SState* st, const uint64_t* __restrict__ src, int64_t lds,
+                            uint64_t* __restrict__ dst, int64_t ldd, int64_t n) {
+  if (st && st->done) return;
+  GRID_LOOP(i, n) {
+    for (int k = 0; k <= W / 2; ++k) dst[k * ldd + i] = src[k * lds + i];
+  }
+}
+
+// GPBiCG, i >= 2: w = v + beta q;  p = r + beta (p - u)
+template <int W>
+__global__ void gp_wp(const SState* st, const uint64_t* __restrict__ S, const uint64_t* v,
+                      const uint64_t* q, const uint64_t* r, uint64_t* p, const uint64_t* u,
+                      uint64_t* w, int64_t ld, int64_t n) {
+  if (st->done) return;
+  Num<W> beta;
+  ld_s<W>(beta, S, BETA);
+  GRID_LOOP(i, n) {
+    Num<W> a, b, c;
+    load<W>(a, q, ld, i);
+    mul_rn<W>(beta, a, b);
+    load<W>(a, v, ld, i);
+    add_rn<W>(a, b, c);
+    store<W>(c, w, ld, i);
+    load<W>(a, p, ld, i);
+    load<W>(b, u, ld, i);
+    sub_rn<W>(a, b, c);
+    mul_rn<W>(beta, c, a);
+    load<W>(b, r, ld, i);
+    add_rn<W>(b, a, c);
+    store<W>(c, p, ld, i);
+  }
+}
+
+// GPBiCG, i = 1: t = r - alpha q;  y = alpha q - r
+template <int W>
+__global__ void gp_ty1(const SState* st, const uint64_t* __restrict__ S, const uint64_t* r,
+                       const uint64_t* q, uint64_t* t, uint64_t* y, int64_t ld, int64_t n) {
+  if (st->done) return;
+  Num<W> alpha;
+  ld_s<W>(alpha, S, ALPHA);
+  GRID_LOOP(i, n) {
+    Num<W> a, aq, c;
+    load<W>(a, q, ld, i);
+    mul_rn<W>(alpha, a, aq);
+    load<W>(a, r, ld, i);
+    sub_rn<W>(a, aq, c);
+    store<W>(c, t, ld, i);
+    sub_rn<W>(aq, a, c);
+    store<W>(c, y, ld, i);
+  }
+}
+
+// GPBiCG, i >= 2: s = t - r;  t = r - alpha q;  y = s - alpha (w - q)
+template <int W>
+__global__ void gp_sty(const SState* st, const uint64_t* __restrict__ S, const uint64_t* r,
+                       const uint64_t* q, const uint64_t* w, uint64_t* s, uint64_t* t,
+                       uint64_t* y, int64_t ld, int64_t n) {
+  if (st->done) return;
+  Num<W> alpha;
+  ld_s<W>(alpha, S, ALPHA);
+  GRID_LOOP(i, n) {
+    Num<W> a, b, c, sv;
+    load<W>(a, t, ld, i);
+    load<W>(b, r, ld, i);
+    sub_rn<W>(a, b, sv);
+    store<W>(sv, s, ld, i);
+    load<W>(a, q, ld, i);
+    mul_rn<W>(alpha, a, c);
+    sub_rn<W>(b, c, a);
+    store<W>(a, t, ld, i);
+    load<W>(a, w, ld, i);
+    load<W>(b, q, ld, i);
+    sub_rn<W>(a, b, c);
+    mul_rn<W>(alpha, c, a);
+    sub_rn<W>(sv, a, c);
+    store<W>(c, y, ld, i);
+  }
+}
+
+// GPBiCG: u = zeta q + eta (s + beta u);  z = zeta r + eta z - alpha u;
+//         x = x + alpha p + z;            r = t - eta y - zeta v
+template <int W>
+__global__ void gp_uzxr(const SState* st, const uint64_t* __restrict__ S, const Vecs V,
+                        uint64_t* x, int64_t ldx) {
+  if (st->done) return;
+  // V.v: 0 q, 1 s, 2 u, 3 r, 4 z, 5 p, 6 t, 7 y, 8 v
+  const int64_t ld = V.ld;
+  GRID_LOOP(i, V.n) {
+    Num<W> sc, a, b, c, un, zn;
+    ld_s<W>(sc, S, BETA);
+    load<W>(a, V.v[2], ld, i);
+    mul_rn<W>(sc, a, b);
+    load<W>(a, V.v[1], ld, i);
+    add_rn<W>(a, b, c);
+    ld_s<W>(sc, S, ETA);
+    mul_rn<W>(sc, c, b);
+    ld_s<W>(sc, S, ZETA);
+    load<W>(a, V.v[0], ld, i);
+    mul_rn<W>(sc, a, c);
+    add_rn<W>(c, b, un);
+    store<W>(un, V.v[2], ld, i);
+    load<W>(a, V.v[3], ld, i);
+    mul_rn<W>(sc, a, b);  // zeta r
+    ld_s<W>(sc, S, ETA);
+    load<W>(a, V.v[4], ld, i);
+    mul_rn<W>(sc, a, c);  // eta z
+    add_rn<W>(b, c, a);
+    ld_s<W>(sc, S, ALPHA);
+    mul_rn<W>(sc, un, b);
+    sub_rn<W>(a, b, zn);
+    store<W>(zn, V.v[4], ld, i);
+    load<W>(a, V.v[5], ld, i);
+    mul_rn<W>(sc, a, b);  // alpha p
+    load<W>(a, x, ldx, i);
+    add_rn<W>(a, b, c);
+    add_rn<W>(c, zn, a);
+    store<W>(a, x, ldx, i);
+    ld_s<W>(sc, S, ETA);
+    load<W>(a, V.v[7], ld, i);
+    mul_rn<W>(sc, a, b);  // eta y
+    load<W>(a, V.v[6], ld, i);
+    sub_rn<W>(a, b, c);
+    ld_s<W>(sc, S, ZETA);
+    load<W>(a, V.v[8], ld, i);
+    mul_rn<W>(sc, a, b);  // zeta v
+    sub_rn<W>(c, b, a);
+    store<W>(a, V.v[3], ld, i);
+  }
+}
+
+// BiCG, i >= 2: p = r + beta p;  p~ = r~ + beta p~
+template <int W>
+__global__ void bi_p(const SState* st, const uint64_t* __restrict__ S, const uint64_t* r,
+                     const uint64_t* rt, uint64_t* p, uint64_t* pt, int64_t ld, int64_t n) {
+  if (st->done) return;
+  GRID_LOOP(i, n) {
+    Num<W> beta, a, b, c;
+    ld_s<W>(beta, S, BETA);
+    load<W>(a, p, ld, i);
+    mul_rn<W>(beta, a, b);
+    load<W>(a, r, ld, i);
+    add_rn<W>(a, b, c);
+    store<W>(c, p, ld, i);
+    load<W>(a, pt, ld, i);
+    mul_rn<W>(beta, a, b);
+    load<W>(a, rt, ld, i);
+    add_rn<W>(a, b, c);
+    store<W>(c, pt, ld, i);
+  }
+}
+
+// BiCG: x = x + alpha p;  r = r - alpha z;  r~ = r~ - alpha z~
+template <int W>
+__global__ void bi_xr(const SState* st, const uint64_t* __restrict__ S, const uint64_t* p,
+                      const uint64_t* z, const uint64_t* zt, uint64_t* r, uint64_t* rt,
+                      uint64_t* x, int64_t ldx, int64_t ld, int64_t n) {
+  if (st->done) return;
+  GRID_LOOP(i, n) {
+    Num<W> alpha, a, b, c;
+    ld_s<W>(alpha, S, ALPHA);
+    load<W>(a, p, ld, i);
+    mul_rn<W>(alpha, a, b);
+    load<W>(a, x, ldx, i);
+    add_rn<W>(a, b, c);
+    store<W>(c, x, ldx, i);
+    load<W>(a, z, ld, i);
+    mul_rn<W>(alpha, a, b);
+    load<W>(a, r, ld, i);
+    sub_rn<W>(a, b, c);
+    store<W>(c, r, ld, i);
+    load<W>(a, zt, ld, i);
+    mul_rn<W>(alpha, a, b);
+    load<W>(a, rt, ld, i);
+    sub_rn<W>(a, b, c);
+    store<W>(c, rt, ld, i);
+  }
+}
+
+int ew_grid(int64_t n) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t b = (n + 127) / 128;
+  const int64_t lim = (int64_t)(sms > 0 ? sms : 1) * 8;
+  if (b > lim) b = lim;
+  return (int)(b < 1 ? 1 : b);
+}
+
+// ---------------------------------------------------------------------------
+// Host driver
+// ---------------------------------------------------------------------------
+
+struct Work {
+  int prec = 0, L = 0;
+  int64_t n = 0, ld = 0;
+  uint64_t* vecs = nullptr;  // nvec vectors of (L+1)*ld words
+  uint64_t* S = nullptr;     // NSCAL scalars of L+1 words
+  SState* st = nullptr;
+  void* dscratch = nullptr;
+  int nvec = 0;
+  uint64_t* vec(int k) const { return vecs + (size_t)k * (L + 1) * ld; }
+  uint64_t* scal(int j) const { return S + (size_t)j * (L + 1); }
+};
+
+mp_status alloc_work(Work& w, int prec, int64_t n, int nvec, cudaStream_t st) {
+  w.prec = prec;
+  w.L = prec / 64;
+  w.n = n;
+  w.ld = n > 0 ? n : 1;
+  w.nvec = nvec;
+  const size_t vb = (size_t)nvec * (w.L + 1) * w.ld * 8;
+  const size_t sb = (size_t)NSCAL * (w.L + 1) * 8;
+  const size_t db = dot_scratch_bytes(prec, 5);
+  MPK_CUDA(cudaMallocAsync((void**)&w.vecs, vb, st));
+  MPK_CUDA(cudaMallocAsync((void**)&w.S, sb, st));
+  MPK_CUDA(cudaMallocAsync((void**)&w.st, sizeof(SState), st));
+  MPK_CUDA(cudaMallocAsync(&w.dscratch, db, st));
+  return init_dot_scratch(w.dscratch, st);
+}
+
+void free_work(Work& w, cudaStream_t st) {
+  cudaFreeAsync(w.vecs, st);
+  cudaFreeAsync(w.S, st);
+  cudaFreeAsync(w.st, st);
+  cudaFreeAsync(w.dscratch, st);
+  w = Work{};
+}
+
+mp_status dot2(const Work& w, const uint64_t* a0, const uint64_t* b0, int o0, const uint64_t* a1,
+               const uint64_t* b1, int o1, cudaStream_t st, const int* gate) {
+  DotArgs d;
+  d.k = a1 ? 2 : 1;
+  d.n = w.n;
+  d.x[0] = a0;
+  d.y[0] = b0;
+  d.x[1] = a1;
+  d.y[1] = b1;
+  for (int j = 0; j < 5; ++j) {
+    d.ldx[j] = d.ldy[j] = w.ld;
+    d.out_ld[j] = 1;
+  }
+  d.out[0] = w.scal(o0);
+  d.out[1] = a1 ? w.scal(o1) : nullptr;
+  return launch_dot(w.prec, d, w.dscratch, gate, st);
+}
+
+struct SolveCall {
+  mp_csr A;
+  mp_vec b, x;
+  mp_solve_opts o;
+  cudaStream_t st;
+};
+
+// One iteration body for i >= 2 (captured into a graph) or i = 1.
+template <int W>
+mp_status gp_iteration(const Work& w, const SolveCall& c, bool first) {
+  enum { R, RT, P, Q, T, V, WV, Y, U, Z, SV };
+  const int64_t n = w.n, ld = w.ld;
+  const int* gate = &w.st->done;
+  cudaStream_t st = c.st;
+  const int g = ew_grid(n);
+  mp_status r;
+  if (first) {
+    copy_kernel<W><<<g, 128, 0, st>>>(w.st, w.vec(R), ld, w.vec(P), ld, n);
+    count_launch();
+  } else {
+    sc_beta<W, true><<<1, 1, 0, st>>>(w.st, w.S);
+    gp_wp<W><<<g, 128, 0, st>>>(w.st, w.S, w.vec(V), w.vec(Q), w.vec(R), w.vec(P), w.vec(U),
+                                w.vec(WV), ld, n);
+    count_launch(2);
+  }
+  if ((r = launch_spmv(c.A, c.A->A, c.o.mode, w.vec(P), ld, w.vec(Q), ld, nullptr, 0, gate, st)) != MP_OK)
+    return r;
+  if ((r = dot2(w, w.vec(RT), w.vec(Q), DEN, nullptr, nullptr, 0, st, gate)) != MP_OK) return r;
+  sc_alpha<W><<<1, 1, 0, st>>>(w.st, w.S);
+  count_launch();
+  if (first) {
+    gp_ty1<W><<<g, 128, 0, st>>>(w.st, w.S, w.vec(R), w.vec(Q), w.vec(T), w.vec(Y), ld, n);
+  } else {
+    gp_sty<W><<<g, 128, 0, st>>>(w.st, w.S, w.vec(R), w.vec(Q), w.vec(WV), w.vec(SV), w.vec(T),
+                                 w.vec(Y), ld, n);
+  }
+  count_launch();
+  if ((r = launch_spmv(c.A, c.A->A, c.o.mode, w.vec(T), ld, w.vec(V), ld, nullptr, 0, gate, st)) != MP_OK)
+    return r;
+  DotArgs d;
+  d.n = n;
+  for (int j = 0; j < 5; ++j) {
+    d.ldx[j] = d.ldy[j] = ld;
+    d.out_ld[j] = 1;
+  }
+  if (first) {
+    d.k = 2;
+    d.x[0] = w.vec(V); d.y[0] = w.vec(T); d.out[0] = w.scal(MU2);
+    d.x[1] = w.vec(V); d.y[1] = w.vec(V); d.out[1] = w.scal(MU5);
+  } else {
+    d.k = 5;
+    d.x[0] = w.vec(Y); d.y[0] = w.vec(Y); d.out[0] = w.scal(MU1);
+    d.x[1] = w.vec(V); d.y[1] = w.vec(T); d.out[1] = w.scal(MU2);
+    d.x[2] = w.vec(Y); d.y[2] = w.vec(T); d.out[2] = w.scal(MU3);
+    d.x[3] = w.vec(V); d.y[3] = w.vec(Y); d.out[3] = w.scal(MU4);
+    d.x[4] = w.vec(V); d.y[4] = w.vec(V); d.out[4] = w.scal(MU5);
+  }
+  if ((r = launch_dot(w.prec, d, w.dscratch, gate, st)) != MP_OK) return r;
+  if (first)
+    sc_zeta1<W><<<1, 1, 0, st>>>(w.st, w.S);
+  else
+    sc_zeta<W><<<1, 1, 0, st>>>(w.st, w.S);
+  count_launch();
+  Vecs V9{};
+  V9.v[0] = w.vec(Q); V9.v[1] = w.vec(SV); V9.v[2] = w.vec(U); V9.v[3] = w.vec(R);
+  V9.v[4] = w.vec(Z); V9.v[5] = w.vec(P); V9.v[6] = w.vec(T); V9.v[7] = w.vec(Y);
+  V9.v[8] = w.vec(V);
+  V9.ld = ld;
+  V9.n = n;
+  gp_uzxr<W><<<g, 128, 0, st>>>(w.st, w.S, V9, c.x.data, c.x.ld);
+  count_launch();
+  if ((r = dot2(w, w.vec(R), w.vec(R), RR, w.vec(RT), w.vec(R), RHO_NEW, st, gate)) != MP_OK)
+    return r;
+  sc_check<W, true><<<1, 1, 0, st>>>(w.st, w.S, c.o.history.data, c.o.history.ld,
+                                     c.o.history.data ? c.o.history.n : 0);
+  count_launch();
+  return launch_check("gpbicg iteration");
+}
+
+template <int W>
+mp_status bi_iteration(const Work& w, const SolveCall& c, bool first) {
+  enum { R, RT, P, PT, Z, ZT };
+  const int64_t n = w.n, ld = w.ld;
+  const int* gate = &w.st->done;
+  cudaStream_t st = c.st;
+  const int g = ew_grid(n);
+  mp_status r;
+  if (first) {
+    copy_kernel<W><<<g, 128, 0, st>>>(w.st, w.vec(R), ld, w.vec(P), ld, n);
+    copy_kernel<W><<<g, 128, 0, st>>>(w.st, w.vec(RT), ld, w.vec(PT), ld, n);
+    count_launch(2);
+  } else {
+    sc_beta<W, false><<<1, 1, 0, st>>>(w.st, w.S);
+    bi_p<W><<<g, 128, 0, st>>>(w.st, w.S, w.vec(R), w.vec(RT), w.vec(P), w.vec(PT), ld, n);
+    count_launch(2);
+  }
+  if ((r = launch_spmv(c.A, c.A->A, c.o.mode, w.vec(P), ld, w.vec(Z), ld, nullptr, 0, gate, st)) != MP_OK)
+    return r;
+  if ((r = launch_spmv(c.A, c.A->AT, c.o.mode, w.vec(PT), ld, w.vec(ZT), ld, nullptr, 0, gate, st)) != MP_OK)
+    return r;
+  if ((r = dot2(w, w.vec(PT), w.vec(Z), DEN, nullptr, nullptr, 0, st, gate)) != MP_OK) return r;
+  sc_alpha<W><<<1, 1, 0, st>>>(w.st, w.S);
+  bi_xr<W><<<g, 128, 0, st>>>(w.st, w.S, w.vec(P), w.vec(Z), w.vec(ZT), w.vec(R), w.vec(RT),
+                              c.x.data, c.x.ld, ld, n);
+  count_launch(2);
+  if ((r = dot2(w, w.vec(R), w.vec(R), RR, w.vec(RT), w.vec(R), RHO_NEW, st, gate)) != MP_OK)
+    return r;
+  sc_check<W, false><<<1, 1, 0, st>>>(w.st, w.S, c.o.history.data, c.o.history.ld,
+                                      c.o.history.data ? c.o.history.n : 0);
+  count_launch();
+  return launch_check("bicg iteration");
+}
+
+template <int W, bool GP>
+mp_status solve_w(const SolveCall& c, mp_solve_info* info) {
+  cudaStream_t st = c.st;
+  const int64_t n = c.A->n;
+  Work w;
+  mp_status r = alloc_work(w, c.A->prec, n, GP ? 11 : 6, st);
+  if (r != MP_OK) {
+    free_work(w, st);
+    return r;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, st);
+  SState init{1, MP_OK, 0, c.o.maxit};
+  const int64_t ld = w.ld;
+  const int g = ew_grid(n);
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  SState hs{};
+  auto body = [&](bool first) {
+    return GP ? gp_iteration<W>(w, c, first) : bi_iteration<W>(w, c, first);
+  };
+  do {
+    cudaError_t ce0 = cudaMemcpyAsync(w.st, &init, sizeof init, cudaMemcpyHostToDevice, st);
+    if (ce0 != cudaSuccess) { r = cuda_error(ce0, "state upload"); break; }
+    for (int k = 0; k < w.nvec; ++k) {
+      set_zero_kernel<W><<<g, 128, 0, st>>>(w.vec(k), ld, n);
+      count_launch();
+    }
+    // r0 = b - A x0 (exact residual), r~ = r0, (r0, r0) and rho_0 = (r~, r0)
+    if ((r = launch_spmv(c.A, c.A->A, MP_EXACT, c.x.data, c.x.ld, w.vec(0), ld, c.b.data, c.b.ld,
+                         nullptr, st)) != MP_OK)
+      break;
+    copy_kernel<W><<<g, 128, 0, st>>>(nullptr, w.vec(0), ld, w.vec(1), ld, n);
+    count_launch();
+    if ((r = dot2(w, w.vec(0), w.vec(0), RR0, w.vec(1), w.vec(0), RHO, st, nullptr)) != MP_OK)
+      break;
+    sc_setup<W><<<1, 1, 0, st>>>(w.st, w.S, c.o.rtol, c.o.atol);
+    count_launch();
+    if ((r = launch_check("solver setup")) != MP_OK) break;
+    // first iteration (not captured)
+    if ((r = body(true)) != MP_OK) break;
+    MPK_CUDA(cudaMemcpyAsync(&hs, w.st, sizeof hs, cudaMemcpyDeviceToHost, st));
+    MPK_CUDA(cudaStreamSynchronize(st));
+    if (hs.done) break;
+    // capture one steady-state iteration
+    cudaError_t ce = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
+    if (ce != cudaSuccess) { r = cuda_error(ce, "cudaStreamBeginCapture"); break; }
+    const int64_t before = mp_launch_count(0);
+    mp_status rb = body(false);
+    const int64_t per_iter = mp_launch_count(0) - before;
+    ce = cudaStreamEndCapture(st, &graph);
+    if (rb != MP_OK) { r = rb; break; }
+    if (ce != cudaSuccess) { r = cuda_error(ce, "cudaStreamEndCapture"); break; }
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    if (ce != cudaSuccess) { r = cuda_error(ce, "cudaGraphInstantiate"); break; }
+    const int poll = c.o.poll_every > 0 ? c.o.poll_every : 1;
+    count_launch(-(int)per_iter);  // the capture itself launched nothing
+    while (true) {
+      for (int k = 0; k < poll; ++k) {
+        ce = cudaGraphLaunch(exec, st);
+        if (ce != cudaSuccess) break;
+        count_launch((int)per_iter);
+      }
+      if (ce != cudaSuccess) { r = cuda_error(ce, "cudaGraphLaunch"); break; }
+      MPK_CUDA(cudaMemcpyAsync(&hs, w.st, sizeof hs, cudaMemcpyDeviceToHost, st));
+      MPK_CUDA(cudaStreamSynchronize(st));
+      if (hs.done) break;
+    }
+  } while (false);
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  cudaEventRecord(e1, st);
+  if (r == MP_OK) {
+    cudaError_t ce = cudaMemcpyAsync(&hs, w.st, sizeof hs, cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) r = cuda_error(ce, "reading the solver state");
+  }
+  if (info) {
+    memset(info, 0, sizeof *info);
+    float ms = 0.f;
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&ms, e0, e1);
+    info->ms = ms;
+    info->iters = hs.iters;
+    info->status = hs.status;
+    double h[2] = {0, 0};
+    // relres from (r,r) and (r0,r0): converted on the device, read back.
+    double* dd = nullptr;
+    if (r == MP_OK && cudaMallocAsync((void**)&dd, 2 * sizeof(double), st) == cudaSuccess) {
+      mp_vec v1{1, c.A->prec, 1, w.scal(RR)}, v2{1, c.A->prec, 1, w.scal(RR0)};
+      if (hs.iters == 0) v1 = v2;
+      mp_vec_to_f64(v1, dd, st);
+      mp_vec_to_f64(v2, dd + 1, st);
+      cudaMemcpyAsync(h, dd, sizeof h, cudaMemcpyDeviceToHost, st);
+      cudaFreeAsync(dd, st);
+      cudaStreamSynchronize(st);
+      info->relres = (h[1] > 0) ? sqrt(h[0] / h[1]) : 0.0;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  free_work(w, st);
+  if (r != MP_OK) return r;
+  cudaStreamSynchronize(st);
+  return static_cast<mp_status>(hs.status);
+}
+
+mp_status solve(bool gp, mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* opts,
+                mp_solve_info* info, void* stream) {
+  if (!A) return set_error(MP_ERR_ARG, "matrix is null");
+  if (!opts) return set_error(MP_ERR_ARG, "opts is null");
+  mp_status r;
+  if ((r = check_vec(b, A->n, A->prec, "b")) != MP_OK) return r;
+  if ((r = check_vec(x, A->n, A->prec, "x")) != MP_OK) return r;
+  if (A->n > 0 && b.data == x.data) return set_error(MP_ERR_ARG, "b and x must not alias");
+  if (!(opts->rtol >= 0) || !(opts->atol >= 0) || !isfinite(opts->rtol) || !isfinite(opts->atol))
+    return set_error(MP_ERR_ARG, "rtol/atol must be finite and >= 0");
+  if (opts->maxit < 0) return set_error(MP_ERR_ARG, "maxit < 0");
+  if (opts->mode != MP_ORDERED && opts->mode != MP_EXACT)
+    return set_error(MP_ERR_ARG, "mode %d", opts->mode);
+  if (opts->history.data) {
+    if ((r = check_vec(opts->history, opts->history.n, A->prec, "history")) != MP_OK) return r;
+  }
+  if (!gp && !A->has_t) return set_error(MP_ERR_ARG, "BiCG needs MP_CSR_TRANSPOSE");
+  if (!status_word()) return set_error(MP_ERR_CUDA, "status word unavailable");
+  SolveCall c{A, b, x, *opts, static_cast<cudaStream_t>(stream)};
+  return dispatch_w(A->prec, [&](auto w) {
+    constexpr int W = decltype(w)::value;
+    return gp ? solve_w<W, true>(c, info) : solve_w<W, false>(c, info);
+  });
+}
+
+}  // namespace
+}  // namespace mpk
+
+extern "C" {
+
+mp_status mp_bicg(mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* opts, mp_solve_info* info,
+                  void* stream) {
+  return mpk::solve(false, A, b, x, opts, info, stream);
+}
+
+mp_status mp_gpbicg(mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* opts, mp_solve_info* info,
+                    void* stream) {
+  return mpk::solve(true, A, b, x, opts, info, stream);
+}
+
+}  // extern "C"

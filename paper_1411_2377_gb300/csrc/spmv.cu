@@ -1,0 +1,356 @@
+// spmv.cu -- p-bit sparse matrix-vector products on the sliced layout.
+//
+// One thread owns one row (a warp owns a 32-row chunk), so the ORDERED
+// row loop of Section 3 -- y <- RN(y + RN(a*x)) in column order, skipping
+// zero factors -- runs unchanged in each thread's registers, and a warp's
+// loads of entry j of its 32 rows are 32 consecutive words of every plane.
+//
+// EXACT rows sum their products exactly: a pre-pass over the row's heads finds
+// the exponent range [Emin, Emax] of its nonzero terms; each exact 2p-bit
+// product P*2^(E-2p) is added as P*2^(E-Emin) into 64-bit signed counters
+// over 32-bit digits (no carries while accumulating); the carries are
+// resolved and the sum rounded once.  Counters live in shared memory,
+// digit-major so that a warp's 32 threads always hit 32 distinct banks.  A
+// row whose span does not fit the per-thread window goes to an overflow list
+// handled by a warp-per-row kernel with a window of the full span cap.
+#include <climits>
+
+#include "internal.h"
+#include "mpdev.cuh"
+
+namespace mpk {
+namespace {
+
+constexpr int kThreads = 128;   // 4 chunks per block
+constexpr int kFastSpan = 512;  // bits of exponent span handled per thread
+
+template <int W>
+struct Win {
+  static constexpr int fast = (kFastSpan + 64 * W + 96) / 32 + 1;  // digits per thread
+  static constexpr int cap = (SPAN_CAP + 64 * W + 96) / 32 + 1;    // digits for the cap
+};
+
+__host__ __device__ inline int digits_for(int64_t span, int W) {
+  return (int)((span + 64 * W + 96) / 32) + 1;
+}
+
+struct SellView {
+  int64_t nchunks, nslots;
+  const int64_t* __restrict__ chunk_off;
+  const int32_t* __restrict__ row_of;
+  const int32_t* __restrict__ row_len;
+  const int32_t* __restrict__ col;
+  const uint64_t* __restrict__ val;
+};
+
+SellView view(const Sell& S) {
+  return SellView{S.nchunks, S.nslots, S.chunk_off, S.row_of, S.row_len, S.col, S.val};
+}
+
+__device__ __forceinline__ void record_status(int* status, int code) {
+  if (status) atomicCAS(status, 0, code);
+}
+
+// ---------------------------------------------------------------------------
+// ORDERED
+// ---------------------------------------------------------------------------
+
+template <int W>
+__global__ void __launch_bounds__(kThreads) spmv_ordered_kernel(
+    const SellView S, const uint64_t* __restrict__ x, int64_t ldx, uint64_t* __restrict__ y,
+    int64_t ldy, const int* __restrict__ gate) {
+  if (gate && *gate) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t chunk = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (chunk >= S.nchunks) return;
+  const int64_t slot = chunk * 32 + lane;
+  const int32_t row = S.row_of[slot];
+  const int32_t len = S.row_len[slot];
+  const int64_t base = S.chunk_off[chunk] + lane;
+  Num<W> acc;
+  set_zero(acc, 0u);
+  for (int32_t j = 0; j < len; ++j) {
+    const int64_t k = base + (int64_t)j * 32;
+    const int32_t c = S.col[k];
+    Num<W> a, xv;
+    load<W>(a, S.val, S.nslots, k);
+    load<W>(xv, x, ldx, c);
+    if (zero_e(a.e) || zero_e(xv.e)) continue;  // zero fast path
+    Num<W> t, s;
+    mul_rn<W>(a, xv, t);
+    add_rn<W>(acc, t, s);
+    acc = s;
+  }
+  if (row >= 0) store<W>(acc, y, ldy, row);
+}
+
+// ---------------------------------------------------------------------------
+// EXACT (and the residual r = RN(b - A x))
+// ---------------------------------------------------------------------------
+
+// Adds (-1)^neg * P * 2^off into counters c[d*stride].
+template <int W>
+__device__ __forceinline__ void add_term(int64_t* c, int stride, const uint32_t (&P)[2 * W],
+                                         int64_t off, uint32_t neg) {
+  uint32_t D[2 * W + 1];
+  shifted_digits<W>(P, (uint32_t)(off & 31), D);
+  int64_t* p = c + (off >> 5) * stride;
+#pragma unroll
+  for (int k = 0; k <= 2 * W; ++k) {
+    const int64_t v = (int64_t)D[k];
+    p[k * stride] += neg ? -v : v;
+  }
+}
+
+template <int W>
+__device__ __forceinline__ void value_as_product(const Num<W>& b, uint32_t (&P)[2 * W]) {
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    P[k] = 0u;
+    P[W + k] = b.m[k];
+  }
+}
+
+template <int W, bool RESID>
+__global__ void __launch_bounds__(kThreads) spmv_exact_kernel(
+    const SellView S, const uint64_t* __restrict__ x, int64_t ldx, uint64_t* __restrict__ y,
+    int64_t ldy, const uint64_t* __restrict__ bv, int64_t ldb, int32_t* __restrict__ ovf,
+    int* __restrict__ status, const int* __restrict__ gate) {
+  extern __shared__ int64_t sacc[];
+  if (gate && *gate) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t chunk = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (chunk >= S.nchunks) return;
+  const int64_t slot = chunk * 32 + lane;
+  const int32_t row = S.row_of[slot];
+  if (row < 0) return;
+  const int32_t len = S.row_len[slot];
+  const int64_t base = S.chunk_off[chunk] + lane;
+
+  // pass 1: exponent range of the nonzero terms
+  int64_t emin = LLONG_MAX, emax = LLONG_MIN;
+  Num<W> b;
+  if (RESID) {
+    load<W>(b, bv, ldb, row);
+    if (!zero_e(b.e)) emin = emax = b.e;
+  }
+  for (int32_t j = 0; j < len; ++j) {
+    const int64_t k = base + (int64_t)j * 32;
+    int64_t ea, ex;
+    uint32_t sa, sx;
+    unpack_head(__ldg(S.val + k), ea, sa);
+    unpack_head(__ldg(x + S.col[k]), ex, sx);
+    if (zero_e(ea) || zero_e(ex)) continue;
+    const int64_t E = ea + ex;
+    emin = min(emin, E);
+    emax = max(emax, E);
+  }
+  Num<W> r;
+  if (emin > emax) {  // no terms
+    set_zero(r, 0u);
+    store<W>(r, y, ldy, row);
+    return;
+  }
+  const int64_t span = emax - emin;
+  if (span > SPAN_CAP) {
+    set_zero(r, 0u);
+    store<W>(r, y, ldy, row);
+    record_status(status, MP_ERR_SPAN);
+    return;
+  }
+  const int nd = digits_for(span, W);
+  if (nd > Win<W>::fast) {
+    const int pos = atomicAdd(ovf, 1);
+    ovf[1 + pos] = (int32_t)slot;
+    return;
+  }
+  const int stride = blockDim.x;
+  int64_t* c = sacc + threadIdx.x;
+  for (int d = 0; d < nd; ++d) c[d * stride] = 0;
+
+  // pass 2: exact products into the counters
+  uint32_t P[2 * W];
+  if (RESID && !zero_e(b.e)) {
+    value_as_product<W>(b, P);
+    add_term<W>(c, stride, P, b.e - emin, b.s);
+  }
+  for (int32_t j = 0; j < len; ++j) {
+    const int64_t k = base + (int64_t)j * 32;
+    const int32_t col = S.col[k];
+    Num<W> a, xv;
+    load<W>(a, S.val, S.nslots, k);
+    load<W>(xv, x, ldx, col);
+    if (zero_e(a.e) || zero_e(xv.e)) continue;
+    mul_full<W>(a.m, xv.m, P);
+    add_term<W>(c, stride, P, a.e + xv.e - emin, a.s ^ xv.s ^ (RESID ? 1u : 0u));
+  }
+  const uint32_t negative = resolve_digits(c, stride, nd);
+  if (negative) negate_words(c, stride, nd);
+  round_words<W>(c, stride, nd, emin - 64 * W, negative, r);
+  store<W>(r, y, ldy, row);
+}
+
+// Rows from the overflow list: one warp per row, lanes over the row's
+// entries, a shared window of the full span cap filled with atomics.
+template <int W, bool RESID>
+__global__ void __launch_bounds__(32) spmv_exact_wide_kernel(
+    const SellView S, const uint64_t* __restrict__ x, int64_t ldx, uint64_t* __restrict__ y,
+    int64_t ldy, const uint64_t* __restrict__ bv, int64_t ldb, const int32_t* __restrict__ ovf,
+    const int* __restrict__ gate) {
+  __shared__ int64_t acc[Win<W>::cap];
+  if (gate && *gate) return;
+  const int count = ovf[0];
+  const int lane = threadIdx.x;
+  for (int item = blockIdx.x; item < count; item += gridDim.x) {
+    const int64_t slot = ovf[1 + item];
+    const int64_t chunk = slot >> 5;
+    const int t = (int)(slot & 31);
+    const int32_t row = S.row_of[slot];
+    const int32_t len = S.row_len[slot];
+    const int64_t base = S.chunk_off[chunk] + t;
+    int64_t emin = LLONG_MAX;
+    Num<W> b;
+    if (RESID) {
+      load<W>(b, bv, ldb, row);
+      if (!zero_e(b.e)) emin = b.e;
+    }
+    for (int32_t j = lane; j < len; j += 32) {
+      const int64_t k = base + (int64_t)j * 32;
+      int64_t ea, ex;
+      uint32_t sa, sx;
+      unpack_head(__ldg(S.val + k), ea, sa);
+      unpack_head(__ldg(x + S.col[k]), ex, sx);
+      if (!zero_e(ea) && !zero_e(ex)) emin = min(emin, ea + ex);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) emin = min(emin, __shfl_xor_sync(0xffffffffu, emin, o));
+    for (int d = lane; d < Win<W>::cap; d += 32) acc[d] = 0;
+    __syncwarp();
+    uint32_t P[2 * W];
+    if (RESID && lane == 0 && !zero_e(b.e)) {
+      value_as_product<W>(b, P);
+      uint32_t D[2 * W + 1];
+      const int64_t off = b.e - emin;
+      shifted_digits<W>(P, (uint32_t)(off & 31), D);
+      for (int k = 0; k <= 2 * W; ++k) {
+        const int64_t v = (int64_t)D[k];
+        atomicAdd((unsigned long long*)&acc[(off >> 5) + k], (unsigned long long)(b.s ? -v : v));
+      }
+    }
+    for (int32_t j = lane; j < len; j += 32) {
+      const int64_t k = base + (int64_t)j * 32;
+      Num<W> a, xv;
+      load<W>(a, S.val, S.nslots, k);
+      load<W>(xv, x, ldx, S.col[k]);
+      if (zero_e(a.e) || zero_e(xv.e)) continue;
+      mul_full<W>(a.m, xv.m, P);
+      uint32_t D[2 * W + 1];
+      const int64_t off = a.e + xv.e - emin;
+      shifted_digits<W>(P, (uint32_t)(off & 31), D);
+      const uint32_t ng = a.s ^ xv.s ^ (RESID ? 1u : 0u);
+      for (int kk = 0; kk <= 2 * W; ++kk) {
+        const int64_t v = (int64_t)D[kk];
+        atomicAdd((unsigned long long*)&acc[(off >> 5) + kk], (unsigned long long)(ng ? -v : v));
+      }
+    }
+    __syncwarp();
+    if (lane == 0) {
+      const int nd = Win<W>::cap;
+      const uint32_t negative = resolve_digits(acc, 1, nd);
+      if (negative) negate_words(acc, 1, nd);
+      Num<W> r;
+      round_words<W>(acc, 1, nd, emin - 64 * W, negative, r);
+      store<W>(r, y, ldy, row);
+    }
+    __syncwarp();
+  }
+}
+
+template <int W>
+mp_status spmv_w(const mp_csr_s* M, const Sell& S, int mode, const uint64_t* x, int64_t ldx,
+                 uint64_t* y, int64_t ldy, const uint64_t* b, int64_t ldb, const int* gate,
+                 cudaStream_t st) {
+  if (S.nchunks == 0) return MP_OK;
+  const SellView V = view(S);
+  const int blocks = (int)((S.nchunks * 32 + kThreads - 1) / kThreads);
+  if (mode == MP_ORDERED && !b) {
+    spmv_ordered_kernel<W><<<blocks, kThreads, 0, st>>>(V, x, ldx, y, ldy, gate);
+    count_launch();
+    return launch_check("spmv_ordered_kernel");
+  }
+  int* status = status_word();
+  if (!status) return set_error(MP_ERR_CUDA, "status word unavailable");
+  MPK_CUDA(cudaMemsetAsync(M->ovf, 0, sizeof(int32_t), st));
+  const size_t smem = (size_t)Win<W>::fast * kThreads * sizeof(int64_t);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (b) {
+    MPK_CUDA(cudaFuncSetAttribute(spmv_exact_kernel<W, true>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    spmv_exact_kernel<W, true><<<blocks, kThreads, smem, st>>>(V, x, ldx, y, ldy, b, ldb, M->ovf,
+                                                               status, gate);
+    spmv_exact_wide_kernel<W, true><<<sms * 4, 32, 0, st>>>(V, x, ldx, y, ldy, b, ldb, M->ovf, gate);
+  } else {
+    MPK_CUDA(cudaFuncSetAttribute(spmv_exact_kernel<W, false>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    spmv_exact_kernel<W, false><<<blocks, kThreads, smem, st>>>(V, x, ldx, y, ldy, nullptr, 0,
+                                                                M->ovf, status, gate);
+    spmv_exact_wide_kernel<W, false><<<sms * 4, 32, 0, st>>>(V, x, ldx, y, ldy, nullptr, 0,
+                                                             M->ovf, gate);
+  }
+  count_launch(2);
+  return launch_check("spmv_exact_kernel");
+}
+
+mp_status check_spmv_args(mp_csr A, const mp_vec& x, const mp_vec& y, int mode) {
+  if (!A) return set_error(MP_ERR_ARG, "matrix is null");
+  if (mode != MP_ORDERED && mode != MP_EXACT) return set_error(MP_ERR_ARG, "mode %d", mode);
+  mp_status r;
+  if ((r = check_vec(x, A->n, A->prec, "x")) != MP_OK) return r;
+  if ((r = check_vec(y, A->n, A->prec, "y")) != MP_OK) return r;
+  if (A->n > 0 && x.data == y.data) return set_error(MP_ERR_ARG, "x and y must not alias");
+  return MP_OK;
+}
+
+}  // namespace
+
+mp_status launch_spmv(const mp_csr_s* M, const Sell& S, int mode, const uint64_t* x, int64_t ldx,
+                      uint64_t* y, int64_t ldy, const uint64_t* b, int64_t ldb, const int* gate,
+                      cudaStream_t st) {
+  return dispatch_w(M->prec, [&](auto w) {
+    constexpr int W = decltype(w)::value;
+    return spmv_w<W>(M, S, mode, x, ldx, y, ldy, b, ldb, gate, st);
+  });
+}
+
+}  // namespace mpk
+
+using namespace mpk;
+
+extern "C" {
+
+mp_status mp_spmv(mp_csr A, mp_vec x, mp_vec y, mp_mode mode, void* stream) {
+  mp_status r = check_spmv_args(A, x, y, mode);
+  if (r != MP_OK) return r;
+  return launch_spmv(A, A->A, mode, x.data, x.ld, y.data, y.ld, nullptr, 0, nullptr,
+                     static_cast<cudaStream_t>(stream));
+}
+
+mp_status mp_spmv_t(mp_csr A, mp_vec x, mp_vec y, mp_mode mode, void* stream) {
+  mp_status r = check_spmv_args(A, x, y, mode);
+  if (r != MP_OK) return r;
+  if (!A->has_t) return set_error(MP_ERR_ARG, "matrix was created without MP_CSR_TRANSPOSE");
+  return launch_spmv(A, A->AT, mode, x.data, x.ld, y.data, y.ld, nullptr, 0, nullptr,
+                     static_cast<cudaStream_t>(stream));
+}
+
+mp_status mp_residual(mp_csr A, mp_vec b, mp_vec x, mp_vec r_, void* stream) {
+  mp_status r = check_spmv_args(A, x, r_, MP_EXACT);
+  if (r != MP_OK) return r;
+  if ((r = check_vec(b, A->n, A->prec, "b")) != MP_OK) return r;
+  return launch_spmv(A, A->A, MP_EXACT, x.data, x.ld, r_.data, r_.ld, b.data, b.ld, nullptr,
+                     static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

@@ -207,6 +207,21 @@ def random_values(count: int, p: int, seed: int, stream0: int = 0, zero_frac: fl
     return out
 
 
+SPMV_N = 1_000_000
+
+
+def spmv_pattern(n: int = SPMV_N, seed: int = 1):
+    """Pattern of the SpMV throughput workload (seed 1, n = 10^6)."""
+    return random_csr_pattern(n, seed=seed)
+
+
+def spmv_values(p: int, nnz: int, n: int, seed: int = 1):
+    """Values (1 % zeros) and x (no zeros) of the SpMV throughput workload."""
+    vals = random_values(nnz, p, seed=seed)
+    x = random_values(n, p, seed=seed + 1, stream0=1000, zero_frac=0.0)
+    return vals, x
+
+
 def ones(n: int, p: int) -> np.ndarray:
     """(L+1, n) planes holding 1.0 (= 0.1_2 * 2^1)."""
     L = p // 64

@@ -1,0 +1,73 @@
+"""Host-side checks of the native library: it builds for sm_103a, loads
+without a GPU, exports every function include/mpkrylov.h declares, and the
+binding's struct layouts match the header.  No compute call is made."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mpkrylov.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mp_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1411_2377_gb300 import _lib, build
+
+    build.build()
+    return _lib.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("mp_csr_create", "mp_csr_create_f64", "mp_csr_destroy", "mp_spmv", "mp_spmv_t",
+                 "mp_dot", "mp_axpy", "mp_bicg", "mp_gpbicg", "mp_check", "mp_last_error"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_the_header(lib):
+    from paper_1411_2377_gb300 import _lib
+
+    assert set(declared_functions()) <= set(_lib.SIGNATURES)
+
+
+def test_status_strings_without_gpu(lib):
+    assert lib.mp_status_string(0) == b"ok"
+    assert b"span" in lib.mp_status_string(5)
+    assert lib.mp_status_string(99) == b"unknown status"
+
+
+def test_struct_layouts():
+    from paper_1411_2377_gb300 import _lib
+
+    assert ctypes.sizeof(_lib.MpVec) == 32
+    assert _lib.MpVec.ld.offset == 16 and _lib.MpVec.data.offset == 24
+    assert ctypes.sizeof(_lib.MpSolveOpts) == 32 + 32
+    assert ctypes.sizeof(_lib.MpSolveInfo) == 32
+
+
+def test_library_is_built_for_sm_103a(lib):
+    """The device code in the library targets sm_103a (cuobjdump lists the
+    embedded ELF architectures; nothing is disassembled)."""
+    import shutil
+    import subprocess
+
+    tool = shutil.which("cuobjdump") or "/usr/local/cuda/bin/cuobjdump"
+    if not os.path.exists(tool):
+        pytest.skip("cuobjdump not available")
+    from paper_1411_2377_gb300 import _lib
+
+    out = subprocess.run([tool, "--list-elf", _lib.LIB_PATH], capture_output=True, text=True)
+    assert "sm_103a" in out.stdout

@@ -1,0 +1,76 @@
+"""Exact dot products and axpy on the GPU vs the oracle, bit for bit."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import assert_bitwise, need_gpu, rand_planes, recs
+
+pytestmark = pytest.mark.gpu
+PRECS = (128, 256, 512, 1024)
+
+
+@pytest.mark.parametrize("p", PRECS)
+@pytest.mark.parametrize("n,lo,hi", [(1, -3, 3), (31, -3, 3), (4097, -40, 40),
+                                     (100_003, -200, 200), (50_000, -1500, 1500)])
+def test_dot(p, n, lo, hi):
+    """Spans inside the per-warp window and (lo/hi = +-1500) the wide path."""
+    mpk = need_gpu()
+    X = rand_planes(n, p, 61 + n, zero_frac=0.02, emin=lo, emax=hi)
+    Y = rand_planes(n, p, 62 + n, zero_frac=0.02, emin=lo, emax=hi)
+    got = mpk.dot(mpk.Vec.from_planes(X, p), mpk.Vec.from_planes(Y, p))
+    want, st = oracle.dot(p, recs(X), recs(Y))
+    assert st == oracle.OK
+    assert_bitwise(got.planes(), want[None], f"dot p={p} n={n}")
+
+
+@pytest.mark.parametrize("p", (128, 512))
+def test_dot_cancellation_zero_and_span_error(p):
+    mpk = need_gpu()
+    n = 1000
+    X = rand_planes(n, p, 71, zero_frac=0.0)
+    Y = rand_planes(n, p, 72, zero_frac=0.0)
+    Yn = Y.copy()
+    Yn[0] ^= np.uint64(1)
+    x2 = mpk.Vec.from_planes(np.concatenate([X, X], axis=1), p)
+    y2 = mpk.Vec.from_planes(np.concatenate([Y, Yn], axis=1), p)
+    got = mpk.dot(x2, y2).records()[0]
+    assert (got[0].view(np.int64) >> 1) == oracle.EXP_ZERO and got[0] & 1 == 0  # +0
+    # empty vectors
+    got = mpk.dot(mpk.Vec.zeros(0, p), mpk.Vec.zeros(0, p)).records()[0]
+    assert (got[0].view(np.int64) >> 1) == oracle.EXP_ZERO
+    # a span beyond the cap: +0 and MP_ERR_SPAN
+    Xr = recs(X)
+    Xr[5, 0] = np.int64(Xr[5, 0].view(np.int64) - 2 * (oracle.SPAN_CAP + 500)).view(np.uint64)
+    out = mpk.dot(mpk.Vec.from_planes(Xr.T.copy(), p), mpk.Vec.from_planes(Y, p), sync=False)
+    with pytest.raises(mpk.MPError) as e:
+        mpk.check()
+    assert e.value.status == 5
+    want, st = oracle.dot(p, Xr, recs(Y))
+    assert st == oracle.ERR_SPAN
+    assert_bitwise(out.planes(), want[None], "dot span error")
+
+
+@pytest.mark.parametrize("p", PRECS)
+def test_axpy(p):
+    mpk = need_gpu()
+    n = 10_001
+    X = rand_planes(n, p, 81, zero_frac=0.05, emin=-60, emax=60)
+    Y = rand_planes(n, p, 82, zero_frac=0.05, emin=-60, emax=60)
+    al = rand_planes(1, p, 83, zero_frac=0.0)
+    y = mpk.Vec.from_planes(Y, p)
+    mpk.axpy(mpk.Vec.from_planes(al, p), mpk.Vec.from_planes(X, p), y)
+    want, _ = oracle.axpy(p, recs(al), recs(X), recs(Y))
+    assert_bitwise(y.planes(), want, f"axpy p={p}")
+
+
+def test_repeated_dots_reuse_scratch():
+    """Back-to-back dots of different precisions and lengths (the scratch
+    span slots are reset by each dot)."""
+    mpk = need_gpu()
+    for i, p in enumerate((128, 1024, 256, 128, 512)):
+        n = 1000 + 997 * i
+        X = rand_planes(n, p, 90 + i, zero_frac=0.01, emin=-10 * i, emax=10 * i + 1)
+        Y = rand_planes(n, p, 95 + i, zero_frac=0.01)
+        got = mpk.dot(mpk.Vec.from_planes(X, p), mpk.Vec.from_planes(Y, p))
+        want, _ = oracle.dot(p, recs(X), recs(Y))
+        assert_bitwise(got.planes(), want[None], f"dot #{i}")

@@ -1,0 +1,122 @@
+"""Device-resident BiCG and GPBiCG vs the oracle: iteration counts, status,
+every iterate's (r_i, r_i) and the final x, bit for bit."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import assert_bitwise, need_gpu, rand_planes, random_csr, recs
+from paper_1411_2377_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+SOLVERS = {"gpbicg": oracle.gpbicg, "bicg": oracle.bicg}
+
+
+def run_both(mpk, name, rowptr, colidx, vals_planes, b_planes, p, mode, rtol, maxit,
+             poll_every=8, x0=None):
+    A = mpk.CSR(rowptr, colidx, vals_planes, p, transpose=True)
+    b = mpk.Vec.from_planes(b_planes, p)
+    x0v = mpk.Vec.from_planes(x0, p) if x0 is not None else None
+    fn = mpk.gpbicg if name == "gpbicg" else mpk.bicg
+    x, info = fn(A, b, x0=x0v, rtol=rtol, maxit=maxit, mode=mode, poll_every=poll_every,
+                 history=True)
+    m = oracle.ORDERED if mode == "ordered" else oracle.EXACT
+    x0r = recs(x0) if x0 is not None else oracle.empty(p, len(rowptr) - 1)
+    xo, it, st, hist = SOLVERS[name](p, m, rowptr, colidx, recs(vals_planes), recs(b_planes),
+                                     x0r, rtol, 0.0, maxit)
+    return x, info, xo, it, st, hist
+
+
+@pytest.mark.parametrize("name", list(SOLVERS))
+def test_stencil_64x64_p128_to_1e30(name):
+    """The 2-D convection-diffusion system on a 64x64 grid at 128 bits,
+    b = A*ones, stopped at relative residual 1e-30: same iteration count,
+    same (r_i, r_i) at every iteration, same x."""
+    mpk = need_gpu()
+    p = 128
+    rowptr, colidx, v64 = synth.stencil2d(64, seed=0)
+    n = len(rowptr) - 1
+    vals = oracle.from_f64(p, v64)
+    b, _ = oracle.spmv(p, oracle.EXACT, rowptr, colidx, vals, oracle.from_f64(p, np.ones(n)))
+    x, info, xo, it, st, hist = run_both(mpk, name, rowptr, colidx, vals.T.copy(), b.T.copy(), p,
+                                         "ordered", 1e-30, 2000)
+    assert st == oracle.OK and info["status"] == 0
+    assert info["iters"] == it
+    assert_bitwise(info["history"].planes(), hist, f"{name} history")
+    assert_bitwise(x.planes(), xo, f"{name} x")
+    assert info["relres"] <= 1e-30
+
+
+@pytest.mark.parametrize("name", list(SOLVERS))
+@pytest.mark.parametrize("p", (128, 256, 512, 1024))
+@pytest.mark.parametrize("mode", ("ordered", "exact"))
+def test_random_systems_every_precision(name, p, mode):
+    mpk = need_gpu()
+    n = 200
+    rowptr, colidx = random_csr(n, seed=p + 7, mean_len=6, max_len=20)
+    # add a dominant diagonal
+    rows = np.repeat(np.arange(n), np.diff(rowptr))
+    allr = np.concatenate([rows, np.arange(n)])
+    allc = np.concatenate([colidx, np.arange(n)])
+    key = np.unique(allr * n + allc)
+    rowptr = np.zeros(n + 1, np.int64)
+    np.add.at(rowptr, key // n + 1, 1)
+    rowptr = np.cumsum(rowptr)
+    colidx = (key % n).astype(np.int32)
+    V = rand_planes(len(colidx), p, 3, zero_frac=0.0, emin=-1, emax=1)
+    Vr = recs(V)
+    for i in range(n):
+        for k in range(rowptr[i], rowptr[i + 1]):
+            if colidx[k] == i:
+                Vr[k] = oracle.from_f64(p, [float(12 + i % 5)])[0]
+    V = Vr.T.copy()
+    b, _ = oracle.spmv(p, oracle.EXACT, rowptr, colidx, Vr, oracle.from_f64(p, np.ones(n)))
+    x, info, xo, it, st, hist = run_both(mpk, name, rowptr, colidx, V, b.T.copy(), p, mode,
+                                         1e-25, 300, poll_every=3)
+    assert (info["status"], info["iters"]) == (st, it)
+    assert_bitwise(info["history"].planes(), hist, f"{name} p={p} {mode} history")
+    assert_bitwise(x.planes(), xo, f"{name} p={p} {mode} x")
+
+
+@pytest.mark.parametrize("name", list(SOLVERS))
+def test_nonzero_x0_noconv_and_poll_interval(name):
+    """x0 != 0 (exact initial residual), maxit reached ("NC"), and a result
+    that does not depend on how often the host polls."""
+    mpk = need_gpu()
+    p = 256
+    rowptr, colidx, v64 = synth.stencil2d(12, seed=3)
+    n = len(rowptr) - 1
+    vals = oracle.from_f64(p, v64)
+    b, _ = oracle.spmv(p, oracle.EXACT, rowptr, colidx, vals, oracle.from_f64(p, np.ones(n)))
+    X0 = rand_planes(n, p, 5, zero_frac=0.2, emin=-3, emax=3)
+    for poll in (1, 5, 64):
+        x, info, xo, it, st, hist = run_both(mpk, name, rowptr, colidx, vals.T.copy(), b.T.copy(),
+                                             p, "exact", 1e-60, 7, poll_every=poll, x0=X0)
+        assert st == oracle.ERR_NOCONV and info["status"] == st and info["iters"] == it == 7
+        assert_bitwise(info["history"].planes(), hist, f"{name} history")
+        assert_bitwise(x.planes(), xo, f"{name} x poll={poll}")
+
+
+@pytest.mark.parametrize("name", list(SOLVERS))
+def test_breakdown_and_trivial(name):
+    mpk = need_gpu()
+    p = 128
+    rowptr = np.array([0, 1, 2], np.int64)
+    colidx = np.array([1, 0], np.int32)
+    vals = oracle.from_f64(p, [1.0, 1.0]).T.copy()
+    b = oracle.from_f64(p, [1.0, 0.0]).T.copy()
+    x, info, xo, it, st, _ = run_both(mpk, name, rowptr, colidx, vals, b, p, "ordered", 1e-30, 10)
+    assert st == oracle.ERR_BREAKDOWN and info["status"] == st and info["iters"] == it == 0
+    assert_bitwise(x.planes(), xo, "breakdown x")
+    zero_b = oracle.empty(p, 2).T.copy()
+    x, info, xo, it, st, _ = run_both(mpk, name, rowptr, colidx, vals, zero_b, p, "ordered",
+                                      1e-30, 10)
+    assert st == oracle.OK and info["status"] == 0 and info["iters"] == 0
+    # scaled identity: one step (GPBiCG takes the zeta = eta = 0 reading)
+    n = 9
+    rp = np.arange(n + 1, dtype=np.int64)
+    ci = np.arange(n, dtype=np.int32)
+    v = oracle.from_f64(p, np.full(n, 3.0)).T.copy()
+    bb = oracle.from_f64(p, np.arange(1.0, n + 1)).T.copy()
+    x, info, xo, it, st, _ = run_both(mpk, name, rp, ci, v, bb, p, "exact", 1e-30, 10)
+    assert (info["status"], info["iters"]) == (st, it) == (oracle.OK, 1)
+    assert_bitwise(x.planes(), xo, "identity x")

@@ -1,0 +1,180 @@
+"""p-bit CSR SpMV (ORDERED / EXACT), A^T products and residuals on the GPU
+vs the oracle, bit for bit, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import assert_bitwise, need_gpu, rand_planes, random_csr, recs
+from paper_1411_2377_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+PRECS = (128, 256, 512, 1024)
+MODES = (("ordered", oracle.ORDERED), ("exact", oracle.EXACT))
+
+
+@pytest.mark.parametrize("p", PRECS)
+def test_spmv_random_ragged(p):
+    """Several 32-row chunks and sigma windows, a ragged tail (n not a
+    multiple of 32), empty rows, long rows, 5% explicit zeros."""
+    mpk = need_gpu()
+    n = 4099 if p <= 256 else 1187
+    rowptr, colidx = random_csr(n, seed=p, mean_len=10, max_len=150, empty_every=17)
+    V = rand_planes(len(colidx), p, 11, zero_frac=0.05, emin=-20, emax=20)
+    X = rand_planes(n, p, 12, zero_frac=0.05, emin=-20, emax=20)
+    A = mpk.CSR(rowptr, colidx, V, p, transpose=True)
+    x = mpk.Vec.from_planes(X, p)
+    for name, m in MODES:
+        y = mpk.spmv(A, x, mode=name)
+        want, st = oracle.spmv(p, m, rowptr, colidx, recs(V), recs(X))
+        assert st == oracle.OK
+        assert_bitwise(y.planes(), want, f"spmv {name} p={p}")
+        yt = mpk.spmv_t(A, x, mode=name)
+        want_t, _ = oracle.spmv_t(p, m, rowptr, colidx, recs(V), recs(X))
+        assert_bitwise(yt.planes(), want_t, f"spmv_t {name} p={p}")
+
+
+@pytest.mark.parametrize("p", (128, 512))
+def test_unsorted_columns_and_explicit_zeros(p):
+    """Columns given out of order are summed in ascending column order; stored
+    zeros change nothing (Section 2's zero fast path)."""
+    mpk = need_gpu()
+    n = 300
+    rowptr, colidx = random_csr(n, seed=5, mean_len=8, max_len=40)
+    V = rand_planes(len(colidx), p, 21, zero_frac=0.1)
+    X = rand_planes(n, p, 22, zero_frac=0.0)
+    # reverse each row's entries
+    perm = np.concatenate([np.arange(rowptr[i + 1] - 1, rowptr[i] - 1, -1) for i in range(n)])
+    A1 = mpk.CSR(rowptr, colidx, V, p)
+    A2 = mpk.CSR(rowptr, colidx[perm], V[:, perm], p)
+    keep = (recs(V)[:, 0].view(np.int64) >> 1) != oracle.EXP_ZERO
+    rows = np.repeat(np.arange(n), np.diff(rowptr))
+    rp3 = np.zeros(n + 1, np.int64)
+    np.add.at(rp3, rows[keep] + 1, 1)
+    A3 = mpk.CSR(np.cumsum(rp3), colidx[keep], V[:, keep], p)
+    x = mpk.Vec.from_planes(X, p)
+    for name, m in MODES:
+        want, _ = oracle.spmv(p, m, rowptr, colidx, recs(V), recs(X))
+        for A in (A1, A2, A3):
+            assert_bitwise(mpk.spmv(A, x, mode=name).planes(), want, f"{name} p={p}")
+
+
+@pytest.mark.parametrize("p", (128, 1024))
+def test_exact_wide_rows_and_span_cap(p):
+    """EXACT rows whose exponent span exceeds the per-thread window take the
+    wide path; spans beyond the cap are reported and give +0."""
+    mpk = need_gpu()
+    n = 64
+    rowptr, colidx = random_csr(n, seed=9, mean_len=20, max_len=60)
+    V = rand_planes(len(colidx), p, 31, zero_frac=0.0, emin=-2, emax=2)
+    X = rand_planes(n, p, 32, zero_frac=0.0, emin=-2, emax=2)
+    Vr = recs(V)
+    # rows 3 and 40: one entry pushed 3000 bits down (wide path); row 7: beyond the cap
+    for r, shift in ((3, 3000), (40, 9000), (7, oracle.SPAN_CAP + 100)):
+        k = rowptr[r]
+        h = Vr[k, 0].view(np.int64)
+        Vr[k, 0] = np.int64(h - 2 * shift).view(np.uint64)
+    V2 = synth.records_to_planes(Vr)
+    A = mpk.CSR(rowptr, colidx, V2, p)
+    x = mpk.Vec.from_planes(X, p)
+    y = mpk.spmv(A, x, mode="exact", sync=False)
+    with pytest.raises(mpk.MPError) as e:
+        mpk.check()
+    assert e.value.status == 5
+    want, st = oracle.spmv(p, oracle.EXACT, rowptr, colidx, Vr, recs(X))
+    assert st == oracle.ERR_SPAN
+    assert_bitwise(y.planes(), want, f"exact wide p={p}")
+    # ORDERED has no span limit
+    yo = mpk.spmv(A, x, mode="ordered")
+    want_o, _ = oracle.spmv(p, oracle.ORDERED, rowptr, colidx, Vr, recs(X))
+    assert_bitwise(yo.planes(), want_o, f"ordered wide p={p}")
+
+
+@pytest.mark.parametrize("p", (128, 256))
+def test_residual(p):
+    mpk = need_gpu()
+    n = 777
+    rowptr, colidx = random_csr(n, seed=13, mean_len=7, max_len=30, empty_every=11)
+    V = rand_planes(len(colidx), p, 41, zero_frac=0.02, emin=-5, emax=5)
+    X = rand_planes(n, p, 42, zero_frac=0.1, emin=-5, emax=5)
+    B = rand_planes(n, p, 43, zero_frac=0.1, emin=-5, emax=5)
+    A = mpk.CSR(rowptr, colidx, V, p)
+    r = mpk.residual(A, mpk.Vec.from_planes(B, p), mpk.Vec.from_planes(X, p))
+    want, _ = oracle.residual(p, rowptr, colidx, recs(V), recs(B), recs(X))
+    assert_bitwise(r.planes(), want, f"residual p={p}")
+
+
+@pytest.mark.parametrize("p", (128, 256, 1024))
+def test_stencil_f64_matrices(p):
+    """Double-valued matrices (the 2-D and 3-D stencils) converted exactly."""
+    mpk = need_gpu()
+    for rowptr, colidx, v64 in (synth.stencil2d(24, 0), synth.stencil3d(8, 2)):
+        n = len(rowptr) - 1
+        A = mpk.CSR(rowptr, colidx, v64, p, transpose=True)
+        X = rand_planes(n, p, 51, zero_frac=0.0, emin=-3, emax=3)
+        vals = oracle.from_f64(p, v64)
+        x = mpk.Vec.from_planes(X, p)
+        for name, m in MODES:
+            want, _ = oracle.spmv(p, m, rowptr, colidx, vals, recs(X))
+            assert_bitwise(mpk.spmv(A, x, mode=name).planes(), want, f"stencil {name} p={p}")
+
+
+def test_bad_inputs_are_rejected():
+    mpk = need_gpu()
+    p = 128
+    rowptr = np.array([0, 2, 3], np.int64)
+    V = rand_planes(3, p, 1, zero_frac=0.0)
+    with pytest.raises(mpk.MPError):  # column out of range
+        mpk.CSR(rowptr, np.array([0, 5, 1], np.int32), V, p)
+    with pytest.raises(mpk.MPError):  # repeated column
+        mpk.CSR(rowptr, np.array([1, 1, 0], np.int32), V, p)
+    bad = V.copy()
+    bad[p // 64, 1] = 0  # unnormalised mantissa
+    with pytest.raises(mpk.MPError):
+        mpk.CSR(rowptr, np.array([0, 1, 1], np.int32), bad, p)
+    with pytest.raises(mpk.MPError):  # NaN
+        mpk.CSR(rowptr, np.array([0, 1, 1], np.int32), np.array([1.0, np.nan, 2.0]), p)
+    with pytest.raises(mpk.MPError):  # unsupported precision
+        mpk.CSR(rowptr, np.array([0, 1, 1], np.int32), np.array([1.0, 3.0, 2.0]), 192)
+    A = mpk.CSR(rowptr, np.array([0, 1, 1], np.int32), V, p)
+    with pytest.raises(mpk.MPError):  # no transpose built
+        mpk.spmv_t(A, mpk.Vec.zeros(2, p))
+    with pytest.raises(mpk.MPError):  # wrong length
+        mpk.spmv(A, mpk.Vec.zeros(3, p))
+    empty = mpk.CSR(np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros((3, 0), np.uint64), p)
+    y = mpk.spmv(empty, mpk.Vec.zeros(0, p))
+    assert y.n == 0
+
+
+_PATTERN = {}
+
+
+@pytest.mark.parametrize("p", PRECS)
+def test_full_size_sampled_rows(p):
+    """The throughput workload at full size (n = 10^6, lognormal rows, band
+    +-5000, 10% far columns, 1% zeros) in the benchmark's launch
+    configuration; ~400 sampled rows recomputed by the oracle one by one."""
+    mpk = need_gpu()
+    if "p" not in _PATTERN:
+        _PATTERN["p"] = synth.spmv_pattern()
+    rowptr, colidx = _PATTERN["p"]
+    n = len(rowptr) - 1
+    V, X = synth.spmv_values(p, len(colidx), n)
+    A = mpk.CSR(rowptr, colidx, V, p)
+    x = mpk.Vec.from_planes(X, p)
+    rows = np.unique(synth.u64(5, 1, np.arange(400)) % np.uint64(n)).astype(np.int64)
+    lens = np.diff(rowptr)
+    rows = np.unique(np.concatenate([rows, [int(np.argmax(lens)), n - 1, 0]]))
+    Xr = recs(X)
+    for name, mode in MODES:
+        y = mpk.spmv(A, x, mode=name).planes()
+        for r in rows:
+            s, e = int(rowptr[r]), int(rowptr[r + 1])
+            m = e - s
+            sub_rp = np.full(m + 1, m, np.int64)
+            sub_rp[0] = 0
+            want, st = oracle.spmv(p, mode, sub_rp, np.arange(m, dtype=np.int32),
+                                   recs(V[:, s:e]), Xr[colidx[s:e]], rows=(0, 1))
+            assert st == oracle.OK
+            assert np.array_equal(y[:, r], want[0]), (name, p, r)
+        del y
+    A.close()
