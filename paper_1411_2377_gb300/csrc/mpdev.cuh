@@ -284,7 +284,7 @@ __device__ __forceinline__ void add_rn(const Num<W>& a_, const Num<W>& b_, Num<W
     }
     // X - Y - sticky: the true subtrahend exceeds Y by less than one guard ulp
     // when bits were lost, so this is the floor of the exact difference.
-    uint32_t bw = sticky;
+    uint32_t bw = sticky != 0u ? 1u : 0u;
 #pragma unroll
     for (int k = 0; k <= W; ++k) {
       const uint64_t t = (uint64_t)X[k] - Y[k] - bw;

@@ -585,8 +585,17 @@ mp_status bi_iteration(const Work& w, const SolveCall& c, bool first) {
 }
 
 template <int W, bool GP>
-mp_status solve_w(const SolveCall& c, mp_solve_info* info) {
-  cudaStream_t st = c.st;
+mp_status solve_w(const SolveCall& cu, mp_solve_info* info) {
+  // The solve runs on a private non-blocking stream fenced to the caller's
+  // stream by events (the legacy default stream cannot be captured).
+  cudaStream_t st = nullptr;
+  cudaEvent_t fence = nullptr;
+  MPK_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  MPK_CUDA(cudaEventCreateWithFlags(&fence, cudaEventDisableTiming));
+  MPK_CUDA(cudaEventRecord(fence, cu.st));
+  MPK_CUDA(cudaStreamWaitEvent(st, fence, 0));
+  SolveCall c = cu;
+  c.st = st;
   const int64_t n = c.A->n;
   Work w;
   mp_status r = alloc_work(w, c.A->prec, n, GP ? 11 : 6, st);
@@ -688,8 +697,12 @@ mp_status solve_w(const SolveCall& c, mp_solve_info* info) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   free_work(w, st);
-  if (r != MP_OK) return r;
+  cudaEventRecord(fence, st);
+  cudaStreamWaitEvent(cu.st, fence, 0);
   cudaStreamSynchronize(st);
+  cudaEventDestroy(fence);
+  cudaStreamDestroy(st);
+  if (r != MP_OK) return r;
   return static_cast<mp_status>(hs.status);
 }
 
