@@ -155,6 +155,31 @@ mp_status mp_vec_from_f64(const double* d, mp_vec out, void* stream);
 /* Nearest double of each value (reporting only). */
 mp_status mp_vec_to_f64(mp_vec a, double* d, void* stream);
 
+/* ---- allocation-free dot product (the paper has no counterpart) ---------- */
+
+/* Longest vectors mp_dot_noalloc accepts (its 64-bit digit counters stay
+ * exact for up to 2^31 - 1 products). */
+#define MP_DOT_NOALLOC_MAX_N INT64_C(2147483647)
+/* Size of the device array that holds mp_dot_noalloc's scratch. */
+#define MP_DOT_NOALLOC_SCRATCH_BYTES 297088
+
+/* The exact dot product of mp_dot (bit-identical results) for callers that
+ * cannot let a library allocate device memory: processes whose GPU memory is
+ * owned by another allocator (a framework's caching allocator that has
+ * reserved the memory, a server held to a fixed memory budget), where a
+ * cudaMalloc would fail or break the budget, and latency-bound callers that
+ * must avoid the device-wide synchronisation cudaMalloc/cudaFree can cause.
+ * It calls no cudaMalloc, cudaFree or other allocating routine: its scratch
+ * is a fixed device array of MP_DOT_NOALLOC_SCRATCH_BYTES inside the library,
+ * held on every GPU that loads the library until the process exits.  The
+ * first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current; make this first call before
+ * any stream capture.  Every call on a device uses the same array, so calls
+ * that overlap on the GPU (for example on two streams without ordering
+ * between them) race and produce wrong results; order them on one stream.
+ * Vectors longer than MP_DOT_NOALLOC_MAX_N give MP_ERR_ARG. */
+mp_status mp_dot_noalloc(mp_vec x, mp_vec y, mp_vec out, void* stream);
+
 /* ---- solvers (Fig. 5, left preconditioner K = I) ------------------------- */
 
 typedef struct {

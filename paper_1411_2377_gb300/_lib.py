@@ -47,6 +47,7 @@ SIGNATURES = {
     "mp_spmv_t": (_i32, [_vp, MpVec, MpVec, _i32, _vp]),
     "mp_residual": (_i32, [_vp, MpVec, MpVec, MpVec, _vp]),
     "mp_dot": (_i32, [MpVec, MpVec, MpVec, _vp]),
+    "mp_dot_noalloc": (_i32, [MpVec, MpVec, MpVec, _vp]),
     "mp_axpy": (_i32, [MpVec, MpVec, MpVec, _vp]),
     "mp_ewise": (_i32, [_i32, MpVec, MpVec, MpVec, _vp]),
     "mp_vec_from_f64": (_i32, [_vp, MpVec, _vp]),

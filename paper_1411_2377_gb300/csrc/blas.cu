@@ -510,3 +510,111 @@ mp_status mp_vec_to_f64(mp_vec a, double* d, void* stream) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// mp_dot_noalloc: the exact dot product with its scratch in a fixed device
+// array instead of memory from cudaMalloc.
+//
+// Some callers cannot let a library allocate device memory: a process whose
+// GPU memory is owned by another allocator (a framework's caching allocator
+// that has reserved the memory, a server held to a fixed memory budget) would
+// see cudaMalloc fail or break its budget, and cudaMalloc/cudaFree can
+// synchronise the device, which latency-bound callers must avoid.  mp_dot
+// allocates its scratch on first use; this variant never does.  Its scratch
+// is the file-scope array below, present on every GPU that loads the
+// library until the process exits.
+// ---------------------------------------------------------------------------
+
+namespace mpk {
+namespace {
+
+constexpr int kNoAllocBlocks = 64;  // grid of the variant (grid-stride loops cover any n)
+constexpr size_t kNoAllocSpanBytes = 16 * sizeof(long long);
+constexpr size_t kNoAllocBytes =
+    kNoAllocSpanBytes + (size_t)kNoAllocBlocks * DotWin<32>::cap * sizeof(int64_t);
+
+static_assert(kNoAllocBytes == MP_DOT_NOALLOC_SCRATCH_BYTES, "scratch size stated in mpkrylov.h");
+
+static __device__ __align__(256) unsigned char g_dot_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[64] = {};
+
+// Device address of the array for the current device, looked up once per
+// device (host code may not use the array's name as a device address).
+mp_status noalloc_scratch(void** out) {
+  int dev = 0;
+  MPK_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return set_error(MP_ERR_CUDA, "device %d out of range", dev);
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_dot_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(g_dot_noalloc_scratch)");
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return MP_OK;
+}
+
+template <int W>
+mp_status dot_noalloc_w(const DotDev& a, void* scratch, int* status, cudaStream_t st) {
+  DotScratch s;
+  s.emin = static_cast<long long*>(scratch);
+  s.emax = s.emin + 5;
+  s.partials = reinterpret_cast<int64_t*>(static_cast<unsigned char*>(scratch) + kNoAllocSpanBytes);
+  int64_t b = (a.n + kDotThreads - 1) / kDotThreads;
+  s.nblocks = (int)(b < 1 ? 1 : (b > kNoAllocBlocks ? kNoAllocBlocks : b));
+  const size_t need = kNoAllocSpanBytes + (size_t)s.nblocks * DotWin<W>::cap * sizeof(int64_t);
+  if (need > kNoAllocBytes)
+    return set_error(MP_ERR_ARG, "mp_dot_noalloc needs %zu scratch bytes, the array holds %zu",
+                     need, kNoAllocBytes);
+  const size_t smem = dot_smem<W>(1);
+  MPK_CUDA(cudaFuncSetAttribute(dot_accum_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
+  // The array keeps the previous call's contents: the span slots must start
+  // from (+inf, -inf); the partials are written before they are read.
+  reset_span_slots<<<1, 32, 0, st>>>(s.emin, s.emax);
+  dot_span_kernel<W><<<s.nblocks, kDotThreads, 0, st>>>(a, s.emin, s.emax, nullptr);
+  dot_accum_kernel<W><<<s.nblocks, kDotThreads, smem, st>>>(a, s, nullptr);
+  dot_accum_wide_kernel<W><<<s.nblocks, 256, 0, st>>>(a, s, nullptr);
+  dot_finalize_kernel<W><<<1, 256, 0, st>>>(a, s, status, nullptr);
+  count_launch(5);
+  return launch_check("mp_dot_noalloc kernels");
+}
+
+}  // namespace
+}  // namespace mpk
+
+extern "C" {
+
+mp_status mp_dot_noalloc(mp_vec x, mp_vec y, mp_vec out, void* stream) {
+  mp_status r;
+  if (!prec_ok(x.prec_bits)) return set_error(MP_ERR_PREC, "precision %d", x.prec_bits);
+  if ((r = check_vec(x, x.n, x.prec_bits, "x")) != MP_OK) return r;
+  if ((r = check_vec(y, x.n, x.prec_bits, "y")) != MP_OK) return r;
+  if ((r = check_vec(out, 1, x.prec_bits, "out")) != MP_OK) return r;
+  if (x.n > MP_DOT_NOALLOC_MAX_N)
+    return set_error(MP_ERR_ARG, "mp_dot_noalloc: length %lld exceeds the maximum %lld",
+                     (long long)x.n, (long long)MP_DOT_NOALLOC_MAX_N);
+  void* scratch = nullptr;
+  if ((r = noalloc_scratch(&scratch)) != MP_OK) return r;
+  int* status = status_word();
+  if (!status) return set_error(MP_ERR_CUDA, "status word unavailable");
+  DotDev a{};
+  a.k = 1;
+  a.n = x.n;
+  a.x[0] = x.data;
+  a.y[0] = y.data;
+  a.ldx[0] = x.ld;
+  a.ldy[0] = y.ld;
+  a.out[0] = out.data;
+  a.out_ld[0] = out.ld;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return dispatch_w(x.prec_bits, [&](auto w) {
+    constexpr int W = decltype(w)::value;
+    return dot_noalloc_w<W>(a, scratch, status, st);
+  });
+}
+
+}  // extern "C"
