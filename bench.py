@@ -69,6 +69,32 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def kernel_source_hash():
+    """Hash of the SpMV kernel sources (recorded with each ncu capture)."""
+    import hashlib
+
+    csrc = os.path.join(ROOT, "paper_1411_2377_gb300", "csrc")
+    parts = [hashlib.sha256(open(os.path.join(csrc, f), "rb").read()).hexdigest()
+             for f in ("spmv.cu", "mpdev.cuh")]
+    return hashlib.sha256("".join(parts).encode()).hexdigest()[:16]
+
+
+def profiled_traffic(kernel_key):
+    """DRAM bytes per launch of a kernel from a committed ncu summary
+    (profiles/*.md lines 'traffic: <kernel> bytes_per_launch=B source=H'),
+    or None when there is none or the kernel sources changed since."""
+    import glob
+    import re
+
+    h = kernel_source_hash()
+    for path in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        for line in open(path):
+            m = re.match(r"traffic: (\S+) bytes_per_launch=(\d+) source=([0-9a-f]+)", line)
+            if m and m.group(1) == kernel_key and m.group(3) == h:
+                return int(m.group(2))
+    return None
+
+
 def algorithmic(n, nnz, products, p):
     """Bytes and 32x32->64 multiplies of one y = A x."""
     L = p // 64
@@ -343,9 +369,10 @@ def run_native(args):
                             "frac": achieved / peak, "bytes": nbytes, "imads": imads,
                             "share": sum(ts) / total_ms})
     dom = max(kernels, key=lambda k: k["ms"])
+    dom_key = f"spmv_{dom['mode']}_kernel<p={dom['p']}>"
     roofline = {"bound": dom["bound"], "achieved": dom["achieved"], "peak": dom["peak"],
-                "unit": dom["unit"], "frac": dom["frac"], "traffic": None,
-                "kernel": f"spmv_{dom['mode']}_kernel<p={dom['p']}>",
+                "unit": dom["unit"], "frac": dom["frac"], "traffic": profiled_traffic(dom_key),
+                "algorithmic_bytes": dom["bytes"], "kernel": dom_key,
                 "peak_source": (f"{peak_src} hbm_gbs" if dom["bound"] == "hbm" else
                                 f"derived: {sms} SMs x 32 IMAD.WIDE/clk x {max_mhz:.0f} MHz")}
 
@@ -371,9 +398,10 @@ def run_native(args):
         e2e = {"value": units / (ms * 1e-3) / 1e9, "unit": "Gnnz/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": h2d}
 
-    solver = None
+    solver = vectors = None
     if not args.no_solver and rank == 0:
         solver = solver_bench(mpk)
+        vectors = vector_bench(mpk, precs, n, hbm, imad_peak)
 
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
@@ -396,12 +424,50 @@ def run_native(args):
                        "parallelism": f"replicas x{world}", "generate_s": round(gen_s, 1)},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks, "imad_probe_per_s": probe, "kernels": kernels, "solver": solver,
+            "vectors": vectors,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
 
         dist.destroy_process_group()
+
+
+def vector_bench(mpk, precs, n, hbm, imad_peak, reps=10):
+    """Exact dot and axpy on n-vectors (values as in the SpMV workload, no
+    zeros): CUDA-event time per call and the fraction of each one's roofline
+    (dot: 2 vectors read, axpy: 2 read + 1 written; (p/32)^2 multiplies per
+    element)."""
+    import torch
+
+    from paper_1411_2377_gb300 import synth
+
+    out = []
+    stream = torch.cuda.current_stream()
+    for p in precs:
+        L = p // 64
+        X = mpk.Vec.from_planes(synth.random_values(n, p, seed=11, zero_frac=0.0), p)
+        Y = mpk.Vec.from_planes(synth.random_values(n, p, seed=12, zero_frac=0.0), p)
+        al = mpk.Vec.from_planes(synth.random_values(1, p, seed=13, zero_frac=0.0), p)
+        d = mpk.Vec.empty(1, p)
+        for name, fn, nbytes in (("dot", lambda: mpk.dot(X, Y, d, sync=False), 2 * n * (8 * L + 8)),
+                                 ("axpy", lambda: mpk.axpy(al, X, Y, sync=False), 3 * n * (8 * L + 8))):
+            for _ in range(3):
+                fn()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            imads = n * (p // 32) ** 2
+            t_hbm, t_alu = nbytes / (hbm * 1e9), imads / imad_peak
+            frac = max(t_hbm, t_alu) / (ms * 1e-3)
+            out.append({"op": name, "p": p, "n": n, "ms": ms, "bound": "alu" if t_alu > t_hbm else "hbm",
+                        "gelem_s": n / (ms * 1e-3) / 1e9, "frac": frac})
+        mpk.check()
+    return out
 
 
 def solver_bench(mpk):

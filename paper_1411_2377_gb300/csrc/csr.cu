@@ -96,21 +96,33 @@ void build_sell(int64_t n, const int64_t* rowptr, const int32_t* cols, const int
     });
   }
   h.nchunks = (n + 31) / 32;
+  // Chunks are laid out (and so scheduled) longest first across the whole
+  // matrix, so the long sequential row chains start at the beginning of a
+  // launch instead of forming its tail; each chunk keeps its 32 rows from one
+  // sigma window (x locality within the chunk).
+  std::vector<int64_t> clen(h.nchunks, 0);
+  for (int64_t c = 0; c < h.nchunks; ++c)
+    for (int t = 0; t < 32 && c * 32 + t < n; ++t) {
+      const int32_t r = perm[c * 32 + t];
+      clen[c] = std::max<int64_t>(clen[c], rowptr[r + 1] - rowptr[r]);
+    }
+  std::vector<int64_t> corder(h.nchunks);
+  std::iota(corder.begin(), corder.end(), 0);
+  std::stable_sort(corder.begin(), corder.end(),
+                   [&](int64_t a, int64_t b) { return clen[a] > clen[b]; });
   h.chunk_off.assign(h.nchunks + 1, 0);
   h.row_of.assign(h.nchunks * 32, -1);
   h.row_len.assign(h.nchunks * 32, 0);
   for (int64_t c = 0; c < h.nchunks; ++c) {
-    int64_t mx = 0;
+    const int64_t src_chunk = corder[c];
     for (int t = 0; t < 32; ++t) {
-      const int64_t i = c * 32 + t;
+      const int64_t i = src_chunk * 32 + t;
       if (i >= n) break;
       const int32_t r = perm[i];
-      const int64_t len = rowptr[r + 1] - rowptr[r];
-      h.row_of[i] = r;
-      h.row_len[i] = (int32_t)len;
-      mx = std::max(mx, len);
+      h.row_of[c * 32 + t] = r;
+      h.row_len[c * 32 + t] = (int32_t)(rowptr[r + 1] - rowptr[r]);
     }
-    h.chunk_off[c + 1] = h.chunk_off[c] + 32 * mx;
+    h.chunk_off[c + 1] = h.chunk_off[c] + 32 * clen[src_chunk];
   }
   h.nslots = h.chunk_off[h.nchunks];
   h.col.assign(h.nslots, 0);

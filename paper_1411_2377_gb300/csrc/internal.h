@@ -12,10 +12,11 @@ namespace mpk {
 
 // Sliced, row-length-sorted layout of a CSR matrix (SELL-32-sigma).  Rows are
 // sorted by length (descending, ties by row index) inside windows of
-// kSigma rows and packed 32 per chunk; chunk c holds its rows' entries
-// column-major, slot chunk_off[c] + j*32 + lane for the j-th entry of the
-// lane's row, so that a warp reading entry j of 32 rows touches 32
-// consecutive slots.  Each row keeps its CSR column order.
+// kSigma rows and packed 32 per chunk; chunks are then ordered longest first.
+// Chunk c holds its rows' entries column-major, slot chunk_off[c] + j*32 +
+// lane for the j-th entry of the lane's row, so that a warp reading entry j
+// of 32 rows touches 32 consecutive slots.  Each row keeps its CSR column
+// order.
 constexpr int kSigma = 4096;
 
 struct Sell {

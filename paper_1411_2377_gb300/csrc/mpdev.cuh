@@ -80,17 +80,67 @@ __device__ __forceinline__ void store(const Num<W>& a, uint64_t* __restrict__ ba
 // Word-array helpers
 // ---------------------------------------------------------------------------
 
+// Carry-chain primitives (PTX add/sub/mad with the carry flag).  A chain is
+// a run of these calls with nothing between them that writes the flag.
+__device__ __forceinline__ uint32_t add_cc(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm volatile("add.cc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+__device__ __forceinline__ uint32_t addc_cc(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm volatile("addc.cc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+__device__ __forceinline__ uint32_t addc(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm volatile("addc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+__device__ __forceinline__ uint32_t sub_cc(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm volatile("sub.cc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+__device__ __forceinline__ uint32_t subc_cc(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm volatile("subc.cc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+__device__ __forceinline__ uint32_t subc(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm volatile("subc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+__device__ __forceinline__ uint32_t mad_lo_cc(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t r;
+  asm volatile("mad.lo.cc.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+  return r;
+}
+__device__ __forceinline__ uint32_t madc_lo_cc(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t r;
+  asm volatile("madc.lo.cc.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+  return r;
+}
+__device__ __forceinline__ uint32_t mad_hi_cc(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t r;
+  asm volatile("mad.hi.cc.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+  return r;
+}
+__device__ __forceinline__ uint32_t madc_hi_cc(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t r;
+  asm volatile("madc.hi.cc.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+  return r;
+}
+
 // m += inc (inc in {0,1}); a carry out of the top means M reached 2^p, which is
 // renormalised to 2^(p-1) with the exponent raised by one.
 template <int W>
 __device__ __forceinline__ void round_increment(uint32_t (&m)[W], int64_t& e, uint32_t inc) {
-  uint32_t c = inc;
+  m[0] = add_cc(m[0], inc);
 #pragma unroll
-  for (int k = 0; k < W; ++k) {
-    const uint32_t t = m[k] + c;
-    c = (t < c) ? 1u : 0u;
-    m[k] = t;
-  }
+  for (int k = 1; k < W; ++k) m[k] = addc_cc(m[k], 0u);
+  const uint32_t c = addc(0u, 0u);
   if (c) {
     m[W - 1] = 0x80000000u;
     e += 1;
@@ -165,10 +215,36 @@ __host__ __device__ constexpr int stages_for(int maxw) {
   return maxw <= 0 ? 0 : (maxw < 2 ? 1 : 1 + stages_for(maxw / 2));
 }
 
-// r[0..2W) = a * b, schoolbook over 32-bit words (IMAD.WIDE.U32 products).
+// r[0..2W) = a * b, schoolbook over 32-bit words.  Row i adds a_i*b in two
+// carry chains: the low halves of a_i*b_j into r[i+j], then the high halves
+// into r[i+j+1]; each 32x32 product costs one mad.lo and one mad.hi and no
+// separate carry additions.  r[i+W] holds the previous row's final carry
+// when row i starts.
 template <int W>
 __device__ __forceinline__ void mul_full(const uint32_t (&a)[W], const uint32_t (&b)[W],
                                          uint32_t (&r)[2 * W]) {
+#pragma unroll
+  for (int k = 0; k < 2 * W; ++k) r[k] = 0u;
+#pragma unroll
+  for (int i = 0; i < W; ++i) {
+    r[i] = mad_lo_cc(a[i], b[0], r[i]);
+#pragma unroll
+    for (int j = 1; j < W; ++j) r[i + j] = madc_lo_cc(a[i], b[j], r[i + j]);
+    r[i + W] = addc(r[i + W], 0u);
+    r[i + 1] = mad_hi_cc(a[i], b[0], r[i + 1]);
+#pragma unroll
+    for (int j = 1; j < W; ++j) r[i + j + 1] = madc_hi_cc(a[i], b[j], r[i + j + 1]);
+    if (i + W + 1 < 2 * W) r[i + W + 1] = addc(0u, 0u);
+  }
+}
+
+// As mul_full, written with 64-bit products and plain additions: no carry
+// flag is involved, so the compiler can overlap the independent products of a
+// row (more instruction-level parallelism, more ALU instructions).  Used where
+// few warps share an SM.
+template <int W>
+__device__ __forceinline__ void mul_full_ilp(const uint32_t (&a)[W], const uint32_t (&b)[W],
+                                             uint32_t (&r)[2 * W]) {
 #pragma unroll
   for (int k = 0; k < 2 * W; ++k) r[k] = 0u;
 #pragma unroll
@@ -213,6 +289,15 @@ __device__ __forceinline__ void mul_rn(const Num<W>& a, const Num<W>& b, Num<W>&
 
 // r = RN(a+b) with the IEEE/MPFR signed-zero rules of round-to-nearest:
 // (+0)+(-0) = +0, (-0)+(-0) = -0, x + (+-0) = x, exact cancellation = +0.
+//
+// The operand of larger magnitude X and the other one Y sit in a frame of
+// W+1 words whose low word guards the kept bits; Y is shifted right by the
+// exponent difference d, bits below the frame collapsing into `sticky`.  One
+// carry chain forms X + Y (same signs) or X - Y - [sticky != 0] = X + ~Y +
+// [sticky == 0] (opposite signs): the true difference exceeds that floor by
+// less than one guard unit, and sticky stays set.  The (W+2)-word result is
+// normalised by one left shift that puts its leading one at the top (a
+// carry-out gives a shift of 31, cancellation more than 32), then rounded.
 template <int W>
 __device__ __forceinline__ void add_rn(const Num<W>& a_, const Num<W>& b_, Num<W>& r) {
   const bool az = zero_e(a_.e), bz = zero_e(b_.e);
@@ -224,7 +309,12 @@ __device__ __forceinline__ void add_rn(const Num<W>& a_, const Num<W>& b_, Num<W
     }
     return;
   }
-  const bool sw = b_.e > a_.e;
+  // |b| > |a| ?  (exponents first, mantissas only when they tie)
+  uint32_t t0 = sub_cc(a_.m[0], b_.m[0]);
+#pragma unroll
+  for (int k = 1; k < W; ++k) t0 = subc_cc(a_.m[k], b_.m[k]);
+  const uint32_t mlt = subc(0u, 0u) & 1u;
+  const bool sw = (b_.e > a_.e) || (b_.e == a_.e && mlt);
   uint32_t X[W + 1], Y[W + 1];
   X[0] = 0u;
   Y[0] = 0u;
@@ -234,7 +324,7 @@ __device__ __forceinline__ void add_rn(const Num<W>& a_, const Num<W>& b_, Num<W
     Y[k + 1] = sw ? a_.m[k] : b_.m[k];
   }
   int64_t e = sw ? b_.e : a_.e;
-  uint32_t s = sw ? b_.s : a_.s;
+  const uint32_t s = sw ? b_.s : a_.s;
   const uint32_t ys = sw ? a_.s : b_.s;
   const int64_t d = sw ? (b_.e - a_.e) : (a_.e - b_.e);
   if (d >= (int64_t)(32 * W + 2)) {
@@ -245,60 +335,29 @@ __device__ __forceinline__ void add_rn(const Num<W>& a_, const Num<W>& b_, Num<W
     r.s = s;
     return;
   }
-  // Y = (Msmall * 2^32) >> d inside a (W+1)-word frame whose low word guards
-  // the kept bits; bits below the frame collapse into `sticky`.
-  uint32_t sticky = shift_right_sticky<W + 1, stages_for(W)>(Y, (uint32_t)d);
-  if (s == ys) {
-    uint32_t c = 0u;
+  const uint32_t sticky = shift_right_sticky<W + 1, stages_for(W)>(Y, (uint32_t)d);
+  const uint32_t sub = (s != ys) ? 1u : 0u;
+  const uint32_t inv = 0u - sub;
+  uint32_t T[W + 2];
+  // X[0] is 0, so the carry-in enters through the low word
+  T[0] = add_cc(Y[0] ^ inv, sub & (sticky == 0u ? 1u : 0u));
 #pragma unroll
-    for (int k = 0; k <= W; ++k) {
-      const uint64_t t = (uint64_t)X[k] + Y[k] + c;
-      X[k] = (uint32_t)t;
-      c = (uint32_t)(t >> 32);
-    }
-    if (c) {  // carry out: one more bit, shift right by one
-      sticky |= X[0] & 1u;
+  for (int k = 1; k <= W; ++k) T[k] = addc_cc(X[k], Y[k] ^ inv);
+  T[W + 1] = addc(0u, 0u) & (sub ^ 1u);
+  uint32_t any = 0u;
 #pragma unroll
-      for (int k = 0; k < W; ++k) X[k] = __funnelshift_r(X[k], X[k + 1], 1);
-      X[W] = (X[W] >> 1) | 0x80000000u;
-      e += 1;
-    }
-  } else {
-    if (d == 0) {
-      int cmp = 0;
-#pragma unroll
-      for (int k = W; k >= 1; --k) cmp = (cmp != 0) ? cmp : ((X[k] > Y[k]) ? 1 : ((X[k] < Y[k]) ? -1 : 0));
-      if (cmp == 0) {
-        set_zero(r, 0u);
-        return;
-      }
-      if (cmp < 0) {
-#pragma unroll
-        for (int k = 1; k <= W; ++k) {
-          const uint32_t t = X[k];
-          X[k] = Y[k];
-          Y[k] = t;
-        }
-        s = ys;
-      }
-    }
-    // X - Y - sticky: the true subtrahend exceeds Y by less than one guard ulp
-    // when bits were lost, so this is the floor of the exact difference.
-    uint32_t bw = sticky != 0u ? 1u : 0u;
-#pragma unroll
-    for (int k = 0; k <= W; ++k) {
-      const uint64_t t = (uint64_t)X[k] - Y[k] - bw;
-      X[k] = (uint32_t)t;
-      bw = (uint32_t)(t >> 63);
-    }
-    const uint32_t lz = count_leading_zeros<W + 1>(X);
-    shift_left<W + 1, stages_for(W)>(X, lz);
-    e -= (int64_t)lz;
+  for (int k = 0; k < W + 2; ++k) any |= T[k];
+  if (any == 0u) {  // exact cancellation
+    set_zero(r, 0u);
+    return;
   }
-  const uint32_t rb = X[0] >> 31;
-  const uint32_t st = (X[0] << 1) | sticky;
+  const uint32_t lz = count_leading_zeros<W + 2>(T);
+  shift_left<W + 2, stages_for(W + 1)>(T, lz);
+  e += 32 - (int64_t)lz;
+  const uint32_t rb = T[1] >> 31;
+  const uint32_t st = (T[1] << 1) | T[0] | sticky;
 #pragma unroll
-  for (int k = 0; k < W; ++k) r.m[k] = X[k + 1];
+  for (int k = 0; k < W; ++k) r.m[k] = T[k + 2];
   r.e = e;
   r.s = s;
   round_increment<W>(r.m, r.e, rb & ((st != 0u) | (r.m[0] & 1u)));

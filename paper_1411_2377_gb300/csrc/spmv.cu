@@ -51,6 +51,13 @@ __device__ __forceinline__ void record_status(int* status, int code) {
   if (status) atomicCAS(status, 0, code);
 }
 
+// Whether a row loop keeps the next entry's operands in registers while the
+// current one is computed (at p = 1024 the extra registers would spill).
+template <int W>
+struct Pipelined {
+  static constexpr bool value = W <= 16;
+};
+
 // ---------------------------------------------------------------------------
 // ORDERED
 // ---------------------------------------------------------------------------
@@ -69,17 +76,45 @@ __global__ void __launch_bounds__(kThreads) spmv_ordered_kernel(
   const int64_t base = S.chunk_off[chunk] + lane;
   Num<W> acc;
   set_zero(acc, 0u);
-  for (int32_t j = 0; j < len; ++j) {
-    const int64_t k = base + (int64_t)j * 32;
-    const int32_t c = S.col[k];
-    Num<W> a, xv;
-    load<W>(a, S.val, S.nslots, k);
-    load<W>(xv, x, ldx, c);
-    if (zero_e(a.e) || zero_e(xv.e)) continue;  // zero fast path
-    Num<W> t, s;
-    mul_rn<W>(a, xv, t);
-    add_rn<W>(acc, t, s);
-    acc = s;
+  if (Pipelined<W>::value) {
+    // Software pipeline: the column index two entries ahead and the operands
+    // one entry ahead are in flight while the current entry is computed.
+    Num<W> an, xn;
+    int32_t c1 = 0;
+    if (len > 0) {
+      const int32_t c0 = S.col[base];
+      if (len > 1) c1 = S.col[base + 32];
+      load<W>(an, S.val, S.nslots, base);
+      load<W>(xn, x, ldx, c0);
+    }
+    for (int32_t j = 0; j < len; ++j) {
+      const Num<W> a = an, xv = xn;
+      if (j + 1 < len) {
+        const int64_t k1 = base + (int64_t)(j + 1) * 32;
+        const int32_t c = c1;
+        if (j + 2 < len) c1 = S.col[k1 + 32];
+        load<W>(an, S.val, S.nslots, k1);
+        load<W>(xn, x, ldx, c);
+      }
+      if (zero_e(a.e) || zero_e(xv.e)) continue;  // zero fast path
+      Num<W> t, s;
+      mul_rn<W>(a, xv, t);
+      add_rn<W>(acc, t, s);
+      acc = s;
+    }
+  } else {
+    for (int32_t j = 0; j < len; ++j) {
+      const int64_t k = base + (int64_t)j * 32;
+      const int32_t c = S.col[k];
+      Num<W> a, xv;
+      load<W>(a, S.val, S.nslots, k);
+      load<W>(xv, x, ldx, c);
+      if (zero_e(a.e) || zero_e(xv.e)) continue;  // zero fast path
+      Num<W> t, s;
+      mul_rn<W>(a, xv, t);
+      add_rn<W>(acc, t, s);
+      acc = s;
+    }
   }
   if (row >= 0) store<W>(acc, y, ldy, row);
 }
@@ -134,16 +169,29 @@ __global__ void __launch_bounds__(kThreads) spmv_exact_kernel(
     load<W>(b, bv, ldb, row);
     if (!zero_e(b.e)) emin = emax = b.e;
   }
-  for (int32_t j = 0; j < len; ++j) {
-    const int64_t k = base + (int64_t)j * 32;
-    int64_t ea, ex;
-    uint32_t sa, sx;
-    unpack_head(__ldg(S.val + k), ea, sa);
-    unpack_head(__ldg(x + S.col[k]), ex, sx);
-    if (zero_e(ea) || zero_e(ex)) continue;
-    const int64_t E = ea + ex;
-    emin = min(emin, E);
-    emax = max(emax, E);
+  // four entries' loads in flight at a time (the heads only)
+  for (int32_t j0 = 0; j0 < len; j0 += 4) {
+    int32_t cc[4];
+    uint64_t ha[4], hx[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t k = base + (int64_t)(j0 + u) * 32;
+      cc[u] = (j0 + u < len) ? S.col[k] : 0;
+      ha[u] = (j0 + u < len) ? __ldg(S.val + k) : pack_head(EXP_ZERO, 0u);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) hx[u] = __ldg(x + cc[u]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      int64_t ea, ex;
+      uint32_t sa, sx;
+      unpack_head(ha[u], ea, sa);
+      unpack_head(hx[u], ex, sx);
+      if (zero_e(ea) || zero_e(ex)) continue;
+      const int64_t E = ea + ex;
+      emin = min(emin, E);
+      emax = max(emax, E);
+    }
   }
   Num<W> r;
   if (emin > emax) {  // no terms
@@ -174,15 +222,45 @@ __global__ void __launch_bounds__(kThreads) spmv_exact_kernel(
     value_as_product<W>(b, P);
     add_term<W>(c, stride, P, b.e - emin, b.s);
   }
-  for (int32_t j = 0; j < len; ++j) {
-    const int64_t k = base + (int64_t)j * 32;
-    const int32_t col = S.col[k];
-    Num<W> a, xv;
-    load<W>(a, S.val, S.nslots, k);
-    load<W>(xv, x, ldx, col);
-    if (zero_e(a.e) || zero_e(xv.e)) continue;
-    mul_full<W>(a.m, xv.m, P);
-    add_term<W>(c, stride, P, a.e + xv.e - emin, a.s ^ xv.s ^ (RESID ? 1u : 0u));
+  if (Pipelined<W>::value) {
+    Num<W> an, xn;
+    int32_t c1 = 0;
+    if (len > 0) {
+      const int32_t c0 = S.col[base];
+      if (len > 1) c1 = S.col[base + 32];
+      load<W>(an, S.val, S.nslots, base);
+      load<W>(xn, x, ldx, c0);
+    }
+    for (int32_t j = 0; j < len; ++j) {
+      const Num<W> a = an, xv = xn;
+      if (j + 1 < len) {
+        const int64_t k1 = base + (int64_t)(j + 1) * 32;
+        const int32_t cn = c1;
+        if (j + 2 < len) c1 = S.col[k1 + 32];
+        load<W>(an, S.val, S.nslots, k1);
+        load<W>(xn, x, ldx, cn);
+      }
+      if (zero_e(a.e) || zero_e(xv.e)) continue;
+      if (W >= 16)
+        mul_full_ilp<W>(a.m, xv.m, P);
+      else
+        mul_full<W>(a.m, xv.m, P);
+      add_term<W>(c, stride, P, a.e + xv.e - emin, a.s ^ xv.s ^ (RESID ? 1u : 0u));
+    }
+  } else {
+    for (int32_t j = 0; j < len; ++j) {
+      const int64_t k = base + (int64_t)j * 32;
+      const int32_t col = S.col[k];
+      Num<W> a, xv;
+      load<W>(a, S.val, S.nslots, k);
+      load<W>(xv, x, ldx, col);
+      if (zero_e(a.e) || zero_e(xv.e)) continue;
+      if (W >= 16)
+        mul_full_ilp<W>(a.m, xv.m, P);
+      else
+        mul_full<W>(a.m, xv.m, P);
+      add_term<W>(c, stride, P, a.e + xv.e - emin, a.s ^ xv.s ^ (RESID ? 1u : 0u));
+    }
   }
   const uint32_t negative = resolve_digits(c, stride, nd);
   if (negative) negate_words(c, stride, nd);
