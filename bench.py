@@ -402,6 +402,8 @@ def run_native(args):
     if not args.no_solver and rank == 0:
         solver = solver_bench(mpk)
         vectors = vector_bench(mpk, precs, n, hbm, imad_peak)
+        solver["refinement"] = refine_bench(mpk)
+        solver["autograd"] = autograd_bench(mpk)
 
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
@@ -468,6 +470,70 @@ def vector_bench(mpk, precs, n, hbm, imad_peak, reps=10):
                         "gelem_s": n / (ms * 1e-3) / 1e9, "frac": frac})
         mpk.check()
     return out
+
+
+def forward_error(mpk, x, p):
+    """max_i |x_i - 1| at p bits (then rounded to a double): the forward error
+    against x_true = ones, which is within ~cond * 2^-p of the exact
+    solution of A x = RN(A ones)."""
+    import torch
+
+    ones = mpk.Vec.from_f64(torch.ones(x.n, dtype=torch.float64), p)
+    d = mpk.ewise(2, x, ones)
+    return float(d.to_f64().abs().max())
+
+
+def refine_bench(mpk, m=100, p=256, plain_cap=400):
+    """Row-scaled 3-D convection-diffusion (m^3 grid, Pe 50, rows scaled by
+    10^(20 U(0,1)), b = A*ones): mixed-precision refinement against plain
+    p-bit BiCG / GPBiCG (capped at plain_cap iterations)."""
+    from paper_1411_2377_gb300 import synth
+
+    rowptr, colidx, v64 = synth.stencil3d(m, seed=2)
+    A = mpk.CSR(rowptr, colidx, v64, p, transpose=True)
+    n = A.n
+    b = mpk.spmv(A, mpk.Vec.from_f64(np.ones(n), p), mode="exact")
+    out = {"workload": f"stencil3d_{m}^3_pe50_rowscale1e20_p{p}", "n": n, "nnz": A.nnz}
+    mpk.refine(A, b, max_outer=1)  # warm-up (builds the FP64 copy)
+    x, info = mpk.refine(A, b, rtol=2.0 ** (-p + 8), max_outer=40)
+    out["refine"] = dict(info, forward_error=forward_error(mpk, x, p))
+    for name, fn in (("gpbicg", mpk.gpbicg), ("bicg", mpk.bicg)):
+        x, info = fn(A, b, rtol=1e-30, maxit=plain_cap, poll_every=32)
+        out[name] = {"iters": info["iters"], "status": info["status"], "ms": info["ms"],
+                     "relres": info["relres"], "forward_error": forward_error(mpk, x, p)}
+    A.close()
+    return out
+
+
+def autograd_bench(mpk, m=256, p=256):
+    """L = sum x^2 for x = A^{-1} b on the m x m 2-D system: forward solve,
+    adjoint solve with A^T and the pattern gradient, against two plain
+    solves."""
+    import torch
+
+    from paper_1411_2377_gb300 import autograd, synth
+
+    rowptr, colidx, v64 = synth.stencil2d(m, seed=0)
+    A = mpk.CSR(rowptr, colidx, v64, p, transpose=True)
+    n = A.n
+    b = mpk.spmv(A, mpk.Vec.from_f64(np.ones(n), p), mode="exact")
+    two = mpk.Vec.from_f64(torch.full((n,), 2.0, dtype=torch.float64), p)
+    autograd.solve(A, b, rtol=1e-30)  # warm-up
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record()
+    x, fi = autograd.solve(A, b, rtol=1e-30)
+    e1.record()
+    xbar = mpk.ewise(0, two, x)
+    lam, g, bi = autograd.adjoint(A, x, xbar, rtol=1e-30)
+    e2.record()
+    e2.synchronize()
+    _, p1 = mpk.gpbicg(A, b, rtol=1e-30, maxit=100_000)
+    _, p2 = mpk.gpbicg(A, b, rtol=1e-30, maxit=100_000)
+    A.close()
+    return {"workload": f"stencil2d_{m}x{m}_p{p}_loss_sum_x2", "n": n,
+            "forward_ms": e0.elapsed_time(e1), "backward_ms": e1.elapsed_time(e2),
+            "forward_iters": fi["iters"], "adjoint_iters": bi["iters"],
+            "two_plain_solves_ms": p1["ms"] + p2["ms"]}
 
 
 def solver_bench(mpk):

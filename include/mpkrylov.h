@@ -189,6 +189,9 @@ typedef struct {
   int32_t mode;      /* mp_mode used for the SpMVs                              */
   int32_t poll_every;/* iterations between host checks of the device flags (>=1)*/
   mp_vec history;    /* optional (data may be NULL): entry i-1 receives (r_i,r_i) */
+  int32_t transpose; /* 1: solve A^T x = b (needs MP_CSR_TRANSPOSE), e.g. an
+                        adjoint system; 0: A x = b                            */
+  int32_t reserved;  /* must be 0                                             */
 } mp_solve_opts;
 
 typedef struct {
@@ -208,6 +211,43 @@ mp_status mp_bicg(mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* opts,
  * r = t - eta y - zeta A t). */
 mp_status mp_gpbicg(mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* opts,
                     mp_solve_info* info, void* stream);
+
+/* ---- mixed-precision iterative refinement (not in the paper) ------------- */
+
+typedef struct {
+  double rtol;         /* stop when max|dx| <= rtol * max|x| (the correction no
+                          longer changes x at this relative level)          */
+  int64_t max_outer;   /* corrections at most                                */
+  double inner_rtol;   /* relative residual of each FP64 inner solve         */
+  int64_t inner_maxit; /* FP64 GPBiCG iterations per inner solve             */
+  int32_t equilibrate; /* 1: scale the rows of the FP64 copy by powers of two */
+  int32_t poll_every;  /* inner iterations between host checks               */
+} mp_refine_opts;
+
+typedef struct {
+  int64_t outer;       /* corrections applied                                */
+  int64_t inner_iters; /* FP64 GPBiCG iterations over all corrections        */
+  int32_t status;      /* MP_OK or MP_ERR_NOCONV                              */
+  double correction;   /* last max|dx| / max|x|                              */
+  double relres;       /* sqrt((r,r)/(b,b)), r = b - A x exact per row       */
+  double ms;           /* wall time on the stream                            */
+} mp_refine_info;
+
+/* Solves A x = b at p bits by iterative refinement: r = RN_row(b - A x)
+ * (EXACT rows, rounded once, as mp_residual), an FP64 GPBiCG solve of
+ * A d = r scaled by 2^-E (E = the largest exponent of r) on a
+ * row-equilibrated FP64 copy of A (built on first use and kept with the
+ * matrix), then x = RN(x + 2^E d).  FP64 is used only inside the inner solve
+ * and its inner products.  x holds x0 on entry.  Returns info->status. */
+mp_status mp_refine(mp_csr A, mp_vec b, mp_vec x, const mp_refine_opts* opts,
+                    mp_refine_info* info, void* stream);
+
+/* Gradient on the sparsity pattern (the backward pass of a differentiated
+ * solve x = A^{-1} b; not in the paper): given the solution x and the adjoint
+ * lam with A^T lam = dL/dx, writes g_k = RN((-lam_i) * x_j) = dL/da_ij for
+ * every stored entry k = (i, j), at the entry's position in the CSR passed to
+ * mp_csr_create (g has n = nnz values).  dL/db is lam itself. */
+mp_status mp_csr_grad(mp_csr A, mp_vec lam, mp_vec x, mp_vec g, void* stream);
 
 /* ---- status -------------------------------------------------------------- */
 

@@ -21,7 +21,7 @@ from ._lib import (EXP_ZERO, MP_EXACT, MP_OP_ADD, MP_OP_DIV, MP_OP_MUL, MP_OP_SU
                    MP_ORDERED, SPAN_CAP)
 
 __all__ = ["MPError", "Vec", "CSR", "spmv", "spmv_t", "residual", "dot", "axpy", "ewise",
-           "bicg", "gpbicg", "check", "launch_count", "imad_probe", "MODES"]
+           "bicg", "gpbicg", "csr_grad", "check", "launch_count", "imad_probe", "MODES"]
 
 MODES = {"ordered": MP_ORDERED, "exact": MP_EXACT, MP_ORDERED: MP_ORDERED, MP_EXACT: MP_EXACT}
 
@@ -237,11 +237,13 @@ def ewise(op: int, a: Vec, b: Vec, out: Vec | None = None, stream=None, sync=Tru
     return out
 
 
-def _solve(fn, name, A, b, x0, rtol, atol, maxit, mode, poll_every, history, stream):
+def _solve(fn, name, A, b, x0, rtol, atol, maxit, mode, poll_every, history, stream,
+           transpose=False):
     x = x0.clone() if x0 is not None else Vec.zeros(A.n, A.prec)
     hist = Vec.empty(max(maxit, 1), A.prec) if history else None
     opts = _lib.MpSolveOpts(float(rtol), float(atol), int(maxit), MODES[mode], int(poll_every),
-                            hist.c() if hist is not None else _lib.MpVec(0, A.prec, 1, None))
+                            hist.c() if hist is not None else _lib.MpVec(0, A.prec, 1, None),
+                            1 if transpose else 0, 0)
     info = _lib.MpSolveInfo()
     st = fn(A.h, b.c(), x.c(), ctypes.byref(opts), ctypes.byref(info), _stream(stream))
     if st not in (0, _lib.MP_ERR_NOCONV, _lib.MP_ERR_BREAKDOWN):
@@ -254,14 +256,44 @@ def _solve(fn, name, A, b, x0, rtol, atol, maxit, mode, poll_every, history, str
 
 
 def bicg(A: CSR, b: Vec, x0: Vec | None = None, rtol=1e-30, atol=0.0, maxit=1000,
-         mode="ordered", poll_every=8, history=False, stream=None):
-    """BiCG (Fig. 5 left, K = I).  Returns (x, info dict)."""
+         mode="ordered", poll_every=8, history=False, stream=None, transpose=False):
+    """BiCG (Fig. 5 left, K = I).  Returns (x, info dict).  transpose=True
+    solves A^T x = b."""
     return _solve(_lib.load().mp_bicg, "mp_bicg", A, b, x0, rtol, atol, maxit, mode,
-                  poll_every, history, stream)
+                  poll_every, history, stream, transpose)
 
 
 def gpbicg(A: CSR, b: Vec, x0: Vec | None = None, rtol=1e-30, atol=0.0, maxit=1000,
-           mode="ordered", poll_every=8, history=False, stream=None):
-    """GPBiCG (Fig. 5 right).  Returns (x, info dict)."""
+           mode="ordered", poll_every=8, history=False, stream=None, transpose=False):
+    """GPBiCG (Fig. 5 right).  Returns (x, info dict).  transpose=True solves
+    A^T x = b (an adjoint system)."""
     return _solve(_lib.load().mp_gpbicg, "mp_gpbicg", A, b, x0, rtol, atol, maxit, mode,
-                  poll_every, history, stream)
+                  poll_every, history, stream, transpose)
+
+
+def refine(A: CSR, b: Vec, x0: Vec | None = None, rtol=1e-34, max_outer=20, inner_rtol=1e-10,
+           inner_maxit=20_000, equilibrate=True, poll_every=16, stream=None):
+    """Mixed-precision iterative refinement (p-bit exact residual, FP64
+    GPBiCG correction on a row-equilibrated FP64 copy of A).  Returns
+    (x, info dict)."""
+    x = x0.clone() if x0 is not None else Vec.zeros(A.n, A.prec)
+    opts = _lib.MpRefineOpts(float(rtol), int(max_outer), float(inner_rtol), int(inner_maxit),
+                             1 if equilibrate else 0, int(poll_every))
+    info = _lib.MpRefineInfo()
+    st = _lib.load().mp_refine(A.h, b.c(), x.c(), ctypes.byref(opts), ctypes.byref(info),
+                               _stream(stream))
+    if st not in (0, _lib.MP_ERR_NOCONV):
+        raise MPError(st, "mp_refine")
+    return x, {"outer": int(info.outer), "inner_iters": int(info.inner_iters),
+               "status": int(info.status), "correction": float(info.correction),
+               "relres": float(info.relres), "ms": float(info.ms)}
+
+
+def csr_grad(A: CSR, lam: Vec, x: Vec, g: Vec | None = None, stream=None, sync=True) -> Vec:
+    """dL/da_ij = RN((-lam_i) x_j) for every stored entry, in the caller's CSR
+    order (lam solves A^T lam = dL/dx)."""
+    g = g if g is not None else Vec.empty(A.nnz, A.prec)
+    _ok(_lib.load().mp_csr_grad(A.h, lam.c(), x.c(), g.c(), _stream(stream)), "mp_csr_grad")
+    if sync:
+        check(stream)
+    return g

@@ -24,11 +24,24 @@ class MpVec(ctypes.Structure):
 class MpSolveOpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("atol", ctypes.c_double),
                 ("maxit", ctypes.c_int64), ("mode", ctypes.c_int32),
-                ("poll_every", ctypes.c_int32), ("history", MpVec)]
+                ("poll_every", ctypes.c_int32), ("history", MpVec),
+                ("transpose", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class MpSolveInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int64), ("status", ctypes.c_int32),
+                ("relres", ctypes.c_double), ("ms", ctypes.c_double)]
+
+
+class MpRefineOpts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("max_outer", ctypes.c_int64),
+                ("inner_rtol", ctypes.c_double), ("inner_maxit", ctypes.c_int64),
+                ("equilibrate", ctypes.c_int32), ("poll_every", ctypes.c_int32)]
+
+
+class MpRefineInfo(ctypes.Structure):
+    _fields_ = [("outer", ctypes.c_int64), ("inner_iters", ctypes.c_int64),
+                ("status", ctypes.c_int32), ("correction", ctypes.c_double),
                 ("relres", ctypes.c_double), ("ms", ctypes.c_double)]
 
 
@@ -56,6 +69,9 @@ SIGNATURES = {
                        ctypes.POINTER(MpSolveInfo), _vp]),
     "mp_gpbicg": (_i32, [_vp, MpVec, MpVec, ctypes.POINTER(MpSolveOpts),
                          ctypes.POINTER(MpSolveInfo), _vp]),
+    "mp_csr_grad": (_i32, [_vp, MpVec, MpVec, MpVec, _vp]),
+    "mp_refine": (_i32, [_vp, MpVec, MpVec, ctypes.POINTER(MpRefineOpts),
+                         ctypes.POINTER(MpRefineInfo), _vp]),
     "mp_check": (_i32, [_vp]),
     "mp_status_string": (ctypes.c_char_p, [_i32]),
     "mp_last_error": (ctypes.c_char_p, []),

@@ -156,6 +156,7 @@ void free_sell(Sell& s) {
   cudaFree(s.row_len);
   cudaFree(s.col);
   cudaFree(s.val);
+  cudaFree(s.src);
   s = Sell{};
 }
 
@@ -181,15 +182,13 @@ mp_status upload_sell(const HostSell& h, int64_t n, int64_t nnz, int L, const ui
   }
   if (h.nslots > 0) {
     MPK_CUDA(cudaMemcpyAsync(S.col, h.col.data(), h.col.size() * 4, cudaMemcpyHostToDevice, st));
-    int64_t* d_src = nullptr;
-    int64_t scratch = 0;
-    if ((r = dalloc(&d_src, h.src.size(), scratch)) != MP_OK) return r;
-    MPK_CUDA(cudaMemcpyAsync(d_src, h.src.data(), h.src.size() * 8, cudaMemcpyHostToDevice, st));
-    gather_planes<<<grid_for(h.nslots, 256), 256, 0, st>>>(d_raw, nnz, d_src, h.nslots, L, S.val);
+    // the slot -> caller position map stays (gradients on the pattern use it)
+    if ((r = dalloc(&S.src, h.src.size(), bytes)) != MP_OK) return r;
+    MPK_CUDA(cudaMemcpyAsync(S.src, h.src.data(), h.src.size() * 8, cudaMemcpyHostToDevice, st));
+    gather_planes<<<grid_for(h.nslots, 256), 256, 0, st>>>(d_raw, nnz, S.src, h.nslots, L, S.val);
     count_launch();
     r = launch_check("gather_planes");
     cudaStreamSynchronize(st);
-    cudaFree(d_src);
     if (r != MP_OK) return r;
   }
   return MP_OK;
@@ -378,6 +377,8 @@ mp_status mp_csr_destroy(mp_csr A) {
   free_sell(A->A);
   free_sell(A->AT);
   cudaFree(A->ovf);
+  cudaFree(A->a64);
+  cudaFree(A->rowscale);
   delete A;
   cudaSetDevice(cur);
   return MP_OK;

@@ -26,6 +26,7 @@ struct Sell {
   int32_t* row_len = nullptr;    // [nchunks * 32]
   int32_t* col = nullptr;        // [nslots]
   uint64_t* val = nullptr;       // [(L+1) * nslots], plane-major
+  int64_t* src = nullptr;        // [nslots], the entry's position in the caller's CSR (-1: padding)
 };
 
 }  // namespace mpk
@@ -38,6 +39,10 @@ struct mp_csr_s {
   mpk::Sell A, AT;
   int32_t* ovf = nullptr;  // [n + 1]: overflow-row count then rows (EXACT wide path)
   int64_t bytes = 0;
+  // FP64 copy for mixed-precision refinement (built on first use): the
+  // row-equilibrated entries 2^-E_i a_ij per slot of A's layout, and 2^-E_i.
+  double* a64 = nullptr;
+  double* rowscale = nullptr;
 };
 
 namespace mpk {
@@ -91,6 +96,7 @@ struct DotArgs {
   int64_t out_ld[5] = {};
 };
 size_t dot_scratch_bytes(int prec, int k);
+mp_status init_dot_scratch(void* scratch, cudaStream_t st);
 mp_status launch_dot(int prec, const DotArgs& a, void* scratch, const int* gate,
                      cudaStream_t st);
 

@@ -30,8 +30,6 @@
 #include "mpdev.cuh"
 
 namespace mpk {
-mp_status init_dot_scratch(void* scratch, cudaStream_t st);
-
 namespace {
 
 struct SState {
@@ -478,6 +476,10 @@ struct SolveCall {
   cudaStream_t st;
 };
 
+// The operator of the solve (A, or A^T for an adjoint solve) and its transpose.
+const Sell& op_a(const SolveCall& c) { return c.o.transpose ? c.A->AT : c.A->A; }
+const Sell& op_at(const SolveCall& c) { return c.o.transpose ? c.A->A : c.A->AT; }
+
 // One iteration body for i >= 2 (captured into a graph) or i = 1.
 template <int W>
 mp_status gp_iteration(const Work& w, const SolveCall& c, bool first) {
@@ -496,7 +498,7 @@ mp_status gp_iteration(const Work& w, const SolveCall& c, bool first) {
                                 w.vec(WV), ld, n);
     count_launch(2);
   }
-  if ((r = launch_spmv(c.A, c.A->A, c.o.mode, w.vec(P), ld, w.vec(Q), ld, nullptr, 0, gate, st)) != MP_OK)
+  if ((r = launch_spmv(c.A, op_a(c),c.o.mode, w.vec(P), ld, w.vec(Q), ld, nullptr, 0, gate, st)) != MP_OK)
     return r;
   if ((r = dot2(w, w.vec(RT), w.vec(Q), DEN, nullptr, nullptr, 0, st, gate)) != MP_OK) return r;
   sc_alpha<W><<<1, 1, 0, st>>>(w.st, w.S);
@@ -508,7 +510,7 @@ mp_status gp_iteration(const Work& w, const SolveCall& c, bool first) {
                                  w.vec(Y), ld, n);
   }
   count_launch();
-  if ((r = launch_spmv(c.A, c.A->A, c.o.mode, w.vec(T), ld, w.vec(V), ld, nullptr, 0, gate, st)) != MP_OK)
+  if ((r = launch_spmv(c.A, op_a(c),c.o.mode, w.vec(T), ld, w.vec(V), ld, nullptr, 0, gate, st)) != MP_OK)
     return r;
   DotArgs d;
   d.n = n;
@@ -567,9 +569,9 @@ mp_status bi_iteration(const Work& w, const SolveCall& c, bool first) {
     bi_p<W><<<g, 128, 0, st>>>(w.st, w.S, w.vec(R), w.vec(RT), w.vec(P), w.vec(PT), ld, n);
     count_launch(2);
   }
-  if ((r = launch_spmv(c.A, c.A->A, c.o.mode, w.vec(P), ld, w.vec(Z), ld, nullptr, 0, gate, st)) != MP_OK)
+  if ((r = launch_spmv(c.A, op_a(c),c.o.mode, w.vec(P), ld, w.vec(Z), ld, nullptr, 0, gate, st)) != MP_OK)
     return r;
-  if ((r = launch_spmv(c.A, c.A->AT, c.o.mode, w.vec(PT), ld, w.vec(ZT), ld, nullptr, 0, gate, st)) != MP_OK)
+  if ((r = launch_spmv(c.A, op_at(c),c.o.mode, w.vec(PT), ld, w.vec(ZT), ld, nullptr, 0, gate, st)) != MP_OK)
     return r;
   if ((r = dot2(w, w.vec(PT), w.vec(Z), DEN, nullptr, nullptr, 0, st, gate)) != MP_OK) return r;
   sc_alpha<W><<<1, 1, 0, st>>>(w.st, w.S);
@@ -624,7 +626,7 @@ mp_status solve_w(const SolveCall& cu, mp_solve_info* info) {
       count_launch();
     }
     // r0 = b - A x0 (exact residual), r~ = r0, (r0, r0) and rho_0 = (r~, r0)
-    if ((r = launch_spmv(c.A, c.A->A, MP_EXACT, c.x.data, c.x.ld, w.vec(0), ld, c.b.data, c.b.ld,
+    if ((r = launch_spmv(c.A, op_a(c),MP_EXACT, c.x.data, c.x.ld, w.vec(0), ld, c.b.data, c.b.ld,
                          nullptr, st)) != MP_OK)
       break;
     copy_kernel<W><<<g, 128, 0, st>>>(nullptr, w.vec(0), ld, w.vec(1), ld, n);
@@ -723,6 +725,11 @@ mp_status solve(bool gp, mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* opts
     if ((r = check_vec(opts->history, opts->history.n, A->prec, "history")) != MP_OK) return r;
   }
   if (!gp && !A->has_t) return set_error(MP_ERR_ARG, "BiCG needs MP_CSR_TRANSPOSE");
+  if (opts->transpose != 0 && opts->transpose != 1)
+    return set_error(MP_ERR_ARG, "transpose must be 0 or 1");
+  if (opts->transpose && !A->has_t)
+    return set_error(MP_ERR_ARG, "a solve with A^T needs MP_CSR_TRANSPOSE");
+  if (opts->reserved != 0) return set_error(MP_ERR_ARG, "reserved must be 0");
   if (!status_word()) return set_error(MP_ERR_CUDA, "status word unavailable");
   SolveCall c{A, b, x, *opts, static_cast<cudaStream_t>(stream)};
   return dispatch_w(A->prec, [&](auto w) {

@@ -344,6 +344,34 @@ __global__ void __launch_bounds__(32) spmv_exact_wide_kernel(
   }
 }
 
+// Gradient of a loss on the sparsity pattern: for every stored a_ij,
+// g[pos(i,j)] = RN((-lam_i) * x_j), pos being the entry's position in the
+// caller's CSR.  Same traversal as the products (thread per row).
+template <int W>
+__global__ void __launch_bounds__(kThreads) pattern_grad_kernel(
+    const SellView S, const int64_t* __restrict__ src, const uint64_t* __restrict__ lam,
+    int64_t ldl, const uint64_t* __restrict__ x, int64_t ldx, uint64_t* __restrict__ g,
+    int64_t ldg) {
+  const int lane = threadIdx.x & 31;
+  const int64_t chunk = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (chunk >= S.nchunks) return;
+  const int64_t slot = chunk * 32 + lane;
+  const int32_t row = S.row_of[slot];
+  if (row < 0) return;
+  const int32_t len = S.row_len[slot];
+  const int64_t base = S.chunk_off[chunk] + lane;
+  Num<W> l;
+  load<W>(l, lam, ldl, row);
+  l.s ^= 1u;
+  for (int32_t j = 0; j < len; ++j) {
+    const int64_t k = base + (int64_t)j * 32;
+    Num<W> xv, t;
+    load<W>(xv, x, ldx, S.col[k]);
+    mul_rn<W>(l, xv, t);
+    store<W>(t, g, ldg, src[k]);
+  }
+}
+
 template <int W>
 mp_status spmv_w(const mp_csr_s* M, const Sell& S, int mode, const uint64_t* x, int64_t ldx,
                  uint64_t* y, int64_t ldy, const uint64_t* b, int64_t ldb, const int* gate,
@@ -421,6 +449,25 @@ mp_status mp_spmv_t(mp_csr A, mp_vec x, mp_vec y, mp_mode mode, void* stream) {
   if (!A->has_t) return set_error(MP_ERR_ARG, "matrix was created without MP_CSR_TRANSPOSE");
   return launch_spmv(A, A->AT, mode, x.data, x.ld, y.data, y.ld, nullptr, 0, nullptr,
                      static_cast<cudaStream_t>(stream));
+}
+
+mp_status mp_csr_grad(mp_csr A, mp_vec lam, mp_vec x, mp_vec g, void* stream) {
+  if (!A) return set_error(MP_ERR_ARG, "matrix is null");
+  mp_status r;
+  if ((r = check_vec(lam, A->n, A->prec, "lam")) != MP_OK) return r;
+  if ((r = check_vec(x, A->n, A->prec, "x")) != MP_OK) return r;
+  if ((r = check_vec(g, A->nnz, A->prec, "g")) != MP_OK) return r;
+  if (A->A.nchunks == 0) return MP_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const SellView V = view(A->A);
+  const int blocks = (int)((A->A.nchunks * 32 + kThreads - 1) / kThreads);
+  return dispatch_w(A->prec, [&](auto w) {
+    constexpr int W = decltype(w)::value;
+    pattern_grad_kernel<W><<<blocks, kThreads, 0, st>>>(V, A->A.src, lam.data, lam.ld, x.data, x.ld,
+                                                        g.data, g.ld);
+    count_launch();
+    return launch_check("pattern_grad_kernel");
+  });
 }
 
 mp_status mp_residual(mp_csr A, mp_vec b, mp_vec x, mp_vec r_, void* stream) {

@@ -54,7 +54,7 @@ def test_struct_layouts():
 
     assert ctypes.sizeof(_lib.MpVec) == 32
     assert _lib.MpVec.ld.offset == 16 and _lib.MpVec.data.offset == 24
-    assert ctypes.sizeof(_lib.MpSolveOpts) == 32 + 32
+    assert ctypes.sizeof(_lib.MpSolveOpts) == 32 + 32 + 8
     assert ctypes.sizeof(_lib.MpSolveInfo) == 32
 
 
