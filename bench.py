@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solver", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batch-systems", type=int, default=64,
+                    help="systems of the batched-solve workload to run (256 = all)")
     return ap.parse_args()
 
 
@@ -404,6 +406,7 @@ def run_native(args):
         vectors = vector_bench(mpk, precs, n, hbm, imad_peak)
         solver["refinement"] = refine_bench(mpk)
         solver["autograd"] = autograd_bench(mpk)
+        solver["batched"] = batch_bench(mpk, count=args.batch_systems)
 
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
@@ -534,6 +537,58 @@ def autograd_bench(mpk, m=256, p=256):
             "forward_ms": e0.elapsed_time(e1), "backward_ms": e1.elapsed_time(e2),
             "forward_iters": fi["iters"], "adjoint_iters": bi["iters"],
             "two_plain_solves_ms": p1["ms"] + p2["ms"]}
+
+
+def batch_bench(mpk, count=64, rtol=1e-25):
+    """The first `count` systems of the batched workload (seed 3): for each
+    precision group, one batched GPBiCG solve of all (system, right-hand side)
+    instances against sequential mp_gpbicg solves of the same instances."""
+    import torch
+
+    from paper_1411_2377_gb300 import synth
+
+    descs = synth.batch_systems(seed=3, count=256)[:count]
+    out = {"workload": f"batch_seed3_{count}_systems", "groups": {}}
+    for p in (128, 256):
+        items = [(s, d) for s, d in enumerate(descs) if d["p"] == p]
+        if not items:
+            continue
+        mats, inst, rhs = {}, [], []
+        for s, d in items:
+            rp, ci, va = synth.batch_matrix(d)
+            mats[s] = mpk.CSR(rp, ci, va, p)
+            n = len(rp) - 1
+            for k in range(d["nrhs"]):
+                inst.append((rp, ci, va))
+                rhs.append(mpk.spmv(mats[s], mpk.Vec.from_f64(np.full(n, k + 1.0), p), mode="exact"))
+        owners = [s for s, d in items for _ in range(d["nrhs"])]
+        B = mpk.Batch(inst, p)
+        b = mpk.Vec.zeros(B.n, p)
+        for k, bk in enumerate(rhs):
+            b.t[:, int(B.offsets[k]):int(B.offsets[k + 1])] = bk.t
+        mpk.batch_gpbicg(B, b, rtol=rtol, maxit=2)  # warm-up (module load, graph)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        x, infos = mpk.batch_gpbicg(B, b, rtol=rtol, maxit=100_000, poll_every=32)
+        e1.record()
+        e1.synchronize()
+        batched_ms = e0.elapsed_time(e1)
+        seq_ms, seq_iters = 0.0, []
+        for k, bk in enumerate(rhs):
+            _, info = mpk.gpbicg(mats[owners[k]], bk, rtol=rtol, maxit=100_000, poll_every=32)
+            seq_ms += info["ms"]
+            seq_iters.append(info["iters"])
+        its = [i["iters"] for i in infos]
+        out["groups"][str(p)] = {
+            "systems": len(items), "instances": len(inst), "total_n": B.n,
+            "batched_ms": batched_ms, "sequential_ms": seq_ms, "speedup": seq_ms / batched_ms,
+            "iters_max": max(its), "iters_mean": sum(its) / len(its),
+            "same_iterations_as_single": its == seq_iters,
+            "converged": sum(1 for i in infos if i["status"] == 0)}
+        B.close()
+        for A in mats.values():
+            A.close()
+    return out
 
 
 def solver_bench(mpk):

@@ -212,6 +212,35 @@ mp_status mp_bicg(mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* opts,
 mp_status mp_gpbicg(mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* opts,
                     mp_solve_info* info, void* stream);
 
+/* ---- batched solves (not in the paper; its solver over a batch) ---------- */
+
+typedef struct mp_batch_s* mp_batch; /* opaque; owns its device storage */
+
+/* Stacks k independent instances of one precision (instance i: an n_each[i]
+ * x n_each[i] CSR matrix with double values, converted exactly) into one
+ * block-diagonal device matrix; several right-hand sides of one system are
+ * passed as several instances with the same arrays.  Instance i owns
+ * elements [off[i], off[i+1]) of the batch's concatenated vectors (see
+ * mp_batch_info). */
+mp_status mp_batch_create_f64(int32_t k, const int64_t* n_each, const int64_t* const* rowptrs,
+                              const int32_t* const* colidxs, const double* const* values,
+                              int32_t prec_bits, void* stream, mp_batch* out);
+
+mp_status mp_batch_destroy(mp_batch B);
+
+/* Number of instances, total length and the k+1 offsets (any may be NULL). */
+mp_status mp_batch_info(mp_batch B, int32_t* k, int64_t* total_n, int64_t* offsets);
+
+/* GPBiCG on every instance at once: one SpMV launch, segmented exact inner
+ * products and per-instance scalars per step, one iteration replayed as a
+ * CUDA graph until every instance has exited.  Each instance's iterates
+ * equal those of mp_gpbicg on that instance alone, bit for bit.  b, x are
+ * concatenated vectors (x: x0 in, solutions out); infos[k] receives each
+ * instance's iterations and status (relres is not computed, ms is the
+ * whole batch).  opts->history must be NULL and opts->transpose 0. */
+mp_status mp_batch_gpbicg(mp_batch B, mp_vec b, mp_vec x, const mp_solve_opts* opts,
+                          mp_solve_info* infos, void* stream);
+
 /* ---- mixed-precision iterative refinement (not in the paper) ------------- */
 
 typedef struct {

@@ -271,6 +271,68 @@ def gpbicg(A: CSR, b: Vec, x0: Vec | None = None, rtol=1e-30, atol=0.0, maxit=10
                   poll_every, history, stream, transpose)
 
 
+class Batch:
+    """Independent systems of one precision stacked for batched solves.
+
+    systems: list of (rowptr, colidx, values float64); several right-hand
+    sides of one system are passed as repeated entries."""
+
+    def __init__(self, systems, prec: int, stream=None):
+        lib = _lib.load()
+        self._keep = []
+        ns, rps, cis, vas = [], [], [], []
+        for rowptr, colidx, values in systems:
+            rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+            ci = np.ascontiguousarray(colidx, dtype=np.int32)
+            va = np.ascontiguousarray(values, dtype=np.float64)
+            self._keep += [rp, ci, va]
+            ns.append(rp.shape[0] - 1)
+            rps.append(rp.ctypes.data)
+            cis.append(ci.ctypes.data)
+            vas.append(va.ctypes.data)
+        k = len(ns)
+        n_arr = np.array(ns, dtype=np.int64)
+        ptrs = [np.array(v, dtype=np.uint64) for v in (rps, cis, vas)]
+        handle = ctypes.c_void_p()
+        st = lib.mp_batch_create_f64(k, n_arr.ctypes.data, ptrs[0].ctypes.data, ptrs[1].ctypes.data,
+                                     ptrs[2].ctypes.data, prec, _stream(stream), ctypes.byref(handle))
+        _ok(st, "mp_batch_create_f64")
+        self._keep = []
+        self.h = handle
+        self.k = k
+        self.prec = prec
+        off = np.zeros(k + 1, dtype=np.int64)
+        total = ctypes.c_int64()
+        _ok(lib.mp_batch_info(self.h, None, ctypes.byref(total),
+                              off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))), "mp_batch_info")
+        self.offsets = off
+        self.n = int(total.value)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            _lib.load().mp_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batch_gpbicg(B: Batch, b: Vec, x0: Vec | None = None, rtol=1e-30, atol=0.0, maxit=100_000,
+                 mode="ordered", poll_every=16, stream=None):
+    """GPBiCG on all instances of a Batch at once.  Returns (x, infos)."""
+    x = x0.clone() if x0 is not None else Vec.zeros(B.n, B.prec)
+    opts = _lib.MpSolveOpts(float(rtol), float(atol), int(maxit), MODES[mode], int(poll_every),
+                            _lib.MpVec(0, B.prec, 1, None), 0, 0)
+    infos = (_lib.MpSolveInfo * B.k)()
+    st = _lib.load().mp_batch_gpbicg(B.h, b.c(), x.c(), ctypes.byref(opts), infos,
+                                     _stream(stream))
+    _ok(st, "mp_batch_gpbicg")
+    return x, [{"iters": int(i.iters), "status": int(i.status), "ms": float(i.ms)} for i in infos]
+
+
 def refine(A: CSR, b: Vec, x0: Vec | None = None, rtol=1e-34, max_outer=20, inner_rtol=1e-10,
            inner_maxit=20_000, equilibrate=True, poll_every=16, stream=None):
     """Mixed-precision iterative refinement (p-bit exact residual, FP64

@@ -106,5 +106,9 @@ mp_status launch_dot(int prec, const DotArgs& a, void* scratch, const int* gate,
 mp_status launch_spmv(const mp_csr_s* M, const Sell& S, int mode, const uint64_t* x, int64_t ldx,
                       uint64_t* y, int64_t ldy, const uint64_t* resid_b, int64_t ldb,
                       const int* gate, cudaStream_t st);
+// y = A x skipping rows whose instance k = rinst[row] has idone[k] != 0.
+mp_status launch_spmv_batched(const mp_csr_s* M, int mode, const uint64_t* x, int64_t ldx,
+                              uint64_t* y, int64_t ldy, const int32_t* rinst, const int* idone,
+                              cudaStream_t st);
 
 }  // namespace mpk

@@ -41,10 +41,18 @@ struct SellView {
   const int32_t* __restrict__ row_len;
   const int32_t* __restrict__ col;
   const uint64_t* __restrict__ val;
+  // optional: rows whose instance is marked done are skipped (batched solves)
+  const int32_t* __restrict__ rinst;
+  const int* __restrict__ idone;
 };
 
-SellView view(const Sell& S) {
-  return SellView{S.nchunks, S.nslots, S.chunk_off, S.row_of, S.row_len, S.col, S.val};
+SellView view(const Sell& S, const int32_t* rinst = nullptr, const int* idone = nullptr) {
+  return SellView{S.nchunks, S.nslots, S.chunk_off, S.row_of, S.row_len, S.col, S.val,
+                  rinst, idone};
+}
+
+__device__ __forceinline__ bool row_skipped(const SellView& S, int32_t row) {
+  return row < 0 || (S.idone != nullptr && S.idone[S.rinst[row]] != 0);
 }
 
 __device__ __forceinline__ void record_status(int* status, int code) {
@@ -72,6 +80,7 @@ __global__ void __launch_bounds__(kThreads) spmv_ordered_kernel(
   if (chunk >= S.nchunks) return;
   const int64_t slot = chunk * 32 + lane;
   const int32_t row = S.row_of[slot];
+  if (row_skipped(S, row)) return;
   const int32_t len = S.row_len[slot];
   const int64_t base = S.chunk_off[chunk] + lane;
   Num<W> acc;
@@ -158,7 +167,7 @@ __global__ void __launch_bounds__(kThreads) spmv_exact_kernel(
   if (chunk >= S.nchunks) return;
   const int64_t slot = chunk * 32 + lane;
   const int32_t row = S.row_of[slot];
-  if (row < 0) return;
+  if (row_skipped(S, row)) return;
   const int32_t len = S.row_len[slot];
   const int64_t base = S.chunk_off[chunk] + lane;
 
@@ -375,9 +384,9 @@ __global__ void __launch_bounds__(kThreads) pattern_grad_kernel(
 template <int W>
 mp_status spmv_w(const mp_csr_s* M, const Sell& S, int mode, const uint64_t* x, int64_t ldx,
                  uint64_t* y, int64_t ldy, const uint64_t* b, int64_t ldb, const int* gate,
-                 cudaStream_t st) {
+                 cudaStream_t st, const int32_t* rinst = nullptr, const int* idone = nullptr) {
   if (S.nchunks == 0) return MP_OK;
-  const SellView V = view(S);
+  const SellView V = view(S, rinst, idone);
   const int blocks = (int)((S.nchunks * 32 + kThreads - 1) / kThreads);
   if (mode == MP_ORDERED && !b) {
     spmv_ordered_kernel<W><<<blocks, kThreads, 0, st>>>(V, x, ldx, y, ldy, gate);
@@ -427,6 +436,15 @@ mp_status launch_spmv(const mp_csr_s* M, const Sell& S, int mode, const uint64_t
   return dispatch_w(M->prec, [&](auto w) {
     constexpr int W = decltype(w)::value;
     return spmv_w<W>(M, S, mode, x, ldx, y, ldy, b, ldb, gate, st);
+  });
+}
+
+mp_status launch_spmv_batched(const mp_csr_s* M, int mode, const uint64_t* x, int64_t ldx,
+                              uint64_t* y, int64_t ldy, const int32_t* rinst, const int* idone,
+                              cudaStream_t st) {
+  return dispatch_w(M->prec, [&](auto w) {
+    constexpr int W = decltype(w)::value;
+    return spmv_w<W>(M, M->A, mode, x, ldx, y, ldy, nullptr, 0, nullptr, st, rinst, idone);
   });
 }
 

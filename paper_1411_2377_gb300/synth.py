@@ -207,6 +207,36 @@ def random_values(count: int, p: int, seed: int, stream0: int = 0, zero_frac: fl
     return out
 
 
+def batch_systems(seed: int = 3, count: int = 256, nmin: int = 1000, nmax: int = 65536):
+    """Descriptions of the batched-solve workload: system s has a size drawn
+    log-uniformly in [nmin, nmax], a 2-D 5-point (side ceil(sqrt n)) or 3-D
+    7-point (side ceil(cbrt n), no row scaling) convection-diffusion matrix,
+    precision 128 or 256 bits and 1-4 right-hand sides (the k-th one is
+    b = A * ((k+1) * ones)).  Returns dicts with kind, m, p, nrhs, mseed."""
+    s = np.arange(count, dtype=np.uint64)
+    u = uniform(seed, S_MISC + 1, s)
+    target = np.exp(math.log(nmin) + u * (math.log(nmax) - math.log(nmin)))
+    kind = np.where(uniform(seed, S_MISC + 2, s) < 0.5, "2d", "3d")
+    prec = np.where(uniform(seed, S_MISC + 3, s) < 0.5, 128, 256)
+    nrhs = 1 + np.minimum((uniform(seed, S_MISC + 4, s) * 4).astype(np.int64), 3)
+    out = []
+    for i in range(count):
+        if kind[i] == "2d":
+            m = int(math.ceil(math.sqrt(target[i])))
+        else:
+            m = int(math.ceil(round(target[i] ** (1.0 / 3.0), 9)))
+        out.append({"kind": str(kind[i]), "m": m, "p": int(prec[i]), "nrhs": int(nrhs[i]),
+                    "mseed": seed * 1000 + i})
+    return out
+
+
+def batch_matrix(desc):
+    """(rowptr, colidx, values) of one batch_systems entry."""
+    if desc["kind"] == "2d":
+        return stencil2d(desc["m"], seed=desc["mseed"])
+    return stencil3d(desc["m"], seed=desc["mseed"], decades=0.0)
+
+
 SPMV_N = 1_000_000
 
 

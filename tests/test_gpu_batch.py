@@ -1,0 +1,59 @@
+"""Batched GPBiCG: every instance of a batch must equal mp_gpbicg on that
+instance alone (iterations, status and x, bit for bit), including instances
+that exit at once, break down, or hit the iteration limit."""
+import numpy as np
+import pytest
+
+from gpu_util import need_gpu
+from paper_1411_2377_gb300 import synth
+
+
+def _instances():
+    sys = [synth.stencil2d(5, seed=1), synth.stencil2d(9, seed=2), synth.stencil3d(3, seed=3, decades=0.0),
+           synth.stencil3d(4, seed=4, decades=20.0),   # row-scaled: slow, may hit maxit
+           (np.array([0, 1, 2], np.int64), np.array([1, 0], np.int32), np.array([1.0, 1.0])),
+           synth.stencil2d(7, seed=5)]
+    # (system index, rhs scale): the [[0,1],[1,0]] system with b = e1 breaks down,
+    # scale 0 gives b = 0 (converged before the first iteration)
+    plan = [(0, 1.0), (1, 1.0), (1, 2.0), (2, 1.0), (3, 1.0), (4, None), (5, 0.0), (5, 3.0)]
+    return sys, plan
+
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("p", (128, 256))
+@pytest.mark.parametrize("mode", ("ordered", "exact"))
+def test_batched_equals_single_solves(p, mode):
+    mpk = need_gpu()
+    import torch
+
+    systems, plan = _instances()
+    inst = [systems[i] for i, _ in plan]
+    B = mpk.Batch(inst, p)
+    b = mpk.Vec.zeros(B.n, p)
+    singles = []
+    for k, (i, scale) in enumerate(plan):
+        rp, ci, va = systems[i]
+        n = len(rp) - 1
+        A = mpk.CSR(rp, ci, va, p)
+        if scale is None:
+            rhs = np.zeros(n)
+            rhs[0] = 1.0
+            bk = mpk.Vec.from_f64(rhs, p)
+        else:
+            bk = mpk.spmv(A, mpk.Vec.from_f64(np.full(n, scale), p), mode="exact")
+        o0, o1 = int(B.offsets[k]), int(B.offsets[k + 1])
+        b.t[:, o0:o1] = bk.t
+        singles.append((A, bk))
+    maxit = 300
+    x, infos = mpk.batch_gpbicg(B, b, rtol=1e-25, maxit=maxit, mode=mode, poll_every=5)
+    statuses = set()
+    for k, (A, bk) in enumerate(singles):
+        xs, info = mpk.gpbicg(A, bk, rtol=1e-25, maxit=maxit, mode=mode)
+        o0, o1 = int(B.offsets[k]), int(B.offsets[k + 1])
+        assert (infos[k]["iters"], infos[k]["status"]) == (info["iters"], info["status"]), k
+        assert torch.equal(x.t[:, o0:o1].cpu(), xs.t.cpu()), k
+        statuses.add(info["status"])
+    assert {0, 6} <= statuses  # converged and breakdown instances present
+
