@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solver", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the default launch configuration instead of autotuning it")
     ap.add_argument("--batch-systems", type=int, default=64,
                     help="systems of the batched-solve workload to run (256 = all)")
     return ap.parse_args()
@@ -288,6 +290,14 @@ def run_native(args):
         xv[p] = mpk.Vec.from_planes(xs[p], p)
         yv[p] = mpk.Vec.empty(n, p)
     slots = {p: mats[p].info()["slots"] for p in precs}
+    tuned = None
+    if not args.no_tune:
+        from paper_1411_2377_gb300 import tune
+
+        # launch configuration per matrix, chosen once before the timed region
+        tuned = {str(p): {m: {k: v for k, v in r.items() if k != "cached"}
+                          for m, r in tune.autotune(mats[p], reps=3, cache=None).items()}
+                 for p in precs}
     stream = torch.cuda.current_stream()
     sptr = ctypes.c_void_p(stream.cuda_stream)
 
@@ -424,7 +434,7 @@ def run_native(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u64 limbs (p-bit RN)", "data": "synthetic",
             "config": {"workload": CONFIG_NAME, "n": n, "nnz": nnz, "precs": precs,
-                       "modes": [m for m, _ in MODES], "slots": slots,
+                       "modes": [m for m, _ in MODES], "slots": slots, "tuned": tuned,
                        "l2": "inputs larger than L2 (matrices >= 448 MB), no flush",
                        "parallelism": f"replicas x{world}", "generate_s": round(gen_s, 1)},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

@@ -164,6 +164,10 @@ class CSR:
         self.nnz = int(rowptr[-1])
         self.prec = prec
         self.transpose = transpose
+        lens = np.diff(rowptr)
+        # row-length histogram in powers of two (bucket k: lengths in [2^(k-1), 2^k))
+        self.row_hist = np.bincount(np.ceil(np.log2(lens + 1)).astype(np.int64)).tolist() \
+            if n > 0 else []
 
     def info(self) -> dict:
         n, nnz, slots, nbytes = (ctypes.c_int64() for _ in range(4))
@@ -172,6 +176,25 @@ class CSR:
                                     ctypes.byref(slots), ctypes.byref(nbytes)), "mp_csr_info")
         return {"n": n.value, "nnz": nnz.value, "prec": p.value, "slots": slots.value,
                 "device_bytes": nbytes.value}
+
+    def set_config(self, mode="ordered", threads_per_block=128, staging=-1):
+        """SpMV launch configuration for one mode (results do not depend on it)."""
+        _ok(_lib.load().mp_csr_set_config(self.h, MODES[mode], int(threads_per_block),
+                                          int(staging)), "mp_csr_set_config")
+
+    def get_config(self, mode="ordered") -> dict:
+        t, s = ctypes.c_int32(), ctypes.c_int32()
+        _ok(_lib.load().mp_csr_get_config(self.h, MODES[mode], ctypes.byref(t), ctypes.byref(s)),
+            "mp_csr_get_config")
+        return {"threads_per_block": t.value, "staging": s.value}
+
+    def tune(self, mode="ordered", reps=5, stream=None) -> dict:
+        """Times every launch configuration of y = A x, keeps the fastest."""
+        t, s, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+        _ok(_lib.load().mp_csr_tune(self.h, MODES[mode], int(reps), ctypes.byref(t),
+                                    ctypes.byref(s), ctypes.byref(ms), _stream(stream)),
+            "mp_csr_tune")
+        return {"threads_per_block": t.value, "staging": s.value, "ms": ms.value}
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:

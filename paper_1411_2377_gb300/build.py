@@ -47,16 +47,32 @@ def _headers_mtime():
     return max(os.path.getmtime(h) for h in hs)
 
 
-def _compile(src: str, verbose_ptxas: bool) -> str:
-    obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+# Translation units compiled once per word count W = p/32 (-DMPK_W=W) and
+# once for their host entry points (-DMPK_W=0), in parallel.
+SPLIT = {"solvers.cu", "batch.cu"}
+WORDS = (0, 4, 8, 16, 32)
+
+
+def units():
+    out = []
+    for s in sources():
+        out += [(s, w) for w in WORDS] if s in SPLIT else [(s, None)]
+    return out
+
+
+def _compile(unit, verbose_ptxas: bool) -> str:
+    src, w = unit
+    obj = os.path.join(BUILD, src.replace(".cu", ".o" if w is None else f"_w{w}.o"))
     cmd = [nvcc(), *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
            "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC, "-c",
            os.path.join(CSRC, src), "-o", obj]
+    if w is not None:
+        cmd.insert(1, f"-DMPK_W={w}")
     if verbose_ptxas:
         cmd[1:1] = ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
-        raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr[-6000:]}")
+        raise RuntimeError(f"nvcc failed for {src} (MPK_W={w}):\n{r.stderr[-6000:]}")
     if verbose_ptxas:
         sys.stderr.write(r.stderr)
     return obj
@@ -68,9 +84,12 @@ def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = N
     newest = max([_headers_mtime()] + [os.path.getmtime(os.path.join(CSRC, s)) for s in srcs])
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
         return LIB
-    jobs = jobs or min(len(srcs), os.cpu_count() or 4)
+    todo = units()
+    # the longest units first: the W = 32 builds dominate
+    todo.sort(key=lambda u: -(u[1] if u[1] is not None else 6))
+    jobs = jobs or min(len(todo), os.cpu_count() or 4)
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose_ptxas), srcs))
+        objs = list(ex.map(lambda u: _compile(u, verbose_ptxas), todo))
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [nvcc(), *ARCH, "-shared", "--cudart", "shared", *objs, "-o", tmp,
            "-Xlinker", f"-rpath,{cuda_lib_dir()}"]

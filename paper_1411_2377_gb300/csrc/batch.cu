@@ -38,12 +38,29 @@ struct mp_batch_s {
   int32_t* d_count = nullptr;  // [k] blocks of each instance
 };
 
+// Compiled once per word count W = p/32 (MPK_W = 4, 8, 16, 32: the kernels
+// and batch_entry<W>) and once with MPK_W = 0 (batch set-up and the C entry
+// points), so that the precisions build in parallel.
+#ifndef MPK_W
+#define MPK_W 0
+#endif
+
+namespace mpk {
+
+constexpr int64_t kBlkElems = 4096;   // elements per reduction block
+
+template <int W>
+mp_status batch_entry(mp_batch_s* B, const mp_vec& b, const mp_vec& x, const mp_solve_opts& o,
+                      mp_solve_info* infos, cudaStream_t st);
+
+}  // namespace mpk
+
+#if MPK_W != 0
 namespace mpk {
 namespace {
 
 constexpr int kBT = 128;              // threads of the reduction blocks
 constexpr int kBW = kBT / 32;
-constexpr int64_t kBlkElems = 4096;   // elements per reduction block
 constexpr int kBFast = 1024;          // per-warp exponent window (bits)
 
 template <int W>
@@ -793,6 +810,23 @@ mp_status batch_solve_w(mp_batch_s* B, const mp_vec& b, const mp_vec& x,
   return r;
 }
 
+}  // namespace
+
+template <int W>
+mp_status batch_entry(mp_batch_s* B, const mp_vec& b, const mp_vec& x, const mp_solve_opts& o,
+                      mp_solve_info* infos, cudaStream_t st) {
+  return batch_solve_w<W>(B, b, x, o, infos, st);
+}
+template mp_status batch_entry<MPK_W>(mp_batch_s*, const mp_vec&, const mp_vec&,
+                                      const mp_solve_opts&, mp_solve_info*, cudaStream_t);
+
+}  // namespace mpk
+
+#else  // MPK_W == 0
+
+namespace mpk {
+namespace {
+
 template <class T>
 mp_status upload(T** d, const std::vector<T>& h, cudaStream_t st) {
   MPK_CUDA(cudaMalloc((void**)d, sizeof(T) * std::max<size_t>(h.size(), 1)));
@@ -938,7 +972,7 @@ mp_status mp_batch_gpbicg(mp_batch B, mp_vec b, mp_vec x, const mp_solve_opts* o
   MPK_CUDA(cudaStreamWaitEvent(st, fence, 0));
   r = dispatch_w(B->prec, [&](auto w) {
     constexpr int W = decltype(w)::value;
-    return batch_solve_w<W>(B, b, x, *opts, infos, st);
+    return batch_entry<W>(B, b, x, *opts, infos, st);
   });
   cudaEventRecord(fence, st);
   cudaStreamWaitEvent(cu, fence, 0);
@@ -949,3 +983,5 @@ mp_status mp_batch_gpbicg(mp_batch B, mp_vec b, mp_vec x, const mp_solve_opts* o
 }
 
 }  // extern "C"
+
+#endif  // MPK_W

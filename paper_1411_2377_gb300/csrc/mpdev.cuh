@@ -380,7 +380,7 @@ __device__ __forceinline__ void sub_rn(const Num<W>& a, const Num<W>& b, Num<W>&
 // (W+2)-word quotient Q of 32W+32 or 32W+33 bits and a remainder R; the kept
 // p bits, the next bit of Q and sticky = (rest of Q or R nonzero) round it.
 template <int W>
-__device__ __forceinline__ void div_rn(const Num<W>& a, const Num<W>& b, Num<W>& r) {
+__device__ __noinline__ void div_rn(const Num<W>& a, const Num<W>& b, Num<W>& r) {
   const uint32_t s = a.s ^ b.s;
   if (zero_e(a.e)) {
     set_zero(r, s);

@@ -29,6 +29,28 @@
 #include "internal.h"
 #include "mpdev.cuh"
 
+// The file is compiled once per word count W = p/32 (MPK_W = 4, 8, 16, 32:
+// the kernels and solve_entry<W>) and once with MPK_W = 0 (argument checks
+// and the C entry points), so that the precisions build in parallel.
+#ifndef MPK_W
+#define MPK_W 0
+#endif
+
+namespace mpk {
+
+struct SolveCall {
+  mp_csr A;
+  mp_vec b, x;
+  mp_solve_opts o;
+  cudaStream_t st;
+};
+
+template <int W>
+mp_status solve_entry(bool gp, const SolveCall& c, mp_solve_info* info);
+
+}  // namespace mpk
+
+#if MPK_W != 0
 namespace mpk {
 namespace {
 
@@ -469,13 +491,6 @@ mp_status dot2(const Work& w, const uint64_t* a0, const uint64_t* b0, int o0, co
   return launch_dot(w.prec, d, w.dscratch, gate, st);
 }
 
-struct SolveCall {
-  mp_csr A;
-  mp_vec b, x;
-  mp_solve_opts o;
-  cudaStream_t st;
-};
-
 // The operator of the solve (A, or A^T for an adjoint solve) and its transpose.
 const Sell& op_a(const SolveCall& c) { return c.o.transpose ? c.A->AT : c.A->A; }
 const Sell& op_at(const SolveCall& c) { return c.o.transpose ? c.A->A : c.A->AT; }
@@ -708,6 +723,21 @@ mp_status solve_w(const SolveCall& cu, mp_solve_info* info) {
   return static_cast<mp_status>(hs.status);
 }
 
+}  // namespace
+
+template <int W>
+mp_status solve_entry(bool gp, const SolveCall& c, mp_solve_info* info) {
+  return gp ? solve_w<W, true>(c, info) : solve_w<W, false>(c, info);
+}
+template mp_status solve_entry<MPK_W>(bool, const SolveCall&, mp_solve_info*);
+
+}  // namespace mpk
+
+#else  // MPK_W == 0
+
+namespace mpk {
+namespace {
+
 mp_status solve(bool gp, mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* opts,
                 mp_solve_info* info, void* stream) {
   if (!A) return set_error(MP_ERR_ARG, "matrix is null");
@@ -734,7 +764,7 @@ mp_status solve(bool gp, mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* opts
   SolveCall c{A, b, x, *opts, static_cast<cudaStream_t>(stream)};
   return dispatch_w(A->prec, [&](auto w) {
     constexpr int W = decltype(w)::value;
-    return gp ? solve_w<W, true>(c, info) : solve_w<W, false>(c, info);
+    return solve_entry<W>(gp, c, info);
   });
 }
 
@@ -754,3 +784,5 @@ mp_status mp_gpbicg(mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* opts, mp_
 }
 
 }  // extern "C"
+
+#endif  // MPK_W

@@ -13,6 +13,7 @@
 // digit-major so that a warp's 32 threads always hit 32 distinct banks.  A
 // row whose span does not fit the per-thread window goes to an overflow list
 // handled by a warp-per-row kernel with a window of the full span cap.
+#include <algorithm>
 #include <climits>
 
 #include "internal.h"
@@ -70,8 +71,8 @@ struct Pipelined {
 // ORDERED
 // ---------------------------------------------------------------------------
 
-template <int W>
-__global__ void __launch_bounds__(kThreads) spmv_ordered_kernel(
+template <int W, bool PIPE>
+__global__ void __launch_bounds__(256) spmv_ordered_kernel(
     const SellView S, const uint64_t* __restrict__ x, int64_t ldx, uint64_t* __restrict__ y,
     int64_t ldy, const int* __restrict__ gate) {
   if (gate && *gate) return;
@@ -85,7 +86,7 @@ __global__ void __launch_bounds__(kThreads) spmv_ordered_kernel(
   const int64_t base = S.chunk_off[chunk] + lane;
   Num<W> acc;
   set_zero(acc, 0u);
-  if (Pipelined<W>::value) {
+  if (PIPE) {
     // Software pipeline: the column index two entries ahead and the operands
     // one entry ahead are in flight while the current entry is computed.
     Num<W> an, xn;
@@ -156,7 +157,7 @@ __device__ __forceinline__ void value_as_product(const Num<W>& b, uint32_t (&P)[
 }
 
 template <int W, bool RESID>
-__global__ void __launch_bounds__(kThreads) spmv_exact_kernel(
+__global__ void __launch_bounds__(256) spmv_exact_kernel(
     const SellView S, const uint64_t* __restrict__ x, int64_t ldx, uint64_t* __restrict__ y,
     int64_t ldy, const uint64_t* __restrict__ bv, int64_t ldb, int32_t* __restrict__ ovf,
     int* __restrict__ status, const int* __restrict__ gate) {
@@ -353,6 +354,17 @@ __global__ void __launch_bounds__(32) spmv_exact_wide_kernel(
   }
 }
 
+// Operand of the tuner: x_i = (-1)^i (1 + (i mod 997) 2^-12), nonzero.
+template <int W>
+__global__ void tune_fill_kernel(uint64_t* x, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    Num<W> v;
+    from_f64<W>(((i & 1) ? -1.0 : 1.0) * (1.0 + (double)(i % 997) * (1.0 / 4096.0)), v);
+    store<W>(v, x, n, i);
+  }
+}
+
 // Gradient of a loss on the sparsity pattern: for every stored a_ij,
 // g[pos(i,j)] = RN((-lam_i) * x_j), pos being the entry's position in the
 // caller's CSR.  Same traversal as the products (thread per row).
@@ -387,30 +399,35 @@ mp_status spmv_w(const mp_csr_s* M, const Sell& S, int mode, const uint64_t* x, 
                  cudaStream_t st, const int32_t* rinst = nullptr, const int* idone = nullptr) {
   if (S.nchunks == 0) return MP_OK;
   const SellView V = view(S, rinst, idone);
-  const int blocks = (int)((S.nchunks * 32 + kThreads - 1) / kThreads);
+  const int tpb = M->cfg_tpb[mode == MP_ORDERED && !b ? 0 : 1];
+  const int blocks = (int)((S.nchunks * 32 + tpb - 1) / tpb);
   if (mode == MP_ORDERED && !b) {
-    spmv_ordered_kernel<W><<<blocks, kThreads, 0, st>>>(V, x, ldx, y, ldy, gate);
+    const bool pipe = M->cfg_pipe < 0 ? Pipelined<W>::value : (M->cfg_pipe != 0);
+    if (pipe && Pipelined<W>::value)
+      spmv_ordered_kernel<W, Pipelined<W>::value><<<blocks, tpb, 0, st>>>(V, x, ldx, y, ldy, gate);
+    else
+      spmv_ordered_kernel<W, false><<<blocks, tpb, 0, st>>>(V, x, ldx, y, ldy, gate);
     count_launch();
     return launch_check("spmv_ordered_kernel");
   }
   int* status = status_word();
   if (!status) return set_error(MP_ERR_CUDA, "status word unavailable");
   MPK_CUDA(cudaMemsetAsync(M->ovf, 0, sizeof(int32_t), st));
-  const size_t smem = (size_t)Win<W>::fast * kThreads * sizeof(int64_t);
+  const size_t smem = (size_t)Win<W>::fast * tpb * sizeof(int64_t);
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (b) {
     MPK_CUDA(cudaFuncSetAttribute(spmv_exact_kernel<W, true>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    spmv_exact_kernel<W, true><<<blocks, kThreads, smem, st>>>(V, x, ldx, y, ldy, b, ldb, M->ovf,
-                                                               status, gate);
+    spmv_exact_kernel<W, true><<<blocks, tpb, smem, st>>>(V, x, ldx, y, ldy, b, ldb, M->ovf,
+                                                          status, gate);
     spmv_exact_wide_kernel<W, true><<<sms * 4, 32, 0, st>>>(V, x, ldx, y, ldy, b, ldb, M->ovf, gate);
   } else {
     MPK_CUDA(cudaFuncSetAttribute(spmv_exact_kernel<W, false>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    spmv_exact_kernel<W, false><<<blocks, kThreads, smem, st>>>(V, x, ldx, y, ldy, nullptr, 0,
-                                                                M->ovf, status, gate);
+    spmv_exact_kernel<W, false><<<blocks, tpb, smem, st>>>(V, x, ldx, y, ldy, nullptr, 0,
+                                                           M->ovf, status, gate);
     spmv_exact_wide_kernel<W, false><<<sms * 4, 32, 0, st>>>(V, x, ldx, y, ldy, nullptr, 0,
                                                              M->ovf, gate);
   }
@@ -467,6 +484,87 @@ mp_status mp_spmv_t(mp_csr A, mp_vec x, mp_vec y, mp_mode mode, void* stream) {
   if (!A->has_t) return set_error(MP_ERR_ARG, "matrix was created without MP_CSR_TRANSPOSE");
   return launch_spmv(A, A->AT, mode, x.data, x.ld, y.data, y.ld, nullptr, 0, nullptr,
                      static_cast<cudaStream_t>(stream));
+}
+
+mp_status mp_csr_set_config(mp_csr A, int32_t mode, int32_t tpb, int32_t pipe) {
+  if (!A) return set_error(MP_ERR_ARG, "matrix is null");
+  if (mode != MP_ORDERED && mode != MP_EXACT) return set_error(MP_ERR_ARG, "mode %d", mode);
+  if (tpb != 32 && tpb != 64 && tpb != 128 && tpb != 256)
+    return set_error(MP_ERR_ARG, "threads per block %d not in {32,64,128,256}", tpb);
+  if (pipe < -1 || pipe > 1) return set_error(MP_ERR_ARG, "staging %d not in {-1,0,1}", pipe);
+  A->cfg_tpb[mode] = tpb;
+  if (mode == MP_ORDERED) A->cfg_pipe = pipe;
+  return MP_OK;
+}
+
+mp_status mp_csr_get_config(mp_csr A, int32_t mode, int32_t* tpb, int32_t* pipe) {
+  if (!A) return set_error(MP_ERR_ARG, "matrix is null");
+  if (mode != MP_ORDERED && mode != MP_EXACT) return set_error(MP_ERR_ARG, "mode %d", mode);
+  if (tpb) *tpb = A->cfg_tpb[mode];
+  if (pipe) {
+    // the staging that runs: none at p = 1024, whatever was asked for
+    const int eff = A->prec > 512 ? 0 : (A->cfg_pipe < 0 ? 1 : A->cfg_pipe);
+    *pipe = mode == MP_ORDERED ? eff : -1;
+  }
+  return MP_OK;
+}
+
+mp_status mp_csr_tune(mp_csr A, int32_t mode, int32_t reps, int32_t* tpb_out, int32_t* pipe_out,
+                      double* ms_out, void* stream) {
+  if (!A) return set_error(MP_ERR_ARG, "matrix is null");
+  if (mode != MP_ORDERED && mode != MP_EXACT) return set_error(MP_ERR_ARG, "mode %d", mode);
+  if (reps < 1) return set_error(MP_ERR_ARG, "reps %d", reps);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int L = A->prec / 64;
+  const int64_t n = A->n > 0 ? A->n : 1;
+  uint64_t *x = nullptr, *y = nullptr;
+  MPK_CUDA(cudaMalloc((void**)&x, sizeof(uint64_t) * (L + 1) * (size_t)n));
+  MPK_CUDA(cudaMalloc((void**)&y, sizeof(uint64_t) * (L + 1) * (size_t)n));
+  mp_status r = dispatch_w(A->prec, [&](auto w) {
+    constexpr int W = decltype(w)::value;
+    tune_fill_kernel<W><<<(int)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, st>>>(x, n);
+    count_launch();
+    return launch_check("tune_fill_kernel");
+  });
+  const int32_t old_tpb = A->cfg_tpb[mode], old_pipe = A->cfg_pipe;
+  float best = 1e30f;
+  int32_t bt = old_tpb, bp = old_pipe;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int pipes_ordered[2] = {0, 1};
+  const int npipe = (mode == MP_ORDERED && A->prec <= 512) ? 2 : 1;
+  for (int32_t tpb : {32, 64, 128, 256}) {
+    for (int pi = 0; pi < npipe && r == MP_OK; ++pi) {
+      A->cfg_tpb[mode] = tpb;
+      if (mode == MP_ORDERED) A->cfg_pipe = (npipe == 2) ? pipes_ordered[pi] : 0;
+      r = launch_spmv(A, A->A, mode, x, n, y, n, nullptr, 0, nullptr, st);
+      cudaEventRecord(e0, st);
+      for (int k = 0; k < reps && r == MP_OK; ++k)
+        r = launch_spmv(A, A->A, mode, x, n, y, n, nullptr, 0, nullptr, st);
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms /= reps;
+      if (r == MP_OK && ms < best) {
+        best = ms;
+        bt = tpb;
+        bp = (mode == MP_ORDERED) ? A->cfg_pipe : old_pipe;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(x);
+  cudaFree(y);
+  A->cfg_tpb[mode] = r == MP_OK ? bt : old_tpb;
+  A->cfg_pipe = r == MP_OK ? bp : old_pipe;
+  if (r != MP_OK) return r;
+  if (tpb_out) *tpb_out = bt;
+  if (pipe_out) *pipe_out = mode == MP_ORDERED ? bp : -1;
+  if (ms_out) *ms_out = best;
+  return MP_OK;
 }
 
 mp_status mp_csr_grad(mp_csr A, mp_vec lam, mp_vec x, mp_vec g, void* stream) {

@@ -71,3 +71,14 @@ def test_library_is_built_for_sm_103a(lib):
 
     out = subprocess.run([tool, "--list-elf", _lib.LIB_PATH], capture_output=True, text=True)
     assert "sm_103a" in out.stdout
+
+
+def test_config_calls_reject_bad_arguments_without_gpu(lib):
+    """Argument checks of the launch-configuration calls run before any
+    device work."""
+    from paper_1411_2377_gb300 import _lib
+
+    t = ctypes.c_int32()
+    assert lib.mp_csr_set_config(None, 0, 128, -1) == _lib.MP_ERR_ARG
+    assert lib.mp_csr_get_config(None, 0, ctypes.byref(t), None) == _lib.MP_ERR_ARG
+    assert lib.mp_csr_tune(None, 1, 3, None, None, None, None) == _lib.MP_ERR_ARG
