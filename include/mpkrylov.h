@@ -115,14 +115,20 @@ mp_status mp_csr_info(mp_csr A, int64_t* n, int64_t* nnz, int32_t* prec_bits,
                       int64_t* slots, int64_t* device_bytes);
 
 /* Launch configuration of the products of A (a tuning knob, not part of the
- * paper): threads per block (32, 64, 128 or 256) for mode MP_ORDERED or
- * MP_EXACT, and for MP_ORDERED whether the row loop stages the next entry's
- * operands in registers (1), does not (0) or uses the precision's default
- * (-1; staging for p <= 512; p = 1024 never stages).  Results do not depend
- * on it.  mp_csr_get_config reports the staging that runs (-1 for EXACT). */
-mp_status mp_csr_set_config(mp_csr A, int32_t mode, int32_t threads_per_block, int32_t staging);
+ * paper; results never depend on it): threads per block (32, 64, 128 or 256)
+ * for mode MP_ORDERED or MP_EXACT, and a variant:
+ *   MP_ORDERED: 1 = the row loop loads the next entry's operands while the
+ *               current one is computed, 0 = it does not (p = 1024 never
+ *               does);
+ *   MP_EXACT:   0 = exact products as 32-bit words added into 32-bit digit
+ *               counters, 1 = products as radix-2^29 column sums (one
+ *               multiply-add per limb pair, no carries) added into
+ *               29-bit digit counters;
+ *   -1 = the library's default for the precision.
+ * mp_csr_get_config reports the variant that runs. */
+mp_status mp_csr_set_config(mp_csr A, int32_t mode, int32_t threads_per_block, int32_t variant);
 mp_status mp_csr_get_config(mp_csr A, int32_t mode, int32_t* threads_per_block,
-                            int32_t* staging);
+                            int32_t* variant);
 
 /* Autotuner: times y = A x (mode) for every configuration above on an
  * internal nonzero x, `reps` launches each, keeps the fastest in A and
@@ -130,7 +136,7 @@ mp_status mp_csr_get_config(mp_csr A, int32_t mode, int32_t* threads_per_block,
  * the duration of the call.  Rows whose exponent span exceeds MP_SPAN_CAP
  * record MP_ERR_SPAN in the status word as in mp_spmv. */
 mp_status mp_csr_tune(mp_csr A, int32_t mode, int32_t reps, int32_t* threads_per_block,
-                      int32_t* staging, double* ms, void* stream);
+                      int32_t* variant, double* ms, void* stream);
 
 /* ---- products ------------------------------------------------------------ */
 

@@ -177,16 +177,18 @@ class CSR:
         return {"n": n.value, "nnz": nnz.value, "prec": p.value, "slots": slots.value,
                 "device_bytes": nbytes.value}
 
-    def set_config(self, mode="ordered", threads_per_block=128, staging=-1):
-        """SpMV launch configuration for one mode (results do not depend on it)."""
+    def set_config(self, mode="ordered", threads_per_block=128, variant=-1):
+        """SpMV launch configuration for one mode (results do not depend on it).
+        variant: ORDERED operand staging (0/1), EXACT product form (0 = word
+        digits, 1 = radix-2^29 column sums), -1 = default."""
         _ok(_lib.load().mp_csr_set_config(self.h, MODES[mode], int(threads_per_block),
-                                          int(staging)), "mp_csr_set_config")
+                                          int(variant)), "mp_csr_set_config")
 
     def get_config(self, mode="ordered") -> dict:
         t, s = ctypes.c_int32(), ctypes.c_int32()
         _ok(_lib.load().mp_csr_get_config(self.h, MODES[mode], ctypes.byref(t), ctypes.byref(s)),
             "mp_csr_get_config")
-        return {"threads_per_block": t.value, "staging": s.value}
+        return {"threads_per_block": t.value, "variant": s.value}
 
     def tune(self, mode="ordered", reps=5, stream=None) -> dict:
         """Times every launch configuration of y = A x, keeps the fastest."""
@@ -194,7 +196,7 @@ class CSR:
         _ok(_lib.load().mp_csr_tune(self.h, MODES[mode], int(reps), ctypes.byref(t),
                                     ctypes.byref(s), ctypes.byref(ms), _stream(stream)),
             "mp_csr_tune")
-        return {"threads_per_block": t.value, "staging": s.value, "ms": ms.value}
+        return {"threads_per_block": t.value, "variant": s.value, "ms": ms.value}
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:

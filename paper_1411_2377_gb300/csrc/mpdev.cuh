@@ -584,4 +584,144 @@ __device__ __forceinline__ void round_words(const int64_t* c, int stride, int nd
   round_increment<W>(r.m, r.e, rb & ((st != 0u) | (r.m[0] & 1u)));
 }
 
+// ---------------------------------------------------------------------------
+// Exact sums over radix-2^29 column sums (high precision)
+// ---------------------------------------------------------------------------
+// With the operands cut into 29-bit limbs, a 32x32-bit multiply-add of two
+// limbs into a 64-bit column sum never overflows: a column of the product
+// sums at most 37 limb products < 2^58 each.  So the exact product
+// Ma * (Mx << s) is formed as column sums C_k = sum_{i+j=k} a_i x_j with one
+// IMAD.WIDE per limb pair and no carry handling, and each C_k enters the
+// counters split as (C_k mod 2^29) at digit k and (C_k >> 29) at digit k+1.
+// Counter digit d has weight 2^(29 d); a term at bit offset off goes to digit
+// off / 29 after shifting one operand left by off mod 29.
+
+constexpr int kR = 29;
+constexpr uint32_t kRMask = (1u << kR) - 1u;
+
+template <int W>
+struct Cols {
+  static constexpr int NA = (32 * W + kR - 1) / kR;           // limbs of Ma
+  static constexpr int NX = (32 * W + kR - 1 + kR - 1) / kR;  // limbs of Mx << s, s < 29
+  static constexpr int NC = NA + NX - 1;                      // columns of the product
+};
+
+// l[i] = bits [29 i, 29 i + 29) of the NW-word number w.
+template <int NW, int NL>
+__device__ __forceinline__ void cut_limbs(const uint32_t (&w)[NW], uint32_t (&l)[NL]) {
+#pragma unroll
+  for (int i = 0; i < NL; ++i) {
+    const int b = kR * i, q = b / 32, r = b % 32;
+    const uint32_t lo = (q < NW) ? w[q] : 0u;
+    const uint32_t hi = (q + 1 < NW) ? w[q + 1] : 0u;
+    l[i] = (r + kR <= 32 ? (lo >> r) : __funnelshift_r(lo, hi, r)) & kRMask;
+  }
+}
+
+// Limbs of M << s (0 <= s < 29).
+template <int W, int NL>
+__device__ __forceinline__ void cut_limbs_shifted(const uint32_t (&m)[W], uint32_t s,
+                                                  uint32_t (&l)[NL]) {
+  uint32_t t[W + 1];
+  t[0] = m[0] << s;
+#pragma unroll
+  for (int k = 1; k < W; ++k) t[k] = __funnelshift_l(m[k - 1], m[k], s);
+  t[W] = __funnelshift_l(m[W - 1], 0u, s);
+  cut_limbs<W + 1, NL>(t, l);
+}
+
+// c[(q + k) * stride] += (-1)^neg * D_k for the digits D of the term
+// Ma * Mx * 2^off, off = 29 q + s.
+template <int W>
+__device__ __forceinline__ void add_product_cols(int64_t* c, int stride, const uint32_t (&a)[W],
+                                                 const uint32_t (&x)[W], uint32_t off,
+                                                 uint32_t neg) {
+  constexpr int NA = Cols<W>::NA, NX = Cols<W>::NX, NC = Cols<W>::NC;
+  const uint32_t q = off / kR, s = off - kR * q;
+  uint32_t al[NA], xl[NX];
+  cut_limbs<W, NA>(a, al);
+  cut_limbs_shifted<W, NX>(x, s, xl);
+  const uint64_t m = neg ? ~0ull : 0ull;  // (d ^ m) - m = -d when neg
+  int64_t* p = c + (int64_t)q * stride;
+  uint64_t carry = 0u;
+  // G columns at a time: their counters are loaded together, then updated
+  // and stored together, so the shared-memory latency is paid once per group
+  constexpr int G = 8;
+#pragma unroll
+  for (int k0 = 0; k0 <= NC; k0 += G) {
+    uint64_t dd[G];
+    int64_t v[G];
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+      const int k = k0 + u;
+      if (k < NC) {
+        uint64_t acc = 0u;
+#pragma unroll
+        for (int i = (k - NX + 1 > 0 ? k - NX + 1 : 0); i <= (k < NA - 1 ? k : NA - 1); ++i)
+          acc += (uint64_t)al[i] * xl[k - i];
+        dd[u] = (uint64_t)((uint32_t)acc & kRMask) + carry;
+        carry = acc >> kR;
+      } else if (k == NC) {
+        dd[u] = carry;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < G; ++u)
+      if (k0 + u <= NC) v[u] = p[(k0 + u) * stride];
+#pragma unroll
+    for (int u = 0; u < G; ++u)
+      if (k0 + u <= NC) p[(k0 + u) * stride] = v[u] + (int64_t)((dd[u] ^ m) - m);
+  }
+}
+
+// c[(q + j) * stride] += (-1)^neg * limb_j(M << s) for the value M * 2^off.
+template <int W>
+__device__ __forceinline__ void add_value_cols(int64_t* c, int stride, const uint32_t (&mv)[W],
+                                               uint32_t off, uint32_t neg) {
+  constexpr int NX = Cols<W>::NX;
+  const uint32_t q = off / kR, s = off - kR * q;
+  uint32_t xl[NX];
+  cut_limbs_shifted<W, NX>(mv, s, xl);
+  int64_t* p = c + (int64_t)q * stride;
+#pragma unroll
+  for (int j = 0; j < NX; ++j) p[j * stride] += neg ? -(int64_t)xl[j] : (int64_t)xl[j];
+}
+
+// Resolves nd signed radix-2^29 counters into the magnitude of their total as
+// 32-bit words stored back in c[0 .. *nw) (slot stride `stride`); returns 1
+// when the total is negative.
+__device__ __forceinline__ uint32_t resolve_cols(int64_t* c, int stride, int nd, int* nw) {
+  int64_t carry = 0;
+  for (int d = 0; d < nd; ++d) {
+    const int64_t t = c[d * stride] + carry;
+    c[d * stride] = t & kRMask;
+    carry = t >> kR;
+  }
+  const uint32_t negative = carry < 0 ? 1u : 0u;
+  if (negative) {  // -total = sum of (-digit) 2^(29 d) + 2^(29 nd)
+    carry = 0;
+    for (int d = 0; d < nd; ++d) {
+      const int64_t t = carry - c[d * stride];
+      c[d * stride] = t & kRMask;
+      carry = t >> kR;
+    }
+  }
+  // repack 29-bit digits into 32-bit words in place (word w <= digit d)
+  uint64_t buf = 0u;
+  int nb = 0, w = 0;
+  for (int d = 0; d < nd; ++d) {
+    buf |= (uint64_t)c[d * stride] << nb;
+    nb += kR;
+    if (nb >= 32) {
+      c[w * stride] = (int64_t)(uint32_t)buf;
+      ++w;
+      buf >>= 32;
+      nb -= 32;
+    }
+  }
+  if (nb > 0) c[(w++) * stride] = (int64_t)(uint32_t)buf;
+  *nw = w;
+  return negative;
+}
+
 }  // namespace mpk

@@ -29,7 +29,18 @@ template <int W>
 struct Win {
   static constexpr int fast = (kFastSpan + 64 * W + 96) / 32 + 1;  // digits per thread
   static constexpr int cap = (SPAN_CAP + 64 * W + 96) / 32 + 1;    // digits for the cap
+  static constexpr int fast_cols = (kFastSpan + 64 * W + 64) / kR + 4;  // radix-2^29 digits
 };
+
+// Radix-2^29 digits of a row whose terms span `span` bits: the terms' digits
+// (offset / 29 + NA + NX) and the carries of up to 2^31 terms plus a sign.
+__host__ __device__ inline int digits_cols(int64_t span, int W) {
+  return (int)((span + 64 * W + 64) / kR) + 4;
+}
+
+// Whether the EXACT kernel uses radix-2^29 column sums when the matrix
+// leaves the choice to the library.
+__host__ __device__ inline bool cols_default(int W) { return W >= 16; }
 
 __host__ __device__ inline int digits_for(int64_t span, int W) {
   return (int)((span + 64 * W + 96) / 32) + 1;
@@ -140,10 +151,22 @@ __device__ __forceinline__ void add_term(int64_t* c, int stride, const uint32_t 
   uint32_t D[2 * W + 1];
   shifted_digits<W>(P, (uint32_t)(off & 31), D);
   int64_t* p = c + (off >> 5) * stride;
+  // G digits at a time: loads together, then stores together (one
+  // shared-memory latency per group instead of one per digit)
+  constexpr int G = 2 * W + 1 < 12 ? 2 * W + 1 : 12;
 #pragma unroll
-  for (int k = 0; k <= 2 * W; ++k) {
-    const int64_t v = (int64_t)D[k];
-    p[k * stride] += neg ? -v : v;
+  for (int k0 = 0; k0 <= 2 * W; k0 += G) {
+    int64_t v[G];
+#pragma unroll
+    for (int u = 0; u < G; ++u)
+      if (k0 + u <= 2 * W) v[u] = p[(k0 + u) * stride];
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+      if (k0 + u <= 2 * W) {
+        const int64_t d = (int64_t)D[k0 + u];
+        p[(k0 + u) * stride] = v[u] + (neg ? -d : d);
+      }
+    }
   }
 }
 
@@ -156,7 +179,7 @@ __device__ __forceinline__ void value_as_product(const Num<W>& b, uint32_t (&P)[
   }
 }
 
-template <int W, bool RESID>
+template <int W, bool RESID, bool COLS>
 __global__ void __launch_bounds__(256) spmv_exact_kernel(
     const SellView S, const uint64_t* __restrict__ x, int64_t ldx, uint64_t* __restrict__ y,
     int64_t ldy, const uint64_t* __restrict__ bv, int64_t ldb, int32_t* __restrict__ ovf,
@@ -216,8 +239,8 @@ __global__ void __launch_bounds__(256) spmv_exact_kernel(
     record_status(status, MP_ERR_SPAN);
     return;
   }
-  const int nd = digits_for(span, W);
-  if (nd > Win<W>::fast) {
+  const int nd = COLS ? digits_cols(span, W) : digits_for(span, W);
+  if (nd > (COLS ? Win<W>::fast_cols : Win<W>::fast)) {
     const int pos = atomicAdd(ovf, 1);
     ovf[1 + pos] = (int32_t)slot;
     return;
@@ -229,9 +252,25 @@ __global__ void __launch_bounds__(256) spmv_exact_kernel(
   // pass 2: exact products into the counters
   uint32_t P[2 * W];
   if (RESID && !zero_e(b.e)) {
-    value_as_product<W>(b, P);
-    add_term<W>(c, stride, P, b.e - emin, b.s);
+    if (COLS) {
+      add_value_cols<W>(c, stride, b.m, (uint32_t)(b.e - emin + 32 * W), b.s);
+    } else {
+      value_as_product<W>(b, P);
+      add_term<W>(c, stride, P, b.e - emin, b.s);
+    }
   }
+  // adds the term a * x (sign already folded into ng)
+  auto term = [&](const Num<W>& a, const Num<W>& xv, uint32_t ng) {
+    if (COLS) {
+      add_product_cols<W>(c, stride, a.m, xv.m, (uint32_t)(a.e + xv.e - emin), ng);
+    } else {
+      if (W >= 16)
+        mul_full_ilp<W>(a.m, xv.m, P);
+      else
+        mul_full<W>(a.m, xv.m, P);
+      add_term<W>(c, stride, P, a.e + xv.e - emin, ng);
+    }
+  };
   if (Pipelined<W>::value) {
     Num<W> an, xn;
     int32_t c1 = 0;
@@ -251,11 +290,7 @@ __global__ void __launch_bounds__(256) spmv_exact_kernel(
         load<W>(xn, x, ldx, cn);
       }
       if (zero_e(a.e) || zero_e(xv.e)) continue;
-      if (W >= 16)
-        mul_full_ilp<W>(a.m, xv.m, P);
-      else
-        mul_full<W>(a.m, xv.m, P);
-      add_term<W>(c, stride, P, a.e + xv.e - emin, a.s ^ xv.s ^ (RESID ? 1u : 0u));
+      term(a, xv, a.s ^ xv.s ^ (RESID ? 1u : 0u));
     }
   } else {
     for (int32_t j = 0; j < len; ++j) {
@@ -265,16 +300,18 @@ __global__ void __launch_bounds__(256) spmv_exact_kernel(
       load<W>(a, S.val, S.nslots, k);
       load<W>(xv, x, ldx, col);
       if (zero_e(a.e) || zero_e(xv.e)) continue;
-      if (W >= 16)
-        mul_full_ilp<W>(a.m, xv.m, P);
-      else
-        mul_full<W>(a.m, xv.m, P);
-      add_term<W>(c, stride, P, a.e + xv.e - emin, a.s ^ xv.s ^ (RESID ? 1u : 0u));
+      term(a, xv, a.s ^ xv.s ^ (RESID ? 1u : 0u));
     }
   }
-  const uint32_t negative = resolve_digits(c, stride, nd);
-  if (negative) negate_words(c, stride, nd);
-  round_words<W>(c, stride, nd, emin - 64 * W, negative, r);
+  if (COLS) {
+    int nw = 0;
+    const uint32_t negative = resolve_cols(c, stride, nd, &nw);
+    round_words<W>(c, stride, nw, emin - 64 * W, negative, r);
+  } else {
+    const uint32_t negative = resolve_digits(c, stride, nd);
+    if (negative) negate_words(c, stride, nd);
+    round_words<W>(c, stride, nd, emin - 64 * W, negative, r);
+  }
   store<W>(r, y, ldy, row);
 }
 
@@ -402,7 +439,7 @@ mp_status spmv_w(const mp_csr_s* M, const Sell& S, int mode, const uint64_t* x, 
   const int tpb = M->cfg_tpb[mode == MP_ORDERED && !b ? 0 : 1];
   const int blocks = (int)((S.nchunks * 32 + tpb - 1) / tpb);
   if (mode == MP_ORDERED && !b) {
-    const bool pipe = M->cfg_pipe < 0 ? Pipelined<W>::value : (M->cfg_pipe != 0);
+    const bool pipe = M->cfg_var[0] < 0 ? Pipelined<W>::value : (M->cfg_var[0] != 0);
     if (pipe && Pipelined<W>::value)
       spmv_ordered_kernel<W, Pipelined<W>::value><<<blocks, tpb, 0, st>>>(V, x, ldx, y, ldy, gate);
     else
@@ -413,21 +450,25 @@ mp_status spmv_w(const mp_csr_s* M, const Sell& S, int mode, const uint64_t* x, 
   int* status = status_word();
   if (!status) return set_error(MP_ERR_CUDA, "status word unavailable");
   MPK_CUDA(cudaMemsetAsync(M->ovf, 0, sizeof(int32_t), st));
-  const size_t smem = (size_t)Win<W>::fast * tpb * sizeof(int64_t);
+  const bool cols = M->cfg_var[1] < 0 ? cols_default(W) : (M->cfg_var[1] != 0);
+  const size_t smem = (size_t)(cols ? Win<W>::fast_cols : Win<W>::fast) * tpb * sizeof(int64_t);
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  auto exact = [&](auto kern, const uint64_t* bb) -> mp_status {
+    MPK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<blocks, tpb, smem, st>>>(V, x, ldx, y, ldy, bb, ldb, M->ovf, status, gate);
+    return MP_OK;
+  };
+  mp_status r;
   if (b) {
-    MPK_CUDA(cudaFuncSetAttribute(spmv_exact_kernel<W, true>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    spmv_exact_kernel<W, true><<<blocks, tpb, smem, st>>>(V, x, ldx, y, ldy, b, ldb, M->ovf,
-                                                          status, gate);
+    r = cols ? exact(spmv_exact_kernel<W, true, true>, b) : exact(spmv_exact_kernel<W, true, false>, b);
+    if (r != MP_OK) return r;
     spmv_exact_wide_kernel<W, true><<<sms * 4, 32, 0, st>>>(V, x, ldx, y, ldy, b, ldb, M->ovf, gate);
   } else {
-    MPK_CUDA(cudaFuncSetAttribute(spmv_exact_kernel<W, false>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    spmv_exact_kernel<W, false><<<blocks, tpb, smem, st>>>(V, x, ldx, y, ldy, nullptr, 0,
-                                                           M->ovf, status, gate);
+    r = cols ? exact(spmv_exact_kernel<W, false, true>, nullptr)
+             : exact(spmv_exact_kernel<W, false, false>, nullptr);
+    if (r != MP_OK) return r;
     spmv_exact_wide_kernel<W, false><<<sms * 4, 32, 0, st>>>(V, x, ldx, y, ldy, nullptr, 0,
                                                              M->ovf, gate);
   }
@@ -486,30 +527,33 @@ mp_status mp_spmv_t(mp_csr A, mp_vec x, mp_vec y, mp_mode mode, void* stream) {
                      static_cast<cudaStream_t>(stream));
 }
 
-mp_status mp_csr_set_config(mp_csr A, int32_t mode, int32_t tpb, int32_t pipe) {
+mp_status mp_csr_set_config(mp_csr A, int32_t mode, int32_t tpb, int32_t variant) {
   if (!A) return set_error(MP_ERR_ARG, "matrix is null");
   if (mode != MP_ORDERED && mode != MP_EXACT) return set_error(MP_ERR_ARG, "mode %d", mode);
   if (tpb != 32 && tpb != 64 && tpb != 128 && tpb != 256)
     return set_error(MP_ERR_ARG, "threads per block %d not in {32,64,128,256}", tpb);
-  if (pipe < -1 || pipe > 1) return set_error(MP_ERR_ARG, "staging %d not in {-1,0,1}", pipe);
+  if (variant < -1 || variant > 1) return set_error(MP_ERR_ARG, "variant %d not in {-1,0,1}", variant);
   A->cfg_tpb[mode] = tpb;
-  if (mode == MP_ORDERED) A->cfg_pipe = pipe;
+  A->cfg_var[mode] = variant;
   return MP_OK;
 }
 
-mp_status mp_csr_get_config(mp_csr A, int32_t mode, int32_t* tpb, int32_t* pipe) {
+// The variant that runs for the matrix's current setting.
+static int effective_variant(const mp_csr_s* A, int mode) {
+  const int W = A->prec / 32;
+  if (mode == MP_ORDERED) return W > 16 ? 0 : (A->cfg_var[0] < 0 ? 1 : A->cfg_var[0]);
+  return A->cfg_var[1] < 0 ? (cols_default(W) ? 1 : 0) : A->cfg_var[1];
+}
+
+mp_status mp_csr_get_config(mp_csr A, int32_t mode, int32_t* tpb, int32_t* variant) {
   if (!A) return set_error(MP_ERR_ARG, "matrix is null");
   if (mode != MP_ORDERED && mode != MP_EXACT) return set_error(MP_ERR_ARG, "mode %d", mode);
   if (tpb) *tpb = A->cfg_tpb[mode];
-  if (pipe) {
-    // the staging that runs: none at p = 1024, whatever was asked for
-    const int eff = A->prec > 512 ? 0 : (A->cfg_pipe < 0 ? 1 : A->cfg_pipe);
-    *pipe = mode == MP_ORDERED ? eff : -1;
-  }
+  if (variant) *variant = effective_variant(A, mode);
   return MP_OK;
 }
 
-mp_status mp_csr_tune(mp_csr A, int32_t mode, int32_t reps, int32_t* tpb_out, int32_t* pipe_out,
+mp_status mp_csr_tune(mp_csr A, int32_t mode, int32_t reps, int32_t* tpb_out, int32_t* var_out,
                       double* ms_out, void* stream) {
   if (!A) return set_error(MP_ERR_ARG, "matrix is null");
   if (mode != MP_ORDERED && mode != MP_EXACT) return set_error(MP_ERR_ARG, "mode %d", mode);
@@ -519,25 +563,28 @@ mp_status mp_csr_tune(mp_csr A, int32_t mode, int32_t reps, int32_t* tpb_out, in
   const int64_t n = A->n > 0 ? A->n : 1;
   uint64_t *x = nullptr, *y = nullptr;
   MPK_CUDA(cudaMalloc((void**)&x, sizeof(uint64_t) * (L + 1) * (size_t)n));
-  MPK_CUDA(cudaMalloc((void**)&y, sizeof(uint64_t) * (L + 1) * (size_t)n));
+  if (cudaMalloc((void**)&y, sizeof(uint64_t) * (L + 1) * (size_t)n) != cudaSuccess) {
+    cudaFree(x);
+    return set_error(MP_ERR_ALLOC, "tuner vectors");
+  }
   mp_status r = dispatch_w(A->prec, [&](auto w) {
     constexpr int W = decltype(w)::value;
     tune_fill_kernel<W><<<(int)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, st>>>(x, n);
     count_launch();
     return launch_check("tune_fill_kernel");
   });
-  const int32_t old_tpb = A->cfg_tpb[mode], old_pipe = A->cfg_pipe;
+  const int32_t old_tpb = A->cfg_tpb[mode], old_var = A->cfg_var[mode];
   float best = 1e30f;
-  int32_t bt = old_tpb, bp = old_pipe;
+  int32_t bt = old_tpb, bv = old_var;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  const int pipes_ordered[2] = {0, 1};
-  const int npipe = (mode == MP_ORDERED && A->prec <= 512) ? 2 : 1;
+  // ORDERED staging exists for p <= 512; EXACT has both product forms
+  const int nvar = (mode == MP_EXACT || A->prec <= 512) ? 2 : 1;
   for (int32_t tpb : {32, 64, 128, 256}) {
-    for (int pi = 0; pi < npipe && r == MP_OK; ++pi) {
+    for (int32_t v = 0; v < nvar && r == MP_OK; ++v) {
       A->cfg_tpb[mode] = tpb;
-      if (mode == MP_ORDERED) A->cfg_pipe = (npipe == 2) ? pipes_ordered[pi] : 0;
+      A->cfg_var[mode] = v;
       r = launch_spmv(A, A->A, mode, x, n, y, n, nullptr, 0, nullptr, st);
       cudaEventRecord(e0, st);
       for (int k = 0; k < reps && r == MP_OK; ++k)
@@ -550,19 +597,20 @@ mp_status mp_csr_tune(mp_csr A, int32_t mode, int32_t reps, int32_t* tpb_out, in
       if (r == MP_OK && ms < best) {
         best = ms;
         bt = tpb;
-        bp = (mode == MP_ORDERED) ? A->cfg_pipe : old_pipe;
+        bv = v;
       }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  cudaStreamSynchronize(st);
   cudaFree(x);
   cudaFree(y);
   A->cfg_tpb[mode] = r == MP_OK ? bt : old_tpb;
-  A->cfg_pipe = r == MP_OK ? bp : old_pipe;
+  A->cfg_var[mode] = r == MP_OK ? bv : old_var;
   if (r != MP_OK) return r;
   if (tpb_out) *tpb_out = bt;
-  if (pipe_out) *pipe_out = mode == MP_ORDERED ? bp : -1;
+  if (var_out) *var_out = effective_variant(A, mode);
   if (ms_out) *ms_out = best;
   return MP_OK;
 }

@@ -1,6 +1,8 @@
 """Launch configurations and the autotuner: every configuration of a
-matrix's products gives the oracle's result bit for bit, the tuner keeps one
-of them, and the on-disk cache reproduces it without timing again."""
+matrix's products (threads per block; ORDERED operand staging; EXACT word
+digits or radix-2^29 column sums) gives the oracle's result bit for bit, the
+tuner keeps one of them, and the on-disk cache reproduces it without timing
+again."""
 import json
 
 import numpy as np
@@ -25,13 +27,14 @@ def test_every_configuration_matches_the_oracle(p):
     for name, m in MODES:
         want, st = oracle.spmv(p, m, rowptr, colidx, recs(V), recs(X))
         want_t, _ = oracle.spmv_t(p, m, rowptr, colidx, recs(V), recs(X))
-        stagings = (0, 1, -1) if name == "ordered" else (-1,)
         for tpb in (32, 64, 128, 256):
-            for s in stagings:
-                A.set_config(name, tpb, s)
+            for v in (0, 1, -1):
+                A.set_config(name, tpb, v)
                 got = A.get_config(name)
                 assert got["threads_per_block"] == tpb
-                what = f"{name} p={p} tpb={tpb} staging={s}"
+                if v >= 0 and not (name == "ordered" and p == 1024):
+                    assert got["variant"] == v
+                what = f"{name} p={p} tpb={tpb} variant={v}"
                 assert_bitwise(mpk.spmv(A, x, mode=name).planes(), want, what)
                 assert_bitwise(mpk.spmv_t(A, x, mode=name).planes(), want_t, "T " + what)
 
@@ -64,8 +67,7 @@ def test_tuner_and_cache(p, tmp_path):
         assert not r["cached"] and r["ms"] > 0
         assert r["threads_per_block"] in (32, 64, 128, 256)
         assert A.get_config(name)["threads_per_block"] == r["threads_per_block"]
-        if name == "ordered":
-            assert r["staging"] in ((0, 1) if p <= 512 else (0,))
+        assert r["variant"] in ((0,) if (name == "ordered" and p == 1024) else (0, 1))
         want, _ = oracle.spmv(p, m, rowptr, colidx, recs(V), recs(X))
         assert_bitwise(mpk.spmv(A, x, mode=name).planes(), want, f"tuned {name} p={p}")
     assert len(json.load(open(cache))) == 2
@@ -74,3 +76,48 @@ def test_tuner_and_cache(p, tmp_path):
     for name, _ in MODES:
         assert again[name]["cached"]
         assert B.get_config(name) == A.get_config(name)
+
+
+@pytest.mark.parametrize("p", (128, 256, 512, 1024))
+@pytest.mark.parametrize("variant", (0, 1))
+def test_exact_variants_on_hard_rows(p, variant):
+    """Both EXACT product forms on rows whose spans sit around the per-thread
+    window (in it, just beyond it: the warp-per-row path), beyond the span
+    cap, with exact cancellation, and in the residual with its b term."""
+    mpk = need_gpu()
+    from paper_1411_2377_gb300 import synth
+
+    n = 300
+    rowptr, colidx = random_csr(n, seed=p + variant, mean_len=12, max_len=40)
+    V = rand_planes(len(colidx), p, 51, zero_frac=0.02, emin=-3, emax=3)
+    X = rand_planes(n, p, 52, zero_frac=0.02, emin=-3, emax=3)
+    Vr, Xr = recs(V), recs(X)
+    # push one entry of some rows down by s bits: spans s + O(10)
+    for r, shift in ((1, 400), (2, 490), (3, 505), (4, 530), (5, 700), (6, 2000),
+                     (8, oracle.SPAN_CAP + 50)):
+        if rowptr[r + 1] > rowptr[r]:
+            k = rowptr[r]
+            Vr[k, 0] = np.int64(Vr[k, 0].view(np.int64) - 2 * shift).view(np.uint64)
+    # row 9: a, -a against equal x values -> exact cancellation (+0)
+    if rowptr[10] - rowptr[9] >= 2:
+        k = rowptr[9]
+        Xr[colidx[k + 1]] = Xr[colidx[k]]
+        Vr[k + 1] = Vr[k]
+        Vr[k + 1, 0] ^= np.uint64(1)
+        Vr[k + 2:rowptr[10]] = 0  # the rest of the row: stored zeros
+        Vr[k + 2:rowptr[10], 0] = np.uint64((oracle.EXP_ZERO * 2) & ((1 << 64) - 1))
+    A = mpk.CSR(rowptr, colidx, synth.records_to_planes(Vr), p, transpose=True)
+    A.set_config("exact", 128, variant)
+    x = mpk.Vec.from_planes(synth.records_to_planes(Xr), p)
+    want, st = oracle.spmv(p, oracle.EXACT, rowptr, colidx, Vr, Xr)
+    assert st == oracle.ERR_SPAN
+    y = mpk.spmv(A, x, mode="exact", sync=False)
+    with pytest.raises(mpk.MPError):
+        mpk.check()
+    assert_bitwise(y.planes(), want, f"exact variant={variant} p={p}")
+    B = rand_planes(n, p, 53, zero_frac=0.1, emin=-300, emax=3)
+    r = mpk.residual(A, mpk.Vec.from_planes(B, p), x, sync=False)
+    with pytest.raises(mpk.MPError):
+        mpk.check()
+    want_r, _ = oracle.residual(p, rowptr, colidx, Vr, recs(B), Xr)
+    assert_bitwise(r.planes(), want_r, f"residual variant={variant} p={p}")
