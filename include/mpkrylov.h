@@ -116,14 +116,14 @@ mp_status mp_csr_info(mp_csr A, int64_t* n, int64_t* nnz, int32_t* prec_bits,
 
 /* Launch configuration of the products of A (a tuning knob, not part of the
  * paper; results never depend on it): threads per block (32, 64, 128 or 256)
- * for mode MP_ORDERED or MP_EXACT, and a variant:
- *   MP_ORDERED: 1 = the row loop loads the next entry's operands while the
- *               current one is computed, 0 = it does not (p = 1024 never
- *               does);
- *   MP_EXACT:   0 = exact products as 32-bit words added into 32-bit digit
- *               counters, 1 = products as radix-2^29 column sums (one
- *               multiply-add per limb pair, no carries) added into
- *               29-bit digit counters;
+ * for mode MP_ORDERED or MP_EXACT, and a variant, a bit field:
+ *   bit 0 (MP_ORDERED only): the row loop loads the next entry's operands
+ *          while the current one is computed (p <= 512; p = 1024 never
+ *          does);
+ *   bit 1: products formed from radix-2^29 column sums (one multiply-add
+ *          per pair of 29-bit limbs, no carries inside the product; EXACT
+ *          then keeps 29-bit digit counters), else from 32-bit words with
+ *          carry chains;
  *   -1 = the library's default for the precision.
  * mp_csr_get_config reports the variant that runs. */
 mp_status mp_csr_set_config(mp_csr A, int32_t mode, int32_t threads_per_block, int32_t variant);

@@ -179,8 +179,8 @@ class CSR:
 
     def set_config(self, mode="ordered", threads_per_block=128, variant=-1):
         """SpMV launch configuration for one mode (results do not depend on it).
-        variant: ORDERED operand staging (0/1), EXACT product form (0 = word
-        digits, 1 = radix-2^29 column sums), -1 = default."""
+        variant: bit field, bit 0 = ORDERED operand staging, bit 1 = products
+        from radix-2^29 column sums; -1 = the library's default."""
         _ok(_lib.load().mp_csr_set_config(self.h, MODES[mode], int(threads_per_block),
                                           int(variant)), "mp_csr_set_config")
 

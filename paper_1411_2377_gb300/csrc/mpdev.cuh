@@ -674,6 +674,63 @@ __device__ __forceinline__ void add_product_cols(int64_t* c, int stride, const u
   }
 }
 
+// r = RN(a*b) as mul_rn, with the exact product formed from radix-2^29
+// column sums: NA^2 multiply-adds into 64-bit columns, one carry pass over
+// the 2 NA digits, then the top W+1 words are reassembled from the digits and
+// everything below them only feeds the sticky bit.
+template <int W>
+__device__ __forceinline__ void mul_rn_cols(const Num<W>& a, const Num<W>& b, Num<W>& r) {
+  constexpr int NA = Cols<W>::NA;
+  constexpr int ND = 2 * NA;                // digits of the product
+  constexpr int WLO = W - 1;                // lowest product word kept (then up to 2W-1)
+  constexpr int KLO = (32 * WLO) / kR;      // first digit reaching word WLO
+  constexpr int R0 = 32 * WLO - kR * KLO;   // bits of digit KLO below word WLO
+  const uint32_t s = a.s ^ b.s;
+  if (zero_e(a.e) || zero_e(b.e)) {
+    set_zero(r, s);
+    return;
+  }
+  uint32_t al[NA], bl[NA];
+  cut_limbs<W, NA>(a.m, al);
+  cut_limbs<W, NA>(b.m, bl);
+  uint32_t D[ND - KLO];
+  uint32_t st = 0u;
+  uint64_t carry = 0u;
+#pragma unroll
+  for (int k = 0; k < ND - 1; ++k) {
+    uint64_t acc = carry;
+#pragma unroll
+    for (int i = (k - NA + 1 > 0 ? k - NA + 1 : 0); i <= (k < NA - 1 ? k : NA - 1); ++i)
+      acc += (uint64_t)al[i] * bl[k - i];
+    const uint32_t d = (uint32_t)acc & kRMask;
+    carry = acc >> kR;
+    if (k < KLO)
+      st |= d;
+    else
+      D[k - KLO] = d;
+  }
+  D[ND - 1 - KLO] = (uint32_t)carry;
+  if (R0 > 0) st |= D[0] & ((1u << R0) - 1u);
+  // P[WLO + j] for j = 0..W: bits [32 (WLO + j), +32) of the product
+  uint32_t T[W + 1];
+#pragma unroll
+  for (int j = 0; j <= W; ++j) {
+    const int bit = 32 * (WLO + j), kk = bit / kR - KLO, rr = bit % kR;
+    uint32_t v = D[kk] >> rr;
+    if (kk + 1 < ND - KLO) v |= D[kk + 1] << (kR - rr);
+    if (2 * kR - rr < 32 && kk + 2 < ND - KLO) v |= D[kk + 2] << (2 * kR - rr);
+    T[j] = v;
+  }
+  const uint32_t sh = 1u - (T[W] >> 31);  // 1 when the product has 2p-1 bits
+#pragma unroll
+  for (int k = 0; k < W; ++k) r.m[k] = __funnelshift_l(T[k], T[k + 1], sh);
+  const uint32_t g = T[0] << sh;
+  st |= g << 1;
+  r.e = a.e + b.e - (int64_t)sh;
+  r.s = s;
+  round_increment<W>(r.m, r.e, (g >> 31) & ((st != 0u) | (r.m[0] & 1u)));
+}
+
 // c[(q + j) * stride] += (-1)^neg * limb_j(M << s) for the value M * 2^off.
 template <int W>
 __device__ __forceinline__ void add_value_cols(int64_t* c, int stride, const uint32_t (&mv)[W],

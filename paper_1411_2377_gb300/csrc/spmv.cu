@@ -38,9 +38,14 @@ __host__ __device__ inline int digits_cols(int64_t span, int W) {
   return (int)((span + 64 * W + 64) / kR) + 4;
 }
 
-// Whether the EXACT kernel uses radix-2^29 column sums when the matrix
-// leaves the choice to the library.
-__host__ __device__ inline bool cols_default(int W) { return W >= 16; }
+// Launch variants (a bit field): bit 0 = the ORDERED row loop stages the
+// next entry's operands (p <= 512 only), bit 1 = products from radix-2^29
+// column sums.  cols_default: whether a mode uses column sums when the
+// matrix leaves the choice to the library.
+constexpr int kVarStage = 1, kVarCols = 2;
+__host__ __device__ inline bool cols_default(int mode, int W) {
+  return mode == MP_EXACT ? W >= 16 : W >= 8;
+}
 
 __host__ __device__ inline int digits_for(int64_t span, int W) {
   return (int)((span + 64 * W + 96) / 32) + 1;
@@ -82,7 +87,7 @@ struct Pipelined {
 // ORDERED
 // ---------------------------------------------------------------------------
 
-template <int W, bool PIPE>
+template <int W, bool PIPE, bool COLS>
 __global__ void __launch_bounds__(256) spmv_ordered_kernel(
     const SellView S, const uint64_t* __restrict__ x, int64_t ldx, uint64_t* __restrict__ y,
     int64_t ldy, const int* __restrict__ gate) {
@@ -119,7 +124,10 @@ __global__ void __launch_bounds__(256) spmv_ordered_kernel(
       }
       if (zero_e(a.e) || zero_e(xv.e)) continue;  // zero fast path
       Num<W> t, s;
-      mul_rn<W>(a, xv, t);
+      if (COLS)
+        mul_rn_cols<W>(a, xv, t);
+      else
+        mul_rn<W>(a, xv, t);
       add_rn<W>(acc, t, s);
       acc = s;
     }
@@ -132,7 +140,10 @@ __global__ void __launch_bounds__(256) spmv_ordered_kernel(
       load<W>(xv, x, ldx, c);
       if (zero_e(a.e) || zero_e(xv.e)) continue;  // zero fast path
       Num<W> t, s;
-      mul_rn<W>(a, xv, t);
+      if (COLS)
+        mul_rn_cols<W>(a, xv, t);
+      else
+        mul_rn<W>(a, xv, t);
       add_rn<W>(acc, t, s);
       acc = s;
     }
@@ -439,18 +450,25 @@ mp_status spmv_w(const mp_csr_s* M, const Sell& S, int mode, const uint64_t* x, 
   const int tpb = M->cfg_tpb[mode == MP_ORDERED && !b ? 0 : 1];
   const int blocks = (int)((S.nchunks * 32 + tpb - 1) / tpb);
   if (mode == MP_ORDERED && !b) {
-    const bool pipe = M->cfg_var[0] < 0 ? Pipelined<W>::value : (M->cfg_var[0] != 0);
-    if (pipe && Pipelined<W>::value)
-      spmv_ordered_kernel<W, Pipelined<W>::value><<<blocks, tpb, 0, st>>>(V, x, ldx, y, ldy, gate);
+    const int var = M->cfg_var[0];
+    const bool pipe = Pipelined<W>::value && (var < 0 || (var & kVarStage));
+    const bool cols = var < 0 ? cols_default(MP_ORDERED, W) : (var & kVarCols) != 0;
+    constexpr bool P = Pipelined<W>::value;
+    if (pipe && cols)
+      spmv_ordered_kernel<W, P, true><<<blocks, tpb, 0, st>>>(V, x, ldx, y, ldy, gate);
+    else if (pipe)
+      spmv_ordered_kernel<W, P, false><<<blocks, tpb, 0, st>>>(V, x, ldx, y, ldy, gate);
+    else if (cols)
+      spmv_ordered_kernel<W, false, true><<<blocks, tpb, 0, st>>>(V, x, ldx, y, ldy, gate);
     else
-      spmv_ordered_kernel<W, false><<<blocks, tpb, 0, st>>>(V, x, ldx, y, ldy, gate);
+      spmv_ordered_kernel<W, false, false><<<blocks, tpb, 0, st>>>(V, x, ldx, y, ldy, gate);
     count_launch();
     return launch_check("spmv_ordered_kernel");
   }
   int* status = status_word();
   if (!status) return set_error(MP_ERR_CUDA, "status word unavailable");
   MPK_CUDA(cudaMemsetAsync(M->ovf, 0, sizeof(int32_t), st));
-  const bool cols = M->cfg_var[1] < 0 ? cols_default(W) : (M->cfg_var[1] != 0);
+  const bool cols = M->cfg_var[1] < 0 ? cols_default(MP_EXACT, W) : (M->cfg_var[1] & kVarCols) != 0;
   const size_t smem = (size_t)(cols ? Win<W>::fast_cols : Win<W>::fast) * tpb * sizeof(int64_t);
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -532,7 +550,7 @@ mp_status mp_csr_set_config(mp_csr A, int32_t mode, int32_t tpb, int32_t variant
   if (mode != MP_ORDERED && mode != MP_EXACT) return set_error(MP_ERR_ARG, "mode %d", mode);
   if (tpb != 32 && tpb != 64 && tpb != 128 && tpb != 256)
     return set_error(MP_ERR_ARG, "threads per block %d not in {32,64,128,256}", tpb);
-  if (variant < -1 || variant > 1) return set_error(MP_ERR_ARG, "variant %d not in {-1,0,1}", variant);
+  if (variant < -1 || variant > 3) return set_error(MP_ERR_ARG, "variant %d not in -1..3", variant);
   A->cfg_tpb[mode] = tpb;
   A->cfg_var[mode] = variant;
   return MP_OK;
@@ -540,9 +558,10 @@ mp_status mp_csr_set_config(mp_csr A, int32_t mode, int32_t tpb, int32_t variant
 
 // The variant that runs for the matrix's current setting.
 static int effective_variant(const mp_csr_s* A, int mode) {
-  const int W = A->prec / 32;
-  if (mode == MP_ORDERED) return W > 16 ? 0 : (A->cfg_var[0] < 0 ? 1 : A->cfg_var[0]);
-  return A->cfg_var[1] < 0 ? (cols_default(W) ? 1 : 0) : A->cfg_var[1];
+  const int W = A->prec / 32, v = A->cfg_var[mode];
+  const bool cols = v < 0 ? cols_default(mode, W) : (v & kVarCols) != 0;
+  const bool stage = mode == MP_ORDERED && W <= 16 && (v < 0 || (v & kVarStage));
+  return (cols ? kVarCols : 0) | (stage ? kVarStage : 0);
 }
 
 mp_status mp_csr_get_config(mp_csr A, int32_t mode, int32_t* tpb, int32_t* variant) {
@@ -579,10 +598,10 @@ mp_status mp_csr_tune(mp_csr A, int32_t mode, int32_t reps, int32_t* tpb_out, in
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  // ORDERED staging exists for p <= 512; EXACT has both product forms
-  const int nvar = (mode == MP_EXACT || A->prec <= 512) ? 2 : 1;
+  // both product forms; ORDERED staging exists for p <= 512 only
+  const int vstep = (mode == MP_EXACT || A->prec > 512) ? kVarCols : 1;
   for (int32_t tpb : {32, 64, 128, 256}) {
-    for (int32_t v = 0; v < nvar && r == MP_OK; ++v) {
+    for (int32_t v = 0; v <= (kVarCols | kVarStage) && r == MP_OK; v += vstep) {
       A->cfg_tpb[mode] = tpb;
       A->cfg_var[mode] = v;
       r = launch_spmv(A, A->A, mode, x, n, y, n, nullptr, 0, nullptr, st);

@@ -28,12 +28,13 @@ def test_every_configuration_matches_the_oracle(p):
         want, st = oracle.spmv(p, m, rowptr, colidx, recs(V), recs(X))
         want_t, _ = oracle.spmv_t(p, m, rowptr, colidx, recs(V), recs(X))
         for tpb in (32, 64, 128, 256):
-            for v in (0, 1, -1):
+            for v in (0, 1, 2, 3, -1):
                 A.set_config(name, tpb, v)
                 got = A.get_config(name)
                 assert got["threads_per_block"] == tpb
-                if v >= 0 and not (name == "ordered" and p == 1024):
-                    assert got["variant"] == v
+                if v >= 0:
+                    stage_ok = name == "ordered" and p <= 512
+                    assert got["variant"] == (v if stage_ok else v & 2)
                 what = f"{name} p={p} tpb={tpb} variant={v}"
                 assert_bitwise(mpk.spmv(A, x, mode=name).planes(), want, what)
                 assert_bitwise(mpk.spmv_t(A, x, mode=name).planes(), want_t, "T " + what)
@@ -43,7 +44,7 @@ def test_bad_configuration_is_rejected():
     mpk = need_gpu()
     rowptr, colidx = random_csr(64, seed=2)
     A = mpk.CSR(rowptr, colidx, np.ones(len(colidx)), 128)
-    for args in (("ordered", 96, -1), ("ordered", 128, 2), ("exact", 512, -1)):
+    for args in (("ordered", 96, -1), ("ordered", 128, 4), ("exact", 512, -1), ("exact", 64, -2)):
         with pytest.raises(mpk.MPError):
             A.set_config(*args)
     assert A.get_config("ordered")["threads_per_block"] == 128
@@ -67,7 +68,7 @@ def test_tuner_and_cache(p, tmp_path):
         assert not r["cached"] and r["ms"] > 0
         assert r["threads_per_block"] in (32, 64, 128, 256)
         assert A.get_config(name)["threads_per_block"] == r["threads_per_block"]
-        assert r["variant"] in ((0,) if (name == "ordered" and p == 1024) else (0, 1))
+        assert r["variant"] in ((0, 1, 2, 3) if (name == "ordered" and p <= 512) else (0, 2))
         want, _ = oracle.spmv(p, m, rowptr, colidx, recs(V), recs(X))
         assert_bitwise(mpk.spmv(A, x, mode=name).planes(), want, f"tuned {name} p={p}")
     assert len(json.load(open(cache))) == 2
@@ -79,7 +80,7 @@ def test_tuner_and_cache(p, tmp_path):
 
 
 @pytest.mark.parametrize("p", (128, 256, 512, 1024))
-@pytest.mark.parametrize("variant", (0, 1))
+@pytest.mark.parametrize("variant", (0, 2))
 def test_exact_variants_on_hard_rows(p, variant):
     """Both EXACT product forms on rows whose spans sit around the per-thread
     window (in it, just beyond it: the warp-per-row path), beyond the span
@@ -121,3 +122,39 @@ def test_exact_variants_on_hard_rows(p, variant):
         mpk.check()
     want_r, _ = oracle.residual(p, rowptr, colidx, Vr, recs(B), Xr)
     assert_bitwise(r.planes(), want_r, f"residual variant={variant} p={p}")
+
+
+def _mantissa_planes(ms, p, exps, signs):
+    """Planes of values (-1)^s * M * 2^(e-p) from integer mantissas M."""
+    L = p // 64
+    out = np.zeros((L + 1, len(ms)), np.uint64)
+    for k, (m, e, sg) in enumerate(zip(ms, exps, signs)):
+        out[0, k] = np.uint64((2 * e + sg) & ((1 << 64) - 1))
+        for l in range(L):
+            out[1 + l, k] = np.uint64((m >> (64 * l)) & ((1 << 64) - 1))
+    return out
+
+
+@pytest.mark.parametrize("p", (128, 256, 512, 1024))
+def test_ordered_products_round_ties_to_even(p):
+    """y_i = RN(a_i x_i) on a diagonal matrix whose products are exact ties
+    (M_a = 2^(p-1) + 2^i, M_x = 2^(p-1) + 2^(p-2-i): the dropped bits are
+    exactly one half) and near-ties, in both product forms."""
+    mpk = need_gpu()
+    ia = [0, 1, 2, 5, 31, 32, 33, p // 2 - 1, p // 2, p - 3]
+    ma, mx = [], []
+    for i in ia:
+        a, x = (1 << (p - 1)) + (1 << i), (1 << (p - 1)) + (1 << (p - 2 - i))
+        ma += [a, a, a + 1]
+        mx += [x, x + (1 << 0), x]
+    n = len(ma)
+    rowptr = np.arange(n + 1, dtype=np.int64)
+    colidx = np.arange(n, dtype=np.int32)
+    V = _mantissa_planes(ma, p, [3] * n, [k % 2 for k in range(n)])
+    X = _mantissa_planes(mx, p, [-7] * n, [0] * n)
+    A = mpk.CSR(rowptr, colidx, V, p)
+    x = mpk.Vec.from_planes(X, p)
+    want, _ = oracle.spmv(p, oracle.ORDERED, rowptr, colidx, recs(V), recs(X))
+    for v in (0, 2):
+        A.set_config("ordered", 128, v)
+        assert_bitwise(mpk.spmv(A, x, mode="ordered").planes(), want, f"ties variant={v} p={p}")
