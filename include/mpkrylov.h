@@ -115,28 +115,37 @@ mp_status mp_csr_info(mp_csr A, int64_t* n, int64_t* nnz, int32_t* prec_bits,
                       int64_t* slots, int64_t* device_bytes);
 
 /* Launch configuration of the products of A (a tuning knob, not part of the
- * paper; results never depend on it): threads per block (32, 64, 128 or 256)
- * for mode MP_ORDERED or MP_EXACT, and a variant, a bit field:
- *   bit 0 (MP_ORDERED only): the row loop loads the next entry's operands
- *          while the current one is computed (p <= 512; p = 1024 never
- *          does);
- *   bit 1: products formed from radix-2^29 column sums (one multiply-add
- *          per pair of 29-bit limbs, no carries inside the product; EXACT
- *          then keeps 29-bit digit counters), else from 32-bit words with
- *          carry chains;
- *   -1 = the library's default for the precision.
- * mp_csr_get_config reports the variant that runs. */
-mp_status mp_csr_set_config(mp_csr A, int32_t mode, int32_t threads_per_block, int32_t variant);
+ * paper; results never depend on it), per mode MP_ORDERED / MP_EXACT:
+ *   threads_per_block: 32, 64, 128 or 256;
+ *   variant, a bit field:
+ *     bit 0: the row loop loads the next entry's operands while the current
+ *            one is computed (MP_ORDERED: p <= 512 only; MP_EXACT: column
+ *            form only, the word form does it at p <= 512);
+ *     bit 1: products formed from radix-2^29 column sums (one multiply-add
+ *            per pair of 29-bit limbs, no carries inside the product; EXACT
+ *            then keeps 29-bit digit counters), else from 32-bit words with
+ *            carry chains;
+ *     bit 2 (MP_EXACT column form): 16 columns computed at a time, not 8;
+ *   carveout: the shared-memory share of the unified L1/shared storage the
+ *            kernels ask for, in percent (more digit windows per SM against
+ *            more L1 for the gathers of x);
+ *   -1 for any of them: the library's default for the precision.
+ * mp_csr_get_config reports the configuration that runs (defaults resolved;
+ * carveout -1 = the driver's choice). */
+mp_status mp_csr_set_config(mp_csr A, int32_t mode, int32_t threads_per_block, int32_t variant,
+                            int32_t carveout);
 mp_status mp_csr_get_config(mp_csr A, int32_t mode, int32_t* threads_per_block,
-                            int32_t* variant);
+                            int32_t* variant, int32_t* carveout);
 
-/* Autotuner: times y = A x (mode) for every configuration above on an
- * internal nonzero x, `reps` launches each, keeps the fastest in A and
- * returns it with its time per product (ms).  Allocates two n-vectors for
- * the duration of the call.  Rows whose exponent span exceeds MP_SPAN_CAP
- * record MP_ERR_SPAN in the status word as in mp_spmv. */
+/* Autotuner: times y = A x (mode) for the configurations above (64-256
+ * threads; every variant; for EXACT the carve-outs default, 25, 50 and 75 %)
+ * on an internal nonzero x, `reps` launches each, keeps the fastest in A and
+ * returns it (as mp_csr_get_config) with its time per product (ms).
+ * Allocates two n-vectors for the duration of the call.  Rows whose exponent
+ * span exceeds MP_SPAN_CAP record MP_ERR_SPAN in the status word as in
+ * mp_spmv. */
 mp_status mp_csr_tune(mp_csr A, int32_t mode, int32_t reps, int32_t* threads_per_block,
-                      int32_t* variant, double* ms, void* stream);
+                      int32_t* variant, int32_t* carveout, double* ms, void* stream);
 
 /* ---- products ------------------------------------------------------------ */
 

@@ -177,26 +177,28 @@ class CSR:
         return {"n": n.value, "nnz": nnz.value, "prec": p.value, "slots": slots.value,
                 "device_bytes": nbytes.value}
 
-    def set_config(self, mode="ordered", threads_per_block=128, variant=-1):
+    def set_config(self, mode="ordered", threads_per_block=-1, variant=-1, carveout=-1):
         """SpMV launch configuration for one mode (results do not depend on it).
-        variant: bit field, bit 0 = ORDERED operand staging, bit 1 = products
-        from radix-2^29 column sums; -1 = the library's default."""
+        variant: bit field, bit 0 = operand staging, bit 1 = products from
+        radix-2^29 column sums, bit 2 = EXACT column sums 16 at a time;
+        carveout: shared-memory percent of L1/shared; -1 = library default."""
         _ok(_lib.load().mp_csr_set_config(self.h, MODES[mode], int(threads_per_block),
-                                          int(variant)), "mp_csr_set_config")
+                                          int(variant), int(carveout)), "mp_csr_set_config")
 
     def get_config(self, mode="ordered") -> dict:
-        t, s = ctypes.c_int32(), ctypes.c_int32()
-        _ok(_lib.load().mp_csr_get_config(self.h, MODES[mode], ctypes.byref(t), ctypes.byref(s)),
-            "mp_csr_get_config")
-        return {"threads_per_block": t.value, "variant": s.value}
+        t, v, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _ok(_lib.load().mp_csr_get_config(self.h, MODES[mode], ctypes.byref(t), ctypes.byref(v),
+                                          ctypes.byref(c)), "mp_csr_get_config")
+        return {"threads_per_block": t.value, "variant": v.value, "carveout": c.value}
 
     def tune(self, mode="ordered", reps=5, stream=None) -> dict:
         """Times every launch configuration of y = A x, keeps the fastest."""
-        t, s, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+        t, v, c, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
         _ok(_lib.load().mp_csr_tune(self.h, MODES[mode], int(reps), ctypes.byref(t),
-                                    ctypes.byref(s), ctypes.byref(ms), _stream(stream)),
-            "mp_csr_tune")
-        return {"threads_per_block": t.value, "variant": s.value, "ms": ms.value}
+                                    ctypes.byref(v), ctypes.byref(c), ctypes.byref(ms),
+                                    _stream(stream)), "mp_csr_tune")
+        return {"threads_per_block": t.value, "variant": v.value, "carveout": c.value,
+                "ms": ms.value}
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:

@@ -56,9 +56,10 @@ SIGNATURES = {
     "mp_csr_create_f64": (_i32, [_i64, _vp, _vp, _vp, _i32, _i32, _vp, ctypes.POINTER(_vp)]),
     "mp_csr_destroy": (_i32, [_vp]),
     "mp_csr_info": (_i32, [_vp, _i64p, _i64p, _i32p, _i64p, _i64p]),
-    "mp_csr_set_config": (_i32, [_vp, _i32, _i32, _i32]),
-    "mp_csr_get_config": (_i32, [_vp, _i32, _i32p, _i32p]),
-    "mp_csr_tune": (_i32, [_vp, _i32, _i32, _i32p, _i32p, ctypes.POINTER(ctypes.c_double), _vp]),
+    "mp_csr_set_config": (_i32, [_vp, _i32, _i32, _i32, _i32]),
+    "mp_csr_get_config": (_i32, [_vp, _i32, _i32p, _i32p, _i32p]),
+    "mp_csr_tune": (_i32, [_vp, _i32, _i32, _i32p, _i32p, _i32p, ctypes.POINTER(ctypes.c_double),
+                           _vp]),
     "mp_spmv": (_i32, [_vp, MpVec, MpVec, _i32, _vp]),
     "mp_spmv_t": (_i32, [_vp, MpVec, MpVec, _i32, _vp]),
     "mp_residual": (_i32, [_vp, MpVec, MpVec, MpVec, _vp]),

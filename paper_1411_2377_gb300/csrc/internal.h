@@ -40,11 +40,12 @@ struct mp_csr_s {
   int32_t* ovf = nullptr;  // [n + 1]: overflow-row count then rows (EXACT wide path)
   int64_t bytes = 0;
   // SpMV launch configuration per mode (ORDERED [0], EXACT [1]), set by
-  // mp_csr_tune / mp_csr_set_config: threads per block, and the variant
-  // (ORDERED: operand staging of the row loop; EXACT: 32-bit word digits or
-  // radix-2^29 column sums; -1: the default for the precision).
-  int32_t cfg_tpb[2] = {128, 128};
+  // mp_csr_tune / mp_csr_set_config: threads per block, variant bits and
+  // shared-memory carve-out (percent); -1 everywhere: the library's default
+  // for the precision.
+  int32_t cfg_tpb[2] = {-1, -1};
   int32_t cfg_var[2] = {-1, -1};
+  int32_t cfg_carve[2] = {-1, -1};
   // FP64 copy for mixed-precision refinement (built on first use): the
   // row-equilibrated entries 2^-E_i a_ij per slot of A's layout, and 2^-E_i.
   double* a64 = nullptr;

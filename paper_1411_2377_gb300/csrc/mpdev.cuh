@@ -632,7 +632,7 @@ __device__ __forceinline__ void cut_limbs_shifted(const uint32_t (&m)[W], uint32
 
 // c[(q + k) * stride] += (-1)^neg * D_k for the digits D of the term
 // Ma * Mx * 2^off, off = 29 q + s.
-template <int W>
+template <int W, int G = 8>
 __device__ __forceinline__ void add_product_cols(int64_t* c, int stride, const uint32_t (&a)[W],
                                                  const uint32_t (&x)[W], uint32_t off,
                                                  uint32_t neg) {
@@ -646,28 +646,36 @@ __device__ __forceinline__ void add_product_cols(int64_t* c, int stride, const u
   uint64_t carry = 0u;
   // G columns at a time: their counters are loaded together, then updated
   // and stored together, so the shared-memory latency is paid once per group
-  constexpr int G = 8;
 #pragma unroll
   for (int k0 = 0; k0 <= NC; k0 += G) {
-    uint64_t dd[G];
+    uint64_t dd[G], acc[G];
     int64_t v[G];
+    // the group's counters are read first (their latency overlaps the
+    // multiply-adds), then the G columns' multiply-adds run interleaved: G
+    // independent chains
+#pragma unroll
+    for (int u = 0; u < G; ++u)
+      if (k0 + u <= NC) v[u] = p[(k0 + u) * stride];
+#pragma unroll
+    for (int u = 0; u < G; ++u) acc[u] = 0u;
+#pragma unroll
+    for (int i = 0; i < NA; ++i) {
+#pragma unroll
+      for (int u = 0; u < G; ++u) {
+        const int j = k0 + u - i;
+        if (k0 + u < NC && j >= 0 && j < NX) acc[u] += (uint64_t)al[i] * xl[j];
+      }
+    }
 #pragma unroll
     for (int u = 0; u < G; ++u) {
       const int k = k0 + u;
       if (k < NC) {
-        uint64_t acc = 0u;
-#pragma unroll
-        for (int i = (k - NX + 1 > 0 ? k - NX + 1 : 0); i <= (k < NA - 1 ? k : NA - 1); ++i)
-          acc += (uint64_t)al[i] * xl[k - i];
-        dd[u] = (uint64_t)((uint32_t)acc & kRMask) + carry;
-        carry = acc >> kR;
+        dd[u] = (uint64_t)((uint32_t)acc[u] & kRMask) + carry;
+        carry = acc[u] >> kR;
       } else if (k == NC) {
         dd[u] = carry;
       }
     }
-#pragma unroll
-    for (int u = 0; u < G; ++u)
-      if (k0 + u <= NC) v[u] = p[(k0 + u) * stride];
 #pragma unroll
     for (int u = 0; u < G; ++u)
       if (k0 + u <= NC) p[(k0 + u) * stride] = v[u] + (int64_t)((dd[u] ^ m) - m);

@@ -38,13 +38,39 @@ __host__ __device__ inline int digits_cols(int64_t span, int W) {
   return (int)((span + 64 * W + 64) / kR) + 4;
 }
 
-// Launch variants (a bit field): bit 0 = the ORDERED row loop stages the
-// next entry's operands (p <= 512 only), bit 1 = products from radix-2^29
-// column sums.  cols_default: whether a mode uses column sums when the
-// matrix leaves the choice to the library.
-constexpr int kVarStage = 1, kVarCols = 2;
-__host__ __device__ inline bool cols_default(int mode, int W) {
-  return mode == MP_EXACT ? W >= 16 : W >= 8;
+// Launch variants (a bit field): bit 0 = the row loop stages the next
+// entry's operands (ORDERED: p <= 512 only; EXACT: column form only, word
+// form stages at p <= 512), bit 1 = products from radix-2^29 column sums,
+// bit 2 = EXACT column sums computed 16 columns at a time instead of 8.
+constexpr int kVarStage = 1, kVarCols = 2, kVarWide = 4;
+// A matrix's launch configuration for one mode with the library's defaults
+// filled in (chosen from measurements of the n = 10^6 sweep on GB300: the
+// word form with a half-and-half L1/shared split for EXACT at p <= 512, the
+// column form with 256 threads at p = 1024; column products for ORDERED from
+// p = 256 on).
+struct LaunchCfg {
+  int tpb;
+  bool stage, cols, wide;
+  int carve;  // -1: the driver's choice
+};
+
+LaunchCfg launch_cfg(const mp_csr_s* M, int mode, int W) {
+  const int v = M->cfg_var[mode];
+  LaunchCfg c;
+  if (mode == MP_ORDERED) {
+    c.cols = v < 0 ? W >= 8 : (v & kVarCols) != 0;
+    c.stage = W <= 16 && (v < 0 || (v & kVarStage));
+    c.wide = false;
+    c.tpb = M->cfg_tpb[0] < 0 ? 128 : M->cfg_tpb[0];
+    c.carve = M->cfg_carve[0];
+  } else {
+    c.cols = v < 0 ? W >= 32 : (v & kVarCols) != 0;
+    c.stage = c.cols ? (v < 0 || (v & kVarStage)) : W <= 16;
+    c.wide = c.cols && v >= 0 && (v & kVarWide);
+    c.tpb = M->cfg_tpb[1] < 0 ? (W >= 32 ? 256 : 128) : M->cfg_tpb[1];
+    c.carve = M->cfg_carve[1] < 0 ? (W <= 16 ? 50 : -1) : M->cfg_carve[1];
+  }
+  return c;
 }
 
 __host__ __device__ inline int digits_for(int64_t span, int W) {
@@ -190,7 +216,7 @@ __device__ __forceinline__ void value_as_product(const Num<W>& b, uint32_t (&P)[
   }
 }
 
-template <int W, bool RESID, bool COLS>
+template <int W, bool RESID, bool COLS, bool PIPE = Pipelined<W>::value || COLS, int G = 8>
 __global__ void __launch_bounds__(256) spmv_exact_kernel(
     const SellView S, const uint64_t* __restrict__ x, int64_t ldx, uint64_t* __restrict__ y,
     int64_t ldy, const uint64_t* __restrict__ bv, int64_t ldb, int32_t* __restrict__ ovf,
@@ -273,7 +299,7 @@ __global__ void __launch_bounds__(256) spmv_exact_kernel(
   // adds the term a * x (sign already folded into ng)
   auto term = [&](const Num<W>& a, const Num<W>& xv, uint32_t ng) {
     if (COLS) {
-      add_product_cols<W>(c, stride, a.m, xv.m, (uint32_t)(a.e + xv.e - emin), ng);
+      add_product_cols<W, G>(c, stride, a.m, xv.m, (uint32_t)(a.e + xv.e - emin), ng);
     } else {
       if (W >= 16)
         mul_full_ilp<W>(a.m, xv.m, P);
@@ -282,7 +308,9 @@ __global__ void __launch_bounds__(256) spmv_exact_kernel(
       add_term<W>(c, stride, P, a.e + xv.e - emin, ng);
     }
   };
-  if (Pipelined<W>::value) {
+  // staging: at p = 1024 only the column form has registers to spare (its
+  // occupancy is bounded by the shared-memory window anyway)
+  if (PIPE) {
     Num<W> an, xn;
     int32_t c1 = 0;
     if (len > 0) {
@@ -447,34 +475,44 @@ mp_status spmv_w(const mp_csr_s* M, const Sell& S, int mode, const uint64_t* x, 
                  cudaStream_t st, const int32_t* rinst = nullptr, const int* idone = nullptr) {
   if (S.nchunks == 0) return MP_OK;
   const SellView V = view(S, rinst, idone);
-  const int tpb = M->cfg_tpb[mode == MP_ORDERED && !b ? 0 : 1];
+  const LaunchCfg cf = launch_cfg(M, mode == MP_ORDERED && !b ? MP_ORDERED : MP_EXACT, W);
+  const int tpb = cf.tpb;
   const int blocks = (int)((S.nchunks * 32 + tpb - 1) / tpb);
   if (mode == MP_ORDERED && !b) {
-    const int var = M->cfg_var[0];
-    const bool pipe = Pipelined<W>::value && (var < 0 || (var & kVarStage));
-    const bool cols = var < 0 ? cols_default(MP_ORDERED, W) : (var & kVarCols) != 0;
     constexpr bool P = Pipelined<W>::value;
-    if (pipe && cols)
-      spmv_ordered_kernel<W, P, true><<<blocks, tpb, 0, st>>>(V, x, ldx, y, ldy, gate);
-    else if (pipe)
-      spmv_ordered_kernel<W, P, false><<<blocks, tpb, 0, st>>>(V, x, ldx, y, ldy, gate);
-    else if (cols)
-      spmv_ordered_kernel<W, false, true><<<blocks, tpb, 0, st>>>(V, x, ldx, y, ldy, gate);
+    auto ordered = [&](auto kern) -> mp_status {
+      if (cf.carve >= 0)
+        MPK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cf.carve));
+      kern<<<blocks, tpb, 0, st>>>(V, x, ldx, y, ldy, gate);
+      return MP_OK;
+    };
+    mp_status r;
+    if (cf.stage && cf.cols)
+      r = ordered(spmv_ordered_kernel<W, P, true>);
+    else if (cf.stage)
+      r = ordered(spmv_ordered_kernel<W, P, false>);
+    else if (cf.cols)
+      r = ordered(spmv_ordered_kernel<W, false, true>);
     else
-      spmv_ordered_kernel<W, false, false><<<blocks, tpb, 0, st>>>(V, x, ldx, y, ldy, gate);
+      r = ordered(spmv_ordered_kernel<W, false, false>);
+    if (r != MP_OK) return r;
     count_launch();
     return launch_check("spmv_ordered_kernel");
   }
   int* status = status_word();
   if (!status) return set_error(MP_ERR_CUDA, "status word unavailable");
   MPK_CUDA(cudaMemsetAsync(M->ovf, 0, sizeof(int32_t), st));
-  const bool cols = M->cfg_var[1] < 0 ? cols_default(MP_EXACT, W) : (M->cfg_var[1] & kVarCols) != 0;
+  const bool cols = cf.cols;
   const size_t smem = (size_t)(cols ? Win<W>::fast_cols : Win<W>::fast) * tpb * sizeof(int64_t);
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   auto exact = [&](auto kern, const uint64_t* bb) -> mp_status {
     MPK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // shared memory vs L1 split: more digit windows per SM, or more cache for
+    // the gathers of x
+    MPK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  cf.carve < 0 ? (int)cudaSharedmemCarveoutDefault : cf.carve));
     kern<<<blocks, tpb, smem, st>>>(V, x, ldx, y, ldy, bb, ldb, M->ovf, status, gate);
     return MP_OK;
   };
@@ -484,8 +522,17 @@ mp_status spmv_w(const mp_csr_s* M, const Sell& S, int mode, const uint64_t* x, 
     if (r != MP_OK) return r;
     spmv_exact_wide_kernel<W, true><<<sms * 4, 32, 0, st>>>(V, x, ldx, y, ldy, b, ldb, M->ovf, gate);
   } else {
-    r = cols ? exact(spmv_exact_kernel<W, false, true>, nullptr)
-             : exact(spmv_exact_kernel<W, false, false>, nullptr);
+    const bool stage = cf.stage, wide = cf.wide;
+    if (!cols)
+      r = exact(spmv_exact_kernel<W, false, false>, nullptr);
+    else if (stage && wide)
+      r = exact(spmv_exact_kernel<W, false, true, true, 16>, nullptr);
+    else if (stage)
+      r = exact(spmv_exact_kernel<W, false, true, true, 8>, nullptr);
+    else if (wide)
+      r = exact(spmv_exact_kernel<W, false, true, false, 16>, nullptr);
+    else
+      r = exact(spmv_exact_kernel<W, false, true, false, 8>, nullptr);
     if (r != MP_OK) return r;
     spmv_exact_wide_kernel<W, false><<<sms * 4, 32, 0, st>>>(V, x, ldx, y, ldy, nullptr, 0,
                                                              M->ovf, gate);
@@ -545,35 +592,34 @@ mp_status mp_spmv_t(mp_csr A, mp_vec x, mp_vec y, mp_mode mode, void* stream) {
                      static_cast<cudaStream_t>(stream));
 }
 
-mp_status mp_csr_set_config(mp_csr A, int32_t mode, int32_t tpb, int32_t variant) {
+mp_status mp_csr_set_config(mp_csr A, int32_t mode, int32_t tpb, int32_t variant,
+                            int32_t carveout) {
   if (!A) return set_error(MP_ERR_ARG, "matrix is null");
   if (mode != MP_ORDERED && mode != MP_EXACT) return set_error(MP_ERR_ARG, "mode %d", mode);
-  if (tpb != 32 && tpb != 64 && tpb != 128 && tpb != 256)
-    return set_error(MP_ERR_ARG, "threads per block %d not in {32,64,128,256}", tpb);
-  if (variant < -1 || variant > 3) return set_error(MP_ERR_ARG, "variant %d not in -1..3", variant);
+  if (tpb != -1 && tpb != 32 && tpb != 64 && tpb != 128 && tpb != 256)
+    return set_error(MP_ERR_ARG, "threads per block %d not in {-1,32,64,128,256}", tpb);
+  if (variant < -1 || variant > 7) return set_error(MP_ERR_ARG, "variant %d not in -1..7", variant);
+  if (carveout < -1 || carveout > 100) return set_error(MP_ERR_ARG, "carve-out %d", carveout);
   A->cfg_tpb[mode] = tpb;
   A->cfg_var[mode] = variant;
+  A->cfg_carve[mode] = carveout;
   return MP_OK;
 }
 
-// The variant that runs for the matrix's current setting.
-static int effective_variant(const mp_csr_s* A, int mode) {
-  const int W = A->prec / 32, v = A->cfg_var[mode];
-  const bool cols = v < 0 ? cols_default(mode, W) : (v & kVarCols) != 0;
-  const bool stage = mode == MP_ORDERED && W <= 16 && (v < 0 || (v & kVarStage));
-  return (cols ? kVarCols : 0) | (stage ? kVarStage : 0);
-}
-
-mp_status mp_csr_get_config(mp_csr A, int32_t mode, int32_t* tpb, int32_t* variant) {
+mp_status mp_csr_get_config(mp_csr A, int32_t mode, int32_t* tpb, int32_t* variant,
+                            int32_t* carveout) {
   if (!A) return set_error(MP_ERR_ARG, "matrix is null");
   if (mode != MP_ORDERED && mode != MP_EXACT) return set_error(MP_ERR_ARG, "mode %d", mode);
-  if (tpb) *tpb = A->cfg_tpb[mode];
-  if (variant) *variant = effective_variant(A, mode);
+  const LaunchCfg c = launch_cfg(A, mode, A->prec / 32);
+  if (tpb) *tpb = c.tpb;
+  if (variant)
+    *variant = (c.cols ? kVarCols : 0) | (c.stage ? kVarStage : 0) | (c.wide ? kVarWide : 0);
+  if (carveout) *carveout = c.carve;
   return MP_OK;
 }
 
 mp_status mp_csr_tune(mp_csr A, int32_t mode, int32_t reps, int32_t* tpb_out, int32_t* var_out,
-                      double* ms_out, void* stream) {
+                      int32_t* carve_out, double* ms_out, void* stream) {
   if (!A) return set_error(MP_ERR_ARG, "matrix is null");
   if (mode != MP_ORDERED && mode != MP_EXACT) return set_error(MP_ERR_ARG, "mode %d", mode);
   if (reps < 1) return set_error(MP_ERR_ARG, "reps %d", reps);
@@ -592,31 +638,47 @@ mp_status mp_csr_tune(mp_csr A, int32_t mode, int32_t reps, int32_t* tpb_out, in
     count_launch();
     return launch_check("tune_fill_kernel");
   });
-  const int32_t old_tpb = A->cfg_tpb[mode], old_var = A->cfg_var[mode];
+  const int32_t old_t = A->cfg_tpb[mode], old_v = A->cfg_var[mode], old_c = A->cfg_carve[mode];
   float best = 1e30f;
-  int32_t bt = old_tpb, bv = old_var;
+  int32_t bt = old_t, bv = old_v, bc = old_c;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  // both product forms; ORDERED staging exists for p <= 512 only
-  const int vstep = (mode == MP_EXACT || A->prec > 512) ? kVarCols : 1;
-  for (int32_t tpb : {32, 64, 128, 256}) {
-    for (int32_t v = 0; v <= (kVarCols | kVarStage) && r == MP_OK; v += vstep) {
-      A->cfg_tpb[mode] = tpb;
-      A->cfg_var[mode] = v;
-      r = launch_spmv(A, A->A, mode, x, n, y, n, nullptr, 0, nullptr, st);
-      cudaEventRecord(e0, st);
-      for (int k = 0; k < reps && r == MP_OK; ++k)
+  // ORDERED: both product forms, staging for p <= 512; EXACT: the word
+  // form, and the column form with and without staging, 8 or 16 columns at
+  // a time, each under four shared-memory carve-outs
+  int32_t vars[5], carves[4] = {-1, 25, 50, 75};
+  int nvar = 0, ncarve = mode == MP_EXACT ? 4 : 1;
+  if (mode == MP_ORDERED) {
+    for (int32_t v = 0; v <= (kVarCols | kVarStage); v += (A->prec > 512 ? kVarCols : 1))
+      vars[nvar++] = v;
+  } else {
+    vars[nvar++] = 0;
+    for (int32_t v : {kVarCols, kVarCols | kVarStage, kVarCols | kVarWide,
+                      kVarCols | kVarStage | kVarWide})
+      vars[nvar++] = v;
+  }
+  for (int32_t tpb : {64, 128, 256}) {
+    for (int vi = 0; vi < nvar && r == MP_OK; ++vi) {
+      for (int ci = 0; ci < ncarve && r == MP_OK; ++ci) {
+        A->cfg_tpb[mode] = tpb;
+        A->cfg_var[mode] = vars[vi];
+        A->cfg_carve[mode] = carves[ci];
         r = launch_spmv(A, A->A, mode, x, n, y, n, nullptr, 0, nullptr, st);
-      cudaEventRecord(e1, st);
-      cudaEventSynchronize(e1);
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      ms /= reps;
-      if (r == MP_OK && ms < best) {
-        best = ms;
-        bt = tpb;
-        bv = v;
+        cudaEventRecord(e0, st);
+        for (int k = 0; k < reps && r == MP_OK; ++k)
+          r = launch_spmv(A, A->A, mode, x, n, y, n, nullptr, 0, nullptr, st);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= reps;
+        if (r == MP_OK && ms < best) {
+          best = ms;
+          bt = tpb;
+          bv = vars[vi];
+          bc = carves[ci];
+        }
       }
     }
   }
@@ -625,13 +687,12 @@ mp_status mp_csr_tune(mp_csr A, int32_t mode, int32_t reps, int32_t* tpb_out, in
   cudaStreamSynchronize(st);
   cudaFree(x);
   cudaFree(y);
-  A->cfg_tpb[mode] = r == MP_OK ? bt : old_tpb;
-  A->cfg_var[mode] = r == MP_OK ? bv : old_var;
+  A->cfg_tpb[mode] = r == MP_OK ? bt : old_t;
+  A->cfg_var[mode] = r == MP_OK ? bv : old_v;
+  A->cfg_carve[mode] = r == MP_OK ? bc : old_c;
   if (r != MP_OK) return r;
-  if (tpb_out) *tpb_out = bt;
-  if (var_out) *var_out = effective_variant(A, mode);
   if (ms_out) *ms_out = best;
-  return MP_OK;
+  return mp_csr_get_config(A, mode, tpb_out, var_out, carve_out);
 }
 
 mp_status mp_csr_grad(mp_csr A, mp_vec lam, mp_vec x, mp_vec g, void* stream) {

@@ -1,8 +1,8 @@
 """Autotuned SpMV launch configurations, cached on disk.
 
 The configuration of a matrix's products (threads per block; the variant:
-register staging of the ORDERED row loop, word or radix-2^29 column
-products in EXACT) changes the time of y = A x, never its
+register staging of the row loop, word or radix-2^29 column products; the
+shared-memory carve-out) changes the time of y = A x, never its
 value.  `autotune` times every configuration once per (GPU, precision,
 mode, row-length histogram) through mp_csr_tune and stores the winner in a
 JSON file, so that later matrices of the same shape class reuse it with
@@ -43,18 +43,19 @@ def _load(path: str) -> dict:
 def autotune(A: CSR, modes=("ordered", "exact"), reps: int = 5, cache: str | None = DEFAULT_CACHE,
              retune: bool = False) -> dict:
     """Sets the fastest launch configuration of A for each mode.  Returns
-    {mode: {"threads_per_block", "variant", "ms" (None when cached), "cached"}}."""
+    {mode: {"threads_per_block", "variant", "carveout", "ms" (None when cached),
+    "cached"}}."""
     store = _load(cache) if cache else {}
     out = {}
     for mode in modes:
         key = signature(A, mode)
         hit = store.get(key)
         if hit is not None and not retune:
-            A.set_config(mode, hit["threads_per_block"], hit["variant"])
+            A.set_config(mode, hit["threads_per_block"], hit["variant"], hit.get("carveout", -1))
             out[mode] = dict(hit, ms=None, cached=True)
             continue
         res = A.tune(mode, reps)
-        store[key] = {"threads_per_block": res["threads_per_block"], "variant": res["variant"]}
+        store[key] = {k: res[k] for k in ("threads_per_block", "variant", "carveout")}
         out[mode] = dict(res, cached=False)
     if cache:
         os.makedirs(os.path.dirname(cache) or ".", exist_ok=True)

@@ -79,6 +79,6 @@ def test_config_calls_reject_bad_arguments_without_gpu(lib):
     from paper_1411_2377_gb300 import _lib
 
     t = ctypes.c_int32()
-    assert lib.mp_csr_set_config(None, 0, 128, -1) == _lib.MP_ERR_ARG
-    assert lib.mp_csr_get_config(None, 0, ctypes.byref(t), None) == _lib.MP_ERR_ARG
-    assert lib.mp_csr_tune(None, 1, 3, None, None, None, None) == _lib.MP_ERR_ARG
+    assert lib.mp_csr_set_config(None, 0, 128, -1, -1) == _lib.MP_ERR_ARG
+    assert lib.mp_csr_get_config(None, 0, ctypes.byref(t), None, None) == _lib.MP_ERR_ARG
+    assert lib.mp_csr_tune(None, 1, 3, None, None, None, None, None) == _lib.MP_ERR_ARG

@@ -27,15 +27,21 @@ def test_every_configuration_matches_the_oracle(p):
     for name, m in MODES:
         want, st = oracle.spmv(p, m, rowptr, colidx, recs(V), recs(X))
         want_t, _ = oracle.spmv_t(p, m, rowptr, colidx, recs(V), recs(X))
-        for tpb in (32, 64, 128, 256):
-            for v in (0, 1, 2, 3, -1):
-                A.set_config(name, tpb, v)
+        for tpb, carve in ((32, -1), (64, 25), (128, 50), (256, 75), (-1, -1)):
+            for v in (0, 1, 2, 3, 6, 7, -1):
+                A.set_config(name, tpb, v, carve)
                 got = A.get_config(name)
-                assert got["threads_per_block"] == tpb
+                if tpb > 0:
+                    assert got["threads_per_block"] == tpb
+                if carve > 0:
+                    assert got["carveout"] == carve
                 if v >= 0:
-                    stage_ok = name == "ordered" and p <= 512
-                    assert got["variant"] == (v if stage_ok else v & 2)
-                what = f"{name} p={p} tpb={tpb} variant={v}"
+                    assert got["variant"] & 2 == v & 2  # the product form asked for
+                    if name == "ordered":
+                        assert got["variant"] == (v & 3 if p <= 512 else v & 2)
+                    elif v & 2:
+                        assert got["variant"] == v
+                what = f"{name} p={p} tpb={tpb} variant={v} carveout={carve}"
                 assert_bitwise(mpk.spmv(A, x, mode=name).planes(), want, what)
                 assert_bitwise(mpk.spmv_t(A, x, mode=name).planes(), want_t, "T " + what)
 
@@ -44,10 +50,12 @@ def test_bad_configuration_is_rejected():
     mpk = need_gpu()
     rowptr, colidx = random_csr(64, seed=2)
     A = mpk.CSR(rowptr, colidx, np.ones(len(colidx)), 128)
-    for args in (("ordered", 96, -1), ("ordered", 128, 4), ("exact", 512, -1), ("exact", 64, -2)):
+    for args in (("ordered", 96, -1, -1), ("ordered", 128, 8, -1), ("exact", 512, -1, -1),
+                 ("exact", 64, -2, -1), ("exact", 64, 0, 101)):
         with pytest.raises(mpk.MPError):
             A.set_config(*args)
-    assert A.get_config("ordered")["threads_per_block"] == 128
+    assert A.get_config("ordered") == {"threads_per_block": 128, "variant": 1, "carveout": -1}
+    assert A.get_config("exact") == {"threads_per_block": 128, "variant": 1, "carveout": 50}
 
 
 @pytest.mark.parametrize("p", (128, 1024))
@@ -68,7 +76,9 @@ def test_tuner_and_cache(p, tmp_path):
         assert not r["cached"] and r["ms"] > 0
         assert r["threads_per_block"] in (32, 64, 128, 256)
         assert A.get_config(name)["threads_per_block"] == r["threads_per_block"]
-        assert r["variant"] in ((0, 1, 2, 3) if (name == "ordered" and p <= 512) else (0, 2))
+        allowed = {"ordered": (0, 1, 2, 3) if p <= 512 else (0, 2),
+                   "exact": (1 if p <= 512 else 0, 2, 3, 6, 7)}[name]
+        assert r["variant"] in allowed
         want, _ = oracle.spmv(p, m, rowptr, colidx, recs(V), recs(X))
         assert_bitwise(mpk.spmv(A, x, mode=name).planes(), want, f"tuned {name} p={p}")
     assert len(json.load(open(cache))) == 2
@@ -80,7 +90,7 @@ def test_tuner_and_cache(p, tmp_path):
 
 
 @pytest.mark.parametrize("p", (128, 256, 512, 1024))
-@pytest.mark.parametrize("variant", (0, 2))
+@pytest.mark.parametrize("variant", (0, 2, 3, 6, 7))
 def test_exact_variants_on_hard_rows(p, variant):
     """Both EXACT product forms on rows whose spans sit around the per-thread
     window (in it, just beyond it: the warp-per-row path), beyond the span
@@ -94,21 +104,30 @@ def test_exact_variants_on_hard_rows(p, variant):
     X = rand_planes(n, p, 52, zero_frac=0.02, emin=-3, emax=3)
     Vr, Xr = recs(V), recs(X)
     # push one entry of some rows down by s bits: spans s + O(10)
-    for r, shift in ((1, 400), (2, 490), (3, 505), (4, 530), (5, 700), (6, 2000),
-                     (8, oracle.SPAN_CAP + 50)):
-        if rowptr[r + 1] > rowptr[r]:
-            k = rowptr[r]
-            Vr[k, 0] = np.int64(Vr[k, 0].view(np.int64) - 2 * shift).view(np.uint64)
-    # row 9: a, -a against equal x values -> exact cancellation (+0)
-    if rowptr[10] - rowptr[9] >= 2:
-        k = rowptr[9]
-        Xr[colidx[k + 1]] = Xr[colidx[k]]
-        Vr[k + 1] = Vr[k]
-        Vr[k + 1, 0] ^= np.uint64(1)
-        Vr[k + 2:rowptr[10]] = 0  # the rest of the row: stored zeros
-        Vr[k + 2:rowptr[10], 0] = np.uint64((oracle.EXP_ZERO * 2) & ((1 << 64) - 1))
+    zero_head = np.uint64((oracle.EXP_ZERO * 2) & ((1 << 64) - 1))
+
+    def nonzeros(r):
+        return [k for k in range(rowptr[r], rowptr[r + 1])
+                if (Vr[k, 0] >> np.uint64(1)) != zero_head >> np.uint64(1)]
+
+    rows = [r for r in range(n) if len(nonzeros(r)) >= 3][:8]
+    assert len(rows) == 8
+    # push one entry of a row down by s bits: spans s + O(10) around the
+    # per-thread window (512 bits), and one beyond the span cap
+    for r, shift in zip(rows, (400, 490, 505, 530, 700, 2000, oracle.SPAN_CAP + 50)):
+        k = nonzeros(r)[0]
+        Vr[k, 0] = np.int64(Vr[k, 0].view(np.int64) - 2 * shift).view(np.uint64)
+    # last row: a, -a against equal x values, the rest stored zeros -> +0
+    r = rows[7]
+    k = rowptr[r]
+    Xr[colidx[k + 1]] = Xr[colidx[k]]
+    Vr[k] = Vr[nonzeros(r)[0]]
+    Vr[k + 1] = Vr[k]
+    Vr[k + 1, 0] ^= np.uint64(1)
+    Vr[k + 2:rowptr[r + 1]] = 0
+    Vr[k + 2:rowptr[r + 1], 0] = zero_head
     A = mpk.CSR(rowptr, colidx, synth.records_to_planes(Vr), p, transpose=True)
-    A.set_config("exact", 128, variant)
+    A.set_config("exact", 128, variant, 50)
     x = mpk.Vec.from_planes(synth.records_to_planes(Xr), p)
     want, st = oracle.spmv(p, oracle.EXACT, rowptr, colidx, Vr, Xr)
     assert st == oracle.ERR_SPAN
@@ -156,5 +175,5 @@ def test_ordered_products_round_ties_to_even(p):
     x = mpk.Vec.from_planes(X, p)
     want, _ = oracle.spmv(p, oracle.ORDERED, rowptr, colidx, recs(V), recs(X))
     for v in (0, 2):
-        A.set_config("ordered", 128, v)
+        A.set_config("ordered", 128, v, -1)
         assert_bitwise(mpk.spmv(A, x, mode="ordered").planes(), want, f"ties variant={v} p={p}")
