@@ -149,13 +149,15 @@ __global__ void __launch_bounds__(kBT) bdot_span_kernel(const BDot a, const Seg 
   }
 }
 
+// smem: per thread FAST 64-bit counters, digit-major ([FAST][threads]).
 template <int W>
-__host__ __device__ constexpr size_t bdot_smem(int k) {
-  return (size_t)kBW * 32 * (2 * W + 1) * 4 + (size_t)kBW * 32 * 8 +
-         (size_t)k * kBW * BWin<W>::fast * 8;
+__host__ __device__ constexpr size_t bdot_smem(int) {
+  return (size_t)BWin<W>::fast * kBT * 8;
 }
 
-// Warp-staged exact accumulation of one block's elements (one instance).
+// Exact accumulation of one block's elements (one instance): each thread adds
+// its pairs' products into its own counter window, then the block sums the
+// windows digit by digit into the block's partial.
 template <int W>
 __global__ void __launch_bounds__(kBT) bdot_accum_kernel(const BDot a, const Seg g, BScr s,
                                                          const int* done) {
@@ -163,69 +165,37 @@ __global__ void __launch_bounds__(kBT) bdot_accum_kernel(const BDot a, const Seg
   const int b = blockIdx.x;
   const int inst = g.blk_inst[b];
   if (done[inst]) return;
-  constexpr int NDIG = 2 * W + 1;
-  constexpr int FAST = BWin<W>::fast;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int64_t* acc = dsm;
-  int32_t* sbase = (int32_t*)(dsm + (size_t)a.k * kBW * FAST);
-  int32_t* ssign = sbase + kBW * 32;
-  uint32_t* stage = (uint32_t*)(ssign + kBW * 32);
-  int32_t* mybase = sbase + warp * 32;
-  int32_t* mysign = ssign + warp * 32;
-  uint32_t* mystage = stage + (size_t)warp * 32 * NDIG;
+  int64_t* c = dsm + threadIdx.x;
   const int64_t lo = g.blk_lo[b], hi = g.blk_hi[b];
   for (int j = 0; j < a.k; ++j) {
     const long long elo = s.emin[(size_t)j * g.K + inst], ehi = s.emax[(size_t)j * g.K + inst];
-    const bool fast = elo <= ehi && (ehi - elo) <= kBFast;
-    if (!fast) continue;  // block-uniform
-    int64_t* aw = acc + ((size_t)j * kBW + warp) * FAST;
-    for (int d = lane; d < FAST; d += 32) aw[d] = 0;
-    __syncwarp();
-    for (int64_t i0 = lo + warp * 32; i0 < hi; i0 += blockDim.x) {
-      const int64_t i = i0 + lane;
-      int32_t base = -1;
-      uint32_t sg = 0;
-      if (i < hi) {
-        Num<W> x, y;
-        load<W>(x, a.x[j], a.ld, i);
-        load<W>(y, a.y[j], a.ld, i);
-        if (!zero_e(x.e) && !zero_e(y.e)) {
-          uint32_t P[2 * W], D[NDIG];
-          mul_full<W>(x.m, y.m, P);
-          const int64_t off = x.e + y.e - elo;
-          shifted_digits<W>(P, (uint32_t)(off & 31), D);
-#pragma unroll
-          for (int k = 0; k < NDIG; ++k) mystage[lane * NDIG + k] = D[k];
-          base = (int32_t)(off >> 5);
-          sg = x.s ^ y.s;
-        }
-      }
-      mybase[lane] = base;
-      mysign[lane] = (int32_t)sg;
-      __syncwarp();
-      for (int src = 0; src < 32; ++src) {
-        const int32_t bb = mybase[src];
-        if (bb < 0) continue;
-        const bool ng = mysign[src] != 0;
-        for (int k = lane; k < NDIG; k += 32) {
-          const int64_t v = (int64_t)mystage[src * NDIG + k];
-          aw[bb + k] += ng ? -v : v;
-        }
-      }
-      __syncwarp();
-    }
-  }
-  __syncthreads();
-  for (int j = 0; j < a.k; ++j) {
-    const long long elo = s.emin[(size_t)j * g.K + inst], ehi = s.emax[(size_t)j * g.K + inst];
-    if (!(elo <= ehi && (ehi - elo) <= kBFast)) continue;
+    if (!(elo <= ehi && (ehi - elo) <= kBFast)) continue;  // block-uniform
     const int nd = bdigits(ehi - elo, W);
-    int64_t* part = s.partials + ((size_t)j * g.nblk + b) * BWin<W>::cap;
-    for (int d = threadIdx.x; d < nd; d += blockDim.x) {
-      int64_t t = 0;
-      for (int w = 0; w < kBW; ++w) t += acc[((size_t)j * kBW + w) * FAST + d];
-      part[d] = t;
+    for (int d = 0; d < nd; ++d) c[d * kBT] = 0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += kBT) {
+      Num<W> x, y;
+      load<W>(x, a.x[j], a.ld, i);
+      load<W>(y, a.y[j], a.ld, i);
+      if (zero_e(x.e) || zero_e(y.e)) continue;
+      uint32_t P[2 * W];
+      if (W >= 16)
+        mul_full_ilp<W>(x.m, y.m, P);
+      else
+        mul_full<W>(x.m, y.m, P);
+      add_term<W>(c, kBT, P, x.e + y.e - elo, x.s ^ y.s);
     }
+    __syncthreads();
+    int64_t* part = s.partials + ((size_t)j * g.nblk + b) * BWin<W>::cap;
+    for (int d = warp; d < nd; d += kBW) {
+      int64_t t = 0;
+#pragma unroll
+      for (int u = 0; u < kBT / 32; ++u) t += dsm[d * kBT + u * 32 + lane];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) part[d] = t;
+    }
+    __syncthreads();
   }
 }
 
@@ -637,6 +607,8 @@ mp_status bdots(const BWork& w, const Seg& g, int k, const uint64_t* const* xs,
   const size_t smem = bdot_smem<W>(k);
   MPK_CUDA(cudaFuncSetAttribute(bdot_accum_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem));
+  MPK_CUDA(cudaFuncSetAttribute(bdot_accum_kernel<W>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared));
   bdot_span_kernel<W><<<g.nblk, kBT, 0, st>>>(a, g, s, done);
   bdot_accum_kernel<W><<<g.nblk, kBT, smem, st>>>(a, g, s, done);
   bdot_wide_kernel<W><<<g.nblk, 256, 0, st>>>(a, g, s, done);

@@ -3,13 +3,15 @@
 // Exact dot products (the inner products of Fig. 5) take three kernels:
 //  1. span: min/max of e_x + e_y over the nonzero pairs (warp reduction, one
 //     64-bit atomicMin/atomicMax per warp: min and max are order-free);
-//  2. accumulate: each lane forms the exact 2p-bit product of its pair,
-//     shifts it onto the 32-bit digit grid anchored at Emin and stages the
-//     2W+1 digits in shared memory; the warp then adds the 32 staged
-//     products digit-parallel into 64-bit signed counters (no atomics, no
-//     carries, no bank conflicts); blocks write their counters as partials;
-//  3. finalize: one block per dot sums the partials per digit (integer sums:
-//     any order gives the same bits), resolves carries and rounds once.
+//  2. accumulate: each thread adds the exact 2p-bit products of its pairs,
+//     shifted onto the 32-bit digit grid anchored at Emin, into its own
+//     window of 64-bit signed counters in shared memory (digit-major, so a
+//     warp's accesses hit 32 banks; no atomics, no carries); the block then
+//     sums its threads' windows digit by digit into one partial per block,
+//     stored digit-major across blocks;
+//  3. finalize: one block per dot sums the partials per digit (a warp per
+//     digit, lanes over blocks; integer sums: any order gives the same
+//     bits), resolves carries and rounds once.
 // A dot whose span exceeds the per-warp window takes a wide variant of step 2
 // with a window of the full span cap.  Up to five dots over the same index
 // range run in one pass, so GPBiCG's mu_1..mu_5 read y, v and t once.
@@ -49,7 +51,7 @@ struct DotDev {
 struct DotScratch {
   long long* emin;  // [5]
   long long* emax;  // [5]
-  int64_t* partials;  // [5][nblocks][cap]
+  int64_t* partials;  // [5][cap][nblocks]: digit-major per dot
   int nblocks;
 };
 
@@ -98,12 +100,16 @@ __global__ void __launch_bounds__(kDotThreads) dot_span_kernel(const DotDev a, l
   }
 }
 
-// smem: [warps][32][2W+1] u32 staged digits, [warps][32] staged bases,
-// [warps][32] staged signs, then [k][warps][fast] int64 counters.
+// smem: per thread FAST 64-bit counters, digit-major ([FAST][threads]).
 template <int W>
-__host__ __device__ constexpr size_t dot_smem(int k) {
-  return (size_t)kDotWarps * 32 * (2 * W + 1) * 4 + (size_t)kDotWarps * 32 * 8 +
-         (size_t)k * kDotWarps * DotWin<W>::fast * 8;
+__host__ __device__ constexpr size_t dot_smem(int) {
+  return (size_t)DotWin<W>::fast * kDotThreads * 8;
+}
+
+__device__ __forceinline__ int64_t warp_sum64(int64_t t) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  return t;
 }
 
 template <int W>
@@ -111,76 +117,37 @@ __global__ void __launch_bounds__(kDotThreads) dot_accum_kernel(const DotDev a, 
                                                                 const int* __restrict__ gate) {
   extern __shared__ int64_t dsm[];
   if (gate && *gate) return;
-  constexpr int NDIG = 2 * W + 1;
-  constexpr int FAST = DotWin<W>::fast;
+  constexpr int CAP = DotWin<W>::cap;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int64_t* acc = dsm;                                           // [k][warps][FAST]
-  int32_t* sbase = (int32_t*)(dsm + (size_t)a.k * kDotWarps * FAST);  // [warps][32]
-  int32_t* ssign = sbase + kDotWarps * 32;                      // [warps][32]
-  uint32_t* stage = (uint32_t*)(ssign + kDotWarps * 32);        // [warps][32][NDIG]
-  int32_t* mybase = sbase + warp * 32;
-  int32_t* mysign = ssign + warp * 32;
-  uint32_t* mystage = stage + (size_t)warp * 32 * NDIG;
-
-  int64_t lo[5];
-  bool fast[5];
+  int64_t* c = dsm + threadIdx.x;
   for (int j = 0; j < a.k; ++j) {
-    lo[j] = s.emin[j];
-    const long long hi = s.emax[j];
-    fast[j] = lo[j] <= hi && (hi - lo[j]) <= kDotFastSpan;
-    int64_t* aj = acc + ((size_t)j * kDotWarps + warp) * FAST;
-    for (int d = lane; d < FAST; d += 32) aj[d] = 0;
-  }
-  __syncwarp();
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t start = (int64_t)blockIdx.x * blockDim.x + warp * 32;
-  for (int64_t i0 = start; i0 < a.n; i0 += stride) {
-    const int64_t i = i0 + lane;
-    for (int j = 0; j < a.k; ++j) {
-      if (!fast[j]) continue;  // warp-uniform
-      int32_t base = -1;
-      uint32_t sg = 0;
-      if (i < a.n) {
-        Num<W> x, y;
-        load<W>(x, a.x[j], a.ldx[j], i);
-        load<W>(y, a.y[j], a.ldy[j], i);
-        if (!zero_e(x.e) && !zero_e(y.e)) {
-          uint32_t P[2 * W], D[NDIG];
-          mul_full<W>(x.m, y.m, P);
-          const int64_t off = x.e + y.e - lo[j];
-          shifted_digits<W>(P, (uint32_t)(off & 31), D);
-#pragma unroll
-          for (int k = 0; k < NDIG; ++k) mystage[lane * NDIG + k] = D[k];
-          base = (int32_t)(off >> 5);
-          sg = x.s ^ y.s;
-        }
-      }
-      mybase[lane] = base;
-      mysign[lane] = (int32_t)sg;
-      __syncwarp();
-      int64_t* aj = acc + ((size_t)j * kDotWarps + warp) * FAST;
-      for (int src = 0; src < 32; ++src) {
-        const int32_t b = mybase[src];
-        if (b < 0) continue;
-        const bool ng = mysign[src] != 0;
-        for (int k = lane; k < NDIG; k += 32) {
-          const int64_t v = (int64_t)mystage[src * NDIG + k];
-          aj[b + k] += ng ? -v : v;
-        }
-      }
-      __syncwarp();
+    const long long lo = s.emin[j], hi = s.emax[j];
+    if (!(lo <= hi && hi - lo <= kDotFastSpan)) continue;  // block-uniform
+    const int nd = dot_digits(hi - lo, W);
+    for (int d = 0; d < nd; ++d) c[d * kDotThreads] = 0;
+    for (int64_t i = blockIdx.x * (int64_t)kDotThreads + threadIdx.x; i < a.n;
+         i += (int64_t)gridDim.x * kDotThreads) {
+      Num<W> x, y;
+      load<W>(x, a.x[j], a.ldx[j], i);
+      load<W>(y, a.y[j], a.ldy[j], i);
+      if (zero_e(x.e) || zero_e(y.e)) continue;
+      uint32_t P[2 * W];
+      if (W >= 16)
+        mul_full_ilp<W>(x.m, y.m, P);
+      else
+        mul_full<W>(x.m, y.m, P);
+      add_term<W>(c, kDotThreads, P, x.e + y.e - lo, x.s ^ y.s);
     }
-  }
-  __syncthreads();
-  for (int j = 0; j < a.k; ++j) {
-    if (!fast[j]) continue;
-    const int nd = dot_digits(s.emax[j] - lo[j], W);
-    int64_t* part = s.partials + ((size_t)j * s.nblocks + blockIdx.x) * DotWin<W>::cap;
-    for (int d = threadIdx.x; d < nd; d += blockDim.x) {
+    __syncthreads();
+    int64_t* part = s.partials + (size_t)j * CAP * s.nblocks;
+    for (int d = warp; d < nd; d += kDotWarps) {
       int64_t t = 0;
-      for (int w = 0; w < kDotWarps; ++w) t += acc[((size_t)j * kDotWarps + w) * FAST + d];
-      part[d] = t;
+#pragma unroll
+      for (int u = 0; u < kDotThreads / 32; ++u) t += dsm[d * kDotThreads + u * 32 + lane];
+      t = warp_sum64(t);
+      if (lane == 0) part[(size_t)d * s.nblocks + blockIdx.x] = t;
     }
+    __syncthreads();
   }
 }
 
@@ -214,8 +181,8 @@ __global__ void __launch_bounds__(256) dot_accum_wide_kernel(const DotDev a, Dot
       }
     }
     __syncthreads();
-    int64_t* part = s.partials + ((size_t)j * s.nblocks + blockIdx.x) * DotWin<W>::cap;
-    for (int d = threadIdx.x; d < nd; d += blockDim.x) part[d] = acc[d];
+    int64_t* part = s.partials + (size_t)j * DotWin<W>::cap * s.nblocks;
+    for (int d = threadIdx.x; d < nd; d += blockDim.x) part[(size_t)d * s.nblocks + blockIdx.x] = acc[d];
     __syncthreads();
   }
 }
@@ -234,11 +201,13 @@ __global__ void __launch_bounds__(256) dot_finalize_kernel(const DotDev a, DotSc
   set_zero(r, 0u);
   if (lo <= hi && hi - lo <= SPAN_CAP) {
     const int nd = dot_digits(hi - lo, W);
-    const int64_t* part = s.partials + (size_t)j * s.nblocks * DotWin<W>::cap;
-    for (int d = threadIdx.x; d < nd; d += blockDim.x) {
+    const int64_t* part = s.partials + (size_t)j * DotWin<W>::cap * s.nblocks;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int d = warp; d < nd; d += nwarps) {
       int64_t t = 0;
-      for (int b = 0; b < s.nblocks; ++b) t += part[(size_t)b * DotWin<W>::cap + d];
-      sum[d] = t;
+      for (int b = lane; b < s.nblocks; b += 32) t += part[(size_t)d * s.nblocks + b];
+      t = warp_sum64(t);
+      if (lane == 0) sum[d] = t;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -286,6 +255,9 @@ mp_status dot_w(const DotArgs& args, void* scratch, const int* gate, cudaStream_
   const size_t smem = dot_smem<W>(a.k);
   MPK_CUDA(cudaFuncSetAttribute(dot_accum_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem));
+  // streamed operands: shared memory for the windows matters more than L1
+  MPK_CUDA(cudaFuncSetAttribute(dot_accum_kernel<W>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared));
   dot_span_kernel<W><<<s.nblocks, kDotThreads, 0, st>>>(a, s.emin, s.emax, gate);
   dot_accum_kernel<W><<<s.nblocks, kDotThreads, smem, st>>>(a, s, gate);
   dot_accum_wide_kernel<W><<<s.nblocks, 256, 0, st>>>(a, s, gate);

@@ -181,32 +181,6 @@ __global__ void __launch_bounds__(256) spmv_ordered_kernel(
 // EXACT (and the residual r = RN(b - A x))
 // ---------------------------------------------------------------------------
 
-// Adds (-1)^neg * P * 2^off into counters c[d*stride].
-template <int W>
-__device__ __forceinline__ void add_term(int64_t* c, int stride, const uint32_t (&P)[2 * W],
-                                         int64_t off, uint32_t neg) {
-  uint32_t D[2 * W + 1];
-  shifted_digits<W>(P, (uint32_t)(off & 31), D);
-  int64_t* p = c + (off >> 5) * stride;
-  // G digits at a time: loads together, then stores together (one
-  // shared-memory latency per group instead of one per digit)
-  constexpr int G = 2 * W + 1 < 12 ? 2 * W + 1 : 12;
-#pragma unroll
-  for (int k0 = 0; k0 <= 2 * W; k0 += G) {
-    int64_t v[G];
-#pragma unroll
-    for (int u = 0; u < G; ++u)
-      if (k0 + u <= 2 * W) v[u] = p[(k0 + u) * stride];
-#pragma unroll
-    for (int u = 0; u < G; ++u) {
-      if (k0 + u <= 2 * W) {
-        const int64_t d = (int64_t)D[k0 + u];
-        p[(k0 + u) * stride] = v[u] + (neg ? -d : d);
-      }
-    }
-  }
-}
-
 template <int W>
 __device__ __forceinline__ void value_as_product(const Num<W>& b, uint32_t (&P)[2 * W]) {
 #pragma unroll
