@@ -41,13 +41,14 @@ __host__ __device__ inline int digits_cols(int64_t span, int W) {
 // Launch variants (a bit field): bit 0 = the row loop stages the next
 // entry's operands (ORDERED: p <= 512 only; EXACT: column form only, word
 // form stages at p <= 512), bit 1 = products from radix-2^29 column sums,
-// bit 2 = EXACT column sums computed 16 columns at a time instead of 8.
+// bit 2 = EXACT: column sums computed 16 columns at a time instead of 8;
+// ORDERED: the register-capped kernel (three blocks of <= 128 threads per SM).
 constexpr int kVarStage = 1, kVarCols = 2, kVarWide = 4;
 // A matrix's launch configuration for one mode with the library's defaults
 // filled in (chosen from measurements of the n = 10^6 sweep on GB300: the
 // word form with a half-and-half L1/shared split for EXACT at p <= 512, the
 // column form with 256 threads at p = 1024; column products for ORDERED from
-// p = 256 on).
+// p = 256 on, register-capped blocks at p = 128 and 1024).
 struct LaunchCfg {
   int tpb;
   bool stage, cols, wide;
@@ -60,8 +61,9 @@ LaunchCfg launch_cfg(const mp_csr_s* M, int mode, int W) {
   if (mode == MP_ORDERED) {
     c.cols = v < 0 ? W >= 8 : (v & kVarCols) != 0;
     c.stage = W <= 16 && (v < 0 || (v & kVarStage));
-    c.wide = false;
     c.tpb = M->cfg_tpb[0] < 0 ? 128 : M->cfg_tpb[0];
+    // register-capped kernel (the default at p = 128 and p = 1024)
+    c.wide = (v < 0 ? (W == 4 || W == 32) : (v & kVarWide) != 0) && c.tpb <= 128;
     c.carve = M->cfg_carve[0];
   } else {
     c.cols = v < 0 ? W >= 32 : (v & kVarCols) != 0;
@@ -114,9 +116,9 @@ struct Pipelined {
 // ---------------------------------------------------------------------------
 
 template <int W, bool PIPE, bool COLS>
-__global__ void __launch_bounds__(256) spmv_ordered_kernel(
-    const SellView S, const uint64_t* __restrict__ x, int64_t ldx, uint64_t* __restrict__ y,
-    int64_t ldy, const int* __restrict__ gate) {
+__device__ __forceinline__ void ordered_rows(const SellView& S, const uint64_t* __restrict__ x,
+                                             int64_t ldx, uint64_t* __restrict__ y, int64_t ldy,
+                                             const int* __restrict__ gate) {
   if (gate && *gate) return;
   const int lane = threadIdx.x & 31;
   const int64_t chunk = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -175,6 +177,23 @@ __global__ void __launch_bounds__(256) spmv_ordered_kernel(
     }
   }
   if (row >= 0) store<W>(acc, y, ldy, row);
+}
+
+template <int W, bool PIPE, bool COLS>
+__global__ void __launch_bounds__(256) spmv_ordered_kernel(
+    const SellView S, const uint64_t* __restrict__ x, int64_t ldx, uint64_t* __restrict__ y,
+    int64_t ldy, const int* __restrict__ gate) {
+  ordered_rows<W, PIPE, COLS>(S, x, ldx, y, ldy, gate);
+}
+
+// The same with at most 128 threads per block and registers capped so that
+// three such blocks fit on an SM: more warps to hide the multiply latency
+// where the uncapped kernel is held to two blocks by its registers.
+template <int W, bool PIPE, bool COLS>
+__global__ void __launch_bounds__(128, 3) spmv_ordered_kernel_capped(
+    const SellView S, const uint64_t* __restrict__ x, int64_t ldx, uint64_t* __restrict__ y,
+    int64_t ldy, const int* __restrict__ gate) {
+  ordered_rows<W, PIPE, COLS>(S, x, ldx, y, ldy, gate);
 }
 
 // ---------------------------------------------------------------------------
@@ -461,14 +480,24 @@ mp_status spmv_w(const mp_csr_s* M, const Sell& S, int mode, const uint64_t* x, 
       return MP_OK;
     };
     mp_status r;
-    if (cf.stage && cf.cols)
+    if (cf.wide && tpb <= 128) {
+      if (cf.stage && cf.cols)
+        r = ordered(spmv_ordered_kernel_capped<W, P, true>);
+      else if (cf.stage)
+        r = ordered(spmv_ordered_kernel_capped<W, P, false>);
+      else if (cf.cols)
+        r = ordered(spmv_ordered_kernel_capped<W, false, true>);
+      else
+        r = ordered(spmv_ordered_kernel_capped<W, false, false>);
+    } else if (cf.stage && cf.cols) {
       r = ordered(spmv_ordered_kernel<W, P, true>);
-    else if (cf.stage)
+    } else if (cf.stage) {
       r = ordered(spmv_ordered_kernel<W, P, false>);
-    else if (cf.cols)
+    } else if (cf.cols) {
       r = ordered(spmv_ordered_kernel<W, false, true>);
-    else
+    } else {
       r = ordered(spmv_ordered_kernel<W, false, false>);
+    }
     if (r != MP_OK) return r;
     count_launch();
     return launch_check("spmv_ordered_kernel");
@@ -626,6 +655,8 @@ mp_status mp_csr_tune(mp_csr A, int32_t mode, int32_t reps, int32_t* tpb_out, in
   if (mode == MP_ORDERED) {
     for (int32_t v = 0; v <= (kVarCols | kVarStage); v += (A->prec > 512 ? kVarCols : 1))
       vars[nvar++] = v;
+    // the register-capped form of the default product form
+    vars[nvar++] = kVarWide | (A->prec >= 256 ? kVarCols : 0) | (A->prec <= 512 ? kVarStage : 0);
   } else {
     vars[nvar++] = 0;
     for (int32_t v : {kVarCols, kVarCols | kVarStage, kVarCols | kVarWide,

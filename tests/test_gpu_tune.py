@@ -38,7 +38,8 @@ def test_every_configuration_matches_the_oracle(p):
                 if v >= 0:
                     assert got["variant"] & 2 == v & 2  # the product form asked for
                     if name == "ordered":
-                        assert got["variant"] == (v & 3 if p <= 512 else v & 2)
+                        capped = 4 if (v & 4 and (tpb if tpb > 0 else 128) <= 128) else 0
+                        assert got["variant"] == (v & 3 if p <= 512 else v & 2) | capped
                     elif v & 2:
                         assert got["variant"] == v
                 what = f"{name} p={p} tpb={tpb} variant={v} carveout={carve}"
@@ -54,7 +55,7 @@ def test_bad_configuration_is_rejected():
                  ("exact", 64, -2, -1), ("exact", 64, 0, 101)):
         with pytest.raises(mpk.MPError):
             A.set_config(*args)
-    assert A.get_config("ordered") == {"threads_per_block": 128, "variant": 1, "carveout": -1}
+    assert A.get_config("ordered") == {"threads_per_block": 128, "variant": 5, "carveout": -1}
     assert A.get_config("exact") == {"threads_per_block": 128, "variant": 1, "carveout": 50}
 
 
@@ -76,7 +77,7 @@ def test_tuner_and_cache(p, tmp_path):
         assert not r["cached"] and r["ms"] > 0
         assert r["threads_per_block"] in (32, 64, 128, 256)
         assert A.get_config(name)["threads_per_block"] == r["threads_per_block"]
-        allowed = {"ordered": (0, 1, 2, 3) if p <= 512 else (0, 2),
+        allowed = {"ordered": ((0, 1, 2, 3, 5, 7) if p <= 512 else (0, 2, 6)),
                    "exact": (1 if p <= 512 else 0, 2, 3, 6, 7)}[name]
         assert r["variant"] in allowed
         want, _ = oracle.spmv(p, m, rowptr, colidx, recs(V), recs(X))
