@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default launch configuration instead of autotuning it")
-    ap.add_argument("--batch-systems", type=int, default=64,
+    ap.add_argument("--batch-systems", type=int, default=256,
                     help="systems of the batched-solve workload to run (256 = all)")
     return ap.parse_args()
 
@@ -549,13 +549,20 @@ def autograd_bench(mpk, m=256, p=256):
             "two_plain_solves_ms": p1["ms"] + p2["ms"]}
 
 
-def batch_bench(mpk, count=64, rtol=1e-25):
+def batch_bench(mpk, count=256, rtol=1e-25):
     """The first `count` systems of the batched workload (seed 3): for each
     precision group, one batched GPBiCG solve of all (system, right-hand side)
-    instances against sequential mp_gpbicg solves of the same instances."""
+    instances against sequential mp_gpbicg solves of the same instances.
+    Every system matrix and each group's block-diagonal matrix get their
+    launch configuration from the autotuner first (reported as "tiles")."""
+    import collections
+
     import torch
 
-    from paper_1411_2377_gb300 import synth
+    from paper_1411_2377_gb300 import synth, tune
+
+    def cfg_key(r):
+        return f"tpb{r['threads_per_block']}/v{r['variant']}/c{r['carveout']}"
 
     descs = synth.batch_systems(seed=3, count=256)[:count]
     out = {"workload": f"batch_seed3_{count}_systems", "groups": {}}
@@ -564,15 +571,19 @@ def batch_bench(mpk, count=64, rtol=1e-25):
         if not items:
             continue
         mats, inst, rhs = {}, [], []
+        sys_tiles = collections.Counter()
         for s, d in items:
             rp, ci, va = synth.batch_matrix(d)
             mats[s] = mpk.CSR(rp, ci, va, p)
+            t = tune.autotune(mats[s], modes=("ordered",), reps=2, cache=None)
+            sys_tiles[cfg_key(t["ordered"])] += 1
             n = len(rp) - 1
             for k in range(d["nrhs"]):
                 inst.append((rp, ci, va))
                 rhs.append(mpk.spmv(mats[s], mpk.Vec.from_f64(np.full(n, k + 1.0), p), mode="exact"))
         owners = [s for s, d in items for _ in range(d["nrhs"])]
         B = mpk.Batch(inst, p)
+        bt = tune.autotune(B.matrix(), modes=("ordered",), reps=2, cache=None)["ordered"]
         b = mpk.Vec.zeros(B.n, p)
         for k, bk in enumerate(rhs):
             b.t[:, int(B.offsets[k]):int(B.offsets[k + 1])] = bk.t
@@ -594,7 +605,8 @@ def batch_bench(mpk, count=64, rtol=1e-25):
             "batched_ms": batched_ms, "sequential_ms": seq_ms, "speedup": seq_ms / batched_ms,
             "iters_max": max(its), "iters_mean": sum(its) / len(its),
             "same_iterations_as_single": its == seq_iters,
-            "converged": sum(1 for i in infos if i["status"] == 0)}
+            "converged": sum(1 for i in infos if i["status"] == 0),
+            "tiles": {"batch_matrix": cfg_key(bt), "systems": dict(sys_tiles)}}
         B.close()
         for A in mats.values():
             A.close()

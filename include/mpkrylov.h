@@ -266,6 +266,12 @@ mp_status mp_batch_destroy(mp_batch B);
 /* Number of instances, total length and the k+1 offsets (any may be NULL). */
 mp_status mp_batch_info(mp_batch B, int32_t* k, int64_t* total_n, int64_t* offsets);
 
+/* The batch's block-diagonal matrix, for mp_csr_set_config / mp_csr_tune /
+ * mp_csr_get_config (its launch configuration is the one the batched solve
+ * uses).  The handle is owned by the batch: valid until mp_batch_destroy,
+ * never passed to mp_csr_destroy. */
+mp_status mp_batch_matrix(mp_batch B, mp_csr* out);
+
 /* GPBiCG on every instance at once: one SpMV launch, segmented exact inner
  * products and per-instance scalars per step, one iteration replayed as a
  * CUDA graph until every instance has exited.  Each instance's iterates

@@ -169,6 +169,15 @@ class CSR:
         self.row_hist = np.bincount(np.ceil(np.log2(lens + 1)).astype(np.int64)).tolist() \
             if n > 0 else []
 
+    @classmethod
+    def _borrowed(cls, handle, n, prec, row_hist, owner):
+        """A view of a matrix another object owns (never destroyed here)."""
+        A = cls.__new__(cls)
+        A.h, A.n, A.prec, A.transpose, A.row_hist = handle, n, prec, False, row_hist
+        A._owner = owner
+        A.nnz = A.info()["nnz"]
+        return A
+
     def info(self) -> dict:
         n, nnz, slots, nbytes = (ctypes.c_int64() for _ in range(4))
         p = ctypes.c_int32()
@@ -202,6 +211,9 @@ class CSR:
                 "ms": ms.value}
 
     def close(self):
+        if getattr(self, "_owner", None) is not None:  # borrowed: the owner frees it
+            self.h = None
+            return
         if getattr(self, "h", None) is not None and self.h.value:
             _lib.load().mp_csr_destroy(self.h)
             self.h = None
@@ -329,12 +341,21 @@ class Batch:
         self.h = handle
         self.k = k
         self.prec = prec
+        self._row_hist = np.bincount(np.ceil(np.log2(np.concatenate(
+            [np.diff(np.asarray(r)) for r, _, _ in systems]) + 1)).astype(np.int64)).tolist()
         off = np.zeros(k + 1, dtype=np.int64)
         total = ctypes.c_int64()
         _ok(lib.mp_batch_info(self.h, None, ctypes.byref(total),
                               off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))), "mp_batch_info")
         self.offsets = off
         self.n = int(total.value)
+
+    def matrix(self) -> "CSR":
+        """The batch's block-diagonal matrix (owned by the batch) for
+        set_config / tune; its launch configuration is the batched solve's."""
+        h = ctypes.c_void_p()
+        _ok(_lib.load().mp_batch_matrix(self.h, ctypes.byref(h)), "mp_batch_matrix")
+        return CSR._borrowed(h, self.n, self.prec, self._row_hist, owner=self)
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:

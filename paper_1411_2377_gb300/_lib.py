@@ -77,6 +77,7 @@ SIGNATURES = {
     "mp_batch_create_f64": (_i32, [_i32, _vp, _vp, _vp, _vp, _i32, _vp, ctypes.POINTER(_vp)]),
     "mp_batch_destroy": (_i32, [_vp]),
     "mp_batch_info": (_i32, [_vp, _i32p, _i64p, _i64p]),
+    "mp_batch_matrix": (_i32, [_vp, ctypes.POINTER(_vp)]),
     "mp_batch_gpbicg": (_i32, [_vp, MpVec, MpVec, ctypes.POINTER(MpSolveOpts),
                                ctypes.POINTER(MpSolveInfo), _vp]),
     "mp_refine": (_i32, [_vp, MpVec, MpVec, ctypes.POINTER(MpRefineOpts),

@@ -922,6 +922,12 @@ mp_status mp_batch_info(mp_batch B, int32_t* k, int64_t* total_n, int64_t* offse
   return MP_OK;
 }
 
+mp_status mp_batch_matrix(mp_batch B, mp_csr* out) {
+  if (!B || !out) return set_error(MP_ERR_ARG, "batch or out is null");
+  *out = B->M;
+  return MP_OK;
+}
+
 mp_status mp_batch_gpbicg(mp_batch B, mp_vec b, mp_vec x, const mp_solve_opts* opts,
                           mp_solve_info* infos, void* stream) {
   if (!B) return set_error(MP_ERR_ARG, "batch is null");

@@ -57,3 +57,39 @@ def test_batched_equals_single_solves(p, mode):
         statuses.add(info["status"])
     assert {0, 6} <= statuses  # converged and breakdown instances present
 
+
+
+def test_batch_matrix_configuration_keeps_results():
+    """The batch's block-diagonal matrix takes launch configurations like any
+    matrix (the autotuner included); the batched solve's iterates do not
+    change with them."""
+    mpk = need_gpu()
+    import torch
+
+    from paper_1411_2377_gb300 import tune
+
+    systems, plan = _instances()
+    inst = [systems[i] for i, _ in plan[:4]]
+    p = 256
+    B = mpk.Batch(inst, p)
+    b = mpk.Vec.zeros(B.n, p)
+    for k, (rp, ci, va) in enumerate(inst):
+        A = mpk.CSR(rp, ci, va, p)
+        n = len(rp) - 1
+        bk = mpk.spmv(A, mpk.Vec.from_f64(np.full(n, 1.0 + k), p), mode="exact")
+        b.t[:, int(B.offsets[k]):int(B.offsets[k + 1])] = bk.t
+    x0, i0 = mpk.batch_gpbicg(B, b, rtol=1e-25, maxit=200, mode="ordered")
+    M = B.matrix()
+    assert M.info()["n"] == B.n
+    for cfg in ((64, 0, -1), (256, 3, 50), (128, 6, -1)):
+        M.set_config("ordered", *cfg)
+        x1, i1 = mpk.batch_gpbicg(B, b, rtol=1e-25, maxit=200, mode="ordered")
+        assert [(a["iters"], a["status"]) for a in i1] == [(a["iters"], a["status"]) for a in i0]
+        assert torch.equal(x1.t.cpu(), x0.t.cpu()), cfg
+    r = tune.autotune(M, modes=("ordered",), reps=1, cache=None)["ordered"]
+    assert M.get_config("ordered")["threads_per_block"] == r["threads_per_block"]
+    x2, _ = mpk.batch_gpbicg(B, b, rtol=1e-25, maxit=200, mode="ordered")
+    assert torch.equal(x2.t.cpu(), x0.t.cpu())
+    M.close()  # a borrowed handle: closing it must not free the batch's matrix
+    x3, _ = mpk.batch_gpbicg(B, b, rtol=1e-25, maxit=200, mode="ordered")
+    assert torch.equal(x3.t.cpu(), x0.t.cpu())
