@@ -128,10 +128,17 @@ mp_status mp_csr_info(mp_csr A, int64_t* n, int64_t* nnz, int32_t* prec_bits,
  *     bit 2: MP_EXACT column form: 16 columns computed at a time, not 8;
  *            MP_ORDERED: registers capped for three blocks of at most 128
  *            threads per SM (ignored above 128 threads per block);
+ *     bit 3: x is first copied into records (each element's L+1 words
+ *            contiguous) and gathered from them: one 16-byte load per two
+ *            words instead of one sector per plane.  The copy lives with the
+ *            matrix (n (L+2) 8 bytes, allocated on first use), so products of
+ *            one matrix with this bit must not run concurrently on several
+ *            streams;
  *   carveout: the shared-memory share of the unified L1/shared storage the
  *            kernels ask for, in percent (more digit windows per SM against
  *            more L1 for the gathers of x);
- *   -1 for any of them: the library's default for the precision.
+ *   -1 for any of them: the library's default for the precision (and, for
+ *            bit 3, the size: on from p = 256 when n >= 65536).
  * mp_csr_get_config reports the configuration that runs (defaults resolved;
  * carveout -1 = the driver's choice). */
 mp_status mp_csr_set_config(mp_csr A, int32_t mode, int32_t threads_per_block, int32_t variant,

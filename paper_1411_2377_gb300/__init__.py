@@ -190,7 +190,7 @@ class CSR:
         """SpMV launch configuration for one mode (results do not depend on it).
         variant: bit field, bit 0 = operand staging, bit 1 = products from
         radix-2^29 column sums, bit 2 = EXACT column sums 16 at a time /
-        ORDERED register-capped blocks;
+        ORDERED register-capped blocks, bit 3 = x gathered from a record copy;
         carveout: shared-memory percent of L1/shared; -1 = library default."""
         _ok(_lib.load().mp_csr_set_config(self.h, MODES[mode], int(threads_per_block),
                                           int(variant), int(carveout)), "mp_csr_set_config")

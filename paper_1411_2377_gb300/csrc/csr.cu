@@ -78,6 +78,7 @@ int grid_for(int64_t n, int threads) {
 
 struct HostSell {
   int64_t nslots = 0, nchunks = 0;
+  double gather_sectors = 0.0;  // mean distinct 4-element groups per warp gather
   std::vector<int64_t> chunk_off;
   std::vector<int32_t> row_of, row_len, col;
   std::vector<int64_t> src;  // raw value index per slot, -1 = padding
@@ -138,6 +139,26 @@ void build_sell(int64_t n, const int64_t* rowptr, const int32_t* cols, const int
       }
     }
   }
+  // How scattered the x gathers are: distinct 32-byte groups of four
+  // consecutive elements that a warp's gather of one plane touches (8 when
+  // the 32 lanes read consecutive columns, up to 32), sampled on every
+  // fourth chunk.  Picks the default gather layout.
+  int64_t groups = 0, touched = 0;
+  for (int64_t c = 0; c < h.nchunks; c += 4) {
+    const int64_t len = (h.chunk_off[c + 1] - h.chunk_off[c]) / 32;
+    for (int64_t j = 0; j < len; ++j) {
+      int32_t g[32];
+      int m = 0;
+      for (int t = 0; t < 32; ++t) {
+        if (j < h.row_len[c * 32 + t]) g[m++] = h.col[h.chunk_off[c] + j * 32 + t] >> 2;
+      }
+      if (m == 0) continue;
+      std::sort(g, g + m);
+      touched += std::unique(g, g + m) - g;
+      ++groups;
+    }
+  }
+  h.gather_sectors = groups ? (double)touched / (double)groups : 0.0;
 }
 
 template <class T>
@@ -311,6 +332,7 @@ mp_status create_impl(int64_t n, const int64_t* rowptr, const int32_t* colidx,
 
   HostSell hs;
   build_sell(n, rowptr, cols.data(), srcs.data(), hs);
+  M->gather_sectors = hs.gather_sectors;
   if ((r = upload_sell(hs, n, nnz, L, d_raw, st, M->A, M->bytes)) != MP_OK) return fail(r);
 
   if (flags & MP_CSR_TRANSPOSE) {
@@ -378,6 +400,7 @@ mp_status mp_csr_destroy(mp_csr A) {
   free_sell(A->AT);
   cudaFree(A->ovf);
   cudaFree(A->a64);
+  cudaFree(A->xrec);
   cudaFree(A->rowscale);
   delete A;
   cudaSetDevice(cur);

@@ -46,6 +46,10 @@ struct mp_csr_s {
   int32_t cfg_tpb[2] = {-1, -1};
   int32_t cfg_var[2] = {-1, -1};
   int32_t cfg_carve[2] = {-1, -1};
+  // record copy of x for the gathers (variant bit 3), allocated on first use
+  uint64_t* xrec = nullptr;
+  // mean distinct 32-byte groups a warp's gather of one x plane touches (8..32)
+  double gather_sectors = 0.0;
   // FP64 copy for mixed-precision refinement (built on first use): the
   // row-equilibrated entries 2^-E_i a_ij per slot of A's layout, and 2^-E_i.
   double* a64 = nullptr;

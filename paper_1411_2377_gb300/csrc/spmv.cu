@@ -42,8 +42,9 @@ __host__ __device__ inline int digits_cols(int64_t span, int W) {
 // entry's operands (ORDERED: p <= 512 only; EXACT: column form only, word
 // form stages at p <= 512), bit 1 = products from radix-2^29 column sums,
 // bit 2 = EXACT: column sums computed 16 columns at a time instead of 8;
-// ORDERED: the register-capped kernel (three blocks of <= 128 threads per SM).
-constexpr int kVarStage = 1, kVarCols = 2, kVarWide = 4;
+// ORDERED: the register-capped kernel (three blocks of <= 128 threads per SM);
+// bit 3 = x gathered from a record copy made before the product.
+constexpr int kVarStage = 1, kVarCols = 2, kVarWide = 4, kVarRec = 8;
 // A matrix's launch configuration for one mode with the library's defaults
 // filled in (chosen from measurements of the n = 10^6 sweep on GB300: the
 // word form with a half-and-half L1/shared split for EXACT at p <= 512, the
@@ -51,13 +52,18 @@ constexpr int kVarStage = 1, kVarCols = 2, kVarWide = 4;
 // p = 256 on, register-capped blocks at p = 128 and 1024).
 struct LaunchCfg {
   int tpb;
-  bool stage, cols, wide;
+  bool stage, cols, wide, rec;
   int carve;  // -1: the driver's choice
 };
 
 LaunchCfg launch_cfg(const mp_csr_s* M, int mode, int W) {
   const int v = M->cfg_var[mode];
   LaunchCfg c;
+  // record copy of x: worth its extra pass over x from p = 256 on when the
+  // gathers are scattered (a stencil's consecutive columns are not) and n is
+  // large enough for the pass to pay
+  c.rec = v < 0 ? (W >= 8 && M->n >= (int64_t(1) << 16) && M->gather_sectors > 16.0)
+                : (v & kVarRec) != 0;
   if (mode == MP_ORDERED) {
     c.cols = v < 0 ? W >= 8 : (v & kVarCols) != 0;
     c.stage = W <= 16 && (v < 0 || (v & kVarStage));
@@ -89,11 +95,66 @@ struct SellView {
   // optional: rows whose instance is marked done are skipped (batched solves)
   const int32_t* __restrict__ rinst;
   const int* __restrict__ idone;
+  // optional: x as records (element i's L+1 words at xrec + i * xrs, xrs even,
+  // 16-byte aligned) for gathers of whole elements instead of one word per plane
+  const uint64_t* __restrict__ xrec;
+  int xrs;
 };
 
 SellView view(const Sell& S, const int32_t* rinst = nullptr, const int* idone = nullptr) {
   return SellView{S.nchunks, S.nslots, S.chunk_off, S.row_of, S.row_len, S.col, S.val,
-                  rinst, idone};
+                  rinst, idone, nullptr, 0};
+}
+
+// Record stride (64-bit words) of a p-bit element: L+1 rounded up to even.
+inline int record_words(int W) { return ((W / 2 + 1) + 1) & ~1; }
+
+// x[c] gathered from the record copy when there is one, else from the planes.
+template <int W>
+__device__ __forceinline__ void gather_x(Num<W>& v, const SellView& S, const uint64_t* __restrict__ x,
+                                         int64_t ldx, int32_t c) {
+  if (S.xrec) {
+    constexpr int L = W / 2;
+    const uint4* r = reinterpret_cast<const uint4*>(S.xrec + (int64_t)c * S.xrs);
+    uint32_t w[2 * ((L + 2) / 2) * 2];
+#pragma unroll
+    for (int k = 0; k < (L + 2) / 2; ++k) {
+      const uint4 q = __ldg(r + k);
+      w[4 * k] = q.x;
+      w[4 * k + 1] = q.y;
+      w[4 * k + 2] = q.z;
+      w[4 * k + 3] = q.w;
+    }
+    unpack_head(((uint64_t)w[1] << 32) | w[0], v.e, v.s);
+#pragma unroll
+    for (int k = 0; k < W; ++k) v.m[k] = w[2 + k];
+  } else {
+    load<W>(v, x, ldx, c);
+  }
+}
+
+__device__ __forceinline__ uint64_t gather_head(const SellView& S, const uint64_t* __restrict__ x,
+                                                int32_t c) {
+  return S.xrec ? __ldg(S.xrec + (int64_t)c * S.xrs) : __ldg(x + c);
+}
+
+// Record copy of x for the gathers (one thread per element).
+template <int W>
+__global__ void to_records_kernel(const uint64_t* __restrict__ x, int64_t ldx, int64_t n,
+                                  uint64_t* __restrict__ xr, int rs) {
+  constexpr int L = W / 2;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t w[(L + 2) / 2 * 2];
+#pragma unroll
+    for (int k = 0; k <= L; ++k) w[k] = __ldg(x + (int64_t)k * ldx + i);
+    if ((L + 1) & 1) w[L + 1] = 0u;
+    uint4* r = reinterpret_cast<uint4*>(xr + i * rs);
+#pragma unroll
+    for (int k = 0; k < (L + 2) / 2; ++k)
+      r[k] = make_uint4((uint32_t)w[2 * k], (uint32_t)(w[2 * k] >> 32), (uint32_t)w[2 * k + 1],
+                        (uint32_t)(w[2 * k + 1] >> 32));
+  }
 }
 
 __device__ __forceinline__ bool row_skipped(const SellView& S, int32_t row) {
@@ -139,7 +200,7 @@ __device__ __forceinline__ void ordered_rows(const SellView& S, const uint64_t* 
       const int32_t c0 = S.col[base];
       if (len > 1) c1 = S.col[base + 32];
       load<W>(an, S.val, S.nslots, base);
-      load<W>(xn, x, ldx, c0);
+      gather_x<W>(xn, S, x, ldx, c0);
     }
     for (int32_t j = 0; j < len; ++j) {
       const Num<W> a = an, xv = xn;
@@ -148,7 +209,7 @@ __device__ __forceinline__ void ordered_rows(const SellView& S, const uint64_t* 
         const int32_t c = c1;
         if (j + 2 < len) c1 = S.col[k1 + 32];
         load<W>(an, S.val, S.nslots, k1);
-        load<W>(xn, x, ldx, c);
+        gather_x<W>(xn, S, x, ldx, c);
       }
       if (zero_e(a.e) || zero_e(xv.e)) continue;  // zero fast path
       Num<W> t, s;
@@ -165,7 +226,7 @@ __device__ __forceinline__ void ordered_rows(const SellView& S, const uint64_t* 
       const int32_t c = S.col[k];
       Num<W> a, xv;
       load<W>(a, S.val, S.nslots, k);
-      load<W>(xv, x, ldx, c);
+      gather_x<W>(xv, S, x, ldx, c);
       if (zero_e(a.e) || zero_e(xv.e)) continue;  // zero fast path
       Num<W> t, s;
       if (COLS)
@@ -243,7 +304,7 @@ __global__ void __launch_bounds__(256) spmv_exact_kernel(
       ha[u] = (j0 + u < len) ? __ldg(S.val + k) : pack_head(EXP_ZERO, 0u);
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) hx[u] = __ldg(x + cc[u]);
+    for (int u = 0; u < 4; ++u) hx[u] = gather_head(S, x, cc[u]);
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       int64_t ea, ex;
@@ -310,7 +371,7 @@ __global__ void __launch_bounds__(256) spmv_exact_kernel(
       const int32_t c0 = S.col[base];
       if (len > 1) c1 = S.col[base + 32];
       load<W>(an, S.val, S.nslots, base);
-      load<W>(xn, x, ldx, c0);
+      gather_x<W>(xn, S, x, ldx, c0);
     }
     for (int32_t j = 0; j < len; ++j) {
       const Num<W> a = an, xv = xn;
@@ -319,7 +380,7 @@ __global__ void __launch_bounds__(256) spmv_exact_kernel(
         const int32_t cn = c1;
         if (j + 2 < len) c1 = S.col[k1 + 32];
         load<W>(an, S.val, S.nslots, k1);
-        load<W>(xn, x, ldx, cn);
+        gather_x<W>(xn, S, x, ldx, cn);
       }
       if (zero_e(a.e) || zero_e(xv.e)) continue;
       term(a, xv, a.s ^ xv.s ^ (RESID ? 1u : 0u));
@@ -330,7 +391,7 @@ __global__ void __launch_bounds__(256) spmv_exact_kernel(
       const int32_t col = S.col[k];
       Num<W> a, xv;
       load<W>(a, S.val, S.nslots, k);
-      load<W>(xv, x, ldx, col);
+      gather_x<W>(xv, S, x, ldx, col);
       if (zero_e(a.e) || zero_e(xv.e)) continue;
       term(a, xv, a.s ^ xv.s ^ (RESID ? 1u : 0u));
     }
@@ -467,9 +528,23 @@ mp_status spmv_w(const mp_csr_s* M, const Sell& S, int mode, const uint64_t* x, 
                  uint64_t* y, int64_t ldy, const uint64_t* b, int64_t ldb, const int* gate,
                  cudaStream_t st, const int32_t* rinst = nullptr, const int* idone = nullptr) {
   if (S.nchunks == 0) return MP_OK;
-  const SellView V = view(S, rinst, idone);
+  SellView V = view(S, rinst, idone);
   const LaunchCfg cf = launch_cfg(M, mode == MP_ORDERED && !b ? MP_ORDERED : MP_EXACT, W);
   const int tpb = cf.tpb;
+  if (cf.rec) {  // gathers from a record copy of x (one pass over x first)
+    mp_csr_s* Mw = const_cast<mp_csr_s*>(M);
+    const int rs = record_words(W);
+    if (!Mw->xrec)
+      MPK_CUDA(cudaMalloc((void**)&Mw->xrec, sizeof(uint64_t) * rs * (size_t)(M->n > 0 ? M->n : 1)));
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t nb = std::min<int64_t>((M->n + 255) / 256, (int64_t)sms * 8);
+    to_records_kernel<W><<<(int)std::max<int64_t>(nb, 1), 256, 0, st>>>(x, ldx, M->n, Mw->xrec, rs);
+    count_launch();
+    V.xrec = Mw->xrec;
+    V.xrs = rs;
+  }
   const int blocks = (int)((S.nchunks * 32 + tpb - 1) / tpb);
   if (mode == MP_ORDERED && !b) {
     constexpr bool P = Pipelined<W>::value;
@@ -601,7 +676,7 @@ mp_status mp_csr_set_config(mp_csr A, int32_t mode, int32_t tpb, int32_t variant
   if (mode != MP_ORDERED && mode != MP_EXACT) return set_error(MP_ERR_ARG, "mode %d", mode);
   if (tpb != -1 && tpb != 32 && tpb != 64 && tpb != 128 && tpb != 256)
     return set_error(MP_ERR_ARG, "threads per block %d not in {-1,32,64,128,256}", tpb);
-  if (variant < -1 || variant > 7) return set_error(MP_ERR_ARG, "variant %d not in -1..7", variant);
+  if (variant < -1 || variant > 15) return set_error(MP_ERR_ARG, "variant %d not in -1..15", variant);
   if (carveout < -1 || carveout > 100) return set_error(MP_ERR_ARG, "carve-out %d", carveout);
   A->cfg_tpb[mode] = tpb;
   A->cfg_var[mode] = variant;
@@ -616,7 +691,8 @@ mp_status mp_csr_get_config(mp_csr A, int32_t mode, int32_t* tpb, int32_t* varia
   const LaunchCfg c = launch_cfg(A, mode, A->prec / 32);
   if (tpb) *tpb = c.tpb;
   if (variant)
-    *variant = (c.cols ? kVarCols : 0) | (c.stage ? kVarStage : 0) | (c.wide ? kVarWide : 0);
+    *variant = (c.cols ? kVarCols : 0) | (c.stage ? kVarStage : 0) | (c.wide ? kVarWide : 0) |
+               (c.rec ? kVarRec : 0);
   if (carveout) *carveout = c.carve;
   return MP_OK;
 }
@@ -650,7 +726,7 @@ mp_status mp_csr_tune(mp_csr A, int32_t mode, int32_t reps, int32_t* tpb_out, in
   // ORDERED: both product forms, staging for p <= 512; EXACT: the word
   // form, and the column form with and without staging, 8 or 16 columns at
   // a time, each under four shared-memory carve-outs
-  int32_t vars[5], carves[4] = {-1, 25, 50, 75};
+  int32_t vars[8], carves[4] = {-1, 25, 50, 75};
   int nvar = 0, ncarve = mode == MP_EXACT ? 4 : 1;
   if (mode == MP_ORDERED) {
     for (int32_t v = 0; v <= (kVarCols | kVarStage); v += (A->prec > 512 ? kVarCols : 1))
@@ -662,6 +738,18 @@ mp_status mp_csr_tune(mp_csr A, int32_t mode, int32_t reps, int32_t* tpb_out, in
     for (int32_t v : {kVarCols, kVarCols | kVarStage, kVarCols | kVarWide,
                       kVarCols | kVarStage | kVarWide})
       vars[nvar++] = v;
+  }
+  // the same gathering x from its record copy, for the default form
+  {
+    const int32_t saved = A->cfg_var[mode];
+    A->cfg_var[mode] = -1;
+    const LaunchCfg d = launch_cfg(A, mode, A->prec / 32);
+    A->cfg_var[mode] = saved;
+    const int32_t dv = (d.cols ? kVarCols : 0) | (d.stage ? kVarStage : 0) | (d.wide ? kVarWide : 0);
+    bool listed = false;
+    for (int i = 0; i < nvar; ++i) listed = listed || vars[i] == dv;
+    if (!listed) vars[nvar++] = dv;
+    vars[nvar++] = dv | kVarRec;
   }
   for (int32_t tpb : {64, 128, 256}) {
     for (int vi = 0; vi < nvar && r == MP_OK; ++vi) {

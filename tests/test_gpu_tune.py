@@ -28,7 +28,7 @@ def test_every_configuration_matches_the_oracle(p):
         want, st = oracle.spmv(p, m, rowptr, colidx, recs(V), recs(X))
         want_t, _ = oracle.spmv_t(p, m, rowptr, colidx, recs(V), recs(X))
         for tpb, carve in ((32, -1), (64, 25), (128, 50), (256, 75), (-1, -1)):
-            for v in (0, 1, 2, 3, 6, 7, -1):
+            for v in (0, 1, 2, 3, 6, 7, 9, 11, 15, -1):
                 A.set_config(name, tpb, v, carve)
                 got = A.get_config(name)
                 if tpb > 0:
@@ -39,7 +39,7 @@ def test_every_configuration_matches_the_oracle(p):
                     assert got["variant"] & 2 == v & 2  # the product form asked for
                     if name == "ordered":
                         capped = 4 if (v & 4 and (tpb if tpb > 0 else 128) <= 128) else 0
-                        assert got["variant"] == (v & 3 if p <= 512 else v & 2) | capped
+                        assert got["variant"] == (v & 3 if p <= 512 else v & 2) | capped | (v & 8)
                     elif v & 2:
                         assert got["variant"] == v
                 what = f"{name} p={p} tpb={tpb} variant={v} carveout={carve}"
@@ -51,7 +51,7 @@ def test_bad_configuration_is_rejected():
     mpk = need_gpu()
     rowptr, colidx = random_csr(64, seed=2)
     A = mpk.CSR(rowptr, colidx, np.ones(len(colidx)), 128)
-    for args in (("ordered", 96, -1, -1), ("ordered", 128, 8, -1), ("exact", 512, -1, -1),
+    for args in (("ordered", 96, -1, -1), ("ordered", 128, 16, -1), ("exact", 512, -1, -1),
                  ("exact", 64, -2, -1), ("exact", 64, 0, 101)):
         with pytest.raises(mpk.MPError):
             A.set_config(*args)
@@ -77,9 +77,9 @@ def test_tuner_and_cache(p, tmp_path):
         assert not r["cached"] and r["ms"] > 0
         assert r["threads_per_block"] in (32, 64, 128, 256)
         assert A.get_config(name)["threads_per_block"] == r["threads_per_block"]
-        allowed = {"ordered": ((0, 1, 2, 3, 5, 7) if p <= 512 else (0, 2, 6)),
-                   "exact": (1 if p <= 512 else 0, 2, 3, 6, 7)}[name]
-        assert r["variant"] in allowed
+        base = {"ordered": ((0, 1, 2, 3, 5, 7) if p <= 512 else (0, 2, 6)),
+                "exact": (0, 1, 2, 3, 6, 7)}[name]
+        assert r["variant"] in set(base) | {v | 8 for v in base}
         want, _ = oracle.spmv(p, m, rowptr, colidx, recs(V), recs(X))
         assert_bitwise(mpk.spmv(A, x, mode=name).planes(), want, f"tuned {name} p={p}")
     assert len(json.load(open(cache))) == 2
