@@ -57,6 +57,10 @@ def _load():
                      ctypes.c_double, ctypes.c_double, _i64, _i64p, _u64p],
         "mpo_gpbicg": [_i32, _i32, _i64, _i64p, _i32p, _u64p, _u64p, _u64p,
                        ctypes.c_double, ctypes.c_double, _i64, _i64p, _u64p],
+        "mpo_cgs": [_i32, _i32, _i64, _i64p, _i32p, _u64p, _u64p, _u64p,
+                    ctypes.c_double, ctypes.c_double, _i64, _i64p, _u64p],
+        "mpo_bicgstab": [_i32, _i32, _i64, _i64p, _i32p, _u64p, _u64p, _u64p,
+                         ctypes.c_double, ctypes.c_double, _i64, _i64p, _u64p],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -205,3 +209,13 @@ def bicg(p, mode, rowptr, colidx, vals, b, x0, rtol, atol, maxit):
 def gpbicg(p, mode, rowptr, colidx, vals, b, x0, rtol, atol, maxit):
     """Returns (x, iterations, status, history of (r_i, r_i))."""
     return _solve(_load().mpo_gpbicg, p, mode, rowptr, colidx, vals, b, x0, rtol, atol, maxit)
+
+
+def cgs(p, mode, rowptr, colidx, vals, b, x0, rtol, atol, maxit):
+    """CGS (textbook form).  Returns (x, iterations, status, history of (r_i, r_i))."""
+    return _solve(_load().mpo_cgs, p, mode, rowptr, colidx, vals, b, x0, rtol, atol, maxit)
+
+
+def bicgstab(p, mode, rowptr, colidx, vals, b, x0, rtol, atol, maxit):
+    """BiCGSTAB (textbook form).  Returns (x, iterations, status, history of (r_i, r_i))."""
+    return _solve(_load().mpo_bicgstab, p, mode, rowptr, colidx, vals, b, x0, rtol, atol, maxit)

@@ -1,4 +1,5 @@
-/* mpo.c -- CPU oracle for p-bit CSR SpMV, exact dot products, BiCG and GPBiCG.
+/* mpo.c -- CPU oracle for p-bit CSR SpMV, exact dot products, BiCG, GPBiCG,
+ * CGS and BiCGSTAB.
  *
  * TEST INFRASTRUCTURE ONLY (see mpo.h).  Deliberately plain and slow: natural
  * numbers are little-endian arrays of 32-bit words handled by schoolbook
@@ -1122,5 +1123,234 @@ done:
   free(u);
   free(z);
   free(sv);
+  return st;
+}
+
+/* CGS (Sonneveld's conjugate gradient squared; Section 4 runs it, the paper
+ * prints no algorithm, so the textbook form with K = I is taken, Saad,
+ * Iterative Methods for Sparse Linear Systems, Alg. 7.6).  With r~ = r0 and
+ * rho_{i-1} = (r~, r_{i-1}):
+ *   i = 1: u = p = r0;  i > 1: beta = rho_{i-1}/rho_{i-2},
+ *   u = r + beta q,  p = u + beta (q + beta p);
+ *   v = A p,  alpha = rho_{i-1} / (r~, v),  q = u - alpha v,  w = u + q,
+ *   x = x + alpha w,  r = r - alpha A w.
+ * Each printed product and sum is rounded, left to right; (r~, v) = 0 and
+ * rho = 0 are breakdowns; the stopping rule is checked once r_i is formed
+ * (the same order of exits as BiCG). */
+int mpo_cgs(int p, int mode, int64_t n, const int64_t *rowptr,
+            const int32_t *colidx, const uint64_t *vals, const uint64_t *b,
+            uint64_t *x, double rtol, double atol, int64_t maxit,
+            int64_t *iters, uint64_t *hist) {
+  int st = solve_args(p, mode, n, rowptr, colidx, vals, b, x, rtol, atol, maxit);
+  *iters = 0;
+  if (st) return st;
+  sysA s = {p, mode, n, rowptr, colidx, vals, (size_t)(p / 64 + 1)};
+  uint64_t *r = vnew(&s), *rt = vnew(&s), *u = vnew(&s), *pv = vnew(&s);
+  uint64_t *q = vnew(&s), *v = vnew(&s), *w = vnew(&s), *aw = vnew(&s);
+  num rr0, rr, thr, rho, rho_prev, alpha, beta, d;
+  st = residual_vec(p, n, rowptr, colidx, vals, b, x, r); /* r0 = b - A x0 */
+  if (st) goto done;
+  vcopy(&s, rt, r); /* r~ = r0 */
+  sdot(&s, r, r, &rr0);
+  conv_threshold(p, rtol, atol, &rr0, &thr);
+  if (num_cmp(&rr0, &thr, p) <= 0) {
+    st = MPO_OK;
+    goto done;
+  }
+  sdot(&s, rt, r, &rho);
+  st = MPO_ERR_NOCONV;
+  for (int64_t i = 1; i <= maxit; i++) {
+    if (rho.zero) {
+      st = MPO_ERR_BREAKDOWN;
+      break;
+    }
+    if (i == 1) {
+      vcopy(&s, u, r);
+      vcopy(&s, pv, r);
+    } else {
+      num_div(&rho, &rho_prev, p, &beta); /* beta = rho_{i-1} / rho_{i-2} */
+      for (int64_t k = 0; k < n; k++) {
+        num rk, qk, pk, a1, a2, a3, uk;
+        vload(r, k, p, &rk);
+        vload(q, k, p, &qk);
+        vload(pv, k, p, &pk);
+        num_mul(&beta, &qk, p, &a1);
+        num_add(&rk, &a1, p, &uk); /* u = r + beta q */
+        vstore(u, k, p, &uk);
+        num_mul(&beta, &pk, p, &a1);
+        num_add(&qk, &a1, p, &a2);
+        num_mul(&beta, &a2, p, &a3);
+        num_add(&uk, &a3, p, &a1); /* p = u + beta (q + beta p) */
+        vstore(pv, k, p, &a1);
+      }
+    }
+    matvec(&s, rowptr, colidx, vals, pv, v); /* v = A p */
+    sdot(&s, rt, v, &d);
+    if (d.zero) {
+      st = MPO_ERR_BREAKDOWN;
+      break;
+    }
+    num_div(&rho, &d, p, &alpha); /* alpha = rho_{i-1} / (r~, v) */
+    for (int64_t k = 0; k < n; k++) {
+      num uk, vk, xk, a1, qk, wk;
+      vload(u, k, p, &uk);
+      vload(v, k, p, &vk);
+      num_mul(&alpha, &vk, p, &a1);
+      num_sub(&uk, &a1, p, &qk); /* q = u - alpha v */
+      vstore(q, k, p, &qk);
+      num_add(&uk, &qk, p, &wk); /* w = u + q */
+      vstore(w, k, p, &wk);
+      vload(x, k, p, &xk);
+      num_mul(&alpha, &wk, p, &a1);
+      num_add(&xk, &a1, p, &qk); /* x = x + alpha w */
+      vstore(x, k, p, &qk);
+    }
+    matvec(&s, rowptr, colidx, vals, w, aw); /* A w */
+    for (int64_t k = 0; k < n; k++) {
+      num rk, ak, a1, a2;
+      vload(r, k, p, &rk);
+      vload(aw, k, p, &ak);
+      num_mul(&alpha, &ak, p, &a1);
+      num_sub(&rk, &a1, p, &a2); /* r = r - alpha A w */
+      vstore(r, k, p, &a2);
+    }
+    *iters = i;
+    sdot(&s, r, r, &rr);
+    if (hist) rec_store(&rr, p, hist + (size_t)(i - 1) * s.rl);
+    rho_prev = rho;
+    sdot(&s, rt, r, &rho);
+    if (num_cmp(&rr, &thr, p) <= 0) {
+      st = MPO_OK;
+      break;
+    }
+  }
+done:
+  free(r);
+  free(rt);
+  free(u);
+  free(pv);
+  free(q);
+  free(v);
+  free(w);
+  free(aw);
+  return st;
+}
+
+/* BiCGSTAB (van der Vorst; Section 4 runs it, the paper prints no algorithm,
+ * so the textbook form with K = I is taken, Saad, Alg. 7.7).  With r~ = r0:
+ *   i = 1: p = r0;  i > 1: beta = (rho_{i-1}/rho_{i-2}) (alpha/omega),
+ *   p = r + beta (p - omega v);
+ *   v = A p,  alpha = rho_{i-1} / (r~, v),  s = r - alpha v,  t = A s,
+ *   omega = (t, s) / (t, t)  (+0 when t = 0),
+ *   x = x + alpha p + omega s,  r = s - omega t.
+ * Each printed product and sum is rounded, left to right; (r~, v) = 0 and
+ * rho = 0 are breakdowns.  Exits after r_i is formed: the stopping rule,
+ * then omega = 0 (the next beta would divide by it) as a breakdown; reaching
+ * maxit wins over a zero rho found for the next iteration. */
+int mpo_bicgstab(int p, int mode, int64_t n, const int64_t *rowptr,
+                 const int32_t *colidx, const uint64_t *vals, const uint64_t *b,
+                 uint64_t *x, double rtol, double atol, int64_t maxit,
+                 int64_t *iters, uint64_t *hist) {
+  int st = solve_args(p, mode, n, rowptr, colidx, vals, b, x, rtol, atol, maxit);
+  *iters = 0;
+  if (st) return st;
+  sysA s = {p, mode, n, rowptr, colidx, vals, (size_t)(p / 64 + 1)};
+  uint64_t *r = vnew(&s), *rt = vnew(&s), *pv = vnew(&s), *v = vnew(&s);
+  uint64_t *sv = vnew(&s), *t = vnew(&s);
+  num rr0, rr, thr, rho, rho_prev, alpha, beta, omega, d, tt, ts, t1, t2;
+  set_zero(&omega, 0);
+  set_zero(&alpha, 0);
+  st = residual_vec(p, n, rowptr, colidx, vals, b, x, r); /* r0 = b - A x0 */
+  if (st) goto done;
+  vcopy(&s, rt, r); /* r~ = r0 */
+  sdot(&s, r, r, &rr0);
+  conv_threshold(p, rtol, atol, &rr0, &thr);
+  if (num_cmp(&rr0, &thr, p) <= 0) {
+    st = MPO_OK;
+    goto done;
+  }
+  sdot(&s, rt, r, &rho);
+  st = MPO_ERR_NOCONV;
+  for (int64_t i = 1; i <= maxit; i++) {
+    if (rho.zero) {
+      st = MPO_ERR_BREAKDOWN;
+      break;
+    }
+    if (i == 1) {
+      vcopy(&s, pv, r);
+    } else {
+      num_div(&rho, &rho_prev, p, &t1);
+      num_div(&alpha, &omega, p, &t2);
+      num_mul(&t1, &t2, p, &beta); /* beta = (rho_{i-1}/rho_{i-2}) (alpha/omega) */
+      for (int64_t k = 0; k < n; k++) {
+        num rk, pk, vk, a1, a2, a3;
+        vload(r, k, p, &rk);
+        vload(pv, k, p, &pk);
+        vload(v, k, p, &vk);
+        num_mul(&omega, &vk, p, &a1);
+        num_sub(&pk, &a1, p, &a2);
+        num_mul(&beta, &a2, p, &a3);
+        num_add(&rk, &a3, p, &a1); /* p = r + beta (p - omega v) */
+        vstore(pv, k, p, &a1);
+      }
+    }
+    matvec(&s, rowptr, colidx, vals, pv, v); /* v = A p */
+    sdot(&s, rt, v, &d);
+    if (d.zero) {
+      st = MPO_ERR_BREAKDOWN;
+      break;
+    }
+    num_div(&rho, &d, p, &alpha); /* alpha = rho_{i-1} / (r~, v) */
+    for (int64_t k = 0; k < n; k++) {
+      num rk, vk, a1, sk;
+      vload(r, k, p, &rk);
+      vload(v, k, p, &vk);
+      num_mul(&alpha, &vk, p, &a1);
+      num_sub(&rk, &a1, p, &sk); /* s = r - alpha v */
+      vstore(sv, k, p, &sk);
+    }
+    matvec(&s, rowptr, colidx, vals, sv, t); /* t = A s */
+    sdot(&s, t, sv, &ts);
+    sdot(&s, t, t, &tt);
+    if (tt.zero)
+      set_zero(&omega, 0);
+    else
+      num_div(&ts, &tt, p, &omega); /* omega = (t, s) / (t, t) */
+    for (int64_t k = 0; k < n; k++) {
+      num xk, pk, sk, tk, a1, a2, a3;
+      vload(x, k, p, &xk);
+      vload(pv, k, p, &pk);
+      vload(sv, k, p, &sk);
+      vload(t, k, p, &tk);
+      num_mul(&alpha, &pk, p, &a1);
+      num_add(&xk, &a1, p, &a2);
+      num_mul(&omega, &sk, p, &a1);
+      num_add(&a2, &a1, p, &a3); /* x = x + alpha p + omega s */
+      vstore(x, k, p, &a3);
+      num_mul(&omega, &tk, p, &a1);
+      num_sub(&sk, &a1, p, &a2); /* r = s - omega t */
+      vstore(r, k, p, &a2);
+    }
+    *iters = i;
+    sdot(&s, r, r, &rr);
+    if (hist) rec_store(&rr, p, hist + (size_t)(i - 1) * s.rl);
+    rho_prev = rho;
+    sdot(&s, rt, r, &rho);
+    if (num_cmp(&rr, &thr, p) <= 0) {
+      st = MPO_OK;
+      break;
+    }
+    if (omega.zero) {
+      st = MPO_ERR_BREAKDOWN;
+      break;
+    }
+  }
+done:
+  free(r);
+  free(rt);
+  free(pv);
+  free(v);
+  free(sv);
+  free(t);
   return st;
 }

@@ -1,4 +1,4 @@
-/* mpo.h -- CPU oracle for p-bit CSR SpMV, exact dot products, BiCG and GPBiCG.
+/* mpo.h -- CPU oracle for p-bit CSR SpMV, exact dot products and the Krylov solvers.
  *
  * TEST INFRASTRUCTURE ONLY.  This library is the slow, plain reference that the
  * GPU path is checked against.  Only the test suite, the smoke check and the
@@ -96,6 +96,17 @@ int mpo_gpbicg(int p, int mode, int64_t n, const int64_t *rowptr,
                const int32_t *colidx, const uint64_t *vals, const uint64_t *b,
                uint64_t *x, double rtol, double atol, int64_t maxit,
                int64_t *iters, uint64_t *hist);
+/* CGS and BiCGSTAB (the other product-type methods of Section 4's tables;
+ * the paper prints no algorithm, the textbook forms with K = I are taken):
+ * same arguments, statuses and exit order as the solvers above. */
+int mpo_cgs(int p, int mode, int64_t n, const int64_t *rowptr,
+            const int32_t *colidx, const uint64_t *vals, const uint64_t *b,
+            uint64_t *x, double rtol, double atol, int64_t maxit,
+            int64_t *iters, uint64_t *hist);
+int mpo_bicgstab(int p, int mode, int64_t n, const int64_t *rowptr,
+                 const int32_t *colidx, const uint64_t *vals, const uint64_t *b,
+                 uint64_t *x, double rtol, double atol, int64_t maxit,
+                 int64_t *iters, uint64_t *hist);
 
 #ifdef __cplusplus
 }

@@ -148,3 +148,94 @@ def bicg(rows, rows_t, b, x, p, mode, rtol, maxit):
         if rr.q <= thr.q:
             return x, i, "ok", hist
     return x, maxit, "noconv", hist
+
+
+def cgs(rows, b, x, p, mode, rtol, maxit):
+    """CGS in the textbook order (each product and sum rounded, left to right)."""
+    R = exact.rmul
+    A_ = exact.radd
+    S_ = exact.rsub
+    D = exact.rdiv
+    r = _residual(rows, b, x, p)
+    rt = list(r)
+    rr0 = _dot(r, r, p)
+    thr = _threshold(rr0, rtol, 0.0, p)
+    hist = []
+    if rr0.q <= thr.q:
+        return x, 0, "ok", hist
+    rho = _dot(rt, r, p)
+    u = pv = q = rho_prev = None
+    for i in range(1, maxit + 1):
+        if rho.q == 0:
+            return x, i - 1, "breakdown", hist
+        if i == 1:
+            u, pv = list(r), list(r)
+        else:
+            beta = D(rho, rho_prev, p)
+            u = [A_(rk, R(beta, qk, p), p) for rk, qk in zip(r, q)]
+            pv = [A_(uk, R(beta, A_(qk, R(beta, pk, p), p), p), p)
+                  for uk, qk, pk in zip(u, q, pv)]
+        v = _spmv(rows, pv, p, mode)
+        d = _dot(rt, v, p)
+        if d.q == 0:
+            return x, i - 1, "breakdown", hist
+        alpha = D(rho, d, p)
+        q = [S_(uk, R(alpha, vk, p), p) for uk, vk in zip(u, v)]
+        w = [A_(uk, qk, p) for uk, qk in zip(u, q)]
+        x = [A_(xk, R(alpha, wk, p), p) for xk, wk in zip(x, w)]
+        aw = _spmv(rows, w, p, mode)
+        r = [S_(rk, R(alpha, ak, p), p) for rk, ak in zip(r, aw)]
+        rr = _dot(r, r, p)
+        hist.append(rr)
+        rho_prev, rho = rho, _dot(rt, r, p)
+        if rr.q <= thr.q:
+            return x, i, "ok", hist
+    return x, maxit, "noconv", hist
+
+
+def bicgstab(rows, b, x, p, mode, rtol, maxit):
+    """BiCGSTAB in the textbook order; omega = +0 when (t, t) = 0."""
+    R = exact.rmul
+    A_ = exact.radd
+    S_ = exact.rsub
+    D = exact.rdiv
+    Z = exact.Val(Fraction(0))
+    r = _residual(rows, b, x, p)
+    rt = list(r)
+    rr0 = _dot(r, r, p)
+    thr = _threshold(rr0, rtol, 0.0, p)
+    hist = []
+    if rr0.q <= thr.q:
+        return x, 0, "ok", hist
+    rho = _dot(rt, r, p)
+    pv = v = rho_prev = None
+    alpha = omega = Z
+    for i in range(1, maxit + 1):
+        if rho.q == 0:
+            return x, i - 1, "breakdown", hist
+        if i == 1:
+            pv = list(r)
+        else:
+            beta = R(D(rho, rho_prev, p), D(alpha, omega, p), p)
+            pv = [A_(rk, R(beta, S_(pk, R(omega, vk, p), p), p), p)
+                  for rk, pk, vk in zip(r, pv, v)]
+        v = _spmv(rows, pv, p, mode)
+        d = _dot(rt, v, p)
+        if d.q == 0:
+            return x, i - 1, "breakdown", hist
+        alpha = D(rho, d, p)
+        s = [S_(rk, R(alpha, vk, p), p) for rk, vk in zip(r, v)]
+        t = _spmv(rows, s, p, mode)
+        tt = _dot(t, t, p)
+        omega = D(_dot(t, s, p), tt, p) if tt.q != 0 else Z
+        x = [A_(A_(xk, R(alpha, pk, p), p), R(omega, sk, p), p)
+             for xk, pk, sk in zip(x, pv, s)]
+        r = [S_(sk, R(omega, tk, p), p) for sk, tk in zip(s, t)]
+        rr = _dot(r, r, p)
+        hist.append(rr)
+        rho_prev, rho = rho, _dot(rt, r, p)
+        if rr.q <= thr.q:
+            return x, i, "ok", hist
+        if omega.q == 0:
+            return x, i, "breakdown", hist
+    return x, maxit, "noconv", hist

@@ -1,4 +1,5 @@
-"""Pins for the oracle's BiCG and GPBiCG (Fig. 5, K = I).
+"""Pins for the oracle's BiCG and GPBiCG (Fig. 5, K = I), CGS and BiCGSTAB
+(Section 4's other product-type methods, textbook forms).
 
 Expectations come from mathematics, not from the oracle: finite termination
 of BiCG-type methods in at most n steps in exact arithmetic (approached at
@@ -17,7 +18,8 @@ import oracle
 import replay
 from paper_1411_2377_gb300 import synth
 
-SOLVERS = {"bicg": oracle.bicg, "gpbicg": oracle.gpbicg}
+SOLVERS = {"bicg": oracle.bicg, "gpbicg": oracle.gpbicg, "cgs": oracle.cgs,
+           "bicgstab": oracle.bicgstab}
 
 
 def rand_system(n, p, seed, density=0.5, emin=-2, emax=2):
@@ -58,8 +60,8 @@ def test_replay_every_iterate_bitwise(name, mode):
     for maxit in (1, 2, 3, 6):
         x, it, st, hist = SOLVERS[name](p, mode, rowptr, colidx, vals, b, x0, 1e-300, 0.0, maxit)
         B = exact.vec_decode(b, p)
-        if name == "gpbicg":
-            xr, itr, str_, hr = replay.gpbicg(rows, B, X0, p, mode, 1e-300, maxit)
+        if name in ("gpbicg", "cgs", "bicgstab"):
+            xr, itr, str_, hr = getattr(replay, name)(rows, B, X0, p, mode, 1e-300, maxit)
         else:
             trp, tci, tv = oracle.transpose(p, rowptr, colidx, vals)
             rows_t = rows_of(trp, tci, tv, p)
