@@ -510,7 +510,8 @@ def refine_bench(mpk, m=100, p=256, plain_cap=400):
     mpk.refine(A, b, max_outer=1)  # warm-up (builds the FP64 copy)
     x, info = mpk.refine(A, b, rtol=2.0 ** (-p + 8), max_outer=40)
     out["refine"] = dict(info, forward_error=forward_error(mpk, x, p))
-    for name, fn in (("gpbicg", mpk.gpbicg), ("bicg", mpk.bicg)):
+    for name, fn in (("gpbicg", mpk.gpbicg), ("bicg", mpk.bicg), ("cgs", mpk.cgs),
+                     ("bicgstab", mpk.bicgstab)):
         x, info = fn(A, b, rtol=1e-30, maxit=plain_cap, poll_every=32)
         out[name] = {"iters": info["iters"], "status": info["status"], "ms": info["ms"],
                      "relres": info["relres"], "forward_error": forward_error(mpk, x, p)}
@@ -614,8 +615,9 @@ def batch_bench(mpk, count=256, rtol=1e-25):
 
 
 def solver_bench(mpk):
-    """GPBiCG and BiCG at 128 bits on the 64x64 convection-diffusion system,
-    b = A*ones, to relative residual 1e-30 (iterations, time on the stream)."""
+    """GPBiCG and BiCG (and CGS, BiCGSTAB) at 128 bits on the 64x64
+    convection-diffusion system, b = A*ones, to relative residual 1e-30
+    (iterations, time on the stream)."""
     from paper_1411_2377_gb300 import synth
 
     p = 128

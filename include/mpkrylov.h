@@ -254,6 +254,26 @@ mp_status mp_bicg(mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* opts,
 mp_status mp_gpbicg(mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* opts,
                     mp_solve_info* info, void* stream);
 
+/* CGS and BiCGSTAB, the other product-type methods of Section 4's tables
+ * (Tables 1-2).  The paper prints no algorithm for them; the textbook forms
+ * with K = I and r~ = r0 are taken:
+ *   CGS:      u = r + beta q, p = u + beta (q + beta p) (u = p = r0 at i = 1),
+ *             v = A p, alpha = rho / (r~, v), q = u - alpha v, w = u + q,
+ *             x = x + alpha w, r = r - alpha A w, beta = rho_i / rho_{i-1};
+ *   BiCGSTAB: p = r + beta (p - omega v) (p = r0 at i = 1), v = A p,
+ *             alpha = rho / (r~, v), s = r - alpha v, t = A s,
+ *             omega = (t, s) / (t, t) (+0 when t = 0), x = x + alpha p +
+ *             omega s, r = s - omega t, beta = (rho_i/rho_{i-1})(alpha/omega).
+ * Every product and sum rounded left to right, inner products exact; the
+ * stopping rule, options and statuses as mp_gpbicg (a zero (r~, v) or rho is
+ * a breakdown; BiCGSTAB ends with MP_ERR_BREAKDOWN on omega = 0 after the
+ * convergence test).  opts->transpose solves with A^T (needs
+ * MP_CSR_TRANSPOSE). */
+mp_status mp_cgs(mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* opts, mp_solve_info* info,
+                 void* stream);
+mp_status mp_bicgstab(mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* opts,
+                      mp_solve_info* info, void* stream);
+
 /* ---- batched solves (not in the paper; its solver over a batch) ---------- */
 
 typedef struct mp_batch_s* mp_batch; /* opaque; owns its device storage */

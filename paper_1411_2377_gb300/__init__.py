@@ -311,6 +311,22 @@ def gpbicg(A: CSR, b: Vec, x0: Vec | None = None, rtol=1e-30, atol=0.0, maxit=10
                   poll_every, history, stream, transpose)
 
 
+def cgs(A: CSR, b: Vec, x0: Vec | None = None, rtol=1e-30, atol=0.0, maxit=1000,
+        mode="ordered", poll_every=8, history=False, stream=None, transpose=False):
+    """CGS (Section 4's product-type method, textbook form, K = I).
+    Returns (x, info dict)."""
+    return _solve(_lib.load().mp_cgs, "mp_cgs", A, b, x0, rtol, atol, maxit, mode,
+                  poll_every, history, stream, transpose)
+
+
+def bicgstab(A: CSR, b: Vec, x0: Vec | None = None, rtol=1e-30, atol=0.0, maxit=1000,
+             mode="ordered", poll_every=8, history=False, stream=None, transpose=False):
+    """BiCGSTAB (Section 4's product-type method, textbook form, K = I).
+    Returns (x, info dict)."""
+    return _solve(_lib.load().mp_bicgstab, "mp_bicgstab", A, b, x0, rtol, atol, maxit, mode,
+                  poll_every, history, stream, transpose)
+
+
 class Batch:
     """Independent systems of one precision stacked for batched solves.
 

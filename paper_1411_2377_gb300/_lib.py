@@ -73,6 +73,10 @@ SIGNATURES = {
                        ctypes.POINTER(MpSolveInfo), _vp]),
     "mp_gpbicg": (_i32, [_vp, MpVec, MpVec, ctypes.POINTER(MpSolveOpts),
                          ctypes.POINTER(MpSolveInfo), _vp]),
+    "mp_cgs": (_i32, [_vp, MpVec, MpVec, ctypes.POINTER(MpSolveOpts),
+                      ctypes.POINTER(MpSolveInfo), _vp]),
+    "mp_bicgstab": (_i32, [_vp, MpVec, MpVec, ctypes.POINTER(MpSolveOpts),
+                           ctypes.POINTER(MpSolveInfo), _vp]),
     "mp_csr_grad": (_i32, [_vp, MpVec, MpVec, MpVec, _vp]),
     "mp_batch_create_f64": (_i32, [_i32, _vp, _vp, _vp, _vp, _i32, _vp, ctypes.POINTER(_vp)]),
     "mp_batch_destroy": (_i32, [_vp]),

@@ -1,4 +1,5 @@
-// solvers.cu -- device-resident BiCG and GPBiCG (Fig. 5, K = I).
+// solvers.cu -- device-resident BiCG and GPBiCG (Fig. 5, K = I), and CGS and
+// BiCGSTAB (the other product-type methods of Section 4, textbook forms).
 //
 // Every step of an iteration is a kernel on the caller's stream: the SpMVs,
 // the exact dot products (fused where they share operands), one-thread
@@ -46,7 +47,7 @@ struct SolveCall {
 };
 
 template <int W>
-mp_status solve_entry(bool gp, const SolveCall& c, mp_solve_info* info);
+mp_status solve_entry(int method, const SolveCall& c, mp_solve_info* info);
 
 }  // namespace mpk
 
@@ -63,8 +64,11 @@ struct SState {
 
 enum Scal {
   RHO, RHO_NEW, RHO_PREV, ALPHA, BETA, ZETA, ETA, DEN, MU1, MU2, MU3, MU4, MU5, RR, RR0, THR,
-  NSCAL
+  OMEGA, TS, TT, NSCAL
 };
+
+// Solvers of the library (the template argument of the driver).
+enum Method { kBiCG = 0, kGPBiCG = 1, kCGS = 2, kBiCGSTAB = 3 };
 
 template <int W>
 __device__ __forceinline__ void ld_s(Num<W>& a, const uint64_t* S, int j) {
@@ -177,17 +181,18 @@ __global__ void sc_zeta(SState* st, uint64_t* S) {
   st_s<W>(z, S, ETA);
 }
 
-// GPBiCG: beta = RN(RN(rho/rho_prev) * RN(alpha/zeta)); BiCG: rho/rho_prev.
-template <int W, bool GP>
+// beta = RN(rho/rho_prev) (BiCG, CGS), or RN(RN(rho/rho_prev) * RN(alpha/d))
+// with d = zeta (GPBiCG) or omega (BiCGSTAB): DIV names d's slot, -1 none.
+template <int W, int DIV>
 __global__ void sc_beta(SState* st, uint64_t* S) {
   if (st->done) return;
   Num<W> rho, rp, q1, a, z, q2, b;
   ld_s<W>(rho, S, RHO);
   ld_s<W>(rp, S, RHO_PREV);
   div_rn<W>(rho, rp, q1);
-  if (GP) {
+  if (DIV >= 0) {
     ld_s<W>(a, S, ALPHA);
-    ld_s<W>(z, S, ZETA);
+    ld_s<W>(z, S, DIV);
     div_rn<W>(a, z, q2);
     mul_rn<W>(q1, q2, b);
     st_s<W>(b, S, BETA);
@@ -197,7 +202,9 @@ __global__ void sc_beta(SState* st, uint64_t* S) {
 }
 
 // End of an iteration: count it, record (r,r), shift rho, decide the exit.
-template <int W, bool GP>
+// ZX: the scalar whose zero ends the iteration after the convergence test
+// (GPBiCG's zeta, BiCGSTAB's omega), -1 none.
+template <int W, int ZX>
 __global__ void sc_check(SState* st, uint64_t* S, uint64_t* hist, int64_t hist_ld,
                          int64_t hist_n) {
   if (st->done) return;
@@ -210,10 +217,10 @@ __global__ void sc_check(SState* st, uint64_t* S, uint64_t* hist, int64_t hist_l
   st_s<W>(rho, S, RHO_PREV);
   st_s<W>(rn, S, RHO);
   ld_s<W>(thr, S, THR);
-  ld_s<W>(z, S, ZETA);
+  ld_s<W>(z, S, ZX >= 0 ? ZX : ZETA);
   if (cmp<W>(rr, thr) <= 0) {
     finish(st, MP_OK);
-  } else if (GP && zero_e(z.e)) {
+  } else if (ZX >= 0 && zero_e(z.e)) {
     finish(st, MP_ERR_BREAKDOWN);
   } else if (st->iters >= st->maxit) {
     finish(st, MP_ERR_NOCONV);
@@ -423,6 +430,143 @@ __global__ void bi_xr(const SState* st, const uint64_t* __restrict__ S, const ui
   }
 }
 
+// BiCGSTAB: omega = RN(TS / TT), +0 when TT = (t, t) = 0.
+template <int W>
+__global__ void sc_omega(SState* st, uint64_t* S) {
+  if (st->done) return;
+  Num<W> ts, tt, om;
+  ld_s<W>(tt, S, TT);
+  if (zero_e(tt.e)) {
+    set_zero(om, 0u);
+  } else {
+    ld_s<W>(ts, S, TS);
+    div_rn<W>(ts, tt, om);
+  }
+  st_s<W>(om, S, OMEGA);
+}
+
+// CGS, i >= 2: u = r + beta q;  p = u + beta (q + beta p)
+template <int W>
+__global__ void cgs_up(const SState* st, const uint64_t* __restrict__ S, const uint64_t* r,
+                       const uint64_t* q, uint64_t* u, uint64_t* p, int64_t ld, int64_t n) {
+  if (st->done) return;
+  GRID_LOOP(i, n) {
+    Num<W> beta, qv, a, b, un;
+    ld_s<W>(beta, S, BETA);
+    load<W>(qv, q, ld, i);
+    mul_rn<W>(beta, qv, a);
+    load<W>(b, r, ld, i);
+    add_rn<W>(b, a, un);
+    store<W>(un, u, ld, i);
+    load<W>(a, p, ld, i);
+    mul_rn<W>(beta, a, b);
+    add_rn<W>(qv, b, a);
+    mul_rn<W>(beta, a, b);
+    add_rn<W>(un, b, a);
+    store<W>(a, p, ld, i);
+  }
+}
+
+// CGS: q = u - alpha v;  w = u + q;  x = x + alpha w
+template <int W>
+__global__ void cgs_qwx(const SState* st, const uint64_t* __restrict__ S, const uint64_t* u,
+                        const uint64_t* v, uint64_t* q, uint64_t* w, uint64_t* x, int64_t ldx,
+                        int64_t ld, int64_t n) {
+  if (st->done) return;
+  GRID_LOOP(i, n) {
+    Num<W> alpha, uv, a, b, qv, wv;
+    ld_s<W>(alpha, S, ALPHA);
+    load<W>(uv, u, ld, i);
+    load<W>(a, v, ld, i);
+    mul_rn<W>(alpha, a, b);
+    sub_rn<W>(uv, b, qv);
+    store<W>(qv, q, ld, i);
+    add_rn<W>(uv, qv, wv);
+    store<W>(wv, w, ld, i);
+    mul_rn<W>(alpha, wv, b);
+    load<W>(a, x, ldx, i);
+    add_rn<W>(a, b, uv);
+    store<W>(uv, x, ldx, i);
+  }
+}
+
+// r = r - SCAL * a  (CGS: alpha A w)
+template <int W, int SCAL>
+__global__ void r_minus(const SState* st, const uint64_t* __restrict__ S, const uint64_t* a,
+                        uint64_t* r, int64_t ld, int64_t n) {
+  if (st->done) return;
+  GRID_LOOP(i, n) {
+    Num<W> sc, av, b, rv, c;
+    ld_s<W>(sc, S, SCAL);
+    load<W>(av, a, ld, i);
+    mul_rn<W>(sc, av, b);
+    load<W>(rv, r, ld, i);
+    sub_rn<W>(rv, b, c);
+    store<W>(c, r, ld, i);
+  }
+}
+
+// BiCGSTAB, i >= 2: p = r + beta (p - omega v)
+template <int W>
+__global__ void bs_p(const SState* st, const uint64_t* __restrict__ S, const uint64_t* r,
+                     const uint64_t* v, uint64_t* p, int64_t ld, int64_t n) {
+  if (st->done) return;
+  GRID_LOOP(i, n) {
+    Num<W> beta, omega, a, b, c;
+    ld_s<W>(beta, S, BETA);
+    ld_s<W>(omega, S, OMEGA);
+    load<W>(a, v, ld, i);
+    mul_rn<W>(omega, a, b);
+    load<W>(a, p, ld, i);
+    sub_rn<W>(a, b, c);
+    mul_rn<W>(beta, c, a);
+    load<W>(b, r, ld, i);
+    add_rn<W>(b, a, c);
+    store<W>(c, p, ld, i);
+  }
+}
+
+// BiCGSTAB: s = r - alpha v
+template <int W>
+__global__ void bs_s(const SState* st, const uint64_t* __restrict__ S, const uint64_t* r,
+                     const uint64_t* v, uint64_t* s, int64_t ld, int64_t n) {
+  if (st->done) return;
+  GRID_LOOP(i, n) {
+    Num<W> alpha, a, b, c;
+    ld_s<W>(alpha, S, ALPHA);
+    load<W>(a, v, ld, i);
+    mul_rn<W>(alpha, a, b);
+    load<W>(a, r, ld, i);
+    sub_rn<W>(a, b, c);
+    store<W>(c, s, ld, i);
+  }
+}
+
+// BiCGSTAB: x = x + alpha p + omega s;  r = s - omega t
+template <int W>
+__global__ void bs_xr(const SState* st, const uint64_t* __restrict__ S, const uint64_t* p,
+                      const uint64_t* s, const uint64_t* t, uint64_t* r, uint64_t* x, int64_t ldx,
+                      int64_t ld, int64_t n) {
+  if (st->done) return;
+  GRID_LOOP(i, n) {
+    Num<W> alpha, omega, a, b, c, sv;
+    ld_s<W>(alpha, S, ALPHA);
+    ld_s<W>(omega, S, OMEGA);
+    load<W>(a, p, ld, i);
+    mul_rn<W>(alpha, a, b);
+    load<W>(a, x, ldx, i);
+    add_rn<W>(a, b, c);
+    load<W>(sv, s, ld, i);
+    mul_rn<W>(omega, sv, b);
+    add_rn<W>(c, b, a);
+    store<W>(a, x, ldx, i);
+    load<W>(a, t, ld, i);
+    mul_rn<W>(omega, a, b);
+    sub_rn<W>(sv, b, c);
+    store<W>(c, r, ld, i);
+  }
+}
+
 int ew_grid(int64_t n) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -508,7 +652,7 @@ mp_status gp_iteration(const Work& w, const SolveCall& c, bool first) {
     copy_kernel<W><<<g, 128, 0, st>>>(w.st, w.vec(R), ld, w.vec(P), ld, n);
     count_launch();
   } else {
-    sc_beta<W, true><<<1, 1, 0, st>>>(w.st, w.S);
+    sc_beta<W, ZETA><<<1, 1, 0, st>>>(w.st, w.S);
     gp_wp<W><<<g, 128, 0, st>>>(w.st, w.S, w.vec(V), w.vec(Q), w.vec(R), w.vec(P), w.vec(U),
                                 w.vec(WV), ld, n);
     count_launch(2);
@@ -561,7 +705,7 @@ mp_status gp_iteration(const Work& w, const SolveCall& c, bool first) {
   count_launch();
   if ((r = dot2(w, w.vec(R), w.vec(R), RR, w.vec(RT), w.vec(R), RHO_NEW, st, gate)) != MP_OK)
     return r;
-  sc_check<W, true><<<1, 1, 0, st>>>(w.st, w.S, c.o.history.data, c.o.history.ld,
+  sc_check<W, ZETA><<<1, 1, 0, st>>>(w.st, w.S, c.o.history.data, c.o.history.ld,
                                      c.o.history.data ? c.o.history.n : 0);
   count_launch();
   return launch_check("gpbicg iteration");
@@ -580,7 +724,7 @@ mp_status bi_iteration(const Work& w, const SolveCall& c, bool first) {
     copy_kernel<W><<<g, 128, 0, st>>>(w.st, w.vec(RT), ld, w.vec(PT), ld, n);
     count_launch(2);
   } else {
-    sc_beta<W, false><<<1, 1, 0, st>>>(w.st, w.S);
+    sc_beta<W, -1><<<1, 1, 0, st>>>(w.st, w.S);
     bi_p<W><<<g, 128, 0, st>>>(w.st, w.S, w.vec(R), w.vec(RT), w.vec(P), w.vec(PT), ld, n);
     count_launch(2);
   }
@@ -595,13 +739,86 @@ mp_status bi_iteration(const Work& w, const SolveCall& c, bool first) {
   count_launch(2);
   if ((r = dot2(w, w.vec(R), w.vec(R), RR, w.vec(RT), w.vec(R), RHO_NEW, st, gate)) != MP_OK)
     return r;
-  sc_check<W, false><<<1, 1, 0, st>>>(w.st, w.S, c.o.history.data, c.o.history.ld,
+  sc_check<W, -1><<<1, 1, 0, st>>>(w.st, w.S, c.o.history.data, c.o.history.ld,
                                       c.o.history.data ? c.o.history.n : 0);
   count_launch();
   return launch_check("bicg iteration");
 }
 
-template <int W, bool GP>
+template <int W>
+mp_status cgs_iteration(const Work& w, const SolveCall& c, bool first) {
+  enum { R, RT, U, P, Q, V, WV, AW };
+  const int64_t n = w.n, ld = w.ld;
+  const int* gate = &w.st->done;
+  cudaStream_t st = c.st;
+  const int g = ew_grid(n);
+  mp_status r;
+  if (first) {
+    copy_kernel<W><<<g, 128, 0, st>>>(w.st, w.vec(R), ld, w.vec(U), ld, n);
+    copy_kernel<W><<<g, 128, 0, st>>>(w.st, w.vec(R), ld, w.vec(P), ld, n);
+    count_launch(2);
+  } else {
+    sc_beta<W, -1><<<1, 1, 0, st>>>(w.st, w.S);
+    cgs_up<W><<<g, 128, 0, st>>>(w.st, w.S, w.vec(R), w.vec(Q), w.vec(U), w.vec(P), ld, n);
+    count_launch(2);
+  }
+  if ((r = launch_spmv(c.A, op_a(c), c.o.mode, w.vec(P), ld, w.vec(V), ld, nullptr, 0, gate, st)) != MP_OK)
+    return r;
+  if ((r = dot2(w, w.vec(RT), w.vec(V), DEN, nullptr, nullptr, 0, st, gate)) != MP_OK) return r;
+  sc_alpha<W><<<1, 1, 0, st>>>(w.st, w.S);
+  cgs_qwx<W><<<g, 128, 0, st>>>(w.st, w.S, w.vec(U), w.vec(V), w.vec(Q), w.vec(WV), c.x.data,
+                                c.x.ld, ld, n);
+  count_launch(2);
+  if ((r = launch_spmv(c.A, op_a(c), c.o.mode, w.vec(WV), ld, w.vec(AW), ld, nullptr, 0, gate, st)) != MP_OK)
+    return r;
+  r_minus<W, ALPHA><<<g, 128, 0, st>>>(w.st, w.S, w.vec(AW), w.vec(R), ld, n);
+  count_launch();
+  if ((r = dot2(w, w.vec(R), w.vec(R), RR, w.vec(RT), w.vec(R), RHO_NEW, st, gate)) != MP_OK)
+    return r;
+  sc_check<W, -1><<<1, 1, 0, st>>>(w.st, w.S, c.o.history.data, c.o.history.ld,
+                                   c.o.history.data ? c.o.history.n : 0);
+  count_launch();
+  return launch_check("cgs iteration");
+}
+
+template <int W>
+mp_status bicgstab_iteration(const Work& w, const SolveCall& c, bool first) {
+  enum { R, RT, P, V, SV, T };
+  const int64_t n = w.n, ld = w.ld;
+  const int* gate = &w.st->done;
+  cudaStream_t st = c.st;
+  const int g = ew_grid(n);
+  mp_status r;
+  if (first) {
+    copy_kernel<W><<<g, 128, 0, st>>>(w.st, w.vec(R), ld, w.vec(P), ld, n);
+    count_launch();
+  } else {
+    sc_beta<W, OMEGA><<<1, 1, 0, st>>>(w.st, w.S);
+    bs_p<W><<<g, 128, 0, st>>>(w.st, w.S, w.vec(R), w.vec(V), w.vec(P), ld, n);
+    count_launch(2);
+  }
+  if ((r = launch_spmv(c.A, op_a(c), c.o.mode, w.vec(P), ld, w.vec(V), ld, nullptr, 0, gate, st)) != MP_OK)
+    return r;
+  if ((r = dot2(w, w.vec(RT), w.vec(V), DEN, nullptr, nullptr, 0, st, gate)) != MP_OK) return r;
+  sc_alpha<W><<<1, 1, 0, st>>>(w.st, w.S);
+  bs_s<W><<<g, 128, 0, st>>>(w.st, w.S, w.vec(R), w.vec(V), w.vec(SV), ld, n);
+  count_launch(2);
+  if ((r = launch_spmv(c.A, op_a(c), c.o.mode, w.vec(SV), ld, w.vec(T), ld, nullptr, 0, gate, st)) != MP_OK)
+    return r;
+  if ((r = dot2(w, w.vec(T), w.vec(SV), TS, w.vec(T), w.vec(T), TT, st, gate)) != MP_OK) return r;
+  sc_omega<W><<<1, 1, 0, st>>>(w.st, w.S);
+  bs_xr<W><<<g, 128, 0, st>>>(w.st, w.S, w.vec(P), w.vec(SV), w.vec(T), w.vec(R), c.x.data,
+                              c.x.ld, ld, n);
+  count_launch(2);
+  if ((r = dot2(w, w.vec(R), w.vec(R), RR, w.vec(RT), w.vec(R), RHO_NEW, st, gate)) != MP_OK)
+    return r;
+  sc_check<W, OMEGA><<<1, 1, 0, st>>>(w.st, w.S, c.o.history.data, c.o.history.ld,
+                                      c.o.history.data ? c.o.history.n : 0);
+  count_launch();
+  return launch_check("bicgstab iteration");
+}
+
+template <int W, int M>
 mp_status solve_w(const SolveCall& cu, mp_solve_info* info) {
   // The solve runs on a private non-blocking stream fenced to the caller's
   // stream by events (the legacy default stream cannot be captured).
@@ -615,7 +832,8 @@ mp_status solve_w(const SolveCall& cu, mp_solve_info* info) {
   c.st = st;
   const int64_t n = c.A->n;
   Work w;
-  mp_status r = alloc_work(w, c.A->prec, n, GP ? 11 : 6, st);
+  constexpr int kVecs = M == kGPBiCG ? 11 : (M == kCGS ? 8 : 6);
+  mp_status r = alloc_work(w, c.A->prec, n, kVecs, st);
   if (r != MP_OK) {
     free_work(w, st);
     return r;
@@ -631,7 +849,12 @@ mp_status solve_w(const SolveCall& cu, mp_solve_info* info) {
   cudaGraphExec_t exec = nullptr;
   SState hs{};
   auto body = [&](bool first) {
-    return GP ? gp_iteration<W>(w, c, first) : bi_iteration<W>(w, c, first);
+    switch (M) {
+      case kGPBiCG: return gp_iteration<W>(w, c, first);
+      case kCGS: return cgs_iteration<W>(w, c, first);
+      case kBiCGSTAB: return bicgstab_iteration<W>(w, c, first);
+      default: return bi_iteration<W>(w, c, first);
+    }
   };
   do {
     cudaError_t ce0 = cudaMemcpyAsync(w.st, &init, sizeof init, cudaMemcpyHostToDevice, st);
@@ -726,10 +949,15 @@ mp_status solve_w(const SolveCall& cu, mp_solve_info* info) {
 }  // namespace
 
 template <int W>
-mp_status solve_entry(bool gp, const SolveCall& c, mp_solve_info* info) {
-  return gp ? solve_w<W, true>(c, info) : solve_w<W, false>(c, info);
+mp_status solve_entry(int method, const SolveCall& c, mp_solve_info* info) {
+  switch (method) {
+    case kGPBiCG: return solve_w<W, kGPBiCG>(c, info);
+    case kCGS: return solve_w<W, kCGS>(c, info);
+    case kBiCGSTAB: return solve_w<W, kBiCGSTAB>(c, info);
+    default: return solve_w<W, kBiCG>(c, info);
+  }
 }
-template mp_status solve_entry<MPK_W>(bool, const SolveCall&, mp_solve_info*);
+template mp_status solve_entry<MPK_W>(int, const SolveCall&, mp_solve_info*);
 
 }  // namespace mpk
 
@@ -738,7 +966,7 @@ template mp_status solve_entry<MPK_W>(bool, const SolveCall&, mp_solve_info*);
 namespace mpk {
 namespace {
 
-mp_status solve(bool gp, mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* opts,
+mp_status solve(int method, mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* opts,
                 mp_solve_info* info, void* stream) {
   if (!A) return set_error(MP_ERR_ARG, "matrix is null");
   if (!opts) return set_error(MP_ERR_ARG, "opts is null");
@@ -754,7 +982,7 @@ mp_status solve(bool gp, mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* opts
   if (opts->history.data) {
     if ((r = check_vec(opts->history, opts->history.n, A->prec, "history")) != MP_OK) return r;
   }
-  if (!gp && !A->has_t) return set_error(MP_ERR_ARG, "BiCG needs MP_CSR_TRANSPOSE");
+  if (method == 0 && !A->has_t) return set_error(MP_ERR_ARG, "BiCG needs MP_CSR_TRANSPOSE");
   if (opts->transpose != 0 && opts->transpose != 1)
     return set_error(MP_ERR_ARG, "transpose must be 0 or 1");
   if (opts->transpose && !A->has_t)
@@ -764,7 +992,7 @@ mp_status solve(bool gp, mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* opts
   SolveCall c{A, b, x, *opts, static_cast<cudaStream_t>(stream)};
   return dispatch_w(A->prec, [&](auto w) {
     constexpr int W = decltype(w)::value;
-    return solve_entry<W>(gp, c, info);
+    return solve_entry<W>(method, c, info);
   });
 }
 
@@ -775,12 +1003,22 @@ extern "C" {
 
 mp_status mp_bicg(mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* opts, mp_solve_info* info,
                   void* stream) {
-  return mpk::solve(false, A, b, x, opts, info, stream);
+  return mpk::solve(0, A, b, x, opts, info, stream);
 }
 
 mp_status mp_gpbicg(mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* opts, mp_solve_info* info,
                     void* stream) {
-  return mpk::solve(true, A, b, x, opts, info, stream);
+  return mpk::solve(1, A, b, x, opts, info, stream);
+}
+
+mp_status mp_cgs(mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* opts, mp_solve_info* info,
+                 void* stream) {
+  return mpk::solve(2, A, b, x, opts, info, stream);
+}
+
+mp_status mp_bicgstab(mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* opts,
+                      mp_solve_info* info, void* stream) {
+  return mpk::solve(3, A, b, x, opts, info, stream);
 }
 
 }  // extern "C"

@@ -1,5 +1,5 @@
-"""Device-resident BiCG and GPBiCG vs the oracle: iteration counts, status,
-every iterate's (r_i, r_i) and the final x, bit for bit."""
+"""Device-resident BiCG, GPBiCG, CGS and BiCGSTAB vs the oracle: iteration
+counts, status, every iterate's (r_i, r_i) and the final x, bit for bit."""
 import numpy as np
 import pytest
 
@@ -8,7 +8,8 @@ from gpu_util import assert_bitwise, need_gpu, rand_planes, random_csr, recs
 from paper_1411_2377_gb300 import synth
 
 pytestmark = pytest.mark.gpu
-SOLVERS = {"gpbicg": oracle.gpbicg, "bicg": oracle.bicg}
+SOLVERS = {"gpbicg": oracle.gpbicg, "bicg": oracle.bicg, "cgs": oracle.cgs,
+           "bicgstab": oracle.bicgstab}
 
 
 def run_both(mpk, name, rowptr, colidx, vals_planes, b_planes, p, mode, rtol, maxit,
@@ -16,7 +17,7 @@ def run_both(mpk, name, rowptr, colidx, vals_planes, b_planes, p, mode, rtol, ma
     A = mpk.CSR(rowptr, colidx, vals_planes, p, transpose=True)
     b = mpk.Vec.from_planes(b_planes, p)
     x0v = mpk.Vec.from_planes(x0, p) if x0 is not None else None
-    fn = mpk.gpbicg if name == "gpbicg" else mpk.bicg
+    fn = getattr(mpk, name)
     x, info = fn(A, b, x0=x0v, rtol=rtol, maxit=maxit, mode=mode, poll_every=poll_every,
                  history=True)
     m = oracle.ORDERED if mode == "ordered" else oracle.EXACT
@@ -120,3 +121,24 @@ def test_breakdown_and_trivial(name):
     x, info, xo, it, st, _ = run_both(mpk, name, rp, ci, v, bb, p, "exact", 1e-30, 10)
     assert (info["status"], info["iters"]) == (st, it) == (oracle.OK, 1)
     assert_bitwise(x.planes(), xo, "identity x")
+
+
+@pytest.mark.parametrize("name", ("cgs", "bicgstab"))
+def test_transposed_solve_matches_the_oracle_on_the_transpose(name):
+    """opts.transpose: the solve with A^T equals the oracle's solve on the
+    explicit transpose."""
+    mpk = need_gpu()
+    p = 256
+    rowptr, colidx, v64 = synth.stencil2d(9, seed=4)
+    vals = synth.records_to_planes(oracle.from_f64(p, v64))
+    n = len(rowptr) - 1
+    trp, tci, tv = oracle.transpose(p, rowptr, colidx, recs(vals))
+    b, _ = oracle.spmv(p, oracle.EXACT, trp, tci, tv, oracle.from_f64(p, np.ones(n)))
+    A = mpk.CSR(rowptr, colidx, vals, p, transpose=True)
+    x, info = getattr(mpk, name)(A, mpk.Vec.from_planes(synth.records_to_planes(b), p),
+                                 rtol=1e-40, maxit=300, history=True, transpose=True)
+    xo, it, st, hist = SOLVERS[name](p, oracle.ORDERED, trp, tci, tv, b, oracle.empty(p, n),
+                                     1e-40, 0.0, 300)
+    assert (info["iters"], info["status"]) == (it, st)
+    assert_bitwise(x.planes(), xo, f"{name} transpose x")
+    assert_bitwise(info["history"].planes(), hist, f"{name} transpose history")
