@@ -417,6 +417,7 @@ def run_native(args):
         solver["refinement"] = refine_bench(mpk)
         solver["autograd"] = autograd_bench(mpk)
         solver["batched"] = batch_bench(mpk, count=args.batch_systems)
+        solver["lotkin"] = lotkin_bench(mpk)
 
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
@@ -611,6 +612,44 @@ def batch_bench(mpk, count=256, rtol=1e-25):
         B.close()
         for A in mats.values():
             A.close()
+    return out
+
+
+def lotkin_bench(mpk, n=2000, precs=(128, 256, 512, 1024), s_list=(0.0, 50.0, 90.0, 99.0),
+                 reps=5):
+    """Section 3's experiment on the GPU: the n x n Lotkin matrix with s %
+    zeros, y = A b with b = A [1..n]^T, as the sparse product (zeros dropped,
+    CSR, autotuned) and as the dense MV (zeros stored); the paper's "speedup
+    ratio" is dense time / sparse time.  Both results are bit-identical."""
+    import torch
+
+    from paper_1411_2377_gb300 import lotkin, tune
+
+    out = {"workload": f"lotkin_n{n}", "rows": []}
+    for p in precs:
+        for s in s_list:
+            A, D = lotkin.lotkin(n, s, p, seed=7)
+            tune.autotune(A, modes=("ordered",), reps=2, cache=None)
+            b = lotkin.rhs(A, n, p)
+            ys, yd = mpk.Vec.empty(n, p), mpk.Vec.empty(n, p)
+            times = {}
+            for name, call in (("sparse", lambda: mpk.spmv(A, b, ys, mode="ordered", sync=False)),
+                               ("dense", lambda: mpk.gemv(D, n, n, b, yd, sync=False))):
+                call()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(reps):
+                    call()
+                e1.record()
+                e1.synchronize()
+                times[name] = e0.elapsed_time(e1) / reps
+            mpk.check()
+            out["rows"].append({"p": p, "s": s, "nnz": A.nnz, "sparse_ms": round(times["sparse"], 4),
+                                "dense_ms": round(times["dense"], 4),
+                                "speedup_ratio": round(times["dense"] / times["sparse"], 2),
+                                "identical": bool(torch.equal(ys.t, yd.t))})
+            A.close()
+            del D
     return out
 
 

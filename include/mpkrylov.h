@@ -346,6 +346,17 @@ mp_status mp_refine(mp_csr A, mp_vec b, mp_vec x, const mp_refine_opts* opts,
  * mp_csr_create (g has n = nnz values).  dL/db is lam itself. */
 mp_status mp_csr_grad(mp_csr A, mp_vec lam, mp_vec x, mp_vec g, void* stream);
 
+/* ---- dense product (Section 3's comparison) ----------------------------- */
+
+/* y = A x for a dense m x n p-bit matrix A stored column-major per plane:
+ * A is an mp_vec of m*n elements (element (i, j) at index j*m + i, plane
+ * stride A.ld), x has n elements, y m.  Each y_i follows the ORDERED row
+ * loop of mp_spmv over all columns (y_i = +0, then y_i = RN(y_i +
+ * RN(a_ij x_j)) for j ascending, zero factors skipped), so it equals the
+ * ORDERED SpMV of the same matrix whether its zeros are stored or dropped
+ * (Section 3 compares exactly these two).  x and y must not alias. */
+mp_status mp_gemv(int64_t m, int64_t n, mp_vec A, mp_vec x, mp_vec y, void* stream);
+
 /* ---- status -------------------------------------------------------------- */
 
 /* Waits for `stream`, then returns and clears the device-side status word of

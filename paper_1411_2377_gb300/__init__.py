@@ -252,6 +252,17 @@ def residual(A: CSR, b: Vec, x: Vec, r: Vec | None = None, stream=None, sync=Tru
     return r
 
 
+def gemv(A: Vec, m: int, n: int, x: Vec, y: Vec | None = None, stream=None,
+         sync=True) -> Vec:
+    """y = A x for a dense m x n matrix held column-major in the Vec A
+    (element (i, j) at j*m + i): Section 3's dense MV, ORDERED row loops."""
+    y = y if y is not None else Vec.empty(m, A.prec)
+    _ok(_lib.load().mp_gemv(int(m), int(n), A.c(), x.c(), y.c(), _stream(stream)), "mp_gemv")
+    if sync:
+        check(stream)
+    return y
+
+
 def dot(x: Vec, y: Vec, out: Vec | None = None, stream=None, sync=True) -> Vec:
     """RN(sum x_i y_i), exact sum rounded once; returns a 1-element Vec."""
     out = out if out is not None else Vec.empty(1, x.prec)

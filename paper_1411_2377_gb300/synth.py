@@ -285,6 +285,20 @@ def small_random_csr(n: int, seed: int, density: float = 0.3, empty_rows: int = 
     return np.cumsum(rowptr), cols.astype(np.int32)
 
 
+def lotkin_pattern(n: int, s_percent: float, seed: int = 7):
+    """Section 3's SpMV workload: the n x n Lotkin matrix (first row ones,
+    a_ij = 1/(i+j-1) below it, 1-based) with each entry dropped with
+    probability s_percent/100 (one draw per (i, j), row-major index).
+    Returns (rowptr, colidx, num, den): the kept entries in row order, each
+    the rational num/den (small integers as float64, exact)."""
+    u = uniform(seed, S_MISC, np.arange(n * n, dtype=np.uint64)).reshape(n, n)
+    rows, cols = np.nonzero(u >= s_percent / 100.0)
+    rowptr = np.zeros(n + 1, np.int64)
+    np.add.at(rowptr, rows + 1, 1)
+    den = np.where(rows == 0, 1, rows + cols + 1).astype(np.float64)
+    return np.cumsum(rowptr), cols.astype(np.int32), np.ones(len(cols)), den
+
+
 def planes_to_records(planes: np.ndarray) -> np.ndarray:
     """(L+1, n) planes -> (n, L+1) records (the oracle's layout)."""
     return np.ascontiguousarray(planes.T)

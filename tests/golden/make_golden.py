@@ -25,19 +25,7 @@ CASES = ((128, 8, 40.0, 7), (256, 6, 25.0, 8))
 
 def lotkin_sparse(n, s_percent, seed):
     """Pattern and the (numerator, denominator) of each stored entry."""
-    u = synth.uniform(seed, synth.S_MISC, np.arange(n * n, dtype=np.uint64)).reshape(n, n)
-    rows, cols, num, den = [], [], [], []
-    for i in range(n):
-        for j in range(n):
-            if u[i, j] < s_percent / 100.0:
-                continue
-            rows.append(i)
-            cols.append(j)
-            num.append(1)
-            den.append(1 if i == 0 else i + j + 1)  # 0-based: 1/(i+j+1)
-    rowptr = np.zeros(n + 1, np.int64)
-    np.add.at(rowptr, np.array(rows, np.int64) + 1, 1)
-    return np.cumsum(rowptr), np.array(cols, np.int32), np.array(num, float), np.array(den, float)
+    return synth.lotkin_pattern(n, s_percent, seed)
 
 
 def hexrec(rec):
