@@ -176,6 +176,15 @@ struct Pipelined {
 // ORDERED
 // ---------------------------------------------------------------------------
 
+// The column form of the ORDERED product: the short product from p = 512 on.
+template <int W>
+__device__ __forceinline__ void ordered_product_cols(const Num<W>& a, const Num<W>& b, Num<W>& r) {
+  if constexpr (W >= 16)
+    mul_rn_short<W>(a, b, r);
+  else
+    mul_rn_cols<W>(a, b, r);
+}
+
 template <int W, bool PIPE, bool COLS>
 __device__ __forceinline__ void ordered_rows(const SellView& S, const uint64_t* __restrict__ x,
                                              int64_t ldx, uint64_t* __restrict__ y, int64_t ldy,
@@ -214,7 +223,7 @@ __device__ __forceinline__ void ordered_rows(const SellView& S, const uint64_t* 
       if (zero_e(a.e) || zero_e(xv.e)) continue;  // zero fast path
       Num<W> t, s;
       if (COLS)
-        mul_rn_cols<W>(a, xv, t);
+        ordered_product_cols<W>(a, xv, t);
       else
         mul_rn<W>(a, xv, t);
       add_rn<W>(acc, t, s);
@@ -230,7 +239,7 @@ __device__ __forceinline__ void ordered_rows(const SellView& S, const uint64_t* 
       if (zero_e(a.e) || zero_e(xv.e)) continue;  // zero fast path
       Num<W> t, s;
       if (COLS)
-        mul_rn_cols<W>(a, xv, t);
+        ordered_product_cols<W>(a, xv, t);
       else
         mul_rn<W>(a, xv, t);
       add_rn<W>(acc, t, s);
