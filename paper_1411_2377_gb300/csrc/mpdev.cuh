@@ -846,6 +846,88 @@ __device__ __forceinline__ void mul_rn_short(const Num<W>& a, const Num<W>& b, N
   round_increment<W>(r.m, r.e, rb & ((any != 0u) | (r.m[0] & 1u)));
 }
 
+// As add_product_cols for a window of counters that starts qrel digits above
+// the term's own digit 0 (qrel = q - window base, may be negative): columns
+// below the window (k < -qrel) are skipped, and errp is set when a skipped
+// column may be nonzero (it is zero when k < la + lx, the indices of the two
+// operands' lowest nonzero limbs).
+template <int W, int G = 8>
+__device__ __forceinline__ void add_product_cols_top(int64_t* c, int stride, const uint32_t (&a)[W],
+                                                     const uint32_t (&x)[W], int qrel, uint32_t s,
+                                                     uint32_t neg, bool& errp) {
+  constexpr int NA = Cols<W>::NA, NX = Cols<W>::NX, NC = Cols<W>::NC;
+  const int kmin = qrel < 0 ? -qrel : 0;
+  if (kmin > NC) {  // the whole term lies below the window
+    errp = true;
+    return;
+  }
+  uint32_t al[NA], xl[NX];
+  cut_limbs<W, NA>(a, al);
+  cut_limbs_shifted<W, NX>(x, s, xl);
+  if (kmin > 0) {
+    int la = NA, lx = NX;
+#pragma unroll
+    for (int i = NA - 1; i >= 0; --i) la = al[i] ? i : la;
+#pragma unroll
+    for (int j = NX - 1; j >= 0; --j) lx = xl[j] ? j : lx;
+    errp = errp || kmin > la + lx;
+  }
+  const uint64_t m = neg ? ~0ull : 0ull;
+  int64_t* p = c + (int64_t)qrel * stride;
+  uint64_t carry = 0u;
+#pragma unroll
+  for (int k0 = 0; k0 <= NC; k0 += G) {
+    if (k0 + G <= kmin) continue;  // the group lies below the window
+    uint64_t dd[G], acc[G];
+    int64_t v[G];
+#pragma unroll
+    for (int u = 0; u < G; ++u)
+      if (k0 + u <= NC && k0 + u >= kmin) v[u] = p[(k0 + u) * stride];
+#pragma unroll
+    for (int u = 0; u < G; ++u) acc[u] = 0u;
+#pragma unroll
+    for (int i = 0; i < NA; ++i) {
+#pragma unroll
+      for (int u = 0; u < G; ++u) {
+        const int j = k0 + u - i;
+        if (k0 + u < NC && j >= 0 && j < NX && k0 + u >= kmin) acc[u] += (uint64_t)al[i] * xl[j];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+      const int k = k0 + u;
+      if (k < NC) {
+        dd[u] = (uint64_t)((uint32_t)acc[u] & kRMask) + carry;
+        carry = acc[u] >> kR;  // 0 below the window: that column's high part is skipped too
+      } else if (k == NC) {
+        dd[u] = carry;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < G; ++u)
+      if (k0 + u <= NC && k0 + u >= kmin) p[(k0 + u) * stride] = v[u] + (int64_t)((dd[u] ^ m) - m);
+  }
+}
+
+// Whether the bits [lo, hi) of the nw-word magnitude c[.*stride] decide a
+// rounding that an error of magnitude below 2^lo cannot change: they must be
+// neither all zeros nor all ones, and at least 8 of them.
+__device__ __forceinline__ bool guard_bits_decide(const int64_t* c, int stride, int nw, int64_t lo,
+                                                  int64_t hi) {
+  if (hi - lo < 8) return false;
+  uint32_t any = 0u, all = 0xffffffffu;
+  for (int64_t w = lo >> 5; w <= (hi - 1) >> 5 && w < nw; ++w) {
+    const int64_t b0 = w << 5;
+    const uint32_t from = lo > b0 ? (uint32_t)(lo - b0) : 0u;
+    const uint32_t to = hi < b0 + 32 ? (uint32_t)(hi - b0) : 32u;  // bits [from, to)
+    const uint32_t mask = (to == 32u ? 0xffffffffu : ((1u << to) - 1u)) & ~((1u << from) - 1u);
+    const uint32_t word = (uint32_t)c[w * stride];
+    any |= word & mask;
+    all &= word | ~mask;
+  }
+  return any != 0u && all != 0xffffffffu;
+}
+
 // c[(q + j) * stride] += (-1)^neg * limb_j(M << s) for the value M * 2^off.
 template <int W>
 __device__ __forceinline__ void add_value_cols(int64_t* c, int stride, const uint32_t (&mv)[W],

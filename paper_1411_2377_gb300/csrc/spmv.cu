@@ -25,11 +25,16 @@ namespace {
 constexpr int kThreads = 128;   // 4 chunks per block
 constexpr int kFastSpan = 512;  // bits of exponent span handled per thread
 
+// Bits of a row sum kept below the top p bits of its largest term by the
+// windowed EXACT form (the rest is checked, not computed; see below).
+constexpr int kTopGuard = 128;
+
 template <int W>
 struct Win {
   static constexpr int fast = (kFastSpan + 64 * W + 96) / 32 + 1;  // digits per thread
   static constexpr int cap = (SPAN_CAP + 64 * W + 96) / 32 + 1;    // digits for the cap
   static constexpr int fast_cols = (kFastSpan + 64 * W + 64) / kR + 4;  // radix-2^29 digits
+  static constexpr int top_cols = (32 * W + 64 + kTopGuard) / kR + 6;   // windowed form
 };
 
 // Radix-2^29 digits of a row whose terms span `span` bits: the terms' digits
@@ -43,16 +48,17 @@ __host__ __device__ inline int digits_cols(int64_t span, int W) {
 // form stages at p <= 512), bit 1 = products from radix-2^29 column sums,
 // bit 2 = EXACT: column sums computed 16 columns at a time instead of 8;
 // ORDERED: the register-capped kernel (three blocks of <= 128 threads per SM);
-// bit 3 = x gathered from a record copy made before the product.
-constexpr int kVarStage = 1, kVarCols = 2, kVarWide = 4, kVarRec = 8;
+// bit 3 = x gathered from a record copy made before the product;
+// bit 4 = EXACT (p >= 512, column form): the windowed kernel.
+constexpr int kVarStage = 1, kVarCols = 2, kVarWide = 4, kVarRec = 8, kVarTop = 16;
 // A matrix's launch configuration for one mode with the library's defaults
 // filled in (chosen from measurements of the n = 10^6 sweep on GB300: the
 // word form with a half-and-half L1/shared split for EXACT at p <= 512, the
-// column form with 256 threads at p = 1024; column products for ORDERED from
-// p = 256 on, register-capped blocks at p = 128 and 1024).
+// windowed column form at p = 1024; column products for ORDERED from p = 256
+// on, register-capped blocks at p = 128 and 1024).
 struct LaunchCfg {
   int tpb;
-  bool stage, cols, wide, rec;
+  bool stage, cols, wide, rec, top;
   int carve;  // -1: the driver's choice
 };
 
@@ -64,6 +70,7 @@ LaunchCfg launch_cfg(const mp_csr_s* M, int mode, int W) {
   // large enough for the pass to pay
   c.rec = v < 0 ? (W >= 8 && M->n >= (int64_t(1) << 16) && M->gather_sectors > 16.0)
                 : (v & kVarRec) != 0;
+  c.top = false;
   if (mode == MP_ORDERED) {
     c.cols = v < 0 ? W >= 8 : (v & kVarCols) != 0;
     c.stage = W <= 16 && (v < 0 || (v & kVarStage));
@@ -73,9 +80,10 @@ LaunchCfg launch_cfg(const mp_csr_s* M, int mode, int W) {
     c.carve = M->cfg_carve[0];
   } else {
     c.cols = v < 0 ? W >= 32 : (v & kVarCols) != 0;
-    c.stage = c.cols ? (v < 0 || (v & kVarStage)) : W <= 16;
+    c.top = c.cols && W >= 16 && (v < 0 ? W >= 32 : (v & kVarTop) != 0);
+    c.stage = c.cols ? (v < 0 ? !c.top : (v & kVarStage) != 0) : W <= 16;
     c.wide = c.cols && v >= 0 && (v & kVarWide);
-    c.tpb = M->cfg_tpb[1] < 0 ? (W >= 32 ? 256 : 128) : M->cfg_tpb[1];
+    c.tpb = M->cfg_tpb[1] < 0 ? 128 : M->cfg_tpb[1];
     c.carve = M->cfg_carve[1] < 0 ? (W <= 16 ? 50 : -1) : M->cfg_carve[1];
   }
   return c;
@@ -417,6 +425,142 @@ __global__ void __launch_bounds__(256) spmv_exact_kernel(
   store<W>(r, y, ldy, row);
 }
 
+// EXACT in a window under the largest term (p >= 512, column products): the
+// counters cover only the top p + kTopGuard bits (plus carries) of the row
+// sum, columns of a product below the window are not computed, and the
+// result is rounded when the bits between the possible error of the skipped
+// columns (< 2^eb) and the round bit decide the rounding (guard_bits_decide),
+// or when every skipped column is provably zero.  Otherwise (heavy
+// cancellation, exact ties) the row goes to the exact warp-per-row kernel
+// through the overflow list, so the result is always the exact sum rounded
+// once.  The window is a third of the full one and about a third of the
+// multiply-adds are skipped.
+template <int W, bool PIPE, int G>
+__global__ void __launch_bounds__(256) spmv_exact_top_kernel(
+    const SellView S, const uint64_t* __restrict__ x, int64_t ldx, uint64_t* __restrict__ y,
+    int64_t ldy, int32_t* __restrict__ ovf, int* __restrict__ status,
+    const int* __restrict__ gate) {
+  extern __shared__ int64_t sacc[];
+  if (gate && *gate) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t chunk = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (chunk >= S.nchunks) return;
+  const int64_t slot = chunk * 32 + lane;
+  const int32_t row = S.row_of[slot];
+  if (row_skipped(S, row)) return;
+  const int32_t len = S.row_len[slot];
+  const int64_t base = S.chunk_off[chunk] + lane;
+  int64_t emin = LLONG_MAX, emax = LLONG_MIN;
+  for (int32_t j0 = 0; j0 < len; j0 += 4) {
+    int32_t cc[4];
+    uint64_t ha[4], hx[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t k = base + (int64_t)(j0 + u) * 32;
+      cc[u] = (j0 + u < len) ? S.col[k] : 0;
+      ha[u] = (j0 + u < len) ? __ldg(S.val + k) : pack_head(EXP_ZERO, 0u);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) hx[u] = gather_head(S, x, cc[u]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      int64_t ea, ex;
+      uint32_t sa, sx;
+      unpack_head(ha[u], ea, sa);
+      unpack_head(hx[u], ex, sx);
+      if (zero_e(ea) || zero_e(ex)) continue;
+      emin = min(emin, ea + ex);
+      emax = max(emax, ea + ex);
+    }
+  }
+  Num<W> r;
+  if (emin > emax) {
+    set_zero(r, 0u);
+    store<W>(r, y, ldy, row);
+    return;
+  }
+  const int64_t span = emax - emin;
+  if (span > SPAN_CAP) {
+    set_zero(r, 0u);
+    store<W>(r, y, ldy, row);
+    record_status(status, MP_ERR_SPAN);
+    return;
+  }
+  const int wb = (int)((span + 32 * W - kTopGuard) / kR);  // window base digit
+  const int nd = digits_cols(span, W) - wb;
+  auto to_exact_path = [&]() {
+    const int pos = atomicAdd(ovf, 1);
+    ovf[1 + pos] = (int32_t)slot;
+  };
+  if (nd > Win<W>::top_cols) {
+    to_exact_path();
+    return;
+  }
+  const int stride = blockDim.x;
+  int64_t* c = sacc + threadIdx.x;
+  for (int d = 0; d < nd; ++d) c[d * stride] = 0;
+  bool errp = false;
+  auto term = [&](const Num<W>& a, const Num<W>& xv) {
+    const uint32_t off = (uint32_t)(a.e + xv.e - emin), q = off / kR;
+    add_product_cols_top<W, G>(c, stride, a.m, xv.m, (int)q - wb, off - kR * q, a.s ^ xv.s, errp);
+  };
+  if (PIPE) {
+    Num<W> an, xn;
+    int32_t c1 = 0;
+    if (len > 0) {
+      const int32_t c0 = S.col[base];
+      if (len > 1) c1 = S.col[base + 32];
+      load<W>(an, S.val, S.nslots, base);
+      gather_x<W>(xn, S, x, ldx, c0);
+    }
+    for (int32_t j = 0; j < len; ++j) {
+      const Num<W> a = an, xv = xn;
+      if (j + 1 < len) {
+        const int64_t k1 = base + (int64_t)(j + 1) * 32;
+        const int32_t cn = c1;
+        if (j + 2 < len) c1 = S.col[k1 + 32];
+        load<W>(an, S.val, S.nslots, k1);
+        gather_x<W>(xn, S, x, ldx, cn);
+      }
+      if (zero_e(a.e) || zero_e(xv.e)) continue;
+      term(a, xv);
+    }
+  } else {
+    for (int32_t j = 0; j < len; ++j) {
+      const int64_t k = base + (int64_t)j * 32;
+      Num<W> a, xv;
+      load<W>(a, S.val, S.nslots, k);
+      gather_x<W>(xv, S, x, ldx, S.col[k]);
+      if (zero_e(a.e) || zero_e(xv.e)) continue;
+      term(a, xv);
+    }
+  }
+  int nw = 0;
+  const uint32_t negative = resolve_cols(c, stride, nd, &nw);
+  int t = nw - 1;
+  while (t >= 0 && (uint32_t)c[t * stride] == 0u) --t;
+  if (t < 0) {  // the window sums to zero: exact only if nothing was skipped
+    if (errp) {
+      to_exact_path();
+    } else {
+      set_zero(r, 0u);
+      store<W>(r, y, ldy, row);
+    }
+    return;
+  }
+  if (errp) {
+    // skipped columns: each < 2^35 at the window's scale, at most 73 per term
+    const int64_t eb = 42 + (32 - __clz((uint32_t)len));
+    const int64_t nb = 32 * (int64_t)t + (32 - __clz((uint32_t)c[t * stride]));
+    if (!guard_bits_decide(c, stride, nw, eb, nb - 32 * W - 1)) {
+      to_exact_path();
+      return;
+    }
+  }
+  round_words<W>(c, stride, nw, emin - 64 * W + (int64_t)kR * wb, negative, r);
+  store<W>(r, y, ldy, row);
+}
+
 // Rows from the overflow list: one warp per row, lanes over the row's
 // entries, a shared window of the full span cap filled with atomics.
 template <int W, bool RESID>
@@ -493,13 +637,27 @@ __global__ void __launch_bounds__(32) spmv_exact_wide_kernel(
   }
 }
 
-// Operand of the tuner: x_i = (-1)^i (1 + (i mod 997) 2^-12), nonzero.
+// Operand of the tuner: nonzero x_i with every mantissa word drawn from an
+// integer hash of (i, word) (top bit set), a random sign and an exponent in
+// [-8, 8], so that the timed products carry full-width operands.
+__device__ __forceinline__ uint32_t tune_hash(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return (uint32_t)(z ^ (z >> 31));
+}
+
 template <int W>
 __global__ void tune_fill_kernel(uint64_t* x, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     Num<W> v;
-    from_f64<W>(((i & 1) ? -1.0 : 1.0) * (1.0 + (double)(i % 997) * (1.0 / 4096.0)), v);
+#pragma unroll
+    for (int k = 0; k < W; ++k) v.m[k] = tune_hash((uint64_t)i * 64 + k);
+    v.m[W - 1] |= 0x80000000u;
+    const uint32_t h = tune_hash((uint64_t)i * 64 + 63);
+    v.e = (int64_t)(h % 17u) - 8;
+    v.s = (h >> 16) & 1u;
     store<W>(v, x, n, i);
   }
 }
@@ -590,7 +748,10 @@ mp_status spmv_w(const mp_csr_s* M, const Sell& S, int mode, const uint64_t* x, 
   if (!status) return set_error(MP_ERR_CUDA, "status word unavailable");
   MPK_CUDA(cudaMemsetAsync(M->ovf, 0, sizeof(int32_t), st));
   const bool cols = cf.cols;
-  const size_t smem = (size_t)(cols ? Win<W>::fast_cols : Win<W>::fast) * tpb * sizeof(int64_t);
+  // the windowed form serves y = A x only; the residual keeps the full window
+  const bool top = cf.top && !b;
+  const size_t smem = (size_t)(top ? Win<W>::top_cols : cols ? Win<W>::fast_cols : Win<W>::fast) *
+                     tpb * sizeof(int64_t);
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -610,7 +771,26 @@ mp_status spmv_w(const mp_csr_s* M, const Sell& S, int mode, const uint64_t* x, 
     spmv_exact_wide_kernel<W, true><<<sms * 4, 32, 0, st>>>(V, x, ldx, y, ldy, b, ldb, M->ovf, gate);
   } else {
     const bool stage = cf.stage, wide = cf.wide;
-    if (!cols)
+    auto launch_top = [&](auto kern) -> mp_status {
+      MPK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      MPK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                    cf.carve < 0 ? (int)cudaSharedmemCarveoutDefault : cf.carve));
+      kern<<<blocks, tpb, smem, st>>>(V, x, ldx, y, ldy, M->ovf, status, gate);
+      return MP_OK;
+    };
+    bool launched = false;
+    if constexpr (W >= 16) {
+      if (top) {
+        r = stage ? (wide ? launch_top(spmv_exact_top_kernel<W, true, 16>)
+                          : launch_top(spmv_exact_top_kernel<W, true, 8>))
+                  : (wide ? launch_top(spmv_exact_top_kernel<W, false, 16>)
+                          : launch_top(spmv_exact_top_kernel<W, false, 8>));
+        launched = true;
+      }
+    }
+    if (launched)
+      ;
+    else if (!cols)
       r = exact(spmv_exact_kernel<W, false, false>, nullptr);
     else if (stage && wide)
       r = exact(spmv_exact_kernel<W, false, true, true, 16>, nullptr);
@@ -685,7 +865,7 @@ mp_status mp_csr_set_config(mp_csr A, int32_t mode, int32_t tpb, int32_t variant
   if (mode != MP_ORDERED && mode != MP_EXACT) return set_error(MP_ERR_ARG, "mode %d", mode);
   if (tpb != -1 && tpb != 32 && tpb != 64 && tpb != 128 && tpb != 256)
     return set_error(MP_ERR_ARG, "threads per block %d not in {-1,32,64,128,256}", tpb);
-  if (variant < -1 || variant > 15) return set_error(MP_ERR_ARG, "variant %d not in -1..15", variant);
+  if (variant < -1 || variant > 31) return set_error(MP_ERR_ARG, "variant %d not in -1..31", variant);
   if (carveout < -1 || carveout > 100) return set_error(MP_ERR_ARG, "carve-out %d", carveout);
   A->cfg_tpb[mode] = tpb;
   A->cfg_var[mode] = variant;
@@ -701,7 +881,7 @@ mp_status mp_csr_get_config(mp_csr A, int32_t mode, int32_t* tpb, int32_t* varia
   if (tpb) *tpb = c.tpb;
   if (variant)
     *variant = (c.cols ? kVarCols : 0) | (c.stage ? kVarStage : 0) | (c.wide ? kVarWide : 0) |
-               (c.rec ? kVarRec : 0);
+               (c.rec ? kVarRec : 0) | (c.top ? kVarTop : 0);
   if (carveout) *carveout = c.carve;
   return MP_OK;
 }
@@ -735,7 +915,7 @@ mp_status mp_csr_tune(mp_csr A, int32_t mode, int32_t reps, int32_t* tpb_out, in
   // ORDERED: both product forms, staging for p <= 512; EXACT: the word
   // form, and the column form with and without staging, 8 or 16 columns at
   // a time, each under four shared-memory carve-outs
-  int32_t vars[8], carves[4] = {-1, 25, 50, 75};
+  int32_t vars[12], carves[4] = {-1, 25, 50, 75};
   int nvar = 0, ncarve = mode == MP_EXACT ? 4 : 1;
   if (mode == MP_ORDERED) {
     for (int32_t v = 0; v <= (kVarCols | kVarStage); v += (A->prec > 512 ? kVarCols : 1))
@@ -747,6 +927,10 @@ mp_status mp_csr_tune(mp_csr A, int32_t mode, int32_t reps, int32_t* tpb_out, in
     for (int32_t v : {kVarCols, kVarCols | kVarStage, kVarCols | kVarWide,
                       kVarCols | kVarStage | kVarWide})
       vars[nvar++] = v;
+    if (A->prec >= 512) {  // the windowed form
+      vars[nvar++] = kVarTop | kVarCols;
+      vars[nvar++] = kVarTop | kVarCols | kVarStage;
+    }
   }
   // the same gathering x from its record copy, for the default form
   {
@@ -754,7 +938,8 @@ mp_status mp_csr_tune(mp_csr A, int32_t mode, int32_t reps, int32_t* tpb_out, in
     A->cfg_var[mode] = -1;
     const LaunchCfg d = launch_cfg(A, mode, A->prec / 32);
     A->cfg_var[mode] = saved;
-    const int32_t dv = (d.cols ? kVarCols : 0) | (d.stage ? kVarStage : 0) | (d.wide ? kVarWide : 0);
+    const int32_t dv = (d.cols ? kVarCols : 0) | (d.stage ? kVarStage : 0) |
+                       (d.wide ? kVarWide : 0) | (d.top ? kVarTop : 0);
     bool listed = false;
     for (int i = 0; i < nvar; ++i) listed = listed || vars[i] == dv;
     if (!listed) vars[nvar++] = dv;

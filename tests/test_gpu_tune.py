@@ -28,7 +28,7 @@ def test_every_configuration_matches_the_oracle(p):
         want, st = oracle.spmv(p, m, rowptr, colidx, recs(V), recs(X))
         want_t, _ = oracle.spmv_t(p, m, rowptr, colidx, recs(V), recs(X))
         for tpb, carve in ((32, -1), (64, 25), (128, 50), (256, 75), (-1, -1)):
-            for v in (0, 1, 2, 3, 6, 7, 9, 11, 15, -1):
+            for v in (0, 1, 2, 3, 6, 7, 9, 11, 15, 18, 19, 27, -1):
                 A.set_config(name, tpb, v, carve)
                 got = A.get_config(name)
                 if tpb > 0:
@@ -41,7 +41,7 @@ def test_every_configuration_matches_the_oracle(p):
                         capped = 4 if (v & 4 and (tpb if tpb > 0 else 128) <= 128) else 0
                         assert got["variant"] == (v & 3 if p <= 512 else v & 2) | capped | (v & 8)
                     elif v & 2:
-                        assert got["variant"] == v
+                        assert got["variant"] == (v if p >= 512 else v & ~16)
                 what = f"{name} p={p} tpb={tpb} variant={v} carveout={carve}"
                 assert_bitwise(mpk.spmv(A, x, mode=name).planes(), want, what)
                 assert_bitwise(mpk.spmv_t(A, x, mode=name).planes(), want_t, "T " + what)
@@ -51,7 +51,7 @@ def test_bad_configuration_is_rejected():
     mpk = need_gpu()
     rowptr, colidx = random_csr(64, seed=2)
     A = mpk.CSR(rowptr, colidx, np.ones(len(colidx)), 128)
-    for args in (("ordered", 96, -1, -1), ("ordered", 128, 16, -1), ("exact", 512, -1, -1),
+    for args in (("ordered", 96, -1, -1), ("ordered", 128, 32, -1), ("exact", 512, -1, -1),
                  ("exact", 64, -2, -1), ("exact", 64, 0, 101)):
         with pytest.raises(mpk.MPError):
             A.set_config(*args)
@@ -78,7 +78,7 @@ def test_tuner_and_cache(p, tmp_path):
         assert r["threads_per_block"] in (32, 64, 128, 256)
         assert A.get_config(name)["threads_per_block"] == r["threads_per_block"]
         base = {"ordered": ((0, 1, 2, 3, 5, 7) if p <= 512 else (0, 2, 6)),
-                "exact": (0, 1, 2, 3, 6, 7)}[name]
+                "exact": (0, 1, 2, 3, 6, 7) + ((18, 19) if p >= 512 else ())}[name]
         assert r["variant"] in set(base) | {v | 8 for v in base}
         want, _ = oracle.spmv(p, m, rowptr, colidx, recs(V), recs(X))
         assert_bitwise(mpk.spmv(A, x, mode=name).planes(), want, f"tuned {name} p={p}")
@@ -91,11 +91,13 @@ def test_tuner_and_cache(p, tmp_path):
 
 
 @pytest.mark.parametrize("p", (128, 256, 512, 1024))
-@pytest.mark.parametrize("variant", (0, 2, 3, 6, 7))
+@pytest.mark.parametrize("variant", (0, 2, 3, 6, 7, 19, 23, 27))
 def test_exact_variants_on_hard_rows(p, variant):
-    """Both EXACT product forms on rows whose spans sit around the per-thread
-    window (in it, just beyond it: the warp-per-row path), beyond the span
-    cap, with exact cancellation, and in the residual with its b term."""
+    """Both EXACT product forms, and the windowed form (bit 4, p >= 512), on
+    rows whose spans sit around the per-thread window (in it, just beyond it:
+    the warp-per-row path), beyond the span cap, with exact cancellation (the
+    windowed form then hands the row to the exact path), and in the residual
+    with its b term."""
     mpk = need_gpu()
     from paper_1411_2377_gb300 import synth
 
@@ -178,3 +180,45 @@ def test_ordered_products_round_ties_to_even(p):
     for v in (0, 2):
         A.set_config("ordered", 128, v, -1)
         assert_bitwise(mpk.spmv(A, x, mode="ordered").planes(), want, f"ties variant={v} p={p}")
+
+
+@pytest.mark.parametrize("p", (512, 1024))
+def test_windowed_exact_on_cancelling_and_integer_rows(p):
+    """The windowed EXACT form against the oracle where its window cannot
+    decide alone: near and exact cancellation of the largest terms, and
+    integer-valued rows whose skipped columns are provably zero."""
+    mpk = need_gpu()
+    from paper_1411_2377_gb300 import synth
+
+    n = 400
+    rowptr, colidx = random_csr(n, seed=p + 77, mean_len=10, max_len=30)
+    V = rand_planes(len(colidx), p, 71, zero_frac=0.0, emin=-40, emax=40)
+    X = rand_planes(n, p, 72, zero_frac=0.0, emin=-40, emax=40)
+    Vr, Xr = recs(V), recs(X)
+    # rows 0..99: the second entry cancels the first (same x, negated a) or
+    # nearly (a with its last bit flipped)
+    for r in range(100):
+        k0, k1 = rowptr[r], rowptr[r + 1]
+        if k1 - k0 < 2:
+            continue
+        Xr[colidx[k0 + 1]] = Xr[colidx[k0]]
+        Vr[k0 + 1] = Vr[k0]
+        Vr[k0 + 1, 0] ^= np.uint64(1)
+        if r % 2:
+            Vr[k0 + 1, 1] ^= np.uint64(1)
+    A = mpk.CSR(rowptr, colidx, synth.records_to_planes(Vr), p)
+    x = mpk.Vec.from_planes(synth.records_to_planes(Xr), p)
+    want, _ = oracle.spmv(p, oracle.EXACT, rowptr, colidx, Vr, Xr)
+    for v in (18, 19, 26, 27):
+        A.set_config("exact", 128, v, -1)
+        assert_bitwise(mpk.spmv(A, x, mode="exact").planes(), want, f"windowed v={v} p={p}")
+    # integers: a_ij in 1..9, x_j in 1..99 (exact products, skipped columns zero)
+    ai = 1.0 + (np.arange(len(colidx)) % 9)
+    xi = 1.0 + (np.arange(n) % 99)
+    B = mpk.CSR(rowptr, colidx, ai, p)
+    xb = mpk.Vec.from_f64(xi, p)
+    wi, _ = oracle.spmv(p, oracle.EXACT, rowptr, colidx, oracle.from_f64(p, ai),
+                        oracle.from_f64(p, xi))
+    for v in (18, 27):
+        B.set_config("exact", 128, v, -1)
+        assert_bitwise(mpk.spmv(B, xb, mode="exact").planes(), wi, f"integers v={v} p={p}")
