@@ -666,7 +666,8 @@ def solver_bench(mpk):
     ones = mpk.Vec.from_f64(np.ones(n), p)
     b = mpk.spmv(A, ones, mode="exact")
     out = {"workload": "stencil2d_64x64_p128_rtol1e-30"}
-    for name, fn in (("gpbicg", mpk.gpbicg), ("bicg", mpk.bicg)):
+    for name, fn in (("gpbicg", mpk.gpbicg), ("bicg", mpk.bicg), ("cgs", mpk.cgs),
+                     ("bicgstab", mpk.bicgstab)):
         fn(A, b, rtol=1e-30, maxit=2000, poll_every=32)  # warm-up
         x, info = fn(A, b, rtol=1e-30, maxit=2000, poll_every=32)
         err = float((x.to_f64() - 1).abs().max())

@@ -67,6 +67,22 @@ __device__ __forceinline__ void load(Num<W>& a, const uint64_t* __restrict__ bas
   load_limbs<W>(a.m, base, ld, i);
 }
 
+// As load, for data read once (a matrix's limbs): the limb words are loaded
+// with the streaming (evict-first) cache hint so that they do not push
+// reusable data (the gathered x) out of L2; the head keeps the normal path
+// (EXACT reads it twice).
+template <int W>
+__device__ __forceinline__ void load_stream(Num<W>& a, const uint64_t* __restrict__ base,
+                                            int64_t ld, int64_t i) {
+  unpack_head(__ldg(base + i), a.e, a.s);
+#pragma unroll
+  for (int k = 0; k < W / 2; ++k) {
+    const uint64_t l = __ldcs(base + (int64_t)(k + 1) * ld + i);
+    a.m[2 * k] = (uint32_t)l;
+    a.m[2 * k + 1] = (uint32_t)(l >> 32);
+  }
+}
+
 template <int W>
 __device__ __forceinline__ void store(const Num<W>& a, uint64_t* __restrict__ base, int64_t ld,
                                       int64_t i) {

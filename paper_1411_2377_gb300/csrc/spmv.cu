@@ -216,7 +216,7 @@ __device__ __forceinline__ void ordered_rows(const SellView& S, const uint64_t* 
     if (len > 0) {
       const int32_t c0 = S.col[base];
       if (len > 1) c1 = S.col[base + 32];
-      load<W>(an, S.val, S.nslots, base);
+      load_stream<W>(an, S.val, S.nslots, base);
       gather_x<W>(xn, S, x, ldx, c0);
     }
     for (int32_t j = 0; j < len; ++j) {
@@ -225,7 +225,7 @@ __device__ __forceinline__ void ordered_rows(const SellView& S, const uint64_t* 
         const int64_t k1 = base + (int64_t)(j + 1) * 32;
         const int32_t c = c1;
         if (j + 2 < len) c1 = S.col[k1 + 32];
-        load<W>(an, S.val, S.nslots, k1);
+        load_stream<W>(an, S.val, S.nslots, k1);
         gather_x<W>(xn, S, x, ldx, c);
       }
       if (zero_e(a.e) || zero_e(xv.e)) continue;  // zero fast path
@@ -242,7 +242,7 @@ __device__ __forceinline__ void ordered_rows(const SellView& S, const uint64_t* 
       const int64_t k = base + (int64_t)j * 32;
       const int32_t c = S.col[k];
       Num<W> a, xv;
-      load<W>(a, S.val, S.nslots, k);
+      load_stream<W>(a, S.val, S.nslots, k);
       gather_x<W>(xv, S, x, ldx, c);
       if (zero_e(a.e) || zero_e(xv.e)) continue;  // zero fast path
       Num<W> t, s;
@@ -387,7 +387,7 @@ __global__ void __launch_bounds__(256) spmv_exact_kernel(
     if (len > 0) {
       const int32_t c0 = S.col[base];
       if (len > 1) c1 = S.col[base + 32];
-      load<W>(an, S.val, S.nslots, base);
+      load_stream<W>(an, S.val, S.nslots, base);
       gather_x<W>(xn, S, x, ldx, c0);
     }
     for (int32_t j = 0; j < len; ++j) {
@@ -396,7 +396,7 @@ __global__ void __launch_bounds__(256) spmv_exact_kernel(
         const int64_t k1 = base + (int64_t)(j + 1) * 32;
         const int32_t cn = c1;
         if (j + 2 < len) c1 = S.col[k1 + 32];
-        load<W>(an, S.val, S.nslots, k1);
+        load_stream<W>(an, S.val, S.nslots, k1);
         gather_x<W>(xn, S, x, ldx, cn);
       }
       if (zero_e(a.e) || zero_e(xv.e)) continue;
@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(256) spmv_exact_kernel(
       const int64_t k = base + (int64_t)j * 32;
       const int32_t col = S.col[k];
       Num<W> a, xv;
-      load<W>(a, S.val, S.nslots, k);
+      load_stream<W>(a, S.val, S.nslots, k);
       gather_x<W>(xv, S, x, ldx, col);
       if (zero_e(a.e) || zero_e(xv.e)) continue;
       term(a, xv, a.s ^ xv.s ^ (RESID ? 1u : 0u));
@@ -510,7 +510,7 @@ __global__ void __launch_bounds__(256) spmv_exact_top_kernel(
     if (len > 0) {
       const int32_t c0 = S.col[base];
       if (len > 1) c1 = S.col[base + 32];
-      load<W>(an, S.val, S.nslots, base);
+      load_stream<W>(an, S.val, S.nslots, base);
       gather_x<W>(xn, S, x, ldx, c0);
     }
     for (int32_t j = 0; j < len; ++j) {
@@ -519,7 +519,7 @@ __global__ void __launch_bounds__(256) spmv_exact_top_kernel(
         const int64_t k1 = base + (int64_t)(j + 1) * 32;
         const int32_t cn = c1;
         if (j + 2 < len) c1 = S.col[k1 + 32];
-        load<W>(an, S.val, S.nslots, k1);
+        load_stream<W>(an, S.val, S.nslots, k1);
         gather_x<W>(xn, S, x, ldx, cn);
       }
       if (zero_e(a.e) || zero_e(xv.e)) continue;
@@ -529,7 +529,7 @@ __global__ void __launch_bounds__(256) spmv_exact_top_kernel(
     for (int32_t j = 0; j < len; ++j) {
       const int64_t k = base + (int64_t)j * 32;
       Num<W> a, xv;
-      load<W>(a, S.val, S.nslots, k);
+      load_stream<W>(a, S.val, S.nslots, k);
       gather_x<W>(xv, S, x, ldx, S.col[k]);
       if (zero_e(a.e) || zero_e(xv.e)) continue;
       term(a, xv);
