@@ -880,7 +880,7 @@ __device__ __forceinline__ void add_product_cols_top(int64_t* c, int stride, con
   uint32_t al[NA], xl[NX];
   cut_limbs<W, NA>(a, al);
   cut_limbs_shifted<W, NX>(x, s, xl);
-  if (kmin > 0) {
+  if (kmin > 0 && !errp) {  // once a skipped column may be nonzero, the row is checked anyway
     int la = NA, lx = NX;
 #pragma unroll
     for (int i = NA - 1; i >= 0; --i) la = al[i] ? i : la;
