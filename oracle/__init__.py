@@ -61,6 +61,10 @@ def _load():
                     ctypes.c_double, ctypes.c_double, _i64, _i64p, _u64p],
         "mpo_bicgstab": [_i32, _i32, _i64, _i64p, _i32p, _u64p, _u64p, _u64p,
                          ctypes.c_double, ctypes.c_double, _i64, _i64p, _u64p],
+        "mpo_bicgstab_ilu0": [_i32, _i32, _i64, _i64p, _i32p, _u64p, _u64p, _u64p,
+                              ctypes.c_double, ctypes.c_double, _i64, _i64p, _u64p],
+        "mpo_ilu0": [_i32, _i64, _i64p, _i32p, _u64p, _u64p],
+        "mpo_ilu0_apply": [_i32, _i64, _i64p, _i32p, _u64p, _u64p, _u64p],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -219,3 +223,30 @@ def cgs(p, mode, rowptr, colidx, vals, b, x0, rtol, atol, maxit):
 def bicgstab(p, mode, rowptr, colidx, vals, b, x0, rtol, atol, maxit):
     """BiCGSTAB (textbook form).  Returns (x, iterations, status, history of (r_i, r_i))."""
     return _solve(_load().mpo_bicgstab, p, mode, rowptr, colidx, vals, b, x0, rtol, atol, maxit)
+
+
+def ilu0(p, rowptr, colidx, vals):
+    """ILU(0) factors in A's CSR order (records).  Returns (lu, status)."""
+    rowptr, colidx = _csr(rowptr, colidx)
+    vals = _recs(vals, p)
+    lu = np.empty_like(vals)
+    st = _load().mpo_ilu0(p, rowptr.shape[0] - 1, _p(rowptr, _i64p), _p(colidx, _i32p),
+                          _p(vals, _u64p), _p(lu, _u64p))
+    return lu, st
+
+
+def ilu0_apply(p, rowptr, colidx, lu, r):
+    """w = (LU)^{-1} r.  Returns (w, status)."""
+    rowptr, colidx = _csr(rowptr, colidx)
+    lu, r = _recs(lu, p), _recs(r, p)
+    w = np.empty_like(r)
+    st = _load().mpo_ilu0_apply(p, rowptr.shape[0] - 1, _p(rowptr, _i64p), _p(colidx, _i32p),
+                                _p(lu, _u64p), _p(r, _u64p), _p(w, _u64p))
+    return w, st
+
+
+def bicgstab_ilu0(p, mode, rowptr, colidx, vals, b, x0, rtol, atol, maxit):
+    """BiCGSTAB right-preconditioned with ILU(0).  Returns (x, iterations,
+    status, history of (r_i, r_i))."""
+    return _solve(_load().mpo_bicgstab_ilu0, p, mode, rowptr, colidx, vals, b, x0, rtol, atol,
+                  maxit)

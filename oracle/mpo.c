@@ -1354,3 +1354,227 @@ done:
   free(t);
   return st;
 }
+
+/* ------------------------------------------------------------------------ */
+/* ILU(0) preconditioning (Section 4's BiCGSTAB+ILU(0) rows; the paper prints
+ * no algorithm, the textbook IKJ form is taken, Saad, Alg. 10.4).  The factors
+ * share A's pattern: L (unit lower, the entries left of the diagonal) and U
+ * (the diagonal and right of it) overwrite a copy of A's values in CSR order.
+ * For each row i, for each stored (i, k) with k < i in ascending k:
+ *   a_ik = RN(a_ik / a_kk);
+ *   for each stored (i, j) with j > k in ascending j, if (k, j) is stored:
+ *     a_ij = RN(a_ij - RN(a_ik a_kj)).
+ * Every operation is rounded; no product is skipped.  A missing or zero
+ * pivot a_kk returns MPO_ERR_DIVZERO. */
+
+static int64_t row_find(const int64_t *rowptr, const int32_t *colidx, int64_t i, int32_t j) {
+  for (int64_t k = rowptr[i]; k < rowptr[i + 1]; k++)
+    if (colidx[k] == j) return k;
+  return -1;
+}
+
+int mpo_ilu0(int p, int64_t n, const int64_t *rowptr, const int32_t *colidx,
+             const uint64_t *vals, uint64_t *lu) {
+  if (!prec_ok(p)) return MPO_ERR_PREC;
+  if (csr_check(n, rowptr, colidx)) return MPO_ERR_ARG;
+  if (vcheck(vals, rowptr[n], p)) return MPO_ERR_ARG;
+  size_t rl = (size_t)(p / 64 + 1);
+  memcpy(lu, vals, sizeof(uint64_t) * rl * (size_t)rowptr[n]);
+  for (int64_t i = 0; i < n; i++) {
+    for (int64_t ik = rowptr[i]; ik < rowptr[i + 1] && colidx[ik] < i; ik++) {
+      const int32_t k = colidx[ik];
+      const int64_t kk = row_find(rowptr, colidx, k, k);
+      if (kk < 0) return MPO_ERR_DIVZERO;
+      num akk, aik, q;
+      vload(lu, kk, p, &akk);
+      if (akk.zero) return MPO_ERR_DIVZERO;
+      vload(lu, ik, p, &aik);
+      num_div(&aik, &akk, p, &q); /* l_ik = a_ik / u_kk */
+      vstore(lu, ik, p, &q);
+      for (int64_t ij = ik + 1; ij < rowptr[i + 1]; ij++) {
+        const int64_t kj = row_find(rowptr, colidx, k, colidx[ij]);
+        if (kj < 0) continue;
+        num akj, aij, t, u;
+        vload(lu, kj, p, &akj);
+        vload(lu, ij, p, &aij);
+        num_mul(&q, &akj, p, &t);
+        num_sub(&aij, &t, p, &u); /* a_ij = a_ij - l_ik u_kj */
+        vstore(lu, ij, p, &u);
+      }
+    }
+  }
+  return MPO_OK;
+}
+
+/* w = (LU)^{-1} r with the factors of mpo_ilu0: forward, y_i = r_i minus the
+ * rounded products l_ik y_k (k < i, ascending), one rounding per step; then
+ * backward from the last row, w_i = RN((y_i minus u_ik w_k, k > i
+ * ascending) / u_ii).  Returns MPO_ERR_DIVZERO on a zero or missing u_ii. */
+static int ilu0_apply(int p, int64_t n, const int64_t *rowptr, const int32_t *colidx,
+                      const uint64_t *lu, const uint64_t *r, uint64_t *w) {
+  for (int64_t i = 0; i < n; i++) { /* forward, into w */
+    num acc, l, y, t, u;
+    vload(r, i, p, &acc);
+    for (int64_t k = rowptr[i]; k < rowptr[i + 1] && colidx[k] < i; k++) {
+      vload(lu, k, p, &l);
+      vload(w, colidx[k], p, &y);
+      num_mul(&l, &y, p, &t);
+      num_sub(&acc, &t, p, &u);
+      acc = u;
+    }
+    vstore(w, i, p, &acc);
+  }
+  for (int64_t i = n - 1; i >= 0; i--) { /* backward, in place */
+    num acc, a, z, t, u, d;
+    int64_t dk = -1;
+    vload(w, i, p, &acc);
+    for (int64_t k = rowptr[i]; k < rowptr[i + 1]; k++) {
+      if (colidx[k] == i) dk = k;
+      if (colidx[k] <= i) continue;
+      vload(lu, k, p, &a);
+      vload(w, colidx[k], p, &z);
+      num_mul(&a, &z, p, &t);
+      num_sub(&acc, &t, p, &u);
+      acc = u;
+    }
+    if (dk < 0) return MPO_ERR_DIVZERO;
+    vload(lu, dk, p, &d);
+    if (d.zero) return MPO_ERR_DIVZERO;
+    num_div(&acc, &d, p, &u);
+    vstore(w, i, p, &u);
+  }
+  return MPO_OK;
+}
+
+int mpo_ilu0_apply(int p, int64_t n, const int64_t *rowptr, const int32_t *colidx,
+                   const uint64_t *lu, const uint64_t *r, uint64_t *w) {
+  if (!prec_ok(p)) return MPO_ERR_PREC;
+  if (csr_check(n, rowptr, colidx)) return MPO_ERR_ARG;
+  if (vcheck(lu, rowptr[n], p) || vcheck(r, n, p)) return MPO_ERR_ARG;
+  return ilu0_apply(p, n, rowptr, colidx, lu, r, w);
+}
+
+/* BiCGSTAB with ILU(0) as a right preconditioner M = LU (the preconditioned
+ * BiCGSTAB of Barrett et al., Templates for the Solution of Linear Systems):
+ * as mpo_bicgstab with p^ = M^{-1} p and s^ = M^{-1} s,
+ *   v = A p^,  t = A s^,  x = x + alpha p^ + omega s^;
+ * r stays the residual b - A x of the unpreconditioned system, so the
+ * stopping rule is unchanged.  A zero pivot of the factorization returns
+ * MPO_ERR_DIVZERO before the first iteration. */
+int mpo_bicgstab_ilu0(int p, int mode, int64_t n, const int64_t *rowptr,
+                      const int32_t *colidx, const uint64_t *vals, const uint64_t *b,
+                      uint64_t *x, double rtol, double atol, int64_t maxit,
+                      int64_t *iters, uint64_t *hist) {
+  int st = solve_args(p, mode, n, rowptr, colidx, vals, b, x, rtol, atol, maxit);
+  *iters = 0;
+  if (st) return st;
+  sysA s = {p, mode, n, rowptr, colidx, vals, (size_t)(p / 64 + 1)};
+  uint64_t *lu = (uint64_t *)malloc(sizeof(uint64_t) * s.rl * (size_t)(rowptr[n] > 0 ? rowptr[n] : 1));
+  if (!lu) die("out of memory");
+  uint64_t *r = vnew(&s), *rt = vnew(&s), *pv = vnew(&s), *ph = vnew(&s), *v = vnew(&s);
+  uint64_t *sv = vnew(&s), *sh = vnew(&s), *t = vnew(&s);
+  num rr0, rr, thr, rho, rho_prev, alpha, beta, omega, d, tt, ts, t1, t2;
+  set_zero(&omega, 0);
+  set_zero(&alpha, 0);
+  st = mpo_ilu0(p, n, rowptr, colidx, vals, lu);
+  if (st) goto done;
+  st = residual_vec(p, n, rowptr, colidx, vals, b, x, r); /* r0 = b - A x0 */
+  if (st) goto done;
+  vcopy(&s, rt, r);
+  sdot(&s, r, r, &rr0);
+  conv_threshold(p, rtol, atol, &rr0, &thr);
+  if (num_cmp(&rr0, &thr, p) <= 0) {
+    st = MPO_OK;
+    goto done;
+  }
+  sdot(&s, rt, r, &rho);
+  st = MPO_ERR_NOCONV;
+  for (int64_t i = 1; i <= maxit; i++) {
+    if (rho.zero) {
+      st = MPO_ERR_BREAKDOWN;
+      break;
+    }
+    if (i == 1) {
+      vcopy(&s, pv, r);
+    } else {
+      num_div(&rho, &rho_prev, p, &t1);
+      num_div(&alpha, &omega, p, &t2);
+      num_mul(&t1, &t2, p, &beta);
+      for (int64_t k = 0; k < n; k++) {
+        num rk, pk, vk, a1, a2, a3;
+        vload(r, k, p, &rk);
+        vload(pv, k, p, &pk);
+        vload(v, k, p, &vk);
+        num_mul(&omega, &vk, p, &a1);
+        num_sub(&pk, &a1, p, &a2);
+        num_mul(&beta, &a2, p, &a3);
+        num_add(&rk, &a3, p, &a1); /* p = r + beta (p - omega v) */
+        vstore(pv, k, p, &a1);
+      }
+    }
+    if ((st = ilu0_apply(p, n, rowptr, colidx, lu, pv, ph)) != MPO_OK) break; /* p^ */
+    matvec(&s, rowptr, colidx, vals, ph, v); /* v = A p^ */
+    sdot(&s, rt, v, &d);
+    if (d.zero) {
+      st = MPO_ERR_BREAKDOWN;
+      break;
+    }
+    num_div(&rho, &d, p, &alpha);
+    for (int64_t k = 0; k < n; k++) {
+      num rk, vk, a1, sk;
+      vload(r, k, p, &rk);
+      vload(v, k, p, &vk);
+      num_mul(&alpha, &vk, p, &a1);
+      num_sub(&rk, &a1, p, &sk); /* s = r - alpha v */
+      vstore(sv, k, p, &sk);
+    }
+    if ((st = ilu0_apply(p, n, rowptr, colidx, lu, sv, sh)) != MPO_OK) break; /* s^ */
+    matvec(&s, rowptr, colidx, vals, sh, t); /* t = A s^ */
+    sdot(&s, t, sv, &ts);
+    sdot(&s, t, t, &tt);
+    if (tt.zero)
+      set_zero(&omega, 0);
+    else
+      num_div(&ts, &tt, p, &omega);
+    for (int64_t k = 0; k < n; k++) {
+      num xk, pk, sk, shk, tk, a1, a2, a3;
+      vload(x, k, p, &xk);
+      vload(ph, k, p, &pk);
+      vload(sh, k, p, &shk);
+      vload(sv, k, p, &sk);
+      vload(t, k, p, &tk);
+      num_mul(&alpha, &pk, p, &a1);
+      num_add(&xk, &a1, p, &a2);
+      num_mul(&omega, &shk, p, &a1);
+      num_add(&a2, &a1, p, &a3); /* x = x + alpha p^ + omega s^ */
+      vstore(x, k, p, &a3);
+      num_mul(&omega, &tk, p, &a1);
+      num_sub(&sk, &a1, p, &a2); /* r = s - omega t */
+      vstore(r, k, p, &a2);
+    }
+    *iters = i;
+    sdot(&s, r, r, &rr);
+    if (hist) rec_store(&rr, p, hist + (size_t)(i - 1) * s.rl);
+    rho_prev = rho;
+    sdot(&s, rt, r, &rho);
+    if (num_cmp(&rr, &thr, p) <= 0) {
+      st = MPO_OK;
+      break;
+    }
+    if (omega.zero) {
+      st = MPO_ERR_BREAKDOWN;
+      break;
+    }
+  }
+done:
+  free(lu);
+  free(r);
+  free(rt);
+  free(pv);
+  free(ph);
+  free(v);
+  free(sv);
+  free(sh);
+  free(t);
+  return st;
+}

@@ -239,3 +239,98 @@ def bicgstab(rows, b, x, p, mode, rtol, maxit):
         if omega.q == 0:
             return x, i, "breakdown", hist
     return x, maxit, "noconv", hist
+
+
+def ilu0(rows, p):
+    """ILU(0) in the textbook IKJ order; rows: list of [(col, Val)] sorted by
+    column.  Returns the factor rows (L left of the diagonal, U from it)."""
+    lu = [list(r) for r in rows]
+    pos = [{c: k for k, (c, _) in enumerate(r)} for r in lu]
+    for i, row in enumerate(lu):
+        for a in range(len(row)):
+            k = row[a][0]
+            if k >= i:
+                break
+            ukk = lu[k][pos[k][k]][1]
+            q = exact.rdiv(row[a][1], ukk, p)
+            row[a] = (k, q)
+            for b in range(a + 1, len(row)):
+                j = row[b][0]
+                if j in pos[k]:
+                    ukj = lu[k][pos[k][j]][1]
+                    row[b] = (j, exact.rsub(row[b][1], exact.rmul(q, ukj, p), p))
+    return lu
+
+
+def ilu0_apply(lu, r, p):
+    """w = (LU)^{-1} r: forward over rows, then backward from the last row."""
+    n = len(lu)
+    w = [None] * n
+    for i in range(n):
+        acc = r[i]
+        for c, v in lu[i]:
+            if c >= i:
+                break
+            acc = exact.rsub(acc, exact.rmul(v, w[c], p), p)
+        w[i] = acc
+    for i in range(n - 1, -1, -1):
+        acc = w[i]
+        d = None
+        for c, v in lu[i]:
+            if c == i:
+                d = v
+            elif c > i:
+                acc = exact.rsub(acc, exact.rmul(v, w[c], p), p)
+        w[i] = exact.rdiv(acc, d, p)
+    return w
+
+
+def bicgstab_ilu0(rows, b, x, p, mode, rtol, maxit):
+    """BiCGSTAB right-preconditioned with ILU(0) (p^ = M^{-1} p, s^ = M^{-1} s)."""
+    R = exact.rmul
+    A_ = exact.radd
+    S_ = exact.rsub
+    D = exact.rdiv
+    Z = exact.Val(Fraction(0))
+    lu = ilu0(rows, p)
+    r = _residual(rows, b, x, p)
+    rt = list(r)
+    rr0 = _dot(r, r, p)
+    thr = _threshold(rr0, rtol, 0.0, p)
+    hist = []
+    if rr0.q <= thr.q:
+        return x, 0, "ok", hist
+    rho = _dot(rt, r, p)
+    pv = v = rho_prev = None
+    alpha = omega = Z
+    for i in range(1, maxit + 1):
+        if rho.q == 0:
+            return x, i - 1, "breakdown", hist
+        if i == 1:
+            pv = list(r)
+        else:
+            beta = R(D(rho, rho_prev, p), D(alpha, omega, p), p)
+            pv = [A_(rk, R(beta, S_(pk, R(omega, vk, p), p), p), p)
+                  for rk, pk, vk in zip(r, pv, v)]
+        ph = ilu0_apply(lu, pv, p)
+        v = _spmv(rows, ph, p, mode)
+        d = _dot(rt, v, p)
+        if d.q == 0:
+            return x, i - 1, "breakdown", hist
+        alpha = D(rho, d, p)
+        s = [S_(rk, R(alpha, vk, p), p) for rk, vk in zip(r, v)]
+        sh = ilu0_apply(lu, s, p)
+        t = _spmv(rows, sh, p, mode)
+        tt = _dot(t, t, p)
+        omega = D(_dot(t, s, p), tt, p) if tt.q != 0 else Z
+        x = [A_(A_(xk, R(alpha, pk, p), p), R(omega, sk, p), p)
+             for xk, pk, sk in zip(x, ph, sh)]
+        r = [S_(sk, R(omega, tk, p), p) for sk, tk in zip(s, t)]
+        rr = _dot(r, r, p)
+        hist.append(rr)
+        rho_prev, rho = rho, _dot(rt, r, p)
+        if rr.q <= thr.q:
+            return x, i, "ok", hist
+        if omega.q == 0:
+            return x, i, "breakdown", hist
+    return x, maxit, "noconv", hist
