@@ -274,6 +274,38 @@ mp_status mp_cgs(mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* opts, mp_sol
 mp_status mp_bicgstab(mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* opts,
                       mp_solve_info* info, void* stream);
 
+/* ---- ILU(0) preconditioning (Section 4's BiCGSTAB+ILU(0) rows) ----------- */
+
+typedef struct mp_ilu_s* mp_ilu; /* opaque; owns its device storage */
+
+/* ILU(0) of A in the textbook IKJ form (the paper prints no algorithm), all
+ * steps rounded and none skipped: for each row i, for each stored (i, k),
+ * k < i ascending, l_ik = RN(a_ik / u_kk) and, for each stored (i, j), j > k
+ * ascending with (k, j) stored, a_ij = RN(a_ij - RN(l_ik u_kj)).  L (unit
+ * lower) and U share A's pattern.  Rows run in dependency levels, one launch
+ * per level.  MP_ERR_DIVZERO: a row without a diagonal entry or a zero
+ * pivot.  Synchronises `stream`. */
+mp_status mp_ilu0_create(mp_csr A, void* stream, mp_ilu* out);
+mp_status mp_ilu0_destroy(mp_ilu M);
+
+/* Levels of the forward and backward triangular solves (launches per solve). */
+mp_status mp_ilu0_info(mp_ilu M, int64_t* levels_l, int64_t* levels_u);
+
+/* The factor values in A's CSR order (sorted columns): lu has nnz elements. */
+mp_status mp_ilu0_factor(mp_ilu M, mp_vec lu, void* stream);
+
+/* w = (LU)^{-1} r: forward y_i = r_i - RN(l_ik y_k) per step for k < i
+ * ascending, then backward w_i = RN((y_i - RN(u_ik w_k) per step for k > i
+ * ascending) / u_ii), one launch per level.  r and w must not alias. */
+mp_status mp_ilu0_apply(mp_ilu M, mp_vec r, mp_vec w, void* stream);
+
+/* BiCGSTAB right-preconditioned with M (Barrett et al.'s preconditioned
+ * BiCGSTAB): as mp_bicgstab with p^ = M^{-1} p, v = A p^, s^ = M^{-1} s,
+ * t = A s^, x = x + alpha p^ + omega s^; r remains b - A x of the original
+ * system, so the stopping rule is unchanged.  opts->transpose must be 0. */
+mp_status mp_bicgstab_ilu0(mp_csr A, mp_ilu M, mp_vec b, mp_vec x, const mp_solve_opts* opts,
+                           mp_solve_info* info, void* stream);
+
 /* ---- batched solves (not in the paper; its solver over a batch) ---------- */
 
 typedef struct mp_batch_s* mp_batch; /* opaque; owns its device storage */

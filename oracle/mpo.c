@@ -1512,7 +1512,11 @@ int mpo_bicgstab_ilu0(int p, int mode, int64_t n, const int64_t *rowptr,
         vstore(pv, k, p, &a1);
       }
     }
-    if ((st = ilu0_apply(p, n, rowptr, colidx, lu, pv, ph)) != MPO_OK) break; /* p^ */
+    int ast = ilu0_apply(p, n, rowptr, colidx, lu, pv, ph); /* p^ */
+    if (ast != MPO_OK) {
+      st = ast;
+      break;
+    }
     matvec(&s, rowptr, colidx, vals, ph, v); /* v = A p^ */
     sdot(&s, rt, v, &d);
     if (d.zero) {
@@ -1528,7 +1532,11 @@ int mpo_bicgstab_ilu0(int p, int mode, int64_t n, const int64_t *rowptr,
       num_sub(&rk, &a1, p, &sk); /* s = r - alpha v */
       vstore(sv, k, p, &sk);
     }
-    if ((st = ilu0_apply(p, n, rowptr, colidx, lu, sv, sh)) != MPO_OK) break; /* s^ */
+    ast = ilu0_apply(p, n, rowptr, colidx, lu, sv, sh); /* s^ */
+    if (ast != MPO_OK) {
+      st = ast;
+      break;
+    }
     matvec(&s, rowptr, colidx, vals, sh, t); /* t = A s^ */
     sdot(&s, t, sv, &ts);
     sdot(&s, t, t, &tt);

@@ -338,6 +338,60 @@ def bicgstab(A: CSR, b: Vec, x0: Vec | None = None, rtol=1e-30, atol=0.0, maxit=
                   poll_every, history, stream, transpose)
 
 
+class ILU0:
+    """ILU(0) factors of a CSR matrix (Section 4's preconditioner, textbook
+    IKJ form), built on the device."""
+
+    def __init__(self, A: CSR, stream=None):
+        h = ctypes.c_void_p()
+        _ok(_lib.load().mp_ilu0_create(A.h, _stream(stream), ctypes.byref(h)), "mp_ilu0_create")
+        self.h = h
+        self.n, self.nnz, self.prec = A.n, A.nnz, A.prec
+
+    def levels(self) -> tuple:
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        _ok(_lib.load().mp_ilu0_info(self.h, ctypes.byref(a), ctypes.byref(b)), "mp_ilu0_info")
+        return a.value, b.value
+
+    def factor(self, stream=None) -> Vec:
+        """L and U values in the matrix's CSR order (sorted columns)."""
+        lu = Vec.empty(self.nnz, self.prec)
+        _ok(_lib.load().mp_ilu0_factor(self.h, lu.c(), _stream(stream)), "mp_ilu0_factor")
+        check(stream)
+        return lu
+
+    def apply(self, r: Vec, w: Vec | None = None, stream=None, sync=True) -> Vec:
+        """w = (LU)^{-1} r."""
+        w = w if w is not None else Vec.empty(self.n, self.prec)
+        _ok(_lib.load().mp_ilu0_apply(self.h, r.c(), w.c(), _stream(stream)), "mp_ilu0_apply")
+        if sync:
+            check(stream)
+        return w
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            _lib.load().mp_ilu0_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def bicgstab_ilu0(A: CSR, M: ILU0, b: Vec, x0: Vec | None = None, rtol=1e-30, atol=0.0,
+                  maxit=1000, mode="ordered", poll_every=8, history=False, stream=None):
+    """BiCGSTAB right-preconditioned with ILU(0).  Returns (x, info dict)."""
+    fn = _lib.load().mp_bicgstab_ilu0
+
+    def call(Ah, bc, xc, opts, info, st):
+        return fn(Ah, M.h, bc, xc, opts, info, st)
+
+    return _solve(call, "mp_bicgstab_ilu0", A, b, x0, rtol, atol, maxit, mode, poll_every,
+                  history, stream)
+
+
 class Batch:
     """Independent systems of one precision stacked for batched solves.
 

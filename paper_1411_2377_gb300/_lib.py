@@ -78,6 +78,13 @@ SIGNATURES = {
     "mp_bicgstab": (_i32, [_vp, MpVec, MpVec, ctypes.POINTER(MpSolveOpts),
                            ctypes.POINTER(MpSolveInfo), _vp]),
     "mp_csr_grad": (_i32, [_vp, MpVec, MpVec, MpVec, _vp]),
+    "mp_ilu0_create": (_i32, [_vp, _vp, ctypes.POINTER(_vp)]),
+    "mp_ilu0_destroy": (_i32, [_vp]),
+    "mp_ilu0_info": (_i32, [_vp, _i64p, _i64p]),
+    "mp_ilu0_factor": (_i32, [_vp, MpVec, _vp]),
+    "mp_ilu0_apply": (_i32, [_vp, MpVec, MpVec, _vp]),
+    "mp_bicgstab_ilu0": (_i32, [_vp, _vp, MpVec, MpVec, ctypes.POINTER(MpSolveOpts),
+                                ctypes.POINTER(MpSolveInfo), _vp]),
     "mp_gemv": (_i32, [_i64, _i64, MpVec, MpVec, MpVec, _vp]),
     "mp_batch_create_f64": (_i32, [_i32, _vp, _vp, _vp, _vp, _i32, _vp, ctypes.POINTER(_vp)]),
     "mp_batch_destroy": (_i32, [_vp]),

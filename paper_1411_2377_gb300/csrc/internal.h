@@ -56,7 +56,30 @@ struct mp_csr_s {
   double* rowscale = nullptr;
 };
 
+// ILU(0) factors of a matrix in CSR order (sorted columns) with the level
+// schedules of the triangular solves (rows of a level depend only on rows of
+// earlier levels).
+struct mp_ilu_s {
+  int64_t n = 0, nnz = 0;
+  int32_t prec = 0;
+  int device = 0;
+  int64_t* rowptr = nullptr;  // [n + 1]
+  int32_t* col = nullptr;     // [nnz]
+  int64_t* diag = nullptr;    // [n] position of (i, i)
+  uint64_t* lu = nullptr;     // [(L+1) * nnz] plane-major, ld = nnz
+  int32_t* rows_l = nullptr;  // rows by forward (and factorisation) level
+  int32_t* rows_u = nullptr;  // rows by backward level
+  int64_t* lvl_l = nullptr;   // host [nl + 1]
+  int64_t* lvl_u = nullptr;   // host [nu + 1]
+  int64_t nl = 0, nu = 0;
+};
+
 namespace mpk {
+
+// w = (LU)^{-1} r with an ILU(0) factor, one launch per level; gate as for
+// the SpMV (a nonzero flag makes every launch return at once).
+mp_status launch_ilu0_apply(const mp_ilu_s* M, const uint64_t* r, int64_t ldr, uint64_t* w,
+                            int64_t ldw, const int* gate, cudaStream_t st);
 
 // ---- errors -------------------------------------------------------------
 mp_status set_error(mp_status s, const char* fmt, ...);

@@ -44,6 +44,7 @@ struct SolveCall {
   mp_vec b, x;
   mp_solve_opts o;
   cudaStream_t st;
+  const mp_ilu_s* pre;  // right preconditioner (BiCGSTAB), or null
 };
 
 template <int W>
@@ -542,24 +543,26 @@ __global__ void bs_s(const SState* st, const uint64_t* __restrict__ S, const uin
   }
 }
 
-// BiCGSTAB: x = x + alpha p + omega s;  r = s - omega t
+// BiCGSTAB: x = x + alpha p + omega s;  r = s - omega t (with a right
+// preconditioner, x takes p^ = M^{-1} p and s^ = M^{-1} s: px, sx)
 template <int W>
-__global__ void bs_xr(const SState* st, const uint64_t* __restrict__ S, const uint64_t* p,
-                      const uint64_t* s, const uint64_t* t, uint64_t* r, uint64_t* x, int64_t ldx,
-                      int64_t ld, int64_t n) {
+__global__ void bs_xr(const SState* st, const uint64_t* __restrict__ S, const uint64_t* px,
+                      const uint64_t* sx, const uint64_t* s, const uint64_t* t, uint64_t* r,
+                      uint64_t* x, int64_t ldx, int64_t ld, int64_t n) {
   if (st->done) return;
   GRID_LOOP(i, n) {
     Num<W> alpha, omega, a, b, c, sv;
     ld_s<W>(alpha, S, ALPHA);
     ld_s<W>(omega, S, OMEGA);
-    load<W>(a, p, ld, i);
+    load<W>(a, px, ld, i);
     mul_rn<W>(alpha, a, b);
     load<W>(a, x, ldx, i);
     add_rn<W>(a, b, c);
-    load<W>(sv, s, ld, i);
+    load<W>(sv, sx, ld, i);
     mul_rn<W>(omega, sv, b);
     add_rn<W>(c, b, a);
     store<W>(a, x, ldx, i);
+    load<W>(sv, s, ld, i);
     load<W>(a, t, ld, i);
     mul_rn<W>(omega, a, b);
     sub_rn<W>(sv, b, c);
@@ -783,7 +786,7 @@ mp_status cgs_iteration(const Work& w, const SolveCall& c, bool first) {
 
 template <int W>
 mp_status bicgstab_iteration(const Work& w, const SolveCall& c, bool first) {
-  enum { R, RT, P, V, SV, T };
+  enum { R, RT, P, V, SV, T, PH, SH };
   const int64_t n = w.n, ld = w.ld;
   const int* gate = &w.st->done;
   cudaStream_t st = c.st;
@@ -797,17 +800,28 @@ mp_status bicgstab_iteration(const Work& w, const SolveCall& c, bool first) {
     bs_p<W><<<g, 128, 0, st>>>(w.st, w.S, w.vec(R), w.vec(V), w.vec(P), ld, n);
     count_launch(2);
   }
-  if ((r = launch_spmv(c.A, op_a(c), c.o.mode, w.vec(P), ld, w.vec(V), ld, nullptr, 0, gate, st)) != MP_OK)
+  // right preconditioning: v = A M^{-1} p, t = A M^{-1} s
+  const uint64_t* pv = w.vec(P);
+  if (c.pre) {
+    if ((r = launch_ilu0_apply(c.pre, w.vec(P), ld, w.vec(PH), ld, gate, st)) != MP_OK) return r;
+    pv = w.vec(PH);
+  }
+  if ((r = launch_spmv(c.A, op_a(c), c.o.mode, pv, ld, w.vec(V), ld, nullptr, 0, gate, st)) != MP_OK)
     return r;
   if ((r = dot2(w, w.vec(RT), w.vec(V), DEN, nullptr, nullptr, 0, st, gate)) != MP_OK) return r;
   sc_alpha<W><<<1, 1, 0, st>>>(w.st, w.S);
   bs_s<W><<<g, 128, 0, st>>>(w.st, w.S, w.vec(R), w.vec(V), w.vec(SV), ld, n);
   count_launch(2);
-  if ((r = launch_spmv(c.A, op_a(c), c.o.mode, w.vec(SV), ld, w.vec(T), ld, nullptr, 0, gate, st)) != MP_OK)
+  const uint64_t* sv = w.vec(SV);
+  if (c.pre) {
+    if ((r = launch_ilu0_apply(c.pre, w.vec(SV), ld, w.vec(SH), ld, gate, st)) != MP_OK) return r;
+    sv = w.vec(SH);
+  }
+  if ((r = launch_spmv(c.A, op_a(c), c.o.mode, sv, ld, w.vec(T), ld, nullptr, 0, gate, st)) != MP_OK)
     return r;
   if ((r = dot2(w, w.vec(T), w.vec(SV), TS, w.vec(T), w.vec(T), TT, st, gate)) != MP_OK) return r;
   sc_omega<W><<<1, 1, 0, st>>>(w.st, w.S);
-  bs_xr<W><<<g, 128, 0, st>>>(w.st, w.S, w.vec(P), w.vec(SV), w.vec(T), w.vec(R), c.x.data,
+  bs_xr<W><<<g, 128, 0, st>>>(w.st, w.S, pv, sv, w.vec(SV), w.vec(T), w.vec(R), c.x.data,
                               c.x.ld, ld, n);
   count_launch(2);
   if ((r = dot2(w, w.vec(R), w.vec(R), RR, w.vec(RT), w.vec(R), RHO_NEW, st, gate)) != MP_OK)
@@ -832,7 +846,7 @@ mp_status solve_w(const SolveCall& cu, mp_solve_info* info) {
   c.st = st;
   const int64_t n = c.A->n;
   Work w;
-  constexpr int kVecs = M == kGPBiCG ? 11 : (M == kCGS ? 8 : 6);
+  const int kVecs = M == kGPBiCG ? 11 : (M == kCGS || c.pre ? 8 : 6);
   mp_status r = alloc_work(w, c.A->prec, n, kVecs, st);
   if (r != MP_OK) {
     free_work(w, st);
@@ -967,7 +981,7 @@ namespace mpk {
 namespace {
 
 mp_status solve(int method, mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* opts,
-                mp_solve_info* info, void* stream) {
+                mp_solve_info* info, void* stream, const mp_ilu_s* pre = nullptr) {
   if (!A) return set_error(MP_ERR_ARG, "matrix is null");
   if (!opts) return set_error(MP_ERR_ARG, "opts is null");
   mp_status r;
@@ -989,7 +1003,9 @@ mp_status solve(int method, mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* o
     return set_error(MP_ERR_ARG, "a solve with A^T needs MP_CSR_TRANSPOSE");
   if (opts->reserved != 0) return set_error(MP_ERR_ARG, "reserved must be 0");
   if (!status_word()) return set_error(MP_ERR_CUDA, "status word unavailable");
-  SolveCall c{A, b, x, *opts, static_cast<cudaStream_t>(stream)};
+  if (pre && (pre->n != A->n || pre->prec != A->prec || opts->transpose))
+    return set_error(MP_ERR_ARG, "preconditioner does not match the matrix (or a transposed solve)");
+  SolveCall c{A, b, x, *opts, static_cast<cudaStream_t>(stream), pre};
   return dispatch_w(A->prec, [&](auto w) {
     constexpr int W = decltype(w)::value;
     return solve_entry<W>(method, c, info);
@@ -1019,6 +1035,12 @@ mp_status mp_cgs(mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* opts, mp_sol
 mp_status mp_bicgstab(mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* opts,
                       mp_solve_info* info, void* stream) {
   return mpk::solve(3, A, b, x, opts, info, stream);
+}
+
+mp_status mp_bicgstab_ilu0(mp_csr A, mp_ilu M, mp_vec b, mp_vec x, const mp_solve_opts* opts,
+                           mp_solve_info* info, void* stream) {
+  if (!M) return mpk::set_error(MP_ERR_ARG, "preconditioner is null");
+  return mpk::solve(3, A, b, x, opts, info, stream, M);
 }
 
 }  // extern "C"

@@ -1,0 +1,105 @@
+"""ILU(0) on the device vs the oracle, bit for bit: the factors, the
+preconditioner application, and BiCGSTAB right-preconditioned with it (every
+iterate's (r_i, r_i), the iteration count, the status and x)."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import assert_bitwise, need_gpu, rand_planes, random_csr, recs
+from paper_1411_2377_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def dominant_system(n, p, seed):
+    rowptr, colidx = random_csr(n, seed=seed, mean_len=6, max_len=20)
+    rows = np.repeat(np.arange(n), np.diff(rowptr))
+    key = np.unique(np.concatenate([rows * n + colidx, np.arange(n) * (n + 1)]))
+    rowptr = np.zeros(n + 1, np.int64)
+    np.add.at(rowptr, key // n + 1, 1)
+    rowptr = np.cumsum(rowptr)
+    colidx = (key % n).astype(np.int32)
+    Vr = recs(rand_planes(len(colidx), p, seed + 1, zero_frac=0.05, emin=-1, emax=1))
+    for i in range(n):
+        for k in range(rowptr[i], rowptr[i + 1]):
+            if colidx[k] == i:
+                Vr[k] = oracle.from_f64(p, [float(10 + i % 7)])[0]
+    return rowptr, colidx, Vr
+
+
+@pytest.mark.parametrize("p", (128, 256, 512, 1024))
+def test_factor_and_apply_match_the_oracle(p):
+    mpk = need_gpu()
+    n = 300
+    rowptr, colidx, Vr = dominant_system(n, p, p + 3)
+    A = mpk.CSR(rowptr, colidx, synth.records_to_planes(Vr), p)
+    M = mpk.ILU0(A)
+    lu_o, st = oracle.ilu0(p, rowptr, colidx, Vr)
+    assert st == oracle.OK
+    assert_bitwise(M.factor().planes(), lu_o, f"ILU(0) factor p={p}")
+    R = rand_planes(n, p, 9, zero_frac=0.1, emin=-5, emax=5)
+    w = M.apply(mpk.Vec.from_planes(R, p))
+    w_o, st = oracle.ilu0_apply(p, rowptr, colidx, lu_o, recs(R))
+    assert st == oracle.OK
+    assert_bitwise(w.planes(), w_o, f"ILU(0) apply p={p}")
+    nl, nu = M.levels()
+    assert 1 <= nl <= n and 1 <= nu <= n
+
+
+@pytest.mark.parametrize("p", (128, 256))
+@pytest.mark.parametrize("mode", ("ordered", "exact"))
+def test_preconditioned_bicgstab_matches_the_oracle(p, mode):
+    mpk = need_gpu()
+    rowptr, colidx, v64 = synth.stencil2d(16, seed=2)
+    n = len(rowptr) - 1
+    vals = oracle.from_f64(p, v64)
+    b, _ = oracle.spmv(p, oracle.EXACT, rowptr, colidx, vals, oracle.from_f64(p, np.ones(n)))
+    A = mpk.CSR(rowptr, colidx, v64, p)
+    M = mpk.ILU0(A)
+    x, info = mpk.bicgstab_ilu0(A, M, mpk.Vec.from_planes(synth.records_to_planes(b), p),
+                                rtol=1e-30, maxit=300, mode=mode, poll_every=3, history=True)
+    m = oracle.ORDERED if mode == "ordered" else oracle.EXACT
+    xo, it, st, hist = oracle.bicgstab_ilu0(p, m, rowptr, colidx, vals, b, oracle.empty(p, n),
+                                            1e-30, 0.0, 300)
+    assert st == oracle.OK
+    assert (info["iters"], info["status"]) == (it, st)
+    assert_bitwise(info["history"].planes(), hist, f"history p={p} {mode}")
+    assert_bitwise(x.planes(), xo, f"x p={p} {mode}")
+    # fewer iterations than without the preconditioner
+    _, plain = mpk.bicgstab(A, mpk.Vec.from_planes(synth.records_to_planes(b), p), rtol=1e-30,
+                            maxit=300, mode=mode)
+    assert info["iters"] < plain["iters"]
+
+
+def test_noconv_and_poll_interval():
+    mpk = need_gpu()
+    p = 512
+    rowptr, colidx, v64 = synth.stencil2d(12, seed=6)
+    n = len(rowptr) - 1
+    Vr = oracle.from_f64(p, v64)
+    B = rand_planes(n, p, 22, zero_frac=0.0, emin=-2, emax=2)
+    A = mpk.CSR(rowptr, colidx, v64, p)
+    M = mpk.ILU0(A)
+    xo, it, st, hist = oracle.bicgstab_ilu0(p, oracle.EXACT, rowptr, colidx, Vr, recs(B),
+                                            oracle.empty(p, n), 1e-200, 0.0, 3)
+    for poll in (1, 7):
+        x, info = mpk.bicgstab_ilu0(A, M, mpk.Vec.from_planes(B, p), rtol=1e-200, maxit=3,
+                                    mode="exact", poll_every=poll, history=True)
+        assert (info["iters"], info["status"]) == (it, st) == (3, oracle.ERR_NOCONV)
+        assert_bitwise(info["history"].planes(), hist, "history")
+        assert_bitwise(x.planes(), xo, "x")
+
+
+def test_zero_pivot_and_missing_diagonal():
+    mpk = need_gpu()
+    p = 128
+    rowptr = np.array([0, 2, 4], np.int64)
+    colidx = np.array([0, 1, 0, 1], np.int32)
+    A = mpk.CSR(rowptr, colidx, np.array([0.0, 1.0, 1.0, 1.0]), p)
+    with pytest.raises(mpk.MPError) as e:
+        mpk.ILU0(A)
+    assert e.value.status == 9
+    B = mpk.CSR(np.array([0, 1, 2], np.int64), np.array([1, 0], np.int32), np.array([1.0, 1.0]), p)
+    with pytest.raises(mpk.MPError) as e:
+        mpk.ILU0(B)
+    assert e.value.status == 9

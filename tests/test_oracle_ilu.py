@@ -179,3 +179,16 @@ def test_bicgstab_ilu0_known_solution_and_fewer_iterations(mode):
         rec_rr = exact.decode(hist[-1], p).q
         assert true_rr > 0
         assert abs(true_rr - rec_rr) / true_rr < Fraction(1, 2 ** 150), k
+
+
+def test_reaching_maxit_is_noconv():
+    """Tables 1-2's "NC": the iteration limit without convergence."""
+    p = 512
+    rowptr, colidx, v64 = synth.stencil2d(12, seed=6)
+    n = len(rowptr) - 1
+    vals = oracle.from_f64(p, v64)
+    b = oracle.from_f64(p, np.linspace(-1.0, 2.0, n))
+    x, it, st, hist = oracle.bicgstab_ilu0(p, oracle.EXACT, rowptr, colidx, vals, b,
+                                           oracle.empty(p, n), 1e-200, 0.0, 3)
+    assert st == oracle.ERR_NOCONV and it == 3 and len(hist) == 3
+    assert exact.decode(hist[-1], p).q > 0
