@@ -138,7 +138,59 @@ __global__ void usolve_level_kernel(const int32_t* __restrict__ rows, int64_t co
   store<W>(q, w, ldw, i);
 }
 
+// The whole forward (L) or backward (U) solve in one block: the levels in
+// order, the rows of a level spread over the threads, a block barrier
+// between levels (a row's inputs are rows of earlier levels, written by
+// threads of this block before the barrier).  One launch instead of one per
+// level, for matrices small enough that one block keeps up.
+template <int W, bool UPPER>
+__global__ void __launch_bounds__(256) trsv_block_kernel(
+    const int32_t* __restrict__ rows, const int64_t* __restrict__ lvl, int64_t nlev,
+    const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+    const int64_t* __restrict__ diag, const uint64_t* __restrict__ lu, int64_t nnz,
+    const uint64_t* __restrict__ r, int64_t ldr, uint64_t* w, int64_t ldw,
+    const int* __restrict__ gate) {
+  if (gate && *gate) return;
+  for (int64_t l = 0; l < nlev; ++l) {
+    const int64_t a = lvl[l], b = lvl[l + 1];
+    for (int64_t t = a + threadIdx.x; t < b; t += blockDim.x) {
+      const int32_t i = rows[t];
+      Num<W> acc;
+      if (UPPER) {
+        load<W>(acc, w, ldw, i);
+        for (int64_t k = diag[i] + 1; k < rowptr[i + 1]; ++k) {
+          Num<W> u, z, pr, s;
+          load<W>(u, lu, nnz, k);
+          load<W>(z, w, ldw, col[k]);
+          mul_rn<W>(u, z, pr);
+          sub_rn<W>(acc, pr, s);
+          acc = s;
+        }
+        Num<W> d, q;
+        load<W>(d, lu, nnz, diag[i]);
+        div_rn<W>(acc, d, q);
+        store<W>(q, w, ldw, i);
+      } else {
+        load<W>(acc, r, ldr, i);
+        for (int64_t k = rowptr[i]; k < rowptr[i + 1] && col[k] < i; ++k) {
+          Num<W> lv, y, pr, s;
+          load<W>(lv, lu, nnz, k);
+          load<W>(y, w, ldw, col[k]);
+          mul_rn<W>(lv, y, pr);
+          sub_rn<W>(acc, pr, s);
+          acc = s;
+        }
+        store<W>(acc, w, ldw, i);
+      }
+    }
+    __syncthreads();
+  }
+}
+
 int blocks_for(int64_t count, int tpb) { return (int)std::max<int64_t>(1, (count + tpb - 1) / tpb); }
+
+// Up to this many rows the solves run as one block (one launch per solve).
+constexpr int64_t kOneBlockRows = 1 << 18;
 
 }  // namespace
 
@@ -147,6 +199,16 @@ mp_status launch_ilu0_apply(const mp_ilu_s* M, const uint64_t* r, int64_t ldr, u
   return dispatch_w(M->prec, [&](auto wc) {
     constexpr int W = decltype(wc)::value;
     constexpr int tpb = 64;
+    if (M->n <= kOneBlockRows) {
+      trsv_block_kernel<W, false><<<1, 256, 0, st>>>(M->rows_l, M->d_lvl_l, M->nl, M->rowptr,
+                                                     M->col, M->diag, M->lu, M->nnz, r, ldr, w,
+                                                     ldw, gate);
+      trsv_block_kernel<W, true><<<1, 256, 0, st>>>(M->rows_u, M->d_lvl_u, M->nu, M->rowptr,
+                                                    M->col, M->diag, M->lu, M->nnz, r, ldr, w,
+                                                    ldw, gate);
+      count_launch(2);
+      return launch_check("ILU(0) triangular solves");
+    }
     for (int64_t l = 0; l < M->nl; ++l) {
       const int64_t cnt = M->lvl_l[l + 1] - M->lvl_l[l];
       lsolve_level_kernel<W><<<blocks_for(cnt, tpb), tpb, 0, st>>>(
@@ -176,6 +238,8 @@ void free_ilu(mp_ilu_s* M) {
   cudaFree(M->lu);
   cudaFree(M->rows_l);
   cudaFree(M->rows_u);
+  cudaFree(M->d_lvl_l);
+  cudaFree(M->d_lvl_u);
   delete[] M->lvl_l;
   delete[] M->lvl_u;
   delete M;
@@ -278,8 +342,12 @@ mp_status mp_ilu0_create(mp_csr A, void* stream, mp_ilu* out) {
   if (!M->lvl_l || !M->lvl_u) return fail(set_error(MP_ERR_ALLOC, "ILU(0) levels"));
   std::copy(ll.begin(), ll.end(), M->lvl_l);
   std::copy(lu_.begin(), lu_.end(), M->lvl_u);
-  if (!dmalloc(&M->rows_l, n) || !dmalloc(&M->rows_u, n))
+  if (!dmalloc(&M->rows_l, n) || !dmalloc(&M->rows_u, n) || !dmalloc(&M->d_lvl_l, ll.size()) ||
+      !dmalloc(&M->d_lvl_u, lu_.size()))
     return fail(set_error(MP_ERR_ALLOC, "ILU(0) levels"));
+  if (cudaMemcpyAsync(M->d_lvl_l, ll.data(), sizeof(int64_t) * ll.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(M->d_lvl_u, lu_.data(), sizeof(int64_t) * lu_.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return fail(set_error(MP_ERR_CUDA, "ILU(0) upload"));
   if (n > 0 && (cudaMemcpyAsync(M->diag, diag.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, st) != cudaSuccess ||
                 cudaMemcpyAsync(M->rows_l, rl.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st) != cudaSuccess ||
                 cudaMemcpyAsync(M->rows_u, ru.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st) != cudaSuccess))

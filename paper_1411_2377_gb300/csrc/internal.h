@@ -71,6 +71,8 @@ struct mp_ilu_s {
   int32_t* rows_u = nullptr;  // rows by backward level
   int64_t* lvl_l = nullptr;   // host [nl + 1]
   int64_t* lvl_u = nullptr;   // host [nu + 1]
+  int64_t* d_lvl_l = nullptr; // device copies of the level boundaries
+  int64_t* d_lvl_u = nullptr;
   int64_t nl = 0, nu = 0;
 };
 
