@@ -165,6 +165,26 @@ def dist_setup(args):
     return world, rank, local
 
 
+def max_over_ranks(value: float, world: int) -> float:
+    """The largest of the ranks' values (the job's time is its slowest
+    rank's); works with NCCL (on the GPU) and gloo (on the CPU)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, max_ms: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest
+    rank's time (weak scaling: each rank has its own replica)."""
+    return units_per_rank * world / (max_ms * 1e-3)
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle (baseline and reference arm)
 # ---------------------------------------------------------------------------
@@ -234,7 +254,7 @@ def run_reference(args):
     build_oracle()
     precs = [int(p) for p in args.precs.split(",")]
     rowptr, colidx, values, xs, _ = build_workload(args.n, precs)
-    per_step = max(0.5, min(12.0, 150.0 / max(1, args.steps + args.warmup)))
+    per_step = max(0.2, min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
         oracle_sample(rowptr, colidx, values, xs, precs, per_step / 4)
     nnz_tot, t_tot, desc = 0, 0.0, ""
@@ -342,15 +362,9 @@ def run_native(args):
     launches = mpk.launch_count(reset=True)
     clocks = sampler.stop()
     mpk.check()
-    total_ms = t0.elapsed_time(t1)
-    if world > 1:
-        import torch.distributed as dist
-
-        tt = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(t0.elapsed_time(t1), world)
     units = args.steps * nnz * len(precs) * len(MODES) * world
-    value = units / (total_ms * 1e-3) / 1e9
+    value = job_throughput(args.steps * nnz * len(precs) * len(MODES), world, total_ms) / 1e9
 
     peaks, peak_src = measured_peaks()
     props = torch.cuda.get_device_properties(local)
