@@ -125,7 +125,9 @@ mp_status mp_csr_info(mp_csr A, int64_t* n, int64_t* nnz, int32_t* prec_bits,
  *            per pair of 29-bit limbs, no carries inside the product; EXACT
  *            then keeps 29-bit digit counters), else from 32-bit words with
  *            carry chains;
- *     bit 2: MP_EXACT column form: 16 columns computed at a time, not 8;
+ *     bit 2: MP_EXACT column form: 16 columns computed at a time, not 8
+ *            (with bit 4: registers capped for four blocks of at most 128
+ *            threads per SM);
  *            MP_ORDERED: registers capped for three blocks of at most 128
  *            threads per SM (ignored above 128 threads per block);
  *     bit 3: x is first copied into records (each element's L+1 words

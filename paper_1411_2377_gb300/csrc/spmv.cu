@@ -46,16 +46,17 @@ __host__ __device__ inline int digits_cols(int64_t span, int W) {
 // Launch variants (a bit field): bit 0 = the row loop stages the next
 // entry's operands (ORDERED: p <= 512 only; EXACT: column form only, word
 // form stages at p <= 512), bit 1 = products from radix-2^29 column sums,
-// bit 2 = EXACT: column sums computed 16 columns at a time instead of 8;
+// bit 2 = EXACT: column sums computed 16 columns at a time instead of 8
+// (windowed form: the register-capped kernel, four 128-thread blocks per SM);
 // ORDERED: the register-capped kernel (three blocks of <= 128 threads per SM);
 // bit 3 = x gathered from a record copy made before the product;
 // bit 4 = EXACT (p >= 512, column form): the windowed kernel.
 constexpr int kVarStage = 1, kVarCols = 2, kVarWide = 4, kVarRec = 8, kVarTop = 16;
 // A matrix's launch configuration for one mode with the library's defaults
 // filled in (chosen from measurements of the n = 10^6 sweep on GB300: the
-// word form with a half-and-half L1/shared split for EXACT at p <= 512, the
-// windowed column form at p = 1024; column products for ORDERED from p = 256
-// on, register-capped blocks at p = 128 and 1024).
+// word form with a half-and-half L1/shared split for EXACT at p <= 256, the
+// register-capped windowed column form from p = 512; column products for
+// ORDERED from p = 256 on, register-capped blocks at p = 128 and 1024).
 struct LaunchCfg {
   int tpb;
   bool stage, cols, wide, rec, top;
@@ -79,12 +80,12 @@ LaunchCfg launch_cfg(const mp_csr_s* M, int mode, int W) {
     c.wide = (v < 0 ? (W == 4 || W == 32) : (v & kVarWide) != 0) && c.tpb <= 128;
     c.carve = M->cfg_carve[0];
   } else {
-    c.cols = v < 0 ? W >= 32 : (v & kVarCols) != 0;
-    c.top = c.cols && W >= 16 && (v < 0 ? W >= 32 : (v & kVarTop) != 0);
-    c.stage = c.cols ? (v < 0 ? !c.top : (v & kVarStage) != 0) : W <= 16;
-    c.wide = c.cols && v >= 0 && (v & kVarWide);
+    c.cols = v < 0 ? W >= 16 : (v & kVarCols) != 0;
+    c.top = c.cols && W >= 16 && (v < 0 || (v & kVarTop) != 0);
+    c.stage = c.cols ? (v < 0 ? W == 16 : (v & kVarStage) != 0) : W <= 16;
+    c.wide = c.cols && (v < 0 ? c.top : (v & kVarWide) != 0);
     c.tpb = M->cfg_tpb[1] < 0 ? 128 : M->cfg_tpb[1];
-    c.carve = M->cfg_carve[1] < 0 ? (W <= 16 ? 50 : -1) : M->cfg_carve[1];
+    c.carve = M->cfg_carve[1] < 0 ? (W <= 8 ? 50 : -1) : M->cfg_carve[1];
   }
   return c;
 }
@@ -435,8 +436,10 @@ __global__ void __launch_bounds__(256) spmv_exact_kernel(
 // through the overflow list, so the result is always the exact sum rounded
 // once.  The window is a third of the full one and about a third of the
 // multiply-adds are skipped.
+// G = 4 marks the register-capped form: at most 128 threads per block and
+// four blocks per SM (the window's 48 KB allow four).
 template <int W, bool PIPE, int G>
-__global__ void __launch_bounds__(256) spmv_exact_top_kernel(
+__global__ void __launch_bounds__(G == 4 ? 128 : 256, G == 4 ? 4 : 1) spmv_exact_top_kernel(
     const SellView S, const uint64_t* __restrict__ x, int64_t ldx, uint64_t* __restrict__ y,
     int64_t ldy, int32_t* __restrict__ ovf, int* __restrict__ status,
     const int* __restrict__ gate) {
@@ -781,10 +784,12 @@ mp_status spmv_w(const mp_csr_s* M, const Sell& S, int mode, const uint64_t* x, 
     bool launched = false;
     if constexpr (W >= 16) {
       if (top) {
-        r = stage ? (wide ? launch_top(spmv_exact_top_kernel<W, true, 16>)
-                          : launch_top(spmv_exact_top_kernel<W, true, 8>))
-                  : (wide ? launch_top(spmv_exact_top_kernel<W, false, 16>)
-                          : launch_top(spmv_exact_top_kernel<W, false, 8>));
+        // bit 2 on the windowed form: the register-capped kernel (<= 128 threads)
+        const bool capped = wide && tpb <= 128;
+        r = capped ? (stage ? launch_top(spmv_exact_top_kernel<W, true, 4>)
+                            : launch_top(spmv_exact_top_kernel<W, false, 4>))
+            : stage ? launch_top(spmv_exact_top_kernel<W, true, 8>)
+                    : launch_top(spmv_exact_top_kernel<W, false, 8>);
         launched = true;
       }
     }
@@ -927,9 +932,11 @@ mp_status mp_csr_tune(mp_csr A, int32_t mode, int32_t reps, int32_t* tpb_out, in
     for (int32_t v : {kVarCols, kVarCols | kVarStage, kVarCols | kVarWide,
                       kVarCols | kVarStage | kVarWide})
       vars[nvar++] = v;
-    if (A->prec >= 512) {  // the windowed form
+    if (A->prec >= 512) {  // the windowed form, plain and register-capped
       vars[nvar++] = kVarTop | kVarCols;
       vars[nvar++] = kVarTop | kVarCols | kVarStage;
+      vars[nvar++] = kVarTop | kVarCols | kVarWide;
+      vars[nvar++] = kVarTop | kVarCols | kVarWide | kVarStage;
     }
   }
   // the same gathering x from its record copy, for the default form

@@ -78,7 +78,7 @@ def test_tuner_and_cache(p, tmp_path):
         assert r["threads_per_block"] in (32, 64, 128, 256)
         assert A.get_config(name)["threads_per_block"] == r["threads_per_block"]
         base = {"ordered": ((0, 1, 2, 3, 5, 7) if p <= 512 else (0, 2, 6)),
-                "exact": (0, 1, 2, 3, 6, 7) + ((18, 19) if p >= 512 else ())}[name]
+                "exact": (0, 1, 2, 3, 6, 7) + ((18, 19, 22, 23) if p >= 512 else ())}[name]
         assert r["variant"] in set(base) | {v | 8 for v in base}
         want, _ = oracle.spmv(p, m, rowptr, colidx, recs(V), recs(X))
         assert_bitwise(mpk.spmv(A, x, mode=name).planes(), want, f"tuned {name} p={p}")
