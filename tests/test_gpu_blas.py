@@ -11,9 +11,10 @@ PRECS = (128, 256, 512, 1024)
 
 @pytest.mark.parametrize("p", PRECS)
 @pytest.mark.parametrize("n,lo,hi", [(1, -3, 3), (31, -3, 3), (4097, -40, 40),
-                                     (100_003, -200, 200), (50_000, -1500, 1500)])
+                                     (2_000, -1500, 1500), (100_003, -200, 200),
+                                     (50_000, -1500, 1500)])
 def test_dot(p, n, lo, hi):
-    """Spans inside the per-warp window and (lo/hi = +-1500) the wide path."""
+    """Spans inside the per-thread window and (lo/hi = +-1500) the wide path."""
     mpk = need_gpu()
     X = rand_planes(n, p, 61 + n, zero_frac=0.02, emin=lo, emax=hi)
     Y = rand_planes(n, p, 62 + n, zero_frac=0.02, emin=lo, emax=hi)
@@ -48,6 +49,46 @@ def test_dot_cancellation_zero_and_span_error(p):
     want, st = oracle.dot(p, Xr, recs(Y))
     assert st == oracle.ERR_SPAN
     assert_bitwise(out.planes(), want[None], "dot span error")
+
+
+@pytest.mark.parametrize("p", (128, 1024))
+@pytest.mark.parametrize("n", (5_000, 70_000))
+def test_dot_block_spans_and_cap(p, n):
+    """One far product among near ones (the wide path), a low and a high
+    outlier in different blocks, and a global span of exactly the cap
+    (accepted) or one past it (+0 and MP_ERR_SPAN)."""
+    mpk = need_gpu()
+    X = rand_planes(n, p, 300 + n, zero_frac=0.01, emin=0, emax=0)
+    Y = rand_planes(n, p, 400 + n, zero_frac=0.01, emin=0, emax=0)
+    Xr = recs(X)
+    Yr = recs(Y)
+
+    def shifted(i, by):
+        h = Xr[i, 0].view(np.int64)
+        return np.int64(h + 2 * by).view(np.uint64)
+
+    lo_i, hi_i, mid_i = n // 7, n - 3, n // 2
+    for i in (lo_i, hi_i, mid_i):  # nonzero at the shifted positions
+        assert (Xr[i, 0].view(np.int64) >> 1) != oracle.EXP_ZERO
+        assert (Yr[i, 0].view(np.int64) >> 1) != oracle.EXP_ZERO
+    cases = (((mid_i, 3000),), ((lo_i, -700), (mid_i, 2500)),
+             ((lo_i, -(oracle.SPAN_CAP // 2)), (hi_i, oracle.SPAN_CAP // 2)),
+             ((lo_i, -(oracle.SPAN_CAP // 2)), (hi_i, oracle.SPAN_CAP // 2 + 1)))
+    for shifts in cases:
+        Z = Xr.copy()
+        for i, by in shifts:
+            Z[i, 0] = shifted(i, by)
+        want, st = oracle.dot(p, Z, Yr)
+        out = mpk.dot(mpk.Vec.from_planes(Z.T.copy(), p), mpk.Vec.from_planes(Y, p), sync=False)
+        if st == oracle.ERR_SPAN:
+            with pytest.raises(mpk.MPError) as e:
+                mpk.check()
+            assert e.value.status == 5
+        else:
+            assert st == oracle.OK
+            mpk.check()
+        assert_bitwise(out.planes(), want[None], f"dot p={p} n={n} shifts={shifts}")
+    assert st == oracle.ERR_SPAN  # the last case is one past the cap
 
 
 @pytest.mark.parametrize("p", PRECS)
