@@ -17,9 +17,12 @@ roofline   = the dominant product (largest share of the step): algorithmic
              bytes (values, column indices, row pointers, x once, y once) at
              the measured HBM peak vs its 32x32->64 multiply count at the
              integer-multiply peak; the slower of the two is the bound.
-cpu_baseline = the oracle (plain C, one thread) on a bounded row sample.
+cpu_baseline = the oracle (plain C) on bounded row samples, on all host cores
+               (rows split over threads) with the one-thread figure beside
+               it, plus the oracle's GPBiCG per iteration on the 64x64 system.
 
---impl reference times the oracle alone (the CPU reference arm).
+--impl reference times the oracle alone on all host cores (the CPU
+reference arm).
 """
 from __future__ import annotations
 
@@ -189,9 +192,20 @@ def job_throughput(units_per_rank: float, world: int, max_ms: float) -> float:
 # CPU oracle (baseline and reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_sample(rowptr, colidx, values, xs, precs, budget_s):
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_sample(rowptr, colidx, values, xs, precs, budget_s, threads=1):
     """Times the oracle on leading row ranges of every (p, mode), about
-    budget_s seconds in total; returns (nnz, seconds, description)."""
+    budget_s seconds of wall time in total; returns (nnz, seconds,
+    description).  With threads > 1 each sample's rows are split into
+    contiguous ranges of about equal nonzeros, one per host thread (rows are
+    independent; the C oracle keeps no state between calls and ctypes
+    releases the interpreter lock while it runs)."""
     import oracle
     from paper_1411_2377_gb300 import synth
 
@@ -202,7 +216,7 @@ def oracle_sample(rowptr, colidx, values, xs, precs, budget_s):
         xr = synth.planes_to_records(xs[p])
         for name, m in MODES:
             rows = 64
-            while True:  # calibrate on a small range, then size the sample
+            while True:  # calibrate on a small range (one thread), then size the sample
                 e = int(rowptr[rows])
                 t0 = time.perf_counter()
                 _sample(oracle, p, m, rowptr, colidx, vrec, xr, rows)
@@ -211,27 +225,63 @@ def oracle_sample(rowptr, colidx, values, xs, precs, budget_s):
                     break
                 rows = min(rows * 4, len(rowptr) - 1)
             rate = e / max(dt, 1e-9)
-            want = int(rate * per)
+            want = int(rate * per * threads)
             rows2 = int(np.searchsorted(rowptr, want))
             rows2 = max(1, min(rows2, len(rowptr) - 1))
             t0 = time.perf_counter()
-            _sample(oracle, p, m, rowptr, colidx, vrec, xr, rows2)
+            _sample(oracle, p, m, rowptr, colidx, vrec, xr, rows2, threads)
             dt = time.perf_counter() - t0
             nn = int(rowptr[rows2])
             tot_nnz += nn
             tot_t += dt
             parts.append(f"p{p}/{name}:{rows2}rows/{nn}nnz")
-    return tot_nnz, tot_t, "oracle, 1 thread, leading rows of the workload: " + ", ".join(parts)
+    who = "1 thread" if threads == 1 else f"{threads} threads over row ranges"
+    return tot_nnz, tot_t, f"oracle, {who}, leading rows of the workload: " + ", ".join(parts)
 
 
-def _sample(oracle, p, mode, rowptr, colidx, vrec, xr, rows):
+def _sample(oracle, p, mode, rowptr, colidx, vrec, xr, rows, threads=1):
     e = int(rowptr[rows])
     rp = np.concatenate([rowptr[: rows + 1], np.full(len(rowptr) - rows - 1, e, np.int64)])
     L1 = p // 64 + 1
     vals = np.ascontiguousarray(vrec[:, :e].T)
     assert vals.shape == (e, L1)
-    y, st = oracle.spmv(p, mode, rp, colidx[:e], vals, xr, rows=(0, rows))
+    if threads <= 1:
+        y, st = oracle.spmv(p, mode, rp, colidx[:e], vals, xr, rows=(0, rows))
+        assert st == oracle.OK
+        return
+    from concurrent.futures import ThreadPoolExecutor
+
+    y = oracle.empty(p, len(rowptr) - 1)
+    cuts = np.searchsorted(rp[: rows + 1], np.linspace(0, e, threads + 1))
+    cuts = np.clip(cuts, 0, rows)
+    cuts[0], cuts[-1] = 0, rows
+    ranges = [(int(u), int(v)) for u, v in zip(cuts[:-1], cuts[1:]) if v > u]
+    ci = colidx[:e]
+    with ThreadPoolExecutor(len(ranges)) as ex:
+        sts = list(ex.map(lambda r: oracle.spmv(p, mode, rp, ci, vals, xr, rows=r, out=y)[1],
+                          ranges))
+    assert all(st == oracle.OK for st in sts)
+
+
+def oracle_solver_sample(iters=64):
+    """The oracle's GPBiCG on the 64x64 stencil at 128 bits (as the GPU
+    solver bench), the first `iters` iterations, one thread: ms per
+    iteration."""
+    import oracle
+    from paper_1411_2377_gb300 import synth
+
+    p = 128
+    rp, ci, v64 = synth.stencil2d(64, seed=0)
+    n = len(rp) - 1
+    vals = oracle.from_f64(p, v64)
+    b, st = oracle.spmv(p, oracle.EXACT, rp, ci, vals, oracle.from_f64(p, np.ones(n)))
     assert st == oracle.OK
+    t0 = time.perf_counter()
+    _, it, st, _ = oracle.gpbicg(p, oracle.ORDERED, rp, ci, vals, b, oracle.empty(p, n), 1e-30,
+                                 0.0, iters)
+    dt = time.perf_counter() - t0
+    return {"workload": "stencil2d_64x64_p128_gpbicg", "iters": int(it), "status": int(st),
+            "ms": round(dt * 1e3, 1), "ms_per_iter": round(dt * 1e3 / max(1, it), 3), "cores": 1}
 
 
 def build_workload(n, precs, on_gpu=True):
@@ -255,11 +305,12 @@ def run_reference(args):
     precs = [int(p) for p in args.precs.split(",")]
     rowptr, colidx, values, xs, _ = build_workload(args.n, precs)
     per_step = max(0.2, min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup)))
+    cores = host_cores()
     for _ in range(args.warmup):
-        oracle_sample(rowptr, colidx, values, xs, precs, per_step / 4)
+        oracle_sample(rowptr, colidx, values, xs, precs, per_step / 4, cores)
     nnz_tot, t_tot, desc = 0, 0.0, ""
     for _ in range(args.steps):
-        nn, dt, desc = oracle_sample(rowptr, colidx, values, xs, precs, per_step)
+        nn, dt, desc = oracle_sample(rowptr, colidx, values, xs, precs, per_step, cores)
         nnz_tot += nn
         t_tot += dt
     value = nnz_tot / t_tot / 1e9
@@ -270,7 +321,7 @@ def run_reference(args):
         "vs_baseline": None, "dtype": "u64 limbs (p-bit RN)", "data": "synthetic",
         "config": {"workload": CONFIG_NAME, "n": args.n, "precs": precs,
                    "modes": [m for m, _ in MODES]},
-        "cpu_baseline": {"value": value, "unit": "Gnnz/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "Gnnz/s", "cores": cores, "kind": "oracle",
                          "sample": desc},
         "e2e": {"value": value, "unit": "Gnnz/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
@@ -438,9 +489,19 @@ def run_native(args):
         from oracle.build import build_oracle
 
         build_oracle()
-        nn, dt, desc = oracle_sample(rowptr, colidx, values, xs, precs, args.cpu_seconds)
-        cpu = {"value": nn / dt / 1e9, "unit": "Gnnz/s", "cores": 1, "kind": "oracle",
-               "sample": desc}
+        cores = host_cores()
+        nn1, dt1, desc1 = oracle_sample(rowptr, colidx, values, xs, precs,
+                                        args.cpu_seconds / (2 if cores > 1 else 1))
+        cpu = {"value": nn1 / dt1 / 1e9, "unit": "Gnnz/s", "cores": 1, "kind": "oracle",
+               "sample": desc1}
+        if cores > 1:  # all host cores over row ranges; the single-thread figure beside it
+            nn, dt, desc = oracle_sample(rowptr, colidx, values, xs, precs,
+                                         args.cpu_seconds / 2, cores)
+            cpu = {"value": nn / dt / 1e9, "unit": "Gnnz/s", "cores": cores, "kind": "oracle",
+                   "sample": desc, "single_thread": {"value": cpu["value"], "cores": 1,
+                                                     "sample": desc1}}
+        if not args.no_solver:
+            cpu["solver"] = oracle_solver_sample()
 
     if rank == 0:
         line = {
@@ -667,6 +728,34 @@ def lotkin_bench(mpk, n=2000, precs=(128, 256, 512, 1024), s_list=(0.0, 50.0, 90
     return out
 
 
+def spmv_latency(mpk, A, x, mode, reps=100):
+    """Device time of one y = A x inside a CUDA graph of `reps` back-to-back
+    products (as the solvers launch them), in microseconds."""
+    import torch
+
+    y = mpk.Vec.empty(A.n, A.prec)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            mpk.spmv(A, x, y, mode=mode, sync=False)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, capture_error_mode="relaxed"):
+        for _ in range(reps):
+            mpk.spmv(A, x, y, mode=mode, sync=False)
+    g.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    g.replay()
+    e1.record()
+    e1.synchronize()
+    mpk.check()
+    return e0.elapsed_time(e1) * 1e3 / reps
+
+
 def solver_bench(mpk):
     """GPBiCG and BiCG (and CGS, BiCGSTAB) at 128 bits on the 64x64
     convection-diffusion system, b = A*ones, to relative residual 1e-30
@@ -680,6 +769,10 @@ def solver_bench(mpk):
     ones = mpk.Vec.from_f64(np.ones(n), p)
     b = mpk.spmv(A, ones, mode="exact")
     out = {"workload": "stencil2d_64x64_p128_rtol1e-30"}
+    nnz = int(rowptr[-1])
+    for m in ("ordered", "exact"):  # the solvers' product alone: latency-bound at this size
+        us = spmv_latency(mpk, A, b, m)
+        out[f"spmv_{m}"] = {"us": round(us, 2), "gnnz_s": round(nnz / (us * 1e-6) / 1e9, 2)}
     for name, fn in (("gpbicg", mpk.gpbicg), ("bicg", mpk.bicg), ("cgs", mpk.cgs),
                      ("bicgstab", mpk.bicgstab)):
         fn(A, b, rtol=1e-30, maxit=2000, poll_every=32)  # warm-up

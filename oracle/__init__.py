@@ -133,12 +133,21 @@ def to_f64(p, a):
     return d
 
 
-def spmv(p, mode, rowptr, colidx, vals, x, rows=None):
-    """y = A x (all rows, or rows[0]:rows[1] with the rest left as +0)."""
+def spmv(p, mode, rowptr, colidx, vals, x, rows=None, out=None):
+    """y = A x (all rows, or rows[0]:rows[1] with the rest left as +0).
+    out: optional (n, p/64 + 1) uint64 C-contiguous record array written in
+    place (only the computed rows), so that callers splitting the rows over
+    threads share one result."""
     rowptr, colidx = _csr(rowptr, colidx)
     vals, x = _recs(vals, p), _recs(x, p)
     n = rowptr.shape[0] - 1
-    y = empty(p, n)
+    if out is None:
+        y = empty(p, n)
+    else:
+        if (out.dtype != np.uint64 or out.shape != (n, p // 64 + 1)
+                or not out.flags["C_CONTIGUOUS"]):
+            raise ValueError("out must be a C-contiguous (n, p/64 + 1) uint64 array")
+        y = out
     r0, r1 = (0, n) if rows is None else rows
     st = _load().mpo_spmv_rows(p, mode, n, _p(rowptr, _i64p), _p(colidx, _i32p),
                                _p(vals, _u64p), _p(x, _u64p), _p(y, _u64p), r0, r1)

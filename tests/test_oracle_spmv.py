@@ -215,3 +215,28 @@ def test_axpy_and_residual(p):
     res0, _ = oracle.residual(p, rowptr, colidx, vals, y, oracle.empty(p, n))
     for i in range(n):
         assert exact.decode(res0[i], p).q == Y[i].q
+
+
+@pytest.mark.parametrize("mode", (oracle.ORDERED, oracle.EXACT))
+def test_row_ranges_on_threads_match_one_call(mode):
+    """Rows are independent: splitting them over host threads that write one
+    shared result (the CPU baseline's all-cores form) gives the one-call
+    result bit for bit."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    p, n = 256, 3000
+    rowptr, colidx = synth.spmv_pattern(n, seed=5)
+    nnz = int(rowptr[-1])
+    vals = rand_recs(nnz, p, 501, zero_frac=0.01, emin=-40, emax=40)
+    x = rand_recs(n, p, 502, zero_frac=0.0, emin=-40, emax=40)
+    want, st = oracle.spmv(p, mode, rowptr, colidx, vals, x)
+    assert st == oracle.OK
+    y = oracle.empty(p, n)
+    cuts = [0, 1, 700, 701, 1900, n]
+    with ThreadPoolExecutor(4) as ex:
+        sts = list(ex.map(lambda r: oracle.spmv(p, mode, rowptr, colidx, vals, x, rows=r,
+                                                out=y)[1], zip(cuts[:-1], cuts[1:])))
+    assert all(s == oracle.OK for s in sts)
+    assert np.array_equal(y, want)
+    with pytest.raises(ValueError):
+        oracle.spmv(p, mode, rowptr, colidx, vals, x, out=np.zeros((n, 3), np.uint64))
