@@ -1,7 +1,8 @@
 """CPU oracle for the p-bit CSR SpMV / exact dot / BiCG / GPBiCG path.
 
-TEST INFRASTRUCTURE ONLY.  This package wraps ``libmpo.so`` (plain C, built from
-``oracle/mpo.c``).  Only the test suite, ``__graft_entry__.smoke()`` and the
+TEST INFRASTRUCTURE ONLY.  This package wraps ``libmpo.so`` and
+``libmpo_wide.so`` (plain C, both built from ``oracle/mpo.c``; the wide build
+holds mantissas up to 8192 bits).  Only the test suite, ``__graft_entry__.smoke()`` and the
 benchmark's CPU-baseline leg may import it; the product package never does.
 
 Values are exchanged as numpy ``uint64`` arrays of shape ``(n, L+1)`` with
@@ -23,7 +24,7 @@ OP_MUL, OP_ADD, OP_SUB, OP_DIV = 0, 1, 2, 3
 EXP_ZERO = -(1 << 61)
 SPAN_CAP = 16384
 
-_lib = None
+_lib = {}
 
 _u64p = ctypes.POINTER(ctypes.c_uint64)
 _i64p = ctypes.POINTER(ctypes.c_int64)
@@ -33,11 +34,13 @@ _i32 = ctypes.c_int
 _i64 = ctypes.c_int64
 
 
-def _load():
-    global _lib
-    if _lib is not None:
-        return _lib
-    path = lib_path()
+def _load(p=0):
+    """The library for precision p: libmpo.so up to 1024 bits, the wide
+    build (same source, 256-word mantissas) above."""
+    wide = p > 1024
+    if _lib.get(wide) is not None:
+        return _lib[wide]
+    path = lib_path(wide)
     if not os.path.exists(path):
         build_oracle()
     lib = ctypes.CDLL(path)
@@ -70,7 +73,7 @@ def _load():
         f = getattr(lib, name)
         f.argtypes = args
         f.restype = ctypes.c_int
-    _lib = lib
+    _lib[wide] = lib
     return lib
 
 
@@ -102,14 +105,14 @@ def empty(p, n):
 def ewise(p, op, a, b):
     a, b = _recs(a, p), _recs(b, p)
     r = np.empty_like(a)
-    st = _load().mpo_ewise(p, op, a.shape[0], _p(a, _u64p), _p(b, _u64p), _p(r, _u64p))
+    st = _load(p).mpo_ewise(p, op, a.shape[0], _p(a, _u64p), _p(b, _u64p), _p(r, _u64p))
     return r, st
 
 
 def cmp(p, a, b):
     a, b = _recs(a, p), _recs(b, p)
     out = ctypes.c_int(0)
-    st = _load().mpo_cmp(p, _p(a, _u64p), _p(b, _u64p), ctypes.byref(out))
+    st = _load(p).mpo_cmp(p, _p(a, _u64p), _p(b, _u64p), ctypes.byref(out))
     if st:
         raise ValueError(f"mpo_cmp status {st}")
     return out.value
@@ -118,7 +121,7 @@ def cmp(p, a, b):
 def from_f64(p, d):
     d = np.ascontiguousarray(d, dtype=np.float64).ravel()
     r = np.empty((d.shape[0], p // 64 + 1), dtype=np.uint64)
-    st = _load().mpo_from_f64(p, d.shape[0], _p(d, _f64p), _p(r, _u64p))
+    st = _load(p).mpo_from_f64(p, d.shape[0], _p(d, _f64p), _p(r, _u64p))
     if st:
         raise ValueError(f"mpo_from_f64 status {st}")
     return r
@@ -127,7 +130,7 @@ def from_f64(p, d):
 def to_f64(p, a):
     a = _recs(a, p)
     d = np.empty(a.shape[0], dtype=np.float64)
-    st = _load().mpo_to_f64(p, a.shape[0], _p(a, _u64p), _p(d, _f64p))
+    st = _load(p).mpo_to_f64(p, a.shape[0], _p(a, _u64p), _p(d, _f64p))
     if st:
         raise ValueError(f"mpo_to_f64 status {st}")
     return d
@@ -149,7 +152,7 @@ def spmv(p, mode, rowptr, colidx, vals, x, rows=None, out=None):
             raise ValueError("out must be a C-contiguous (n, p/64 + 1) uint64 array")
         y = out
     r0, r1 = (0, n) if rows is None else rows
-    st = _load().mpo_spmv_rows(p, mode, n, _p(rowptr, _i64p), _p(colidx, _i32p),
+    st = _load(p).mpo_spmv_rows(p, mode, n, _p(rowptr, _i64p), _p(colidx, _i32p),
                                _p(vals, _u64p), _p(x, _u64p), _p(y, _u64p), r0, r1)
     return y, st
 
@@ -159,7 +162,7 @@ def spmv_t(p, mode, rowptr, colidx, vals, x):
     vals, x = _recs(vals, p), _recs(x, p)
     n = rowptr.shape[0] - 1
     y = empty(p, n)
-    st = _load().mpo_spmv_t(p, mode, n, _p(rowptr, _i64p), _p(colidx, _i32p),
+    st = _load(p).mpo_spmv_t(p, mode, n, _p(rowptr, _i64p), _p(colidx, _i32p),
                             _p(vals, _u64p), _p(x, _u64p), _p(y, _u64p))
     return y, st
 
@@ -172,7 +175,7 @@ def transpose(p, rowptr, colidx, vals):
     trp = np.empty(n + 1, dtype=np.int64)
     tci = np.empty(max(nnz, 1), dtype=np.int32)
     tv = np.empty((max(nnz, 1), p // 64 + 1), dtype=np.uint64)
-    st = _load().mpo_transpose(p, n, _p(rowptr, _i64p), _p(colidx, _i32p), _p(vals, _u64p),
+    st = _load(p).mpo_transpose(p, n, _p(rowptr, _i64p), _p(colidx, _i32p), _p(vals, _u64p),
                                _p(trp, _i64p), _p(tci, _i32p), _p(tv, _u64p))
     if st:
         raise ValueError(f"mpo_transpose status {st}")
@@ -182,14 +185,14 @@ def transpose(p, rowptr, colidx, vals):
 def dot(p, x, y):
     x, y = _recs(x, p), _recs(y, p)
     out = empty(p, 1)
-    st = _load().mpo_dot(p, x.shape[0], _p(x, _u64p), _p(y, _u64p), _p(out, _u64p))
+    st = _load(p).mpo_dot(p, x.shape[0], _p(x, _u64p), _p(y, _u64p), _p(out, _u64p))
     return out[0], st
 
 
 def axpy(p, alpha, x, y):
     alpha, x = _recs(alpha, p), _recs(x, p)
     y = _recs(y, p).copy()
-    st = _load().mpo_axpy(p, x.shape[0], _p(alpha, _u64p), _p(x, _u64p), _p(y, _u64p))
+    st = _load(p).mpo_axpy(p, x.shape[0], _p(alpha, _u64p), _p(x, _u64p), _p(y, _u64p))
     return y, st
 
 
@@ -197,7 +200,7 @@ def residual(p, rowptr, colidx, vals, b, x):
     rowptr, colidx = _csr(rowptr, colidx)
     vals, b, x = _recs(vals, p), _recs(b, p), _recs(x, p)
     r = np.empty_like(b)
-    st = _load().mpo_residual(p, b.shape[0], _p(rowptr, _i64p), _p(colidx, _i32p),
+    st = _load(p).mpo_residual(p, b.shape[0], _p(rowptr, _i64p), _p(colidx, _i32p),
                               _p(vals, _u64p), _p(b, _u64p), _p(x, _u64p), _p(r, _u64p))
     return r, st
 
@@ -216,22 +219,22 @@ def _solve(fn, p, mode, rowptr, colidx, vals, b, x0, rtol, atol, maxit):
 
 def bicg(p, mode, rowptr, colidx, vals, b, x0, rtol, atol, maxit):
     """Returns (x, iterations, status, history of (r_i, r_i))."""
-    return _solve(_load().mpo_bicg, p, mode, rowptr, colidx, vals, b, x0, rtol, atol, maxit)
+    return _solve(_load(p).mpo_bicg, p, mode, rowptr, colidx, vals, b, x0, rtol, atol, maxit)
 
 
 def gpbicg(p, mode, rowptr, colidx, vals, b, x0, rtol, atol, maxit):
     """Returns (x, iterations, status, history of (r_i, r_i))."""
-    return _solve(_load().mpo_gpbicg, p, mode, rowptr, colidx, vals, b, x0, rtol, atol, maxit)
+    return _solve(_load(p).mpo_gpbicg, p, mode, rowptr, colidx, vals, b, x0, rtol, atol, maxit)
 
 
 def cgs(p, mode, rowptr, colidx, vals, b, x0, rtol, atol, maxit):
     """CGS (textbook form).  Returns (x, iterations, status, history of (r_i, r_i))."""
-    return _solve(_load().mpo_cgs, p, mode, rowptr, colidx, vals, b, x0, rtol, atol, maxit)
+    return _solve(_load(p).mpo_cgs, p, mode, rowptr, colidx, vals, b, x0, rtol, atol, maxit)
 
 
 def bicgstab(p, mode, rowptr, colidx, vals, b, x0, rtol, atol, maxit):
     """BiCGSTAB (textbook form).  Returns (x, iterations, status, history of (r_i, r_i))."""
-    return _solve(_load().mpo_bicgstab, p, mode, rowptr, colidx, vals, b, x0, rtol, atol, maxit)
+    return _solve(_load(p).mpo_bicgstab, p, mode, rowptr, colidx, vals, b, x0, rtol, atol, maxit)
 
 
 def ilu0(p, rowptr, colidx, vals):
@@ -239,7 +242,7 @@ def ilu0(p, rowptr, colidx, vals):
     rowptr, colidx = _csr(rowptr, colidx)
     vals = _recs(vals, p)
     lu = np.empty_like(vals)
-    st = _load().mpo_ilu0(p, rowptr.shape[0] - 1, _p(rowptr, _i64p), _p(colidx, _i32p),
+    st = _load(p).mpo_ilu0(p, rowptr.shape[0] - 1, _p(rowptr, _i64p), _p(colidx, _i32p),
                           _p(vals, _u64p), _p(lu, _u64p))
     return lu, st
 
@@ -249,7 +252,7 @@ def ilu0_apply(p, rowptr, colidx, lu, r):
     rowptr, colidx = _csr(rowptr, colidx)
     lu, r = _recs(lu, p), _recs(r, p)
     w = np.empty_like(r)
-    st = _load().mpo_ilu0_apply(p, rowptr.shape[0] - 1, _p(rowptr, _i64p), _p(colidx, _i32p),
+    st = _load(p).mpo_ilu0_apply(p, rowptr.shape[0] - 1, _p(rowptr, _i64p), _p(colidx, _i32p),
                                 _p(lu, _u64p), _p(r, _u64p), _p(w, _u64p))
     return w, st
 
@@ -257,5 +260,5 @@ def ilu0_apply(p, rowptr, colidx, lu, r):
 def bicgstab_ilu0(p, mode, rowptr, colidx, vals, b, x0, rtol, atol, maxit):
     """BiCGSTAB right-preconditioned with ILU(0).  Returns (x, iterations,
     status, history of (r_i, r_i))."""
-    return _solve(_load().mpo_bicgstab_ilu0, p, mode, rowptr, colidx, vals, b, x0, rtol, atol,
+    return _solve(_load(p).mpo_bicgstab_ilu0, p, mode, rowptr, colidx, vals, b, x0, rtol, atol,
                   maxit)

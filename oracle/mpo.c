@@ -18,7 +18,11 @@
 #include <stdlib.h>
 #include <string.h>
 
-#define WMAX 32 /* 32-bit words in a 1024-bit mantissa */
+/* 32-bit words of the largest mantissa this build holds: 32 (p <= 1024) by
+ * default, 256 (p <= 8192) in the wide build (-DWMAX=256). */
+#ifndef WMAX
+#define WMAX 32
+#endif
 
 typedef struct {
   int neg;  /* 1 = negative */
@@ -32,7 +36,10 @@ static void die(const char *msg) {
   abort();
 }
 
-static int prec_ok(int p) { return p == 128 || p == 256 || p == 512 || p == 1024; }
+static int prec_ok(int p) {
+  return (p == 128 || p == 256 || p == 512 || p == 1024 || p == 2048 || p == 4096 || p == 8192) &&
+         p / 32 <= WMAX;
+}
 
 /* ------------------------------------------------------------------------ */
 /* Natural numbers: little-endian 32-bit words                              */

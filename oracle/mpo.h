@@ -7,7 +7,9 @@
  *
  * Arithmetic follows the paper's MPFR setting (Section 2): every operation is a
  * correctly rounded binary operation at precision p, round-to-nearest with ties
- * to even (MPFR's RN).  p is one of 128, 256, 512, 1024.
+ * to even (MPFR's RN).  p is one of 128, 256, 512, 1024 (libmpo.so) or also
+ * 2048, 4096, 8192 (libmpo_wide.so, the same source built with -DWMAX=256;
+ * the paper's solves of Tables 1-2 need up to 8192 bits).
  *
  * Value record ("interchange record"), L = p/64 uint64 words + 1 head word:
  *   rec[0]     head = exp*2 + sign   (int64; sign 1 = negative)

@@ -12,6 +12,7 @@ import oracle
 from paper_1411_2377_gb300 import synth
 
 PRECS = (128, 256, 512, 1024)
+WIDE = (2048, 4096, 8192)  # the wide build (the paper's solves of Tables 1-2 reach 8192 bits)
 OPS = {
     oracle.OP_MUL: exact.rmul,
     oracle.OP_ADD: exact.radd,
@@ -52,10 +53,30 @@ def test_random_pairs_vs_fractions(p, op):
         check_ewise(p, op, a, b)
 
 
-@pytest.mark.parametrize("p", PRECS)
+@pytest.mark.parametrize("p", WIDE)
+@pytest.mark.parametrize("op", list(OPS))
+def test_wide_random_pairs_vs_fractions(p, op):
+    """The wide build at 2048-8192 bits against exact rationals."""
+    n = 60
+    for seed, (emin, emax) in ((31, (-3, 3)), (32, (-2 * p, 2 * p))):
+        a = synth.planes_to_records(synth.random_values(n, p, seed + op, zero_frac=0.05,
+                                                        emin=emin, emax=emax))
+        b = synth.planes_to_records(synth.random_values(n, p, seed + 100 + op, zero_frac=0.05,
+                                                        emin=emin, emax=emax))
+        check_ewise(p, op, a, b)
+
+
+def test_narrow_build_rejects_wide_precisions():
+    """libmpo.so holds 1024-bit mantissas at most and says so."""
+    a = oracle.empty(2048, 1)
+    assert oracle._load(0).mpo_dot(2048, 1, oracle._p(a, oracle._u64p), oracle._p(a, oracle._u64p),
+                                   oracle._p(a, oracle._u64p)) == oracle.ERR_PREC
+
+
+@pytest.mark.parametrize("p", PRECS + (2048,))
 def test_random_pairs_vs_mpmath(p):
     libmp = pytest.importorskip("mpmath.libmp")
-    n = 3000
+    n = 3000 if p <= 1024 else 500
     a = synth.planes_to_records(synth.random_values(n, p, 21, zero_frac=0.0, emin=-70, emax=70))
     b = synth.planes_to_records(synth.random_values(n, p, 22, zero_frac=0.0, emin=-70, emax=70))
 
@@ -76,7 +97,7 @@ def test_random_pairs_vs_mpmath(p):
             assert (-1) ** sign * Fraction(man) * Fraction(2) ** ex == got, (op, i)
 
 
-@pytest.mark.parametrize("p", PRECS)
+@pytest.mark.parametrize("p", PRECS + WIDE)
 def test_product_ties_both_parities(p):
     """Products whose exact value lies exactly halfway between two p-bit
     numbers: Ma = 2^(p-1) + k (k odd and even) times Mb = 3 * 2^(p-2)."""
@@ -93,7 +114,7 @@ def test_product_ties_both_parities(p):
     check_ewise(p, oracle.OP_MUL, np.stack(a), np.stack(b))
 
 
-@pytest.mark.parametrize("p", PRECS)
+@pytest.mark.parametrize("p", PRECS + WIDE)
 def test_sum_ties_carry_and_binade_edges(p):
     """x + y where y sits at or just below half an ulp of x, including the
     power-of-two x whose lower neighbour is only half an ulp away, and sums
@@ -117,7 +138,7 @@ def test_sum_ties_carry_and_binade_edges(p):
     assert exact.decode(r[0], p).q == 1
 
 
-@pytest.mark.parametrize("p", (128, 1024))
+@pytest.mark.parametrize("p", (128, 1024, 8192))
 def test_signed_zero_table(p):
     """IEEE/MPFR signed-zero rules in round-to-nearest."""
     pz = exact.encode(exact.Val(Fraction(0)), p)
@@ -136,7 +157,7 @@ def test_signed_zero_table(p):
     assert exact.decode(r[1], p).key() == (0, True)
 
 
-@pytest.mark.parametrize("p", PRECS)
+@pytest.mark.parametrize("p", PRECS + WIDE)
 def test_division_exact_quotients_and_zero_divisor(p):
     ints = [1, 2, 3, 5, 6, 7, 10, 12, 48, 96, 1 << 40, 3 << 60]
     a = np.stack([exact.encode(exact.Val(Fraction(x * y)), p) for x in ints for y in ints])
@@ -150,7 +171,7 @@ def test_division_exact_quotients_and_zero_divisor(p):
     assert st == oracle.ERR_DIVZERO
 
 
-@pytest.mark.parametrize("p", PRECS)
+@pytest.mark.parametrize("p", PRECS + WIDE)
 def test_compare(p):
     vals = [Fraction(-3), Fraction(-1, 3), Fraction(0), Fraction(1, 7), Fraction(2), Fraction(1 << 200)]
     recs = [exact.encode(exact.Val(exact.round_rne(v, p)), p) for v in vals]
@@ -161,7 +182,7 @@ def test_compare(p):
     assert oracle.cmp(p, nz, recs[2]) == 0
 
 
-@pytest.mark.parametrize("p", PRECS)
+@pytest.mark.parametrize("p", PRECS + WIDE)
 def test_from_f64_is_exact(p):
     d = np.array([0.0, -0.0, 1.0, -1.5, 0.1, 1e300, -1e-300, 5e-324, -2.2250738585072014e-308,
                   np.nextafter(1.0, 2.0), 2.0 ** 1023 * 1.9999999999999998, 123456.789])

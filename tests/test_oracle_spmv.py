@@ -32,7 +32,8 @@ def exact_row(vals, cols, x, p):
     return exact.exact_sum([a.q * x[c].q for a, c in zip(vals, cols)], p)
 
 
-CASES = [(128, 7, 0.5), (128, 9, 0.3), (256, 8, 0.4), (512, 6, 0.6), (1024, 5, 0.7)]
+CASES = [(128, 7, 0.5), (128, 9, 0.3), (256, 8, 0.4), (512, 6, 0.6), (1024, 5, 0.7),
+         (2048, 6, 0.5), (4096, 5, 0.5), (8192, 4, 0.7)]
 
 
 @pytest.mark.parametrize("p,n,density", CASES)
@@ -133,7 +134,7 @@ def test_transpose_vs_dense(p):
             assert exact.same(want, exact.decode(y[j], p))
 
 
-@pytest.mark.parametrize("p", (128, 256, 512, 1024))
+@pytest.mark.parametrize("p", (128, 256, 512, 1024, 2048, 8192))
 def test_dot_vs_fractions(p):
     for seed, (emin, emax) in ((1, (-5, 5)), (2, (-300, 300))):
         n = 257
@@ -146,7 +147,7 @@ def test_dot_vs_fractions(p):
         assert exact.same(want, exact.decode(r, p))
 
 
-@pytest.mark.parametrize("p", (128, 256))
+@pytest.mark.parametrize("p", (128, 256, 8192))
 def test_dot_cancellation_and_zeros(p):
     x = rand_recs(50, p, 71, zero_frac=0.0)
     y = rand_recs(50, p, 72, zero_frac=0.0)
@@ -168,7 +169,7 @@ def test_dot_cancellation_and_zeros(p):
     assert exact.decode(r, p).q == exact.round_rne(1 + Fraction(3, 2 ** p), p)
 
 
-@pytest.mark.parametrize("p", (128, 512))
+@pytest.mark.parametrize("p", (128, 512, 2048))
 def test_span_cap(p):
     """Exponent spans up to the cap are summed exactly; beyond it both
     implementations report a span error (the row becomes +0)."""
@@ -193,7 +194,7 @@ def test_span_cap(p):
         assert exact.decode(yv[1], p).q == 1  # the other row is unaffected
 
 
-@pytest.mark.parametrize("p", (128, 1024))
+@pytest.mark.parametrize("p", (128, 1024, 4096))
 def test_axpy_and_residual(p):
     n = 30
     x = rand_recs(n, p, 81)
