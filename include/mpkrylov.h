@@ -11,10 +11,14 @@
  *
  * Number format.  A value is (-1)^s * M * 2^(e-p) with 2^(p-1) <= M < 2^p
  * (MPFR's 0.1xxx_2 * 2^e convention, Section 2), or a signed zero
- * (e == MP_EXP_ZERO, M = 0).  p is one of 128, 256, 512, 1024.  Every
- * operation rounds to nearest, ties to even (MPFR's RN); NaN, infinities and
- * the other rounding modes are not represented.  Nonzero exponents must
- * satisfy |e| < 2^60.
+ * (e == MP_EXP_ZERO, M = 0).  p is one of 128, 256, 512, 1024 for every
+ * call; p = 2048, 4096, 8192 (the precisions at which the solves of the
+ * paper's Tables 1-2 converge) are accepted by mp_csr_create,
+ * mp_csr_create_f64, mp_spmv, mp_spmv_t (both modes), mp_dot and mp_axpy,
+ * which run a warp-per-value form there; every other call returns
+ * MP_ERR_PREC for them.  Every operation rounds to nearest, ties to even
+ * (MPFR's RN); NaN, infinities and the other rounding modes are not
+ * represented.  Nonzero exponents must satisfy |e| < 2^60.
  *
  * Memory layout ("planes").  A vector of n values with L = p/64 is L+1
  * planes of uint64 words: plane 0 holds the head words e*2 + s (as int64
@@ -45,7 +49,7 @@ extern "C" {
 typedef enum {
   MP_OK = 0,
   MP_ERR_ARG = 1,       /* invalid argument; mp_last_error() has the details */
-  MP_ERR_PREC = 2,      /* prec_bits not in {128, 256, 512, 1024}             */
+  MP_ERR_PREC = 2,      /* prec_bits not supported by the call (see above)    */
   MP_ERR_ALLOC = 3,     /* device or host allocation failed                    */
   MP_ERR_CUDA = 4,      /* a CUDA call failed (no device, launch error, ...)   */
   MP_ERR_SPAN = 5,      /* exact sum with exponent span > MP_SPAN_CAP          */

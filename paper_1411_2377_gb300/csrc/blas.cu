@@ -382,12 +382,13 @@ extern "C" {
 
 mp_status mp_dot(mp_vec x, mp_vec y, mp_vec out, void* stream) {
   mp_status r;
-  if (!prec_ok(x.prec_bits)) return set_error(MP_ERR_PREC, "precision %d", x.prec_bits);
+  const bool big = prec_big(x.prec_bits);
+  if (!prec_ok(x.prec_bits) && !big) return set_error(MP_ERR_PREC, "precision %d", x.prec_bits);
   if ((r = check_vec(x, x.n, x.prec_bits, "x")) != MP_OK) return r;
   if ((r = check_vec(y, x.n, x.prec_bits, "y")) != MP_OK) return r;
   if ((r = check_vec(out, 1, x.prec_bits, "out")) != MP_OK) return r;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const size_t bytes = dot_scratch_bytes(x.prec_bits, 1);
+  const size_t bytes = big ? dot_big_scratch_bytes(x.prec_bits) : dot_scratch_bytes(x.prec_bits, 1);
   int dev = 0;
   MPK_CUDA(cudaGetDevice(&dev));
   void* scratch = nullptr;
@@ -401,6 +402,9 @@ mp_status mp_dot(mp_vec x, mp_vec y, mp_vec out, void* stream) {
       g_dot_bytes[dev] = bytes;
     }
   }
+  if (big)
+    return launch_dot_big(x.prec_bits, x.data, x.ld, y.data, y.ld, x.n, out.data, out.ld, scratch,
+                          st);
   DotArgs a;
   a.k = 1;
   a.n = x.n;
@@ -415,12 +419,14 @@ mp_status mp_dot(mp_vec x, mp_vec y, mp_vec out, void* stream) {
 
 mp_status mp_axpy(mp_vec alpha, mp_vec x, mp_vec y, void* stream) {
   mp_status r;
-  if (!prec_ok(x.prec_bits)) return set_error(MP_ERR_PREC, "precision %d", x.prec_bits);
+  const bool big = prec_big(x.prec_bits);
+  if (!prec_ok(x.prec_bits) && !big) return set_error(MP_ERR_PREC, "precision %d", x.prec_bits);
   if ((r = check_vec(alpha, 1, x.prec_bits, "alpha")) != MP_OK) return r;
   if ((r = check_vec(x, x.n, x.prec_bits, "x")) != MP_OK) return r;
   if ((r = check_vec(y, x.n, x.prec_bits, "y")) != MP_OK) return r;
   if (x.n == 0) return MP_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (big) return launch_axpy_big(x.prec_bits, alpha.data, x.n, x.data, x.ld, y.data, y.ld, st);
   return dispatch_w(x.prec_bits, [&](auto w) {
     constexpr int W = decltype(w)::value;
     axpy_kernel<W><<<ew_blocks(x.n), 256, 0, st>>>(alpha.data, x.n, x.data, x.ld, y.data, y.ld);

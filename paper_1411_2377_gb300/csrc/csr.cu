@@ -53,6 +53,29 @@ __global__ void f64_to_planes(const double* __restrict__ d, int64_t n, uint64_t*
   }
 }
 
+// The same for p > 1024 (L limbs): a double's 53-bit mantissa m lands in
+// the top limb (M = m 2^(p-53)), the other limbs are zero.
+__global__ void f64_to_planes_wide(const double* __restrict__ d, int64_t n, int L,
+                                   uint64_t* __restrict__ out, unsigned long long* bad) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const double v = d[k];
+    uint64_t top = 0;
+    int64_t e = EXP_ZERO;
+    if (!isfinite(v)) {
+      atomicMin(bad, (unsigned long long)k);
+    } else if (v != 0.0) {
+      int ex = 0;
+      const double f = frexp(fabs(v), &ex);  // [1/2, 1)
+      top = (uint64_t)ldexp(f, 53) << 11;
+      e = ex;
+    }
+    out[k] = pack_head(e, signbit(v) ? 1u : 0u);
+    for (int j = 1; j < L; ++j) out[(int64_t)j * n + k] = 0;
+    out[(int64_t)L * n + k] = top;
+  }
+}
+
 // out slot s <- raw value src[s] (padding slots, src = -1, become +0).
 __global__ void gather_planes(const uint64_t* __restrict__ raw, int64_t nnz,
                               const int64_t* __restrict__ src, int64_t nslots, int L,
@@ -222,7 +245,8 @@ mp_status create_impl(int64_t n, const int64_t* rowptr, const int32_t* colidx,
                       int32_t flags, void* stream, mp_csr* out) {
   if (!out) return set_error(MP_ERR_ARG, "out is null");
   *out = nullptr;
-  if (!prec_ok(prec)) return set_error(MP_ERR_PREC, "precision %d not in {128,256,512,1024}", prec);
+  if (!prec_ok(prec) && !prec_big(prec))
+    return set_error(MP_ERR_PREC, "precision %d not in {128,256,512,1024,2048,4096,8192}", prec);
   if (n < 0 || n >= (int64_t(1) << 31)) return set_error(MP_ERR_ARG, "n = %lld out of range", (long long)n);
   if (!rowptr) return set_error(MP_ERR_ARG, "rowptr is null");
   if (rowptr[0] != 0) return set_error(MP_ERR_ARG, "rowptr[0] = %lld, expected 0", (long long)rowptr[0]);
@@ -307,12 +331,18 @@ mp_status create_impl(int64_t n, const int64_t* rowptr, const int32_t* colidx,
       double* d64 = nullptr;
       if ((r = dalloc(&d64, nnz, tmp)) != MP_OK) return fail(r);
       cudaMemcpyAsync(d64, values64, (size_t)nnz * 8, cudaMemcpyHostToDevice, st);
-      r = dispatch_w(prec, [&](auto w) {
-        constexpr int W = decltype(w)::value;
-        f64_to_planes<W><<<grid_for(nnz, 256), 256, 0, st>>>(d64, nnz, d_raw, d_bad);
+      if (prec_big(prec)) {
+        f64_to_planes_wide<<<grid_for(nnz, 256), 256, 0, st>>>(d64, nnz, L, d_raw, d_bad);
         count_launch();
-        return launch_check("f64_to_planes");
-      });
+        r = launch_check("f64_to_planes_wide");
+      } else {
+        r = dispatch_w(prec, [&](auto w) {
+          constexpr int W = decltype(w)::value;
+          f64_to_planes<W><<<grid_for(nnz, 256), 256, 0, st>>>(d64, nnz, d_raw, d_bad);
+          count_launch();
+          return launch_check("f64_to_planes");
+        });
+      }
       cudaStreamSynchronize(st);
       cudaFree(d64);
       if (r != MP_OK) return fail(r);

@@ -99,6 +99,8 @@ mp_status launch_check(const char* what);  // cudaGetLastError after a launch
 
 // ---- precision ------------------------------------------------------------
 inline bool prec_ok(int p) { return p == 128 || p == 256 || p == 512 || p == 1024; }
+// 2048, 4096, 8192: one value per warp (bigp.cu); SpMV, dot and axpy only.
+inline bool prec_big(int p) { return p == 2048 || p == 4096 || p == 8192; }
 inline int planes_of(int p) { return p / 64 + 1; }
 
 mp_status check_vec(const mp_vec& v, int64_t n, int prec, const char* name);
@@ -114,6 +116,17 @@ mp_status dispatch_w(int p, F&& f) {
     default: return set_error(MP_ERR_PREC, "precision %d not in {128,256,512,1024}", p);
   }
 }
+
+// ---- p > 1024 (bigp.cu) ------------------------------------------------------
+mp_status launch_spmv_big(const mp_csr_s* M, const Sell& S, int mode, const uint64_t* x,
+                          int64_t ldx, uint64_t* y, int64_t ldy, const int* gate,
+                          cudaStream_t st);
+size_t dot_big_scratch_bytes(int prec);
+// scratch: a dot scratch whose header span slots are (+inf, -inf)
+mp_status launch_dot_big(int prec, const uint64_t* x, int64_t ldx, const uint64_t* y, int64_t ldy,
+                         int64_t n, uint64_t* out, int64_t ldo, void* scratch, cudaStream_t st);
+mp_status launch_axpy_big(int prec, const uint64_t* al, int64_t n, const uint64_t* x, int64_t ldx,
+                          uint64_t* y, int64_t ldy, cudaStream_t st);
 
 // ---- scratch ---------------------------------------------------------------
 // Per-device scratch of the standalone dot product (grown on demand).

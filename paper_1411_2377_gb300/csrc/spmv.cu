@@ -828,6 +828,10 @@ mp_status check_spmv_args(mp_csr A, const mp_vec& x, const mp_vec& y, int mode) 
 mp_status launch_spmv(const mp_csr_s* M, const Sell& S, int mode, const uint64_t* x, int64_t ldx,
                       uint64_t* y, int64_t ldy, const uint64_t* b, int64_t ldb, const int* gate,
                       cudaStream_t st) {
+  if (prec_big(M->prec)) {
+    if (b) return set_error(MP_ERR_PREC, "residual at p = %d: only p <= 1024", M->prec);
+    return launch_spmv_big(M, S, mode, x, ldx, y, ldy, gate, st);
+  }
   return dispatch_w(M->prec, [&](auto w) {
     constexpr int W = decltype(w)::value;
     return spmv_w<W>(M, S, mode, x, ldx, y, ldy, b, ldb, gate, st);
@@ -896,6 +900,9 @@ mp_status mp_csr_tune(mp_csr A, int32_t mode, int32_t reps, int32_t* tpb_out, in
   if (!A) return set_error(MP_ERR_ARG, "matrix is null");
   if (mode != MP_ORDERED && mode != MP_EXACT) return set_error(MP_ERR_ARG, "mode %d", mode);
   if (reps < 1) return set_error(MP_ERR_ARG, "reps %d", reps);
+  if (prec_big(A->prec))
+    return set_error(MP_ERR_PREC, "p = %d runs one fixed warp-per-row form; the tuner covers p <= 1024",
+                     A->prec);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int L = A->prec / 64;
   const int64_t n = A->n > 0 ? A->n : 1;

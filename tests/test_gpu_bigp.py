@@ -1,0 +1,167 @@
+"""p = 2048, 4096, 8192 (the warp-per-value form): SpMV in both modes and
+its transpose, exact dots and axpy on the GPU vs the oracle's wide build, bit
+for bit, through the C ABI; calls outside that set refuse the precision."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import assert_bitwise, need_gpu, rand_planes, random_csr, recs
+
+pytestmark = pytest.mark.gpu
+WIDE = (2048, 4096, 8192)
+MODES = (("ordered", oracle.ORDERED), ("exact", oracle.EXACT))
+
+
+@pytest.mark.parametrize("p", WIDE)
+def test_spmv_and_transpose(p):
+    """Ragged rows (empty, long), 5% explicit zeros, n not a multiple of 32,
+    exponents over +-40 (ORDERED rounds every product and sum)."""
+    mpk = need_gpu()
+    n = {2048: 301, 4096: 133, 8192: 70}[p]
+    rowptr, colidx = random_csr(n, seed=p + 1, mean_len=8, max_len=60, empty_every=13)
+    V = rand_planes(len(colidx), p, 31, zero_frac=0.05, emin=-40, emax=40)
+    X = rand_planes(n, p, 32, zero_frac=0.05, emin=-40, emax=40)
+    A = mpk.CSR(rowptr, colidx, V, p, transpose=True)
+    x = mpk.Vec.from_planes(X, p)
+    for name, m in MODES:
+        want, st = oracle.spmv(p, m, rowptr, colidx, recs(V), recs(X))
+        assert st == oracle.OK
+        assert_bitwise(mpk.spmv(A, x, mode=name).planes(), want, f"spmv {name} p={p}")
+        want_t, st = oracle.spmv_t(p, m, rowptr, colidx, recs(V), recs(X))
+        assert st == oracle.OK
+        assert_bitwise(mpk.spmv_t(A, x, mode=name).planes(), want_t, f"spmv_t {name} p={p}")
+
+
+@pytest.mark.parametrize("p", (2048, 8192))
+def test_exact_rows_cancelling_wide_and_over_the_cap(p):
+    """EXACT rows whose products cancel to +0 or to a few low bits, a row
+    spanning thousands of bits, and a row past the span cap (+0 and
+    MP_ERR_SPAN); ORDERED on the same rows."""
+    mpk = need_gpu()
+    n = 6
+    X = rand_planes(n, p, 41, zero_frac=0.0, emin=-3, emax=3)
+    V0 = rand_planes(n, p, 42, zero_frac=0.0, emin=-3, emax=3)
+    Xr, Vr = recs(X), recs(V0)
+    rows = []
+    # row 1: a x0 + (-a) x0 = 0 exactly; row 2: the same with one low bit changed
+    neg = Vr[0].copy()
+    neg[0] ^= np.uint64(1)
+    tweak = neg.copy()
+    tweak[1] ^= np.uint64(1)
+    rows.append([(0, Vr[0]), (1, Vr[1]), (2, Vr[2])])
+    rows.append([(0, Vr[0]), (3, neg)])
+    rows.append([(0, Vr[0]), (3, tweak)])
+    far = Vr[4].copy()
+    far[0] = np.uint64((int(far[0].view(np.int64)) + 2 * 5000) & ((1 << 64) - 1))
+    rows.append([(1, Vr[1]), (4, far), (5, Vr[5])])
+    over = Vr[4].copy()
+    over[0] = np.uint64((int(over[0].view(np.int64)) + 2 * (oracle.SPAN_CAP + 100)) & ((1 << 64) - 1))
+    rows.append([(2, Vr[2]), (4, over)])
+    rows.append([])
+    # duplicate x0 into column 3 so that rows 1-2 cancel a x0 against itself
+    Xr[3] = Xr[0]
+    rowptr = np.zeros(n + 1, np.int64)
+    cols, vals = [], []
+    for i, r in enumerate(rows):
+        rowptr[i + 1] = rowptr[i] + len(r)
+        for c, v in r:
+            cols.append(c)
+            vals.append(v)
+    colidx = np.array(cols, np.int32)
+    vrec = np.stack(vals)
+    A = mpk.CSR(rowptr, colidx, np.ascontiguousarray(vrec.T), p)
+    x = mpk.Vec.from_planes(np.ascontiguousarray(Xr.T), p)
+    want, st = oracle.spmv(p, oracle.EXACT, rowptr, colidx, vrec, Xr)
+    assert st == oracle.ERR_SPAN
+    y = mpk.spmv(A, x, mode="exact", sync=False)
+    with pytest.raises(mpk.MPError) as e:
+        mpk.check()
+    assert e.value.status == 5
+    assert_bitwise(y.planes(), want, f"exact p={p}")
+    assert (want[1, 0].view(np.int64) >> 1) == oracle.EXP_ZERO and want[1, 0] & 1 == 0
+    want, st = oracle.spmv(p, oracle.ORDERED, rowptr, colidx, vrec, Xr)
+    assert st == oracle.OK
+    assert_bitwise(mpk.spmv(A, x, mode="ordered").planes(), want, f"ordered p={p}")
+
+
+@pytest.mark.parametrize("p", WIDE)
+@pytest.mark.parametrize("n,lo,hi", [(1, -3, 3), (257, -40, 40), (1000, -1500, 1500)])
+def test_dot(p, n, lo, hi):
+    mpk = need_gpu()
+    X = rand_planes(n, p, 51 + n, zero_frac=0.02, emin=lo, emax=hi)
+    Y = rand_planes(n, p, 52 + n, zero_frac=0.02, emin=lo, emax=hi)
+    got = mpk.dot(mpk.Vec.from_planes(X, p), mpk.Vec.from_planes(Y, p))
+    want, st = oracle.dot(p, recs(X), recs(Y))
+    assert st == oracle.OK
+    assert_bitwise(got.planes(), want[None], f"dot p={p} n={n}")
+
+
+@pytest.mark.parametrize("p", (2048, 8192))
+def test_dot_cancellation_empty_and_span_error(p):
+    mpk = need_gpu()
+    n = 300
+    X = rand_planes(n, p, 61, zero_frac=0.0)
+    Y = rand_planes(n, p, 62, zero_frac=0.0)
+    Yn = Y.copy()
+    Yn[0] ^= np.uint64(1)
+    x2 = mpk.Vec.from_planes(np.concatenate([X, X], axis=1), p)
+    got = mpk.dot(x2, mpk.Vec.from_planes(np.concatenate([Y, Yn], axis=1), p)).records()[0]
+    assert (got[0].view(np.int64) >> 1) == oracle.EXP_ZERO and got[0] & 1 == 0
+    got = mpk.dot(mpk.Vec.zeros(0, p), mpk.Vec.zeros(0, p)).records()[0]
+    assert (got[0].view(np.int64) >> 1) == oracle.EXP_ZERO
+    Xr = recs(X)
+    Xr[5, 0] = np.int64(Xr[5, 0].view(np.int64) - 2 * (oracle.SPAN_CAP + 500)).view(np.uint64)
+    out = mpk.dot(mpk.Vec.from_planes(Xr.T.copy(), p), mpk.Vec.from_planes(Y, p), sync=False)
+    with pytest.raises(mpk.MPError) as e:
+        mpk.check()
+    assert e.value.status == 5
+    want, st = oracle.dot(p, Xr, recs(Y))
+    assert st == oracle.ERR_SPAN
+    assert_bitwise(out.planes(), want[None], "dot span error")
+    # the span slots were reset: the next dot is exact again
+    got = mpk.dot(mpk.Vec.from_planes(X, p), mpk.Vec.from_planes(Y, p))
+    want, st = oracle.dot(p, recs(X), recs(Y))
+    assert_bitwise(got.planes(), want[None], "dot after the span error")
+
+
+@pytest.mark.parametrize("p", WIDE)
+def test_axpy_with_signed_zeros(p):
+    mpk = need_gpu()
+    n = 200
+    X = rand_planes(n, p, 71, zero_frac=0.1, emin=-60, emax=60)
+    Y = rand_planes(n, p, 72, zero_frac=0.1, emin=-60, emax=60)
+    Yr = recs(Y)
+    Yr[::7, 0] |= np.uint64(1)  # some -0 (and some negated values)
+    Y = np.ascontiguousarray(Yr.T)
+    al = rand_planes(1, p, 73, zero_frac=0.0)
+    for alpha, arec in ((mpk.Vec.from_planes(al, p), recs(al)),
+                        (mpk.Vec.zeros(1, p), oracle.empty(p, 1))):
+        y = mpk.Vec.from_planes(Y, p)
+        mpk.axpy(alpha, mpk.Vec.from_planes(X, p), y)
+        want, _ = oracle.axpy(p, arec, recs(X), recs(Y))
+        assert_bitwise(y.planes(), want, f"axpy p={p}")
+
+
+@pytest.mark.parametrize("p", (2048, 8192))
+def test_f64_matrix_and_precision_refusals(p):
+    """mp_csr_create_f64 at the wide precisions is exact; calls outside
+    SpMV / dot / axpy return MP_ERR_PREC."""
+    mpk = need_gpu()
+    n = 50
+    rowptr, colidx = random_csr(n, seed=7, mean_len=4, max_len=10)
+    v64 = np.linspace(-3.5, 7.25, len(colidx))
+    v64[::9] = 0.0
+    A = mpk.CSR(rowptr, colidx, v64, p)
+    X = rand_planes(n, p, 81, zero_frac=0.0, emin=-5, emax=5)
+    vrec = oracle.from_f64(p, v64)
+    for name, m in MODES:
+        want, _ = oracle.spmv(p, m, rowptr, colidx, vrec, recs(X))
+        assert_bitwise(mpk.spmv(A, mpk.Vec.from_planes(X, p), mode=name).planes(), want,
+                       f"f64 matrix {name} p={p}")
+    b = mpk.Vec.from_planes(X, p)
+    with pytest.raises(mpk.MPError) as e:
+        mpk.gpbicg(A, b, maxit=2)
+    assert e.value.status == 2
+    with pytest.raises(mpk.MPError) as e:
+        mpk.residual(A, b, mpk.Vec.zeros(n, p))
+    assert e.value.status == 2
