@@ -483,6 +483,7 @@ def run_native(args):
         solver["autograd"] = autograd_bench(mpk)
         solver["batched"] = batch_bench(mpk, count=args.batch_systems)
         solver["lotkin"] = lotkin_bench(mpk)
+        solver["wide"] = wide_bench(mpk, imad_peak)
 
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
@@ -502,6 +503,7 @@ def run_native(args):
                                                      "sample": desc1}}
         if not args.no_solver:
             cpu["solver"] = oracle_solver_sample()
+            cpu["wide"] = oracle_wide_sample()
 
     if rank == 0:
         line = {
@@ -726,6 +728,93 @@ def lotkin_bench(mpk, n=2000, precs=(128, 256, 512, 1024), s_list=(0.0, 50.0, 90
             A.close()
             del D
     return out
+
+
+WIDE_PRECS = (2048, 4096, 8192)
+
+
+def wide_bench(mpk, imad_peak, n=20000, reps=5):
+    """p = 2048, 4096, 8192 (one value per warp): ORDERED and EXACT products on
+    the SpMV workload's pattern at n = 2*10^4 (values as there), and exact dot
+    and axpy on 10^4 elements; CUDA-event time per call and the fraction of
+    the 32-bit-multiply peak ((p/32)^2 per stored nonzero or element; the
+    bytes are far below the HBM bound at these precisions)."""
+    import torch
+
+    from paper_1411_2377_gb300 import synth
+
+    rowptr, colidx = synth.spmv_pattern(n)
+    nnz = int(rowptr[-1])
+    out = {"workload": f"spmv_pattern_n{n}_nnz{nnz}", "rows": []}
+
+    def timed(call):
+        call()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            call()
+        e1.record()
+        e1.synchronize()
+        mpk.check()
+        return e0.elapsed_time(e1) / reps
+
+    for p in WIDE_PRECS:
+        vals, xs = synth.spmv_values(p, nnz, n)
+        A = mpk.CSR(rowptr, colidx, vals, p)
+        x = mpk.Vec.from_planes(xs, p)
+        y = mpk.Vec.empty(n, p)
+        mults = nnz * (p // 32) ** 2
+        for mode in ("ordered", "exact"):
+            ms = timed(lambda: mpk.spmv(A, x, y, mode=mode, sync=False))
+            out["rows"].append({"op": f"spmv_{mode}", "p": p, "ms": round(ms, 4),
+                                "gnnz_s": round(nnz / (ms * 1e-3) / 1e9, 4),
+                                "t_mult_s": round(mults / (ms * 1e-3) / 1e12, 3),
+                                "frac": round(mults / (ms * 1e-3) / imad_peak, 3)})
+        A.close()
+        m = 10000
+        X = mpk.Vec.from_planes(xs[:, :m].copy(), p)
+        Y = mpk.Vec.from_planes(synth.random_values(m, p, seed=5, zero_frac=0.0), p)
+        al = mpk.Vec.from_planes(synth.random_values(1, p, seed=6, zero_frac=0.0), p)
+        d = mpk.Vec.empty(1, p)
+        mults = m * (p // 32) ** 2
+        for op, call in (("dot", lambda: mpk.dot(X, Y, d, sync=False)),
+                         ("axpy", lambda: mpk.axpy(al, X, Y, sync=False))):
+            ms = timed(call)
+            out["rows"].append({"op": op, "p": p, "n": m, "ms": round(ms, 4),
+                                "t_mult_s": round(mults / (ms * 1e-3) / 1e12, 3),
+                                "frac": round(mults / (ms * 1e-3) / imad_peak, 3)})
+        del x, y, X, Y
+    return out
+
+
+def oracle_wide_sample(budget_s=4.0, n=20000):
+    """The oracle's wide build on leading rows of the same n = 2*10^4 product
+    (ORDERED and EXACT, p = 2048 / 4096 / 8192), one thread: stored nonzeros
+    per second for each."""
+    import oracle
+    from paper_1411_2377_gb300 import synth
+
+    rowptr, colidx = synth.spmv_pattern(n)
+    nnz = int(rowptr[-1])
+    per = budget_s / (2 * len(WIDE_PRECS))
+    rows_out = []
+    for p in WIDE_PRECS:
+        vals, xs = synth.spmv_values(p, nnz, n)
+        xr = synth.planes_to_records(xs)
+        for name, m in MODES:
+            rows = 4
+            while True:
+                t0 = time.perf_counter()
+                _sample(oracle, p, m, rowptr, colidx, vals, xr, rows)
+                dt = time.perf_counter() - t0
+                if dt > per or rows >= n:
+                    break
+                rows = min(rows * 2, n)
+            e = int(rowptr[rows])
+            rows_out.append({"p": p, "mode": name, "rows": rows, "nnz": e,
+                             "gnnz_s": e / dt / 1e9, "cores": 1})
+    return rows_out
 
 
 def spmv_latency(mpk, A, x, mode, reps=100):

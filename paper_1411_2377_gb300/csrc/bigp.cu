@@ -91,29 +91,46 @@ __device__ __forceinline__ void wstore(const uint32_t* src, int64_t e, uint32_t 
 
 // ---- the four warp steps -----------------------------------------------------
 
+// One step of a column sum: (c2:c1:c0) += u * v.
+__device__ __forceinline__ void mac96(uint32_t& c0, uint32_t& c1, uint32_t& c2, uint32_t u,
+                                      uint32_t v) {
+  asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\t"
+      "madc.hi.cc.u32 %1, %3, %4, %1;\n\t"
+      "addc.u32 %2, %2, 0;"
+      : "+r"(c0), "+r"(c1), "+r"(c2)
+      : "r"(u), "r"(v));
+}
+
 // cnt[0 .. 2W+2) <- counters with sum_k cnt[k] 2^(32k) = a * b exactly (each
 // in [0, 3 * 2^32)).  Column k of the schoolbook product, sum over i of
 // a_i b_(k-i), is at most W (2^32-1)^2 < 2^72: three words (c0, c1, c2),
-// which land on digits k, k+1, k+2.
+// which land on digits k, k+1, k+2.  A lane takes the column pairs
+// (2g, 2g+1), g = lane (mod 32): the pair walks one range of i, and the b
+// word of column 2g at step i is the one column 2g+1 needs at step i+1, so a
+// step loads one a and one b word for two multiply-adds (out-of-range
+// operands are taken as 0).  Pairs g and g + 32 t give every lane about the
+// same number of steps.
 template <int W>
 __device__ __forceinline__ void wmul(const uint32_t* a, const uint32_t* b, const WarpMem& m,
                                      int lane) {
-  for (int k = lane; k < 2 * W; k += 32) {
-    uint32_t c0 = 0, c1 = 0, c2 = 0;
-    if (k < 2 * W - 1) {
-      const int lo = k < W ? 0 : k - W + 1, hi = k < W ? k : W - 1;
-      for (int i = lo; i <= hi; ++i) {
-        const uint32_t u = a[i], v = b[k - i];
-        asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\t"
-            "madc.hi.cc.u32 %1, %3, %4, %1;\n\t"
-            "addc.u32 %2, %2, 0;"
-            : "+r"(c0), "+r"(c1), "+r"(c2)
-            : "r"(u), "r"(v));
-      }
+  for (int g = lane; g < W; g += 32) {
+    const int k = 2 * g;
+    const int lo = k < W ? 0 : k - W + 1, hi = k + 1 < W ? k + 1 : W - 1;
+    uint32_t c0 = 0, c1 = 0, c2 = 0, d0 = 0, d1 = 0, d2 = 0;
+    uint32_t bn = (k + 1 - lo <= W - 1) ? b[k + 1 - lo] : 0u;  // column k+1's b at i = lo
+    for (int i = lo; i <= hi; ++i) {
+      const uint32_t u = a[i];
+      const uint32_t bk = (k - i >= 0) ? b[k - i] : 0u;
+      mac96(c0, c1, c2, u, bk);
+      mac96(d0, d1, d2, u, bn);
+      bn = bk;
     }
     m.P0[k] = c0;
     m.P1[k] = c1;
     m.P2[k] = c2;
+    m.P0[k + 1] = d0;
+    m.P1[k + 1] = d1;
+    m.P2[k + 1] = d2;
   }
   __syncwarp();
   for (int k = lane; k < 2 * W + 2; k += 32) {
@@ -367,19 +384,28 @@ struct BigSell {
   const uint64_t* val;
 };
 
+// Rows go to warps through a work counter (next, zero at launch): row slots
+// come longest first (the layout sorts chunks by length), so the longest rows
+// start first and the short ones fill in, which a fixed round-robin split of
+// a few rows per warp cannot balance.
+__device__ __forceinline__ int64_t next_row(unsigned* next, int lane) {
+  unsigned r = 0;
+  if (lane == 0) r = atomicAdd(next, 1u);
+  return (int64_t)__shfl_sync(kFull, r, 0);
+}
+
 template <int W>
 __global__ void __launch_bounds__(kBigThreads) big_ordered_kernel(BigSell S,
                                                                   const uint64_t* __restrict__ x,
                                                                   int64_t ldx, uint64_t* y,
-                                                                  int64_t ldy,
+                                                                  int64_t ldy, unsigned* next,
                                                                   const int* __restrict__ gate) {
   extern __shared__ __align__(16) unsigned char smem[];
   if (gate && *gate) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const WarpMem m = carve<W>(smem, warp, false);
   const int64_t nrs = S.nchunks * 32;
-  for (int64_t rs = (int64_t)blockIdx.x * kBigWarps + warp; rs < nrs;
-       rs += (int64_t)gridDim.x * kBigWarps) {
+  for (int64_t rs = next_row(next, lane); rs < nrs; rs = next_row(next, lane)) {
     const int row = S.row_of[rs];
     if (row < 0) continue;
     const int len = S.row_len[rs];
@@ -419,14 +445,14 @@ __global__ void __launch_bounds__(kBigThreads) big_exact_kernel(BigSell S,
                                                                 const uint64_t* __restrict__ x,
                                                                 int64_t ldx, uint64_t* y,
                                                                 int64_t ldy, int* status,
+                                                                unsigned* next,
                                                                 const int* __restrict__ gate) {
   extern __shared__ __align__(16) unsigned char smem[];
   if (gate && *gate) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const WarpMem m = carve<W>(smem, warp, true);
   const int64_t nrs = S.nchunks * 32;
-  for (int64_t rs = (int64_t)blockIdx.x * kBigWarps + warp; rs < nrs;
-       rs += (int64_t)gridDim.x * kBigWarps) {
+  for (int64_t rs = next_row(next, lane); rs < nrs; rs = next_row(next, lane)) {
     const int row = S.row_of[rs];
     if (row < 0) continue;
     const int len = S.row_len[rs];
@@ -677,6 +703,9 @@ mp_status launch_spmv_big(const mp_csr_s* M, const Sell& S, int mode, const uint
                           cudaStream_t st) {
   if (S.nchunks == 0) return MP_OK;
   BigSell B{S.nslots, S.nchunks, S.chunk_off, S.row_of, S.row_len, S.col, S.val};
+  // the matrix's overflow-list word (unused at these precisions) is the row counter
+  unsigned* next = reinterpret_cast<unsigned*>(M->ovf);
+  MPK_CUDA(cudaMemsetAsync(next, 0, sizeof(unsigned), st));
   return dispatch_big(M->prec, [&](auto w) -> mp_status {
     constexpr int W = decltype(w)::value;
     int grid = 0;
@@ -684,13 +713,13 @@ mp_status launch_spmv_big(const mp_csr_s* M, const Sell& S, int mode, const uint
     if (mode == MP_ORDERED) {
       const size_t sm = (size_t)kBigWarps * BigMem<W>::bytes(false);
       if ((r = big_grid(big_ordered_kernel<W>, sm, S.nchunks * 32, &grid)) != MP_OK) return r;
-      big_ordered_kernel<W><<<grid, kBigThreads, sm, st>>>(B, x, ldx, y, ldy, gate);
+      big_ordered_kernel<W><<<grid, kBigThreads, sm, st>>>(B, x, ldx, y, ldy, next, gate);
     } else {
       const size_t sm = (size_t)kBigWarps * BigMem<W>::bytes(true);
       if ((r = big_grid(big_exact_kernel<W>, sm, S.nchunks * 32, &grid)) != MP_OK) return r;
       int* status = status_word();
       if (!status) return set_error(MP_ERR_CUDA, "status word unavailable");
-      big_exact_kernel<W><<<grid, kBigThreads, sm, st>>>(B, x, ldx, y, ldy, status, gate);
+      big_exact_kernel<W><<<grid, kBigThreads, sm, st>>>(B, x, ldx, y, ldy, status, next, gate);
     }
     count_launch();
     return launch_check(mode == MP_ORDERED ? "big_ordered_kernel" : "big_exact_kernel");
