@@ -20,358 +20,12 @@
 // cap); a dot one rounding of the exact sum; axpy y <- RN(y + RN(alpha x)).
 // The work is bound by the 32-bit multiplies ((p/32)^2 per product), not by
 // bytes: at p = 2048 a stored nonzero carries 4096 multiplies for 264 bytes.
-#include <climits>
-
-#include "internal.h"
-#include "mpdev.cuh"
+#include "bigp.cuh"
 
 namespace mpk {
 namespace {
 
-constexpr int kBigWarps = 4;
-constexpr int kBigThreads = 32 * kBigWarps;
-constexpr unsigned kFull = 0xffffffffu;
-constexpr int64_t kMask32 = 0xffffffffLL;
-
-// Per-warp shared memory: [cnt int64 x kCnt][acc int64 x kAcc (exact forms)]
-// [A, X, Y, T: W words each][P0, P1, P2: 2W words each].
-template <int W>
-struct BigMem {
-  static constexpr int kP = 32 * W;
-  static constexpr int kCnt = 2 * W + 4;  // product counters, then the two-term window
-  static constexpr int kAcc = (SPAN_CAP + 2 * kP + 96) / 32 + 2;  // exact window at the span cap
-  __host__ __device__ static constexpr size_t bytes(bool exact) {
-    return 8 * (size_t)(kCnt + (exact ? kAcc : 0)) + 4 * (size_t)(4 * W + 6 * W);
-  }
-};
-
-struct WarpMem {
-  int64_t* cnt;
-  int64_t* acc;
-  uint32_t *A, *X, *Y, *T, *P0, *P1, *P2;
-};
-
-template <int W>
-__device__ __forceinline__ WarpMem carve(unsigned char* smem, int warp, bool exact) {
-  unsigned char* b = smem + (size_t)warp * BigMem<W>::bytes(exact);
-  WarpMem m;
-  m.cnt = reinterpret_cast<int64_t*>(b);
-  m.acc = m.cnt + BigMem<W>::kCnt;
-  uint32_t* w = reinterpret_cast<uint32_t*>(m.cnt + BigMem<W>::kCnt + (exact ? BigMem<W>::kAcc : 0));
-  m.A = w;
-  m.X = w + W;
-  m.Y = w + 2 * W;
-  m.T = w + 3 * W;
-  m.P0 = w + 4 * W;
-  m.P1 = w + 6 * W;
-  m.P2 = w + 8 * W;
-  return m;
-}
-
-// ---- plane-major records <-> shared memory ----------------------------------
-
-template <int W>
-__device__ __forceinline__ void wload(uint32_t* dst, const uint64_t* __restrict__ v, int64_t ld,
-                                      int64_t i, int lane) {
-  for (int k = lane; k < W / 2; k += 32) {
-    const uint64_t limb = __ldg(v + (int64_t)(k + 1) * ld + i);
-    dst[2 * k] = (uint32_t)limb;
-    dst[2 * k + 1] = (uint32_t)(limb >> 32);
-  }
-}
-
-template <int W>
-__device__ __forceinline__ void wstore(const uint32_t* src, int64_t e, uint32_t s,
-                                       uint64_t* __restrict__ v, int64_t ld, int64_t i, int lane) {
-  const bool z = zero_e(e);
-  for (int k = lane; k < W / 2; k += 32)
-    v[(int64_t)(k + 1) * ld + i] = z ? 0ull : ((uint64_t)src[2 * k] | ((uint64_t)src[2 * k + 1] << 32));
-  if (lane == 0) v[i] = pack_head(z ? EXP_ZERO : e, s);
-}
-
-// ---- the four warp steps -----------------------------------------------------
-
-// One step of a column sum: (c2:c1:c0) += u * v.
-__device__ __forceinline__ void mac96(uint32_t& c0, uint32_t& c1, uint32_t& c2, uint32_t u,
-                                      uint32_t v) {
-  asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\t"
-      "madc.hi.cc.u32 %1, %3, %4, %1;\n\t"
-      "addc.u32 %2, %2, 0;"
-      : "+r"(c0), "+r"(c1), "+r"(c2)
-      : "r"(u), "r"(v));
-}
-
-// cnt[0 .. 2W+2) <- counters with sum_k cnt[k] 2^(32k) = a * b exactly (each
-// in [0, 3 * 2^32)).  Column k of the schoolbook product, sum over i of
-// a_i b_(k-i), is at most W (2^32-1)^2 < 2^72: three words (c0, c1, c2),
-// which land on digits k, k+1, k+2.  A lane takes the column pairs
-// (2g, 2g+1), g = lane (mod 32): the pair walks one range of i, and the b
-// word of column 2g at step i is the one column 2g+1 needs at step i+1, so a
-// step loads one a and one b word for two multiply-adds (out-of-range
-// operands are taken as 0).  Pairs g and g + 32 t give every lane about the
-// same number of steps.
-template <int W>
-__device__ __forceinline__ void wmul(const uint32_t* a, const uint32_t* b, const WarpMem& m,
-                                     int lane) {
-  for (int g = lane; g < W; g += 32) {
-    const int k = 2 * g;
-    const int lo = k < W ? 0 : k - W + 1, hi = k + 1 < W ? k + 1 : W - 1;
-    uint32_t c0 = 0, c1 = 0, c2 = 0, d0 = 0, d1 = 0, d2 = 0;
-    uint32_t bn = (k + 1 - lo <= W - 1) ? b[k + 1 - lo] : 0u;  // column k+1's b at i = lo
-    for (int i = lo; i <= hi; ++i) {
-      const uint32_t u = a[i];
-      const uint32_t bk = (k - i >= 0) ? b[k - i] : 0u;
-      mac96(c0, c1, c2, u, bk);
-      mac96(d0, d1, d2, u, bn);
-      bn = bk;
-    }
-    m.P0[k] = c0;
-    m.P1[k] = c1;
-    m.P2[k] = c2;
-    m.P0[k + 1] = d0;
-    m.P1[k + 1] = d1;
-    m.P2[k + 1] = d2;
-  }
-  __syncwarp();
-  for (int k = lane; k < 2 * W + 2; k += 32) {
-    int64_t v = 0;
-    if (k < 2 * W) v += m.P0[k];
-    if (k >= 1 && k <= 2 * W) v += m.P1[k - 1];
-    if (k >= 2) v += m.P2[k - 2];
-    m.cnt[k] = v;
-  }
-  __syncwarp();
-}
-
-__device__ __forceinline__ void run_of(int n, int lane, int& b, int& e) {
-  const int per = (n + 31) >> 5;
-  b = min(lane * per, n);
-  e = min(b + per, n);
-}
-
-// Signed counters c[0..n) -> words in [0, 2^32) (kept in the int64 slots).
-// Returns the carry out of the top word: 0 for a non-negative total, -1 for a
-// negative one (the window is sized so that the total fits).  Each lane
-// resolves its own run; the carry out of lane l enters lane l+1 in the next
-// round, so at most 32 rounds run.
-__device__ __forceinline__ int64_t wresolve(int64_t* c, int n, int lane) {
-  int b, e;
-  run_of(n, lane, b, e);
-  int64_t carry = 0;
-  for (int i = b; i < e; ++i) {
-    const int64_t v = c[i] + carry;
-    c[i] = v & kMask32;
-    carry = v >> 32;
-  }
-  int64_t top = 0;
-  for (int round = 0; round < 33; ++round) {
-    top += __shfl_sync(kFull, carry, 31);
-    int64_t cin = __shfl_up_sync(kFull, carry, 1);
-    if (lane == 0) cin = 0;
-    if (!__any_sync(kFull, cin != 0)) break;
-    for (int i = b; i < e && cin != 0; ++i) {
-      const int64_t v = c[i] + cin;
-      c[i] = v & kMask32;
-      cin = v >> 32;
-    }
-    carry = cin;
-  }
-  return top;
-}
-
-// Two's complement of the words c[0..n): invert, then +1 (a lane takes the
-// carry when every lower lane's run was all ones after the inversion).
-__device__ __forceinline__ void wnegate(int64_t* c, int n, int lane) {
-  int b, e;
-  run_of(n, lane, b, e);
-  bool ones = true;
-  for (int i = b; i < e; ++i) {
-    c[i] = (~c[i]) & kMask32;
-    ones = ones && c[i] == kMask32;
-  }
-  const unsigned m = __ballot_sync(kFull, ones);
-  const unsigned lower = (1u << lane) - 1u;
-  if ((~m & lower) == 0u) {
-    for (int i = b; i < e; ++i) {
-      c[i] = (c[i] + 1) & kMask32;
-      if (c[i] != 0) break;
-    }
-  }
-}
-
-// Index of the highest set bit of the words c[0..n), or -1 for zero.
-__device__ __forceinline__ int wtopbit(const int64_t* c, int n, int lane) {
-  int b, e;
-  run_of(n, lane, b, e);
-  int best = -1;
-  for (int i = e - 1; i >= b; --i) {
-    if (c[i] != 0) {
-      best = i * 32 + 31 - __clz((unsigned)c[i]);
-      break;
-    }
-  }
-  return __reduce_max_sync(kFull, best);
-}
-
-// 32 bits of the integer c[0..n) starting at bit pos (bits outside are 0).
-__device__ __forceinline__ uint32_t wbits32(const int64_t* c, int n, int64_t pos) {
-  if (pos >= 32LL * n || pos <= -32) return 0u;
-  const int64_t q = pos >> 5;
-  const int r = (int)(pos & 31);
-  const uint64_t lo = (q >= 0 && q < n) ? (uint64_t)(uint32_t)c[q] : 0ull;
-  const uint64_t hi = (q + 1 < n) ? (uint64_t)(uint32_t)c[q + 1] : 0ull;
-  return (uint32_t)(((hi << 32) | lo) >> r);
-}
-
-// out[0..W) <- the p = 32W bits of c[0..n) below and including bit B (the
-// leading bit), rounded to nearest with ties to even on the bits below.
-// Returns 1 when the rounding carried out of the top (the mantissa is then
-// 2^(p-1) and the caller raises the exponent), else 0.
-template <int W>
-__device__ __forceinline__ int wround(const int64_t* c, int n, int B, uint32_t* out, int lane) {
-  const int64_t s = (int64_t)B - 32 * W + 1;  // bit of c that becomes the result's lsb
-  for (int j = lane; j < W; j += 32) out[j] = wbits32(c, n, s + 32 * (int64_t)j);
-  uint32_t rbit = 0;
-  bool sticky = false;
-  if (s > 0) {
-    const int64_t rb = s - 1;  // the round bit; sticky = any bit below it
-    rbit = (uint32_t)(c[rb >> 5] >> (rb & 31)) & 1u;
-    int b, e;
-    run_of(n, lane, b, e);
-    uint64_t any = 0;
-    for (int i = b; i < e; ++i) {
-      const int64_t w0 = 32LL * i;
-      if (w0 + 32 <= rb)
-        any |= (uint64_t)c[i];
-      else if (w0 < rb)
-        any |= (uint64_t)c[i] & ((1ull << (rb - w0)) - 1ull);
-    }
-    sticky = __any_sync(kFull, any != 0);
-  }
-  __syncwarp();
-  if (!(rbit && (sticky || (out[0] & 1u)))) return 0;
-  constexpr int per = W / 32;
-  const int b = lane * per;
-  bool ones = true;
-  for (int i = b; i < b + per; ++i) ones = ones && out[i] == 0xffffffffu;
-  const unsigned m = __ballot_sync(kFull, ones);
-  const unsigned lower = (1u << lane) - 1u;
-  if ((~m & lower) == 0u) {
-    for (int i = b; i < b + per; ++i)
-      if (++out[i] != 0u) break;
-  }
-  __syncwarp();
-  if (m != kFull) return 0;
-  for (int j = lane; j < W; j += 32) out[j] = (j == W - 1) ? 0x80000000u : 0u;
-  __syncwarp();
-  return 1;
-}
-
-// out <- RN(a * b) for nonzero a, b (mantissas in shared memory); e = ea + eb.
-// Returns the result's exponent.
-template <int W>
-__device__ __forceinline__ int64_t wmul_rn(const uint32_t* a, const uint32_t* b, int64_t e,
-                                           const WarpMem& m, uint32_t* out, int lane) {
-  wmul<W>(a, b, m, lane);
-  wresolve(m.cnt, 2 * W + 2, lane);
-  __syncwarp();
-  const int B = wtopbit(m.cnt, 2 * W + 2, lane);  // 2p-2 or 2p-1
-  const int inc = wround<W>(m.cnt, 2 * W + 2, B, out, lane);
-  return e + B + 1 - 64LL * W + inc;
-}
-
-// (Y, ye, ys) <- RN(y + t) for nonzero y and t.  Exact sum of the two on the
-// grid of the smaller exponent, then one rounding; when the exponents differ
-// by p + 2 or more the smaller is below a quarter ulp of the larger and the
-// sum rounds to the larger.  An exact cancellation gives +0.
-template <int W>
-__device__ __forceinline__ void wadd(uint32_t* Y, int64_t& ye, uint32_t& ys, const uint32_t* T,
-                                     int64_t te, uint32_t ts, int64_t* win, int lane) {
-  const bool ybig = ye >= te;
-  const uint32_t* big = ybig ? Y : T;
-  const uint32_t* sml = ybig ? T : Y;
-  const int64_t eb = ybig ? ye : te, es = ybig ? te : ye;
-  const uint32_t sb = ybig ? ys : ts, ss = ybig ? ts : ys;
-  const int64_t d = eb - es;
-  if (d >= 32LL * W + 2) {
-    if (!ybig) {
-      for (int j = lane; j < W; j += 32) Y[j] = T[j];
-      ye = te;
-      ys = ts;
-      __syncwarp();
-    }
-    return;
-  }
-  constexpr int N = 2 * W + 4;
-  const bool sub = sb != ss;
-  for (int i = lane; i < N; i += 32)
-    win[i] = i < W ? (sub ? -(int64_t)sml[i] : (int64_t)sml[i]) : 0;
-  __syncwarp();
-  const int q = (int)(d >> 5), r = (int)(d & 31);
-  for (int k = lane; k < W; k += 32) win[q + k] += (uint32_t)((uint64_t)big[k] << r);
-  __syncwarp();
-  for (int k = lane; k < W; k += 32) win[q + k + 1] += (uint32_t)(((uint64_t)big[k] << r) >> 32);
-  __syncwarp();
-  const bool neg = wresolve(win, N, lane) < 0;
-  __syncwarp();
-  if (neg) {
-    wnegate(win, N, lane);
-    __syncwarp();
-  }
-  const int B = wtopbit(win, N, lane);
-  if (B < 0) {
-    ye = EXP_ZERO;
-    ys = 0u;
-    return;
-  }
-  const int inc = wround<W>(win, N, B, Y, lane);
-  ye = es + B + 1 - 32LL * W + inc;
-  ys = sb ^ (neg ? 1u : 0u);
-}
-
-// acc[q ..] += (-1)^neg * (the 2W words in m.cnt) * 2^off, off = 32q + r.
-template <int W>
-__device__ __forceinline__ void wplace(int64_t* acc, const WarpMem& m, int64_t off, bool neg,
-                                       int lane) {
-  const int64_t q = off >> 5;
-  const int r = (int)(off & 31);
-  for (int k = lane; k < 2 * W; k += 32) {
-    const int64_t v = (int64_t)(uint32_t)((uint64_t)m.cnt[k] << r);
-    acc[q + k] += neg ? -v : v;
-  }
-  __syncwarp();
-  for (int k = lane; k < 2 * W; k += 32) {
-    const int64_t v = (int64_t)(uint32_t)(((uint64_t)m.cnt[k] << r) >> 32);
-    acc[q + k + 1] += neg ? -v : v;
-  }
-  __syncwarp();
-}
-
-// Rounds the exact window acc[0..n) (bit i of weight 2^(e0 + i)) into
-// (Y, e, s); an exactly zero window gives +0.
-template <int W>
-__device__ __forceinline__ void wfinish(int64_t* acc, int n, int64_t e0, uint32_t* Y, int64_t& e,
-                                        uint32_t& s, int lane) {
-  const bool neg = wresolve(acc, n, lane) < 0;
-  __syncwarp();
-  if (neg) {
-    wnegate(acc, n, lane);
-    __syncwarp();
-  }
-  const int B = wtopbit(acc, n, lane);
-  if (B < 0) {
-    e = EXP_ZERO;
-    s = 0u;
-    return;
-  }
-  const int inc = wround<W>(acc, n, B, Y, lane);
-  e = e0 + B + 1 + inc;  // M 2^(e - p) with M's lsb at bit B - p + 1 of the window
-  s = neg ? 1u : 0u;
-}
-
-__device__ __forceinline__ int exact_words(int64_t span, int W) {
-  return (int)((span + 64LL * W + 96) / 32) + 1;
-}
+using namespace bigp;
 
 // ---- SpMV ----------------------------------------------------------------------
 
@@ -446,11 +100,15 @@ __global__ void __launch_bounds__(kBigThreads) big_exact_kernel(BigSell S,
                                                                 int64_t ldx, uint64_t* y,
                                                                 int64_t ldy, int* status,
                                                                 unsigned* next,
+                                                                const uint64_t* __restrict__ rb,
+                                                                int64_t ldb,
                                                                 const int* __restrict__ gate) {
+  // rb != nullptr: the residual y = RN(b - A x), b_i an extra exact term.
   extern __shared__ __align__(16) unsigned char smem[];
   if (gate && *gate) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const WarpMem m = carve<W>(smem, warp, true);
+  const uint32_t flip = rb ? 1u : 0u;
   const int64_t nrs = S.nchunks * 32;
   for (int64_t rs = next_row(next, lane); rs < nrs; rs = next_row(next, lane)) {
     const int row = S.row_of[rs];
@@ -470,6 +128,15 @@ __global__ void __launch_bounds__(kBigThreads) big_exact_kernel(BigSell S,
       lo = min(lo, (long long)(ea + ex));
       hi = max(hi, (long long)(ea + ex));
     }
+    int64_t eb = EXP_ZERO;
+    uint32_t sb = 0u;
+    if (rb) {
+      unpack_head(__ldg(rb + row), eb, sb);
+      if (!zero_e(eb) && lane == 0) {
+        lo = min(lo, (long long)eb);
+        hi = max(hi, (long long)eb);
+      }
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       lo = min(lo, __shfl_xor_sync(kFull, lo, o));
@@ -483,6 +150,13 @@ __global__ void __launch_bounds__(kBigThreads) big_exact_kernel(BigSell S,
       const int n = exact_words(hi - lo, W);
       for (int i = lane; i < n; i += 32) m.acc[i] = 0;
       __syncwarp();
+      if (!zero_e(eb)) {  // b = (Mb 2^p) 2^(eb - 2p): its words sit above W zero words
+        wload<W>(m.A, rb, ldb, row, lane);
+        __syncwarp();
+        for (int k = lane; k < 2 * W; k += 32) m.cnt[k] = k < W ? 0 : (int64_t)m.A[k - W];
+        __syncwarp();
+        wplace<W>(m.acc, m, eb - lo, sb != 0u, lane);
+      }
       for (int j = 0; j < len; ++j) {
         const int64_t slot = base + 32LL * j;
         int64_t ea, ex;
@@ -498,7 +172,7 @@ __global__ void __launch_bounds__(kBigThreads) big_exact_kernel(BigSell S,
         wmul<W>(m.A, m.X, m, lane);
         wresolve(m.cnt, 2 * W + 2, lane);
         __syncwarp();
-        wplace<W>(m.acc, m, ea + ex - lo, (sa ^ sx) != 0u, lane);
+        wplace<W>(m.acc, m, ea + ex - lo, (sa ^ sx ^ flip) != 0u, lane);
       }
       // bit i of the window weighs 2^(lo - 2p + i)
       wfinish<W>(m.acc, n, (int64_t)lo - 64LL * W, m.Y, ye, ys, lane);
@@ -513,7 +187,9 @@ __global__ void __launch_bounds__(kBigThreads) big_exact_kernel(BigSell S,
 // Span slots are the dot scratch's header (slot 0: lowest, slot 5: highest
 // e_x + e_y), reset to (+inf, -inf) by the finalize for the next use.
 __global__ void big_dot_span_kernel(const uint64_t* __restrict__ x, const uint64_t* __restrict__ y,
-                                    int64_t n, long long* emin, long long* emax) {
+                                    int64_t n, long long* emin, long long* emax,
+                                    const int* __restrict__ gate) {
+  if (gate && *gate) return;
   long long lo = LLONG_MAX, hi = LLONG_MIN;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -541,8 +217,10 @@ __global__ void big_dot_span_kernel(const uint64_t* __restrict__ x, const uint64
 template <int W>
 __global__ void __launch_bounds__(kBigThreads) big_dot_accum_kernel(
     const uint64_t* __restrict__ x, int64_t ldx, const uint64_t* __restrict__ y, int64_t ldy,
-    int64_t n, const long long* __restrict__ span, int64_t* part, int nb) {
+    int64_t n, const long long* __restrict__ span, int64_t* part, int nb,
+    const int* __restrict__ gate) {
   extern __shared__ __align__(16) unsigned char smem[];
+  if (gate && *gate) return;
   const long long lo = span[0], hi = span[5];
   if (!(lo <= hi && hi - lo <= SPAN_CAP)) return;  // block-uniform
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -580,8 +258,10 @@ template <int W>
 __global__ void __launch_bounds__(256) big_dot_finalize_kernel(long long* span,
                                                                const int64_t* __restrict__ part,
                                                                int nb, uint64_t* out,
-                                                               int64_t ldo, int* status) {
+                                                               int64_t ldo, int* status,
+                                                               const int* __restrict__ gate) {
   extern __shared__ __align__(16) unsigned char smem[];
+  if (gate && *gate) return;
   const long long lo = span[0], hi = span[5];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const WarpMem m = carve<W>(smem, 0, true);
@@ -699,8 +379,9 @@ int big_dot_blocks(int64_t n) {
 }  // namespace
 
 mp_status launch_spmv_big(const mp_csr_s* M, const Sell& S, int mode, const uint64_t* x,
-                          int64_t ldx, uint64_t* y, int64_t ldy, const int* gate,
-                          cudaStream_t st) {
+                          int64_t ldx, uint64_t* y, int64_t ldy, const uint64_t* rb, int64_t ldb,
+                          const int* gate, cudaStream_t st) {
+  if (rb && mode != MP_EXACT) return set_error(MP_ERR_ARG, "a residual is an EXACT row sum");
   if (S.nchunks == 0) return MP_OK;
   BigSell B{S.nslots, S.nchunks, S.chunk_off, S.row_of, S.row_len, S.col, S.val};
   // the matrix's overflow-list word (unused at these precisions) is the row counter
@@ -719,7 +400,8 @@ mp_status launch_spmv_big(const mp_csr_s* M, const Sell& S, int mode, const uint
       if ((r = big_grid(big_exact_kernel<W>, sm, S.nchunks * 32, &grid)) != MP_OK) return r;
       int* status = status_word();
       if (!status) return set_error(MP_ERR_CUDA, "status word unavailable");
-      big_exact_kernel<W><<<grid, kBigThreads, sm, st>>>(B, x, ldx, y, ldy, status, next, gate);
+      big_exact_kernel<W><<<grid, kBigThreads, sm, st>>>(B, x, ldx, y, ldy, status, next, rb, ldb,
+                                                           gate);
     }
     count_launch();
     return launch_check(mode == MP_ORDERED ? "big_ordered_kernel" : "big_exact_kernel");
@@ -733,7 +415,8 @@ size_t dot_big_scratch_bytes(int prec) {
 }
 
 mp_status launch_dot_big(int prec, const uint64_t* x, int64_t ldx, const uint64_t* y, int64_t ldy,
-                         int64_t n, uint64_t* out, int64_t ldo, void* scratch, cudaStream_t st) {
+                         int64_t n, uint64_t* out, int64_t ldo, void* scratch, const int* gate,
+                         cudaStream_t st) {
   int* status = status_word();
   if (!status) return set_error(MP_ERR_CUDA, "status word unavailable");
   long long* span = static_cast<long long*>(scratch);
@@ -750,9 +433,9 @@ mp_status launch_dot_big(int prec, const uint64_t* x, int64_t ldx, const uint64_
     int sgrid = (int)((n + 255) / 256);
     if (sgrid > big_sm_count() * 4) sgrid = big_sm_count() * 4;
     if (sgrid < 1) sgrid = 1;
-    big_dot_span_kernel<<<sgrid, 256, 0, st>>>(x, y, n, span, span + 5);
-    big_dot_accum_kernel<W><<<nb, kBigThreads, sm, st>>>(x, ldx, y, ldy, n, span, part, nb);
-    big_dot_finalize_kernel<W><<<1, 256, sm1, st>>>(span, part, nb, out, ldo, status);
+    big_dot_span_kernel<<<sgrid, 256, 0, st>>>(x, y, n, span, span + 5, gate);
+    big_dot_accum_kernel<W><<<nb, kBigThreads, sm, st>>>(x, ldx, y, ldy, n, span, part, nb, gate);
+    big_dot_finalize_kernel<W><<<1, 256, sm1, st>>>(span, part, nb, out, ldo, status, gate);
     count_launch(3);
     return launch_check("big dot kernels");
   });

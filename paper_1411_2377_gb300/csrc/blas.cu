@@ -404,7 +404,7 @@ mp_status mp_dot(mp_vec x, mp_vec y, mp_vec out, void* stream) {
   }
   if (big)
     return launch_dot_big(x.prec_bits, x.data, x.ld, y.data, y.ld, x.n, out.data, out.ld, scratch,
-                          st);
+                          nullptr, st);
   DotArgs a;
   a.k = 1;
   a.n = x.n;

@@ -118,13 +118,18 @@ mp_status dispatch_w(int p, F&& f) {
 }
 
 // ---- p > 1024 (bigp.cu) ------------------------------------------------------
+// rb != nullptr: r = RN(b - A x) (EXACT).  gate as for launch_spmv.
 mp_status launch_spmv_big(const mp_csr_s* M, const Sell& S, int mode, const uint64_t* x,
-                          int64_t ldx, uint64_t* y, int64_t ldy, const int* gate,
-                          cudaStream_t st);
+                          int64_t ldx, uint64_t* y, int64_t ldy, const uint64_t* rb, int64_t ldb,
+                          const int* gate, cudaStream_t st);
 size_t dot_big_scratch_bytes(int prec);
 // scratch: a dot scratch whose header span slots are (+inf, -inf)
 mp_status launch_dot_big(int prec, const uint64_t* x, int64_t ldx, const uint64_t* y, int64_t ldy,
-                         int64_t n, uint64_t* out, int64_t ldo, void* scratch, cudaStream_t st);
+                         int64_t n, uint64_t* out, int64_t ldo, void* scratch, const int* gate,
+                         cudaStream_t st);
+// BiCG (method 0) and GPBiCG (method 1) at p > 1024 (bigp_solve.cu)
+mp_status solve_big(int method, mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* opts,
+                    mp_solve_info* info, cudaStream_t st);
 mp_status launch_axpy_big(int prec, const uint64_t* al, int64_t n, const uint64_t* x, int64_t ldx,
                           uint64_t* y, int64_t ldy, cudaStream_t st);
 

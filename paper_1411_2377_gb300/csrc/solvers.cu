@@ -1005,6 +1005,10 @@ mp_status solve(int method, mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* o
   if (!status_word()) return set_error(MP_ERR_CUDA, "status word unavailable");
   if (pre && (pre->n != A->n || pre->prec != A->prec || opts->transpose))
     return set_error(MP_ERR_ARG, "preconditioner does not match the matrix (or a transposed solve)");
+  if (prec_big(A->prec)) {
+    if (pre) return set_error(MP_ERR_PREC, "ILU(0) at p = %d: only p <= 1024", A->prec);
+    return solve_big(method, A, b, x, opts, info, static_cast<cudaStream_t>(stream));
+  }
   SolveCall c{A, b, x, *opts, static_cast<cudaStream_t>(stream), pre};
   return dispatch_w(A->prec, [&](auto w) {
     constexpr int W = decltype(w)::value;

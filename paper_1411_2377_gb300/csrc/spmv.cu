@@ -828,10 +828,7 @@ mp_status check_spmv_args(mp_csr A, const mp_vec& x, const mp_vec& y, int mode) 
 mp_status launch_spmv(const mp_csr_s* M, const Sell& S, int mode, const uint64_t* x, int64_t ldx,
                       uint64_t* y, int64_t ldy, const uint64_t* b, int64_t ldb, const int* gate,
                       cudaStream_t st) {
-  if (prec_big(M->prec)) {
-    if (b) return set_error(MP_ERR_PREC, "residual at p = %d: only p <= 1024", M->prec);
-    return launch_spmv_big(M, S, mode, x, ldx, y, ldy, gate, st);
-  }
+  if (prec_big(M->prec)) return launch_spmv_big(M, S, mode, x, ldx, y, ldy, b, ldb, gate, st);
   return dispatch_w(M->prec, [&](auto w) {
     constexpr int W = decltype(w)::value;
     return spmv_w<W>(M, S, mode, x, ldx, y, ldy, b, ldb, gate, st);

@@ -144,8 +144,8 @@ def test_axpy_with_signed_zeros(p):
 
 @pytest.mark.parametrize("p", (2048, 8192))
 def test_f64_matrix_and_precision_refusals(p):
-    """mp_csr_create_f64 at the wide precisions is exact; calls outside
-    SpMV / dot / axpy return MP_ERR_PREC."""
+    """mp_csr_create_f64 at the wide precisions is exact, the residual is
+    exact; CGS (outside BiCG / GPBiCG) returns MP_ERR_PREC."""
     mpk = need_gpu()
     n = 50
     rowptr, colidx = random_csr(n, seed=7, mean_len=4, max_len=10)
@@ -160,8 +160,75 @@ def test_f64_matrix_and_precision_refusals(p):
                        f"f64 matrix {name} p={p}")
     b = mpk.Vec.from_planes(X, p)
     with pytest.raises(mpk.MPError) as e:
-        mpk.gpbicg(A, b, maxit=2)
+        mpk.cgs(A, b, maxit=2)
     assert e.value.status == 2
-    with pytest.raises(mpk.MPError) as e:
-        mpk.residual(A, b, mpk.Vec.zeros(n, p))
-    assert e.value.status == 2
+    # the residual b - A x is one exact row sum at these precisions too
+    xv = mpk.Vec.from_planes(rand_planes(n, p, 82, zero_frac=0.1, emin=-5, emax=5), p)
+    want, _ = oracle.residual(p, rowptr, colidx, vrec, recs(X), xv.records())
+    assert_bitwise(mpk.residual(A, b, xv).planes(), want, f"residual p={p}")
+
+
+def _dominant_system(p, n, seed):
+    rowptr, colidx = random_csr(n, seed=seed, mean_len=5, max_len=14)
+    rows = np.repeat(np.arange(n), np.diff(rowptr))
+    key = np.unique(np.concatenate([rows, np.arange(n)]) * n +
+                    np.concatenate([colidx, np.arange(n)]))
+    rowptr = np.zeros(n + 1, np.int64)
+    np.add.at(rowptr, key // n + 1, 1)
+    rowptr = np.cumsum(rowptr)
+    colidx = (key % n).astype(np.int32)
+    Vr = recs(rand_planes(len(colidx), p, seed + 1, zero_frac=0.0, emin=-1, emax=1))
+    for i in range(n):
+        for k in range(rowptr[i], rowptr[i + 1]):
+            if colidx[k] == i:
+                Vr[k] = oracle.from_f64(p, [float(10 + i % 7)])[0]
+    b, _ = oracle.spmv(p, oracle.EXACT, rowptr, colidx, Vr, oracle.from_f64(p, np.ones(n)))
+    return rowptr, colidx, Vr, b
+
+
+@pytest.mark.parametrize("name", ("bicg", "gpbicg"))
+@pytest.mark.parametrize("p,mode,n,rtol", [(2048, "ordered", 120, 1e-200),
+                                           (2048, "exact", 120, 1e-200),
+                                           (4096, "ordered", 60, 1e-300),
+                                           (8192, "ordered", 40, 1e-300)])
+def test_solvers_vs_oracle(name, p, mode, n, rtol):
+    """BiCG and GPBiCG at the wide precisions: status, iteration count, every
+    iterate's (r_i, r_i) and x bit for bit against the oracle's wide build;
+    x0 nonzero so that r0 = b - A x0 goes through the exact residual."""
+    mpk = need_gpu()
+    rowptr, colidx, Vr, b = _dominant_system(p, n, seed=p // 64 + n)
+    X0 = rand_planes(n, p, 99, zero_frac=0.2, emin=-2, emax=0)
+    A = mpk.CSR(rowptr, colidx, np.ascontiguousarray(Vr.T), p, transpose=True)
+    fn = getattr(mpk, name)
+    maxit = 40
+    x, info = fn(A, mpk.Vec.from_planes(np.ascontiguousarray(b.T), p),
+                 x0=mpk.Vec.from_planes(X0, p), rtol=rtol, maxit=maxit, mode=mode, poll_every=3,
+                 history=True)
+    m = oracle.ORDERED if mode == "ordered" else oracle.EXACT
+    xo, it, st, hist = getattr(oracle, name)(p, m, rowptr, colidx, Vr, b, recs(X0), rtol, 0.0,
+                                             maxit)
+    assert (info["status"], info["iters"]) == (st, it)
+    assert it > 3
+    assert_bitwise(info["history"].planes(), hist, f"{name} p={p} {mode} history")
+    assert_bitwise(x.planes(), xo, f"{name} p={p} {mode} x")
+
+
+@pytest.mark.parametrize("name", ("bicg", "gpbicg"))
+def test_solver_exits_at_the_wide_precisions(name):
+    """A diagonal system converges in one step (zeta = 0 / t = 0 paths), a
+    zero right-hand side returns at once, maxit = 0 is NC."""
+    mpk = need_gpu()
+    p, n = 2048, 33
+    rowptr = np.arange(n + 1, dtype=np.int64)
+    colidx = np.arange(n, dtype=np.int32)
+    Vr = oracle.from_f64(p, np.full(n, 4.0))
+    A = mpk.CSR(rowptr, colidx, np.ascontiguousarray(Vr.T), p, transpose=True)
+    fn = getattr(mpk, name)
+    for b in (oracle.from_f64(p, np.linspace(1, 3, n)), oracle.empty(p, n)):
+        for maxit in (0, 5):
+            x, info = fn(A, mpk.Vec.from_planes(np.ascontiguousarray(b.T), p), rtol=1e-30,
+                         maxit=maxit, poll_every=1, history=True)
+            xo, it, st, hist = getattr(oracle, name)(p, oracle.ORDERED, rowptr, colidx, Vr, b,
+                                                     oracle.empty(p, n), 1e-30, 0.0, maxit)
+            assert (info["status"], info["iters"]) == (st, it), (maxit, st, it)
+            assert_bitwise(x.planes(), xo, f"{name} exit case x")
