@@ -504,6 +504,7 @@ def run_native(args):
         if not args.no_solver:
             cpu["solver"] = oracle_solver_sample()
             cpu["wide"] = oracle_wide_sample()
+            cpu["wide_solver"] = oracle_wide_solver_sample()
 
     if rank == 0:
         line = {
@@ -785,7 +786,39 @@ def wide_bench(mpk, imad_peak, n=20000, reps=5):
                                 "t_mult_s": round(mults / (ms * 1e-3) / 1e12, 3),
                                 "frac": round(mults / (ms * 1e-3) / imad_peak, 3)})
         del x, y, X, Y
+    # the solvers at 2048 bits on the 64x64 system of the solver bench
+    rowptr, colidx, v64 = synth.stencil2d(64, seed=0)
+    p = 2048
+    A = mpk.CSR(rowptr, colidx, v64, p, transpose=True)
+    b = mpk.spmv(A, mpk.Vec.from_f64(np.ones(len(rowptr) - 1), p), mode="exact")
+    out["solvers_p2048"] = {"workload": "stencil2d_64x64_p2048_rtol1e-30"}
+    for name, fn in (("gpbicg", mpk.gpbicg), ("bicg", mpk.bicg)):
+        xs, info = fn(A, b, rtol=1e-30, maxit=2000, poll_every=32)
+        out["solvers_p2048"][name] = {"iters": info["iters"], "status": info["status"],
+                                      "ms": round(info["ms"], 2),
+                                      "ms_per_iter": round(info["ms"] / max(1, info["iters"]), 3),
+                                      "relres": info["relres"]}
+    A.close()
     return out
+
+
+def oracle_wide_solver_sample(iters=2):
+    """The oracle's GPBiCG at 2048 bits on the 64x64 system, the first
+    `iters` iterations, one thread: ms per iteration."""
+    import oracle
+    from paper_1411_2377_gb300 import synth
+
+    p = 2048
+    rp, ci, v64 = synth.stencil2d(64, seed=0)
+    n = len(rp) - 1
+    vals = oracle.from_f64(p, v64)
+    b, st = oracle.spmv(p, oracle.EXACT, rp, ci, vals, oracle.from_f64(p, np.ones(n)))
+    t0 = time.perf_counter()
+    _, it, st, _ = oracle.gpbicg(p, oracle.ORDERED, rp, ci, vals, b, oracle.empty(p, n), 1e-30,
+                                 0.0, iters)
+    dt = time.perf_counter() - t0
+    return {"workload": "stencil2d_64x64_p2048_gpbicg", "iters": int(it),
+            "ms_per_iter": round(dt * 1e3 / max(1, it), 1), "cores": 1}
 
 
 def oracle_wide_sample(budget_s=4.0, n=20000):

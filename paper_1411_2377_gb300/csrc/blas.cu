@@ -332,6 +332,55 @@ __global__ void from_f64_kernel(const double* __restrict__ d, int64_t n, uint64_
   }
 }
 
+// The same two conversions for p > 1024 (L limbs, a thread per element): a
+// double's 53-bit mantissa lands in the top limb; the nearest double takes
+// the top 53 bits, the next bit and a sticky bit over all lower limbs.
+__global__ void from_f64_wide_kernel(const double* __restrict__ d, int64_t n, uint64_t* out,
+                                     int64_t ld, int L, int* status) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double v = d[i];
+    if (!isfinite(v)) {
+      atomicCAS(status, 0, (int)MP_ERR_ARG);
+      v = 0.0;
+    }
+    uint64_t top = 0;
+    int64_t e = EXP_ZERO;
+    if (v != 0.0) {
+      int ex = 0;
+      top = (uint64_t)ldexp(frexp(fabs(v), &ex), 53) << 11;
+      e = ex;
+    }
+    out[i] = pack_head(e, signbit(v) ? 1u : 0u);
+    for (int k = 1; k < L; ++k) out[(int64_t)k * ld + i] = 0;
+    out[(int64_t)L * ld + i] = top;
+  }
+}
+
+__global__ void to_f64_wide_kernel(const uint64_t* __restrict__ a, int64_t n, int64_t ld, int L,
+                                   double* d) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t e;
+    uint32_t s;
+    unpack_head(a[i], e, s);
+    if (zero_e(e)) {
+      d[i] = s ? -0.0 : 0.0;
+      continue;
+    }
+    const uint64_t t = a[(int64_t)L * ld + i];
+    uint64_t rest = 0;
+    for (int k = 1; k < L; ++k) rest |= a[(int64_t)k * ld + i];
+    uint64_t q = t >> 11;
+    const uint64_t rb = (t >> 10) & 1u;
+    const bool sticky = (t & 0x3ffu) != 0u || rest != 0u;
+    if (rb && (sticky || (q & 1u))) q += 1u;
+    const int64_t ec = e < -4000 ? -4000 : (e > 4000 ? 4000 : e);
+    const double v = ldexp((double)q, (int)ec - 53);
+    d[i] = s ? -v : v;
+  }
+}
+
 template <int W>
 __global__ void to_f64_kernel(const uint64_t* __restrict__ a, int64_t n, int64_t ld, double* d) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -457,13 +506,20 @@ mp_status mp_ewise(int32_t op, mp_vec a, mp_vec b, mp_vec out, void* stream) {
 
 mp_status mp_vec_from_f64(const double* d, mp_vec out, void* stream) {
   mp_status r;
-  if (!prec_ok(out.prec_bits)) return set_error(MP_ERR_PREC, "precision %d", out.prec_bits);
+  const bool big = prec_big(out.prec_bits);
+  if (!prec_ok(out.prec_bits) && !big) return set_error(MP_ERR_PREC, "precision %d", out.prec_bits);
   if ((r = check_vec(out, out.n, out.prec_bits, "out")) != MP_OK) return r;
   if (out.n == 0) return MP_OK;
   if (!d) return set_error(MP_ERR_ARG, "d is null");
   int* status = status_word();
   if (!status) return set_error(MP_ERR_CUDA, "status word unavailable");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (big) {
+    from_f64_wide_kernel<<<ew_blocks(out.n), 256, 0, st>>>(d, out.n, out.data, out.ld,
+                                                           out.prec_bits / 64, status);
+    count_launch();
+    return launch_check("from_f64_wide_kernel");
+  }
   return dispatch_w(out.prec_bits, [&](auto w) {
     constexpr int W = decltype(w)::value;
     from_f64_kernel<W><<<ew_blocks(out.n), 256, 0, st>>>(d, out.n, out.data, out.ld, status);
@@ -474,11 +530,17 @@ mp_status mp_vec_from_f64(const double* d, mp_vec out, void* stream) {
 
 mp_status mp_vec_to_f64(mp_vec a, double* d, void* stream) {
   mp_status r;
-  if (!prec_ok(a.prec_bits)) return set_error(MP_ERR_PREC, "precision %d", a.prec_bits);
+  const bool big = prec_big(a.prec_bits);
+  if (!prec_ok(a.prec_bits) && !big) return set_error(MP_ERR_PREC, "precision %d", a.prec_bits);
   if ((r = check_vec(a, a.n, a.prec_bits, "a")) != MP_OK) return r;
   if (a.n == 0) return MP_OK;
   if (!d) return set_error(MP_ERR_ARG, "d is null");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (big) {
+    to_f64_wide_kernel<<<ew_blocks(a.n), 256, 0, st>>>(a.data, a.n, a.ld, a.prec_bits / 64, d);
+    count_launch();
+    return launch_check("to_f64_wide_kernel");
+  }
   return dispatch_w(a.prec_bits, [&](auto w) {
     constexpr int W = decltype(w)::value;
     to_f64_kernel<W><<<ew_blocks(a.n), 256, 0, st>>>(a.data, a.n, a.ld, d);

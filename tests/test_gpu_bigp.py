@@ -232,3 +232,22 @@ def test_solver_exits_at_the_wide_precisions(name):
                                                      oracle.empty(p, n), 1e-30, 0.0, maxit)
             assert (info["status"], info["iters"]) == (st, it), (maxit, st, it)
             assert_bitwise(x.planes(), xo, f"{name} exit case x")
+
+
+@pytest.mark.parametrize("p", WIDE)
+def test_f64_conversions(p):
+    """Doubles to p bits exactly, p bits to the nearest double (ties to even,
+    a sticky bit from every lower limb), as the oracle's wide build."""
+    mpk = need_gpu()
+    import torch
+
+    d = np.array([0.0, -0.0, 1.0, -1.5, 0.1, 1e300, -1e-300, 5e-324, 123456.789,
+                  np.nextafter(1.0, 2.0)])
+    v = mpk.Vec.from_f64(torch.as_tensor(d), p)
+    assert_bitwise(v.planes(), oracle.from_f64(p, d), f"from_f64 p={p}")
+    R = recs(rand_planes(300, p, 91, zero_frac=0.05, emin=-900, emax=900))
+    R[:5, p // 64] = np.uint64(1 << 63) | np.uint64((1 << 10))  # exactly half an ulp of a double
+    R[:5, 1:p // 64] = 0
+    got = mpk.Vec.from_planes(np.ascontiguousarray(R.T), p).to_f64().cpu().numpy()
+    want = oracle.to_f64(p, R)
+    assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
