@@ -734,19 +734,23 @@ def lotkin_bench(mpk, n=2000, precs=(128, 256, 512, 1024), s_list=(0.0, 50.0, 90
 WIDE_PRECS = (2048, 4096, 8192)
 
 
-def wide_bench(mpk, imad_peak, n=20000, reps=5):
+WIDE_N = {2048: 200_000, 4096: 100_000, 8192: 50_000}
+
+
+def wide_bench(mpk, imad_peak, reps=5):
     """p = 2048, 4096, 8192 (one value per warp): ORDERED and EXACT products on
-    the SpMV workload's pattern at n = 2*10^4 (values as there), and exact dot
-    and axpy on 10^4 elements; CUDA-event time per call and the fraction of
-    the 32-bit-multiply peak ((p/32)^2 per stored nonzero or element; the
-    bytes are far below the HBM bound at these precisions)."""
+    the SpMV workload's recipe at n = 2*10^5, 10^5, 5*10^4 (about 3.2M, 1.6M,
+    0.8M stored nonzeros: enough rows per warp that the longest row, which a
+    warp walks alone, does not set the time), and exact dot and axpy on 10^4
+    elements; CUDA-event time per call and the fraction of the 32-bit-multiply
+    peak ((p/32)^2 per stored nonzero or element; the bytes are far below the
+    HBM bound at these precisions)."""
     import torch
 
     from paper_1411_2377_gb300 import synth
 
-    rowptr, colidx = synth.spmv_pattern(n)
-    nnz = int(rowptr[-1])
-    out = {"workload": f"spmv_pattern_n{n}_nnz{nnz}", "rows": []}
+    out = {"workload": "spmv_pattern_" + "_".join(f"p{p}n{n}" for p, n in WIDE_N.items()),
+           "rows": []}
 
     def timed(call):
         call()
@@ -761,6 +765,9 @@ def wide_bench(mpk, imad_peak, n=20000, reps=5):
         return e0.elapsed_time(e1) / reps
 
     for p in WIDE_PRECS:
+        n = WIDE_N[p]
+        rowptr, colidx = synth.spmv_pattern(n)
+        nnz = int(rowptr[-1])
         vals, xs = synth.spmv_values(p, nnz, n)
         A = mpk.CSR(rowptr, colidx, vals, p)
         x = mpk.Vec.from_planes(xs, p)
@@ -768,7 +775,7 @@ def wide_bench(mpk, imad_peak, n=20000, reps=5):
         mults = nnz * (p // 32) ** 2
         for mode in ("ordered", "exact"):
             ms = timed(lambda: mpk.spmv(A, x, y, mode=mode, sync=False))
-            out["rows"].append({"op": f"spmv_{mode}", "p": p, "ms": round(ms, 4),
+            out["rows"].append({"op": f"spmv_{mode}", "p": p, "n": n, "nnz": nnz, "ms": round(ms, 4),
                                 "gnnz_s": round(nnz / (ms * 1e-3) / 1e9, 4),
                                 "t_mult_s": round(mults / (ms * 1e-3) / 1e12, 3),
                                 "frac": round(mults / (ms * 1e-3) / imad_peak, 3)})

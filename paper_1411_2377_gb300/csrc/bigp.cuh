@@ -100,13 +100,16 @@ __device__ __forceinline__ void wmul(const uint32_t* a, const uint32_t* b, const
     const int lo = k < W ? 0 : k - W + 1, hi = k + 1 < W ? k + 1 : W - 1;
     uint32_t c0 = 0, c1 = 0, c2 = 0, d0 = 0, d1 = 0, d2 = 0;
     uint32_t bn = (k + 1 - lo <= W - 1) ? b[k + 1 - lo] : 0u;  // column k+1's b at i = lo
-    for (int i = lo; i <= hi; ++i) {
+    const int last = hi < k ? hi : k;  // i <= k: column k's b index stays >= 0
+#pragma unroll 4
+    for (int i = lo; i <= last; ++i) {
       const uint32_t u = a[i];
-      const uint32_t bk = (k - i >= 0) ? b[k - i] : 0u;
+      const uint32_t bk = b[k - i];
       mac96(c0, c1, c2, u, bk);
       mac96(d0, d1, d2, u, bn);
       bn = bk;
     }
+    if (hi > last) mac96(d0, d1, d2, a[hi], bn);  // i = k + 1 < W: column k+1 alone
     m.P0[k] = c0;
     m.P1[k] = c1;
     m.P2[k] = c2;
