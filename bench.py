@@ -46,6 +46,14 @@ METRIC = "p-bit CSR SpMV Gnnz/s vs roofline"
 CONFIG_NAME = "spmv_sweep_n1e6_lognormal16_band5000_p128-1024"
 
 
+def workload_name(n, precs):
+    """The default sweep's name, or the same recipe at another size or set
+    of precisions."""
+    if n == 1_000_000 and list(precs) == [128, 256, 512, 1024]:
+        return CONFIG_NAME
+    return f"spmv_sweep_n{n}_lognormal16_band5000_p" + "-".join(str(p) for p in precs)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -319,7 +327,7 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t_tot / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64 limbs (p-bit RN)", "data": "synthetic",
-        "config": {"workload": CONFIG_NAME, "n": args.n, "precs": precs,
+        "config": {"workload": workload_name(args.n, precs), "n": args.n, "precs": precs,
                    "modes": [m for m, _ in MODES]},
         "cpu_baseline": {"value": value, "unit": "Gnnz/s", "cores": cores, "kind": "oracle",
                          "sample": desc},
@@ -512,7 +520,7 @@ def run_native(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u64 limbs (p-bit RN)", "data": "synthetic",
-            "config": {"workload": CONFIG_NAME, "n": n, "nnz": nnz, "precs": precs,
+            "config": {"workload": workload_name(n, precs), "n": n, "nnz": nnz, "precs": precs,
                        "modes": [m for m, _ in MODES], "slots": slots, "tuned": tuned,
                        "l2": "inputs larger than L2 (matrices >= 448 MB), no flush",
                        "parallelism": f"replicas x{world}", "generate_s": round(gen_s, 1)},
