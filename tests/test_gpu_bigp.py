@@ -251,3 +251,24 @@ def test_f64_conversions(p):
     got = mpk.Vec.from_planes(np.ascontiguousarray(R.T), p).to_f64().cpu().numpy()
     want = oracle.to_f64(p, R)
     assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
+
+
+@pytest.mark.parametrize("name", ("bicg", "gpbicg"))
+def test_transposed_solve(name):
+    """A^T x = b at 2048 bits (the adjoint solve): the oracle solves the
+    explicit transpose (rows of A^T list the original rows ascending, the
+    order the device's A^T keeps)."""
+    mpk = need_gpu()
+    p, n = 2048, 90
+    rowptr, colidx, Vr, b = _dominant_system(p, n, seed=5)
+    A = mpk.CSR(rowptr, colidx, np.ascontiguousarray(Vr.T), p, transpose=True)
+    x, info = getattr(mpk, name)(A, mpk.Vec.from_planes(np.ascontiguousarray(b.T), p),
+                                 rtol=1e-150, maxit=30, poll_every=4, history=True,
+                                 transpose=True)
+    rt, ct, vt = oracle.transpose(p, rowptr, colidx, Vr)
+    xo, it, st, hist = getattr(oracle, name)(p, oracle.ORDERED, rt, ct, vt, b, oracle.empty(p, n),
+                                             1e-150, 0.0, 30)
+    assert (info["status"], info["iters"]) == (st, it)
+    assert it > 3
+    assert_bitwise(info["history"].planes(), hist, f"{name} transposed history")
+    assert_bitwise(x.planes(), xo, f"{name} transposed x")
