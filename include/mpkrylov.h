@@ -15,9 +15,11 @@
  * call; p = 2048, 4096, 8192 (the precisions at which the solves of the
  * paper's Tables 1-2 converge) are accepted by mp_csr_create,
  * mp_csr_create_f64, mp_spmv, mp_spmv_t (both modes), mp_residual, mp_dot,
- * mp_axpy, mp_vec_from_f64, mp_vec_to_f64, mp_bicg and mp_gpbicg, which run
- * a warp-per-value form there (one value per warp, mantissa in shared
- * memory); every other call returns MP_ERR_PREC for them.  Every operation rounds to nearest, ties to even
+ * mp_axpy, mp_vec_from_f64, mp_vec_to_f64, mp_bicg, mp_gpbicg, mp_cgs and
+ * mp_bicgstab, which run a warp-per-value form there (one value per warp,
+ * mantissa in shared memory); every other call (ILU(0), refinement, batched
+ * solves, the pattern gradient, the dense MV, the tuner) returns MP_ERR_PREC
+ * for them.  Every operation rounds to nearest, ties to even
  * (MPFR's RN); NaN, infinities and the other rounding modes are not
  * represented.  Nonzero exponents must satisfy |e| < 2^60.
  *

@@ -1,5 +1,6 @@
-// bigp_solve.cu -- BiCG and GPBiCG (Fig. 5, K = I) at p = 2048, 4096, 8192,
-// the precisions at which the paper's solves of Tables 1-2 converge.
+// bigp_solve.cu -- BiCG and GPBiCG (Fig. 5, K = I), CGS and BiCGSTAB (the
+// other product-type methods of Tables 1-2, textbook forms) at p = 2048,
+// 4096, 8192, the precisions at which the paper's solves converge.
 //
 // Same readings and operation order as the p <= 1024 drivers: r0 = RN(b - A x0)
 // row by row exactly, r~ = r0, exact inner products, every vector update
@@ -424,7 +425,7 @@ mp_status big_grid(K kernel, size_t smem, int64_t units, int* grid) {
 
 enum Slot {
   RHO, RHO_PREV, ALPHA, BETA, ZETA, ETA, DEN, MU1, MU2, MU3, MU4, MU5, TAU, RR, RR0, THR, T1, T2,
-  T3, NSLOT
+  T3, OMEGA, TS, TT, NSLOT
 };
 
 struct Prog {
@@ -501,7 +502,8 @@ mp_status solve_big_w(int method, mp_csr A, mp_vec b, mp_vec x, const mp_solve_o
   s.st = st;
   s.hist = o->history.data;
   s.hist_ld = o->history.ld;
-  const int nvec = method == 0 ? 7 : 13;  // the last one holds the iterate
+  static const int kVecs[4] = {7, 13, 10, 8};  // BiCG, GPBiCG, CGS, BiCGSTAB
+  const int nvec = kVecs[method];                // the last one holds the iterate
   const size_t vbytes = sizeof(uint64_t) * (L + 1) * (size_t)s.ld;
   uint64_t* V = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -572,6 +574,58 @@ mp_status solve_big_w(int method, mp_csr A, mp_vec b, mp_vec x, const mp_solve_o
         if ((r = s.lin(xw, xw, pv, ALPHA, 0)) != MP_OK) break;      // x = x + alpha p
         if ((r = s.lin(rv, rv, z, ALPHA, kNegB)) != MP_OK) break;   // r = r - alpha z
         if ((r = s.lin(rt, rt, zt, ALPHA, kNegB)) != MP_OK) break;  // r~ = r~ - alpha z~
+      } else if (method == 2) {  // CGS (textbook form, the oracle's reading)
+        uint64_t *u = vec(3), *q = vec(4), *v = vec(5), *w = vec(6), *aw = vec(7), *tmp = vec(8);
+        Prog p0;
+        p0.add(kBrkZ, 0, RHO);
+        if (i > 1) p0.add(kDiv, BETA, RHO, RHO_PREV);
+        if ((r = s.run(p0)) != MP_OK) break;
+        if (i == 1) {
+          if ((r = copy(u, s.ld, rv, s.ld)) != MP_OK) break;
+          if ((r = copy(pv, s.ld, rv, s.ld)) != MP_OK) break;
+        } else {
+          if ((r = s.lin(u, rv, q, BETA, 0)) != MP_OK) break;     // u = r + beta q
+          if ((r = s.lin(tmp, q, pv, BETA, 0)) != MP_OK) break;   // q + beta p
+          if ((r = s.lin(pv, u, tmp, BETA, 0)) != MP_OK) break;   // p = u + beta (q + beta p)
+        }
+        if ((r = s.spmv(*s.SA, pv, v)) != MP_OK) break;  // v = A p
+        if ((r = s.dot(rt, v, DEN)) != MP_OK) break;
+        Prog p1;
+        p1.add(kBrkZ, 0, DEN).add(kDiv, ALPHA, RHO, DEN);
+        if ((r = s.run(p1)) != MP_OK) break;
+        if ((r = s.lin(q, u, v, ALPHA, kNegB)) != MP_OK) break;  // q = u - alpha v
+        if ((r = s.lin(w, u, q, -1, 0)) != MP_OK) break;         // w = u + q
+        if ((r = s.lin(xw, xw, w, ALPHA, 0)) != MP_OK) break;    // x = x + alpha w
+        if ((r = s.spmv(*s.SA, w, aw)) != MP_OK) break;          // A w
+        if ((r = s.lin(rv, rv, aw, ALPHA, kNegB)) != MP_OK) break;  // r = r - alpha A w
+      } else if (method == 3) {  // BiCGSTAB (textbook form, the oracle's reading)
+        uint64_t *v = vec(3), *sv = vec(4), *t = vec(5), *tmp = vec(6);
+        Prog p0;
+        p0.add(kBrkZ, 0, RHO);
+        if (i > 1)
+          p0.add(kDiv, T1, RHO, RHO_PREV).add(kDiv, T2, ALPHA, OMEGA).add(kMul, BETA, T1, T2);
+        if ((r = s.run(p0)) != MP_OK) break;
+        if (i == 1) {
+          if ((r = copy(pv, s.ld, rv, s.ld)) != MP_OK) break;
+        } else {
+          if ((r = s.lin(tmp, pv, v, OMEGA, kNegB)) != MP_OK) break;  // p - omega v
+          if ((r = s.lin(pv, rv, tmp, BETA, 0)) != MP_OK) break;      // p = r + beta (p - omega v)
+        }
+        if ((r = s.spmv(*s.SA, pv, v)) != MP_OK) break;  // v = A p
+        if ((r = s.dot(rt, v, DEN)) != MP_OK) break;
+        Prog p1;
+        p1.add(kBrkZ, 0, DEN).add(kDiv, ALPHA, RHO, DEN);
+        if ((r = s.run(p1)) != MP_OK) break;
+        if ((r = s.lin(sv, rv, v, ALPHA, kNegB)) != MP_OK) break;  // s = r - alpha v
+        if ((r = s.spmv(*s.SA, sv, t)) != MP_OK) break;            // t = A s
+        if ((r = s.dot(t, sv, TS)) != MP_OK) break;
+        if ((r = s.dot(t, t, TT)) != MP_OK) break;
+        Prog p2;
+        p2.add(kDivZ, OMEGA, TS, TT);  // omega = (t, s) / (t, t), +0 when t = 0
+        if ((r = s.run(p2)) != MP_OK) break;
+        if ((r = s.lin(xw, xw, pv, ALPHA, 0)) != MP_OK) break;     // x + alpha p
+        if ((r = s.lin(xw, xw, sv, OMEGA, 0)) != MP_OK) break;     // ... + omega s
+        if ((r = s.lin(rv, sv, t, OMEGA, kNegB)) != MP_OK) break;  // r = s - omega t
       } else {  // GPBiCG
         uint64_t *q = vec(3), *t = vec(4), *v = vec(5), *w = vec(6), *y = vec(7), *u = vec(8),
                  *z = vec(9), *sv = vec(10), *tmp = vec(11);
@@ -645,6 +699,7 @@ mp_status solve_big_w(int method, mp_csr A, mp_vec b, mp_vec x, const mp_solve_o
       if (s.hist && i - 1 < o->history.n) p4.add(kHist, 0, RR, 0, (int32_t)(i - 1));
       p4.add(kDoneLe, 0, RR, THR);
       if (method == 1) p4.add(kBrkZ, 0, ZETA);
+      if (method == 3) p4.add(kBrkZ, 0, OMEGA);
       if ((r = s.run(p4)) != MP_OK) break;
       if (i % poll == 0 || i == o->maxit) {
         MPK_CUDA(cudaMemcpyAsync(&hs, s.bs, sizeof hs, cudaMemcpyDeviceToHost, st));
@@ -687,8 +742,7 @@ mp_status solve_big_w(int method, mp_csr A, mp_vec b, mp_vec x, const mp_solve_o
 
 mp_status solve_big(int method, mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* opts,
                     mp_solve_info* info, cudaStream_t st) {
-  if (method != 0 && method != 1)
-    return set_error(MP_ERR_PREC, "at p = %d only BiCG and GPBiCG run", A->prec);
+  if (method < 0 || method > 3) return set_error(MP_ERR_ARG, "method %d", method);
   switch (A->prec) {
     case 2048: return solve_big_w<64>(method, A, b, x, opts, info, st);
     case 4096: return solve_big_w<128>(method, A, b, x, opts, info, st);

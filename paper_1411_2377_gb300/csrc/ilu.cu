@@ -264,6 +264,7 @@ extern "C" {
 mp_status mp_ilu0_create(mp_csr A, void* stream, mp_ilu* out) {
   if (!A || !out) return set_error(MP_ERR_ARG, "matrix or out is null");
   *out = nullptr;
+  if (!prec_ok(A->prec)) return set_error(MP_ERR_PREC, "ILU(0) at p = %d: p <= 1024", A->prec);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int64_t n = A->n, nnz = A->nnz, nch = A->A.nchunks;
   const int L = A->prec / 64;

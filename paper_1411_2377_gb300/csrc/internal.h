@@ -127,7 +127,7 @@ size_t dot_big_scratch_bytes(int prec);
 mp_status launch_dot_big(int prec, const uint64_t* x, int64_t ldx, const uint64_t* y, int64_t ldy,
                          int64_t n, uint64_t* out, int64_t ldo, void* scratch, const int* gate,
                          cudaStream_t st);
-// BiCG (method 0) and GPBiCG (method 1) at p > 1024 (bigp_solve.cu)
+// BiCG (method 0), GPBiCG (1), CGS (2), BiCGSTAB (3) at p > 1024 (bigp_solve.cu)
 mp_status solve_big(int method, mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* opts,
                     mp_solve_info* info, cudaStream_t st);
 mp_status launch_axpy_big(int prec, const uint64_t* al, int64_t n, const uint64_t* x, int64_t ldx,

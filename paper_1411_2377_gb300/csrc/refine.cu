@@ -625,6 +625,7 @@ mp_status mp_refine(mp_csr A, mp_vec b, mp_vec x, const mp_refine_opts* opts, mp
                     void* stream) {
   if (!A) return set_error(MP_ERR_ARG, "matrix is null");
   if (!opts) return set_error(MP_ERR_ARG, "opts is null");
+  if (!prec_ok(A->prec)) return set_error(MP_ERR_PREC, "refinement at p = %d: p <= 1024", A->prec);
   mp_status r;
   if ((r = check_vec(b, A->n, A->prec, "b")) != MP_OK) return r;
   if ((r = check_vec(x, A->n, A->prec, "x")) != MP_OK) return r;

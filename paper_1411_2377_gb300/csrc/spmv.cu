@@ -995,6 +995,7 @@ mp_status mp_csr_tune(mp_csr A, int32_t mode, int32_t reps, int32_t* tpb_out, in
 
 mp_status mp_csr_grad(mp_csr A, mp_vec lam, mp_vec x, mp_vec g, void* stream) {
   if (!A) return set_error(MP_ERR_ARG, "matrix is null");
+  if (!prec_ok(A->prec)) return set_error(MP_ERR_PREC, "pattern gradient at p = %d: p <= 1024", A->prec);
   mp_status r;
   if ((r = check_vec(lam, A->n, A->prec, "lam")) != MP_OK) return r;
   if ((r = check_vec(x, A->n, A->prec, "x")) != MP_OK) return r;
