@@ -807,7 +807,8 @@ def wide_bench(mpk, imad_peak, reps=5):
     A = mpk.CSR(rowptr, colidx, v64, p, transpose=True)
     b = mpk.spmv(A, mpk.Vec.from_f64(np.ones(len(rowptr) - 1), p), mode="exact")
     out["solvers_p2048"] = {"workload": "stencil2d_64x64_p2048_rtol1e-30"}
-    for name, fn in (("gpbicg", mpk.gpbicg), ("bicg", mpk.bicg)):
+    for name, fn in (("gpbicg", mpk.gpbicg), ("bicg", mpk.bicg), ("cgs", mpk.cgs),
+                     ("bicgstab", mpk.bicgstab)):
         xs, info = fn(A, b, rtol=1e-30, maxit=2000, poll_every=32)
         out["solvers_p2048"][name] = {"iters": info["iters"], "status": info["status"],
                                       "ms": round(info["ms"], 2),
