@@ -175,16 +175,19 @@ __device__ int64_t wdiv(const uint32_t* Ma, int64_t ea, const uint32_t* Mb, int6
                         uint32_t* Q, int64_t* S, uint32_t* out, int lane) {
   constexpr int N = DivRun<W>::N, PER = DivRun<W>::PER, P = 32 * W;
   constexpr int NQ = W + 4;
+  // The first p - 1 steps only shift Ma's top bits in: R < 2^(p-1) <= Mb,
+  // so no quotient bit can be set.  Start after them with R = Ma >> 1 (the
+  // bits of N above bit p + 2).
   uint32_t R[PER], D[PER];
 #pragma unroll
   for (int k = 0; k < PER; ++k) {
     const int w = lane * PER + k;
-    R[k] = 0u;
+    R[k] = (w < W) ? (Ma[w] >> 1) | (w + 1 < W ? Ma[w + 1] << 31 : 0u) : 0u;
     D[k] = (w < W) ? Mb[w] : 0u;
   }
   for (int k = lane; k < NQ; k += 32) Q[k] = 0u;
   __syncwarp();
-  for (int i = 2 * P + 1; i >= 0; --i) {
+  for (int i = P + 2; i >= 0; --i) {
     // R = 2 R + bit i of N (bit i - p - 2 of Ma)
     const int j = i - P - 2;
     const uint32_t nbit = (j >= 0) ? (Ma[j >> 5] >> (j & 31)) & 1u : 0u;
