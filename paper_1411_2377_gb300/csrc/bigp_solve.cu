@@ -155,92 +155,70 @@ struct SProg {
   double f[2];
 };
 
-// Number of 32-bit words a lane holds in the long division (remainder and
-// divisor of p + 2 bits, with room to spare).
-template <int W>
-struct DivRun {
-  static constexpr int N = W + 2;
-  static constexpr int PER = (N + 31) / 32;
-};
-
-// q = RN(a / b) for nonzero a, b (mantissas Ma, Mb in shared memory): binary
-// long division of N = Ma 2^(p+2) by Mb, one quotient bit per step, then
-// S = 2 floor(N/Mb) + [remainder != 0] rounded once (S carries the exact
-// round and sticky bits, as the division is never exact to a midpoint).
-// Remainder and divisor sit in registers, PER words per lane; the shift,
-// compare and subtract cross lanes by shuffles and ballots (the borrow into
-// each lane from the generate / propagate masks).  Returns the exponent.
+// q = RN(a / b) for nonzero a, b (mantissas Ma, Mb in shared memory): the
+// quotient Q = floor(N / Mb) of N = Ma 2^(p+2) by schoolbook long division in
+// base 2^32 (Knuth, TAOCP vol. 2, 4.3.1, Algorithm D; Mb has its top bit set,
+// so it needs no normalisation), then S = 2Q + [remainder != 0] rounded once
+// (S carries the exact round and sticky bits; a quotient of two p-bit numbers
+// is never exactly a midpoint).  Each of the W + 2 quotient words: the
+// estimate from the top two words of the running remainder and the divisor's
+// top two words (uniform across the warp), then the remainder window minus
+// the estimate times Mb as signed 64-bit counters (lanes over words),
+// resolved across lanes; a negative window takes Mb back once and the
+// estimate one less.  U (2W + 2 words), C (W + 2 counters), Q (W + 4 words)
+// and S (W + 5 counters) are shared-memory scratch.  Returns the exponent.
 template <int W>
 __device__ int64_t wdiv(const uint32_t* Ma, int64_t ea, const uint32_t* Mb, int64_t eb,
-                        uint32_t* Q, int64_t* S, uint32_t* out, int lane) {
-  constexpr int N = DivRun<W>::N, PER = DivRun<W>::PER, P = 32 * W;
-  constexpr int NQ = W + 4;
-  // The first p - 1 steps only shift Ma's top bits in: R < 2^(p-1) <= Mb,
-  // so no quotient bit can be set.  Start after them with R = Ma >> 1 (the
-  // bits of N above bit p + 2).
-  uint32_t R[PER], D[PER];
-#pragma unroll
-  for (int k = 0; k < PER; ++k) {
-    const int w = lane * PER + k;
-    R[k] = (w < W) ? (Ma[w] >> 1) | (w + 1 < W ? Ma[w + 1] << 31 : 0u) : 0u;
-    D[k] = (w < W) ? Mb[w] : 0u;
+                        uint32_t* U, int64_t* C, uint32_t* Q, int64_t* S, uint32_t* out, int lane) {
+  constexpr int n = W, m = W + 1, P = 32 * W, NQ = W + 4, NS = W + 5;
+  for (int k = lane; k < 2 * W + 2; k += 32) {  // U = (4 Ma) 2^(32 W)
+    uint32_t v = 0u;
+    if (k >= W && k <= 2 * W) {
+      const int i = k - W;
+      const uint32_t lo = i < W ? Ma[i] : 0u, below = i > 0 ? Ma[i - 1] : 0u;
+      v = (lo << 2) | (below >> 30);
+    }
+    U[k] = v;
   }
   for (int k = lane; k < NQ; k += 32) Q[k] = 0u;
   __syncwarp();
-  for (int i = P + 2; i >= 0; --i) {
-    // R = 2 R + bit i of N (bit i - p - 2 of Ma)
-    const int j = i - P - 2;
-    const uint32_t nbit = (j >= 0) ? (Ma[j >> 5] >> (j & 31)) & 1u : 0u;
-    const uint32_t top = R[PER - 1] >> 31;
-    uint32_t cin = __shfl_up_sync(kFull, top, 1);
-    if (lane == 0) cin = nbit;
-#pragma unroll
-    for (int k = PER - 1; k > 0; --k) R[k] = (R[k] << 1) | (R[k - 1] >> 31);
-    R[0] = (R[0] << 1) | cin;
-    // R >= D ?  The highest lane holding a differing word decides.
-    int gt = 0;
-    bool diff = false;
-#pragma unroll
-    for (int k = PER - 1; k >= 0; --k) {
-      if (!diff && R[k] != D[k]) {
-        diff = true;
-        gt = R[k] > D[k];
-      }
+  const uint32_t v1 = Mb[n - 1], v2 = Mb[n - 2];
+  for (int j = m; j >= 0; --j) {
+    const uint64_t num = ((uint64_t)U[j + n] << 32) | U[j + n - 1];
+    uint64_t qh = num / v1, rh = num % v1;
+    while (qh >= (1ull << 32) || qh * v2 > ((rh << 32) | U[j + n - 2])) {
+      qh -= 1;
+      rh += v1;
+      if (rh >= (1ull << 32)) break;
     }
-    const unsigned dm = __ballot_sync(kFull, diff);
-    bool ge = true;
-    if (dm) ge = __shfl_sync(kFull, gt, 31 - __clz(dm)) != 0;
-    if (ge) {
-      // R -= D: lane borrows out alone when its words are below D's,
-      // passes a borrow through when they are equal.
-      const unsigned g = __ballot_sync(kFull, diff && !gt);
-      const unsigned pr = __ballot_sync(kFull, !diff);
-      const unsigned bin = ((g << 1) + pr) ^ pr;
-      uint32_t br = (bin >> lane) & 1u;
-#pragma unroll
-      for (int k = 0; k < PER; ++k) {
-        const uint64_t v = (uint64_t)R[k] - D[k] - br;
-        R[k] = (uint32_t)v;
-        br = (uint32_t)(v >> 63);
-      }
-      if (lane == 0 && i < 32 * NQ) Q[i >> 5] |= 1u << (i & 31);
+    for (int k = lane; k <= n; k += 32) {
+      const uint64_t t0 = k < n ? qh * Mb[k] : 0ull, t1 = k > 0 ? qh * Mb[k - 1] : 0ull;
+      C[k] = (int64_t)U[j + k] - (int64_t)(uint32_t)t0 - (int64_t)(t1 >> 32);
     }
+    __syncwarp();
+    const int64_t top = wresolve(C, n + 1, lane);
+    __syncwarp();
+    if (top < 0) {  // the estimate was one too large
+      qh -= 1;
+      for (int k = lane; k < n; k += 32) C[k] += Mb[k];
+      __syncwarp();
+      wresolve(C, n + 1, lane);
+      __syncwarp();
+    }
+    for (int k = lane; k <= n; k += 32) U[j + k] = (uint32_t)C[k];
+    if (lane == 0) Q[j] = (uint32_t)qh;
     __syncwarp();
   }
   bool rnz = false;
-#pragma unroll
-  for (int k = 0; k < PER; ++k) rnz = rnz || R[k] != 0u;
+  for (int k = lane; k < n; k += 32) rnz = rnz || U[k] != 0u;
   const uint32_t sticky = __any_sync(kFull, rnz) ? 1u : 0u;
-  // S = 2 Q + sticky
-  constexpr int NS = NQ + 1;
-  for (int k = lane; k < NS; k += 32) {
+  for (int k = lane; k < NS; k += 32) {  // S = 2 Q + sticky
     const uint32_t lo = (k < NQ) ? Q[k] : 0u, below = (k > 0) ? Q[k - 1] : 0u;
     S[k] = (int64_t)(uint32_t)((lo << 1) | (below >> 31) | (k == 0 ? sticky : 0u));
   }
   __syncwarp();
   const int B = wtopbit(S, NS, lane);
   const int inc = wround<W>(S, NS, B, out, lane);
-  (void)N;
   return (int64_t)B + 1 + ea - eb - P - 3 + inc;
 }
 
@@ -302,6 +280,7 @@ __global__ void __launch_bounds__(32) sprog_kernel(uint64_t* S, BState* st, SPro
   unsigned char* extra = smem + BigMem<W>::bytes(false);
   int64_t* SW = reinterpret_cast<int64_t*>(extra);            // [W + 5]
   uint32_t* Qw = reinterpret_cast<uint32_t*>(SW + (W + 6));   // [W + 4]
+  uint32_t* Uw = Qw + (W + 4);                                // [2W + 2]
   for (int pc = 0; pc < prog.n; ++pc) {
     const SOp o = prog.op[pc];
     uint64_t* dst = S + (int64_t)o.d * REC;
@@ -356,7 +335,7 @@ __global__ void __launch_bounds__(32) sprog_kernel(uint64_t* S, BState* st, SPro
           wload<W>(m.A, pa, 1, 0, lane);
           wload<W>(m.X, pb, 1, 0, lane);
           __syncwarp();
-          e = wdiv<W>(m.A, ea, m.X, eb, Qw, SW, m.T, lane);
+          e = wdiv<W>(m.A, ea, m.X, eb, Uw, m.cnt, Qw, SW, m.T, lane);
         }
         wstore<W>(m.T, e, s, dst, 1, 0, lane);
         break;
@@ -472,7 +451,8 @@ struct Solver {
     return launch_dot_big(A->prec, x, ld, y, ld, n, slot(s), 1, dscr, gate(), st);
   }
   mp_status run(const Prog& pr) {
-    const size_t sm = BigMem<W>::bytes(false) + 8 * (size_t)(W + 6) + 4 * (size_t)(W + 4);
+    const size_t sm =
+        BigMem<W>::bytes(false) + 8 * (size_t)(W + 6) + 4 * (size_t)(W + 4) + 4 * (size_t)(2 * W + 2);
     MPK_CUDA(cudaFuncSetAttribute(sprog_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)sm));
     sprog_kernel<W><<<1, 32, sm, st>>>(S, bs, pr.p, hist, hist_ld);
