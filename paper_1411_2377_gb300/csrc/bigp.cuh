@@ -86,16 +86,19 @@ __device__ __forceinline__ void mac96(uint32_t& c0, uint32_t& c1, uint32_t& c2, 
 // cnt[0 .. 2W+2) <- counters with sum_k cnt[k] 2^(32k) = a * b exactly (each
 // in [0, 3 * 2^32)).  Column k of the schoolbook product, sum over i of
 // a_i b_(k-i), is at most W (2^32-1)^2 < 2^72: three words (c0, c1, c2),
-// which land on digits k, k+1, k+2.  A lane takes the column pairs
-// (2g, 2g+1), g = lane (mod 32): the pair walks one range of i, and the b
-// word of column 2g at step i is the one column 2g+1 needs at step i+1, so a
-// step loads one a and one b word for two multiply-adds (out-of-range
-// operands are taken as 0).  Pairs g and g + 32 t give every lane about the
-// same number of steps.
+// which land on digits k, k+1, k+2.  A lane takes column pairs (2g, 2g+1):
+// the pair walks one range of i, and the b word of column 2g at step i is the
+// one column 2g+1 needs at step i+1, so a step loads one a and one b word for
+// two multiply-adds.  The W pairs are dealt out longest walk first, 32 per
+// pass, so that the lanes of a pass (which run in lockstep) have walks of
+// nearly equal length.
 template <int W>
 __device__ __forceinline__ void wmul(const uint32_t* a, const uint32_t* b, const WarpMem& m,
                                      int lane) {
-  for (int g = lane; g < W; g += 32) {
+  for (int r = lane; r < W; r += 32) {
+    // pairs taken in order of their walk length (W, W-1, W-2, ...): the 32
+    // lanes of one pass walk nearly the same number of steps
+    const int g = (r & 1) ? W / 2 + (r >> 1) : W / 2 - 1 - (r >> 1);
     const int k = 2 * g;
     const int lo = k < W ? 0 : k - W + 1, hi = k + 1 < W ? k + 1 : W - 1;
     uint32_t c0 = 0, c1 = 0, c2 = 0, d0 = 0, d1 = 0, d2 = 0;
