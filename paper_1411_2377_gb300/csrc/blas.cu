@@ -12,8 +12,8 @@
 //  3. finalize: one block per dot sums the partials per digit (a warp per
 //     digit, lanes over blocks; integer sums: any order gives the same
 //     bits), resolves carries and rounds once.
-// A dot whose span exceeds the per-warp window takes a wide variant of step 2
-// with a window of the full span cap.  Up to five dots over the same index
+// A dot whose span exceeds the per-thread windows takes, inside step 2, one
+// block-wide window of the full span cap filled with shared-memory atomics.  Up to five dots over the same index
 // range run in one pass, so GPBiCG's mu_1..mu_5 read y, v and t once.
 #include <climits>
 #include <mutex>
@@ -116,14 +116,42 @@ template <int W>
 __global__ void __launch_bounds__(kDotThreads) dot_accum_kernel(const DotDev a, DotScratch s,
                                                                 const int* __restrict__ gate) {
   extern __shared__ int64_t dsm[];
+  __shared__ int64_t acc[DotWin<W>::cap];  // the block-wide window of a wide span
   if (gate && *gate) return;
   constexpr int CAP = DotWin<W>::cap;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int64_t* c = dsm + threadIdx.x;
   for (int j = 0; j < a.k; ++j) {
     const long long lo = s.emin[j], hi = s.emax[j];
-    if (!(lo <= hi && hi - lo <= kDotFastSpan)) continue;  // block-uniform
+    if (!(lo <= hi && hi - lo <= SPAN_CAP)) continue;  // block-uniform
     const int nd = dot_digits(hi - lo, W);
+    if (hi - lo > kDotFastSpan) {
+      // a span beyond the per-thread windows: one block-wide window with
+      // shared-memory atomics (rare: the solvers' vectors stay well inside)
+      for (int d = threadIdx.x; d < nd; d += kDotThreads) acc[d] = 0;
+      __syncthreads();
+      for (int64_t i = blockIdx.x * (int64_t)kDotThreads + threadIdx.x; i < a.n;
+           i += (int64_t)gridDim.x * kDotThreads) {
+        Num<W> x, y;
+        load<W>(x, a.x[j], a.ldx[j], i);
+        load<W>(y, a.y[j], a.ldy[j], i);
+        if (zero_e(x.e) || zero_e(y.e)) continue;
+        uint32_t P[2 * W], D[2 * W + 1];
+        mul_full<W>(x.m, y.m, P);
+        const int64_t off = x.e + y.e - lo;
+        shifted_digits<W>(P, (uint32_t)(off & 31), D);
+        const bool ng = (x.s ^ y.s) != 0;
+        for (int k = 0; k <= 2 * W; ++k) {
+          const int64_t v = (int64_t)D[k];
+          atomicAdd((unsigned long long*)&acc[(off >> 5) + k], (unsigned long long)(ng ? -v : v));
+        }
+      }
+      __syncthreads();
+      int64_t* part = s.partials + (size_t)j * CAP * s.nblocks;
+      for (int d = threadIdx.x; d < nd; d += kDotThreads) part[(size_t)d * s.nblocks + blockIdx.x] = acc[d];
+      __syncthreads();
+      continue;
+    }
     for (int d = 0; d < nd; ++d) c[d * kDotThreads] = 0;
     for (int64_t i = blockIdx.x * (int64_t)kDotThreads + threadIdx.x; i < a.n;
          i += (int64_t)gridDim.x * kDotThreads) {
@@ -147,42 +175,6 @@ __global__ void __launch_bounds__(kDotThreads) dot_accum_kernel(const DotDev a, 
       t = warp_sum64(t);
       if (lane == 0) part[(size_t)d * s.nblocks + blockIdx.x] = t;
     }
-    __syncthreads();
-  }
-}
-
-// Dots whose span lies in (fast window, cap]: one block-wide window with
-// shared-memory atomics.  Exits at once when no dot needs it.
-template <int W>
-__global__ void __launch_bounds__(256) dot_accum_wide_kernel(const DotDev a, DotScratch s,
-                                                             const int* __restrict__ gate) {
-  __shared__ int64_t acc[DotWin<W>::cap];
-  if (gate && *gate) return;
-  for (int j = 0; j < a.k; ++j) {
-    const long long lo = s.emin[j], hi = s.emax[j];
-    if (!(lo <= hi && hi - lo > kDotFastSpan && hi - lo <= SPAN_CAP)) continue;
-    const int nd = dot_digits(hi - lo, W);
-    for (int d = threadIdx.x; d < nd; d += blockDim.x) acc[d] = 0;
-    __syncthreads();
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-      Num<W> x, y;
-      load<W>(x, a.x[j], a.ldx[j], i);
-      load<W>(y, a.y[j], a.ldy[j], i);
-      if (zero_e(x.e) || zero_e(y.e)) continue;
-      uint32_t P[2 * W], D[2 * W + 1];
-      mul_full<W>(x.m, y.m, P);
-      const int64_t off = x.e + y.e - lo;
-      shifted_digits<W>(P, (uint32_t)(off & 31), D);
-      const bool ng = (x.s ^ y.s) != 0;
-      for (int k = 0; k <= 2 * W; ++k) {
-        const int64_t v = (int64_t)D[k];
-        atomicAdd((unsigned long long*)&acc[(off >> 5) + k], (unsigned long long)(ng ? -v : v));
-      }
-    }
-    __syncthreads();
-    int64_t* part = s.partials + (size_t)j * DotWin<W>::cap * s.nblocks;
-    for (int d = threadIdx.x; d < nd; d += blockDim.x) part[(size_t)d * s.nblocks + blockIdx.x] = acc[d];
     __syncthreads();
   }
 }
@@ -260,9 +252,8 @@ mp_status dot_w(const DotArgs& args, void* scratch, const int* gate, cudaStream_
                                 (int)cudaSharedmemCarveoutMaxShared));
   dot_span_kernel<W><<<s.nblocks, kDotThreads, 0, st>>>(a, s.emin, s.emax, gate);
   dot_accum_kernel<W><<<s.nblocks, kDotThreads, smem, st>>>(a, s, gate);
-  dot_accum_wide_kernel<W><<<s.nblocks, 256, 0, st>>>(a, s, gate);
   dot_finalize_kernel<W><<<a.k, 256, 0, st>>>(a, s, status, gate);
-  count_launch(4);
+  count_launch(3);
   return launch_check("dot kernels");
 }
 
@@ -617,9 +608,8 @@ mp_status dot_noalloc_w(const DotDev& a, void* scratch, int* status, cudaStream_
   reset_span_slots<<<1, 32, 0, st>>>(s.emin, s.emax);
   dot_span_kernel<W><<<s.nblocks, kDotThreads, 0, st>>>(a, s.emin, s.emax, nullptr);
   dot_accum_kernel<W><<<s.nblocks, kDotThreads, smem, st>>>(a, s, nullptr);
-  dot_accum_wide_kernel<W><<<s.nblocks, 256, 0, st>>>(a, s, nullptr);
   dot_finalize_kernel<W><<<1, 256, 0, st>>>(a, s, status, nullptr);
-  count_launch(5);
+  count_launch(4);
   return launch_check("mp_dot_noalloc kernels");
 }
 
