@@ -346,27 +346,7 @@ mp_status dispatch_big(int p, F&& f) {
   }
 }
 
-int big_sm_count() {
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  return sms > 0 ? sms : 1;
-}
 
-// Grid of a warp-per-unit kernel over `units`: resident blocks of all SMs at
-// most (grid-stride loops cover the rest).
-template <class K>
-mp_status big_grid(K kernel, size_t smem, int64_t units, int* grid) {
-  MPK_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int per_sm = 0;
-  MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBigThreads, smem));
-  if (per_sm < 1) return set_error(MP_ERR_CUDA, "no resident block for %zu shared bytes", smem);
-  int64_t b = (units + kBigWarps - 1) / kBigWarps;
-  const int64_t lim = (int64_t)big_sm_count() * per_sm;
-  if (b > lim) b = lim;
-  *grid = (int)(b < 1 ? 1 : b);
-  return MP_OK;
-}
 
 template <int W>
 int big_dot_blocks(int64_t n) {

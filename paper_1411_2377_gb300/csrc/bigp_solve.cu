@@ -390,20 +390,6 @@ __global__ void __launch_bounds__(32) sprog_kernel(uint64_t* S, BState* st, SPro
 
 // ---- host driver -----------------------------------------------------------------
 
-template <class K>
-mp_status big_grid(K kernel, size_t smem, int64_t units, int* grid) {
-  MPK_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int per_sm = 0, dev = 0, sms = 0;
-  MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBigThreads, smem));
-  if (per_sm < 1) return set_error(MP_ERR_CUDA, "no resident block for %zu shared bytes", smem);
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int64_t b = (units + kBigWarps - 1) / kBigWarps;
-  const int64_t lim = (int64_t)(sms > 0 ? sms : 1) * per_sm;
-  if (b > lim) b = lim;
-  *grid = (int)(b < 1 ? 1 : b);
-  return MP_OK;
-}
 
 enum Slot {
   RHO, RHO_PREV, ALPHA, BETA, ZETA, ETA, DEN, MU1, MU2, MU3, MU4, MU5, TAU, RR, RR0, THR, T1, T2,
