@@ -82,3 +82,35 @@ def test_config_calls_reject_bad_arguments_without_gpu(lib):
     assert lib.mp_csr_set_config(None, 0, 128, -1, -1) == _lib.MP_ERR_ARG
     assert lib.mp_csr_get_config(None, 0, ctypes.byref(t), None, None) == _lib.MP_ERR_ARG
     assert lib.mp_csr_tune(None, 1, 3, None, None, None, None, None) == _lib.MP_ERR_ARG
+
+
+def test_precision_sets_without_gpu(lib):
+    """p = 2048 / 4096 / 8192 pass the precision checks of the calls that
+    support them (and then stop at the missing device), other p and the
+    calls kept at p <= 1024 refuse them before any device work."""
+    import numpy as np
+
+    from paper_1411_2377_gb300 import _lib
+
+    rowptr = np.array([0, 1], np.int64)
+    col = np.array([0], np.int32)
+    v = np.array([2.0])
+    out = ctypes.c_void_p()
+
+    def create(p):
+        return lib.mp_csr_create_f64(1, rowptr.ctypes.data, col.ctypes.data, v.ctypes.data, p, 0,
+                                     None, ctypes.byref(out))
+
+    for p in (2048, 4096, 8192):
+        assert create(p) == _lib.MP_ERR_CUDA, p
+    for p in (64, 3000, 16384):
+        assert create(p) == _lib.MP_ERR_PREC, p
+    buf = np.zeros(33 * 4, np.uint64)
+    x = _lib.MpVec(4, 2048, 4, buf.ctypes.data)
+    o = _lib.MpVec(1, 2048, 1, buf.ctypes.data)
+    assert lib.mp_dot(x, x, o, None) == _lib.MP_ERR_CUDA
+    assert lib.mp_ewise(0, x, x, x, None) == _lib.MP_ERR_PREC
+    assert lib.mp_gemv(2, 2, x, _lib.MpVec(2, 2048, 2, buf.ctypes.data),
+                       _lib.MpVec(2, 2048, 2, buf.ctypes.data), None) == _lib.MP_ERR_PREC
+    bad = _lib.MpVec(4, 3000, 4, buf.ctypes.data)
+    assert lib.mp_dot(bad, bad, bad, None) == _lib.MP_ERR_PREC
