@@ -362,14 +362,25 @@ def run_native(args):
     n = args.n
     rowptr, colidx, values, xs, gen_s = build_workload(n, precs)
     nnz = len(colidx)
-    mats, xv, yv, products = {}, {}, {}, {}
+    mats, xv, yv, products, create_ms = {}, {}, {}, {}, {}
     for p in precs:
         heads = values[p][0].view(np.int64) >> 1
         products[p] = int(np.count_nonzero(heads != mpk.EXP_ZERO))
-        mats[p] = mpk.CSR(rowptr, colidx, values[p], p)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mats[p] = mpk.CSR(rowptr, colidx, values[p], p)  # validation, layout, upload
+        torch.cuda.synchronize()
+        create_ms[str(p)] = round((time.perf_counter() - t0) * 1e3, 1)
         xv[p] = mpk.Vec.from_planes(xs[p], p)
         yv[p] = mpk.Vec.empty(n, p)
     slots = {p: mats[p].info()["slots"] for p in precs}
+    # the same creation with the explicit transpose (BiCG's A^T), smallest p
+    p0 = min(precs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mpk.CSR(rowptr, colidx, values[p0], p0, transpose=True).close()
+    torch.cuda.synchronize()
+    create_ms[f"{p0}_with_transpose"] = round((time.perf_counter() - t0) * 1e3, 1)
     tuned = None
     if not args.no_tune:
         from paper_1411_2377_gb300 import tune
@@ -557,7 +568,8 @@ def run_native(args):
             "config": {"workload": workload_name(n, precs), "n": n, "nnz": nnz, "precs": precs,
                        "modes": [m for m, _ in MODES], "slots": slots, "tuned": tuned,
                        "l2": "inputs larger than L2 (matrices >= 448 MB), no flush",
-                       "parallelism": f"replicas x{world}", "generate_s": round(gen_s, 1)},
+                       "parallelism": f"replicas x{world}", "generate_s": round(gen_s, 1),
+                       "create_ms": create_ms},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks, "imad_probe_per_s": probe, "kernels": kernels, "solver": solver,
             "vectors": vectors,
