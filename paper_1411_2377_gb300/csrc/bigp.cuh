@@ -39,7 +39,8 @@ __device__ __forceinline__ WarpMem carve(unsigned char* smem, int warp, bool exa
   WarpMem m;
   m.cnt = reinterpret_cast<int64_t*>(b);
   m.acc = m.cnt + BigMem<W>::kCnt;
-  uint32_t* w = reinterpret_cast<uint32_t*>(m.cnt + BigMem<W>::kCnt + (exact ? BigMem<W>::kAcc : 0));
+  uint32_t* w =
+      reinterpret_cast<uint32_t*>(m.cnt + BigMem<W>::kCnt + (exact ? BigMem<W>::kAcc : 0));
   m.A = w;
   m.X = w + W;
   m.Y = w + 2 * W;
@@ -67,7 +68,8 @@ __device__ __forceinline__ void wstore(const uint32_t* src, int64_t e, uint32_t 
                                        uint64_t* __restrict__ v, int64_t ld, int64_t i, int lane) {
   const bool z = zero_e(e);
   for (int k = lane; k < W / 2; k += 32)
-    v[(int64_t)(k + 1) * ld + i] = z ? 0ull : ((uint64_t)src[2 * k] | ((uint64_t)src[2 * k + 1] << 32));
+    v[(int64_t)(k + 1) * ld + i] =
+        z ? 0ull : ((uint64_t)src[2 * k] | ((uint64_t)src[2 * k + 1] << 32));
   if (lane == 0) v[i] = pack_head(z ? EXP_ZERO : e, s);
 }
 

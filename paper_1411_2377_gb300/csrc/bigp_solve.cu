@@ -425,7 +425,8 @@ struct Solver {
     int grid = 0;
     mp_status r;
     if ((r = big_grid(lin_kernel<W>, sm, n, &grid)) != MP_OK) return r;
-    lin_kernel<W><<<grid, kBigThreads, sm, st>>>(out, a, b, alpha_slot < 0 ? nullptr : slot(alpha_slot),
+    const uint64_t* al = alpha_slot < 0 ? nullptr : slot(alpha_slot);
+    lin_kernel<W><<<grid, kBigThreads, sm, st>>>(out, a, b, al,
                                                  ld, n, flags, gate());
     count_launch();
     return launch_check("lin_kernel");
@@ -438,7 +439,8 @@ struct Solver {
   }
   mp_status run(const Prog& pr) {
     const size_t sm =
-        BigMem<W>::bytes(false) + 8 * (size_t)(W + 6) + 4 * (size_t)(W + 4) + 4 * (size_t)(2 * W + 2);
+        BigMem<W>::bytes(false) + 8 * (size_t)(W + 6) + 4 * (size_t)(W + 4) +
+        4 * (size_t)(2 * W + 2);
     MPK_CUDA(cudaFuncSetAttribute(sprog_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)sm));
     sprog_kernel<W><<<1, 32, sm, st>>>(S, bs, pr.p, hist, hist_ld);
@@ -453,7 +455,8 @@ double rec_to_double(const uint64_t* rec, int L) {
   const int64_t e = h >> 1;
   if (e == EXP_ZERO) return 0.0;
   const double m = (double)(rec[L] >> 11) * 0x1p-53;
-  return ((h & 1) ? -1.0 : 1.0) * std::ldexp(m, (int)std::max<int64_t>(-4000, std::min<int64_t>(4000, e)));
+  const int ec = (int)std::max<int64_t>(-4000, std::min<int64_t>(4000, e));
+  return ((h & 1) ? -1.0 : 1.0) * std::ldexp(m, ec);
 }
 
 template <int W>
@@ -478,22 +481,30 @@ mp_status solve_big_w(int method, mp_csr A, mp_vec b, mp_vec x, const mp_solve_o
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   BState hs{0, MP_ERR_NOCONV, 0};
   mp_status r = MP_OK;
+  // a failing CUDA call ends the solve through the cleanup below
+  auto ok = [&](cudaError_t e, const char* what) {
+    return e == cudaSuccess ? MP_OK : cuda_error(e, what);
+  };
   do {
-    MPK_CUDA(cudaMalloc((void**)&V, vbytes * nvec));
-    MPK_CUDA(cudaMalloc((void**)&s.S, sizeof(uint64_t) * (L + 1) * NSLOT));
-    MPK_CUDA(cudaMalloc((void**)&s.bs, sizeof(BState)));
-    MPK_CUDA(cudaMalloc(&s.dscr, dot_big_scratch_bytes(A->prec)));
+    if ((r = ok(cudaMalloc((void**)&V, vbytes * nvec), "cudaMalloc")) != MP_OK) break;
+    r = ok(cudaMalloc((void**)&s.S, sizeof(uint64_t) * (L + 1) * NSLOT),
+           "cudaMalloc");
+    if (r != MP_OK) break;
+    if ((r = ok(cudaMalloc((void**)&s.bs, sizeof(BState)), "cudaMalloc")) != MP_OK) break;
+    if ((r = ok(cudaMalloc(&s.dscr, dot_big_scratch_bytes(A->prec)), "cudaMalloc")) != MP_OK) break;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, st);
-    MPK_CUDA(cudaMemcpyAsync(s.bs, &hs, sizeof hs, cudaMemcpyHostToDevice, st));
+    r = ok(cudaMemcpyAsync(s.bs, &hs, sizeof hs, cudaMemcpyHostToDevice, st),
+           "cudaMemcpyAsync");
+    if (r != MP_OK) break;
     init_span_kernel<<<1, 32, 0, st>>>(static_cast<long long*>(s.dscr));
     init_slots_kernel<<<1, 256, 0, st>>>(s.S, NSLOT, L);
     count_launch(2);
     auto vec = [&](int k) { return V + (size_t)k * (L + 1) * s.ld; };
     for (int k = 0; k < nvec; ++k) {  // every work vector starts as +0 (GPBiCG's u = z = s = 0)
-      zero_vec_kernel<<<(int)std::min<int64_t>((s.ld + 255) / 256, 1024), 256, 0, st>>>(vec(k), s.ld,
-                                                                                       s.ld, L);
+      const int zg = (int)std::min<int64_t>((s.ld + 255) / 256, 1024);
+      zero_vec_kernel<<<zg, 256, 0, st>>>(vec(k), s.ld, s.ld, L);
       count_launch();
     }
     auto copy = [&](uint64_t* dst, int64_t ldd, const uint64_t* src, int64_t lds) -> mp_status {
@@ -671,16 +682,20 @@ mp_status solve_big_w(int method, mp_csr A, mp_vec b, mp_vec x, const mp_solve_o
       if (method == 3) p4.add(kBrkZ, 0, OMEGA);
       if ((r = s.run(p4)) != MP_OK) break;
       if (i % poll == 0 || i == o->maxit) {
-        MPK_CUDA(cudaMemcpyAsync(&hs, s.bs, sizeof hs, cudaMemcpyDeviceToHost, st));
-        MPK_CUDA(cudaStreamSynchronize(st));
+        r = ok(cudaMemcpyAsync(&hs, s.bs, sizeof hs, cudaMemcpyDeviceToHost, st),
+               "cudaMemcpyAsync");
+        if (r != MP_OK) break;
+        if ((r = ok(cudaStreamSynchronize(st), "cudaStreamSynchronize")) != MP_OK) break;
         if (hs.gate) break;
       }
     }
     if (r != MP_OK) break;
     if ((r = copy(x.data, x.ld, xw, s.ld)) != MP_OK) break;  // x holds the last iterate
     cudaEventRecord(e1, st);
-    MPK_CUDA(cudaMemcpyAsync(&hs, s.bs, sizeof hs, cudaMemcpyDeviceToHost, st));
-    MPK_CUDA(cudaStreamSynchronize(st));
+    r = ok(cudaMemcpyAsync(&hs, s.bs, sizeof hs, cudaMemcpyDeviceToHost, st),
+           "cudaMemcpyAsync");
+    if (r != MP_OK) break;
+    if ((r = ok(cudaStreamSynchronize(st), "cudaStreamSynchronize")) != MP_OK) break;
     if (info) {
       memset(info, 0, sizeof *info);
       float ms = 0.f;
@@ -689,9 +704,11 @@ mp_status solve_big_w(int method, mp_csr A, mp_vec b, mp_vec x, const mp_solve_o
       info->iters = hs.iters;
       info->status = hs.status;
       std::vector<uint64_t> h(2 * (L + 1));
-      MPK_CUDA(cudaMemcpy(h.data(), s.slot(hs.iters == 0 ? RR0 : RR), 8 * (L + 1),
-                          cudaMemcpyDeviceToHost));
-      MPK_CUDA(cudaMemcpy(h.data() + L + 1, s.slot(RR0), 8 * (L + 1), cudaMemcpyDeviceToHost));
+      if ((r = ok(cudaMemcpy(h.data(), s.slot(hs.iters == 0 ? RR0 : RR), 8 * (L + 1),
+                          cudaMemcpyDeviceToHost), "cudaMemcpy")) != MP_OK) break;
+      r = ok(cudaMemcpy(h.data() + L + 1, s.slot(RR0), 8 * (L + 1), cudaMemcpyDeviceToHost),
+             "cudaMemcpy");
+      if (r != MP_OK) break;
       const double a = rec_to_double(h.data(), L), c = rec_to_double(h.data() + L + 1, L);
       info->relres = c > 0 ? std::sqrt(a / c) : 0.0;
     }
