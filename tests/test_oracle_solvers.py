@@ -220,3 +220,33 @@ def test_printed_gpbicg_updates_break_the_residual_invariant():
 
     assert max(run(printed=False)) < 1e-12
     assert run(printed=True)[0] > 1e-3
+
+
+@pytest.mark.parametrize("name", list(SOLVERS))
+def test_wide_build_replay_and_finite_termination(name):
+    """The wide build's solvers: the exact-arithmetic replay of every iterate
+    at 2048 bits (n = 4, two iterations), and termination in at most n
+    steps with the residual below 1e-300 relative at 4096 bits."""
+    p, n = 2048, 4
+    rowptr, colidx, vals, b = rand_system(n, p, 5)
+    rows = rows_of(rowptr, colidx, vals, p)
+    x0 = oracle.empty(p, n)
+    X0 = exact.vec_decode(x0, p)
+    B = exact.vec_decode(b, p)
+    x, it, st, hist = SOLVERS[name](p, oracle.ORDERED, rowptr, colidx, vals, b, x0, 1e-300, 0.0,
+                                    2)
+    if name == "bicg":
+        trp, tci, tv = oracle.transpose(p, rowptr, colidx, vals)
+        xr, itr, _, hr = replay.bicg(rows, rows_of(trp, tci, tv, p), B, X0, p, oracle.ORDERED,
+                                     1e-300, 2)
+    else:
+        xr, itr, _, hr = getattr(replay, name)(rows, B, X0, p, oracle.ORDERED, 1e-300, 2)
+    assert it == itr
+    assert [v.key() for v in xr] == [exact.decode(r, p).key() for r in x]
+    assert [v.key() for v in hr] == [exact.decode(r, p).key() for r in hist]
+    p = 4096
+    rowptr, colidx, vals, b = rand_system(n, p, 6)
+    x, it, st, _ = SOLVERS[name](p, oracle.ORDERED, rowptr, colidx, vals, b,
+                                 oracle.empty(p, n), 1e-300, 0.0, 3 * n)
+    assert st == oracle.OK and it <= n
+    assert max(abs(v - 1) for v in to_frac(x, p)) < Fraction(1, 10 ** 290)
