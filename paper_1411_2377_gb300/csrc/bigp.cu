@@ -5,7 +5,7 @@
 // Above 1024 bits a value no longer fits in one thread's registers, so each
 // value is handled by a whole warp.  Mantissas sit in the warp's slice of
 // shared memory; the 32 lanes split the W^2 partial products of a product
-// (lane l takes the schoolbook columns k = l mod 32, each column a 96-bit
+// (each lane walks pairs of adjacent schoolbook columns, each column a 96-bit
 // mad.lo.cc / madc.hi.cc / addc chain); carries, the sign, the leading bit and
 // the rounding are resolved across the lanes, each lane owning a contiguous
 // run of words (carries move up one lane per round by shuffles, a round-up
