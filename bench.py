@@ -272,10 +272,10 @@ def _sample(oracle, p, mode, rowptr, colidx, vrec, xr, rows, threads=1):
     assert all(st == oracle.OK for st in sts)
 
 
-def oracle_solver_sample(iters=64):
-    """The oracle's GPBiCG on the 64x64 stencil at 128 bits (as the GPU
-    solver bench), the first `iters` iterations, one thread: ms per
-    iteration."""
+def oracle_solver_sample(iters=2000):
+    """The oracle's GPBiCG on the 64x64 stencil at 128 bits to 1e-30 (the GPU
+    solver bench's solve, in full: 258 iterations, a few seconds), one
+    thread: the time and ms per iteration."""
     import oracle
     from paper_1411_2377_gb300 import synth
 
