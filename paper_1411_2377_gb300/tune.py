@@ -45,6 +45,9 @@ def autotune(A: CSR, modes=("ordered", "exact"), reps: int = 5, cache: str | Non
     """Sets the fastest launch configuration of A for each mode.  Returns
     {mode: {"threads_per_block", "variant", "carveout", "ms" (None when cached),
     "cached"}}."""
+    if A.prec > 1024:  # one fixed warp-per-row form at 2048-8192 bits: nothing to tune
+        return {mode: {"threads_per_block": 128, "variant": -1, "carveout": -1, "ms": None,
+                       "cached": False, "fixed": True} for mode in modes}
     store = _load(cache) if cache else {}
     out = {}
     for mode in modes:

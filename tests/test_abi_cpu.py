@@ -114,3 +114,19 @@ def test_precision_sets_without_gpu(lib):
                        _lib.MpVec(2, 2048, 2, buf.ctypes.data), None) == _lib.MP_ERR_PREC
     bad = _lib.MpVec(4, 3000, 4, buf.ctypes.data)
     assert lib.mp_dot(bad, bad, bad, None) == _lib.MP_ERR_PREC
+
+
+def test_autotune_leaves_the_wide_precisions_alone():
+    """At 2048-8192 bits the products have one fixed form: the tuner reports
+    it without touching the device or the cache."""
+    from paper_1411_2377_gb300 import tune
+
+    class Wide:
+        prec = 2048
+
+        def tune(self, *a):
+            raise AssertionError("no timing at the wide precisions")
+
+    out = tune.autotune(Wide(), cache=None)
+    assert set(out) == {"ordered", "exact"}
+    assert all(v["fixed"] and v["variant"] == -1 for v in out.values())
