@@ -5,6 +5,16 @@ The compute path is the native library libmpkrylov.so (hand-written sm_103a
 CUDA behind a C ABI, include/mpkrylov.h); this module only marshals
 arguments.  PyTorch provides device memory and the current stream.
 
+Surface: :class:`CSR` (with its transpose, launch configuration and tuner),
+:class:`Vec`, :func:`spmv` / :func:`spmv_t` (ORDERED or EXACT rows),
+:func:`residual`, :func:`dot`, :func:`axpy`, :func:`ewise`; the solvers
+:func:`bicg`, :func:`gpbicg`, :func:`cgs`, :func:`bicgstab`,
+:func:`bicgstab_ilu0` (with :class:`ILU0`); mixed-precision refinement,
+batched solves (:class:`Batch`), the dense MV and the differentiable solve
+(``autograd``).  Precisions: 128, 256, 512, 1024 bits everywhere; 2048,
+4096, 8192 bits for the products, residual, dot, axpy, conversions and the
+four unpreconditioned solvers.
+
 Vectors (:class:`Vec`) hold p-bit values as ``L+1`` planes of 64-bit words
 (``L = p // 64``) in a ``torch.int64`` CUDA tensor of shape ``(L+1, n)``:
 plane 0 the head words ``exp*2 + sign``, planes 1..L the mantissa limbs,
