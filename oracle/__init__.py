@@ -66,6 +66,8 @@ def _load(p=0):
                          ctypes.c_double, ctypes.c_double, _i64, _i64p, _u64p],
         "mpo_bicgstab_ilu0": [_i32, _i32, _i64, _i64p, _i32p, _u64p, _u64p, _u64p,
                               ctypes.c_double, ctypes.c_double, _i64, _i64p, _u64p],
+        "mpo_bicgstab_ilu0_right": [_i32, _i32, _i64, _i64p, _i32p, _u64p, _u64p, _u64p,
+                                    ctypes.c_double, ctypes.c_double, _i64, _i64p, _u64p],
         "mpo_ilu0": [_i32, _i64, _i64p, _i32p, _u64p, _u64p],
         "mpo_ilu0_apply": [_i32, _i64, _i64p, _i32p, _u64p, _u64p, _u64p],
     }
@@ -257,8 +259,14 @@ def ilu0_apply(p, rowptr, colidx, lu, r):
     return w, st
 
 
-def bicgstab_ilu0(p, mode, rowptr, colidx, vals, b, x0, rtol, atol, maxit):
-    """BiCGSTAB right-preconditioned with ILU(0).  Returns (x, iterations,
-    status, history of (r_i, r_i))."""
-    return _solve(_load(p).mpo_bicgstab_ilu0, p, mode, rowptr, colidx, vals, b, x0, rtol, atol,
-                  maxit)
+def bicgstab_ilu0(p, mode, rowptr, colidx, vals, b, x0, rtol, atol, maxit, side="left"):
+    """BiCGSTAB preconditioned with ILU(0) K = LU.  side="left" (Section 4.2):
+    BiCGSTAB on K^{-1}A x = K^{-1}b, the history holds (r^_i, r^_i) of the
+    preconditioned residual r^ = K^{-1}(b - A x); side="right": r stays
+    b - A x and the history holds (r_i, r_i).  Returns (x, iterations,
+    status, history)."""
+    lib = _load(p)
+    if side not in ("left", "right"):
+        raise ValueError(side)
+    fn = lib.mpo_bicgstab_ilu0 if side == "left" else lib.mpo_bicgstab_ilu0_right
+    return _solve(fn, p, mode, rowptr, colidx, vals, b, x0, rtol, atol, maxit)

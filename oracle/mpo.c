@@ -1467,8 +1467,9 @@ int mpo_ilu0_apply(int p, int64_t n, const int64_t *rowptr, const int32_t *colid
  *   v = A p^,  t = A s^,  x = x + alpha p^ + omega s^;
  * r stays the residual b - A x of the unpreconditioned system, so the
  * stopping rule is unchanged.  A zero pivot of the factorization returns
- * MPO_ERR_DIVZERO before the first iteration. */
-int mpo_bicgstab_ilu0(int p, int mode, int64_t n, const int64_t *rowptr,
+ * MPO_ERR_DIVZERO before the first iteration.  Kept beside the paper's left
+ * form (mpo_bicgstab_ilu0) as an option. */
+int mpo_bicgstab_ilu0_right(int p, int mode, int64_t n, const int64_t *rowptr,
                       const int32_t *colidx, const uint64_t *vals, const uint64_t *b,
                       uint64_t *x, double rtol, double atol, int64_t maxit,
                       int64_t *iters, uint64_t *hist) {
@@ -1591,5 +1592,147 @@ done:
   free(sv);
   free(sh);
   free(t);
+  return st;
+}
+
+/* BiCGSTAB with ILU(0) as the left preconditioner K = LU: the paper's
+ * "BiCGSTAB method with ILU(0) for left preconditioning" (Section 4.2,
+ * Table 3; Fig. 5 calls K the matrix for left preconditioning and applies it
+ * by solving K w = r).  The method is BiCGSTAB (as mpo_bicgstab, the same op
+ * order) run on the preconditioned system K^{-1} A x = K^{-1} b, so every
+ * residual it carries is a preconditioned one:
+ *   r^_0 = K^{-1} (b - A x_0)  (the exact residual, rounded once, then K^{-1}),
+ *   r~ = r^_0, rho = (r~, r^),
+ *   p = r^ (i = 1), else p = RN(r^ + RN(beta RN(p - RN(omega v)))),
+ *   v = K^{-1} (A p), alpha = RN(rho / (r~, v)), s = RN(r^ - RN(alpha v)),
+ *   t = K^{-1} (A s), omega = RN((t, s) / (t, t)) (+0 when (t, t) = 0),
+ *   x = RN(RN(x + RN(alpha p)) + RN(omega s)), r^ = RN(s - RN(omega t)).
+ * The stopping rule and the history take the recursive preconditioned
+ * residual: (r^, r^) <= RN(RN(rtol^2) (r^_0, r^_0)) + RN(atol^2).  The true
+ * residual b - A x is not formed during the iteration.  Exits as
+ * mpo_bicgstab; a zero pivot returns MPO_ERR_DIVZERO before iteration 1. */
+int mpo_bicgstab_ilu0(int p, int mode, int64_t n, const int64_t *rowptr,
+                      const int32_t *colidx, const uint64_t *vals, const uint64_t *b,
+                      uint64_t *x, double rtol, double atol, int64_t maxit,
+                      int64_t *iters, uint64_t *hist) {
+  int st = solve_args(p, mode, n, rowptr, colidx, vals, b, x, rtol, atol, maxit);
+  *iters = 0;
+  if (st) return st;
+  sysA s = {p, mode, n, rowptr, colidx, vals, (size_t)(p / 64 + 1)};
+  uint64_t *lu = (uint64_t *)malloc(sizeof(uint64_t) * s.rl * (size_t)(rowptr[n] > 0 ? rowptr[n] : 1));
+  if (!lu) die("out of memory");
+  uint64_t *r = vnew(&s), *rt = vnew(&s), *pv = vnew(&s), *v = vnew(&s);
+  uint64_t *sv = vnew(&s), *t = vnew(&s), *q = vnew(&s);
+  num rr0, rr, thr, rho, rho_prev, alpha, beta, omega, d, tt, ts, t1, t2;
+  set_zero(&omega, 0);
+  set_zero(&alpha, 0);
+  st = mpo_ilu0(p, n, rowptr, colidx, vals, lu);
+  if (st) goto done;
+  st = residual_vec(p, n, rowptr, colidx, vals, b, x, q); /* b - A x0 */
+  if (st) goto done;
+  st = ilu0_apply(p, n, rowptr, colidx, lu, q, r); /* r^0 = K^{-1} (b - A x0) */
+  if (st) goto done;
+  vcopy(&s, rt, r);
+  sdot(&s, r, r, &rr0);
+  conv_threshold(p, rtol, atol, &rr0, &thr);
+  if (num_cmp(&rr0, &thr, p) <= 0) {
+    st = MPO_OK;
+    goto done;
+  }
+  sdot(&s, rt, r, &rho);
+  st = MPO_ERR_NOCONV;
+  for (int64_t i = 1; i <= maxit; i++) {
+    if (rho.zero) {
+      st = MPO_ERR_BREAKDOWN;
+      break;
+    }
+    if (i == 1) {
+      vcopy(&s, pv, r);
+    } else {
+      num_div(&rho, &rho_prev, p, &t1);
+      num_div(&alpha, &omega, p, &t2);
+      num_mul(&t1, &t2, p, &beta);
+      for (int64_t k = 0; k < n; k++) {
+        num rk, pk, vk, a1, a2, a3;
+        vload(r, k, p, &rk);
+        vload(pv, k, p, &pk);
+        vload(v, k, p, &vk);
+        num_mul(&omega, &vk, p, &a1);
+        num_sub(&pk, &a1, p, &a2);
+        num_mul(&beta, &a2, p, &a3);
+        num_add(&rk, &a3, p, &a1); /* p = r^ + beta (p - omega v) */
+        vstore(pv, k, p, &a1);
+      }
+    }
+    matvec(&s, rowptr, colidx, vals, pv, q); /* A p */
+    int ast = ilu0_apply(p, n, rowptr, colidx, lu, q, v); /* v = K^{-1} A p */
+    if (ast != MPO_OK) {
+      st = ast;
+      break;
+    }
+    sdot(&s, rt, v, &d);
+    if (d.zero) {
+      st = MPO_ERR_BREAKDOWN;
+      break;
+    }
+    num_div(&rho, &d, p, &alpha);
+    for (int64_t k = 0; k < n; k++) {
+      num rk, vk, a1, sk;
+      vload(r, k, p, &rk);
+      vload(v, k, p, &vk);
+      num_mul(&alpha, &vk, p, &a1);
+      num_sub(&rk, &a1, p, &sk); /* s = r^ - alpha v */
+      vstore(sv, k, p, &sk);
+    }
+    matvec(&s, rowptr, colidx, vals, sv, q); /* A s */
+    ast = ilu0_apply(p, n, rowptr, colidx, lu, q, t); /* t = K^{-1} A s */
+    if (ast != MPO_OK) {
+      st = ast;
+      break;
+    }
+    sdot(&s, t, sv, &ts);
+    sdot(&s, t, t, &tt);
+    if (tt.zero)
+      set_zero(&omega, 0);
+    else
+      num_div(&ts, &tt, p, &omega);
+    for (int64_t k = 0; k < n; k++) {
+      num xk, pk, sk, tk, a1, a2, a3;
+      vload(x, k, p, &xk);
+      vload(pv, k, p, &pk);
+      vload(sv, k, p, &sk);
+      vload(t, k, p, &tk);
+      num_mul(&alpha, &pk, p, &a1);
+      num_add(&xk, &a1, p, &a2);
+      num_mul(&omega, &sk, p, &a1);
+      num_add(&a2, &a1, p, &a3); /* x = x + alpha p + omega s */
+      vstore(x, k, p, &a3);
+      num_mul(&omega, &tk, p, &a1);
+      num_sub(&sk, &a1, p, &a2); /* r^ = s - omega t */
+      vstore(r, k, p, &a2);
+    }
+    *iters = i;
+    sdot(&s, r, r, &rr);
+    if (hist) rec_store(&rr, p, hist + (size_t)(i - 1) * s.rl);
+    rho_prev = rho;
+    sdot(&s, rt, r, &rho);
+    if (num_cmp(&rr, &thr, p) <= 0) {
+      st = MPO_OK;
+      break;
+    }
+    if (omega.zero) {
+      st = MPO_ERR_BREAKDOWN;
+      break;
+    }
+  }
+done:
+  free(lu);
+  free(r);
+  free(rt);
+  free(pv);
+  free(v);
+  free(sv);
+  free(t);
+  free(q);
   return st;
 }

@@ -113,7 +113,11 @@ int mpo_bicgstab(int p, int mode, int64_t n, const int64_t *rowptr,
 /* ILU(0) (textbook IKJ form, every operation rounded): lu receives L (unit
  * lower, left of the diagonal) and U (diagonal and right) in A's CSR order.
  * mpo_ilu0_apply computes w = (LU)^{-1} r.  mpo_bicgstab_ilu0 is BiCGSTAB
- * right-preconditioned with M = LU.  A zero pivot returns MPO_ERR_DIVZERO. */
+ * left-preconditioned with K = LU (Section 4.2: BiCGSTAB on K^{-1} A x =
+ * K^{-1} b; the stopping rule and the history take the preconditioned
+ * residual K^{-1}(b - A x)); mpo_bicgstab_ilu0_right is the right-
+ * preconditioned form (r stays b - A x).  A zero pivot returns
+ * MPO_ERR_DIVZERO. */
 int mpo_ilu0(int p, int64_t n, const int64_t *rowptr, const int32_t *colidx,
              const uint64_t *vals, uint64_t *lu);
 int mpo_ilu0_apply(int p, int64_t n, const int64_t *rowptr, const int32_t *colidx,
@@ -122,6 +126,10 @@ int mpo_bicgstab_ilu0(int p, int mode, int64_t n, const int64_t *rowptr,
                       const int32_t *colidx, const uint64_t *vals, const uint64_t *b,
                       uint64_t *x, double rtol, double atol, int64_t maxit,
                       int64_t *iters, uint64_t *hist);
+int mpo_bicgstab_ilu0_right(int p, int mode, int64_t n, const int64_t *rowptr,
+                            const int32_t *colidx, const uint64_t *vals, const uint64_t *b,
+                            uint64_t *x, double rtol, double atol, int64_t maxit,
+                            int64_t *iters, uint64_t *hist);
 
 #ifdef __cplusplus
 }

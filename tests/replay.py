@@ -285,8 +285,12 @@ def ilu0_apply(lu, r, p):
     return w
 
 
-def bicgstab_ilu0(rows, b, x, p, mode, rtol, maxit):
-    """BiCGSTAB right-preconditioned with ILU(0) (p^ = M^{-1} p, s^ = M^{-1} s)."""
+def bicgstab_ilu0(rows, b, x, p, mode, rtol, maxit, side="left"):
+    """BiCGSTAB preconditioned with ILU(0) K = LU.  Left (the paper's,
+    Section 4.2): BiCGSTAB on K^{-1}A x = K^{-1}b, the residual carried and
+    tested is r^ = K^{-1}(b - A x).  Right: p^ = K^{-1} p, s^ = K^{-1} s."""
+    if side == "left":
+        return _bicgstab_left(rows, b, x, p, mode, rtol, maxit)
     R = exact.rmul
     A_ = exact.radd
     S_ = exact.rsub
@@ -325,6 +329,54 @@ def bicgstab_ilu0(rows, b, x, p, mode, rtol, maxit):
         omega = D(_dot(t, s, p), tt, p) if tt.q != 0 else Z
         x = [A_(A_(xk, R(alpha, pk, p), p), R(omega, sk, p), p)
              for xk, pk, sk in zip(x, ph, sh)]
+        r = [S_(sk, R(omega, tk, p), p) for sk, tk in zip(s, t)]
+        rr = _dot(r, r, p)
+        hist.append(rr)
+        rho_prev, rho = rho, _dot(rt, r, p)
+        if rr.q <= thr.q:
+            return x, i, "ok", hist
+        if omega.q == 0:
+            return x, i, "breakdown", hist
+    return x, maxit, "noconv", hist
+
+
+def _bicgstab_left(rows, b, x, p, mode, rtol, maxit):
+    R = exact.rmul
+    A_ = exact.radd
+    S_ = exact.rsub
+    D = exact.rdiv
+    Z = exact.Val(Fraction(0))
+    lu = ilu0(rows, p)
+    r = ilu0_apply(lu, _residual(rows, b, x, p), p)
+    rt = list(r)
+    rr0 = _dot(r, r, p)
+    thr = _threshold(rr0, rtol, 0.0, p)
+    hist = []
+    if rr0.q <= thr.q:
+        return x, 0, "ok", hist
+    rho = _dot(rt, r, p)
+    pv = v = rho_prev = None
+    alpha = omega = Z
+    for i in range(1, maxit + 1):
+        if rho.q == 0:
+            return x, i - 1, "breakdown", hist
+        if i == 1:
+            pv = list(r)
+        else:
+            beta = R(D(rho, rho_prev, p), D(alpha, omega, p), p)
+            pv = [A_(rk, R(beta, S_(pk, R(omega, vk, p), p), p), p)
+                  for rk, pk, vk in zip(r, pv, v)]
+        v = ilu0_apply(lu, _spmv(rows, pv, p, mode), p)
+        d = _dot(rt, v, p)
+        if d.q == 0:
+            return x, i - 1, "breakdown", hist
+        alpha = D(rho, d, p)
+        s = [S_(rk, R(alpha, vk, p), p) for rk, vk in zip(r, v)]
+        t = ilu0_apply(lu, _spmv(rows, s, p, mode), p)
+        tt = _dot(t, t, p)
+        omega = D(_dot(t, s, p), tt, p) if tt.q != 0 else Z
+        x = [A_(A_(xk, R(alpha, pk, p), p), R(omega, sk, p), p)
+             for xk, pk, sk in zip(x, pv, s)]
         r = [S_(sk, R(omega, tk, p), p) for sk, tk in zip(s, t)]
         rr = _dot(r, r, p)
         hist.append(rr)
