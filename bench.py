@@ -614,6 +614,17 @@ def vector_bench(mpk, precs, n, hbm, imad_peak, reps=10):
             frac = max(t_hbm, t_alu) / (ms * 1e-3)
             out.append({"op": name, "p": p, "n": n, "ms": ms, "bound": "alu" if t_alu > t_hbm else "hbm",
                         "gelem_s": n / (ms * 1e-3) / 1e9, "frac": frac})
+        # the allocation-free dot (fixed 64-block scratch) on the same vectors
+        lib, sp = mpk._lib.load(), mpk._stream(None)
+        for _ in range(3):
+            lib.mp_dot_noalloc(X.c(), Y.c(), d.c(), sp)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            lib.mp_dot_noalloc(X.c(), Y.c(), d.c(), sp)
+        e1.record(stream)
+        e1.synchronize()
+        out.append({"op": "dot_noalloc", "p": p, "n": n, "ms": e0.elapsed_time(e1) / reps})
         mpk.check()
     return out
 
@@ -964,7 +975,8 @@ def solver_bench(mpk):
         err = float((x.to_f64() - 1).abs().max())
         out[name] = {"iters": info["iters"], "status": info["status"], "ms": round(info["ms"], 3),
                      "relres": info["relres"], "max_abs_err": err}
-    # BiCGSTAB right-preconditioned with ILU(0) (Section 4's preconditioned rows)
+    # BiCGSTAB with ILU(0) as the left preconditioner (Section 4.2, Table 3;
+    # the stopping rule takes the preconditioned residual), and the right form
     import time as _time
 
     import torch
@@ -974,14 +986,14 @@ def solver_bench(mpk):
     M = mpk.ILU0(A)
     torch.cuda.synchronize()
     factor_ms = (_time.perf_counter() - t0) * 1e3
-    mpk.bicgstab_ilu0(A, M, b, rtol=1e-30, maxit=2000, poll_every=32)  # warm-up
-    x, info = mpk.bicgstab_ilu0(A, M, b, rtol=1e-30, maxit=2000, poll_every=32)
-    err = float((x.to_f64() - 1).abs().max())
     nl, nu = M.levels()
-    out["bicgstab_ilu0"] = {"iters": info["iters"], "status": info["status"],
-                            "ms": round(info["ms"], 3), "relres": info["relres"],
-                            "max_abs_err": err, "factor_ms": round(factor_ms, 3),
-                            "levels": [nl, nu]}
+    for side, key in (("left", "bicgstab_ilu0"), ("right", "bicgstab_ilu0_right")):
+        mpk.bicgstab_ilu0(A, M, b, rtol=1e-30, maxit=2000, poll_every=32, side=side)  # warm-up
+        x, info = mpk.bicgstab_ilu0(A, M, b, rtol=1e-30, maxit=2000, poll_every=32, side=side)
+        err = float((x.to_f64() - 1).abs().max())
+        out[key] = {"side": side, "iters": info["iters"], "status": info["status"],
+                    "ms": round(info["ms"], 3), "relres": info["relres"],
+                    "max_abs_err": err, "factor_ms": round(factor_ms, 3), "levels": [nl, nu]}
     M.close()
     A.close()
     return out

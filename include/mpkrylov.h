@@ -228,7 +228,10 @@ mp_status mp_vec_to_f64(mp_vec a, double* d, void* stream);
  * any stream capture.  Every call on a device uses the same array, so calls
  * that overlap on the GPU (for example on two streams without ordering
  * between them) race and produce wrong results; order them on one stream.
- * Vectors longer than MP_DOT_NOALLOC_MAX_N give MP_ERR_ARG. */
+ * Precisions: p in {128, 256, 512, 1024} only (MP_ERR_PREC otherwise; the
+ * wide precisions 2048-8192 need mp_dot).  Vectors longer than
+ * MP_DOT_NOALLOC_MAX_N give MP_ERR_ARG; both refusals come before any CUDA
+ * call. */
 mp_status mp_dot_noalloc(mp_vec x, mp_vec y, mp_vec out, void* stream);
 
 /* ---- solvers (Fig. 5, left preconditioner K = I) ------------------------- */
@@ -308,12 +311,25 @@ mp_status mp_ilu0_factor(mp_ilu M, mp_vec lu, void* stream);
  * ascending) / u_ii), one launch per level.  r and w must not alias. */
 mp_status mp_ilu0_apply(mp_ilu M, mp_vec r, mp_vec w, void* stream);
 
-/* BiCGSTAB right-preconditioned with M (Barrett et al.'s preconditioned
- * BiCGSTAB): as mp_bicgstab with p^ = M^{-1} p, v = A p^, s^ = M^{-1} s,
- * t = A s^, x = x + alpha p^ + omega s^; r remains b - A x of the original
- * system, so the stopping rule is unchanged.  opts->transpose must be 0. */
+/* BiCGSTAB with ILU(0) as the left preconditioner K = LU (Section 4.2 and
+ * Table 3 run BiCGSTAB left-preconditioned by ILU(0); Fig. 5 names K the
+ * left-preconditioning matrix and applies it by solving K w = r).  BiCGSTAB (mp_bicgstab's steps and op order) on the system
+ * K^{-1} A x = K^{-1} b: r^0 = K^{-1} RN(b - A x0), v = K^{-1}(A p),
+ * t = K^{-1}(A s), x = RN(RN(x + RN(alpha p)) + RN(omega s)),
+ * r^ = RN(s - RN(omega t)).  The stopping rule, info->relres and the
+ * history take the recursive preconditioned residual r^ against r^0; the
+ * true residual b - A x is not formed.  opts->transpose must be 0; M must
+ * come from mp_ilu0_create on A.  Statuses as mp_bicgstab, plus
+ * MP_ERR_ARG for a preconditioner of another matrix. */
 mp_status mp_bicgstab_ilu0(mp_csr A, mp_ilu M, mp_vec b, mp_vec x, const mp_solve_opts* opts,
                            mp_solve_info* info, void* stream);
+
+/* The right-preconditioned form, kept as an option (Barrett et al.'s
+ * preconditioned BiCGSTAB): p^ = K^{-1} p, v = A p^, s^ = K^{-1} s,
+ * t = A s^, x = x + alpha p^ + omega s^; r remains b - A x of the original
+ * system, so the stopping rule is the unpreconditioned one. */
+mp_status mp_bicgstab_ilu0_right(mp_csr A, mp_ilu M, mp_vec b, mp_vec x,
+                                 const mp_solve_opts* opts, mp_solve_info* info, void* stream);
 
 /* ---- batched solves (not in the paper; its solver over a batch) ---------- */
 
@@ -412,6 +428,19 @@ const char* mp_last_error(void);
 /* Kernels launched by this library on the calling thread since the counter
  * was last reset (reset = 1 clears it after reading). */
 int64_t mp_launch_count(int32_t reset);
+
+/* Error-path testing (no counterpart in the paper).  mp_debug_fail arms one
+ * named host-side site so that, after `after` further passes through it, the
+ * CUDA call there is reported as failed once (cudaErrorUnknown) without
+ * being made; the library must then return MP_ERR_CUDA and release what the
+ * call had allocated.  Sites: "solver poll" (the host's read of a p <= 1024
+ * solver's device state).  site = NULL or "" disarms.  Nothing reaches the
+ * GPU: the fault is a fake status on the host.  mp_debug_pool_used returns
+ * the bytes in use in the current device's default stream-ordered memory
+ * pool (where the solvers take their work memory), to check that a failed
+ * call gave them back. */
+mp_status mp_debug_fail(const char* site, int64_t after);
+mp_status mp_debug_pool_used(int64_t* bytes);
 
 /* Throughput probe of the 32x32->64-bit multiply-add that the p-bit products
  * are made of: runs a dependency-free IMAD.WIDE.U32 loop on every SM and

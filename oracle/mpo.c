@@ -1595,10 +1595,9 @@ done:
   return st;
 }
 
-/* BiCGSTAB with ILU(0) as the left preconditioner K = LU: the paper's
- * "BiCGSTAB method with ILU(0) for left preconditioning" (Section 4.2,
- * Table 3; Fig. 5 calls K the matrix for left preconditioning and applies it
- * by solving K w = r).  The method is BiCGSTAB (as mpo_bicgstab, the same op
+/* BiCGSTAB with ILU(0) as the left preconditioner K = LU, the paper's
+ * preconditioned method (Section 4.2, Table 3; Fig. 5 calls K the matrix for
+ * left preconditioning and applies it by solving K w = r).  The method is BiCGSTAB (as mpo_bicgstab, the same op
  * order) run on the preconditioned system K^{-1} A x = K^{-1} b, so every
  * residual it carries is a preconditioned one:
  *   r^_0 = K^{-1} (b - A x_0)  (the exact residual, rounded once, then K^{-1}),

@@ -391,15 +391,21 @@ class ILU0:
 
 
 def bicgstab_ilu0(A: CSR, M: ILU0, b: Vec, x0: Vec | None = None, rtol=1e-30, atol=0.0,
-                  maxit=1000, mode="ordered", poll_every=8, history=False, stream=None):
-    """BiCGSTAB right-preconditioned with ILU(0).  Returns (x, info dict)."""
-    fn = _lib.load().mp_bicgstab_ilu0
+                  maxit=1000, mode="ordered", poll_every=8, history=False, stream=None,
+                  side="left"):
+    """BiCGSTAB preconditioned with ILU(0) K = LU.  side="left" (Section 4.2,
+    the paper's form): BiCGSTAB on K^{-1}A x = K^{-1}b, and the stopping rule,
+    relres and history take the preconditioned residual K^{-1}(b - A x);
+    side="right": r stays b - A x.  Returns (x, info dict)."""
+    if side not in ("left", "right"):
+        raise ValueError(f"side must be 'left' or 'right', not {side!r}")
+    name = "mp_bicgstab_ilu0" if side == "left" else "mp_bicgstab_ilu0_right"
+    fn = getattr(_lib.load(), name)
 
     def call(Ah, bc, xc, opts, info, st):
         return fn(Ah, M.h, bc, xc, opts, info, st)
 
-    return _solve(call, "mp_bicgstab_ilu0", A, b, x0, rtol, atol, maxit, mode, poll_every,
-                  history, stream)
+    return _solve(call, name, A, b, x0, rtol, atol, maxit, mode, poll_every, history, stream)
 
 
 class Batch:

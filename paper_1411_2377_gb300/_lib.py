@@ -85,6 +85,8 @@ SIGNATURES = {
     "mp_ilu0_apply": (_i32, [_vp, MpVec, MpVec, _vp]),
     "mp_bicgstab_ilu0": (_i32, [_vp, _vp, MpVec, MpVec, ctypes.POINTER(MpSolveOpts),
                                 ctypes.POINTER(MpSolveInfo), _vp]),
+    "mp_bicgstab_ilu0_right": (_i32, [_vp, _vp, MpVec, MpVec, ctypes.POINTER(MpSolveOpts),
+                                      ctypes.POINTER(MpSolveInfo), _vp]),
     "mp_gemv": (_i32, [_i64, _i64, MpVec, MpVec, MpVec, _vp]),
     "mp_batch_create_f64": (_i32, [_i32, _vp, _vp, _vp, _vp, _i32, _vp, ctypes.POINTER(_vp)]),
     "mp_batch_destroy": (_i32, [_vp]),
@@ -98,6 +100,8 @@ SIGNATURES = {
     "mp_status_string": (ctypes.c_char_p, [_i32]),
     "mp_last_error": (ctypes.c_char_p, []),
     "mp_launch_count": (_i64, [_i32]),
+    "mp_debug_fail": (_i32, [ctypes.c_char_p, _i64]),
+    "mp_debug_pool_used": (_i32, [_i64p]),
     "mp_imad_probe": (_i32, [ctypes.POINTER(ctypes.c_double), _vp]),
 }
 

@@ -92,6 +92,11 @@ mp_status cuda_error(cudaError_t e, const char* where);
     if (e_ != cudaSuccess) return ::mpk::cuda_error(e_, #call);     \
   } while (0)
 
+// Host-side fault injection for the error paths: returns cudaErrorUnknown
+// once when mp_debug_fail armed `site` and its countdown has run out, else
+// cudaSuccess.  Costs one relaxed atomic load when nothing is armed.
+cudaError_t injected_fault(const char* site);
+
 // ---- device status word and launch accounting ---------------------------
 int* status_word();  // device address of the current device's status word
 void count_launch(int k = 1);

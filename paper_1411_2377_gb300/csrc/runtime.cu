@@ -1,5 +1,6 @@
 // runtime.cu -- status codes, error strings, the per-device status word, the
 // launch counter, the standalone scratch buffer and the IMAD throughput probe.
+#include <atomic>
 #include <cstdarg>
 #include <cstring>
 #include <mutex>
@@ -21,6 +22,25 @@ int* g_status_addr[64] = {};
 void* g_scratch[64] = {};
 size_t g_scratch_bytes[64] = {};
 }  // namespace
+
+namespace {
+std::atomic<int> g_fail_armed{0};
+char g_fail_site[64] = "";
+int64_t g_fail_after = 0;
+}  // namespace
+
+cudaError_t injected_fault(const char* site) {
+  if (!g_fail_armed.load(std::memory_order_relaxed)) return cudaSuccess;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_fail_armed.load(std::memory_order_relaxed) || strcmp(site, g_fail_site) != 0)
+    return cudaSuccess;
+  if (g_fail_after > 0) {
+    --g_fail_after;
+    return cudaSuccess;
+  }
+  g_fail_armed.store(0);
+  return cudaErrorUnknown;
+}
 
 mp_status set_error(mp_status s, const char* fmt, ...) {
   va_list ap;
@@ -124,6 +144,33 @@ const char* mp_status_string(mp_status s) {
 }
 
 const char* mp_last_error(void) { return g_err; }
+
+mp_status mp_debug_fail(const char* site, int64_t after) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!site || !site[0]) {
+    g_fail_armed.store(0);
+    g_fail_site[0] = 0;
+    return MP_OK;
+  }
+  if (strlen(site) >= sizeof g_fail_site || after < 0)
+    return set_error(MP_ERR_ARG, "fault site name too long or negative countdown");
+  strcpy(g_fail_site, site);
+  g_fail_after = after;
+  g_fail_armed.store(1);
+  return MP_OK;
+}
+
+mp_status mp_debug_pool_used(int64_t* bytes) {
+  if (!bytes) return set_error(MP_ERR_ARG, "bytes is null");
+  int dev = 0;
+  MPK_CUDA(cudaGetDevice(&dev));
+  cudaMemPool_t pool;
+  MPK_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+  uint64_t used = 0;
+  MPK_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used));
+  *bytes = (int64_t)used;
+  return MP_OK;
+}
 
 int64_t mp_launch_count(int32_t reset) {
   const int64_t v = g_launches;

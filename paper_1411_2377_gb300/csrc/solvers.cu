@@ -44,7 +44,8 @@ struct SolveCall {
   mp_vec b, x;
   mp_solve_opts o;
   cudaStream_t st;
-  const mp_ilu_s* pre;  // right preconditioner (BiCGSTAB), or null
+  const mp_ilu_s* pre;  // ILU(0) preconditioner K (BiCGSTAB), or null
+  int pre_left;         // 1: K applied on the left (Section 4.2), 0: on the right
 };
 
 template <int W>
@@ -800,24 +801,33 @@ mp_status bicgstab_iteration(const Work& w, const SolveCall& c, bool first) {
     bs_p<W><<<g, 128, 0, st>>>(w.st, w.S, w.vec(R), w.vec(V), w.vec(P), ld, n);
     count_launch(2);
   }
-  // right preconditioning: v = A M^{-1} p, t = A M^{-1} s
+  // right preconditioning: v = A K^{-1} p, t = A K^{-1} s (x takes K^{-1} p
+  // and K^{-1} s); left: v = K^{-1} A p, t = K^{-1} A s (PH and SH hold A p
+  // and A s), and r is the preconditioned residual K^{-1}(b - A x)
+  const bool left = c.pre && c.pre_left;
   const uint64_t* pv = w.vec(P);
-  if (c.pre) {
+  if (c.pre && !left) {
     if ((r = launch_ilu0_apply(c.pre, w.vec(P), ld, w.vec(PH), ld, gate, st)) != MP_OK) return r;
     pv = w.vec(PH);
   }
-  if ((r = launch_spmv(c.A, op_a(c), c.o.mode, pv, ld, w.vec(V), ld, nullptr, 0, gate, st)) != MP_OK)
+  if ((r = launch_spmv(c.A, op_a(c), c.o.mode, pv, ld, left ? w.vec(PH) : w.vec(V), ld, nullptr,
+                       0, gate, st)) != MP_OK)
+    return r;
+  if (left && (r = launch_ilu0_apply(c.pre, w.vec(PH), ld, w.vec(V), ld, gate, st)) != MP_OK)
     return r;
   if ((r = dot2(w, w.vec(RT), w.vec(V), DEN, nullptr, nullptr, 0, st, gate)) != MP_OK) return r;
   sc_alpha<W><<<1, 1, 0, st>>>(w.st, w.S);
   bs_s<W><<<g, 128, 0, st>>>(w.st, w.S, w.vec(R), w.vec(V), w.vec(SV), ld, n);
   count_launch(2);
   const uint64_t* sv = w.vec(SV);
-  if (c.pre) {
+  if (c.pre && !left) {
     if ((r = launch_ilu0_apply(c.pre, w.vec(SV), ld, w.vec(SH), ld, gate, st)) != MP_OK) return r;
     sv = w.vec(SH);
   }
-  if ((r = launch_spmv(c.A, op_a(c), c.o.mode, sv, ld, w.vec(T), ld, nullptr, 0, gate, st)) != MP_OK)
+  if ((r = launch_spmv(c.A, op_a(c), c.o.mode, sv, ld, left ? w.vec(SH) : w.vec(T), ld, nullptr,
+                       0, gate, st)) != MP_OK)
+    return r;
+  if (left && (r = launch_ilu0_apply(c.pre, w.vec(SH), ld, w.vec(T), ld, gate, st)) != MP_OK)
     return r;
   if ((r = dot2(w, w.vec(T), w.vec(SV), TS, w.vec(T), w.vec(T), TT, st, gate)) != MP_OK) return r;
   sc_omega<W><<<1, 1, 0, st>>>(w.st, w.S);
@@ -838,10 +848,15 @@ mp_status solve_w(const SolveCall& cu, mp_solve_info* info) {
   // stream by events (the legacy default stream cannot be captured).
   cudaStream_t st = nullptr;
   cudaEvent_t fence = nullptr;
-  MPK_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-  MPK_CUDA(cudaEventCreateWithFlags(&fence, cudaEventDisableTiming));
-  MPK_CUDA(cudaEventRecord(fence, cu.st));
-  MPK_CUDA(cudaStreamWaitEvent(st, fence, 0));
+  cudaError_t ces = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (ces == cudaSuccess) ces = cudaEventCreateWithFlags(&fence, cudaEventDisableTiming);
+  if (ces == cudaSuccess) ces = cudaEventRecord(fence, cu.st);
+  if (ces == cudaSuccess) ces = cudaStreamWaitEvent(st, fence, 0);
+  if (ces != cudaSuccess) {
+    if (fence) cudaEventDestroy(fence);
+    if (st) cudaStreamDestroy(st);
+    return cuda_error(ces, "solver stream set-up");
+  }
   SolveCall c = cu;
   c.st = st;
   const int64_t n = c.A->n;
@@ -877,10 +892,15 @@ mp_status solve_w(const SolveCall& cu, mp_solve_info* info) {
       set_zero_kernel<W><<<g, 128, 0, st>>>(w.vec(k), ld, n);
       count_launch();
     }
-    // r0 = b - A x0 (exact residual), r~ = r0, (r0, r0) and rho_0 = (r~, r0)
-    if ((r = launch_spmv(c.A, op_a(c),MP_EXACT, c.x.data, c.x.ld, w.vec(0), ld, c.b.data, c.b.ld,
+    // r0 = b - A x0 (exact residual), r~ = r0, (r0, r0) and rho_0 = (r~, r0);
+    // with a left preconditioner r0 = K^{-1}(b - A x0), the residual formed
+    // in the last work vector first
+    const bool left = c.pre && c.pre_left;
+    uint64_t* r0 = left ? w.vec(w.nvec - 1) : w.vec(0);
+    if ((r = launch_spmv(c.A, op_a(c), MP_EXACT, c.x.data, c.x.ld, r0, ld, c.b.data, c.b.ld,
                          nullptr, st)) != MP_OK)
       break;
+    if (left && (r = launch_ilu0_apply(c.pre, r0, ld, w.vec(0), ld, nullptr, st)) != MP_OK) break;
     copy_kernel<W><<<g, 128, 0, st>>>(nullptr, w.vec(0), ld, w.vec(1), ld, n);
     count_launch();
     if ((r = dot2(w, w.vec(0), w.vec(0), RR0, w.vec(1), w.vec(0), RHO, st, nullptr)) != MP_OK)
@@ -890,8 +910,10 @@ mp_status solve_w(const SolveCall& cu, mp_solve_info* info) {
     if ((r = launch_check("solver setup")) != MP_OK) break;
     // first iteration (not captured)
     if ((r = body(true)) != MP_OK) break;
-    MPK_CUDA(cudaMemcpyAsync(&hs, w.st, sizeof hs, cudaMemcpyDeviceToHost, st));
-    MPK_CUDA(cudaStreamSynchronize(st));
+    cudaError_t cer = injected_fault("solver poll");
+    if (cer == cudaSuccess) cer = cudaMemcpyAsync(&hs, w.st, sizeof hs, cudaMemcpyDeviceToHost, st);
+    if (cer == cudaSuccess) cer = cudaStreamSynchronize(st);
+    if (cer != cudaSuccess) { r = cuda_error(cer, "reading the solver state"); break; }
     if (hs.done) break;
     // capture one steady-state iteration
     cudaError_t ce = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
@@ -913,8 +935,10 @@ mp_status solve_w(const SolveCall& cu, mp_solve_info* info) {
         count_launch((int)per_iter);
       }
       if (ce != cudaSuccess) { r = cuda_error(ce, "cudaGraphLaunch"); break; }
-      MPK_CUDA(cudaMemcpyAsync(&hs, w.st, sizeof hs, cudaMemcpyDeviceToHost, st));
-      MPK_CUDA(cudaStreamSynchronize(st));
+      ce = injected_fault("solver poll");
+      if (ce == cudaSuccess) ce = cudaMemcpyAsync(&hs, w.st, sizeof hs, cudaMemcpyDeviceToHost, st);
+      if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+      if (ce != cudaSuccess) { r = cuda_error(ce, "reading the solver state"); break; }
       if (hs.done) break;
     }
   } while (false);
@@ -981,7 +1005,8 @@ namespace mpk {
 namespace {
 
 mp_status solve(int method, mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* opts,
-                mp_solve_info* info, void* stream, const mp_ilu_s* pre = nullptr) {
+                mp_solve_info* info, void* stream, const mp_ilu_s* pre = nullptr,
+                int pre_left = 1) {
   if (!A) return set_error(MP_ERR_ARG, "matrix is null");
   if (!opts) return set_error(MP_ERR_ARG, "opts is null");
   mp_status r;
@@ -1009,7 +1034,7 @@ mp_status solve(int method, mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* o
     if (pre) return set_error(MP_ERR_PREC, "ILU(0) at p = %d: only p <= 1024", A->prec);
     return solve_big(method, A, b, x, opts, info, static_cast<cudaStream_t>(stream));
   }
-  SolveCall c{A, b, x, *opts, static_cast<cudaStream_t>(stream), pre};
+  SolveCall c{A, b, x, *opts, static_cast<cudaStream_t>(stream), pre, pre_left};
   return dispatch_w(A->prec, [&](auto w) {
     constexpr int W = decltype(w)::value;
     return solve_entry<W>(method, c, info);
@@ -1044,7 +1069,13 @@ mp_status mp_bicgstab(mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* opts,
 mp_status mp_bicgstab_ilu0(mp_csr A, mp_ilu M, mp_vec b, mp_vec x, const mp_solve_opts* opts,
                            mp_solve_info* info, void* stream) {
   if (!M) return mpk::set_error(MP_ERR_ARG, "preconditioner is null");
-  return mpk::solve(3, A, b, x, opts, info, stream, M);
+  return mpk::solve(3, A, b, x, opts, info, stream, M, 1);
+}
+
+mp_status mp_bicgstab_ilu0_right(mp_csr A, mp_ilu M, mp_vec b, mp_vec x,
+                                 const mp_solve_opts* opts, mp_solve_info* info, void* stream) {
+  if (!M) return mpk::set_error(MP_ERR_ARG, "preconditioner is null");
+  return mpk::solve(3, A, b, x, opts, info, stream, M, 0);
 }
 
 }  // extern "C"

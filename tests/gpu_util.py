@@ -60,3 +60,25 @@ def random_csr(n, seed, mean_len=12, max_len=96, band=None, empty_every=0):
     np.cumsum(ln, out=rowptr[1:])
     colidx = np.concatenate(cols).astype(np.int32) if cols else np.zeros(0, np.int32)
     return rowptr, colidx
+
+
+def oracle_spmv_threads(oracle, p, mode, rowptr, colidx, vals_recs, x_recs, threads=None):
+    """The oracle's y = A x over all rows, split into contiguous row ranges of
+    about equal nonzeros run on host threads (rows are independent and the C
+    oracle releases the interpreter lock, so the result equals one call's)."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+
+    n = len(rowptr) - 1
+    threads = threads or max(1, min(32, os.cpu_count() or 1))
+    y = oracle.empty(p, n)
+    nnz = int(rowptr[-1])
+    cuts = np.searchsorted(rowptr, np.linspace(0, nnz, threads + 1))
+    cuts = np.clip(cuts, 0, n)
+    cuts[0], cuts[-1] = 0, n
+    ranges = [(int(u), int(v)) for u, v in zip(cuts[:-1], cuts[1:]) if v > u]
+    with ThreadPoolExecutor(max(1, len(ranges))) as ex:
+        sts = list(ex.map(lambda r: oracle.spmv(p, mode, rowptr, colidx, vals_recs, x_recs,
+                                                rows=r, out=y)[1], ranges))
+    assert all(st == oracle.OK for st in sts), sts
+    return y

@@ -130,3 +130,33 @@ def test_autotune_leaves_the_wide_precisions_alone():
     out = tune.autotune(Wide(), cache=None)
     assert set(out) == {"ordered", "exact"}
     assert all(v["fixed"] and v["variant"] == -1 for v in out.values())
+
+
+def test_noalloc_dot_refusals_without_gpu(lib):
+    """mp_dot_noalloc refuses, on the host and before any CUDA call, vectors
+    longer than MP_DOT_NOALLOC_MAX_N (a length-2^31 view of a 4-element host
+    buffer: nothing reads it) and the wide precisions, which only mp_dot
+    takes."""
+    import numpy as np
+
+    from paper_1411_2377_gb300 import _lib
+
+    buf = np.zeros(3 * 4, np.uint64)
+    n = 2 ** 31
+    big = _lib.MpVec(n, 128, n, buf.ctypes.data)
+    out = _lib.MpVec(1, 128, 1, buf.ctypes.data)
+    assert lib.mp_dot_noalloc(big, big, out, None) == _lib.MP_ERR_ARG
+    assert b"maximum" in lib.mp_last_error()
+    wide = np.zeros(33 * 4, np.uint64)
+    x = _lib.MpVec(4, 2048, 4, wide.ctypes.data)
+    o = _lib.MpVec(1, 2048, 1, wide.ctypes.data)
+    assert lib.mp_dot_noalloc(x, x, o, None) == _lib.MP_ERR_PREC
+    assert lib.mp_dot(x, x, o, None) == _lib.MP_ERR_CUDA  # accepted, then no device
+
+
+def test_fault_hook_arguments_without_gpu(lib):
+    from paper_1411_2377_gb300 import _lib
+
+    assert lib.mp_debug_fail(b"x" * 80, 0) == _lib.MP_ERR_ARG
+    assert lib.mp_debug_fail(b"solver poll", -1) == _lib.MP_ERR_ARG
+    assert lib.mp_debug_fail(None, 0) == _lib.MP_OK

@@ -1,10 +1,12 @@
-"""Batched GPBiCG: every instance of a batch must equal mp_gpbicg on that
-instance alone (iterations, status and x, bit for bit), including instances
-that exit at once, break down, or hit the iteration limit."""
+"""Batched GPBiCG: every instance of a batch must equal the oracle's GPBiCG
+on that instance alone, and mp_gpbicg's (iterations, status and x, bit for
+bit), including instances that exit at once, break down, or hit the
+iteration limit."""
 import numpy as np
 import pytest
 
-from gpu_util import need_gpu
+import oracle
+from gpu_util import assert_bitwise, need_gpu
 from paper_1411_2377_gb300 import synth
 
 
@@ -22,9 +24,30 @@ def _instances():
 pytestmark = pytest.mark.gpu
 
 
+def _rhs(systems, plan, p):
+    """Each instance's b, formed by the oracle: RN(A (scale * ones)) exactly
+    rounded, or e1 (the breakdown system)."""
+    out = []
+    for i, scale in plan:
+        rp, ci, va = systems[i]
+        n = len(rp) - 1
+        if scale is None:
+            rhs = np.zeros(n)
+            rhs[0] = 1.0
+            out.append(oracle.from_f64(p, rhs))
+        else:
+            b, st = oracle.spmv(p, oracle.EXACT, rp, ci, oracle.from_f64(p, va),
+                                oracle.from_f64(p, np.full(n, scale)))
+            assert st == oracle.OK
+            out.append(b)
+    return out
+
+
 @pytest.mark.parametrize("p", (128, 256))
 @pytest.mark.parametrize("mode", ("ordered", "exact"))
-def test_batched_equals_single_solves(p, mode):
+def test_batched_matches_the_oracle_and_single_solves(p, mode):
+    """Every instance's iterations, status and x equal the oracle's GPBiCG on
+    that instance alone, and mp_gpbicg's (bit for bit)."""
     mpk = need_gpu()
     import torch
 
@@ -32,31 +55,29 @@ def test_batched_equals_single_solves(p, mode):
     inst = [systems[i] for i, _ in plan]
     B = mpk.Batch(inst, p)
     b = mpk.Vec.zeros(B.n, p)
-    singles = []
-    for k, (i, scale) in enumerate(plan):
-        rp, ci, va = systems[i]
-        n = len(rp) - 1
-        A = mpk.CSR(rp, ci, va, p)
-        if scale is None:
-            rhs = np.zeros(n)
-            rhs[0] = 1.0
-            bk = mpk.Vec.from_f64(rhs, p)
-        else:
-            bk = mpk.spmv(A, mpk.Vec.from_f64(np.full(n, scale), p), mode="exact")
+    rhs = _rhs(systems, plan, p)
+    for k, bk in enumerate(rhs):
         o0, o1 = int(B.offsets[k]), int(B.offsets[k + 1])
-        b.t[:, o0:o1] = bk.t
-        singles.append((A, bk))
+        b.t[:, o0:o1] = torch.from_numpy(np.ascontiguousarray(bk.T).view(np.int64)).to(b.t.device)
     maxit = 300
+    om = oracle.ORDERED if mode == "ordered" else oracle.EXACT
     x, infos = mpk.batch_gpbicg(B, b, rtol=1e-25, maxit=maxit, mode=mode, poll_every=5)
     statuses = set()
-    for k, (A, bk) in enumerate(singles):
-        xs, info = mpk.gpbicg(A, bk, rtol=1e-25, maxit=maxit, mode=mode)
+    for k, ((i, _), bk) in enumerate(zip(plan, rhs)):
+        rp, ci, va = systems[i]
+        n = len(rp) - 1
+        xo, it, st, _ = oracle.gpbicg(p, om, rp, ci, oracle.from_f64(p, va), bk,
+                                      oracle.empty(p, n), 1e-25, 0.0, maxit)
         o0, o1 = int(B.offsets[k]), int(B.offsets[k + 1])
-        assert (infos[k]["iters"], infos[k]["status"]) == (info["iters"], info["status"]), k
+        assert (infos[k]["iters"], infos[k]["status"]) == (it, st), k
+        assert_bitwise(x.t[:, o0:o1].cpu().numpy().view(np.uint64), xo, f"instance {k}")
+        A = mpk.CSR(rp, ci, va, p)
+        xs, info = mpk.gpbicg(A, mpk.Vec.from_planes(np.ascontiguousarray(bk.T), p),
+                              rtol=1e-25, maxit=maxit, mode=mode)
+        assert (info["iters"], info["status"]) == (it, st), k
         assert torch.equal(x.t[:, o0:o1].cpu(), xs.t.cpu()), k
-        statuses.add(info["status"])
-    assert {0, 6} <= statuses  # converged and breakdown instances present
-
+        statuses.add(st)
+    assert {oracle.OK, oracle.ERR_BREAKDOWN} <= statuses
 
 
 def test_batch_matrix_configuration_keeps_results():

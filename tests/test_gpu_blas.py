@@ -115,3 +115,25 @@ def test_repeated_dots_reuse_scratch():
         got = mpk.dot(mpk.Vec.from_planes(X, p), mpk.Vec.from_planes(Y, p))
         want, _ = oracle.dot(p, recs(X), recs(Y))
         assert_bitwise(got.planes(), want[None], f"dot #{i}")
+
+
+@pytest.mark.parametrize("p", (128, 1024))
+def test_dot_at_the_benchmark_size(p):
+    """The exact dot on the benchmark's vectors (n = 10^6, SpMV-workload
+    values, the grid-stride path), through mp_dot and mp_dot_noalloc, equal
+    to the oracle's exact dot."""
+    mpk = need_gpu()
+    from paper_1411_2377_gb300 import synth
+
+    n = 1_000_000
+    X = synth.random_values(n, p, seed=11, zero_frac=0.0)
+    Y = synth.random_values(n, p, seed=12, zero_frac=0.0)
+    x, y = mpk.Vec.from_planes(X, p), mpk.Vec.from_planes(Y, p)
+    want, st = oracle.dot(p, recs(X), recs(Y))
+    assert st == oracle.OK
+    assert_bitwise(mpk.dot(x, y).planes(), want[None], f"dot p={p} n=1e6")
+    lib = mpk._lib.load()
+    out = mpk.Vec.empty(1, p)
+    assert lib.mp_dot_noalloc(x.c(), y.c(), out.c(), mpk._stream(None)) == 0
+    mpk.check()
+    assert_bitwise(out.planes(), want[None], f"dot_noalloc p={p} n=1e6")

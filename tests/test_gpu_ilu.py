@@ -1,6 +1,8 @@
 """ILU(0) on the device vs the oracle, bit for bit: the factors, the
-preconditioner application, and BiCGSTAB right-preconditioned with it (every
-iterate's (r_i, r_i), the iteration count, the status and x)."""
+preconditioner application (one-block and one-launch-per-level forms), and
+BiCGSTAB preconditioned with it, left (Section 4.2, the paper's form) and
+right (every iterate's residual norm, the iteration count, the status and
+x)."""
 import numpy as np
 import pytest
 
@@ -46,9 +48,10 @@ def test_factor_and_apply_match_the_oracle(p):
     assert 1 <= nl <= n and 1 <= nu <= n
 
 
-@pytest.mark.parametrize("p", (128, 256))
+@pytest.mark.parametrize("side", ("left", "right"))
+@pytest.mark.parametrize("p", (128, 256, 1024))
 @pytest.mark.parametrize("mode", ("ordered", "exact"))
-def test_preconditioned_bicgstab_matches_the_oracle(p, mode):
+def test_preconditioned_bicgstab_matches_the_oracle(p, mode, side):
     mpk = need_gpu()
     rowptr, colidx, v64 = synth.stencil2d(16, seed=2)
     n = len(rowptr) - 1
@@ -57,21 +60,23 @@ def test_preconditioned_bicgstab_matches_the_oracle(p, mode):
     A = mpk.CSR(rowptr, colidx, v64, p)
     M = mpk.ILU0(A)
     x, info = mpk.bicgstab_ilu0(A, M, mpk.Vec.from_planes(synth.records_to_planes(b), p),
-                                rtol=1e-30, maxit=300, mode=mode, poll_every=3, history=True)
+                                rtol=1e-30, maxit=300, mode=mode, poll_every=3, history=True,
+                                side=side)
     m = oracle.ORDERED if mode == "ordered" else oracle.EXACT
     xo, it, st, hist = oracle.bicgstab_ilu0(p, m, rowptr, colidx, vals, b, oracle.empty(p, n),
-                                            1e-30, 0.0, 300)
+                                            1e-30, 0.0, 300, side=side)
     assert st == oracle.OK
     assert (info["iters"], info["status"]) == (it, st)
-    assert_bitwise(info["history"].planes(), hist, f"history p={p} {mode}")
-    assert_bitwise(x.planes(), xo, f"x p={p} {mode}")
+    assert_bitwise(info["history"].planes(), hist, f"history p={p} {mode} {side}")
+    assert_bitwise(x.planes(), xo, f"x p={p} {mode} {side}")
     # fewer iterations than without the preconditioner
     _, plain = mpk.bicgstab(A, mpk.Vec.from_planes(synth.records_to_planes(b), p), rtol=1e-30,
                             maxit=300, mode=mode)
     assert info["iters"] < plain["iters"]
 
 
-def test_noconv_and_poll_interval():
+@pytest.mark.parametrize("side", ("left", "right"))
+def test_noconv_and_poll_interval(side):
     mpk = need_gpu()
     p = 512
     rowptr, colidx, v64 = synth.stencil2d(12, seed=6)
@@ -81,10 +86,10 @@ def test_noconv_and_poll_interval():
     A = mpk.CSR(rowptr, colidx, v64, p)
     M = mpk.ILU0(A)
     xo, it, st, hist = oracle.bicgstab_ilu0(p, oracle.EXACT, rowptr, colidx, Vr, recs(B),
-                                            oracle.empty(p, n), 1e-200, 0.0, 3)
+                                            oracle.empty(p, n), 1e-200, 0.0, 3, side=side)
     for poll in (1, 7):
         x, info = mpk.bicgstab_ilu0(A, M, mpk.Vec.from_planes(B, p), rtol=1e-200, maxit=3,
-                                    mode="exact", poll_every=poll, history=True)
+                                    mode="exact", poll_every=poll, history=True, side=side)
         assert (info["iters"], info["status"]) == (it, st) == (3, oracle.ERR_NOCONV)
         assert_bitwise(info["history"].planes(), hist, "history")
         assert_bitwise(x.planes(), xo, "x")
@@ -103,3 +108,25 @@ def test_zero_pivot_and_missing_diagonal():
     with pytest.raises(mpk.MPError) as e:
         mpk.ILU0(B)
     assert e.value.status == 9
+
+
+def test_apply_beyond_one_block_matches_the_oracle():
+    """n > 2^18 rows: the solves run one launch per level instead of one
+    block looping over the levels (2-D stencil, 2 * 520 - 1 levels each)."""
+    mpk = need_gpu()
+    p = 128
+    rowptr, colidx, v64 = synth.stencil2d(520, seed=4)
+    n = len(rowptr) - 1
+    assert n > 2 ** 18
+    vals = oracle.from_f64(p, v64)
+    A = mpk.CSR(rowptr, colidx, v64, p)
+    M = mpk.ILU0(A)
+    assert M.levels() == (2 * 520 - 1, 2 * 520 - 1)
+    lu_o, st = oracle.ilu0(p, rowptr, colidx, vals)
+    assert st == oracle.OK
+    assert_bitwise(M.factor().planes(), lu_o, "ILU(0) factor n=270400")
+    R = rand_planes(n, p, 31, zero_frac=0.02, emin=-4, emax=4)
+    w = M.apply(mpk.Vec.from_planes(R, p))
+    w_o, st = oracle.ilu0_apply(p, rowptr, colidx, lu_o, recs(R))
+    assert st == oracle.OK
+    assert_bitwise(w.planes(), w_o, "ILU(0) apply n=270400")

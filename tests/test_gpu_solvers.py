@@ -142,3 +142,43 @@ def test_transposed_solve_matches_the_oracle_on_the_transpose(name):
     assert (info["iters"], info["status"]) == (it, st)
     assert_bitwise(x.planes(), xo, f"{name} transpose x")
     assert_bitwise(info["history"].planes(), hist, f"{name} transpose history")
+
+
+@pytest.mark.parametrize("after", (0, 2))
+def test_failed_state_read_returns_cuda_status_and_releases_work_memory(after):
+    """A CUDA failure while the host reads the solver's device state (made on
+    the host by the library's fault hook: nothing faults on the GPU) returns
+    MP_ERR_CUDA and gives back the solve's graph, events, stream and work
+    memory; the next solve is unaffected and still matches the oracle."""
+    import ctypes
+    import torch
+
+    mpk = need_gpu()
+    lib = mpk._lib.load()
+    p = 256
+    rowptr, colidx, v64 = synth.stencil2d(16, seed=0)
+    n = len(rowptr) - 1
+    vals = oracle.from_f64(p, v64)
+    b, _ = oracle.spmv(p, oracle.EXACT, rowptr, colidx, vals, oracle.from_f64(p, np.ones(n)))
+    A = mpk.CSR(rowptr, colidx, v64, p)
+    bv = mpk.Vec.from_planes(synth.records_to_planes(b), p)
+    torch.cuda.synchronize()
+    used = ctypes.c_int64()
+    assert lib.mp_debug_pool_used(ctypes.byref(used)) == 0
+    before = used.value
+    assert lib.mp_debug_fail(b"solver poll", after) == 0
+    try:
+        with pytest.raises(mpk.MPError) as e:
+            mpk.gpbicg(A, bv, rtol=1e-40, maxit=200, poll_every=1)
+    finally:
+        lib.mp_debug_fail(None, 0)
+    assert e.value.status == 4  # MP_ERR_CUDA
+    assert b"reading the solver state" in lib.mp_last_error()
+    torch.cuda.synchronize()
+    assert lib.mp_debug_pool_used(ctypes.byref(used)) == 0
+    assert used.value == before
+    x, info = mpk.gpbicg(A, bv, rtol=1e-40, maxit=200)
+    xo, it, st, _ = oracle.gpbicg(p, oracle.ORDERED, rowptr, colidx, vals, b,
+                                  oracle.empty(p, n), 1e-40, 0.0, 200)
+    assert (info["iters"], info["status"]) == (it, st) == (it, oracle.OK)
+    assert_bitwise(x.planes(), xo, "x after the failed solve")

@@ -4,7 +4,8 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_util import assert_bitwise, need_gpu, rand_planes, random_csr, recs
+from gpu_util import (assert_bitwise, need_gpu, oracle_spmv_threads, rand_planes, random_csr,
+                      recs)
 from paper_1411_2377_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -149,32 +150,42 @@ _PATTERN = {}
 
 
 @pytest.mark.parametrize("p", PRECS)
-def test_full_size_sampled_rows(p):
+def test_full_size_every_row(p):
     """The throughput workload at full size (n = 10^6, lognormal rows, band
-    +-5000, 10% far columns, 1% zeros) in the benchmark's launch
-    configuration; ~400 sampled rows recomputed by the oracle one by one."""
+    +-5000, 10% far columns, 1% zeros): every row of y = A x, both modes,
+    bit-identical to the oracle (run over the host's cores) in the launch
+    configuration the benchmark times (autotuned as it does), in the
+    library's default one, and in every variant code 0-31 of the launch
+    configuration (whatever the tuner could pick)."""
     mpk = need_gpu()
+    from paper_1411_2377_gb300 import tune
+
     if "p" not in _PATTERN:
         _PATTERN["p"] = synth.spmv_pattern()
     rowptr, colidx = _PATTERN["p"]
     n = len(rowptr) - 1
     V, X = synth.spmv_values(p, len(colidx), n)
+    Vr, Xr = recs(V), recs(X)
     A = mpk.CSR(rowptr, colidx, V, p)
+    del V
     x = mpk.Vec.from_planes(X, p)
-    rows = np.unique(synth.u64(5, 1, np.arange(400)) % np.uint64(n)).astype(np.int64)
-    lens = np.diff(rowptr)
-    rows = np.unique(np.concatenate([rows, [int(np.argmax(lens)), n - 1, 0]]))
-    Xr = recs(X)
+    y = mpk.Vec.empty(n, p)
+    tuned = tune.autotune(A, reps=3, cache=None)
     for name, mode in MODES:
-        y = mpk.spmv(A, x, mode=name).planes()
-        for r in rows:
-            s, e = int(rowptr[r]), int(rowptr[r + 1])
-            m = e - s
-            sub_rp = np.full(m + 1, m, np.int64)
-            sub_rp[0] = 0
-            want, st = oracle.spmv(p, mode, sub_rp, np.arange(m, dtype=np.int32),
-                                   recs(V[:, s:e]), Xr[colidx[s:e]], rows=(0, 1))
-            assert st == oracle.OK
-            assert np.array_equal(y[:, r], want[0]), (name, p, r)
-        del y
+        want = oracle_spmv_threads(oracle, p, mode, rowptr, colidx, Vr, Xr).T
+
+        def check(what):
+            mpk.spmv(A, x, y, mode=name)
+            got = y.planes()
+            bad = np.nonzero(np.any(got != want, axis=0))[0]
+            assert bad.size == 0, f"{name} p={p} {what}: {bad.size} rows differ, first {bad[:5]}"
+
+        t = tuned[name]
+        A.set_config(name, t["threads_per_block"], t["variant"], t["carveout"])
+        check(f"tuned {t}")
+        carve = 50 if name == "exact" else -1
+        for v in range(-1, 32):
+            A.set_config(name, 128, v, carve)
+            check(f"variant {v}")
+        del want
     A.close()

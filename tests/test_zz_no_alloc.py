@@ -6,14 +6,17 @@ cudaMalloc/cudaFree can cause.  Its scratch is one fixed device array inside
 the library that every call reuses, so its results must equal mp_dot's bit
 for bit on consecutive calls, whatever the previous call left in the array.
 
-This file is collected last, so a run that stops at the first failure has
-already run every other test.  It passes alone in a fresh process as well:
-the first mp_dot_noalloc call on the device does the array's set-up."""
+The length limit is refused on the host before any device work; that check
+runs without a GPU in test_abi_cpu.py.  This file is collected last, so a run
+that stops at the first failure has already run every other test.  It passes
+alone in a fresh process as well: the first mp_dot_noalloc call on the device
+does the array's set-up."""
 
 import numpy as np
 import pytest
 
-from gpu_util import need_gpu, rand_planes
+import oracle
+from gpu_util import need_gpu, rand_planes, recs
 
 pytestmark = pytest.mark.gpu
 
@@ -44,15 +47,8 @@ def test_noalloc_dot_matches_dot_on_two_calls_in_a_row():
     # and once more after the smaller call, to see no state carried over
     again = _dot(lib, mpk, "mp_dot_noalloc", *vecs[0])
     assert np.array_equal(again, refs[0])
-
-
-def test_noalloc_dot_rejects_lengths_beyond_the_maximum():
-    mpk = need_gpu()
-    lib = mpk._lib.load()
-    small = mpk.Vec.zeros(4, 128)
-    n = 2 ** 31  # one beyond MP_DOT_NOALLOC_MAX_N; rejected before any kernel runs
-    big = mpk._lib.MpVec(n, 128, n, small.t.data_ptr())
-    out = mpk.Vec.empty(1, 128)
-    st = lib.mp_dot_noalloc(big, big, out.c(), mpk._stream(None))
-    assert st == 1
-    assert b"maximum" in lib.mp_last_error()
+    # both entry points against the oracle's exact dot (one rounding)
+    for g, (x, y), (p, *_rest) in zip(got, vecs, cases):
+        want, st = oracle.dot(p, recs(x.planes()), recs(y.planes()))
+        assert st == oracle.OK
+        assert np.array_equal(np.ascontiguousarray(g.T)[0], want), p
