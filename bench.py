@@ -293,6 +293,29 @@ def oracle_solver_sample(iters=2000):
             "ms": round(dt * 1e3, 1), "ms_per_iter": round(dt * 1e3 / max(1, it), 3), "cores": 1}
 
 
+def oracle_cfg3_sample(m=100, p=256, iters=1):
+    """The oracle's BiCG and GPBiCG on the row-scaled 3-D system (m^3 grid,
+    n = 10^6, p = 256 bits), one thread: the set-up (exact residual, first
+    dots) plus `iters` iterations, timed together -- a full solve or 20
+    iterations would take minutes on the host (one later GPBiCG iteration
+    is about 20 s)."""
+    import oracle
+    from paper_1411_2377_gb300 import synth
+
+    rp, ci, v64 = synth.stencil3d(m, seed=2)
+    n = len(rp) - 1
+    vals = oracle.from_f64(p, v64)
+    b, _ = oracle.spmv(p, oracle.EXACT, rp, ci, vals, oracle.from_f64(p, np.ones(n)))
+    out = {"workload": f"stencil3d_{m}^3_pe50_rowscale1e20_p{p}", "cores": 1,
+           "sample": f"set-up + {iters} iteration(s) per solver"}
+    for name, fn in (("gpbicg", oracle.gpbicg), ("bicg", oracle.bicg)):
+        t0 = time.perf_counter()
+        _, it, st, _ = fn(p, oracle.ORDERED, rp, ci, vals, b, oracle.empty(p, n), 1e-30, 0.0, iters)
+        out[name] = {"iters": int(it), "status": int(st),
+                     "ms_setup_plus_iters": round((time.perf_counter() - t0) * 1e3, 1)}
+    return out
+
+
 def build_workload(n, precs, on_gpu=True):
     from paper_1411_2377_gb300 import synth
 
@@ -558,6 +581,7 @@ def run_native(args):
             cpu["solver"] = oracle_solver_sample()
             cpu["wide"] = oracle_wide_sample()
             cpu["wide_solver"] = oracle_wide_solver_sample()
+            cpu["solver_cfg3"] = oracle_cfg3_sample()
 
     if rank == 0:
         line = {

@@ -212,7 +212,7 @@ mp_status mp_vec_to_f64(mp_vec a, double* d, void* stream);
  * exact for up to 2^31 - 1 products). */
 #define MP_DOT_NOALLOC_MAX_N INT64_C(2147483647)
 /* Size of the device array that holds mp_dot_noalloc's scratch. */
-#define MP_DOT_NOALLOC_SCRATCH_BYTES 297088
+#define MP_DOT_NOALLOC_SCRATCH_BYTES 298112
 
 /* The exact dot product of mp_dot (bit-identical results) for callers that
  * cannot let a library allocate device memory: processes whose GPU memory is
@@ -241,23 +241,32 @@ typedef struct {
   double atol;
   int64_t maxit;     /* iteration limit ("NC" beyond it)                        */
   int32_t mode;      /* mp_mode used for the SpMVs                              */
-  int32_t poll_every;/* iterations between host checks of the device flags (>=1)*/
+  int32_t poll_every;/* p > 1024: iterations between host checks of the device
+                        flags (>= 1); the solvers at p <= 1024 and the batched
+                        solve iterate in a device-side loop and ignore it     */
   mp_vec history;    /* optional (data may be NULL): entry i-1 receives (r_i,r_i) */
   int32_t transpose; /* 1: solve A^T x = b (needs MP_CSR_TRANSPOSE), e.g. an
                         adjoint system; 0: A x = b                            */
-  int32_t reserved;  /* must be 0                                             */
+  int32_t time_limit_ms; /* 0: none.  > 0 (p <= 1024 and the batched solve):
+                        the solve ends with MP_ERR_TIMEOUT when an iteration
+                        finishes more than this many milliseconds after the
+                        set-up (device clock); x holds that iterate          */
 } mp_solve_opts;
 
 typedef struct {
   int64_t iters;  /* completed iterations                                   */
-  int32_t status; /* MP_OK (converged), MP_ERR_NOCONV or MP_ERR_BREAKDOWN   */
+  int32_t status; /* MP_OK (converged), MP_ERR_NOCONV, MP_ERR_BREAKDOWN or
+                     MP_ERR_TIMEOUT (time_limit_ms ran out)                 */
   double relres;  /* sqrt((r,r)/(r0,r0)) of the last iterate, as a double    */
   double ms;      /* wall time of the solve on the stream                    */
 } mp_solve_info;
 
 /* BiCG (Fig. 5 left).  x holds x0 on entry and the last iterate on return.
- * The iteration runs on the device; the host reads a few status bytes every
- * poll_every iterations.  Returns info->status.  Needs MP_CSR_TRANSPOSE. */
+ * The iteration runs on the device: after the first iteration the host
+ * launches one CUDA graph whose conditional while node replays an iteration
+ * until the device state says the solve has ended, then reads a few status
+ * bytes (p > 1024: a graph replayed poll_every times between host checks).
+ * Returns info->status.  Needs MP_CSR_TRANSPOSE. */
 mp_status mp_bicg(mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* opts,
                   mp_solve_info* info, void* stream);
 

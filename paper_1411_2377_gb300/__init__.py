@@ -299,15 +299,15 @@ def ewise(op: int, a: Vec, b: Vec, out: Vec | None = None, stream=None, sync=Tru
 
 
 def _solve(fn, name, A, b, x0, rtol, atol, maxit, mode, poll_every, history, stream,
-           transpose=False):
+           transpose=False, time_limit_ms=0):
     x = x0.clone() if x0 is not None else Vec.zeros(A.n, A.prec)
     hist = Vec.empty(max(maxit, 1), A.prec) if history else None
     opts = _lib.MpSolveOpts(float(rtol), float(atol), int(maxit), MODES[mode], int(poll_every),
                             hist.c() if hist is not None else _lib.MpVec(0, A.prec, 1, None),
-                            1 if transpose else 0, 0)
+                            1 if transpose else 0, int(time_limit_ms))
     info = _lib.MpSolveInfo()
     st = fn(A.h, b.c(), x.c(), ctypes.byref(opts), ctypes.byref(info), _stream(stream))
-    if st not in (0, _lib.MP_ERR_NOCONV, _lib.MP_ERR_BREAKDOWN):
+    if st not in (0, _lib.MP_ERR_NOCONV, _lib.MP_ERR_BREAKDOWN, _lib.MP_ERR_TIMEOUT):
         raise MPError(st, name)
     res = {"iters": int(info.iters), "status": int(info.status), "relres": float(info.relres),
            "ms": float(info.ms)}
@@ -317,35 +317,39 @@ def _solve(fn, name, A, b, x0, rtol, atol, maxit, mode, poll_every, history, str
 
 
 def bicg(A: CSR, b: Vec, x0: Vec | None = None, rtol=1e-30, atol=0.0, maxit=1000,
-         mode="ordered", poll_every=8, history=False, stream=None, transpose=False):
+         mode="ordered", poll_every=8, history=False, stream=None, transpose=False,
+         time_limit_ms=0):
     """BiCG (Fig. 5 left, K = I).  Returns (x, info dict).  transpose=True
     solves A^T x = b."""
     return _solve(_lib.load().mp_bicg, "mp_bicg", A, b, x0, rtol, atol, maxit, mode,
-                  poll_every, history, stream, transpose)
+                  poll_every, history, stream, transpose, time_limit_ms)
 
 
 def gpbicg(A: CSR, b: Vec, x0: Vec | None = None, rtol=1e-30, atol=0.0, maxit=1000,
-           mode="ordered", poll_every=8, history=False, stream=None, transpose=False):
+           mode="ordered", poll_every=8, history=False, stream=None, transpose=False,
+           time_limit_ms=0):
     """GPBiCG (Fig. 5 right).  Returns (x, info dict).  transpose=True solves
     A^T x = b (an adjoint system)."""
     return _solve(_lib.load().mp_gpbicg, "mp_gpbicg", A, b, x0, rtol, atol, maxit, mode,
-                  poll_every, history, stream, transpose)
+                  poll_every, history, stream, transpose, time_limit_ms)
 
 
 def cgs(A: CSR, b: Vec, x0: Vec | None = None, rtol=1e-30, atol=0.0, maxit=1000,
-        mode="ordered", poll_every=8, history=False, stream=None, transpose=False):
+        mode="ordered", poll_every=8, history=False, stream=None, transpose=False,
+        time_limit_ms=0):
     """CGS (Section 4's product-type method, textbook form, K = I).
     Returns (x, info dict)."""
     return _solve(_lib.load().mp_cgs, "mp_cgs", A, b, x0, rtol, atol, maxit, mode,
-                  poll_every, history, stream, transpose)
+                  poll_every, history, stream, transpose, time_limit_ms)
 
 
 def bicgstab(A: CSR, b: Vec, x0: Vec | None = None, rtol=1e-30, atol=0.0, maxit=1000,
-             mode="ordered", poll_every=8, history=False, stream=None, transpose=False):
+             mode="ordered", poll_every=8, history=False, stream=None, transpose=False,
+             time_limit_ms=0):
     """BiCGSTAB (Section 4's product-type method, textbook form, K = I).
     Returns (x, info dict)."""
     return _solve(_lib.load().mp_bicgstab, "mp_bicgstab", A, b, x0, rtol, atol, maxit, mode,
-                  poll_every, history, stream, transpose)
+                  poll_every, history, stream, transpose, time_limit_ms)
 
 
 class ILU0:
@@ -392,7 +396,7 @@ class ILU0:
 
 def bicgstab_ilu0(A: CSR, M: ILU0, b: Vec, x0: Vec | None = None, rtol=1e-30, atol=0.0,
                   maxit=1000, mode="ordered", poll_every=8, history=False, stream=None,
-                  side="left"):
+                  side="left", time_limit_ms=0):
     """BiCGSTAB preconditioned with ILU(0) K = LU.  side="left" (Section 4.2,
     the paper's form): BiCGSTAB on K^{-1}A x = K^{-1}b, and the stopping rule,
     relres and history take the preconditioned residual K^{-1}(b - A x);
@@ -405,7 +409,8 @@ def bicgstab_ilu0(A: CSR, M: ILU0, b: Vec, x0: Vec | None = None, rtol=1e-30, at
     def call(Ah, bc, xc, opts, info, st):
         return fn(Ah, M.h, bc, xc, opts, info, st)
 
-    return _solve(call, name, A, b, x0, rtol, atol, maxit, mode, poll_every, history, stream)
+    return _solve(call, name, A, b, x0, rtol, atol, maxit, mode, poll_every, history, stream,
+                  time_limit_ms=time_limit_ms)
 
 
 class Batch:
@@ -467,11 +472,11 @@ class Batch:
 
 
 def batch_gpbicg(B: Batch, b: Vec, x0: Vec | None = None, rtol=1e-30, atol=0.0, maxit=100_000,
-                 mode="ordered", poll_every=16, stream=None):
+                 mode="ordered", poll_every=16, stream=None, time_limit_ms=0):
     """GPBiCG on all instances of a Batch at once.  Returns (x, infos)."""
     x = x0.clone() if x0 is not None else Vec.zeros(B.n, B.prec)
     opts = _lib.MpSolveOpts(float(rtol), float(atol), int(maxit), MODES[mode], int(poll_every),
-                            _lib.MpVec(0, B.prec, 1, None), 0, 0)
+                            _lib.MpVec(0, B.prec, 1, None), 0, int(time_limit_ms))
     infos = (_lib.MpSolveInfo * B.k)()
     st = _lib.load().mp_batch_gpbicg(B.h, b.c(), x.c(), ctypes.byref(opts), infos,
                                      _stream(stream))

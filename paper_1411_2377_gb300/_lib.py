@@ -25,7 +25,7 @@ class MpSolveOpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("atol", ctypes.c_double),
                 ("maxit", ctypes.c_int64), ("mode", ctypes.c_int32),
                 ("poll_every", ctypes.c_int32), ("history", MpVec),
-                ("transpose", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("transpose", ctypes.c_int32), ("time_limit_ms", ctypes.c_int32)]
 
 
 class MpSolveInfo(ctypes.Structure):

@@ -11,7 +11,9 @@
 // updates look up each element's instance and leave finished instances
 // untouched.  Each instance follows exactly the steps of mp_gpbicg (the same
 // readings of Fig. 5), so its iterates equal a single-system solve bit for
-// bit.  One steady-state iteration is captured as a CUDA graph.
+// bit.  After the first iteration the whole batch iterates on the device in
+// one graph launch: a conditional while node replays one captured iteration
+// until the last instance finishes (or the time limit ends them).
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -89,6 +91,11 @@ struct BState {
   long long* iters;  // [K]
   long long maxit;
   int* ndone;        // one word: instances finished
+  int K;
+  int has_loop;      // set in the captured iteration: `loop` runs it on the device
+  cudaGraphConditionalHandle loop;
+  unsigned long long* t0;       // device time (ns) at the set-up
+  unsigned long long limit_ns;  // 0: no time limit
 };
 
 // Batched inner products: up to 5 pairs; out[j] is a K-vector of scalars.
@@ -293,10 +300,12 @@ __device__ __forceinline__ void sts(const Num<W>& a, uint64_t* S, int K, int j, 
   store<W>(a, S + (size_t)j * (W / 2 + 1) * K, K, k);
 }
 
+// Instance k ends; the thread that ends the last instance also ends the
+// device-side loop that replays the iteration (one call: no race).
 __device__ __forceinline__ void bfinish(const BState& b, int k, int status) {
   b.status[k] = status;
   b.done[k] = 1;
-  atomicAdd(b.ndone, 1);
+  if (atomicAdd(b.ndone, 1) + 1 == b.K && b.has_loop) cudaGraphSetConditional(b.loop, 0u);
 }
 
 #define INSTANCE_LOOP(k, K) \
@@ -322,6 +331,7 @@ __global__ void bsc_setup(BState b, uint64_t* S, int K, double rtol, double atol
     b.iters[k] = 0;
     b.status[k] = MP_OK;
     b.done[k] = 0;
+    if (k == 0) *b.t0 = device_ns();
     if (cmp<W>(rr0, thr) <= 0)
       bfinish(b, k, MP_OK);
     else if (b.maxit <= 0)
@@ -428,6 +438,8 @@ __global__ void bsc_check(BState b, uint64_t* S, int K) {
       bfinish(b, k, MP_ERR_NOCONV);
     else if (zero_e(rn.e))
       bfinish(b, k, MP_ERR_BREAKDOWN);
+    else if (b.limit_ns != 0 && device_ns() - *b.t0 > b.limit_ns)
+      bfinish(b, k, MP_ERR_TIMEOUT);
   }
 }
 
@@ -685,14 +697,32 @@ mp_status batch_solve_w(mp_batch_s* B, const mp_vec& b, const mp_vec& x,
   const int K = w.K;
   const int64_t N = w.N;
   const size_t cap = (size_t)BWin<W>::cap;
-  MPK_CUDA(cudaMallocAsync((void**)&w.vecs, sizeof(uint64_t) * 11 * (w.L + 1) * (size_t)N, st));
-  MPK_CUDA(cudaMallocAsync((void**)&w.S, sizeof(uint64_t) * NBS * (w.L + 1) * (size_t)K, st));
-  MPK_CUDA(cudaMallocAsync((void**)&w.words, sizeof(int) * (2 * (size_t)K + 1), st));
-  MPK_CUDA(cudaMallocAsync((void**)&w.iters, sizeof(long long) * (size_t)K, st));
-  MPK_CUDA(cudaMallocAsync((void**)&w.span, sizeof(long long) * 10 * (size_t)K, st));
-  MPK_CUDA(cudaMallocAsync((void**)&w.partials, sizeof(int64_t) * 5 * (size_t)B->nblk * cap, st));
+  auto free_all = [&]() {
+    cudaFreeAsync(w.vecs, st);
+    cudaFreeAsync(w.S, st);
+    cudaFreeAsync(w.words, st);
+    cudaFreeAsync(w.iters, st);
+    cudaFreeAsync(w.span, st);
+    cudaFreeAsync(w.partials, st);
+    cudaStreamSynchronize(st);
+  };
+  cudaError_t ca = cudaMallocAsync((void**)&w.vecs, sizeof(uint64_t) * 11 * (w.L + 1) * (size_t)N, st);
+  if (ca == cudaSuccess)
+    ca = cudaMallocAsync((void**)&w.S, sizeof(uint64_t) * NBS * (w.L + 1) * (size_t)K, st);
+  if (ca == cudaSuccess) ca = cudaMallocAsync((void**)&w.words, sizeof(int) * (2 * (size_t)K + 1), st);
+  if (ca == cudaSuccess)
+    ca = cudaMallocAsync((void**)&w.iters, sizeof(long long) * ((size_t)K + 1), st);
+  if (ca == cudaSuccess) ca = cudaMallocAsync((void**)&w.span, sizeof(long long) * 10 * (size_t)K, st);
+  if (ca == cudaSuccess)
+    ca = cudaMallocAsync((void**)&w.partials, sizeof(int64_t) * 5 * (size_t)B->nblk * cap, st);
+  if (ca != cudaSuccess) {
+    free_all();
+    return cuda_error(ca, "batch work memory");
+  }
   Seg g{K, B->nblk, B->d_inst, B->d_blk_inst, B->d_blk_lo, B->d_blk_hi, B->d_first, B->d_count};
-  BState bs{w.words, w.words + K, w.iters, (long long)o.maxit, w.words + 2 * K};
+  BState bs{w.words, w.words + K, w.iters, (long long)o.maxit, w.words + 2 * K, K, 0, {},
+             reinterpret_cast<unsigned long long*>(w.iters + K),
+             (unsigned long long)o.time_limit_ms * 1000000ull};
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -702,7 +732,8 @@ mp_status batch_solve_w(mp_batch_s* B, const mp_vec& b, const mp_vec& x,
   cudaGraphExec_t exec = nullptr;
   int ndone = 0;
   do {
-    MPK_CUDA(cudaMemsetAsync(w.words, 0, sizeof(int) * (2 * (size_t)K + 1), st));
+    cudaError_t cez = cudaMemsetAsync(w.words, 0, sizeof(int) * (2 * (size_t)K + 1), st);
+    if (cez != cudaSuccess) { r = cuda_error(cez, "batch state reset"); break; }
     bspan_reset<<<egrid(5 * K), 128, 0, st>>>(w.span, w.span + 5 * (size_t)K, 5 * (int64_t)K);
     count_launch();
     const int eg = egrid(N);
@@ -725,31 +756,47 @@ mp_status batch_solve_w(mp_batch_s* B, const mp_vec& b, const mp_vec& x,
     bsc_setup<W><<<(K + 127) / 128, 128, 0, st>>>(bs, w.S, K, o.rtol, o.atol);
     count_launch();
     if ((r = b_iteration<W>(B, w, g, bs, x, o.mode, true, st)) != MP_OK) break;
-    MPK_CUDA(cudaMemcpyAsync(&ndone, bs.ndone, sizeof ndone, cudaMemcpyDeviceToHost, st));
-    MPK_CUDA(cudaStreamSynchronize(st));
+    cudaError_t cer = cudaMemcpyAsync(&ndone, bs.ndone, sizeof ndone, cudaMemcpyDeviceToHost, st);
+    if (cer == cudaSuccess) cer = cudaStreamSynchronize(st);
+    if (cer != cudaSuccess) { r = cuda_error(cer, "reading the batch state"); break; }
     if (ndone >= K) break;
-    cudaError_t ce = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
-    if (ce != cudaSuccess) { r = cuda_error(ce, "cudaStreamBeginCapture"); break; }
+    // The remaining iterations run on the device in one graph launch: a
+    // conditional while node whose body is one captured iteration; the
+    // instance that finishes last ends the loop (bfinish).
+    cudaGraphConditionalHandle loop{};
+    cudaGraphNodeParams cp{};
+    cudaGraphNode_t node = nullptr;
+    cudaError_t ce = cudaGraphCreate(&graph, 0);
+    if (ce == cudaSuccess)
+      ce = cudaGraphConditionalHandleCreate(&loop, graph, 1u, cudaGraphCondAssignDefault);
+    if (ce == cudaSuccess) {
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = loop;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      ce = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+    }
+    if (ce != cudaSuccess) { r = cuda_error(ce, "building the batched iteration loop"); break; }
+    cudaGraph_t bodyg = cp.conditional.phGraph_out[0];
+    BState lbs = bs;
+    lbs.has_loop = 1;
+    lbs.loop = loop;
+    ce = cudaStreamBeginCaptureToGraph(st, bodyg, nullptr, nullptr, 0,
+                                       cudaStreamCaptureModeRelaxed);
+    if (ce != cudaSuccess) { r = cuda_error(ce, "cudaStreamBeginCaptureToGraph"); break; }
     const int64_t before = mp_launch_count(0);
-    mp_status rb = b_iteration<W>(B, w, g, bs, x, o.mode, false, st);
+    mp_status rb = b_iteration<W>(B, w, g, lbs, x, o.mode, false, st);
     const int64_t per = mp_launch_count(0) - before;
-    ce = cudaStreamEndCapture(st, &graph);
+    ce = cudaStreamEndCapture(st, &bodyg);
+    count_launch(-(int)per);
     if (rb != MP_OK) { r = rb; break; }
     if (ce != cudaSuccess) { r = cuda_error(ce, "cudaStreamEndCapture"); break; }
-    count_launch(-(int)per);
     ce = cudaGraphInstantiate(&exec, graph, 0);
     if (ce != cudaSuccess) { r = cuda_error(ce, "cudaGraphInstantiate"); break; }
-    const int poll = o.poll_every > 0 ? o.poll_every : 8;
-    while (true) {
-      for (int it = 0; it < poll && ce == cudaSuccess; ++it) {
-        ce = cudaGraphLaunch(exec, st);
-        count_launch((int)per);
-      }
-      if (ce == cudaSuccess) ce = cudaMemcpyAsync(&ndone, bs.ndone, sizeof ndone, cudaMemcpyDeviceToHost, st);
-      if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
-      if (ce != cudaSuccess) { r = cuda_error(ce, "batched graph"); break; }
-      if (ndone >= K) break;
-    }
+    ce = cudaGraphLaunch(exec, st);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(&ndone, bs.ndone, sizeof ndone, cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) { r = cuda_error(ce, "batched iteration loop"); break; }
   } while (false);
   if (exec) cudaGraphExecDestroy(exec);
   if (graph) cudaGraphDestroy(graph);
@@ -772,13 +819,7 @@ mp_status batch_solve_w(mp_batch_s* B, const mp_vec& b, const mp_vec& x,
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  cudaFreeAsync(w.vecs, st);
-  cudaFreeAsync(w.S, st);
-  cudaFreeAsync(w.words, st);
-  cudaFreeAsync(w.iters, st);
-  cudaFreeAsync(w.span, st);
-  cudaFreeAsync(w.partials, st);
-  cudaStreamSynchronize(st);
+  free_all();
   return r;
 }
 

@@ -183,13 +183,22 @@ __device__ int64_t wdiv(const uint32_t* Ma, int64_t ea, const uint32_t* Mb, int6
   for (int k = lane; k < NQ; k += 32) Q[k] = 0u;
   __syncwarp();
   const uint32_t v1 = Mb[n - 1], v2 = Mb[n - 2];
+  const uint32_t vinv = (uint32_t)(~uint64_t(0) / v1);  // div2by1's reciprocal of v1
   for (int j = m; j >= 0; --j) {
-    const uint64_t num = ((uint64_t)U[j + n] << 32) | U[j + n - 1];
-    uint64_t qh = num / v1, rh = num % v1;
-    while (qh >= (1ull << 32) || qh * v2 > ((rh << 32) | U[j + n - 2])) {
+    // estimate from the top two words (the top word never exceeds v1; when
+    // equal the estimate is 2^32 - 1 with remainder U[j+n-1] + v1)
+    uint64_t qh, rh;
+    if (U[j + n] >= v1) {
+      qh = 0xffffffffu;
+      rh = (uint64_t)U[j + n - 1] + v1;
+    } else {
+      uint32_t rr;
+      qh = div2by1(U[j + n], U[j + n - 1], v1, vinv, rr);
+      rh = rr;
+    }
+    while ((rh >> 32) == 0u && qh * v2 > ((rh << 32) | U[j + n - 2])) {
       qh -= 1;
       rh += v1;
-      if (rh >= (1ull << 32)) break;
     }
     for (int k = lane; k <= n; k += 32) {
       const uint64_t t0 = k < n ? qh * Mb[k] : 0ull, t1 = k > 0 ? qh * Mb[k - 1] : 0ull;

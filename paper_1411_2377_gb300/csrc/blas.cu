@@ -1,228 +1,16 @@
-// blas.cu -- exact dot products, axpy, elementwise operations, conversions.
-//
-// Exact dot products (the inner products of Fig. 5) take three kernels:
-//  1. span: min/max of e_x + e_y over the nonzero pairs (warp reduction, one
-//     64-bit atomicMin/atomicMax per warp: min and max are order-free);
-//  2. accumulate: each thread adds the exact 2p-bit products of its pairs,
-//     shifted onto the 32-bit digit grid anchored at Emin, into its own
-//     window of 64-bit signed counters in shared memory (digit-major, so a
-//     warp's accesses hit 32 banks; no atomics, no carries); the block then
-//     sums its threads' windows digit by digit into one partial per block,
-//     stored digit-major across blocks;
-//  3. finalize: one block per dot sums the partials per digit (a warp per
-//     digit, lanes over blocks; integer sums: any order gives the same
-//     bits), resolves carries and rounds once.
-// A dot whose span exceeds the per-thread windows takes, inside step 2, one
-// block-wide window of the full span cap filled with shared-memory atomics.  Up to five dots over the same index
-// range run in one pass, so GPBiCG's mu_1..mu_5 read y, v and t once.
+// blas.cu -- exact dot products (dot.cuh: two kernels per group of up to
+// five dots), axpy, elementwise operations, conversions.
 #include <climits>
 #include <mutex>
 
+#include "dot.cuh"
 #include "internal.h"
 #include "mpdev.cuh"
 
 namespace mpk {
 namespace {
 
-constexpr int kDotThreads = 128;
-constexpr int kDotWarps = kDotThreads / 32;
-constexpr int kDotFastSpan = 1024;
-
-template <int W>
-struct DotWin {
-  static constexpr int fast = (kDotFastSpan + 64 * W + 96) / 32 + 1;
-  static constexpr int cap = (SPAN_CAP + 64 * W + 96) / 32 + 1;
-};
-
-__host__ __device__ inline int dot_digits(int64_t span, int W) {
-  return (int)((span + 64 * W + 96) / 32) + 1;
-}
-
-struct DotDev {
-  int k;
-  int64_t n;
-  const uint64_t* x[5];
-  const uint64_t* y[5];
-  int64_t ldx[5], ldy[5];
-  uint64_t* out[5];
-  int64_t out_ld[5];
-};
-
-struct DotScratch {
-  long long* emin;  // [5]
-  long long* emax;  // [5]
-  int64_t* partials;  // [5][cap][nblocks]: digit-major per dot
-  int nblocks;
-};
-
-int sm_count() {
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  return sms > 0 ? sms : 1;
-}
-
-int dot_blocks(int64_t n) {
-  int64_t b = (n + kDotThreads - 1) / kDotThreads;
-  const int64_t lim = (int64_t)sm_count() * 4;
-  if (b > lim) b = lim;
-  if (b < 1) b = 1;
-  return (int)b;
-}
-
-template <int W>
-__global__ void __launch_bounds__(kDotThreads) dot_span_kernel(const DotDev a, long long* emin,
-                                                               long long* emax,
-                                                               const int* __restrict__ gate) {
-  if (gate && *gate) return;
-  const int lane = threadIdx.x & 31;
-  for (int j = 0; j < a.k; ++j) {
-    long long lo = LLONG_MAX, hi = LLONG_MIN;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-      int64_t ex, ey;
-      uint32_t sx, sy;
-      unpack_head(__ldg(a.x[j] + i), ex, sx);
-      unpack_head(__ldg(a.y[j] + i), ey, sy);
-      if (zero_e(ex) || zero_e(ey)) continue;
-      lo = min(lo, (long long)(ex + ey));
-      hi = max(hi, (long long)(ex + ey));
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-      hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-    }
-    if (lane == 0 && lo <= hi) {
-      atomicMin(emin + j, lo);
-      atomicMax(emax + j, hi);
-    }
-  }
-}
-
-// smem: per thread FAST 64-bit counters, digit-major ([FAST][threads]).
-template <int W>
-__host__ __device__ constexpr size_t dot_smem(int) {
-  return (size_t)DotWin<W>::fast * kDotThreads * 8;
-}
-
-__device__ __forceinline__ int64_t warp_sum64(int64_t t) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-  return t;
-}
-
-template <int W>
-__global__ void __launch_bounds__(kDotThreads) dot_accum_kernel(const DotDev a, DotScratch s,
-                                                                const int* __restrict__ gate) {
-  extern __shared__ int64_t dsm[];
-  __shared__ int64_t acc[DotWin<W>::cap];  // the block-wide window of a wide span
-  if (gate && *gate) return;
-  constexpr int CAP = DotWin<W>::cap;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int64_t* c = dsm + threadIdx.x;
-  for (int j = 0; j < a.k; ++j) {
-    const long long lo = s.emin[j], hi = s.emax[j];
-    if (!(lo <= hi && hi - lo <= SPAN_CAP)) continue;  // block-uniform
-    const int nd = dot_digits(hi - lo, W);
-    if (hi - lo > kDotFastSpan) {
-      // a span beyond the per-thread windows: one block-wide window with
-      // shared-memory atomics (rare: the solvers' vectors stay well inside)
-      for (int d = threadIdx.x; d < nd; d += kDotThreads) acc[d] = 0;
-      __syncthreads();
-      for (int64_t i = blockIdx.x * (int64_t)kDotThreads + threadIdx.x; i < a.n;
-           i += (int64_t)gridDim.x * kDotThreads) {
-        Num<W> x, y;
-        load<W>(x, a.x[j], a.ldx[j], i);
-        load<W>(y, a.y[j], a.ldy[j], i);
-        if (zero_e(x.e) || zero_e(y.e)) continue;
-        uint32_t P[2 * W], D[2 * W + 1];
-        mul_full<W>(x.m, y.m, P);
-        const int64_t off = x.e + y.e - lo;
-        shifted_digits<W>(P, (uint32_t)(off & 31), D);
-        const bool ng = (x.s ^ y.s) != 0;
-        for (int k = 0; k <= 2 * W; ++k) {
-          const int64_t v = (int64_t)D[k];
-          atomicAdd((unsigned long long*)&acc[(off >> 5) + k], (unsigned long long)(ng ? -v : v));
-        }
-      }
-      __syncthreads();
-      int64_t* part = s.partials + (size_t)j * CAP * s.nblocks;
-      for (int d = threadIdx.x; d < nd; d += kDotThreads) part[(size_t)d * s.nblocks + blockIdx.x] = acc[d];
-      __syncthreads();
-      continue;
-    }
-    for (int d = 0; d < nd; ++d) c[d * kDotThreads] = 0;
-    for (int64_t i = blockIdx.x * (int64_t)kDotThreads + threadIdx.x; i < a.n;
-         i += (int64_t)gridDim.x * kDotThreads) {
-      Num<W> x, y;
-      load<W>(x, a.x[j], a.ldx[j], i);
-      load<W>(y, a.y[j], a.ldy[j], i);
-      if (zero_e(x.e) || zero_e(y.e)) continue;
-      uint32_t P[2 * W];
-      if (W >= 16)
-        mul_full_ilp<W>(x.m, y.m, P);
-      else
-        mul_full<W>(x.m, y.m, P);
-      add_term<W>(c, kDotThreads, P, x.e + y.e - lo, x.s ^ y.s);
-    }
-    __syncthreads();
-    int64_t* part = s.partials + (size_t)j * CAP * s.nblocks;
-    for (int d = warp; d < nd; d += kDotWarps) {
-      int64_t t = 0;
-#pragma unroll
-      for (int u = 0; u < kDotThreads / 32; ++u) t += dsm[d * kDotThreads + u * 32 + lane];
-      t = warp_sum64(t);
-      if (lane == 0) part[(size_t)d * s.nblocks + blockIdx.x] = t;
-    }
-    __syncthreads();
-  }
-}
-
-// One block per dot: sum partials, resolve carries, round once.  Resets the
-// span slots for the next use.
-template <int W>
-__global__ void __launch_bounds__(256) dot_finalize_kernel(const DotDev a, DotScratch s,
-                                                           int* __restrict__ status,
-                                                           const int* __restrict__ gate) {
-  __shared__ int64_t sum[DotWin<W>::cap];
-  if (gate && *gate) return;
-  const int j = blockIdx.x;
-  const long long lo = s.emin[j], hi = s.emax[j];
-  Num<W> r;
-  set_zero(r, 0u);
-  if (lo <= hi && hi - lo <= SPAN_CAP) {
-    const int nd = dot_digits(hi - lo, W);
-    const int64_t* part = s.partials + (size_t)j * DotWin<W>::cap * s.nblocks;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (int d = warp; d < nd; d += nwarps) {
-      int64_t t = 0;
-      for (int b = lane; b < s.nblocks; b += 32) t += part[(size_t)d * s.nblocks + b];
-      t = warp_sum64(t);
-      if (lane == 0) sum[d] = t;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const uint32_t negative = resolve_digits(sum, 1, nd);
-      if (negative) negate_words(sum, 1, nd);
-      round_words<W>(sum, 1, nd, (int64_t)lo - 64 * W, negative, r);
-    }
-  } else if (lo <= hi && threadIdx.x == 0 && status) {
-    atomicCAS(status, 0, (int)MP_ERR_SPAN);
-  }
-  if (threadIdx.x == 0) {
-    store<W>(r, a.out[j], a.out_ld[j], 0);
-    s.emin[j] = LLONG_MAX;
-    s.emax[j] = LLONG_MIN;
-  }
-}
-
-__global__ void reset_span_slots(long long* emin, long long* emax) {
-  if (threadIdx.x < 5) {
-    emin[threadIdx.x] = LLONG_MAX;
-    emax[threadIdx.x] = LLONG_MIN;
-  }
-}
+int sm_count() { return dot_sm_count(); }
 
 template <int W>
 mp_status dot_w(const DotArgs& args, void* scratch, const int* gate, cudaStream_t st) {
@@ -237,24 +25,9 @@ mp_status dot_w(const DotArgs& args, void* scratch, const int* gate, cudaStream_
     a.out[j] = args.out[j];
     a.out_ld[j] = args.out_ld[j];
   }
-  DotScratch s;
-  s.emin = static_cast<long long*>(scratch);
-  s.emax = s.emin + 5;
-  s.partials = reinterpret_cast<int64_t*>(s.emin + 16);
-  s.nblocks = dot_blocks(args.n);
   int* status = status_word();
   if (!status) return set_error(MP_ERR_CUDA, "status word unavailable");
-  const size_t smem = dot_smem<W>(a.k);
-  MPK_CUDA(cudaFuncSetAttribute(dot_accum_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem));
-  // streamed operands: shared memory for the windows matters more than L1
-  MPK_CUDA(cudaFuncSetAttribute(dot_accum_kernel<W>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                (int)cudaSharedmemCarveoutMaxShared));
-  dot_span_kernel<W><<<s.nblocks, kDotThreads, 0, st>>>(a, s.emin, s.emax, gate);
-  dot_accum_kernel<W><<<s.nblocks, kDotThreads, smem, st>>>(a, s, gate);
-  dot_finalize_kernel<W><<<a.k, 256, 0, st>>>(a, s, status, gate);
-  count_launch(3);
-  return launch_check("dot kernels");
+  return dot_launch<W>(a, scratch, dot_blocks(args.n), status, gate, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -385,10 +158,14 @@ __global__ void to_f64_kernel(const uint64_t* __restrict__ a, int64_t n, int64_t
 }  // namespace
 
 size_t dot_scratch_bytes(int prec, int k) {
-  const int W = prec / 32;
-  const int cap = (SPAN_CAP + 64 * W + 96) / 32 + 1;
   const int nb = dot_blocks(int64_t(1) << 40);  // the largest grid
-  return 16 * sizeof(long long) + (size_t)(k < 1 ? 1 : k) * nb * cap * sizeof(int64_t);
+  const int kk = k < 1 ? 1 : k;
+  switch (prec) {
+    case 128: return dot_scratch_size<4>(kk, nb);
+    case 256: return dot_scratch_size<8>(kk, nb);
+    case 512: return dot_scratch_size<16>(kk, nb);
+    default: return dot_scratch_size<32>(kk, nb);
+  }
 }
 
 mp_status launch_dot(int prec, const DotArgs& a, void* scratch, const int* gate,
@@ -400,12 +177,11 @@ mp_status launch_dot(int prec, const DotArgs& a, void* scratch, const int* gate,
   });
 }
 
-// Initialises the span slots at the head of a dot scratch buffer.
+// Zeroes the head of a dot scratch buffer (the finalize's arrival counter).
 mp_status init_dot_scratch(void* scratch, cudaStream_t st) {
-  long long* e = static_cast<long long*>(scratch);
-  reset_span_slots<<<1, 32, 0, st>>>(e, e + 5);
+  reset_dot_head<<<1, 32, 0, st>>>(static_cast<long long*>(scratch));
   count_launch();
-  return launch_check("reset_span_slots");
+  return launch_check("reset_dot_head");
 }
 
 }  // namespace mpk
@@ -560,9 +336,7 @@ namespace mpk {
 namespace {
 
 constexpr int kNoAllocBlocks = 64;  // grid of the variant (grid-stride loops cover any n)
-constexpr size_t kNoAllocSpanBytes = 16 * sizeof(long long);
-constexpr size_t kNoAllocBytes =
-    kNoAllocSpanBytes + (size_t)kNoAllocBlocks * DotWin<32>::cap * sizeof(int64_t);
+constexpr size_t kNoAllocBytes = dot_scratch_size<32>(1, kNoAllocBlocks);
 
 static_assert(kNoAllocBytes == MP_DOT_NOALLOC_SCRATCH_BYTES, "scratch size stated in mpkrylov.h");
 
@@ -590,27 +364,17 @@ mp_status noalloc_scratch(void** out) {
 
 template <int W>
 mp_status dot_noalloc_w(const DotDev& a, void* scratch, int* status, cudaStream_t st) {
-  DotScratch s;
-  s.emin = static_cast<long long*>(scratch);
-  s.emax = s.emin + 5;
-  s.partials = reinterpret_cast<int64_t*>(static_cast<unsigned char*>(scratch) + kNoAllocSpanBytes);
-  int64_t b = (a.n + kDotThreads - 1) / kDotThreads;
-  s.nblocks = (int)(b < 1 ? 1 : (b > kNoAllocBlocks ? kNoAllocBlocks : b));
-  const size_t need = kNoAllocSpanBytes + (size_t)s.nblocks * DotWin<W>::cap * sizeof(int64_t);
+  const int64_t b = (a.n + kDotThreads - 1) / kDotThreads;
+  const int nb = (int)(b < 1 ? 1 : (b > kNoAllocBlocks ? kNoAllocBlocks : b));
+  const size_t need = dot_scratch_size<W>(1, nb);
   if (need > kNoAllocBytes)
     return set_error(MP_ERR_ARG, "mp_dot_noalloc needs %zu scratch bytes, the array holds %zu",
                      need, kNoAllocBytes);
-  const size_t smem = dot_smem<W>(1);
-  MPK_CUDA(cudaFuncSetAttribute(dot_accum_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem));
-  // The array keeps the previous call's contents: the span slots must start
-  // from (+inf, -inf); the partials are written before they are read.
-  reset_span_slots<<<1, 32, 0, st>>>(s.emin, s.emax);
-  dot_span_kernel<W><<<s.nblocks, kDotThreads, 0, st>>>(a, s.emin, s.emax, nullptr);
-  dot_accum_kernel<W><<<s.nblocks, kDotThreads, smem, st>>>(a, s, nullptr);
-  dot_finalize_kernel<W><<<1, 256, 0, st>>>(a, s, status, nullptr);
-  count_launch(4);
-  return launch_check("mp_dot_noalloc kernels");
+  // The array keeps the previous call's contents.  Nothing needs clearing:
+  // every block writes its exponent range before the finalize reads it, the
+  // finalize reads only the partial digits the blocks wrote in this call,
+  // and this form runs no step after the dot (its arrival counter is unused).
+  return dot_launch<W>(a, scratch, nb, status, nullptr, st);
 }
 
 }  // namespace

@@ -1,0 +1,331 @@
+// dot.cuh -- exact dot products (the inner products (.,.) of Fig. 5) in two
+// kernels, shared by mp_dot, mp_dot_noalloc and the solvers.
+//
+//  1. accumulate: each block first finds the exponent range [lo_b, hi_b] of
+//     e_x + e_y over its own nonzero pairs, anchors its digit grid at
+//     a_b = lo_b rounded down to a multiple of 32, and adds the exact 2p-bit
+//     products into per-thread windows of 64-bit signed counters in shared
+//     memory (digit-major, so a warp's accesses hit 32 banks; no atomics, no
+//     carries); the block sums its threads' windows digit by digit into one
+//     partial per block (digit-major across blocks).  A block whose own span
+//     exceeds the per-thread windows takes one block-wide window with
+//     shared-memory atomics instead.
+//  2. finalize: one block per dot takes the global range (min of the lo_b,
+//     max of the hi_b: the span cap is checked on it), anchors at A = lo
+//     rounded down to a multiple of 32, sums the partials per global digit
+//     (block b's digit d is global digit d + (a_b - A)/32: whole digits, so
+//     the sum is exact integer addition in any order), resolves carries and
+//     rounds once.
+// The last finalize block to finish (an arrival counter; nothing waits) can
+// run a caller-supplied step on the results -- the solvers' scalar
+// recurrences -- so that a solver iteration needs no separate scalar launch.
+// Up to five dots over the same index range run in one pass.
+#pragma once
+#include <climits>
+#include <type_traits>
+
+#include "internal.h"
+#include "mpdev.cuh"
+
+namespace mpk {
+
+constexpr int kDotThreads = 128;
+constexpr int kDotWarps = kDotThreads / 32;
+constexpr int kDotFastSpan = 1024;    // span (bits) the per-thread windows cover
+constexpr int kDotMaxBlocks = 1024;   // grid bound of the accumulate kernel
+
+__host__ __device__ inline int dot_digits(int64_t span, int W) {
+  return (int)((span + 64 * W + 96) / 32) + 1;
+}
+
+template <int W>
+struct DotWin {
+  static constexpr int fast = (kDotFastSpan + 64 * W + 96) / 32 + 1;
+  // a range up to the span cap, measured from its anchor (up to 31 bits lower)
+  static constexpr int cap = (SPAN_CAP + 31 + 64 * W + 96) / 32 + 1;
+};
+
+struct DotDev {
+  int k;
+  int64_t n;
+  const uint64_t* x[5];
+  const uint64_t* y[5];
+  int64_t ldx[5], ldy[5];
+  uint64_t* out[5];
+  int64_t out_ld[5];
+};
+
+// Scratch layout: a 16-word head (word 0: the finalize's arrival counter),
+// then per (dot, block) the range lo/hi, then the partials [k][cap][nblocks].
+constexpr int kDotHeadWords = 16;
+
+struct DotScratch {
+  int* arrive;
+  long long* lo;      // [5][nblocks]
+  long long* hi;      // [5][nblocks]
+  int64_t* partials;  // [5][cap][nblocks]
+  int nblocks;
+};
+
+template <int W>
+constexpr size_t dot_scratch_size(int k, int nblocks) {
+  return (size_t)kDotHeadWords * 8 + (size_t)2 * k * nblocks * 8 +
+         (size_t)k * nblocks * DotWin<W>::cap * 8;
+}
+
+template <int W>
+inline DotScratch dot_scratch_view(void* base, int k, int nblocks) {
+  DotScratch s;
+  long long* h = static_cast<long long*>(base);
+  s.arrive = reinterpret_cast<int*>(h);
+  s.lo = h + kDotHeadWords;
+  s.hi = s.lo + (size_t)k * nblocks;
+  s.partials = reinterpret_cast<int64_t*>(s.hi + (size_t)k * nblocks);
+  s.nblocks = nblocks;
+  return s;
+}
+
+__device__ __forceinline__ int64_t warp_sum64(int64_t t) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  return t;
+}
+
+// smem of the accumulate kernel: per thread `fast` 64-bit counters,
+// digit-major ([fast][threads]).
+template <int W>
+__host__ __device__ constexpr size_t dot_smem() {
+  return (size_t)DotWin<W>::fast * kDotThreads * 8;
+}
+
+// Block-wide min and max (every thread returns them).
+__device__ __forceinline__ void block_minmax(long long& lo, long long& hi, long long* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  __syncthreads();  // red may hold a previous call's values still being read
+  if (lane == 0) {
+    red[warp] = lo;
+    red[32 + warp] = hi;
+  }
+  __syncthreads();
+  lo = red[0];
+  hi = red[32];
+  for (int w = 1; w < nw; ++w) {
+    lo = min(lo, red[w]);
+    hi = max(hi, red[32 + w]);
+  }
+}
+
+template <int W>
+__global__ void __launch_bounds__(kDotThreads) dot_accum_kernel(const DotDev a, DotScratch s,
+                                                                const int* __restrict__ gate) {
+  extern __shared__ int64_t dsm[];
+  __shared__ int64_t acc[DotWin<W>::cap];  // the block-wide window of a wide block span
+  __shared__ long long red[64];
+  if (gate && *gate) return;
+  constexpr int CAP = DotWin<W>::cap;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nb = s.nblocks;
+  int64_t* c = dsm + threadIdx.x;
+  for (int j = 0; j < a.k; ++j) {
+    // this block's exponent range of the nonzero pairs (heads only)
+    long long lo = LLONG_MAX, hi = LLONG_MIN;
+    for (int64_t i = blockIdx.x * (int64_t)kDotThreads + threadIdx.x; i < a.n;
+         i += (int64_t)gridDim.x * kDotThreads) {
+      int64_t ex, ey;
+      uint32_t sx, sy;
+      unpack_head(__ldg(a.x[j] + i), ex, sx);
+      unpack_head(__ldg(a.y[j] + i), ey, sy);
+      if (zero_e(ex) || zero_e(ey)) continue;
+      lo = min(lo, (long long)(ex + ey));
+      hi = max(hi, (long long)(ex + ey));
+    }
+    block_minmax(lo, hi, red);
+    if (threadIdx.x == 0) {
+      s.lo[(size_t)j * nb + blockIdx.x] = lo;
+      s.hi[(size_t)j * nb + blockIdx.x] = hi;
+    }
+    // nothing to add, or a range the finalize rejects (the global span is
+    // at least this block's): no partial is written or read
+    if (!(lo <= hi && hi - lo <= SPAN_CAP)) continue;  // block-uniform
+    const long long anchor = (lo >> 5) * 32;            // lo rounded down to a multiple of 32
+    const int nd = dot_digits(hi - anchor, W);
+    int64_t* part = s.partials + (size_t)j * CAP * nb;
+    if (hi - anchor > kDotFastSpan) {
+      // a span beyond the per-thread windows: one block-wide window with
+      // shared-memory atomics (rare: the solvers' vectors stay well inside)
+      for (int d = threadIdx.x; d < nd; d += kDotThreads) acc[d] = 0;
+      __syncthreads();
+      for (int64_t i = blockIdx.x * (int64_t)kDotThreads + threadIdx.x; i < a.n;
+           i += (int64_t)gridDim.x * kDotThreads) {
+        Num<W> x, y;
+        load<W>(x, a.x[j], a.ldx[j], i);
+        load<W>(y, a.y[j], a.ldy[j], i);
+        if (zero_e(x.e) || zero_e(y.e)) continue;
+        uint32_t P[2 * W], D[2 * W + 1];
+        mul_full<W>(x.m, y.m, P);
+        const int64_t off = x.e + y.e - anchor;
+        shifted_digits<W>(P, (uint32_t)(off & 31), D);
+        const bool ng = (x.s ^ y.s) != 0;
+        for (int k = 0; k <= 2 * W; ++k) {
+          const int64_t v = (int64_t)D[k];
+          atomicAdd((unsigned long long*)&acc[(off >> 5) + k], (unsigned long long)(ng ? -v : v));
+        }
+      }
+      __syncthreads();
+      for (int d = threadIdx.x; d < nd; d += kDotThreads) part[(size_t)d * nb + blockIdx.x] = acc[d];
+      __syncthreads();
+      continue;
+    }
+    for (int d = 0; d < nd; ++d) c[d * kDotThreads] = 0;
+    for (int64_t i = blockIdx.x * (int64_t)kDotThreads + threadIdx.x; i < a.n;
+         i += (int64_t)gridDim.x * kDotThreads) {
+      Num<W> x, y;
+      load<W>(x, a.x[j], a.ldx[j], i);
+      load<W>(y, a.y[j], a.ldy[j], i);
+      if (zero_e(x.e) || zero_e(y.e)) continue;
+      uint32_t P[2 * W];
+      if (W >= 16)
+        mul_full_ilp<W>(x.m, y.m, P);
+      else
+        mul_full<W>(x.m, y.m, P);
+      add_term<W>(c, kDotThreads, P, x.e + y.e - anchor, x.s ^ y.s);
+    }
+    __syncthreads();
+    for (int d = warp; d < nd; d += kDotWarps) {
+      int64_t t = 0;
+#pragma unroll
+      for (int u = 0; u < kDotThreads / 32; ++u) t += dsm[d * kDotThreads + u * 32 + lane];
+      t = warp_sum64(t);
+      if (lane == 0) part[(size_t)d * nb + blockIdx.x] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// The finalize kernel's default: no step after the dots.
+struct NoPost {
+  __device__ void operator()() const {}
+};
+
+// One block per dot: the global range from the blocks' ranges, the span cap,
+// the partials summed per global digit, carries resolved, one rounding.  The
+// block that finishes last then runs post() on thread 0 (the results of all
+// blocks are visible to it: each block fences its result before it counts
+// itself in; post() must read them with loads that bypass L1).
+template <int W, class Post = NoPost>
+__global__ void __launch_bounds__(256) dot_finalize_kernel(const DotDev a, DotScratch s,
+                                                           int* __restrict__ status,
+                                                           const int* __restrict__ gate,
+                                                           Post post) {
+  constexpr int CAP = DotWin<W>::cap;
+  __shared__ int64_t sum[CAP];
+  __shared__ int off_of[kDotMaxBlocks];  // block b's digit offset, -1: no partial
+  __shared__ int nd_of[kDotMaxBlocks];
+  __shared__ long long red[64];
+  if (gate && *gate) return;
+  const int j = blockIdx.x, nb = s.nblocks;
+  const long long* blo = s.lo + (size_t)j * nb;
+  const long long* bhi = s.hi + (size_t)j * nb;
+  long long lo = LLONG_MAX, hi = LLONG_MIN;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    lo = min(lo, blo[b]);
+    hi = max(hi, bhi[b]);
+  }
+  block_minmax(lo, hi, red);
+  Num<W> r;
+  set_zero(r, 0u);
+  if (lo <= hi && hi - lo <= SPAN_CAP) {
+    const long long A = (lo >> 5) * 32;
+    const int nd = dot_digits(hi - A, W);
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+      const long long l = blo[b], h = bhi[b];
+      if (l <= h) {
+        const long long ab = (l >> 5) * 32;
+        off_of[b] = (int)((ab - A) >> 5);
+        nd_of[b] = dot_digits(h - ab, W);
+      } else {
+        off_of[b] = -1;
+        nd_of[b] = 0;
+      }
+    }
+    __syncthreads();
+    const int64_t* part = s.partials + (size_t)j * CAP * nb;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int g = warp; g < nd; g += nwarps) {
+      int64_t t = 0;
+      for (int b = lane; b < nb; b += 32) {
+        const int d = g - off_of[b];
+        if (off_of[b] >= 0 && d >= 0 && d < nd_of[b]) t += part[(size_t)d * nb + b];
+      }
+      t = warp_sum64(t);
+      if (lane == 0) sum[g] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const uint32_t negative = resolve_digits(sum, 1, nd);
+      if (negative) negate_words(sum, 1, nd);
+      round_words<W>(sum, 1, nd, (int64_t)A - 64 * W, negative, r);
+    }
+  } else if (lo <= hi && threadIdx.x == 0 && status) {
+    atomicCAS(status, 0, (int)MP_ERR_SPAN);
+  }
+  if (threadIdx.x == 0) store<W>(r, a.out[j], a.out_ld[j], 0);
+  if constexpr (!std::is_same<Post, NoPost>::value) {
+    if (threadIdx.x == 0) {
+      __threadfence();
+      if (atomicAdd(s.arrive, 1) == (int)gridDim.x - 1) {
+        atomicExch(s.arrive, 0);
+        __threadfence();
+        post();
+      }
+    }
+  }
+}
+
+// Sets the head of a dot scratch buffer (the arrival counter) to zero.
+template <int = 0>
+__global__ void reset_dot_head(long long* head) {
+  if (threadIdx.x < kDotHeadWords) head[threadIdx.x] = 0;
+}
+
+inline int dot_sm_count() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+
+// Blocks of the accumulate kernel: one per 128 elements, at most 4 per SM.
+inline int dot_blocks(int64_t n) {
+  int64_t b = (n + kDotThreads - 1) / kDotThreads;
+  int64_t lim = (int64_t)dot_sm_count() * 4;
+  if (lim > kDotMaxBlocks) lim = kDotMaxBlocks;
+  if (b > lim) b = lim;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+// Launches the two kernels of k <= 5 dots on `st` (scratch: at least
+// dot_scratch_size<W>(a.k, nblocks) bytes whose arrival counter is zero).
+template <int W, class Post = NoPost>
+mp_status dot_launch(const DotDev& a, void* scratch, int nblocks, int* status, const int* gate,
+                     cudaStream_t st, Post post = Post()) {
+  const DotScratch s = dot_scratch_view<W>(scratch, a.k, nblocks);
+  const size_t smem = dot_smem<W>();
+  MPK_CUDA(cudaFuncSetAttribute(dot_accum_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
+  // streamed operands: shared memory for the windows matters more than L1
+  MPK_CUDA(cudaFuncSetAttribute(dot_accum_kernel<W>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared));
+  dot_accum_kernel<W><<<nblocks, kDotThreads, smem, st>>>(a, s, gate);
+  dot_finalize_kernel<W, Post><<<a.k, 256, 0, st>>>(a, s, status, gate, post);
+  count_launch(2);
+  return launch_check("dot kernels");
+}
+
+}  // namespace mpk

@@ -13,10 +13,19 @@
 #pragma once
 #include <cstdint>
 
+#include "chains.cuh"
+
 namespace mpk {
 
 constexpr int64_t EXP_ZERO = -(int64_t(1) << 61);
 constexpr int SPAN_CAP = 16384;  // largest exponent span an exact sum accepts
+
+// The device's global nanosecond timer (solver time limits).
+__device__ __forceinline__ unsigned long long device_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 template <int W>
 struct Num {
@@ -96,67 +105,15 @@ __device__ __forceinline__ void store(const Num<W>& a, uint64_t* __restrict__ ba
 // Word-array helpers
 // ---------------------------------------------------------------------------
 
-// Carry-chain primitives (PTX add/sub/mad with the carry flag).  A chain is
-// a run of these calls with nothing between them that writes the flag.
-__device__ __forceinline__ uint32_t add_cc(uint32_t a, uint32_t b) {
-  uint32_t r;
-  asm volatile("add.cc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
-  return r;
-}
-__device__ __forceinline__ uint32_t addc_cc(uint32_t a, uint32_t b) {
-  uint32_t r;
-  asm volatile("addc.cc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
-  return r;
-}
-__device__ __forceinline__ uint32_t addc(uint32_t a, uint32_t b) {
-  uint32_t r;
-  asm volatile("addc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
-  return r;
-}
-__device__ __forceinline__ uint32_t sub_cc(uint32_t a, uint32_t b) {
-  uint32_t r;
-  asm volatile("sub.cc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
-  return r;
-}
-__device__ __forceinline__ uint32_t subc_cc(uint32_t a, uint32_t b) {
-  uint32_t r;
-  asm volatile("subc.cc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
-  return r;
-}
-__device__ __forceinline__ uint32_t subc(uint32_t a, uint32_t b) {
-  uint32_t r;
-  asm volatile("subc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
-  return r;
-}
-__device__ __forceinline__ uint32_t mad_lo_cc(uint32_t a, uint32_t b, uint32_t c) {
-  uint32_t r;
-  asm volatile("mad.lo.cc.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
-  return r;
-}
-__device__ __forceinline__ uint32_t madc_lo_cc(uint32_t a, uint32_t b, uint32_t c) {
-  uint32_t r;
-  asm volatile("madc.lo.cc.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
-  return r;
-}
-__device__ __forceinline__ uint32_t mad_hi_cc(uint32_t a, uint32_t b, uint32_t c) {
-  uint32_t r;
-  asm volatile("mad.hi.cc.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
-  return r;
-}
-__device__ __forceinline__ uint32_t madc_hi_cc(uint32_t a, uint32_t b, uint32_t c) {
-  uint32_t r;
-  asm volatile("madc.hi.cc.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
-  return r;
-}
+// Carry-flag chains (chains.cuh) are whole inline-PTX statements: a chain's
+// add.cc / addc.cc / mad*.cc steps and the carry flag between them are never
+// split across statements.
 
 // m += inc (inc in {0,1}); a carry out of the top means M reached 2^p, which is
 // renormalised to 2^(p-1) with the exponent raised by one.
 template <int W>
 __device__ __forceinline__ void round_increment(uint32_t (&m)[W], int64_t& e, uint32_t inc) {
-  m[0] = add_cc(m[0], inc);
-#pragma unroll
-  for (int k = 1; k < W; ++k) m[k] = addc_cc(m[k], 0u);
-  const uint32_t c = addc(0u, 0u);
+  const uint32_t c = chain_inc<W>(m, inc);
   if (c) {
     m[W - 1] = 0x80000000u;
     e += 1;
@@ -239,19 +196,21 @@ __host__ __device__ constexpr int stages_for(int maxw) {
 template <int W>
 __device__ __forceinline__ void mul_full(const uint32_t (&a)[W], const uint32_t (&b)[W],
                                          uint32_t (&r)[2 * W]) {
+  uint32_t R[2 * W + 1];  // R[2W] takes the top row's final carry (zero)
 #pragma unroll
-  for (int k = 0; k < 2 * W; ++k) r[k] = 0u;
+  for (int k = 0; k <= 2 * W; ++k) R[k] = 0u;
 #pragma unroll
   for (int i = 0; i < W; ++i) {
-    r[i] = mad_lo_cc(a[i], b[0], r[i]);
+    uint32_t win[W + 2];
 #pragma unroll
-    for (int j = 1; j < W; ++j) r[i + j] = madc_lo_cc(a[i], b[j], r[i + j]);
-    r[i + W] = addc(r[i + W], 0u);
-    r[i + 1] = mad_hi_cc(a[i], b[0], r[i + 1]);
+    for (int k = 0; k < W + 2; ++k) win[k] = (i + k <= 2 * W) ? R[i + k] : 0u;
+    chain_mul_row<W>(win, a[i], b);
 #pragma unroll
-    for (int j = 1; j < W; ++j) r[i + j + 1] = madc_hi_cc(a[i], b[j], r[i + j + 1]);
-    if (i + W + 1 < 2 * W) r[i + W + 1] = addc(0u, 0u);
+    for (int k = 0; k < W + 2; ++k)
+      if (i + k <= 2 * W) R[i + k] = win[k];
   }
+#pragma unroll
+  for (int k = 0; k < 2 * W; ++k) r[k] = R[k];
 }
 
 // As mul_full, written with 64-bit products and plain additions: no carry
@@ -326,10 +285,7 @@ __device__ __forceinline__ void add_rn(const Num<W>& a_, const Num<W>& b_, Num<W
     return;
   }
   // |b| > |a| ?  (exponents first, mantissas only when they tie)
-  uint32_t t0 = sub_cc(a_.m[0], b_.m[0]);
-#pragma unroll
-  for (int k = 1; k < W; ++k) t0 = subc_cc(a_.m[k], b_.m[k]);
-  const uint32_t mlt = subc(0u, 0u) & 1u;
+  const uint32_t mlt = chain_borrow<W>(a_.m, b_.m);
   const bool sw = (b_.e > a_.e) || (b_.e == a_.e && mlt);
   uint32_t X[W + 1], Y[W + 1];
   X[0] = 0u;
@@ -354,26 +310,56 @@ __device__ __forceinline__ void add_rn(const Num<W>& a_, const Num<W>& b_, Num<W
   const uint32_t sticky = shift_right_sticky<W + 1, stages_for(W)>(Y, (uint32_t)d);
   const uint32_t sub = (s != ys) ? 1u : 0u;
   const uint32_t inv = 0u - sub;
-  uint32_t T[W + 2];
+  uint32_t T[W + 2], Yi[W + 1];
+#pragma unroll
+  for (int k = 0; k <= W; ++k) Yi[k] = Y[k] ^ inv;
   // X[0] is 0, so the carry-in enters through the low word
-  T[0] = add_cc(Y[0] ^ inv, sub & (sticky == 0u ? 1u : 0u));
+  chain_add_frame<W>(T, X, Yi, sub & (sticky == 0u ? 1u : 0u));
+  T[W + 1] &= (sub ^ 1u);
+  uint32_t rb, st;
+  if (sub && d <= 1) {
+    // near case: the difference may cancel any number of leading bits (or
+    // all of them): count the leading zeros and shift them out
+    uint32_t any = 0u;
 #pragma unroll
-  for (int k = 1; k <= W; ++k) T[k] = addc_cc(X[k], Y[k] ^ inv);
-  T[W + 1] = addc(0u, 0u) & (sub ^ 1u);
-  uint32_t any = 0u;
+    for (int k = 0; k < W + 2; ++k) any |= T[k];
+    if (any == 0u) {  // exact cancellation
+      set_zero(r, 0u);
+      return;
+    }
+    const uint32_t lz = count_leading_zeros<W + 2>(T);
+    shift_left<W + 2, stages_for(W + 1)>(T, lz);
+    e += 32 - (int64_t)lz;
+    rb = T[1] >> 31;
+    st = (T[1] << 1) | T[0] | sticky;
 #pragma unroll
-  for (int k = 0; k < W + 2; ++k) any |= T[k];
-  if (any == 0u) {  // exact cancellation
-    set_zero(r, 0u);
-    return;
+    for (int k = 0; k < W; ++k) r.m[k] = T[k + 2];
+  } else {
+    // far case (a sum, or a difference whose smaller operand is below half
+    // the larger): the leading one is at bit 32W+32 (a carry out), 32W+31 or
+    // 32W+30 of T, so the normalising shift lz is 31, 32 or 33 and the kept
+    // words, round bit and sticky bit are fixed funnel shifts of T
+    const uint32_t carry = T[W + 1] & 1u;
+    const uint32_t top = T[W] >> 31;
+    if (carry) {  // lz = 31
+#pragma unroll
+      for (int k = 0; k < W; ++k) r.m[k] = __funnelshift_r(T[k + 1], T[k + 2], 1);
+      rb = T[1] & 1u;
+      st = T[0] | sticky;
+      e += 1;
+    } else if (top) {  // lz = 32
+#pragma unroll
+      for (int k = 0; k < W; ++k) r.m[k] = T[k + 1];
+      rb = T[0] >> 31;
+      st = (T[0] << 1) | sticky;
+    } else {  // lz = 33
+#pragma unroll
+      for (int k = 0; k < W; ++k) r.m[k] = __funnelshift_r(T[k], T[k + 1], 31);
+      rb = (T[0] >> 30) & 1u;
+      st = (T[0] << 2) | sticky;
+      e -= 1;
+    }
   }
-  const uint32_t lz = count_leading_zeros<W + 2>(T);
-  shift_left<W + 2, stages_for(W + 1)>(T, lz);
-  e += 32 - (int64_t)lz;
-  const uint32_t rb = T[1] >> 31;
-  const uint32_t st = (T[1] << 1) | T[0] | sticky;
-#pragma unroll
-  for (int k = 0; k < W; ++k) r.m[k] = T[k + 2];
   r.e = e;
   r.s = s;
   round_increment<W>(r.m, r.e, rb & ((st != 0u) | (r.m[0] & 1u)));
@@ -391,10 +377,37 @@ __device__ __forceinline__ void sub_rn(const Num<W>& a, const Num<W>& b, Num<W>&
   add_rn<W>(a, nb, r);
 }
 
+// floor((u1 2^32 + u0) / d) and its remainder for a normalised word d (top
+// bit set) and u1 < d, from the reciprocal v = floor((2^64 - 1)/d) - 2^32
+// computed once per divisor: the 2/1 division by an invariant integer of
+// Moller and Granlund ("Improved division by invariant integers", IEEE
+// Trans. Computers 60(2), 2011): one 32x32->64 multiply, a two-word add, one
+// low multiply and at most two corrections, instead of a 64-bit division.
+__device__ __forceinline__ uint32_t div2by1(uint32_t u1, uint32_t u0, uint32_t d, uint32_t v,
+                                            uint32_t& rem) {
+  const uint64_t q = (uint64_t)v * u1 + (((uint64_t)u1 << 32) | u0);  // < 2^64 as u1 < d
+  uint32_t q1 = (uint32_t)(q >> 32) + 1u;
+  const uint32_t q0 = (uint32_t)q;
+  uint32_t r = u0 - q1 * d;
+  if (r > q0) {
+    q1 -= 1u;
+    r += d;
+  }
+  if (r >= d) {
+    q1 += 1u;
+    r -= d;
+  }
+  rem = r;
+  return q1;
+}
+
 // r = RN(a/b) for b != 0 (callers test b first).  Knuth's algorithm D in base
 // 2^32 divides N = Ma * 2^(32(W+1)) by Mb (normalised: top bit set), giving a
 // (W+2)-word quotient Q of 32W+32 or 32W+33 bits and a remainder R; the kept
 // p bits, the next bit of Q and sticky = (rest of Q or R nonzero) round it.
+// Each quotient word is estimated from the top two remainder words and Mb's
+// top word by div2by1 (Mb's top word is the invariant divisor), then
+// corrected with the next word as the algorithm prescribes.
 template <int W>
 __device__ __noinline__ void div_rn(const Num<W>& a, const Num<W>& b, Num<W>& r) {
   const uint32_t s = a.s ^ b.s;
@@ -410,16 +423,24 @@ __device__ __noinline__ void div_rn(const Num<W>& a, const Num<W>& b, Num<W>& r)
   u[2 * W + 1] = 0u;
   uint32_t q[W + 2];
   const uint64_t vt = b.m[W - 1], vt2 = b.m[W - 2];
+  const uint32_t vinv = (uint32_t)(~uint64_t(0) / vt);  // floor((2^64-1)/vt) - 2^32
 #pragma unroll
   for (int j = W + 1; j >= 0; --j) {
-    const uint64_t num = ((uint64_t)u[j + W] << 32) | u[j + W - 1];
-    uint64_t qhat = num / vt;
-    uint64_t rhat = num - qhat * vt;
+    // the remainder's top word never exceeds vt; when equal the estimate is
+    // 2^32 - 1 with remainder u0 + vt (which may exceed a word)
+    uint64_t qhat, rhat;
+    if (u[j + W] >= (uint32_t)vt) {
+      qhat = 0xffffffffu;
+      rhat = (uint64_t)u[j + W - 1] + vt;
+    } else {
+      uint32_t rr;
+      qhat = div2by1(u[j + W], u[j + W - 1], (uint32_t)vt, vinv, rr);
+      rhat = rr;
+    }
     const uint64_t u2 = (j + W - 2 >= 0) ? u[j + W - 2] : 0u;
-    while ((qhat >> 32) != 0u || qhat * vt2 > ((rhat << 32) | u2)) {
+    while ((rhat >> 32) == 0u && qhat * vt2 > ((rhat << 32) | u2)) {
       qhat -= 1u;
       rhat += vt;
-      if ((rhat >> 32) != 0u) break;
     }
     uint64_t carry = 0u;
     uint32_t bw = 0u;

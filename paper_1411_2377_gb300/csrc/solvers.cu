@@ -2,15 +2,18 @@
 // BiCGSTAB (the other product-type methods of Section 4, textbook forms).
 //
 // Every step of an iteration is a kernel on the caller's stream: the SpMVs,
-// the exact dot products (fused where they share operands), one-thread
-// scalar kernels for the recurrences' coefficients (p-bit divisions
-// included), and fused vector updates that evaluate the figure's formulas
-// with each product and sum rounded, left to right.  A device state word
-// ("done") gates every kernel: once a scalar kernel decides convergence,
-// breakdown or the iteration limit, later launches return at once, so the
-// host can run several iterations between polls and the result does not
-// depend on the poll interval.  From the second iteration on, one iteration
-// is captured once as a CUDA graph and replayed.
+// the exact dot products (fused where they share operands; two kernels per
+// group, dot.cuh), and fused vector updates that evaluate the figure's
+// formulas with each product and sum rounded, left to right.  The scalar
+// recurrences (alpha, zeta and eta, omega, the stopping rule and the next
+// beta; p-bit divisions included) run on one thread at the end of the dot
+// group whose results they take, in that group's finalize kernel, so no
+// launch carries a scalar step alone.  A device state word ("done") gates
+// every kernel: once a scalar step decides convergence, breakdown or the
+// iteration limit, later launches return at once, so the host can run
+// several iterations between polls and the result does not depend on the
+// poll interval.  From the second iteration on, one iteration is captured
+// once as a CUDA graph and replayed.
 //
 // Readings of Fig. 5 (shared with the oracle):
 //  * GPBiCG uses z = zeta r + eta z - alpha u and r = t - eta y - zeta A t
@@ -27,6 +30,7 @@
 #include <cstring>
 #include <vector>
 
+#include "dot.cuh"
 #include "internal.h"
 #include "mpdev.cuh"
 
@@ -59,9 +63,14 @@ namespace {
 
 struct SState {
   int done;    // gate for every kernel of the solve
-  int status;  // MP_OK, MP_ERR_BREAKDOWN, MP_ERR_NOCONV
+  int status;  // MP_OK, MP_ERR_BREAKDOWN, MP_ERR_NOCONV, MP_ERR_TIMEOUT
   long long iters;
   long long maxit;
+  cudaGraphConditionalHandle loop;  // the device-side iteration loop (has_loop)
+  int has_loop;
+  int pad;
+  unsigned long long t0;        // device time (ns) at the set-up
+  unsigned long long limit_ns;  // 0: no time limit
 };
 
 enum Scal {
@@ -72,28 +81,43 @@ enum Scal {
 // Solvers of the library (the template argument of the driver).
 enum Method { kBiCG = 0, kGPBiCG = 1, kCGS = 2, kBiCGSTAB = 3 };
 
+// Scalar slots are read through L2 (the post-steps below read slots that other
+// blocks of the same kernel wrote).
 template <int W>
 __device__ __forceinline__ void ld_s(Num<W>& a, const uint64_t* S, int j) {
-  load<W>(a, S + (size_t)j * (W / 2 + 1), 1, 0);
+  const uint64_t* p = S + (size_t)j * (W / 2 + 1);
+  unpack_head(__ldcg(p), a.e, a.s);
+#pragma unroll
+  for (int k = 0; k < W / 2; ++k) {
+    const uint64_t l = __ldcg(p + 1 + k);
+    a.m[2 * k] = (uint32_t)l;
+    a.m[2 * k + 1] = (uint32_t)(l >> 32);
+  }
 }
 template <int W>
 __device__ __forceinline__ void st_s(const Num<W>& a, uint64_t* S, int j) {
   store<W>(a, S + (size_t)j * (W / 2 + 1), 1, 0);
 }
 
+// Ends the solve: every later kernel returns at once, and the device-side
+// loop that replays the iteration stops after the current pass.
 __device__ __forceinline__ void finish(SState* st, int status) {
   st->status = status;
   st->done = 1;
+  if (st->has_loop) cudaGraphSetConditional(st->loop, 0u);
 }
 
+
 // ---------------------------------------------------------------------------
-// Scalar kernels (one thread)
+// Scalar steps.  Each runs on one thread right after the dot products it
+// consumes: the last block of those dots' finalize kernel calls it (dot.cuh),
+// so an iteration launches no scalar kernel of its own.
 // ---------------------------------------------------------------------------
 
 // thr = RN(RN(T*(r0,r0)) + A) with T = RN(rtol^2), A = RN(atol^2); exits
 // before the first iteration when (r0,r0) <= thr or rho = 0.
 template <int W>
-__global__ void sc_setup(SState* st, uint64_t* S, double rtol, double atol) {
+__device__ void s_setup(SState* st, uint64_t* S, double rtol, double atol) {
   Num<W> rt, at, T, A, t, thr, rr0, rho, z;
   from_f64<W>(rtol, rt);
   from_f64<W>(atol, at);
@@ -111,6 +135,7 @@ __global__ void sc_setup(SState* st, uint64_t* S, double rtol, double atol) {
   st->iters = 0;
   st->status = MP_OK;
   st->done = 0;
+  st->t0 = device_ns();
   if (cmp<W>(rr0, thr) <= 0) {
     finish(st, MP_OK);
   } else if (st->maxit <= 0) {
@@ -122,7 +147,7 @@ __global__ void sc_setup(SState* st, uint64_t* S, double rtol, double atol) {
 
 // alpha = RN(rho / DEN); DEN = 0 is a breakdown.
 template <int W>
-__global__ void sc_alpha(SState* st, uint64_t* S) {
+__device__ void s_alpha(SState* st, uint64_t* S) {
   if (st->done) return;
   Num<W> rho, d, a;
   ld_s<W>(d, S, DEN);
@@ -137,7 +162,7 @@ __global__ void sc_alpha(SState* st, uint64_t* S) {
 
 // GPBiCG i = 1: zeta = mu2/mu5 (mu5 = 0 -> 0), eta = 0.
 template <int W>
-__global__ void sc_zeta1(SState* st, uint64_t* S) {
+__device__ void s_zeta1(SState* st, uint64_t* S) {
   if (st->done) return;
   Num<W> m2, m5, z;
   ld_s<W>(m2, S, MU2);
@@ -154,7 +179,7 @@ __global__ void sc_zeta1(SState* st, uint64_t* S) {
 // tau = mu5 mu1 - mu4 mu4; zeta = (mu1 mu2 - mu3 mu4)/tau;
 // eta = (mu5 mu3 - mu4 mu2)/tau; tau = 0 -> zeta = eta = 0.
 template <int W>
-__global__ void sc_zeta(SState* st, uint64_t* S) {
+__device__ void s_zeta(SState* st, uint64_t* S) {
   if (st->done) return;
   Num<W> m1, m2, m3, m4, m5, a, b, c, tau, z;
   ld_s<W>(m1, S, MU1);
@@ -183,11 +208,25 @@ __global__ void sc_zeta(SState* st, uint64_t* S) {
   st_s<W>(z, S, ETA);
 }
 
+// BiCGSTAB: omega = RN(TS / TT), +0 when TT = (t, t) = 0.
+template <int W>
+__device__ void s_omega(SState* st, uint64_t* S) {
+  if (st->done) return;
+  Num<W> ts, tt, om;
+  ld_s<W>(tt, S, TT);
+  if (zero_e(tt.e)) {
+    set_zero(om, 0u);
+  } else {
+    ld_s<W>(ts, S, TS);
+    div_rn<W>(ts, tt, om);
+  }
+  st_s<W>(om, S, OMEGA);
+}
+
 // beta = RN(rho/rho_prev) (BiCG, CGS), or RN(RN(rho/rho_prev) * RN(alpha/d))
 // with d = zeta (GPBiCG) or omega (BiCGSTAB): DIV names d's slot, -1 none.
 template <int W, int DIV>
-__global__ void sc_beta(SState* st, uint64_t* S) {
-  if (st->done) return;
+__device__ void s_beta(uint64_t* S) {
   Num<W> rho, rp, q1, a, z, q2, b;
   ld_s<W>(rho, S, RHO);
   ld_s<W>(rp, S, RHO_PREV);
@@ -205,10 +244,14 @@ __global__ void sc_beta(SState* st, uint64_t* S) {
 
 // End of an iteration: count it, record (r,r), shift rho, decide the exit.
 // ZX: the scalar whose zero ends the iteration after the convergence test
-// (GPBiCG's zeta, BiCGSTAB's omega), -1 none.
-template <int W, int ZX>
-__global__ void sc_check(SState* st, uint64_t* S, uint64_t* hist, int64_t hist_ld,
-                         int64_t hist_n) {
+// (GPBiCG's zeta, BiCGSTAB's omega), -1 none.  A time limit, when set, ends
+// the solve (MP_ERR_TIMEOUT) once an iteration finishes past it.  When the
+// solve goes on, the next iteration's beta (divisor slot BDIV, -1 none) is
+// formed here: its inputs are final at this point, and the next iteration
+// then starts with its vector update.
+template <int W, int ZX, int BDIV>
+__device__ void s_check(SState* st, uint64_t* S, uint64_t* hist, int64_t hist_ld,
+                        int64_t hist_n) {
   if (st->done) return;
   Num<W> rr, thr, rho, rn, z;
   st->iters += 1;
@@ -228,8 +271,52 @@ __global__ void sc_check(SState* st, uint64_t* S, uint64_t* hist, int64_t hist_l
     finish(st, MP_ERR_NOCONV);
   } else if (zero_e(rn.e)) {
     finish(st, MP_ERR_BREAKDOWN);
+  } else if (st->limit_ns != 0 && device_ns() - st->t0 > st->limit_ns) {
+    finish(st, MP_ERR_TIMEOUT);
+  } else {
+    s_beta<W, BDIV>(S);
   }
 }
+
+// The steps as the dot finalize's post-step functors.
+template <int W>
+struct PostSetup {
+  SState* st;
+  uint64_t* S;
+  double rtol, atol;
+  __device__ void operator()() const { s_setup<W>(st, S, rtol, atol); }
+};
+template <int W>
+struct PostAlpha {
+  SState* st;
+  uint64_t* S;
+  __device__ void operator()() const { s_alpha<W>(st, S); }
+};
+template <int W, bool FIRST>
+struct PostZeta {
+  SState* st;
+  uint64_t* S;
+  __device__ void operator()() const {
+    if (FIRST)
+      s_zeta1<W>(st, S);
+    else
+      s_zeta<W>(st, S);
+  }
+};
+template <int W>
+struct PostOmega {
+  SState* st;
+  uint64_t* S;
+  __device__ void operator()() const { s_omega<W>(st, S); }
+};
+template <int W, int ZX, int BDIV>
+struct PostCheck {
+  SState* st;
+  uint64_t* S;
+  uint64_t* hist;
+  int64_t hist_ld, hist_n;
+  __device__ void operator()() const { s_check<W, ZX, BDIV>(st, S, hist, hist_ld, hist_n); }
+};
 
 // ---------------------------------------------------------------------------
 // Vector kernels (gated)
@@ -432,21 +519,6 @@ __global__ void bi_xr(const SState* st, const uint64_t* __restrict__ S, const ui
   }
 }
 
-// BiCGSTAB: omega = RN(TS / TT), +0 when TT = (t, t) = 0.
-template <int W>
-__global__ void sc_omega(SState* st, uint64_t* S) {
-  if (st->done) return;
-  Num<W> ts, tt, om;
-  ld_s<W>(tt, S, TT);
-  if (zero_e(tt.e)) {
-    set_zero(om, 0u);
-  } else {
-    ld_s<W>(ts, S, TS);
-    div_rn<W>(ts, tt, om);
-  }
-  st_s<W>(om, S, OMEGA);
-}
-
 // CGS, i >= 2: u = r + beta q;  p = u + beta (q + beta p)
 template <int W>
 __global__ void cgs_up(const SState* st, const uint64_t* __restrict__ S, const uint64_t* r,
@@ -591,6 +663,7 @@ struct Work {
   uint64_t* vecs = nullptr;  // nvec vectors of (L+1)*ld words
   uint64_t* S = nullptr;     // NSCAL scalars of L+1 words
   SState* st = nullptr;
+  int* status = nullptr;     // the device status word (span errors of the dots)
   void* dscratch = nullptr;
   int nvec = 0;
   uint64_t* vec(int k) const { return vecs + (size_t)k * (L + 1) * ld; }
@@ -606,6 +679,8 @@ mp_status alloc_work(Work& w, int prec, int64_t n, int nvec, cudaStream_t st) {
   const size_t vb = (size_t)nvec * (w.L + 1) * w.ld * 8;
   const size_t sb = (size_t)NSCAL * (w.L + 1) * 8;
   const size_t db = dot_scratch_bytes(prec, 5);
+  w.status = status_word();
+  if (!w.status) return set_error(MP_ERR_CUDA, "status word unavailable");
   MPK_CUDA(cudaMallocAsync((void**)&w.vecs, vb, st));
   MPK_CUDA(cudaMallocAsync((void**)&w.S, sb, st));
   MPK_CUDA(cudaMallocAsync((void**)&w.st, sizeof(SState), st));
@@ -621,9 +696,11 @@ void free_work(Work& w, cudaStream_t st) {
   w = Work{};
 }
 
+// One or two dots (a0.b0 -> slot o0, a1.b1 -> slot o1) followed by `post`.
+template <int W, class Post>
 mp_status dot2(const Work& w, const uint64_t* a0, const uint64_t* b0, int o0, const uint64_t* a1,
-               const uint64_t* b1, int o1, cudaStream_t st, const int* gate) {
-  DotArgs d;
+               const uint64_t* b1, int o1, cudaStream_t st, const int* gate, Post post) {
+  DotDev d{};
   d.k = a1 ? 2 : 1;
   d.n = w.n;
   d.x[0] = a0;
@@ -636,7 +713,16 @@ mp_status dot2(const Work& w, const uint64_t* a0, const uint64_t* b0, int o0, co
   }
   d.out[0] = w.scal(o0);
   d.out[1] = a1 ? w.scal(o1) : nullptr;
-  return launch_dot(w.prec, d, w.dscratch, gate, st);
+  return dot_launch<W, Post>(d, w.dscratch, dot_blocks(w.n), w.status, gate, st, post);
+}
+
+// The end-of-iteration dots (r, r) and (r~, r) with the convergence check.
+template <int W, int ZX, int BDIV>
+mp_status check_dots(const Work& w, const SolveCall& c, uint64_t* r, uint64_t* rt, cudaStream_t st,
+                     const int* gate) {
+  const PostCheck<W, ZX, BDIV> post{w.st, w.S, c.o.history.data, c.o.history.ld,
+                                    c.o.history.data ? c.o.history.n : 0};
+  return dot2<W>(w, r, r, RR, rt, r, RHO_NEW, st, gate, post);
 }
 
 // The operator of the solve (A, or A^T for an adjoint solve) and its transpose.
@@ -655,17 +741,16 @@ mp_status gp_iteration(const Work& w, const SolveCall& c, bool first) {
   if (first) {
     copy_kernel<W><<<g, 128, 0, st>>>(w.st, w.vec(R), ld, w.vec(P), ld, n);
     count_launch();
-  } else {
-    sc_beta<W, ZETA><<<1, 1, 0, st>>>(w.st, w.S);
+  } else {  // beta was formed by the previous iteration's check
     gp_wp<W><<<g, 128, 0, st>>>(w.st, w.S, w.vec(V), w.vec(Q), w.vec(R), w.vec(P), w.vec(U),
                                 w.vec(WV), ld, n);
-    count_launch(2);
+    count_launch();
   }
   if ((r = launch_spmv(c.A, op_a(c),c.o.mode, w.vec(P), ld, w.vec(Q), ld, nullptr, 0, gate, st)) != MP_OK)
     return r;
-  if ((r = dot2(w, w.vec(RT), w.vec(Q), DEN, nullptr, nullptr, 0, st, gate)) != MP_OK) return r;
-  sc_alpha<W><<<1, 1, 0, st>>>(w.st, w.S);
-  count_launch();
+  if ((r = dot2<W>(w, w.vec(RT), w.vec(Q), DEN, nullptr, nullptr, 0, st, gate,
+                   PostAlpha<W>{w.st, w.S})) != MP_OK)
+    return r;
   if (first) {
     gp_ty1<W><<<g, 128, 0, st>>>(w.st, w.S, w.vec(R), w.vec(Q), w.vec(T), w.vec(Y), ld, n);
   } else {
@@ -675,7 +760,7 @@ mp_status gp_iteration(const Work& w, const SolveCall& c, bool first) {
   count_launch();
   if ((r = launch_spmv(c.A, op_a(c),c.o.mode, w.vec(T), ld, w.vec(V), ld, nullptr, 0, gate, st)) != MP_OK)
     return r;
-  DotArgs d;
+  DotDev d{};
   d.n = n;
   for (int j = 0; j < 5; ++j) {
     d.ldx[j] = d.ldy[j] = ld;
@@ -693,12 +778,11 @@ mp_status gp_iteration(const Work& w, const SolveCall& c, bool first) {
     d.x[3] = w.vec(V); d.y[3] = w.vec(Y); d.out[3] = w.scal(MU4);
     d.x[4] = w.vec(V); d.y[4] = w.vec(V); d.out[4] = w.scal(MU5);
   }
-  if ((r = launch_dot(w.prec, d, w.dscratch, gate, st)) != MP_OK) return r;
-  if (first)
-    sc_zeta1<W><<<1, 1, 0, st>>>(w.st, w.S);
-  else
-    sc_zeta<W><<<1, 1, 0, st>>>(w.st, w.S);
-  count_launch();
+  r = first ? dot_launch<W>(d, w.dscratch, dot_blocks(n), w.status, gate, st,
+                            PostZeta<W, true>{w.st, w.S})
+            : dot_launch<W>(d, w.dscratch, dot_blocks(n), w.status, gate, st,
+                            PostZeta<W, false>{w.st, w.S});
+  if (r != MP_OK) return r;
   Vecs V9{};
   V9.v[0] = w.vec(Q); V9.v[1] = w.vec(SV); V9.v[2] = w.vec(U); V9.v[3] = w.vec(R);
   V9.v[4] = w.vec(Z); V9.v[5] = w.vec(P); V9.v[6] = w.vec(T); V9.v[7] = w.vec(Y);
@@ -707,11 +791,7 @@ mp_status gp_iteration(const Work& w, const SolveCall& c, bool first) {
   V9.n = n;
   gp_uzxr<W><<<g, 128, 0, st>>>(w.st, w.S, V9, c.x.data, c.x.ld);
   count_launch();
-  if ((r = dot2(w, w.vec(R), w.vec(R), RR, w.vec(RT), w.vec(R), RHO_NEW, st, gate)) != MP_OK)
-    return r;
-  sc_check<W, ZETA><<<1, 1, 0, st>>>(w.st, w.S, c.o.history.data, c.o.history.ld,
-                                     c.o.history.data ? c.o.history.n : 0);
-  count_launch();
+  if ((r = check_dots<W, ZETA, ZETA>(w, c, w.vec(R), w.vec(RT), st, gate)) != MP_OK) return r;
   return launch_check("gpbicg iteration");
 }
 
@@ -727,25 +807,21 @@ mp_status bi_iteration(const Work& w, const SolveCall& c, bool first) {
     copy_kernel<W><<<g, 128, 0, st>>>(w.st, w.vec(R), ld, w.vec(P), ld, n);
     copy_kernel<W><<<g, 128, 0, st>>>(w.st, w.vec(RT), ld, w.vec(PT), ld, n);
     count_launch(2);
-  } else {
-    sc_beta<W, -1><<<1, 1, 0, st>>>(w.st, w.S);
+  } else {  // beta was formed by the previous iteration's check
     bi_p<W><<<g, 128, 0, st>>>(w.st, w.S, w.vec(R), w.vec(RT), w.vec(P), w.vec(PT), ld, n);
-    count_launch(2);
+    count_launch();
   }
   if ((r = launch_spmv(c.A, op_a(c),c.o.mode, w.vec(P), ld, w.vec(Z), ld, nullptr, 0, gate, st)) != MP_OK)
     return r;
   if ((r = launch_spmv(c.A, op_at(c),c.o.mode, w.vec(PT), ld, w.vec(ZT), ld, nullptr, 0, gate, st)) != MP_OK)
     return r;
-  if ((r = dot2(w, w.vec(PT), w.vec(Z), DEN, nullptr, nullptr, 0, st, gate)) != MP_OK) return r;
-  sc_alpha<W><<<1, 1, 0, st>>>(w.st, w.S);
+  if ((r = dot2<W>(w, w.vec(PT), w.vec(Z), DEN, nullptr, nullptr, 0, st, gate,
+                   PostAlpha<W>{w.st, w.S})) != MP_OK)
+    return r;
   bi_xr<W><<<g, 128, 0, st>>>(w.st, w.S, w.vec(P), w.vec(Z), w.vec(ZT), w.vec(R), w.vec(RT),
                               c.x.data, c.x.ld, ld, n);
-  count_launch(2);
-  if ((r = dot2(w, w.vec(R), w.vec(R), RR, w.vec(RT), w.vec(R), RHO_NEW, st, gate)) != MP_OK)
-    return r;
-  sc_check<W, -1><<<1, 1, 0, st>>>(w.st, w.S, c.o.history.data, c.o.history.ld,
-                                      c.o.history.data ? c.o.history.n : 0);
   count_launch();
+  if ((r = check_dots<W, -1, -1>(w, c, w.vec(R), w.vec(RT), st, gate)) != MP_OK) return r;
   return launch_check("bicg iteration");
 }
 
@@ -761,27 +837,23 @@ mp_status cgs_iteration(const Work& w, const SolveCall& c, bool first) {
     copy_kernel<W><<<g, 128, 0, st>>>(w.st, w.vec(R), ld, w.vec(U), ld, n);
     copy_kernel<W><<<g, 128, 0, st>>>(w.st, w.vec(R), ld, w.vec(P), ld, n);
     count_launch(2);
-  } else {
-    sc_beta<W, -1><<<1, 1, 0, st>>>(w.st, w.S);
+  } else {  // beta was formed by the previous iteration's check
     cgs_up<W><<<g, 128, 0, st>>>(w.st, w.S, w.vec(R), w.vec(Q), w.vec(U), w.vec(P), ld, n);
-    count_launch(2);
+    count_launch();
   }
   if ((r = launch_spmv(c.A, op_a(c), c.o.mode, w.vec(P), ld, w.vec(V), ld, nullptr, 0, gate, st)) != MP_OK)
     return r;
-  if ((r = dot2(w, w.vec(RT), w.vec(V), DEN, nullptr, nullptr, 0, st, gate)) != MP_OK) return r;
-  sc_alpha<W><<<1, 1, 0, st>>>(w.st, w.S);
+  if ((r = dot2<W>(w, w.vec(RT), w.vec(V), DEN, nullptr, nullptr, 0, st, gate,
+                   PostAlpha<W>{w.st, w.S})) != MP_OK)
+    return r;
   cgs_qwx<W><<<g, 128, 0, st>>>(w.st, w.S, w.vec(U), w.vec(V), w.vec(Q), w.vec(WV), c.x.data,
                                 c.x.ld, ld, n);
-  count_launch(2);
+  count_launch();
   if ((r = launch_spmv(c.A, op_a(c), c.o.mode, w.vec(WV), ld, w.vec(AW), ld, nullptr, 0, gate, st)) != MP_OK)
     return r;
   r_minus<W, ALPHA><<<g, 128, 0, st>>>(w.st, w.S, w.vec(AW), w.vec(R), ld, n);
   count_launch();
-  if ((r = dot2(w, w.vec(R), w.vec(R), RR, w.vec(RT), w.vec(R), RHO_NEW, st, gate)) != MP_OK)
-    return r;
-  sc_check<W, -1><<<1, 1, 0, st>>>(w.st, w.S, c.o.history.data, c.o.history.ld,
-                                   c.o.history.data ? c.o.history.n : 0);
-  count_launch();
+  if ((r = check_dots<W, -1, -1>(w, c, w.vec(R), w.vec(RT), st, gate)) != MP_OK) return r;
   return launch_check("cgs iteration");
 }
 
@@ -796,10 +868,9 @@ mp_status bicgstab_iteration(const Work& w, const SolveCall& c, bool first) {
   if (first) {
     copy_kernel<W><<<g, 128, 0, st>>>(w.st, w.vec(R), ld, w.vec(P), ld, n);
     count_launch();
-  } else {
-    sc_beta<W, OMEGA><<<1, 1, 0, st>>>(w.st, w.S);
+  } else {  // beta was formed by the previous iteration's check
     bs_p<W><<<g, 128, 0, st>>>(w.st, w.S, w.vec(R), w.vec(V), w.vec(P), ld, n);
-    count_launch(2);
+    count_launch();
   }
   // right preconditioning: v = A K^{-1} p, t = A K^{-1} s (x takes K^{-1} p
   // and K^{-1} s); left: v = K^{-1} A p, t = K^{-1} A s (PH and SH hold A p
@@ -815,10 +886,11 @@ mp_status bicgstab_iteration(const Work& w, const SolveCall& c, bool first) {
     return r;
   if (left && (r = launch_ilu0_apply(c.pre, w.vec(PH), ld, w.vec(V), ld, gate, st)) != MP_OK)
     return r;
-  if ((r = dot2(w, w.vec(RT), w.vec(V), DEN, nullptr, nullptr, 0, st, gate)) != MP_OK) return r;
-  sc_alpha<W><<<1, 1, 0, st>>>(w.st, w.S);
+  if ((r = dot2<W>(w, w.vec(RT), w.vec(V), DEN, nullptr, nullptr, 0, st, gate,
+                   PostAlpha<W>{w.st, w.S})) != MP_OK)
+    return r;
   bs_s<W><<<g, 128, 0, st>>>(w.st, w.S, w.vec(R), w.vec(V), w.vec(SV), ld, n);
-  count_launch(2);
+  count_launch();
   const uint64_t* sv = w.vec(SV);
   if (c.pre && !left) {
     if ((r = launch_ilu0_apply(c.pre, w.vec(SV), ld, w.vec(SH), ld, gate, st)) != MP_OK) return r;
@@ -829,16 +901,13 @@ mp_status bicgstab_iteration(const Work& w, const SolveCall& c, bool first) {
     return r;
   if (left && (r = launch_ilu0_apply(c.pre, w.vec(SH), ld, w.vec(T), ld, gate, st)) != MP_OK)
     return r;
-  if ((r = dot2(w, w.vec(T), w.vec(SV), TS, w.vec(T), w.vec(T), TT, st, gate)) != MP_OK) return r;
-  sc_omega<W><<<1, 1, 0, st>>>(w.st, w.S);
+  if ((r = dot2<W>(w, w.vec(T), w.vec(SV), TS, w.vec(T), w.vec(T), TT, st, gate,
+                   PostOmega<W>{w.st, w.S})) != MP_OK)
+    return r;
   bs_xr<W><<<g, 128, 0, st>>>(w.st, w.S, pv, sv, w.vec(SV), w.vec(T), w.vec(R), c.x.data,
                               c.x.ld, ld, n);
-  count_launch(2);
-  if ((r = dot2(w, w.vec(R), w.vec(R), RR, w.vec(RT), w.vec(R), RHO_NEW, st, gate)) != MP_OK)
-    return r;
-  sc_check<W, OMEGA><<<1, 1, 0, st>>>(w.st, w.S, c.o.history.data, c.o.history.ld,
-                                      c.o.history.data ? c.o.history.n : 0);
   count_launch();
+  if ((r = check_dots<W, OMEGA, OMEGA>(w, c, w.vec(R), w.vec(RT), st, gate)) != MP_OK) return r;
   return launch_check("bicgstab iteration");
 }
 
@@ -871,7 +940,11 @@ mp_status solve_w(const SolveCall& cu, mp_solve_info* info) {
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   cudaEventRecord(e0, st);
-  SState init{1, MP_OK, 0, c.o.maxit};
+  SState init{};
+  init.done = 1;
+  init.status = MP_OK;
+  init.maxit = c.o.maxit;
+  init.limit_ns = (unsigned long long)c.o.time_limit_ms * 1000000ull;
   const int64_t ld = w.ld;
   const int g = ew_grid(n);
   cudaGraph_t graph = nullptr;
@@ -903,10 +976,9 @@ mp_status solve_w(const SolveCall& cu, mp_solve_info* info) {
     if (left && (r = launch_ilu0_apply(c.pre, r0, ld, w.vec(0), ld, nullptr, st)) != MP_OK) break;
     copy_kernel<W><<<g, 128, 0, st>>>(nullptr, w.vec(0), ld, w.vec(1), ld, n);
     count_launch();
-    if ((r = dot2(w, w.vec(0), w.vec(0), RR0, w.vec(1), w.vec(0), RHO, st, nullptr)) != MP_OK)
+    if ((r = dot2<W>(w, w.vec(0), w.vec(0), RR0, w.vec(1), w.vec(0), RHO, st, nullptr,
+                     PostSetup<W>{w.st, w.S, c.o.rtol, c.o.atol})) != MP_OK)
       break;
-    sc_setup<W><<<1, 1, 0, st>>>(w.st, w.S, c.o.rtol, c.o.atol);
-    count_launch();
     if ((r = launch_check("solver setup")) != MP_OK) break;
     // first iteration (not captured)
     if ((r = body(true)) != MP_OK) break;
@@ -915,32 +987,50 @@ mp_status solve_w(const SolveCall& cu, mp_solve_info* info) {
     if (cer == cudaSuccess) cer = cudaStreamSynchronize(st);
     if (cer != cudaSuccess) { r = cuda_error(cer, "reading the solver state"); break; }
     if (hs.done) break;
-    // capture one steady-state iteration
-    cudaError_t ce = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
-    if (ce != cudaSuccess) { r = cuda_error(ce, "cudaStreamBeginCapture"); break; }
+    // The remaining iterations run on the device in one graph launch: a
+    // conditional while node whose body is one captured iteration.  finish()
+    // clears the loop's condition wherever the solve ends (the stopping rule,
+    // a breakdown, maxit, the time limit), so no host poll is needed.
+    cudaGraphConditionalHandle loop{};
+    cudaGraphNodeParams cp{};
+    cudaGraphNode_t node = nullptr;
+    cudaError_t ce = cudaGraphCreate(&graph, 0);
+    if (ce == cudaSuccess)
+      ce = cudaGraphConditionalHandleCreate(&loop, graph, 1u, cudaGraphCondAssignDefault);
+    if (ce == cudaSuccess) {
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = loop;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      ce = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+    }
+    if (ce != cudaSuccess) { r = cuda_error(ce, "building the iteration loop"); break; }
+    cudaGraph_t bodyg = cp.conditional.phGraph_out[0];
+    const int one = 1;
+    ce = cudaMemcpyAsync(&w.st->loop, &loop, sizeof loop, cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(&w.st->has_loop, &one, sizeof one, cudaMemcpyHostToDevice, st);
+    if (ce != cudaSuccess) { r = cuda_error(ce, "loop handle upload"); break; }
+    ce = cudaStreamBeginCaptureToGraph(st, bodyg, nullptr, nullptr, 0,
+                                       cudaStreamCaptureModeRelaxed);
+    if (ce != cudaSuccess) { r = cuda_error(ce, "cudaStreamBeginCaptureToGraph"); break; }
     const int64_t before = mp_launch_count(0);
     mp_status rb = body(false);
     const int64_t per_iter = mp_launch_count(0) - before;
-    ce = cudaStreamEndCapture(st, &graph);
+    count_launch(-(int)per_iter);  // the capture itself launched nothing
+    ce = cudaStreamEndCapture(st, &bodyg);
     if (rb != MP_OK) { r = rb; break; }
     if (ce != cudaSuccess) { r = cuda_error(ce, "cudaStreamEndCapture"); break; }
     ce = cudaGraphInstantiate(&exec, graph, 0);
     if (ce != cudaSuccess) { r = cuda_error(ce, "cudaGraphInstantiate"); break; }
-    const int poll = c.o.poll_every > 0 ? c.o.poll_every : 1;
-    count_launch(-(int)per_iter);  // the capture itself launched nothing
-    while (true) {
-      for (int k = 0; k < poll; ++k) {
-        ce = cudaGraphLaunch(exec, st);
-        if (ce != cudaSuccess) break;
-        count_launch((int)per_iter);
-      }
-      if (ce != cudaSuccess) { r = cuda_error(ce, "cudaGraphLaunch"); break; }
-      ce = injected_fault("solver poll");
-      if (ce == cudaSuccess) ce = cudaMemcpyAsync(&hs, w.st, sizeof hs, cudaMemcpyDeviceToHost, st);
-      if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
-      if (ce != cudaSuccess) { r = cuda_error(ce, "reading the solver state"); break; }
-      if (hs.done) break;
-    }
+    const long long it0 = hs.iters;
+    ce = cudaGraphLaunch(exec, st);
+    if (ce != cudaSuccess) { r = cuda_error(ce, "cudaGraphLaunch"); break; }
+    ce = injected_fault("solver poll");
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(&hs, w.st, sizeof hs, cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) { r = cuda_error(ce, "reading the solver state"); break; }
+    count_launch((int)(per_iter * (hs.iters - it0)));
   } while (false);
   if (exec) cudaGraphExecDestroy(exec);
   if (graph) cudaGraphDestroy(graph);
@@ -1026,12 +1116,14 @@ mp_status solve(int method, mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* o
     return set_error(MP_ERR_ARG, "transpose must be 0 or 1");
   if (opts->transpose && !A->has_t)
     return set_error(MP_ERR_ARG, "a solve with A^T needs MP_CSR_TRANSPOSE");
-  if (opts->reserved != 0) return set_error(MP_ERR_ARG, "reserved must be 0");
+  if (opts->time_limit_ms < 0) return set_error(MP_ERR_ARG, "time_limit_ms < 0");
   if (!status_word()) return set_error(MP_ERR_CUDA, "status word unavailable");
   if (pre && (pre->n != A->n || pre->prec != A->prec || opts->transpose))
     return set_error(MP_ERR_ARG, "preconditioner does not match the matrix (or a transposed solve)");
   if (prec_big(A->prec)) {
     if (pre) return set_error(MP_ERR_PREC, "ILU(0) at p = %d: only p <= 1024", A->prec);
+    if (opts->time_limit_ms != 0)
+      return set_error(MP_ERR_ARG, "time_limit_ms: only the solvers at p <= 1024 take a limit");
     return solve_big(method, A, b, x, opts, info, static_cast<cudaStream_t>(stream));
   }
   SolveCall c{A, b, x, *opts, static_cast<cudaStream_t>(stream), pre, pre_left};

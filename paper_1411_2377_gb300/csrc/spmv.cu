@@ -288,6 +288,113 @@ __device__ __forceinline__ void value_as_product(const Num<W>& b, uint32_t (&P)[
   }
 }
 
+// y_i of an EXACT product (no b term) in one pass over the row: the thread's
+// window of counters (the per-thread span kFastSpan, as in the two-pass
+// form) is anchored kFastSpan/2 bits below the row's first nonzero term, so
+// no pre-pass over the row's exponents is needed.  Every term that lands in
+// the window is added as it is read; a term outside it (the row's terms span
+// more than kFastSpan/2 bits around the first one) sends the row to the
+// overflow list, whose warp-per-row kernel computes it from scratch.  The
+// range [emin, emax] of the terms seen bounds the digits that are resolved
+// and rounded, exactly as the two-pass form's window anchored at emin.
+template <int W, bool COLS, bool PIPE, int G>
+__device__ __forceinline__ void exact_row_one_pass(const SellView& S,
+                                                   const uint64_t* __restrict__ x, int64_t ldx,
+                                                   uint64_t* __restrict__ y, int64_t ldy,
+                                                   int32_t* __restrict__ ovf, int64_t slot,
+                                                   int32_t row, int32_t len, int64_t base) {
+  extern __shared__ int64_t sacc[];
+  constexpr int NDW = COLS ? Win<W>::fast_cols : Win<W>::fast;
+  constexpr int64_t H = kFastSpan / 2;
+  constexpr int R = COLS ? kR : 32;  // bits per counter digit
+  const int stride = blockDim.x;
+  int64_t* c = sacc + threadIdx.x;
+#pragma unroll 4
+  for (int d = 0; d < NDW; ++d) c[d * stride] = 0;
+  int64_t eb = 0, emin = LLONG_MAX, emax = LLONG_MIN;
+  bool over = false;
+  uint32_t P[2 * W];
+  // adds a * x (sign folded into ng) at bit offset off in [0, 2H]
+  auto term = [&](const Num<W>& a, const Num<W>& xv, uint32_t ng) {
+    const int64_t E = a.e + xv.e;
+    if (emin > emax) eb = E - H;  // the first term sets the anchor
+    const int64_t off = E - eb;
+    if (off < 0 || off > 2 * H) {
+      over = true;
+      return;
+    }
+    emin = min(emin, E);
+    emax = max(emax, E);
+    if (COLS) {
+      add_product_cols<W, G>(c, stride, a.m, xv.m, (uint32_t)off, ng);
+    } else {
+      if (W >= 16)
+        mul_full_ilp<W>(a.m, xv.m, P);
+      else
+        mul_full<W>(a.m, xv.m, P);
+      add_term<W>(c, stride, P, off, ng);
+    }
+  };
+  if (PIPE) {
+    Num<W> an, xn;
+    int32_t c1 = 0;
+    if (len > 0) {
+      const int32_t c0 = S.col[base];
+      if (len > 1) c1 = S.col[base + 32];
+      load_stream<W>(an, S.val, S.nslots, base);
+      gather_x<W>(xn, S, x, ldx, c0);
+    }
+    for (int32_t j = 0; j < len && !over; ++j) {
+      const Num<W> a = an, xv = xn;
+      if (j + 1 < len) {
+        const int64_t k1 = base + (int64_t)(j + 1) * 32;
+        const int32_t cn = c1;
+        if (j + 2 < len) c1 = S.col[k1 + 32];
+        load_stream<W>(an, S.val, S.nslots, k1);
+        gather_x<W>(xn, S, x, ldx, cn);
+      }
+      if (zero_e(a.e) || zero_e(xv.e)) continue;
+      term(a, xv, a.s ^ xv.s);
+    }
+  } else {
+    for (int32_t j = 0; j < len && !over; ++j) {
+      const int64_t k = base + (int64_t)j * 32;
+      const int32_t col = S.col[k];
+      Num<W> a, xv;
+      load_stream<W>(a, S.val, S.nslots, k);
+      gather_x<W>(xv, S, x, ldx, col);
+      if (zero_e(a.e) || zero_e(xv.e)) continue;
+      term(a, xv, a.s ^ xv.s);
+    }
+  }
+  if (over) {
+    const int pos = atomicAdd(ovf, 1);
+    ovf[1 + pos] = (int32_t)slot;
+    return;
+  }
+  Num<W> r;
+  if (emin > emax) {  // no terms
+    set_zero(r, 0u);
+    store<W>(r, y, ldy, row);
+    return;
+  }
+  // digits below d0 hold nothing: resolve from d0, whose weight is 2^(lo - 2p)
+  const int d0 = (int)((emin - eb) / R);
+  const int64_t lo = eb + (int64_t)R * d0;
+  int64_t* c0 = c + d0 * stride;
+  if (COLS) {
+    int nw = 0;
+    const uint32_t negative = resolve_cols(c0, stride, digits_cols(emax - lo, W), &nw);
+    round_words<W>(c0, stride, nw, lo - 64 * W, negative, r);
+  } else {
+    const int nd = digits_for(emax - lo, W);
+    const uint32_t negative = resolve_digits(c0, stride, nd);
+    if (negative) negate_words(c0, stride, nd);
+    round_words<W>(c0, stride, nd, lo - 64 * W, negative, r);
+  }
+  store<W>(r, y, ldy, row);
+}
+
 template <int W, bool RESID, bool COLS, bool PIPE = Pipelined<W>::value || COLS, int G = 8>
 __global__ void __launch_bounds__(256) spmv_exact_kernel(
     const SellView S, const uint64_t* __restrict__ x, int64_t ldx, uint64_t* __restrict__ y,
@@ -304,7 +411,11 @@ __global__ void __launch_bounds__(256) spmv_exact_kernel(
   const int32_t len = S.row_len[slot];
   const int64_t base = S.chunk_off[chunk] + lane;
 
-  // pass 1: exponent range of the nonzero terms
+  if constexpr (!RESID) {
+    exact_row_one_pass<W, COLS, PIPE, G>(S, x, ldx, y, ldy, ovf, slot, row, len, base);
+    return;
+  }
+  // the residual: pass 1, the exponent range of the nonzero terms
   int64_t emin = LLONG_MAX, emax = LLONG_MIN;
   Num<W> b;
   if (RESID) {
@@ -565,12 +676,14 @@ __global__ void __launch_bounds__(G == 4 ? 128 : 256, G == 4 ? 4 : 1) spmv_exact
 }
 
 // Rows from the overflow list: one warp per row, lanes over the row's
-// entries, a shared window of the full span cap filled with atomics.
+// entries, a shared window of the full span cap filled with atomics.  A row
+// whose terms span more than the cap gives +0 and MP_ERR_SPAN (the one-pass
+// form sends rows here without measuring their span).
 template <int W, bool RESID>
 __global__ void __launch_bounds__(32) spmv_exact_wide_kernel(
     const SellView S, const uint64_t* __restrict__ x, int64_t ldx, uint64_t* __restrict__ y,
     int64_t ldy, const uint64_t* __restrict__ bv, int64_t ldb, const int32_t* __restrict__ ovf,
-    const int* __restrict__ gate) {
+    int* __restrict__ status, const int* __restrict__ gate) {
   __shared__ int64_t acc[Win<W>::cap];
   if (gate && *gate) return;
   const int count = ovf[0];
@@ -582,11 +695,11 @@ __global__ void __launch_bounds__(32) spmv_exact_wide_kernel(
     const int32_t row = S.row_of[slot];
     const int32_t len = S.row_len[slot];
     const int64_t base = S.chunk_off[chunk] + t;
-    int64_t emin = LLONG_MAX;
+    int64_t emin = LLONG_MAX, emax = LLONG_MIN;
     Num<W> b;
     if (RESID) {
       load<W>(b, bv, ldb, row);
-      if (!zero_e(b.e)) emin = b.e;
+      if (!zero_e(b.e)) emin = emax = b.e;
     }
     for (int32_t j = lane; j < len; j += 32) {
       const int64_t k = base + (int64_t)j * 32;
@@ -594,10 +707,26 @@ __global__ void __launch_bounds__(32) spmv_exact_wide_kernel(
       uint32_t sa, sx;
       unpack_head(__ldg(S.val + k), ea, sa);
       unpack_head(__ldg(x + S.col[k]), ex, sx);
-      if (!zero_e(ea) && !zero_e(ex)) emin = min(emin, ea + ex);
+      if (!zero_e(ea) && !zero_e(ex)) {
+        emin = min(emin, ea + ex);
+        emax = max(emax, ea + ex);
+      }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) emin = min(emin, __shfl_xor_sync(0xffffffffu, emin, o));
+    for (int o = 16; o > 0; o >>= 1) {
+      emin = min(emin, __shfl_xor_sync(0xffffffffu, emin, o));
+      emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+    }
+    if (emin > emax || emax - emin > SPAN_CAP) {  // no terms (y = +0), or beyond the cap
+      if (lane == 0) {
+        Num<W> z;
+        set_zero(z, 0u);
+        store<W>(z, y, ldy, row);
+        if (emin <= emax) record_status(status, MP_ERR_SPAN);
+      }
+      __syncwarp();
+      continue;
+    }
     for (int d = lane; d < Win<W>::cap; d += 32) acc[d] = 0;
     __syncwarp();
     uint32_t P[2 * W];
@@ -771,7 +900,8 @@ mp_status spmv_w(const mp_csr_s* M, const Sell& S, int mode, const uint64_t* x, 
   if (b) {
     r = cols ? exact(spmv_exact_kernel<W, true, true>, b) : exact(spmv_exact_kernel<W, true, false>, b);
     if (r != MP_OK) return r;
-    spmv_exact_wide_kernel<W, true><<<sms * 4, 32, 0, st>>>(V, x, ldx, y, ldy, b, ldb, M->ovf, gate);
+    spmv_exact_wide_kernel<W, true><<<sms * 4, 32, 0, st>>>(V, x, ldx, y, ldy, b, ldb, M->ovf,
+                                                            status, gate);
   } else {
     const bool stage = cf.stage, wide = cf.wide;
     auto launch_top = [&](auto kern) -> mp_status {
@@ -807,7 +937,7 @@ mp_status spmv_w(const mp_csr_s* M, const Sell& S, int mode, const uint64_t* x, 
       r = exact(spmv_exact_kernel<W, false, true, false, 8>, nullptr);
     if (r != MP_OK) return r;
     spmv_exact_wide_kernel<W, false><<<sms * 4, 32, 0, st>>>(V, x, ldx, y, ldy, nullptr, 0,
-                                                             M->ovf, gate);
+                                                             M->ovf, status, gate);
   }
   count_launch(2);
   return launch_check("spmv_exact_kernel");

@@ -114,3 +114,38 @@ def test_batch_matrix_configuration_keeps_results():
     M.close()  # a borrowed handle: closing it must not free the batch's matrix
     x3, _ = mpk.batch_gpbicg(B, b, rtol=1e-25, maxit=200, mode="ordered")
     assert torch.equal(x3.t.cpu(), x0.t.cpu())
+
+
+def test_batch_time_limit_ends_the_device_loop():
+    """time_limit_ms on the batched solve: instances still running when an
+    iteration ends past the limit stop with MP_ERR_TIMEOUT, each holding the
+    iterate the oracle reaches in the same number of iterations (it reports
+    NC there); instances that finished before keep their own status."""
+    mpk = need_gpu()
+    import torch
+
+    p = 512
+    systems = [synth.stencil2d(24, seed=11), synth.stencil2d(3, seed=12)]
+    plan = [(0, 1.0), (1, 1.0), (0, 2.0)]
+    inst = [systems[i] for i, _ in plan]
+    B = mpk.Batch(inst, p)
+    b = mpk.Vec.zeros(B.n, p)
+    rhs = _rhs(systems, plan, p)
+    for k, bk in enumerate(rhs):
+        o0, o1 = int(B.offsets[k]), int(B.offsets[k + 1])
+        b.t[:, o0:o1] = torch.from_numpy(np.ascontiguousarray(bk.T).view(np.int64)).to(b.t.device)
+    x, infos = mpk.batch_gpbicg(B, b, rtol=1e-300, maxit=100_000, time_limit_ms=1)
+    statuses = [i["status"] for i in infos]
+    assert 8 in statuses  # MP_ERR_TIMEOUT
+    for k, ((i, _), bk) in enumerate(zip(plan, rhs)):
+        rp, ci, va = systems[i]
+        n = len(rp) - 1
+        it = infos[k]["iters"]
+        xo, ito, sto, _ = oracle.gpbicg(p, oracle.ORDERED, rp, ci, oracle.from_f64(p, va), bk,
+                                        oracle.empty(p, n), 1e-300, 0.0, max(it, 0))
+        if infos[k]["status"] == 8:
+            assert it >= 1 and (ito, sto) == (it, oracle.ERR_NOCONV)
+        else:
+            assert (ito, sto) == (it, infos[k]["status"])
+        o0, o1 = int(B.offsets[k]), int(B.offsets[k + 1])
+        assert_bitwise(x.t[:, o0:o1].cpu().numpy().view(np.uint64), xo, f"instance {k}")

@@ -144,12 +144,13 @@ def test_transposed_solve_matches_the_oracle_on_the_transpose(name):
     assert_bitwise(info["history"].planes(), hist, f"{name} transpose history")
 
 
-@pytest.mark.parametrize("after", (0, 2))
+@pytest.mark.parametrize("after", (0, 1))
 def test_failed_state_read_returns_cuda_status_and_releases_work_memory(after):
-    """A CUDA failure while the host reads the solver's device state (made on
-    the host by the library's fault hook: nothing faults on the GPU) returns
-    MP_ERR_CUDA and gives back the solve's graph, events, stream and work
-    memory; the next solve is unaffected and still matches the oracle."""
+    """A CUDA failure while the host reads the solver's device state (after
+    the first iteration, after = 0; after the device-side loop, after = 1;
+    made on the host by the library's fault hook: nothing faults on the GPU)
+    returns MP_ERR_CUDA and gives back the solve's graph, events, stream and
+    work memory; the next solve is unaffected and still matches the oracle."""
     import ctypes
     import torch
 
@@ -182,3 +183,36 @@ def test_failed_state_read_returns_cuda_status_and_releases_work_memory(after):
                                   oracle.empty(p, n), 1e-40, 0.0, 200)
     assert (info["iters"], info["status"]) == (it, st) == (it, oracle.OK)
     assert_bitwise(x.planes(), xo, "x after the failed solve")
+
+
+@pytest.mark.parametrize("name", ("gpbicg", "bicg"))
+def test_time_limit_ends_the_device_loop(name):
+    """time_limit_ms: the device-side loop ends with MP_ERR_TIMEOUT once an
+    iteration finishes past the limit (a 1 ms limit on a solve that needs
+    far longer); x holds that iterate, equal to the oracle's after the same
+    number of iterations; the next solve without a limit is unaffected."""
+    import torch
+
+    mpk = need_gpu()
+    p = 1024
+    rowptr, colidx, v64 = synth.stencil2d(40, seed=0)
+    n = len(rowptr) - 1
+    vals = oracle.from_f64(p, v64)
+    b, _ = oracle.spmv(p, oracle.EXACT, rowptr, colidx, vals, oracle.from_f64(p, np.ones(n)))
+    A = mpk.CSR(rowptr, colidx, v64, p, transpose=True)
+    bv = mpk.Vec.from_planes(synth.records_to_planes(b), p)
+    fn = getattr(mpk, name)
+    x, info = fn(A, bv, rtol=1e-300, maxit=100_000, time_limit_ms=1)
+    assert info["status"] == 8  # MP_ERR_TIMEOUT
+    it = info["iters"]
+    assert 1 <= it < 100_000
+    xo, ito, sto, _ = SOLVERS[name](p, oracle.ORDERED, rowptr, colidx, vals, b,
+                                    oracle.empty(p, n), 1e-300, 0.0, it)
+    assert (ito, sto) == (it, oracle.ERR_NOCONV)
+    assert_bitwise(x.planes(), xo, "x at the time limit")
+    torch.cuda.synchronize()
+    x2, info2 = fn(A, bv, rtol=1e-30, maxit=5000)
+    xo2, it2, st2, _ = SOLVERS[name](p, oracle.ORDERED, rowptr, colidx, vals, b,
+                                     oracle.empty(p, n), 1e-30, 0.0, 5000)
+    assert (info2["iters"], info2["status"]) == (it2, st2)
+    assert_bitwise(x2.planes(), xo2, "x after the timed-out solve")
