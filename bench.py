@@ -86,12 +86,13 @@ def measured_peaks():
 
 
 def kernel_source_hash():
-    """Hash of the SpMV kernel sources (recorded with each ncu capture)."""
+    """Hash of the SpMV kernel sources and of the layout builder that orders
+    their work (recorded with each ncu capture)."""
     import hashlib
 
     csrc = os.path.join(ROOT, "paper_1411_2377_gb300", "csrc")
     parts = [hashlib.sha256(open(os.path.join(csrc, f), "rb").read()).hexdigest()
-             for f in ("spmv.cu", "mpdev.cuh", "chains.cuh")]
+             for f in ("spmv.cu", "mpdev.cuh", "chains.cuh", "csr.cu")]
     return hashlib.sha256("".join(parts).encode()).hexdigest()[:16]
 
 

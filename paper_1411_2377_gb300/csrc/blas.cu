@@ -27,7 +27,7 @@ mp_status dot_w(const DotArgs& args, void* scratch, const int* gate, cudaStream_
   }
   int* status = status_word();
   if (!status) return set_error(MP_ERR_CUDA, "status word unavailable");
-  return dot_launch<W>(a, scratch, dot_blocks(args.n), status, gate, st);
+  return dot_launch<W>(a, scratch, dot_blocks<W>(args.n), status, gate, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -158,13 +158,13 @@ __global__ void to_f64_kernel(const uint64_t* __restrict__ a, int64_t n, int64_t
 }  // namespace
 
 size_t dot_scratch_bytes(int prec, int k) {
-  const int nb = dot_blocks(int64_t(1) << 40);  // the largest grid
+  const int64_t big = int64_t(1) << 40;  // the largest grid
   const int kk = k < 1 ? 1 : k;
   switch (prec) {
-    case 128: return dot_scratch_size<4>(kk, nb);
-    case 256: return dot_scratch_size<8>(kk, nb);
-    case 512: return dot_scratch_size<16>(kk, nb);
-    default: return dot_scratch_size<32>(kk, nb);
+    case 128: return dot_scratch_size<4>(kk, dot_blocks<4>(big));
+    case 256: return dot_scratch_size<8>(kk, dot_blocks<8>(big));
+    case 512: return dot_scratch_size<16>(kk, dot_blocks<16>(big));
+    default: return dot_scratch_size<32>(kk, dot_blocks<32>(big));
   }
 }
 

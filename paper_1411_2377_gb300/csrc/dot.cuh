@@ -1,8 +1,10 @@
 // dot.cuh -- exact dot products (the inner products (.,.) of Fig. 5) in two
 // kernels, shared by mp_dot, mp_dot_noalloc and the solvers.
 //
-//  1. accumulate: each block first finds the exponent range [lo_b, hi_b] of
-//     e_x + e_y over its own nonzero pairs, anchors its digit grid at
+//  1. accumulate (a grid of nblocks x k: blockIdx.y is the dot, so the k
+//     dots of a group run at once): each block first finds the exponent
+//     range [lo_b, hi_b] of e_x + e_y over its own nonzero pairs (for its
+//     dot), anchors its digit grid at
 //     a_b = lo_b rounded down to a multiple of 32, and adds the exact 2p-bit
 //     products into per-thread windows of 64-bit signed counters in shared
 //     memory (digit-major, so a warp's accesses hit 32 banks; no atomics, no
@@ -12,10 +14,12 @@
 //     shared-memory atomics instead.
 //  2. finalize: one block per dot takes the global range (min of the lo_b,
 //     max of the hi_b: the span cap is checked on it), anchors at A = lo
-//     rounded down to a multiple of 32, sums the partials per global digit
-//     (block b's digit d is global digit d + (a_b - A)/32: whole digits, so
-//     the sum is exact integer addition in any order), resolves carries and
-//     rounds once.
+//     rounded down to a multiple of 32, and adds each block's partial into a
+//     shared window at the block's digit offset (block b's digit d is global
+//     digit d + (a_b - A)/32: whole digits; all threads stride over the
+//     (block, digit) pairs, reading each block's digits coalesced, and add
+//     them with 64-bit shared atomics -- exact integer addition, so the order
+//     does not matter), resolves carries and rounds once.
 // The last finalize block to finish (an arrival counter; nothing waits) can
 // run a caller-supplied step on the results -- the solvers' scalar
 // recurrences -- so that a solver iteration needs no separate scalar launch.
@@ -56,14 +60,16 @@ struct DotDev {
 };
 
 // Scratch layout: a 16-word head (word 0: the finalize's arrival counter),
-// then per (dot, block) the range lo/hi, then the partials [k][cap][nblocks].
+// then per (dot, block) the range lo/hi, then the partials [k][nblocks][cap]
+// (block-major: a block's digits are contiguous, read coalesced by the
+// finalize whatever the block's digit offset).
 constexpr int kDotHeadWords = 16;
 
 struct DotScratch {
   int* arrive;
   long long* lo;      // [5][nblocks]
   long long* hi;      // [5][nblocks]
-  int64_t* partials;  // [5][cap][nblocks]
+  int64_t* partials;  // [5][nblocks][cap]
   int nblocks;
 };
 
@@ -131,7 +137,8 @@ __global__ void __launch_bounds__(kDotThreads) dot_accum_kernel(const DotDev a, 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nb = s.nblocks;
   int64_t* c = dsm + threadIdx.x;
-  for (int j = 0; j < a.k; ++j) {
+  const int j = blockIdx.y;  // the dot this block works on
+  {
     // this block's exponent range of the nonzero pairs (heads only)
     long long lo = LLONG_MAX, hi = LLONG_MIN;
     for (int64_t i = blockIdx.x * (int64_t)kDotThreads + threadIdx.x; i < a.n;
@@ -151,10 +158,10 @@ __global__ void __launch_bounds__(kDotThreads) dot_accum_kernel(const DotDev a, 
     }
     // nothing to add, or a range the finalize rejects (the global span is
     // at least this block's): no partial is written or read
-    if (!(lo <= hi && hi - lo <= SPAN_CAP)) continue;  // block-uniform
+    if (!(lo <= hi && hi - lo <= SPAN_CAP)) return;  // block-uniform
     const long long anchor = (lo >> 5) * 32;            // lo rounded down to a multiple of 32
     const int nd = dot_digits(hi - anchor, W);
-    int64_t* part = s.partials + (size_t)j * CAP * nb;
+    int64_t* part = s.partials + ((size_t)j * nb + blockIdx.x) * CAP;
     if (hi - anchor > kDotFastSpan) {
       // a span beyond the per-thread windows: one block-wide window with
       // shared-memory atomics (rare: the solvers' vectors stay well inside)
@@ -177,9 +184,8 @@ __global__ void __launch_bounds__(kDotThreads) dot_accum_kernel(const DotDev a, 
         }
       }
       __syncthreads();
-      for (int d = threadIdx.x; d < nd; d += kDotThreads) part[(size_t)d * nb + blockIdx.x] = acc[d];
-      __syncthreads();
-      continue;
+      for (int d = threadIdx.x; d < nd; d += kDotThreads) part[d] = acc[d];
+      return;
     }
     for (int d = 0; d < nd; ++d) c[d * kDotThreads] = 0;
     for (int64_t i = blockIdx.x * (int64_t)kDotThreads + threadIdx.x; i < a.n;
@@ -201,22 +207,22 @@ __global__ void __launch_bounds__(kDotThreads) dot_accum_kernel(const DotDev a, 
 #pragma unroll
       for (int u = 0; u < kDotThreads / 32; ++u) t += dsm[d * kDotThreads + u * 32 + lane];
       t = warp_sum64(t);
-      if (lane == 0) part[(size_t)d * nb + blockIdx.x] = t;
+      if (lane == 0) part[d] = t;
     }
-    __syncthreads();
   }
 }
 
-// The finalize kernel's default: no step after the dots.
+// The finalize kernel's default: no step after the dots.  A step is called
+// by the 32 threads of the last block's first warp with their lane index.
 struct NoPost {
-  __device__ void operator()() const {}
+  __device__ void operator()(int) const {}
 };
 
 // One block per dot: the global range from the blocks' ranges, the span cap,
 // the partials summed per global digit, carries resolved, one rounding.  The
-// block that finishes last then runs post() on thread 0 (the results of all
-// blocks are visible to it: each block fences its result before it counts
-// itself in; post() must read them with loads that bypass L1).
+// block that finishes last then runs post(lane) on its first warp (the
+// results of all blocks are visible to it: each block fences its result
+// before it counts itself in; post must read them with loads that bypass L1).
 template <int W, class Post = NoPost>
 __global__ void __launch_bounds__(256) dot_finalize_kernel(const DotDev a, DotScratch s,
                                                            int* __restrict__ status,
@@ -224,9 +230,10 @@ __global__ void __launch_bounds__(256) dot_finalize_kernel(const DotDev a, DotSc
                                                            Post post) {
   constexpr int CAP = DotWin<W>::cap;
   __shared__ int64_t sum[CAP];
-  __shared__ int off_of[kDotMaxBlocks];  // block b's digit offset, -1: no partial
-  __shared__ int nd_of[kDotMaxBlocks];
   __shared__ long long red[64];
+  __shared__ int off_of[kDotMaxBlocks];  // block b's digit offset (its nd_of[b] = 0: no partial)
+  __shared__ int nd_of[kDotMaxBlocks];
+  __shared__ int ndmax;
   if (gate && *gate) return;
   const int j = blockIdx.x, nb = s.nblocks;
   const long long* blo = s.lo + (size_t)j * nb;
@@ -242,28 +249,32 @@ __global__ void __launch_bounds__(256) dot_finalize_kernel(const DotDev a, DotSc
   if (lo <= hi && hi - lo <= SPAN_CAP) {
     const long long A = (lo >> 5) * 32;
     const int nd = dot_digits(hi - A, W);
+    if (threadIdx.x == 0) ndmax = 0;
+    for (int d = threadIdx.x; d < nd; d += blockDim.x) sum[d] = 0;
+    __syncthreads();
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
       const long long l = blo[b], h = bhi[b];
-      if (l <= h) {
+      int ndb = 0, off = 0;
+      if (l <= h) {  // else no nonzero pairs in that block
         const long long ab = (l >> 5) * 32;
-        off_of[b] = (int)((ab - A) >> 5);
-        nd_of[b] = dot_digits(h - ab, W);
-      } else {
-        off_of[b] = -1;
-        nd_of[b] = 0;
+        off = (int)((ab - A) >> 5);
+        ndb = dot_digits(h - ab, W);
       }
+      off_of[b] = off;
+      nd_of[b] = ndb;
+      atomicMax(&ndmax, ndb);
     }
     __syncthreads();
-    const int64_t* part = s.partials + (size_t)j * CAP * nb;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (int g = warp; g < nd; g += nwarps) {
-      int64_t t = 0;
-      for (int b = lane; b < nb; b += 32) {
-        const int d = g - off_of[b];
-        if (off_of[b] >= 0 && d >= 0 && d < nd_of[b]) t += part[(size_t)d * nb + b];
-      }
-      t = warp_sum64(t);
-      if (lane == 0) sum[g] = t;
+    // every (block, digit) pair: block b's digit d enters global digit
+    // d + off_of[b] by a shared 64-bit atomic add (integer: any order);
+    // consecutive items are consecutive digits of one block (coalesced)
+    const int m = ndmax;
+    const int64_t* part = s.partials + (size_t)j * nb * CAP;
+    for (int q = threadIdx.x; q < nb * m; q += blockDim.x) {
+      const int b = q / m, d = q - b * m;
+      if (d < nd_of[b])
+        atomicAdd(reinterpret_cast<unsigned long long*>(&sum[off_of[b] + d]),
+                  (unsigned long long)part[(size_t)b * CAP + d]);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -276,14 +287,17 @@ __global__ void __launch_bounds__(256) dot_finalize_kernel(const DotDev a, DotSc
   }
   if (threadIdx.x == 0) store<W>(r, a.out[j], a.out_ld[j], 0);
   if constexpr (!std::is_same<Post, NoPost>::value) {
+    __shared__ int is_last;
     if (threadIdx.x == 0) {
       __threadfence();
-      if (atomicAdd(s.arrive, 1) == (int)gridDim.x - 1) {
+      is_last = atomicAdd(s.arrive, 1) == (int)gridDim.x - 1;
+      if (is_last) {
         atomicExch(s.arrive, 0);
         __threadfence();
-        post();
       }
     }
+    __syncthreads();
+    if (is_last && threadIdx.x < 32) post((int)threadIdx.x);
   }
 }
 
@@ -300,11 +314,22 @@ inline int dot_sm_count() {
   return sms > 0 ? sms : 1;
 }
 
-// Blocks of the accumulate kernel: one per 128 elements, at most 4 per SM.
+// Blocks of the accumulate kernel: one per 128 elements, at most one wave
+// of resident blocks (as many per SM as their digit windows fit in its
+// shared memory, at most 4): more blocks would only add partials for the
+// finalize to merge.
+template <int W>
 inline int dot_blocks(int64_t n) {
-  int64_t b = (n + kDotThreads - 1) / kDotThreads;
-  int64_t lim = (int64_t)dot_sm_count() * 4;
+  int dev = 0, smem_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  const size_t per_block =
+      dot_smem<W>() + sizeof(int64_t) * DotWin<W>::cap + sizeof(long long) * 64 + 1024;
+  int fit = smem_sm > 0 ? (int)((size_t)smem_sm / per_block) : 1;
+  fit = fit < 1 ? 1 : (fit > 4 ? 4 : fit);
+  int64_t lim = (int64_t)dot_sm_count() * fit;
   if (lim > kDotMaxBlocks) lim = kDotMaxBlocks;
+  int64_t b = (n + kDotThreads - 1) / kDotThreads;
   if (b > lim) b = lim;
   if (b < 1) b = 1;
   return (int)b;
@@ -322,7 +347,7 @@ mp_status dot_launch(const DotDev& a, void* scratch, int nblocks, int* status, c
   // streamed operands: shared memory for the windows matters more than L1
   MPK_CUDA(cudaFuncSetAttribute(dot_accum_kernel<W>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                 (int)cudaSharedmemCarveoutMaxShared));
-  dot_accum_kernel<W><<<nblocks, kDotThreads, smem, st>>>(a, s, gate);
+  dot_accum_kernel<W><<<dim3(nblocks, a.k), kDotThreads, smem, st>>>(a, s, gate);
   dot_finalize_kernel<W, Post><<<a.k, 256, 0, st>>>(a, s, status, gate, post);
   count_launch(2);
   return launch_check("dot kernels");

@@ -177,35 +177,45 @@ __device__ void s_zeta1(SState* st, uint64_t* S) {
 }
 
 // tau = mu5 mu1 - mu4 mu4; zeta = (mu1 mu2 - mu3 mu4)/tau;
-// eta = (mu5 mu3 - mu4 mu2)/tau; tau = 0 -> zeta = eta = 0.
+// eta = (mu5 mu3 - mu4 mu2)/tau; tau = 0 -> zeta = eta = 0.  Lanes 0-2 of
+// the warp form tau and the two numerators at once (one code path, the
+// operands chosen by lane), then lanes 1 and 2 divide; each value takes the
+// same rounded operations as one thread computing them in turn.
 template <int W>
-__device__ void s_zeta(SState* st, uint64_t* S) {
+__device__ void s_zeta(SState* st, uint64_t* S, int lane) {
+  __shared__ Num<W> part[3];  // tau, zeta's numerator, eta's numerator
   if (st->done) return;
-  Num<W> m1, m2, m3, m4, m5, a, b, c, tau, z;
-  ld_s<W>(m1, S, MU1);
-  ld_s<W>(m4, S, MU4);
-  ld_s<W>(m5, S, MU5);
-  mul_rn<W>(m5, m1, a);
-  mul_rn<W>(m4, m4, b);
-  sub_rn<W>(a, b, tau);
-  if (zero_e(tau.e)) {
-    set_zero(z, 0u);
-    st_s<W>(z, S, ZETA);
-    st_s<W>(z, S, ETA);
-    return;
+  if (lane < 3) {
+    const int i1 = lane == 0 ? MU5 : (lane == 1 ? MU1 : MU5);
+    const int j1 = lane == 0 ? MU1 : (lane == 1 ? MU2 : MU3);
+    const int i2 = lane == 0 ? MU4 : (lane == 1 ? MU3 : MU4);
+    const int j2 = lane == 0 ? MU4 : (lane == 1 ? MU4 : MU2);
+    Num<W> x1, y1, x2, y2, a, b, c;
+    ld_s<W>(x1, S, i1);
+    ld_s<W>(y1, S, j1);
+    ld_s<W>(x2, S, i2);
+    ld_s<W>(y2, S, j2);
+    mul_rn<W>(x1, y1, a);
+    mul_rn<W>(x2, y2, b);
+    sub_rn<W>(a, b, c);
+    part[lane] = c;
   }
-  ld_s<W>(m2, S, MU2);
-  ld_s<W>(m3, S, MU3);
-  mul_rn<W>(m1, m2, a);
-  mul_rn<W>(m3, m4, b);
-  sub_rn<W>(a, b, c);
-  div_rn<W>(c, tau, z);
-  st_s<W>(z, S, ZETA);
-  mul_rn<W>(m5, m3, a);
-  mul_rn<W>(m4, m2, b);
-  sub_rn<W>(a, b, c);
-  div_rn<W>(c, tau, z);
-  st_s<W>(z, S, ETA);
+  __syncwarp();
+  if (lane < 3) {
+    const Num<W> tau = part[0];
+    Num<W> z;
+    if (zero_e(tau.e)) {
+      if (lane == 0) {
+        set_zero(z, 0u);
+        st_s<W>(z, S, ZETA);
+        st_s<W>(z, S, ETA);
+      }
+    } else if (lane > 0) {
+      const Num<W> num = part[lane];
+      div_rn<W>(num, tau, z);
+      st_s<W>(z, S, lane == 1 ? ZETA : ETA);
+    }
+  }
 }
 
 // BiCGSTAB: omega = RN(TS / TT), +0 when TT = (t, t) = 0.
@@ -223,36 +233,34 @@ __device__ void s_omega(SState* st, uint64_t* S) {
   st_s<W>(om, S, OMEGA);
 }
 
-// beta = RN(rho/rho_prev) (BiCG, CGS), or RN(RN(rho/rho_prev) * RN(alpha/d))
-// with d = zeta (GPBiCG) or omega (BiCGSTAB): DIV names d's slot, -1 none.
-template <int W, int DIV>
-__device__ void s_beta(uint64_t* S) {
-  Num<W> rho, rp, q1, a, z, q2, b;
-  ld_s<W>(rho, S, RHO);
-  ld_s<W>(rp, S, RHO_PREV);
-  div_rn<W>(rho, rp, q1);
-  if (DIV >= 0) {
-    ld_s<W>(a, S, ALPHA);
-    ld_s<W>(z, S, DIV);
-    div_rn<W>(a, z, q2);
-    mul_rn<W>(q1, q2, b);
-    st_s<W>(b, S, BETA);
-  } else {
-    st_s<W>(q1, S, BETA);
-  }
-}
-
 // End of an iteration: count it, record (r,r), shift rho, decide the exit.
 // ZX: the scalar whose zero ends the iteration after the convergence test
 // (GPBiCG's zeta, BiCGSTAB's omega), -1 none.  A time limit, when set, ends
 // the solve (MP_ERR_TIMEOUT) once an iteration finishes past it.  When the
-// solve goes on, the next iteration's beta (divisor slot BDIV, -1 none) is
-// formed here: its inputs are final at this point, and the next iteration
-// then starts with its vector update.
+// solve goes on, the next iteration's beta = RN(rho_i/rho_{i-1}) (BiCG,
+// CGS) or RN(RN(rho_i/rho_{i-1}) * RN(alpha/d)) with d = zeta (GPBiCG) or
+// omega (BiCGSTAB) (BDIV names d's slot, -1 none) is formed here: its inputs
+// are final at this point, and the next iteration then starts with its
+// vector update.  Lanes 0 and 1 start beta's two divisions from the slots
+// the check shifts into place (rho_i = RHO_NEW, rho_{i-1} = RHO) while lane 0
+// decides the exit; beta is stored only when the solve goes on.
 template <int W, int ZX, int BDIV>
 __device__ void s_check(SState* st, uint64_t* S, uint64_t* hist, int64_t hist_ld,
-                        int64_t hist_n) {
+                        int64_t hist_n, int lane) {
+  __shared__ Num<W> q[2];
   if (st->done) return;
+  if (lane == 0 || (lane == 1 && BDIV >= 0)) {
+    Num<W> num, den, r;
+    ld_s<W>(num, S, lane == 0 ? RHO_NEW : ALPHA);
+    ld_s<W>(den, S, lane == 0 ? RHO : (BDIV >= 0 ? BDIV : RHO));
+    if (zero_e(den.e))
+      set_zero(r, 0u);  // the solve ends in this check (a zero rho or d): beta is not used
+    else
+      div_rn<W>(num, den, r);
+    q[lane] = r;
+  }
+  __syncwarp();
+  if (lane != 0) return;
   Num<W> rr, thr, rho, rn, z;
   st->iters += 1;
   ld_s<W>(rr, S, RR);
@@ -273,41 +281,53 @@ __device__ void s_check(SState* st, uint64_t* S, uint64_t* hist, int64_t hist_ld
     finish(st, MP_ERR_BREAKDOWN);
   } else if (st->limit_ns != 0 && device_ns() - st->t0 > st->limit_ns) {
     finish(st, MP_ERR_TIMEOUT);
+  } else if (BDIV >= 0) {
+    Num<W> b;
+    mul_rn<W>(q[0], q[1], b);
+    st_s<W>(b, S, BETA);
   } else {
-    s_beta<W, BDIV>(S);
+    st_s<W>(q[0], S, BETA);
   }
 }
 
-// The steps as the dot finalize's post-step functors.
+// The steps as the dot finalize's post-step functors (called by the 32 lanes
+// of one warp; the one-thread steps run on lane 0).
 template <int W>
 struct PostSetup {
   SState* st;
   uint64_t* S;
   double rtol, atol;
-  __device__ void operator()() const { s_setup<W>(st, S, rtol, atol); }
+  __device__ void operator()(int lane) const {
+    if (lane == 0) s_setup<W>(st, S, rtol, atol);
+  }
 };
 template <int W>
 struct PostAlpha {
   SState* st;
   uint64_t* S;
-  __device__ void operator()() const { s_alpha<W>(st, S); }
+  __device__ void operator()(int lane) const {
+    if (lane == 0) s_alpha<W>(st, S);
+  }
 };
 template <int W, bool FIRST>
 struct PostZeta {
   SState* st;
   uint64_t* S;
-  __device__ void operator()() const {
-    if (FIRST)
-      s_zeta1<W>(st, S);
-    else
-      s_zeta<W>(st, S);
+  __device__ void operator()(int lane) const {
+    if (FIRST) {
+      if (lane == 0) s_zeta1<W>(st, S);
+    } else {
+      s_zeta<W>(st, S, lane);
+    }
   }
 };
 template <int W>
 struct PostOmega {
   SState* st;
   uint64_t* S;
-  __device__ void operator()() const { s_omega<W>(st, S); }
+  __device__ void operator()(int lane) const {
+    if (lane == 0) s_omega<W>(st, S);
+  }
 };
 template <int W, int ZX, int BDIV>
 struct PostCheck {
@@ -315,7 +335,9 @@ struct PostCheck {
   uint64_t* S;
   uint64_t* hist;
   int64_t hist_ld, hist_n;
-  __device__ void operator()() const { s_check<W, ZX, BDIV>(st, S, hist, hist_ld, hist_n); }
+  __device__ void operator()(int lane) const {
+    s_check<W, ZX, BDIV>(st, S, hist, hist_ld, hist_n, lane);
+  }
 };
 
 // ---------------------------------------------------------------------------
@@ -713,7 +735,7 @@ mp_status dot2(const Work& w, const uint64_t* a0, const uint64_t* b0, int o0, co
   }
   d.out[0] = w.scal(o0);
   d.out[1] = a1 ? w.scal(o1) : nullptr;
-  return dot_launch<W, Post>(d, w.dscratch, dot_blocks(w.n), w.status, gate, st, post);
+  return dot_launch<W, Post>(d, w.dscratch, dot_blocks<W>(w.n), w.status, gate, st, post);
 }
 
 // The end-of-iteration dots (r, r) and (r~, r) with the convergence check.
@@ -778,9 +800,9 @@ mp_status gp_iteration(const Work& w, const SolveCall& c, bool first) {
     d.x[3] = w.vec(V); d.y[3] = w.vec(Y); d.out[3] = w.scal(MU4);
     d.x[4] = w.vec(V); d.y[4] = w.vec(V); d.out[4] = w.scal(MU5);
   }
-  r = first ? dot_launch<W>(d, w.dscratch, dot_blocks(n), w.status, gate, st,
+  r = first ? dot_launch<W>(d, w.dscratch, dot_blocks<W>(n), w.status, gate, st,
                             PostZeta<W, true>{w.st, w.S})
-            : dot_launch<W>(d, w.dscratch, dot_blocks(n), w.status, gate, st,
+            : dot_launch<W>(d, w.dscratch, dot_blocks<W>(n), w.status, gate, st,
                             PostZeta<W, false>{w.st, w.S});
   if (r != MP_OK) return r;
   Vecs V9{};

@@ -189,3 +189,31 @@ def test_full_size_every_row(p):
             check(f"variant {v}")
         del want
     A.close()
+
+
+@pytest.mark.parametrize("p", (128, 256))
+def test_device_transpose_with_a_long_column_and_unsorted_rows(p):
+    """A and A^T laid out on the device: column 3 holds 600 entries (its row of
+    A^T is longer than one thread sorts, so the host sorts it) and every input
+    row lists its columns in reverse (the host sorts those rows); A x and A^T x
+    bit-identical to the oracle in both modes."""
+    mpk = need_gpu()
+    n = 700
+    rowptr, colidx = random_csr(n, seed=41, mean_len=5, max_len=20)
+    rows = [set(colidx[rowptr[i]:rowptr[i + 1]].tolist()) for i in range(n)]
+    for i in range(600):
+        rows[i].add(3)
+    cols = [sorted(r) for r in rows]
+    rowptr = np.zeros(n + 1, np.int64)
+    rowptr[1:] = np.cumsum([len(c) for c in cols])
+    colidx = np.array([c for r in cols for c in r], np.int32)
+    V = rand_planes(len(colidx), p, 51, zero_frac=0.05)
+    X = rand_planes(n, p, 52, zero_frac=0.0)
+    perm = np.concatenate([np.arange(rowptr[i + 1] - 1, rowptr[i] - 1, -1) for i in range(n)])
+    A = mpk.CSR(rowptr, colidx[perm], V[:, perm], p, transpose=True)
+    x = mpk.Vec.from_planes(X, p)
+    for name, m in MODES:
+        want, _ = oracle.spmv(p, m, rowptr, colidx, recs(V), recs(X))
+        want_t, _ = oracle.spmv_t(p, m, rowptr, colidx, recs(V), recs(X))
+        assert_bitwise(mpk.spmv(A, x, mode=name).planes(), want, f"{name} p={p}")
+        assert_bitwise(mpk.spmv_t(A, x, mode=name).planes(), want_t, f"T {name} p={p}")
