@@ -101,6 +101,55 @@ def test_gradient_vs_512bit_central_differences():
         assert abs(d - LAM[i]) <= Fraction(1, 10 ** 40) * max(abs(v) for v in LAM), i
 
 
+def test_p256_gradient_vs_512bit_central_differences():
+    """The differentiated solve at the precision it is used at (p = 256, 2-D
+    system, L = sum x^2): the adjoint gradient at 32 stored entries and 4
+    entries of b against central differences taken at 512 bits (h = 2^-100,
+    the perturbed systems solved at 512 bits to 1e-140; the 256-bit values
+    and b are exact at 512 bits, so both sides differentiate the same
+    function).  The 256-bit gradient carries about kappa * 2^-256 of relative
+    error, the differences about h^2: both far below the 1e-40 tolerance."""
+    mpk = need_gpu()
+    from paper_1411_2377_gb300 import autograd
+
+    p, q = 256, 512
+    rowptr, colidx, v64, vals, b = _system(16, p, seed=11)
+    n = len(rowptr) - 1
+    nnz = len(colidx)
+    A = mpk.CSR(rowptr, colidx, v64, p, transpose=True)
+    x, _ = autograd.solve(A, mpk.Vec.from_planes(b.T.copy(), p), rtol=1e-70)
+    two = mpk.Vec.from_f64(np.full(n, 2.0), p)
+    lam, g, _ = autograd.adjoint(A, x, mpk.ewise(0, two, x), rtol=1e-70)
+    G = [exact.decode(r, p).q for r in g.records()]
+    LAM = [exact.decode(r, p).q for r in lam.records()]
+    # the same values and b at 512 bits (exact: they have at most 256 bits)
+    vq = np.array([exact.encode(exact.decode(r, p), q) for r in vals], np.uint64)
+    bq = np.array([exact.encode(exact.decode(r, p), q) for r in b], np.uint64)
+    h = Fraction(1, 2 ** 100)
+    ks = np.unique(synth.u64(21, 1, np.arange(32)) % np.uint64(nnz)).astype(np.int64)
+    scale = max(abs(v) for v in G)
+    vr = vq.copy()
+    for k in ks:
+        a = exact.decode(vq[k], q).q
+        fd = []
+        for sgn in (1, -1):
+            vr[k] = exact.encode(exact.Val(a + sgn * h), q)
+            fd.append(_loss(mpk, rowptr, colidx, vr.T.copy(), bq.T.copy(), q, 1e-140))
+        vr[k] = vq[k]
+        d = (fd[0] - fd[1]) / (2 * h)
+        assert abs(d - G[k]) <= Fraction(1, 10 ** 40) * scale, (k, float(d), float(G[k]))
+    br = bq.copy()
+    for i in (0, n // 3, n // 2, n - 1):
+        bi = exact.decode(bq[i], q).q
+        fd = []
+        for sgn in (1, -1):
+            br[i] = exact.encode(exact.Val(bi + sgn * h), q)
+            fd.append(_loss(mpk, rowptr, colidx, vq.T.copy(), br.T.copy(), q, 1e-140))
+        br[i] = bq[i]
+        d = (fd[0] - fd[1]) / (2 * h)
+        assert abs(d - LAM[i]) <= Fraction(1, 10 ** 40) * max(abs(v) for v in LAM), i
+
+
 def test_torch_autograd_function():
     mpk = need_gpu()
     import torch
