@@ -265,7 +265,8 @@ typedef struct {
  * The iteration runs on the device: after the first iteration the host
  * launches one CUDA graph whose conditional while node replays an iteration
  * until the device state says the solve has ended, then reads a few status
- * bytes (p > 1024: a graph replayed poll_every times between host checks).
+ * bytes (p > 1024: the iterations are launched from the host, which reads
+ * the device state every poll_every iterations).
  * Returns info->status.  Needs MP_CSR_TRANSPOSE. */
 mp_status mp_bicg(mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* opts,
                   mp_solve_info* info, void* stream);
@@ -304,8 +305,9 @@ typedef struct mp_ilu_s* mp_ilu; /* opaque; owns its device storage */
  * k < i ascending, l_ik = RN(a_ik / u_kk) and, for each stored (i, j), j > k
  * ascending with (k, j) stored, a_ij = RN(a_ij - RN(l_ik u_kj)).  L (unit
  * lower) and U share A's pattern.  Rows run in dependency levels, one launch
- * per level.  MP_ERR_DIVZERO: a row without a diagonal entry or a zero
- * pivot.  Synchronises `stream`. */
+ * per level (one thread per row at p <= 1024, one warp per row at p = 2048,
+ * 4096, 8192, the precisions of Table 3's converging runs).  MP_ERR_DIVZERO:
+ * a row without a diagonal entry or a zero pivot.  Synchronises `stream`. */
 mp_status mp_ilu0_create(mp_csr A, void* stream, mp_ilu* out);
 mp_status mp_ilu0_destroy(mp_ilu M);
 

@@ -319,6 +319,82 @@ __device__ __forceinline__ void wadd(uint32_t* Y, int64_t& ye, uint32_t& ys, con
   ys = sb ^ (neg ? 1u : 0u);
 }
 
+// q = RN(a / b) for nonzero a, b (mantissas Ma, Mb in shared memory): the
+// quotient Q = floor(N / Mb) of N = Ma 2^(p+2) by schoolbook long division in
+// base 2^32 (Knuth, TAOCP vol. 2, 4.3.1, Algorithm D; Mb has its top bit set,
+// so it needs no normalisation), then S = 2Q + [remainder != 0] rounded once
+// (S carries the exact round and sticky bits; a quotient of two p-bit numbers
+// is never exactly a midpoint).  Each of the W + 2 quotient words: the
+// estimate from the top two words of the running remainder and the divisor's
+// top two words (uniform across the warp), then the remainder window minus
+// the estimate times Mb as signed 64-bit counters (lanes over words),
+// resolved across lanes; a negative window takes Mb back once and the
+// estimate one less.  U (2W + 2 words), C (W + 2 counters), Q (W + 4 words)
+// and S (W + 5 counters) are shared-memory scratch.  Returns the exponent.
+template <int W>
+__device__ int64_t wdiv(const uint32_t* Ma, int64_t ea, const uint32_t* Mb, int64_t eb,
+                        uint32_t* U, int64_t* C, uint32_t* Q, int64_t* S, uint32_t* out, int lane) {
+  constexpr int n = W, m = W + 1, P = 32 * W, NQ = W + 4, NS = W + 5;
+  for (int k = lane; k < 2 * W + 2; k += 32) {  // U = (4 Ma) 2^(32 W)
+    uint32_t v = 0u;
+    if (k >= W && k <= 2 * W) {
+      const int i = k - W;
+      const uint32_t lo = i < W ? Ma[i] : 0u, below = i > 0 ? Ma[i - 1] : 0u;
+      v = (lo << 2) | (below >> 30);
+    }
+    U[k] = v;
+  }
+  for (int k = lane; k < NQ; k += 32) Q[k] = 0u;
+  __syncwarp();
+  const uint32_t v1 = Mb[n - 1], v2 = Mb[n - 2];
+  const uint32_t vinv = (uint32_t)(~uint64_t(0) / v1);  // div2by1's reciprocal of v1
+  for (int j = m; j >= 0; --j) {
+    // estimate from the top two words (the top word never exceeds v1; when
+    // equal the estimate is 2^32 - 1 with remainder U[j+n-1] + v1)
+    uint64_t qh, rh;
+    if (U[j + n] >= v1) {
+      qh = 0xffffffffu;
+      rh = (uint64_t)U[j + n - 1] + v1;
+    } else {
+      uint32_t rr;
+      qh = div2by1(U[j + n], U[j + n - 1], v1, vinv, rr);
+      rh = rr;
+    }
+    while ((rh >> 32) == 0u && qh * v2 > ((rh << 32) | U[j + n - 2])) {
+      qh -= 1;
+      rh += v1;
+    }
+    for (int k = lane; k <= n; k += 32) {
+      const uint64_t t0 = k < n ? qh * Mb[k] : 0ull, t1 = k > 0 ? qh * Mb[k - 1] : 0ull;
+      C[k] = (int64_t)U[j + k] - (int64_t)(uint32_t)t0 - (int64_t)(t1 >> 32);
+    }
+    __syncwarp();
+    const int64_t top = wresolve(C, n + 1, lane);
+    __syncwarp();
+    if (top < 0) {  // the estimate was one too large
+      qh -= 1;
+      for (int k = lane; k < n; k += 32) C[k] += Mb[k];
+      __syncwarp();
+      wresolve(C, n + 1, lane);
+      __syncwarp();
+    }
+    for (int k = lane; k <= n; k += 32) U[j + k] = (uint32_t)C[k];
+    if (lane == 0) Q[j] = (uint32_t)qh;
+    __syncwarp();
+  }
+  bool rnz = false;
+  for (int k = lane; k < n; k += 32) rnz = rnz || U[k] != 0u;
+  const uint32_t sticky = __any_sync(kFull, rnz) ? 1u : 0u;
+  for (int k = lane; k < NS; k += 32) {  // S = 2 Q + sticky
+    const uint32_t lo = (k < NQ) ? Q[k] : 0u, below = (k > 0) ? Q[k - 1] : 0u;
+    S[k] = (int64_t)(uint32_t)((lo << 1) | (below >> 31) | (k == 0 ? sticky : 0u));
+  }
+  __syncwarp();
+  const int B = wtopbit(S, NS, lane);
+  const int inc = wround<W>(S, NS, B, out, lane);
+  return (int64_t)B + 1 + ea - eb - P - 3 + inc;
+}
+
 // acc[q ..] += (-1)^neg * (the 2W words in m.cnt) * 2^off, off = 32q + r.
 template <int W>
 __device__ __forceinline__ void wplace(int64_t* acc, const WarpMem& m, int64_t off, bool neg,

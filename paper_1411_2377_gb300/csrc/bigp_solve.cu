@@ -1,6 +1,8 @@
 // bigp_solve.cu -- BiCG and GPBiCG (Fig. 5, K = I), CGS and BiCGSTAB (the
 // other product-type methods of Tables 1-2, textbook forms) at p = 2048,
-// 4096, 8192, the precisions at which the paper's solves converge.
+// 4096, 8192, the precisions at which the paper's solves converge; BiCGSTAB
+// also with ILU(0) (bigp_ilu.cu) as the left preconditioner of Section 4.2
+// and Table 3, or as a right one.
 //
 // Same readings and operation order as the p <= 1024 drivers: r0 = RN(b - A x0)
 // row by row exactly, r~ = r0, exact inner products, every vector update
@@ -154,82 +156,6 @@ struct SProg {
   int n;
   double f[2];
 };
-
-// q = RN(a / b) for nonzero a, b (mantissas Ma, Mb in shared memory): the
-// quotient Q = floor(N / Mb) of N = Ma 2^(p+2) by schoolbook long division in
-// base 2^32 (Knuth, TAOCP vol. 2, 4.3.1, Algorithm D; Mb has its top bit set,
-// so it needs no normalisation), then S = 2Q + [remainder != 0] rounded once
-// (S carries the exact round and sticky bits; a quotient of two p-bit numbers
-// is never exactly a midpoint).  Each of the W + 2 quotient words: the
-// estimate from the top two words of the running remainder and the divisor's
-// top two words (uniform across the warp), then the remainder window minus
-// the estimate times Mb as signed 64-bit counters (lanes over words),
-// resolved across lanes; a negative window takes Mb back once and the
-// estimate one less.  U (2W + 2 words), C (W + 2 counters), Q (W + 4 words)
-// and S (W + 5 counters) are shared-memory scratch.  Returns the exponent.
-template <int W>
-__device__ int64_t wdiv(const uint32_t* Ma, int64_t ea, const uint32_t* Mb, int64_t eb,
-                        uint32_t* U, int64_t* C, uint32_t* Q, int64_t* S, uint32_t* out, int lane) {
-  constexpr int n = W, m = W + 1, P = 32 * W, NQ = W + 4, NS = W + 5;
-  for (int k = lane; k < 2 * W + 2; k += 32) {  // U = (4 Ma) 2^(32 W)
-    uint32_t v = 0u;
-    if (k >= W && k <= 2 * W) {
-      const int i = k - W;
-      const uint32_t lo = i < W ? Ma[i] : 0u, below = i > 0 ? Ma[i - 1] : 0u;
-      v = (lo << 2) | (below >> 30);
-    }
-    U[k] = v;
-  }
-  for (int k = lane; k < NQ; k += 32) Q[k] = 0u;
-  __syncwarp();
-  const uint32_t v1 = Mb[n - 1], v2 = Mb[n - 2];
-  const uint32_t vinv = (uint32_t)(~uint64_t(0) / v1);  // div2by1's reciprocal of v1
-  for (int j = m; j >= 0; --j) {
-    // estimate from the top two words (the top word never exceeds v1; when
-    // equal the estimate is 2^32 - 1 with remainder U[j+n-1] + v1)
-    uint64_t qh, rh;
-    if (U[j + n] >= v1) {
-      qh = 0xffffffffu;
-      rh = (uint64_t)U[j + n - 1] + v1;
-    } else {
-      uint32_t rr;
-      qh = div2by1(U[j + n], U[j + n - 1], v1, vinv, rr);
-      rh = rr;
-    }
-    while ((rh >> 32) == 0u && qh * v2 > ((rh << 32) | U[j + n - 2])) {
-      qh -= 1;
-      rh += v1;
-    }
-    for (int k = lane; k <= n; k += 32) {
-      const uint64_t t0 = k < n ? qh * Mb[k] : 0ull, t1 = k > 0 ? qh * Mb[k - 1] : 0ull;
-      C[k] = (int64_t)U[j + k] - (int64_t)(uint32_t)t0 - (int64_t)(t1 >> 32);
-    }
-    __syncwarp();
-    const int64_t top = wresolve(C, n + 1, lane);
-    __syncwarp();
-    if (top < 0) {  // the estimate was one too large
-      qh -= 1;
-      for (int k = lane; k < n; k += 32) C[k] += Mb[k];
-      __syncwarp();
-      wresolve(C, n + 1, lane);
-      __syncwarp();
-    }
-    for (int k = lane; k <= n; k += 32) U[j + k] = (uint32_t)C[k];
-    if (lane == 0) Q[j] = (uint32_t)qh;
-    __syncwarp();
-  }
-  bool rnz = false;
-  for (int k = lane; k < n; k += 32) rnz = rnz || U[k] != 0u;
-  const uint32_t sticky = __any_sync(kFull, rnz) ? 1u : 0u;
-  for (int k = lane; k < NS; k += 32) {  // S = 2 Q + sticky
-    const uint32_t lo = (k < NQ) ? Q[k] : 0u, below = (k > 0) ? Q[k - 1] : 0u;
-    S[k] = (int64_t)(uint32_t)((lo << 1) | (below >> 31) | (k == 0 ? sticky : 0u));
-  }
-  __syncwarp();
-  const int B = wtopbit(S, NS, lane);
-  const int inc = wround<W>(S, NS, B, out, lane);
-  return (int64_t)B + 1 + ea - eb - P - 3 + inc;
-}
 
 // -1, 0, 1 as a - b (zeros of either sign equal), mantissas in shared memory.
 template <int W>
@@ -470,7 +396,7 @@ double rec_to_double(const uint64_t* rec, int L) {
 
 template <int W>
 mp_status solve_big_w(int method, mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* o,
-                      mp_solve_info* info, cudaStream_t st) {
+                      mp_solve_info* info, cudaStream_t st, const mp_ilu_s* pre, int pre_left) {
   constexpr int L = W / 2;
   const int64_t n = A->n;
   Solver<W> s;
@@ -484,7 +410,9 @@ mp_status solve_big_w(int method, mp_csr A, mp_vec b, mp_vec x, const mp_solve_o
   s.hist = o->history.data;
   s.hist_ld = o->history.ld;
   static const int kVecs[4] = {7, 13, 10, 8};  // BiCG, GPBiCG, CGS, BiCGSTAB
-  const int nvec = kVecs[method];                // the last one holds the iterate
+  // the last one holds the iterate; an ILU(0) preconditioner adds two
+  const int nvec = kVecs[method] + (pre ? 2 : 0);
+  const bool left = pre && pre_left;
   const size_t vbytes = sizeof(uint64_t) * (L + 1) * (size_t)s.ld;
   uint64_t* V = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -524,10 +452,13 @@ mp_status solve_big_w(int method, mp_csr A, mp_vec b, mp_vec x, const mp_solve_o
     };
     uint64_t *rv = vec(0), *rt = vec(1), *pv = vec(2), *xw = vec(nvec - 1);
     if ((r = copy(xw, s.ld, x.data, x.ld)) != MP_OK) break;  // the iterate, ld = n
-    // r0 = RN(b - A x0) row by row exactly, r~ = r0
-    if ((r = launch_spmv_big(A, *s.SA, MP_EXACT, x.data, x.ld, rv, s.ld, b.data, b.ld, s.gate(),
+    // r0 = RN(b - A x0) row by row exactly, r~ = r0; with a left
+    // preconditioner r0 = K^{-1} RN(b - A x0), the residual formed in vec(7)
+    uint64_t* r0 = left ? vec(7) : rv;
+    if ((r = launch_spmv_big(A, *s.SA, MP_EXACT, x.data, x.ld, r0, s.ld, b.data, b.ld, s.gate(),
                              st)) != MP_OK)
       break;
+    if (left && (r = launch_ilu0_apply(pre, r0, s.ld, rv, s.ld, s.gate(), st)) != MP_OK) break;
     if ((r = copy(rt, s.ld, rv, s.ld)) != MP_OK) break;
     if ((r = s.dot(rv, rv, RR0)) != MP_OK) break;
     {
@@ -589,6 +520,10 @@ mp_status solve_big_w(int method, mp_csr A, mp_vec b, mp_vec x, const mp_solve_o
         if ((r = s.lin(rv, rv, aw, ALPHA, kNegB)) != MP_OK) break;  // r = r - alpha A w
       } else if (method == 3) {  // BiCGSTAB (textbook form, the oracle's reading)
         uint64_t *v = vec(3), *sv = vec(4), *t = vec(5), *tmp = vec(6);
+        // ILU(0): right, v = A K^{-1} p and t = A K^{-1} s with x taking
+        // K^{-1} p and K^{-1} s; left, v = K^{-1} A p and t = K^{-1} A s
+        // (vec(7) and vec(8) hold K^{-1} p, K^{-1} s or A p, A s)
+        uint64_t *ph = pre ? vec(7) : nullptr, *sh = pre ? vec(8) : nullptr;
         Prog p0;
         p0.add(kBrkZ, 0, RHO);
         if (i > 1)
@@ -600,20 +535,32 @@ mp_status solve_big_w(int method, mp_csr A, mp_vec b, mp_vec x, const mp_solve_o
           if ((r = s.lin(tmp, pv, v, OMEGA, kNegB)) != MP_OK) break;  // p - omega v
           if ((r = s.lin(pv, rv, tmp, BETA, 0)) != MP_OK) break;      // p = r + beta (p - omega v)
         }
-        if ((r = s.spmv(*s.SA, pv, v)) != MP_OK) break;  // v = A p
+        const uint64_t* pu = pv;  // what x takes alpha times
+        if (pre && !left) {
+          if ((r = launch_ilu0_apply(pre, pv, s.ld, ph, s.ld, s.gate(), st)) != MP_OK) break;
+          pu = ph;
+        }
+        if ((r = s.spmv(*s.SA, pu, left ? ph : v)) != MP_OK) break;  // v = A p
+        if (left && (r = launch_ilu0_apply(pre, ph, s.ld, v, s.ld, s.gate(), st)) != MP_OK) break;
         if ((r = s.dot(rt, v, DEN)) != MP_OK) break;
         Prog p1;
         p1.add(kBrkZ, 0, DEN).add(kDiv, ALPHA, RHO, DEN);
         if ((r = s.run(p1)) != MP_OK) break;
         if ((r = s.lin(sv, rv, v, ALPHA, kNegB)) != MP_OK) break;  // s = r - alpha v
-        if ((r = s.spmv(*s.SA, sv, t)) != MP_OK) break;            // t = A s
+        const uint64_t* su = sv;  // what x takes omega times
+        if (pre && !left) {
+          if ((r = launch_ilu0_apply(pre, sv, s.ld, sh, s.ld, s.gate(), st)) != MP_OK) break;
+          su = sh;
+        }
+        if ((r = s.spmv(*s.SA, su, left ? sh : t)) != MP_OK) break;  // t = A s
+        if (left && (r = launch_ilu0_apply(pre, sh, s.ld, t, s.ld, s.gate(), st)) != MP_OK) break;
         if ((r = s.dot(t, sv, TS)) != MP_OK) break;
         if ((r = s.dot(t, t, TT)) != MP_OK) break;
         Prog p2;
         p2.add(kDivZ, OMEGA, TS, TT);  // omega = (t, s) / (t, t), +0 when t = 0
         if ((r = s.run(p2)) != MP_OK) break;
-        if ((r = s.lin(xw, xw, pv, ALPHA, 0)) != MP_OK) break;     // x + alpha p
-        if ((r = s.lin(xw, xw, sv, OMEGA, 0)) != MP_OK) break;     // ... + omega s
+        if ((r = s.lin(xw, xw, pu, ALPHA, 0)) != MP_OK) break;     // x + alpha p
+        if ((r = s.lin(xw, xw, su, OMEGA, 0)) != MP_OK) break;     // ... + omega s
         if ((r = s.lin(rv, sv, t, OMEGA, kNegB)) != MP_OK) break;  // r = s - omega t
       } else {  // GPBiCG
         uint64_t *q = vec(3), *t = vec(4), *v = vec(5), *w = vec(6), *y = vec(7), *u = vec(8),
@@ -736,12 +683,13 @@ mp_status solve_big_w(int method, mp_csr A, mp_vec b, mp_vec x, const mp_solve_o
 }  // namespace
 
 mp_status solve_big(int method, mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* opts,
-                    mp_solve_info* info, cudaStream_t st) {
+                    mp_solve_info* info, cudaStream_t st, const mp_ilu_s* pre, int pre_left) {
   if (method < 0 || method > 3) return set_error(MP_ERR_ARG, "method %d", method);
+  if (pre && method != 3) return set_error(MP_ERR_ARG, "ILU(0) is BiCGSTAB's preconditioner");
   switch (A->prec) {
-    case 2048: return solve_big_w<64>(method, A, b, x, opts, info, st);
-    case 4096: return solve_big_w<128>(method, A, b, x, opts, info, st);
-    case 8192: return solve_big_w<256>(method, A, b, x, opts, info, st);
+    case 2048: return solve_big_w<64>(method, A, b, x, opts, info, st, pre, pre_left);
+    case 4096: return solve_big_w<128>(method, A, b, x, opts, info, st, pre, pre_left);
+    case 8192: return solve_big_w<256>(method, A, b, x, opts, info, st, pre, pre_left);
     default: return set_error(MP_ERR_PREC, "precision %d", A->prec);
   }
 }

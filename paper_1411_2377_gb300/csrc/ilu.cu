@@ -14,7 +14,8 @@
 //   forward:  y_i = r_i - RN(l_ik y_k) for k < i ascending, rounded per step;
 //   backward: w_i = RN((y_i - RN(u_ik w_k) for k > i ascending) / u_ii).
 // Nothing is skipped (zero products included), so signed zeros follow the
-// same steps as in the oracle.
+// same steps as in the oracle.  At p = 2048-8192 the factorisation and the
+// solves are bigp_ilu.cu's warp-per-row kernels on the same storage.
 #include <algorithm>
 #include <vector>
 
@@ -24,14 +25,15 @@
 namespace mpk {
 namespace {
 
-// Sliced layout -> CSR order: thread per (chunk, lane) row.
-template <int W>
+// Sliced layout -> CSR order: thread per (chunk, lane) row; `planes` words
+// per value (head and limbs).
 __global__ void to_csr_kernel(int64_t nchunks, const int64_t* __restrict__ chunk_off,
                               const int32_t* __restrict__ row_of,
                               const int32_t* __restrict__ row_len,
                               const int32_t* __restrict__ scol, const uint64_t* __restrict__ sval,
                               int64_t nslots, const int64_t* __restrict__ rowptr,
-                              int32_t* __restrict__ col, uint64_t* __restrict__ lu, int64_t nnz) {
+                              int32_t* __restrict__ col, uint64_t* __restrict__ lu, int64_t nnz,
+                              int planes) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nchunks * 32) return;
   const int64_t c = t >> 5;
@@ -43,8 +45,7 @@ __global__ void to_csr_kernel(int64_t nchunks, const int64_t* __restrict__ chunk
     const int64_t s = chunk_off[c] + (int64_t)j * 32 + lane;
     const int64_t k = rowptr[row] + j;
     col[k] = scol[s];
-#pragma unroll
-    for (int q = 0; q <= W / 2; ++q) lu[(int64_t)q * nnz + k] = sval[(int64_t)q * nslots + s];
+    for (int q = 0; q < planes; ++q) lu[(int64_t)q * nnz + k] = sval[(int64_t)q * nslots + s];
   }
 }
 
@@ -196,6 +197,7 @@ constexpr int64_t kOneBlockRows = 1 << 18;
 
 mp_status launch_ilu0_apply(const mp_ilu_s* M, const uint64_t* r, int64_t ldr, uint64_t* w,
                             int64_t ldw, const int* gate, cudaStream_t st) {
+  if (prec_big(M->prec)) return launch_ilu0_apply_big(M, r, ldr, w, ldw, gate, st);
   return dispatch_w(M->prec, [&](auto wc) {
     constexpr int W = decltype(wc)::value;
     constexpr int tpb = 64;
@@ -264,7 +266,8 @@ extern "C" {
 mp_status mp_ilu0_create(mp_csr A, void* stream, mp_ilu* out) {
   if (!A || !out) return set_error(MP_ERR_ARG, "matrix or out is null");
   *out = nullptr;
-  if (!prec_ok(A->prec)) return set_error(MP_ERR_PREC, "ILU(0) at p = %d: p <= 1024", A->prec);
+  if (!prec_ok(A->prec) && !prec_big(A->prec))
+    return set_error(MP_ERR_PREC, "ILU(0) at p = %d", A->prec);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int64_t n = A->n, nnz = A->nnz, nch = A->A.nchunks;
   const int L = A->prec / 64;
@@ -289,12 +292,12 @@ mp_status mp_ilu0_create(mp_csr A, void* stream, mp_ilu* out) {
   M->n = n;
   M->nnz = nnz;
   M->prec = A->prec;
-  MPK_CUDA(cudaGetDevice(&M->device));
   auto fail = [&](mp_status s) {
     cudaStreamSynchronize(st);
     free_ilu(M);
     return s;
   };
+  if (cudaError_t ce = cudaGetDevice(&M->device)) return fail(cuda_error(ce, "cudaGetDevice"));
   auto dmalloc = [&](auto** p, size_t count) -> bool {
     return cudaMalloc((void**)p, sizeof(**p) * std::max<size_t>(count, 1)) == cudaSuccess;
   };
@@ -304,16 +307,13 @@ mp_status mp_ilu0_create(mp_csr A, void* stream, mp_ilu* out) {
   if (cudaMemcpyAsync(M->rowptr, rowptr.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice,
                       st) != cudaSuccess)
     return fail(set_error(MP_ERR_CUDA, "ILU(0) upload"));
-  mp_status r = dispatch_w(A->prec, [&](auto w) {
-    constexpr int W = decltype(w)::value;
-    if (nch > 0) {
-      to_csr_kernel<W><<<blocks_for(nch * 32, 128), 128, 0, st>>>(
-          nch, A->A.chunk_off, A->A.row_of, A->A.row_len, A->A.col, A->A.val, A->A.nslots,
-          M->rowptr, M->col, M->lu, nnz);
-      count_launch();
-    }
-    return launch_check("to_csr_kernel");
-  });
+  if (nch > 0) {
+    to_csr_kernel<<<blocks_for(nch * 32, 128), 128, 0, st>>>(
+        nch, A->A.chunk_off, A->A.row_of, A->A.row_len, A->A.col, A->A.val, A->A.nslots,
+        M->rowptr, M->col, M->lu, nnz, L + 1);
+    count_launch();
+  }
+  mp_status r = launch_check("to_csr_kernel");
   if (r != MP_OK) return fail(r);
   std::vector<int32_t> col(nnz);
   if (nnz > 0 && (cudaMemcpyAsync(col.data(), M->col, sizeof(int32_t) * nnz,
@@ -360,7 +360,8 @@ mp_status mp_ilu0_create(mp_csr A, void* stream, mp_ilu* out) {
     cudaFree(dz);
     return fail(set_error(MP_ERR_ALLOC, "ILU(0) status"));
   }
-  r = dispatch_w(A->prec, [&](auto w) {
+  if (prec_big(A->prec)) r = launch_ilu0_factor_big(M, dz, st);
+  else r = dispatch_w(A->prec, [&](auto w) {
     constexpr int W = decltype(w)::value;
     for (int64_t l = 0; l < M->nl; ++l) {
       const int64_t cnt = M->lvl_l[l + 1] - M->lvl_l[l];

@@ -82,6 +82,11 @@ namespace mpk {
 // the SpMV (a nonzero flag makes every launch return at once).
 mp_status launch_ilu0_apply(const mp_ilu_s* M, const uint64_t* r, int64_t ldr, uint64_t* w,
                             int64_t ldw, const int* gate, cudaStream_t st);
+// The same at p = 2048, 4096, 8192 (bigp_ilu.cu), and the factorisation
+// there (zero pivots set *status to MP_ERR_DIVZERO).
+mp_status launch_ilu0_apply_big(const mp_ilu_s* M, const uint64_t* r, int64_t ldr, uint64_t* w,
+                                int64_t ldw, const int* gate, cudaStream_t st);
+mp_status launch_ilu0_factor_big(const mp_ilu_s* M, int* status, cudaStream_t st);
 
 // ---- errors -------------------------------------------------------------
 mp_status set_error(mp_status s, const char* fmt, ...);
@@ -133,8 +138,10 @@ mp_status launch_dot_big(int prec, const uint64_t* x, int64_t ldx, const uint64_
                          int64_t n, uint64_t* out, int64_t ldo, void* scratch, const int* gate,
                          cudaStream_t st);
 // BiCG (method 0), GPBiCG (1), CGS (2), BiCGSTAB (3) at p > 1024 (bigp_solve.cu)
+// pre: ILU(0) preconditioner of BiCGSTAB (left when pre_left, else right)
 mp_status solve_big(int method, mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* opts,
-                    mp_solve_info* info, cudaStream_t st);
+                    mp_solve_info* info, cudaStream_t st, const mp_ilu_s* pre = nullptr,
+                    int pre_left = 1);
 mp_status launch_axpy_big(int prec, const uint64_t* al, int64_t n, const uint64_t* x, int64_t ldx,
                           uint64_t* y, int64_t ldy, cudaStream_t st);
 

@@ -1143,10 +1143,10 @@ mp_status solve(int method, mp_csr A, mp_vec b, mp_vec x, const mp_solve_opts* o
   if (pre && (pre->n != A->n || pre->prec != A->prec || opts->transpose))
     return set_error(MP_ERR_ARG, "preconditioner does not match the matrix (or a transposed solve)");
   if (prec_big(A->prec)) {
-    if (pre) return set_error(MP_ERR_PREC, "ILU(0) at p = %d: only p <= 1024", A->prec);
     if (opts->time_limit_ms != 0)
       return set_error(MP_ERR_ARG, "time_limit_ms: only the solvers at p <= 1024 take a limit");
-    return solve_big(method, A, b, x, opts, info, static_cast<cudaStream_t>(stream));
+    return solve_big(method, A, b, x, opts, info, static_cast<cudaStream_t>(stream), pre,
+                     pre_left);
   }
   SolveCall c{A, b, x, *opts, static_cast<cudaStream_t>(stream), pre, pre_left};
   return dispatch_w(A->prec, [&](auto w) {

@@ -130,3 +130,111 @@ def test_apply_beyond_one_block_matches_the_oracle():
     w_o, st = oracle.ilu0_apply(p, rowptr, colidx, lu_o, recs(R))
     assert st == oracle.OK
     assert_bitwise(w.planes(), w_o, "ILU(0) apply n=270400")
+
+
+@pytest.mark.parametrize("p,n", [(2048, 150), (4096, 70), (8192, 40)])
+def test_wide_factor_and_apply_match_the_oracle(p, n):
+    """p = 2048-8192 (the warp-per-row kernels): factors with zero entries
+    (5% of the stored values), then (LU)^{-1} r, against the oracle's wide
+    build bit for bit."""
+    mpk = need_gpu()
+    rowptr, colidx, Vr = dominant_system(n, p, p // 64 + 5)
+    A = mpk.CSR(rowptr, colidx, synth.records_to_planes(Vr), p)
+    M = mpk.ILU0(A)
+    lu_o, st = oracle.ilu0(p, rowptr, colidx, Vr)
+    assert st == oracle.OK
+    assert_bitwise(M.factor().planes(), lu_o, f"ILU(0) factor p={p}")
+    R = rand_planes(n, p, 19, zero_frac=0.1, emin=-5, emax=5)
+    w = M.apply(mpk.Vec.from_planes(R, p))
+    w_o, st = oracle.ilu0_apply(p, rowptr, colidx, lu_o, recs(R))
+    assert st == oracle.OK
+    assert_bitwise(w.planes(), w_o, f"ILU(0) apply p={p}")
+
+
+WIDE_CASES = [(2048, "ordered", 8), (2048, "exact", 8), (4096, "ordered", 6),
+              (8192, "ordered", 5)]
+
+
+def _wide_system(p, grid):
+    rowptr, colidx, v64 = synth.stencil2d(grid, seed=3)
+    n = len(rowptr) - 1
+    vals = oracle.from_f64(p, v64)
+    b, _ = oracle.spmv(p, oracle.EXACT, rowptr, colidx, vals, oracle.from_f64(p, np.ones(n)))
+    return rowptr, colidx, v64, vals, b
+
+
+@pytest.fixture(scope="module")
+def wide_oracle():
+    """The oracle's preconditioned and plain solves of every wide case, run
+    at once on host threads (the C oracle releases the interpreter lock; its
+    correctly rounded division makes one ILU(0) solve take seconds)."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+
+    def run(key):
+        p, mode, grid, side = key
+        rowptr, colidx, _, vals, b = _wide_system(p, grid)
+        n = len(rowptr) - 1
+        m = oracle.ORDERED if mode == "ordered" else oracle.EXACT
+        if side == "plain":
+            return oracle.bicgstab(p, m, rowptr, colidx, vals, b, oracle.empty(p, n), 1e-60, 0.0,
+                                   200)
+        return oracle.bicgstab_ilu0(p, m, rowptr, colidx, vals, b, oracle.empty(p, n), 1e-60,
+                                    0.0, 200, side=side)
+
+    keys = [c + (side,) for c in WIDE_CASES for side in ("left", "right", "plain")]
+    with ThreadPoolExecutor(max(1, min(len(keys), os.cpu_count() or 1))) as ex:
+        return dict(zip(keys, ex.map(run, keys)))
+
+
+@pytest.mark.parametrize("side", ("left", "right"))
+@pytest.mark.parametrize("p,mode,grid", WIDE_CASES)
+def test_wide_preconditioned_bicgstab_matches_the_oracle(p, mode, grid, side, wide_oracle):
+    """Table 3's precisions: BiCGSTAB+ILU(0) at 2048-8192 bits on a 2-D
+    convection-diffusion stencil, every iterate's residual norm, the count,
+    the status and x against the oracle; fewer iterations than plain
+    BiCGSTAB on the same system (the oracle's count)."""
+    mpk = need_gpu()
+    rowptr, colidx, v64, vals, b = _wide_system(p, grid)
+    A = mpk.CSR(rowptr, colidx, v64, p)
+    M = mpk.ILU0(A)
+    x, info = mpk.bicgstab_ilu0(A, M, mpk.Vec.from_planes(synth.records_to_planes(b), p),
+                                rtol=1e-60, maxit=200, mode=mode, poll_every=4, history=True,
+                                side=side)
+    xo, it, st, hist = wide_oracle[(p, mode, grid, side)]
+    assert st == oracle.OK
+    assert (info["iters"], info["status"]) == (it, st)
+    assert_bitwise(info["history"].planes(), hist, f"history p={p} {mode} {side}")
+    assert_bitwise(x.planes(), xo, f"x p={p} {mode} {side}")
+    assert it < wide_oracle[(p, mode, grid, "plain")][1]
+
+
+def test_wide_noconv_zero_pivot_and_missing_diagonal():
+    """At 2048 bits: maxit = 3 stops NC with the oracle's third iterate; a zero
+    pivot and a row without its diagonal entry refuse the factor
+    (MP_ERR_DIVZERO)."""
+    mpk = need_gpu()
+    p = 2048
+    rowptr, colidx, v64 = synth.stencil2d(9, seed=6)
+    n = len(rowptr) - 1
+    Vr = oracle.from_f64(p, v64)
+    B = rand_planes(n, p, 23, zero_frac=0.0, emin=-2, emax=2)
+    A = mpk.CSR(rowptr, colidx, v64, p)
+    M = mpk.ILU0(A)
+    for side in ("left", "right"):
+        xo, it, st, hist = oracle.bicgstab_ilu0(p, oracle.EXACT, rowptr, colidx, Vr, recs(B),
+                                                oracle.empty(p, n), 1e-200, 0.0, 3, side=side)
+        x, info = mpk.bicgstab_ilu0(A, M, mpk.Vec.from_planes(B, p), rtol=1e-200, maxit=3,
+                                    mode="exact", poll_every=1, history=True, side=side)
+        assert (info["iters"], info["status"]) == (it, st) == (3, oracle.ERR_NOCONV)
+        assert_bitwise(info["history"].planes(), hist, f"history {side}")
+        assert_bitwise(x.planes(), xo, f"x {side}")
+    rp = np.array([0, 2, 4], np.int64)
+    ci = np.array([0, 1, 0, 1], np.int32)
+    with pytest.raises(mpk.MPError) as e:
+        mpk.ILU0(mpk.CSR(rp, ci, np.array([0.0, 1.0, 1.0, 1.0]), p))
+    assert e.value.status == 9
+    with pytest.raises(mpk.MPError) as e:
+        mpk.ILU0(mpk.CSR(np.array([0, 1, 2], np.int64), np.array([1, 0], np.int32),
+                         np.array([1.0, 1.0]), p))
+    assert e.value.status == 9
