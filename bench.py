@@ -607,6 +607,7 @@ def run_native(args):
         solver["batched"] = batch_bench(mpk, count=args.batch_systems)
         solver["lotkin"] = lotkin_bench(mpk)
         solver["wide"] = wide_bench(mpk, imad_peak)
+        solver["table3"] = table3_bench(mpk)
 
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
@@ -945,6 +946,49 @@ def wide_bench(mpk, imad_peak, reps=5):
                                       "ms_per_iter": round(info["ms"] / max(1, info["iters"]), 3),
                                       "relres": info["relres"]}
     A.close()
+    return out
+
+
+def table3_bench(mpk, precs=(512, 1024, 2048, 4096, 8192), maxit=600):
+    """Section 4.2's Table 3 on a synthetic stand-in: plain BiCGSTAB against
+    BiCGSTAB with ILU(0) as the left preconditioner at 512-8192 bits.  The
+    paper's matrix (cavity04, n = 317) is not available; the stand-in is the
+    7-point convection-diffusion matrix on a 7^3 grid (n = 343; Peclet 50,
+    rows scaled over 20 decades: the large-solver recipe at a cavity04 size),
+    b = A*ones, the paper's stopping rule ||r_k|| <= 1e-20 ||r_0|| + 1e-50
+    as (rtol, atol).  Iterations, status and time on the stream; the ILU(0)
+    time includes the factorisation, as the paper's does."""
+    import time as _time
+
+    import torch
+
+    from paper_1411_2377_gb300 import synth
+
+    rowptr, colidx, v64 = synth.stencil3d(7, seed=2)
+    n = len(rowptr) - 1
+    out = {"workload": "stencil3d_7x7x7_pe50_rowscale20_rtol1e-20_atol1e-50", "n": n,
+           "maxit": maxit, "rows": []}
+    for p in precs:
+        A = mpk.CSR(rowptr, colidx, v64, p)
+        b = mpk.spmv(A, mpk.Vec.from_f64(np.ones(n), p), mode="exact")
+        row = {"p": p}
+        _, info = mpk.bicgstab(A, b, rtol=1e-20, atol=1e-50, maxit=maxit, poll_every=32)
+        row["bicgstab"] = {"iters": info["iters"], "status": info["status"],
+                           "ms": round(info["ms"], 2), "relres": info["relres"]}
+        torch.cuda.synchronize()
+        t0 = _time.perf_counter()
+        M = mpk.ILU0(A)
+        torch.cuda.synchronize()
+        factor_ms = (_time.perf_counter() - t0) * 1e3
+        _, info = mpk.bicgstab_ilu0(A, M, b, rtol=1e-20, atol=1e-50, maxit=maxit, poll_every=32,
+                                    side="left")
+        row["bicgstab_ilu0"] = {"iters": info["iters"], "status": info["status"],
+                                "ms": round(info["ms"] + factor_ms, 2),
+                                "factor_ms": round(factor_ms, 2), "relres": info["relres"],
+                                "levels": list(M.levels())}
+        out["rows"].append(row)
+        M.close()
+        A.close()
     return out
 
 
