@@ -30,6 +30,7 @@
 
 #include "internal.h"
 #include "mpdev.cuh"
+#include "pdl.cuh"
 
 namespace mpk {
 
@@ -126,90 +127,113 @@ __device__ __forceinline__ void block_minmax(long long& lo, long long& hi, long 
   }
 }
 
+// The elements one block takes for a dot: i = base + threadIdx.x + m stride
+// (m >= 0) while i < end, read through map[i] when map is not null (a
+// negative entry: no element).  The accumulate kernel's grid-stride share is
+// (blockIdx.x T, gridDim.x T, n, null).
+struct DotRange {
+  int64_t base, stride, end;
+  const int32_t* map;
+};
+
+// The partial of dot j over block b's elements of r (all kDotThreads threads
+// of the block call it; block-uniform returns): the block's exponent range
+// goes to s.lo/s.hi, its digits to s.partials.  dsm: dot_smem<W>() bytes of
+// per-thread windows; acc: DotWin<W>::cap counters; red: 64 words.
+template <int W>
+__device__ void dot_block_partial(const DotDev& a, const DotScratch& s, int j, int b,
+                                  const DotRange r, int64_t* dsm, int64_t* acc, long long* red) {
+  constexpr int CAP = DotWin<W>::cap;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nb = s.nblocks;
+  int64_t* c = dsm + threadIdx.x;
+  auto index = [&](int64_t t) -> int64_t { return r.map ? (int64_t)__ldg(r.map + t) : t; };
+  // this block's exponent range of the nonzero pairs (heads only)
+  long long lo = LLONG_MAX, hi = LLONG_MIN;
+  for (int64_t t = r.base + threadIdx.x; t < r.end; t += r.stride) {
+    const int64_t i = index(t);
+    if (i < 0) continue;
+    int64_t ex, ey;
+    uint32_t sx, sy;
+    unpack_head(__ldg(a.x[j] + i), ex, sx);
+    unpack_head(__ldg(a.y[j] + i), ey, sy);
+    if (zero_e(ex) || zero_e(ey)) continue;
+    lo = min(lo, (long long)(ex + ey));
+    hi = max(hi, (long long)(ex + ey));
+  }
+  block_minmax(lo, hi, red);
+  if (threadIdx.x == 0) {
+    s.lo[(size_t)j * nb + b] = lo;
+    s.hi[(size_t)j * nb + b] = hi;
+  }
+  // nothing to add, or a range the finalize rejects (the global span is
+  // at least this block's): no partial is written or read
+  if (!(lo <= hi && hi - lo <= SPAN_CAP)) return;  // block-uniform
+  const long long anchor = (lo >> 5) * 32;            // lo rounded down to a multiple of 32
+  const int nd = dot_digits(hi - anchor, W);
+  int64_t* part = s.partials + ((size_t)j * nb + b) * CAP;
+  if (hi - anchor > kDotFastSpan) {
+    // a span beyond the per-thread windows: one block-wide window with
+    // shared-memory atomics (rare: the solvers' vectors stay well inside)
+    for (int d = threadIdx.x; d < nd; d += kDotThreads) acc[d] = 0;
+    __syncthreads();
+    for (int64_t t = r.base + threadIdx.x; t < r.end; t += r.stride) {
+      const int64_t i = index(t);
+      if (i < 0) continue;
+      Num<W> x, y;
+      load<W>(x, a.x[j], a.ldx[j], i);
+      load<W>(y, a.y[j], a.ldy[j], i);
+      if (zero_e(x.e) || zero_e(y.e)) continue;
+      uint32_t P[2 * W], D[2 * W + 1];
+      mul_full<W>(x.m, y.m, P);
+      const int64_t off = x.e + y.e - anchor;
+      shifted_digits<W>(P, (uint32_t)(off & 31), D);
+      const bool ng = (x.s ^ y.s) != 0;
+      for (int k = 0; k <= 2 * W; ++k) {
+        const int64_t v = (int64_t)D[k];
+        atomicAdd((unsigned long long*)&acc[(off >> 5) + k], (unsigned long long)(ng ? -v : v));
+      }
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < nd; d += kDotThreads) part[d] = acc[d];
+    return;
+  }
+  for (int d = 0; d < nd; ++d) c[d * kDotThreads] = 0;
+  for (int64_t t = r.base + threadIdx.x; t < r.end; t += r.stride) {
+    const int64_t i = index(t);
+    if (i < 0) continue;
+    Num<W> x, y;
+    load<W>(x, a.x[j], a.ldx[j], i);
+    load<W>(y, a.y[j], a.ldy[j], i);
+    if (zero_e(x.e) || zero_e(y.e)) continue;
+    uint32_t P[2 * W];
+    if (W >= 16)
+      mul_full_ilp<W>(x.m, y.m, P);
+    else
+      mul_full<W>(x.m, y.m, P);
+    add_term<W>(c, kDotThreads, P, x.e + y.e - anchor, x.s ^ y.s);
+  }
+  __syncthreads();
+  for (int d = warp; d < nd; d += kDotWarps) {
+    int64_t t = 0;
+#pragma unroll
+    for (int u = 0; u < kDotThreads / 32; ++u) t += dsm[d * kDotThreads + u * 32 + lane];
+    t = warp_sum64(t);
+    if (lane == 0) part[d] = t;
+  }
+}
+
 template <int W>
 __global__ void __launch_bounds__(kDotThreads) dot_accum_kernel(const DotDev a, DotScratch s,
                                                                 const int* __restrict__ gate) {
   extern __shared__ int64_t dsm[];
   __shared__ int64_t acc[DotWin<W>::cap];  // the block-wide window of a wide block span
   __shared__ long long red[64];
+  pdl_begin();
   if (gate && *gate) return;
-  constexpr int CAP = DotWin<W>::cap;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nb = s.nblocks;
-  int64_t* c = dsm + threadIdx.x;
-  const int j = blockIdx.y;  // the dot this block works on
-  {
-    // this block's exponent range of the nonzero pairs (heads only)
-    long long lo = LLONG_MAX, hi = LLONG_MIN;
-    for (int64_t i = blockIdx.x * (int64_t)kDotThreads + threadIdx.x; i < a.n;
-         i += (int64_t)gridDim.x * kDotThreads) {
-      int64_t ex, ey;
-      uint32_t sx, sy;
-      unpack_head(__ldg(a.x[j] + i), ex, sx);
-      unpack_head(__ldg(a.y[j] + i), ey, sy);
-      if (zero_e(ex) || zero_e(ey)) continue;
-      lo = min(lo, (long long)(ex + ey));
-      hi = max(hi, (long long)(ex + ey));
-    }
-    block_minmax(lo, hi, red);
-    if (threadIdx.x == 0) {
-      s.lo[(size_t)j * nb + blockIdx.x] = lo;
-      s.hi[(size_t)j * nb + blockIdx.x] = hi;
-    }
-    // nothing to add, or a range the finalize rejects (the global span is
-    // at least this block's): no partial is written or read
-    if (!(lo <= hi && hi - lo <= SPAN_CAP)) return;  // block-uniform
-    const long long anchor = (lo >> 5) * 32;            // lo rounded down to a multiple of 32
-    const int nd = dot_digits(hi - anchor, W);
-    int64_t* part = s.partials + ((size_t)j * nb + blockIdx.x) * CAP;
-    if (hi - anchor > kDotFastSpan) {
-      // a span beyond the per-thread windows: one block-wide window with
-      // shared-memory atomics (rare: the solvers' vectors stay well inside)
-      for (int d = threadIdx.x; d < nd; d += kDotThreads) acc[d] = 0;
-      __syncthreads();
-      for (int64_t i = blockIdx.x * (int64_t)kDotThreads + threadIdx.x; i < a.n;
-           i += (int64_t)gridDim.x * kDotThreads) {
-        Num<W> x, y;
-        load<W>(x, a.x[j], a.ldx[j], i);
-        load<W>(y, a.y[j], a.ldy[j], i);
-        if (zero_e(x.e) || zero_e(y.e)) continue;
-        uint32_t P[2 * W], D[2 * W + 1];
-        mul_full<W>(x.m, y.m, P);
-        const int64_t off = x.e + y.e - anchor;
-        shifted_digits<W>(P, (uint32_t)(off & 31), D);
-        const bool ng = (x.s ^ y.s) != 0;
-        for (int k = 0; k <= 2 * W; ++k) {
-          const int64_t v = (int64_t)D[k];
-          atomicAdd((unsigned long long*)&acc[(off >> 5) + k], (unsigned long long)(ng ? -v : v));
-        }
-      }
-      __syncthreads();
-      for (int d = threadIdx.x; d < nd; d += kDotThreads) part[d] = acc[d];
-      return;
-    }
-    for (int d = 0; d < nd; ++d) c[d * kDotThreads] = 0;
-    for (int64_t i = blockIdx.x * (int64_t)kDotThreads + threadIdx.x; i < a.n;
-         i += (int64_t)gridDim.x * kDotThreads) {
-      Num<W> x, y;
-      load<W>(x, a.x[j], a.ldx[j], i);
-      load<W>(y, a.y[j], a.ldy[j], i);
-      if (zero_e(x.e) || zero_e(y.e)) continue;
-      uint32_t P[2 * W];
-      if (W >= 16)
-        mul_full_ilp<W>(x.m, y.m, P);
-      else
-        mul_full<W>(x.m, y.m, P);
-      add_term<W>(c, kDotThreads, P, x.e + y.e - anchor, x.s ^ y.s);
-    }
-    __syncthreads();
-    for (int d = warp; d < nd; d += kDotWarps) {
-      int64_t t = 0;
-#pragma unroll
-      for (int u = 0; u < kDotThreads / 32; ++u) t += dsm[d * kDotThreads + u * 32 + lane];
-      t = warp_sum64(t);
-      if (lane == 0) part[d] = t;
-    }
-  }
+  const DotRange r{blockIdx.x * (int64_t)kDotThreads, (int64_t)gridDim.x * kDotThreads, a.n,
+                   nullptr};
+  dot_block_partial<W>(a, s, (int)blockIdx.y, (int)blockIdx.x, r, dsm, acc, red);
 }
 
 // The finalize kernel's default: no step after the dots.  A step is called
@@ -218,86 +242,112 @@ struct NoPost {
   __device__ void operator()(int) const {}
 };
 
-// One block per dot: the global range from the blocks' ranges, the span cap,
-// the partials summed per global digit, carries resolved, one rounding.  The
-// block that finishes last then runs post(lane) on its first warp (the
-// results of all blocks are visible to it: each block fences its result
-// before it counts itself in; post must read them with loads that bypass L1).
-template <int W, class Post = NoPost>
-__global__ void __launch_bounds__(256) dot_finalize_kernel(const DotDev a, DotScratch s,
-                                                           int* __restrict__ status,
-                                                           const int* __restrict__ gate,
-                                                           Post post) {
-  constexpr int CAP = DotWin<W>::cap;
-  __shared__ int64_t sum[CAP];
-  __shared__ long long red[64];
-  __shared__ int off_of[kDotMaxBlocks];  // block b's digit offset (its nd_of[b] = 0: no partial)
-  __shared__ int nd_of[kDotMaxBlocks];
-  __shared__ int ndmax;
-  if (gate && *gate) return;
-  const int j = blockIdx.x, nb = s.nblocks;
+// Shared memory of one block's finalize of a dot.
+template <int W>
+struct DotFinSmem {
+  int64_t sum[DotWin<W>::cap];
+  long long red[64];
+  int off_of[kDotMaxBlocks];  // block b's digit offset (its nd_of[b] = 0: no partial)
+  int nd_of[kDotMaxBlocks];
+  int ndmax;
+};
+
+// Dot j by the calling block (any block size that is a multiple of 32): the
+// global range from the blocks' ranges, the span cap, the partials summed
+// per global digit, carries resolved, one rounding, stored to a.out[j].
+template <int W>
+__device__ void dot_finalize_one(const DotDev& a, const DotScratch& s, int j,
+                                 int* __restrict__ status, DotFinSmem<W>& f) {
+  const int nb = s.nblocks;
   const long long* blo = s.lo + (size_t)j * nb;
   const long long* bhi = s.hi + (size_t)j * nb;
   long long lo = LLONG_MAX, hi = LLONG_MIN;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-    lo = min(lo, blo[b]);
-    hi = max(hi, bhi[b]);
+    lo = min(lo, __ldcg(blo + b));
+    hi = max(hi, __ldcg(bhi + b));
   }
-  block_minmax(lo, hi, red);
+  block_minmax(lo, hi, f.red);
   Num<W> r;
   set_zero(r, 0u);
   if (lo <= hi && hi - lo <= SPAN_CAP) {
     const long long A = (lo >> 5) * 32;
     const int nd = dot_digits(hi - A, W);
-    if (threadIdx.x == 0) ndmax = 0;
-    for (int d = threadIdx.x; d < nd; d += blockDim.x) sum[d] = 0;
+    if (threadIdx.x == 0) f.ndmax = 0;
+    for (int d = threadIdx.x; d < nd; d += blockDim.x) f.sum[d] = 0;
     __syncthreads();
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-      const long long l = blo[b], h = bhi[b];
+      const long long l = __ldcg(blo + b), h = __ldcg(bhi + b);
       int ndb = 0, off = 0;
       if (l <= h) {  // else no nonzero pairs in that block
         const long long ab = (l >> 5) * 32;
         off = (int)((ab - A) >> 5);
         ndb = dot_digits(h - ab, W);
       }
-      off_of[b] = off;
-      nd_of[b] = ndb;
-      atomicMax(&ndmax, ndb);
+      f.off_of[b] = off;
+      f.nd_of[b] = ndb;
+      atomicMax(&f.ndmax, ndb);
     }
     __syncthreads();
     // every (block, digit) pair: block b's digit d enters global digit
     // d + off_of[b] by a shared 64-bit atomic add (integer: any order);
     // consecutive items are consecutive digits of one block (coalesced)
-    const int m = ndmax;
-    const int64_t* part = s.partials + (size_t)j * nb * CAP;
+    const int m = f.ndmax;
+    const int64_t* part = s.partials + (size_t)j * nb * DotWin<W>::cap;
     for (int q = threadIdx.x; q < nb * m; q += blockDim.x) {
       const int b = q / m, d = q - b * m;
-      if (d < nd_of[b])
-        atomicAdd(reinterpret_cast<unsigned long long*>(&sum[off_of[b] + d]),
-                  (unsigned long long)part[(size_t)b * CAP + d]);
+      if (d < f.nd_of[b])
+        atomicAdd(reinterpret_cast<unsigned long long*>(&f.sum[f.off_of[b] + d]),
+                  (unsigned long long)__ldcg(part + (size_t)b * DotWin<W>::cap + d));
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      const uint32_t negative = resolve_digits(sum, 1, nd);
-      if (negative) negate_words(sum, 1, nd);
-      round_words<W>(sum, 1, nd, (int64_t)A - 64 * W, negative, r);
+      const uint32_t negative = resolve_digits(f.sum, 1, nd);
+      if (negative) negate_words(f.sum, 1, nd);
+      round_words<W>(f.sum, 1, nd, (int64_t)A - 64 * W, negative, r);
     }
   } else if (lo <= hi && threadIdx.x == 0 && status) {
     atomicCAS(status, 0, (int)MP_ERR_SPAN);
   }
   if (threadIdx.x == 0) store<W>(r, a.out[j], a.out_ld[j], 0);
-  if constexpr (!std::is_same<Post, NoPost>::value) {
-    __shared__ int is_last;
-    if (threadIdx.x == 0) {
+}
+
+// Counts one finished dot of a group of k on the scratch's arrival counter;
+// true in the block that finished the last one (it then sees every dot's
+// result: each is fenced before it is counted, and must be read with loads
+// that bypass L1).  Called by every thread of the block.
+__device__ __forceinline__ bool dot_arrive_last(const DotScratch& s, int k) {
+  __shared__ int is_last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    is_last = atomicAdd(s.arrive, 1) == k - 1;
+    if (is_last) {
+      atomicExch(s.arrive, 0);
       __threadfence();
-      is_last = atomicAdd(s.arrive, 1) == (int)gridDim.x - 1;
-      if (is_last) {
-        atomicExch(s.arrive, 0);
-        __threadfence();
-      }
     }
-    __syncthreads();
-    if (is_last && threadIdx.x < 32) post((int)threadIdx.x);
+  }
+  __syncthreads();
+  return is_last != 0;
+}
+
+// One block per dot; the block that finishes last then runs post(lane) on
+// its first warp.
+template <int W, class Post = NoPost>
+__global__ void __launch_bounds__(256) dot_finalize_kernel(const DotDev a, DotScratch s,
+                                                           int* __restrict__ status,
+                                                           const int* __restrict__ gate,
+                                                           Post post) {
+  __shared__ DotFinSmem<W> f;
+  pdl_begin();
+  if (gate && *gate) return;
+  dot_finalize_one<W>(a, s, (int)blockIdx.x, status, f);
+  if constexpr (!std::is_same<Post, NoPost>::value) {
+    // one dot: this block is the last (its result is thread 0's own store)
+    bool last = true;
+    if (gridDim.x > 1)
+      last = dot_arrive_last(s, (int)gridDim.x);
+    else
+      __syncthreads();
+    if (last && threadIdx.x < 32) post((int)threadIdx.x);
   }
 }
 
@@ -347,8 +397,8 @@ mp_status dot_launch(const DotDev& a, void* scratch, int nblocks, int* status, c
   // streamed operands: shared memory for the windows matters more than L1
   MPK_CUDA(cudaFuncSetAttribute(dot_accum_kernel<W>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                 (int)cudaSharedmemCarveoutMaxShared));
-  dot_accum_kernel<W><<<dim3(nblocks, a.k), kDotThreads, smem, st>>>(a, s, gate);
-  dot_finalize_kernel<W, Post><<<a.k, 256, 0, st>>>(a, s, status, gate, post);
+  launch_pdl(dot_accum_kernel<W>, dim3(nblocks, a.k), dim3(kDotThreads), smem, st, a, s, gate);
+  launch_pdl(dot_finalize_kernel<W, Post>, dim3(a.k), dim3(256), 0, st, a, s, status, gate, post);
   count_launch(2);
   return launch_check("dot kernels");
 }

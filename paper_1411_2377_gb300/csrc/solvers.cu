@@ -365,41 +365,54 @@ __global__ void set_zero_kernel(uint64_t* a, int64_t ld, int64_t n) {
 template <int W>
 __global__ void copy_kernel(const SState* st, const uint64_t* __restrict__ src, int64_t lds,
                             uint64_t* __restrict__ dst, int64_t ldd, int64_t n) {
+  pdl_begin();
   if (st && st->done) return;
   GRID_LOOP(i, n) {
     for (int k = 0; k <= W / 2; ++k) dst[k * ldd + i] = src[k * lds + i];
   }
 }
 
-// GPBiCG, i >= 2: w = v + beta q;  p = r + beta (p - u)
+// The update steps below load every operand of an element before they
+// compute and store: a store to one vector cannot then hold back a load from
+// another (the compiler must assume they may alias), so the loads' latency
+// overlaps instead of adding up along the element's chain of operations.
+
+// GPBiCG, i >= 2, element i: w = v + beta q;  p = r + beta (p - u)
+template <int W>
+__device__ __forceinline__ void gp_wp_elem(int64_t i, const Num<W>& beta, const uint64_t* v,
+                                           const uint64_t* q, const uint64_t* r, uint64_t* p,
+                                           const uint64_t* u, uint64_t* w, int64_t ld) {
+  Num<W> qi, vi, pi, ui, ri, a, b, c;
+  load<W>(qi, q, ld, i);
+  load<W>(vi, v, ld, i);
+  load<W>(pi, p, ld, i);
+  load<W>(ui, u, ld, i);
+  load<W>(ri, r, ld, i);
+  mul_rn<W>(beta, qi, b);
+  add_rn<W>(vi, b, c);
+  store<W>(c, w, ld, i);
+  sub_rn<W>(pi, ui, c);
+  mul_rn<W>(beta, c, a);
+  add_rn<W>(ri, a, c);
+  store<W>(c, p, ld, i);
+}
+
 template <int W>
 __global__ void gp_wp(const SState* st, const uint64_t* __restrict__ S, const uint64_t* v,
                       const uint64_t* q, const uint64_t* r, uint64_t* p, const uint64_t* u,
                       uint64_t* w, int64_t ld, int64_t n) {
+  pdl_begin();
   if (st->done) return;
   Num<W> beta;
   ld_s<W>(beta, S, BETA);
-  GRID_LOOP(i, n) {
-    Num<W> a, b, c;
-    load<W>(a, q, ld, i);
-    mul_rn<W>(beta, a, b);
-    load<W>(a, v, ld, i);
-    add_rn<W>(a, b, c);
-    store<W>(c, w, ld, i);
-    load<W>(a, p, ld, i);
-    load<W>(b, u, ld, i);
-    sub_rn<W>(a, b, c);
-    mul_rn<W>(beta, c, a);
-    load<W>(b, r, ld, i);
-    add_rn<W>(b, a, c);
-    store<W>(c, p, ld, i);
-  }
+  GRID_LOOP(i, n) gp_wp_elem<W>(i, beta, v, q, r, p, u, w, ld);
 }
 
 // GPBiCG, i = 1: t = r - alpha q;  y = alpha q - r
 template <int W>
 __global__ void gp_ty1(const SState* st, const uint64_t* __restrict__ S, const uint64_t* r,
                        const uint64_t* q, uint64_t* t, uint64_t* y, int64_t ld, int64_t n) {
+  pdl_begin();
   if (st->done) return;
   Num<W> alpha;
   ld_s<W>(alpha, S, ALPHA);
@@ -415,101 +428,111 @@ __global__ void gp_ty1(const SState* st, const uint64_t* __restrict__ S, const u
   }
 }
 
-// GPBiCG, i >= 2: s = t - r;  t = r - alpha q;  y = s - alpha (w - q)
+// GPBiCG, i >= 2, element i: s = t - r;  t = r - alpha q;  y = s - alpha (w - q)
+template <int W>
+__device__ __forceinline__ void gp_sty_elem(int64_t i, const Num<W>& alpha, const uint64_t* r,
+                                            const uint64_t* q, const uint64_t* w, uint64_t* s,
+                                            uint64_t* t, uint64_t* y, int64_t ld) {
+  Num<W> ti, ri, qi, wi, a, c, sv;
+  load<W>(ti, t, ld, i);
+  load<W>(ri, r, ld, i);
+  load<W>(qi, q, ld, i);
+  load<W>(wi, w, ld, i);
+  sub_rn<W>(ti, ri, sv);
+  store<W>(sv, s, ld, i);
+  mul_rn<W>(alpha, qi, c);
+  sub_rn<W>(ri, c, a);
+  store<W>(a, t, ld, i);
+  sub_rn<W>(wi, qi, c);
+  mul_rn<W>(alpha, c, a);
+  sub_rn<W>(sv, a, c);
+  store<W>(c, y, ld, i);
+}
+
 template <int W>
 __global__ void gp_sty(const SState* st, const uint64_t* __restrict__ S, const uint64_t* r,
                        const uint64_t* q, const uint64_t* w, uint64_t* s, uint64_t* t,
                        uint64_t* y, int64_t ld, int64_t n) {
+  pdl_begin();
   if (st->done) return;
   Num<W> alpha;
   ld_s<W>(alpha, S, ALPHA);
-  GRID_LOOP(i, n) {
-    Num<W> a, b, c, sv;
-    load<W>(a, t, ld, i);
-    load<W>(b, r, ld, i);
-    sub_rn<W>(a, b, sv);
-    store<W>(sv, s, ld, i);
-    load<W>(a, q, ld, i);
-    mul_rn<W>(alpha, a, c);
-    sub_rn<W>(b, c, a);
-    store<W>(a, t, ld, i);
-    load<W>(a, w, ld, i);
-    load<W>(b, q, ld, i);
-    sub_rn<W>(a, b, c);
-    mul_rn<W>(alpha, c, a);
-    sub_rn<W>(sv, a, c);
-    store<W>(c, y, ld, i);
-  }
+  GRID_LOOP(i, n) gp_sty_elem<W>(i, alpha, r, q, w, s, t, y, ld);
 }
 
-// GPBiCG: u = zeta q + eta (s + beta u);  z = zeta r + eta z - alpha u;
-//         x = x + alpha p + z;            r = t - eta y - zeta v
+// GPBiCG, element i: u = zeta q + eta (s + beta u);  z = zeta r + eta z - alpha u;
+//                    x = x + alpha p + z;            r = t - eta y - zeta v
+// V.v: 0 q, 1 s, 2 u, 3 r, 4 z, 5 p, 6 t, 7 y, 8 v
+template <int W>
+__device__ __forceinline__ void gp_uzxr_elem(int64_t i, const Num<W>& beta, const Num<W>& eta,
+                                             const Num<W>& zeta, const Num<W>& alpha,
+                                             const Vecs& V, uint64_t* x, int64_t ldx) {
+  const int64_t ld = V.ld;
+  Num<W> qi, si, ui, ri, zi, pi, xi, yi, ti, vi, a, b, c, un, zn;
+  load<W>(ui, V.v[2], ld, i);
+  load<W>(si, V.v[1], ld, i);
+  load<W>(qi, V.v[0], ld, i);
+  load<W>(ri, V.v[3], ld, i);
+  load<W>(zi, V.v[4], ld, i);
+  load<W>(pi, V.v[5], ld, i);
+  load<W>(xi, x, ldx, i);
+  load<W>(yi, V.v[7], ld, i);
+  load<W>(ti, V.v[6], ld, i);
+  load<W>(vi, V.v[8], ld, i);
+  mul_rn<W>(beta, ui, b);
+  add_rn<W>(si, b, c);
+  mul_rn<W>(eta, c, b);
+  mul_rn<W>(zeta, qi, c);
+  add_rn<W>(c, b, un);
+  store<W>(un, V.v[2], ld, i);
+  mul_rn<W>(zeta, ri, b);  // zeta r
+  mul_rn<W>(eta, zi, c);   // eta z
+  add_rn<W>(b, c, a);
+  mul_rn<W>(alpha, un, b);
+  sub_rn<W>(a, b, zn);
+  store<W>(zn, V.v[4], ld, i);
+  mul_rn<W>(alpha, pi, b);  // alpha p
+  add_rn<W>(xi, b, c);
+  add_rn<W>(c, zn, a);
+  store<W>(a, x, ldx, i);
+  mul_rn<W>(eta, yi, b);  // eta y
+  sub_rn<W>(ti, b, c);
+  mul_rn<W>(zeta, vi, b);  // zeta v
+  sub_rn<W>(c, b, a);
+  store<W>(a, V.v[3], ld, i);
+}
+
 template <int W>
 __global__ void gp_uzxr(const SState* st, const uint64_t* __restrict__ S, const Vecs V,
                         uint64_t* x, int64_t ldx) {
+  pdl_begin();
   if (st->done) return;
-  // V.v: 0 q, 1 s, 2 u, 3 r, 4 z, 5 p, 6 t, 7 y, 8 v
-  const int64_t ld = V.ld;
-  GRID_LOOP(i, V.n) {
-    Num<W> sc, a, b, c, un, zn;
-    ld_s<W>(sc, S, BETA);
-    load<W>(a, V.v[2], ld, i);
-    mul_rn<W>(sc, a, b);
-    load<W>(a, V.v[1], ld, i);
-    add_rn<W>(a, b, c);
-    ld_s<W>(sc, S, ETA);
-    mul_rn<W>(sc, c, b);
-    ld_s<W>(sc, S, ZETA);
-    load<W>(a, V.v[0], ld, i);
-    mul_rn<W>(sc, a, c);
-    add_rn<W>(c, b, un);
-    store<W>(un, V.v[2], ld, i);
-    load<W>(a, V.v[3], ld, i);
-    mul_rn<W>(sc, a, b);  // zeta r
-    ld_s<W>(sc, S, ETA);
-    load<W>(a, V.v[4], ld, i);
-    mul_rn<W>(sc, a, c);  // eta z
-    add_rn<W>(b, c, a);
-    ld_s<W>(sc, S, ALPHA);
-    mul_rn<W>(sc, un, b);
-    sub_rn<W>(a, b, zn);
-    store<W>(zn, V.v[4], ld, i);
-    load<W>(a, V.v[5], ld, i);
-    mul_rn<W>(sc, a, b);  // alpha p
-    load<W>(a, x, ldx, i);
-    add_rn<W>(a, b, c);
-    add_rn<W>(c, zn, a);
-    store<W>(a, x, ldx, i);
-    ld_s<W>(sc, S, ETA);
-    load<W>(a, V.v[7], ld, i);
-    mul_rn<W>(sc, a, b);  // eta y
-    load<W>(a, V.v[6], ld, i);
-    sub_rn<W>(a, b, c);
-    ld_s<W>(sc, S, ZETA);
-    load<W>(a, V.v[8], ld, i);
-    mul_rn<W>(sc, a, b);  // zeta v
-    sub_rn<W>(c, b, a);
-    store<W>(a, V.v[3], ld, i);
-  }
+  Num<W> beta, eta, zeta, alpha;
+  ld_s<W>(beta, S, BETA);
+  ld_s<W>(eta, S, ETA);
+  ld_s<W>(zeta, S, ZETA);
+  ld_s<W>(alpha, S, ALPHA);
+  GRID_LOOP(i, V.n) gp_uzxr_elem<W>(i, beta, eta, zeta, alpha, V, x, ldx);
 }
 
 // BiCG, i >= 2: p = r + beta p;  p~ = r~ + beta p~
 template <int W>
 __global__ void bi_p(const SState* st, const uint64_t* __restrict__ S, const uint64_t* r,
                      const uint64_t* rt, uint64_t* p, uint64_t* pt, int64_t ld, int64_t n) {
+  pdl_begin();
   if (st->done) return;
   GRID_LOOP(i, n) {
-    Num<W> beta, a, b, c;
+    Num<W> beta, pi, ri, pti, rti, b, c;
     ld_s<W>(beta, S, BETA);
-    load<W>(a, p, ld, i);
-    mul_rn<W>(beta, a, b);
-    load<W>(a, r, ld, i);
-    add_rn<W>(a, b, c);
+    load<W>(pi, p, ld, i);
+    load<W>(ri, r, ld, i);
+    load<W>(pti, pt, ld, i);
+    load<W>(rti, rt, ld, i);
+    mul_rn<W>(beta, pi, b);
+    add_rn<W>(ri, b, c);
     store<W>(c, p, ld, i);
-    load<W>(a, pt, ld, i);
-    mul_rn<W>(beta, a, b);
-    load<W>(a, rt, ld, i);
-    add_rn<W>(a, b, c);
+    mul_rn<W>(beta, pti, b);
+    add_rn<W>(rti, b, c);
     store<W>(c, pt, ld, i);
   }
 }
@@ -519,24 +542,25 @@ template <int W>
 __global__ void bi_xr(const SState* st, const uint64_t* __restrict__ S, const uint64_t* p,
                       const uint64_t* z, const uint64_t* zt, uint64_t* r, uint64_t* rt,
                       uint64_t* x, int64_t ldx, int64_t ld, int64_t n) {
+  pdl_begin();
   if (st->done) return;
   GRID_LOOP(i, n) {
-    Num<W> alpha, a, b, c;
+    Num<W> alpha, pi, xi, zi, ri, zti, rti, b, c;
     ld_s<W>(alpha, S, ALPHA);
-    load<W>(a, p, ld, i);
-    mul_rn<W>(alpha, a, b);
-    load<W>(a, x, ldx, i);
-    add_rn<W>(a, b, c);
+    load<W>(pi, p, ld, i);
+    load<W>(xi, x, ldx, i);
+    load<W>(zi, z, ld, i);
+    load<W>(ri, r, ld, i);
+    load<W>(zti, zt, ld, i);
+    load<W>(rti, rt, ld, i);
+    mul_rn<W>(alpha, pi, b);
+    add_rn<W>(xi, b, c);
     store<W>(c, x, ldx, i);
-    load<W>(a, z, ld, i);
-    mul_rn<W>(alpha, a, b);
-    load<W>(a, r, ld, i);
-    sub_rn<W>(a, b, c);
+    mul_rn<W>(alpha, zi, b);
+    sub_rn<W>(ri, b, c);
     store<W>(c, r, ld, i);
-    load<W>(a, zt, ld, i);
-    mul_rn<W>(alpha, a, b);
-    load<W>(a, rt, ld, i);
-    sub_rn<W>(a, b, c);
+    mul_rn<W>(alpha, zti, b);
+    sub_rn<W>(rti, b, c);
     store<W>(c, rt, ld, i);
   }
 }
@@ -545,17 +569,18 @@ __global__ void bi_xr(const SState* st, const uint64_t* __restrict__ S, const ui
 template <int W>
 __global__ void cgs_up(const SState* st, const uint64_t* __restrict__ S, const uint64_t* r,
                        const uint64_t* q, uint64_t* u, uint64_t* p, int64_t ld, int64_t n) {
+  pdl_begin();
   if (st->done) return;
   GRID_LOOP(i, n) {
-    Num<W> beta, qv, a, b, un;
+    Num<W> beta, qv, ri, pi, a, b, un;
     ld_s<W>(beta, S, BETA);
     load<W>(qv, q, ld, i);
+    load<W>(ri, r, ld, i);
+    load<W>(pi, p, ld, i);
     mul_rn<W>(beta, qv, a);
-    load<W>(b, r, ld, i);
-    add_rn<W>(b, a, un);
+    add_rn<W>(ri, a, un);
     store<W>(un, u, ld, i);
-    load<W>(a, p, ld, i);
-    mul_rn<W>(beta, a, b);
+    mul_rn<W>(beta, pi, b);
     add_rn<W>(qv, b, a);
     mul_rn<W>(beta, a, b);
     add_rn<W>(un, b, a);
@@ -568,20 +593,21 @@ template <int W>
 __global__ void cgs_qwx(const SState* st, const uint64_t* __restrict__ S, const uint64_t* u,
                         const uint64_t* v, uint64_t* q, uint64_t* w, uint64_t* x, int64_t ldx,
                         int64_t ld, int64_t n) {
+  pdl_begin();
   if (st->done) return;
   GRID_LOOP(i, n) {
-    Num<W> alpha, uv, a, b, qv, wv;
+    Num<W> alpha, uv, vi, xi, b, qv, wv;
     ld_s<W>(alpha, S, ALPHA);
     load<W>(uv, u, ld, i);
-    load<W>(a, v, ld, i);
-    mul_rn<W>(alpha, a, b);
+    load<W>(vi, v, ld, i);
+    load<W>(xi, x, ldx, i);
+    mul_rn<W>(alpha, vi, b);
     sub_rn<W>(uv, b, qv);
     store<W>(qv, q, ld, i);
     add_rn<W>(uv, qv, wv);
     store<W>(wv, w, ld, i);
     mul_rn<W>(alpha, wv, b);
-    load<W>(a, x, ldx, i);
-    add_rn<W>(a, b, uv);
+    add_rn<W>(xi, b, uv);
     store<W>(uv, x, ldx, i);
   }
 }
@@ -590,6 +616,7 @@ __global__ void cgs_qwx(const SState* st, const uint64_t* __restrict__ S, const 
 template <int W, int SCAL>
 __global__ void r_minus(const SState* st, const uint64_t* __restrict__ S, const uint64_t* a,
                         uint64_t* r, int64_t ld, int64_t n) {
+  pdl_begin();
   if (st->done) return;
   GRID_LOOP(i, n) {
     Num<W> sc, av, b, rv, c;
@@ -606,6 +633,7 @@ __global__ void r_minus(const SState* st, const uint64_t* __restrict__ S, const 
 template <int W>
 __global__ void bs_p(const SState* st, const uint64_t* __restrict__ S, const uint64_t* r,
                      const uint64_t* v, uint64_t* p, int64_t ld, int64_t n) {
+  pdl_begin();
   if (st->done) return;
   GRID_LOOP(i, n) {
     Num<W> beta, omega, a, b, c;
@@ -626,6 +654,7 @@ __global__ void bs_p(const SState* st, const uint64_t* __restrict__ S, const uin
 template <int W>
 __global__ void bs_s(const SState* st, const uint64_t* __restrict__ S, const uint64_t* r,
                      const uint64_t* v, uint64_t* s, int64_t ld, int64_t n) {
+  pdl_begin();
   if (st->done) return;
   GRID_LOOP(i, n) {
     Num<W> alpha, a, b, c;
@@ -644,23 +673,24 @@ template <int W>
 __global__ void bs_xr(const SState* st, const uint64_t* __restrict__ S, const uint64_t* px,
                       const uint64_t* sx, const uint64_t* s, const uint64_t* t, uint64_t* r,
                       uint64_t* x, int64_t ldx, int64_t ld, int64_t n) {
+  pdl_begin();
   if (st->done) return;
   GRID_LOOP(i, n) {
-    Num<W> alpha, omega, a, b, c, sv;
+    Num<W> alpha, omega, pxi, xi, sxi, si, ti, a, b, c;
     ld_s<W>(alpha, S, ALPHA);
     ld_s<W>(omega, S, OMEGA);
-    load<W>(a, px, ld, i);
-    mul_rn<W>(alpha, a, b);
-    load<W>(a, x, ldx, i);
-    add_rn<W>(a, b, c);
-    load<W>(sv, sx, ld, i);
-    mul_rn<W>(omega, sv, b);
+    load<W>(pxi, px, ld, i);
+    load<W>(xi, x, ldx, i);
+    load<W>(sxi, sx, ld, i);
+    load<W>(si, s, ld, i);
+    load<W>(ti, t, ld, i);
+    mul_rn<W>(alpha, pxi, b);
+    add_rn<W>(xi, b, c);
+    mul_rn<W>(omega, sxi, b);
     add_rn<W>(c, b, a);
     store<W>(a, x, ldx, i);
-    load<W>(sv, s, ld, i);
-    load<W>(a, t, ld, i);
-    mul_rn<W>(omega, a, b);
-    sub_rn<W>(sv, b, c);
+    mul_rn<W>(omega, ti, b);
+    sub_rn<W>(si, b, c);
     store<W>(c, r, ld, i);
   }
 }
@@ -761,10 +791,10 @@ mp_status gp_iteration(const Work& w, const SolveCall& c, bool first) {
   const int g = ew_grid(n);
   mp_status r;
   if (first) {
-    copy_kernel<W><<<g, 128, 0, st>>>(w.st, w.vec(R), ld, w.vec(P), ld, n);
+    launch_pdl(copy_kernel<W>, g, 128, 0, st, w.st, w.vec(R), ld, w.vec(P), ld, n);
     count_launch();
   } else {  // beta was formed by the previous iteration's check
-    gp_wp<W><<<g, 128, 0, st>>>(w.st, w.S, w.vec(V), w.vec(Q), w.vec(R), w.vec(P), w.vec(U),
+    launch_pdl(gp_wp<W>, g, 128, 0, st, w.st, w.S, w.vec(V), w.vec(Q), w.vec(R), w.vec(P), w.vec(U),
                                 w.vec(WV), ld, n);
     count_launch();
   }
@@ -774,9 +804,9 @@ mp_status gp_iteration(const Work& w, const SolveCall& c, bool first) {
                    PostAlpha<W>{w.st, w.S})) != MP_OK)
     return r;
   if (first) {
-    gp_ty1<W><<<g, 128, 0, st>>>(w.st, w.S, w.vec(R), w.vec(Q), w.vec(T), w.vec(Y), ld, n);
+    launch_pdl(gp_ty1<W>, g, 128, 0, st, w.st, w.S, w.vec(R), w.vec(Q), w.vec(T), w.vec(Y), ld, n);
   } else {
-    gp_sty<W><<<g, 128, 0, st>>>(w.st, w.S, w.vec(R), w.vec(Q), w.vec(WV), w.vec(SV), w.vec(T),
+    launch_pdl(gp_sty<W>, g, 128, 0, st, w.st, w.S, w.vec(R), w.vec(Q), w.vec(WV), w.vec(SV), w.vec(T),
                                  w.vec(Y), ld, n);
   }
   count_launch();
@@ -811,7 +841,7 @@ mp_status gp_iteration(const Work& w, const SolveCall& c, bool first) {
   V9.v[8] = w.vec(V);
   V9.ld = ld;
   V9.n = n;
-  gp_uzxr<W><<<g, 128, 0, st>>>(w.st, w.S, V9, c.x.data, c.x.ld);
+  launch_pdl(gp_uzxr<W>, g, 128, 0, st, w.st, w.S, V9, c.x.data, c.x.ld);
   count_launch();
   if ((r = check_dots<W, ZETA, ZETA>(w, c, w.vec(R), w.vec(RT), st, gate)) != MP_OK) return r;
   return launch_check("gpbicg iteration");
@@ -826,11 +856,11 @@ mp_status bi_iteration(const Work& w, const SolveCall& c, bool first) {
   const int g = ew_grid(n);
   mp_status r;
   if (first) {
-    copy_kernel<W><<<g, 128, 0, st>>>(w.st, w.vec(R), ld, w.vec(P), ld, n);
-    copy_kernel<W><<<g, 128, 0, st>>>(w.st, w.vec(RT), ld, w.vec(PT), ld, n);
+    launch_pdl(copy_kernel<W>, g, 128, 0, st, w.st, w.vec(R), ld, w.vec(P), ld, n);
+    launch_pdl(copy_kernel<W>, g, 128, 0, st, w.st, w.vec(RT), ld, w.vec(PT), ld, n);
     count_launch(2);
   } else {  // beta was formed by the previous iteration's check
-    bi_p<W><<<g, 128, 0, st>>>(w.st, w.S, w.vec(R), w.vec(RT), w.vec(P), w.vec(PT), ld, n);
+    launch_pdl(bi_p<W>, g, 128, 0, st, w.st, w.S, w.vec(R), w.vec(RT), w.vec(P), w.vec(PT), ld, n);
     count_launch();
   }
   if ((r = launch_spmv(c.A, op_a(c),c.o.mode, w.vec(P), ld, w.vec(Z), ld, nullptr, 0, gate, st)) != MP_OK)
@@ -840,7 +870,7 @@ mp_status bi_iteration(const Work& w, const SolveCall& c, bool first) {
   if ((r = dot2<W>(w, w.vec(PT), w.vec(Z), DEN, nullptr, nullptr, 0, st, gate,
                    PostAlpha<W>{w.st, w.S})) != MP_OK)
     return r;
-  bi_xr<W><<<g, 128, 0, st>>>(w.st, w.S, w.vec(P), w.vec(Z), w.vec(ZT), w.vec(R), w.vec(RT),
+  launch_pdl(bi_xr<W>, g, 128, 0, st, w.st, w.S, w.vec(P), w.vec(Z), w.vec(ZT), w.vec(R), w.vec(RT),
                               c.x.data, c.x.ld, ld, n);
   count_launch();
   if ((r = check_dots<W, -1, -1>(w, c, w.vec(R), w.vec(RT), st, gate)) != MP_OK) return r;
@@ -856,11 +886,11 @@ mp_status cgs_iteration(const Work& w, const SolveCall& c, bool first) {
   const int g = ew_grid(n);
   mp_status r;
   if (first) {
-    copy_kernel<W><<<g, 128, 0, st>>>(w.st, w.vec(R), ld, w.vec(U), ld, n);
-    copy_kernel<W><<<g, 128, 0, st>>>(w.st, w.vec(R), ld, w.vec(P), ld, n);
+    launch_pdl(copy_kernel<W>, g, 128, 0, st, w.st, w.vec(R), ld, w.vec(U), ld, n);
+    launch_pdl(copy_kernel<W>, g, 128, 0, st, w.st, w.vec(R), ld, w.vec(P), ld, n);
     count_launch(2);
   } else {  // beta was formed by the previous iteration's check
-    cgs_up<W><<<g, 128, 0, st>>>(w.st, w.S, w.vec(R), w.vec(Q), w.vec(U), w.vec(P), ld, n);
+    launch_pdl(cgs_up<W>, g, 128, 0, st, w.st, w.S, w.vec(R), w.vec(Q), w.vec(U), w.vec(P), ld, n);
     count_launch();
   }
   if ((r = launch_spmv(c.A, op_a(c), c.o.mode, w.vec(P), ld, w.vec(V), ld, nullptr, 0, gate, st)) != MP_OK)
@@ -868,12 +898,12 @@ mp_status cgs_iteration(const Work& w, const SolveCall& c, bool first) {
   if ((r = dot2<W>(w, w.vec(RT), w.vec(V), DEN, nullptr, nullptr, 0, st, gate,
                    PostAlpha<W>{w.st, w.S})) != MP_OK)
     return r;
-  cgs_qwx<W><<<g, 128, 0, st>>>(w.st, w.S, w.vec(U), w.vec(V), w.vec(Q), w.vec(WV), c.x.data,
+  launch_pdl(cgs_qwx<W>, g, 128, 0, st, w.st, w.S, w.vec(U), w.vec(V), w.vec(Q), w.vec(WV), c.x.data,
                                 c.x.ld, ld, n);
   count_launch();
   if ((r = launch_spmv(c.A, op_a(c), c.o.mode, w.vec(WV), ld, w.vec(AW), ld, nullptr, 0, gate, st)) != MP_OK)
     return r;
-  r_minus<W, ALPHA><<<g, 128, 0, st>>>(w.st, w.S, w.vec(AW), w.vec(R), ld, n);
+  launch_pdl(r_minus<W, ALPHA>, g, 128, 0, st, w.st, w.S, w.vec(AW), w.vec(R), ld, n);
   count_launch();
   if ((r = check_dots<W, -1, -1>(w, c, w.vec(R), w.vec(RT), st, gate)) != MP_OK) return r;
   return launch_check("cgs iteration");
@@ -888,10 +918,10 @@ mp_status bicgstab_iteration(const Work& w, const SolveCall& c, bool first) {
   const int g = ew_grid(n);
   mp_status r;
   if (first) {
-    copy_kernel<W><<<g, 128, 0, st>>>(w.st, w.vec(R), ld, w.vec(P), ld, n);
+    launch_pdl(copy_kernel<W>, g, 128, 0, st, w.st, w.vec(R), ld, w.vec(P), ld, n);
     count_launch();
   } else {  // beta was formed by the previous iteration's check
-    bs_p<W><<<g, 128, 0, st>>>(w.st, w.S, w.vec(R), w.vec(V), w.vec(P), ld, n);
+    launch_pdl(bs_p<W>, g, 128, 0, st, w.st, w.S, w.vec(R), w.vec(V), w.vec(P), ld, n);
     count_launch();
   }
   // right preconditioning: v = A K^{-1} p, t = A K^{-1} s (x takes K^{-1} p
@@ -911,7 +941,7 @@ mp_status bicgstab_iteration(const Work& w, const SolveCall& c, bool first) {
   if ((r = dot2<W>(w, w.vec(RT), w.vec(V), DEN, nullptr, nullptr, 0, st, gate,
                    PostAlpha<W>{w.st, w.S})) != MP_OK)
     return r;
-  bs_s<W><<<g, 128, 0, st>>>(w.st, w.S, w.vec(R), w.vec(V), w.vec(SV), ld, n);
+  launch_pdl(bs_s<W>, g, 128, 0, st, w.st, w.S, w.vec(R), w.vec(V), w.vec(SV), ld, n);
   count_launch();
   const uint64_t* sv = w.vec(SV);
   if (c.pre && !left) {
@@ -926,7 +956,7 @@ mp_status bicgstab_iteration(const Work& w, const SolveCall& c, bool first) {
   if ((r = dot2<W>(w, w.vec(T), w.vec(SV), TS, w.vec(T), w.vec(T), TT, st, gate,
                    PostOmega<W>{w.st, w.S})) != MP_OK)
     return r;
-  bs_xr<W><<<g, 128, 0, st>>>(w.st, w.S, pv, sv, w.vec(SV), w.vec(T), w.vec(R), c.x.data,
+  launch_pdl(bs_xr<W>, g, 128, 0, st, w.st, w.S, pv, sv, w.vec(SV), w.vec(T), w.vec(R), c.x.data,
                               c.x.ld, ld, n);
   count_launch();
   if ((r = check_dots<W, OMEGA, OMEGA>(w, c, w.vec(R), w.vec(RT), st, gate)) != MP_OK) return r;
@@ -996,7 +1026,7 @@ mp_status solve_w(const SolveCall& cu, mp_solve_info* info) {
                          nullptr, st)) != MP_OK)
       break;
     if (left && (r = launch_ilu0_apply(c.pre, r0, ld, w.vec(0), ld, nullptr, st)) != MP_OK) break;
-    copy_kernel<W><<<g, 128, 0, st>>>(nullptr, w.vec(0), ld, w.vec(1), ld, n);
+    launch_pdl(copy_kernel<W>, g, 128, 0, st, nullptr, w.vec(0), ld, w.vec(1), ld, n);
     count_launch();
     if ((r = dot2<W>(w, w.vec(0), w.vec(0), RR0, w.vec(1), w.vec(0), RHO, st, nullptr,
                      PostSetup<W>{w.st, w.S, c.o.rtol, c.o.atol})) != MP_OK)
