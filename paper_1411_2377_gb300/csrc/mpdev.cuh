@@ -317,9 +317,10 @@ __device__ __forceinline__ void add_rn(const Num<W>& a_, const Num<W>& b_, Num<W
   chain_add_frame<W>(T, X, Yi, sub & (sticky == 0u ? 1u : 0u));
   T[W + 1] &= (sub ^ 1u);
   uint32_t rb, st;
-  if (sub && d <= 1) {
-    // near case: the difference may cancel any number of leading bits (or
-    // all of them): count the leading zeros and shift them out
+  const uint32_t carry = T[W + 1] & 1u;
+  if (carry == 0u && T[W] == 0u) {
+    // 32 or more leading bits cancelled (a difference with d <= 1 only), or
+    // all of them: count the leading zeros and shift them out
     uint32_t any = 0u;
 #pragma unroll
     for (int k = 0; k < W + 2; ++k) any |= T[k];
@@ -335,30 +336,24 @@ __device__ __forceinline__ void add_rn(const Num<W>& a_, const Num<W>& b_, Num<W
 #pragma unroll
     for (int k = 0; k < W; ++k) r.m[k] = T[k + 2];
   } else {
-    // far case (a sum, or a difference whose smaller operand is below half
-    // the larger): the leading one is at bit 32W+32 (a carry out), 32W+31 or
-    // 32W+30 of T, so the normalising shift lz is 31, 32 or 33 and the kept
-    // words, round bit and sticky bit are fixed funnel shifts of T
-    const uint32_t carry = T[W + 1] & 1u;
-    const uint32_t top = T[W] >> 31;
-    if (carry) {  // lz = 31
+    // the leading one is the carry out (bit 32W+32 of T) or a bit of T[W]
+    // (lz0 = its leading zeros: 0 for a sum without carry, 1 for a far
+    // difference, up to 31 for a near one).  With U = T one word down on a
+    // carry, the kept words are the funnel shifts of U by s = 31 (carry) or
+    // lz0; the word below them gives the round bit and, with what U drops
+    // and the frame's sticky bit, the sticky bit.  One path for every lane.
+    const uint32_t lz0 = __clz(T[W]);
+    const uint32_t sh = carry ? 31u : lz0;
+    uint32_t U[W + 1];
 #pragma unroll
-      for (int k = 0; k < W; ++k) r.m[k] = __funnelshift_r(T[k + 1], T[k + 2], 1);
-      rb = T[1] & 1u;
-      st = T[0] | sticky;
-      e += 1;
-    } else if (top) {  // lz = 32
+    for (int k = 0; k <= W; ++k) U[k] = carry ? T[k + 1] : T[k];
+    const uint32_t um1 = carry ? T[0] : 0u;
 #pragma unroll
-      for (int k = 0; k < W; ++k) r.m[k] = T[k + 1];
-      rb = T[0] >> 31;
-      st = (T[0] << 1) | sticky;
-    } else {  // lz = 33
-#pragma unroll
-      for (int k = 0; k < W; ++k) r.m[k] = __funnelshift_r(T[k], T[k + 1], 31);
-      rb = (T[0] >> 30) & 1u;
-      st = (T[0] << 2) | sticky;
-      e -= 1;
-    }
+    for (int k = 0; k < W; ++k) r.m[k] = __funnelshift_l(U[k], U[k + 1], sh);
+    const uint32_t v = __funnelshift_l(um1, U[0], sh);
+    rb = v >> 31;
+    st = (v << 1) | (um1 << sh) | sticky;
+    e += carry ? (int64_t)1 : -(int64_t)lz0;
   }
   r.e = e;
   r.s = s;

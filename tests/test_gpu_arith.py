@@ -72,6 +72,43 @@ def test_all_pairs_of_edge_values(p):
         assert_bitwise(out.planes(), want, f"{name} edges p={p}")
 
 
+@pytest.mark.parametrize("p", PRECS)
+def test_cancellation_depths(p):
+    """Differences of operands one binade apart or in the same binade whose
+    leading bits cancel to every depth from 0 to p - 1 bits (the leading one
+    landing in every bit of the top words and below them), with and without
+    nonzero bits under the difference's leading one, and the same pairs
+    added with opposite signs: add and sub against the oracle."""
+    mpk = need_gpu()
+    rng = np.random.default_rng(p + 17)
+    h = 1 << (p - 1)
+    A, B = [], []
+    for j in range(p - 1):  # |M1 - M2| has its leading one at bit j
+        for rep in range(2):
+            low = int(rng.integers(0, 1 << min(j, 62))) if (rep and j) else 0
+            diff = (1 << j) + (low % (1 << j) if j else 0)
+            M2 = h + int(rng.integers(0, 1 << min(p - 2, 62)))
+            M1 = M2 + diff
+            if M1 >= 2 * h:
+                M2 -= diff
+                M1 = M2 + diff
+            for e2 in (0, -1):  # same binade, or b one binade lower (d = 1)
+                a = Fraction(M1) * Fraction(2) ** (3 - p)
+                b = Fraction(M2) * Fraction(2) ** (3 + e2 - p)
+                A.append(exact.encode(exact.Val(a), p))
+                B.append(exact.encode(exact.Val(b), p))
+                A.append(exact.encode(exact.Val(-a), p))
+                B.append(exact.encode(exact.Val(-b), p))
+    A, B = np.stack(A), np.stack(B)
+    a = mpk.Vec.from_planes(A.T.copy(), p)
+    b = mpk.Vec.from_planes(B.T.copy(), p)
+    for name in ("sub", "add"):
+        code, ocode = OPS[name]
+        want, st = oracle.ewise(p, ocode, A, B)
+        assert st == oracle.OK
+        assert_bitwise(mpk.ewise(code, a, b).planes(), want, f"{name} cancellation p={p}")
+
+
 def test_division_by_zero_is_reported():
     mpk = need_gpu()
     p = 256
