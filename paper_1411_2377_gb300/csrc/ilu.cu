@@ -25,6 +25,20 @@
 namespace mpk {
 namespace {
 
+// Loads through L2 only, for data the same kernel writes (the factor's row
+// in the factorisation, w in the one-block solves), which the read-only
+// path (ld.global.nc) does not allow.
+template <int W>
+__device__ __forceinline__ void load_w(Num<W>& a, const uint64_t* w, int64_t ld, int64_t i) {
+  unpack_head(__ldcg(w + i), a.e, a.s);
+#pragma unroll
+  for (int k = 0; k < W / 2; ++k) {
+    const uint64_t l = __ldcg(w + (int64_t)(k + 1) * ld + i);
+    a.m[2 * k] = (uint32_t)l;
+    a.m[2 * k + 1] = (uint32_t)(l >> 32);
+  }
+}
+
 // Sliced layout -> CSR order: thread per (chunk, lane) row; `planes` words
 // per value (head and limbs).
 __global__ void to_csr_kernel(int64_t nchunks, const int64_t* __restrict__ chunk_off,
@@ -61,12 +75,12 @@ __global__ void ilu_level_kernel(const int32_t* __restrict__ rows, int64_t count
   for (int64_t ik = a; ik < b && col[ik] < i; ++ik) {
     const int32_t k = col[ik];
     Num<W> ukk, aik, l;
-    load<W>(ukk, lu, nnz, diag[k]);
+    load_w<W>(ukk, lu, nnz, diag[k]);
     if (zero_e(ukk.e)) {
       atomicCAS(status, 0, (int)MP_ERR_DIVZERO);
       return;
     }
-    load<W>(aik, lu, nnz, ik);
+    load_w<W>(aik, lu, nnz, ik);
     div_rn<W>(aik, ukk, l);
     store<W>(l, lu, nnz, ik);
     int64_t q = diag[k] + 1;  // row k's entries right of its diagonal
@@ -77,15 +91,15 @@ __global__ void ilu_level_kernel(const int32_t* __restrict__ rows, int64_t count
       if (q >= qe) break;
       if (col[q] != j) continue;
       Num<W> ukj, aij, t1, t2;
-      load<W>(ukj, lu, nnz, q);
-      load<W>(aij, lu, nnz, ij);
+      load_w<W>(ukj, lu, nnz, q);
+      load_w<W>(aij, lu, nnz, ij);
       mul_rn<W>(l, ukj, t1);
       sub_rn<W>(aij, t1, t2);
       store<W>(t2, lu, nnz, ij);
     }
   }
   Num<W> d;
-  load<W>(d, lu, nnz, diag[i]);
+  load_w<W>(d, lu, nnz, diag[i]);
   if (zero_e(d.e)) atomicCAS(status, 0, (int)MP_ERR_DIVZERO);
 }
 
@@ -158,11 +172,11 @@ __global__ void __launch_bounds__(256) trsv_block_kernel(
       const int32_t i = rows[t];
       Num<W> acc;
       if (UPPER) {
-        load<W>(acc, w, ldw, i);
+        load_w<W>(acc, w, ldw, i);
         for (int64_t k = diag[i] + 1; k < rowptr[i + 1]; ++k) {
           Num<W> u, z, pr, s;
           load<W>(u, lu, nnz, k);
-          load<W>(z, w, ldw, col[k]);
+          load_w<W>(z, w, ldw, col[k]);
           mul_rn<W>(u, z, pr);
           sub_rn<W>(acc, pr, s);
           acc = s;
@@ -176,7 +190,7 @@ __global__ void __launch_bounds__(256) trsv_block_kernel(
         for (int64_t k = rowptr[i]; k < rowptr[i + 1] && col[k] < i; ++k) {
           Num<W> lv, y, pr, s;
           load<W>(lv, lu, nnz, k);
-          load<W>(y, w, ldw, col[k]);
+          load_w<W>(y, w, ldw, col[k]);
           mul_rn<W>(lv, y, pr);
           sub_rn<W>(acc, pr, s);
           acc = s;
