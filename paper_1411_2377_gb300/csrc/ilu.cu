@@ -25,17 +25,55 @@
 namespace mpk {
 namespace {
 
-// Loads through L2 only, for data the same kernel writes (the factor's row
-// in the factorisation, w in the one-block solves), which the read-only
-// path (ld.global.nc) does not allow.
+// Plain (weak) loads, for data the same kernel writes: a row's own factor
+// entries in the factorisation (written by the same thread) and w in the
+// one-block solves (written by threads of the same block before a barrier,
+// which orders them for every load of the block).  Only the read-only path
+// (ld.global.nc, what load() uses) may not see such writes.
 template <int W>
 __device__ __forceinline__ void load_w(Num<W>& a, const uint64_t* w, int64_t ld, int64_t i) {
-  unpack_head(__ldcg(w + i), a.e, a.s);
+  unpack_head(w[i], a.e, a.s);
 #pragma unroll
   for (int k = 0; k < W / 2; ++k) {
-    const uint64_t l = __ldcg(w + (int64_t)(k + 1) * ld + i);
+    const uint64_t l = w[(int64_t)(k + 1) * ld + i];
     a.m[2 * k] = (uint32_t)l;
     a.m[2 * k + 1] = (uint32_t)(l >> 32);
+  }
+}
+
+// acc <- RN(acc - RN(f_k z_k)) for k = k0, ..., k1 - 1 in turn (f the factor
+// entries, z = w at their columns): the products do not depend on acc, so
+// their loads and multiplications run in batches of B (4, 2 or 1 by the
+// registers a value takes), then the batch's subtractions in order.  WL:
+// load w with plain loads (the one-block solves, where this kernel wrote it).
+template <int W, bool WL>
+__device__ __forceinline__ void sub_products(Num<W>& acc, const uint64_t* __restrict__ lu,
+                                             int64_t nnz, const int32_t* __restrict__ col,
+                                             const uint64_t* w, int64_t ldw, int64_t k0,
+                                             int64_t k1) {
+  constexpr int B = W <= 8 ? 4 : (W <= 16 ? 2 : 1);
+  for (int64_t k = k0; k < k1; k += B) {
+    Num<W> pr[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      if (k + u < k1) {
+        Num<W> f, z;
+        load<W>(f, lu, nnz, k + u);
+        if (WL)
+          load_w<W>(z, w, ldw, col[k + u]);
+        else
+          load<W>(z, w, ldw, col[k + u]);
+        mul_rn<W>(f, z, pr[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      if (k + u < k1) {
+        Num<W> t;
+        sub_rn<W>(acc, pr[u], t);
+        acc = t;
+      }
+    }
   }
 }
 
@@ -107,6 +145,7 @@ template <int W>
 __global__ void lsolve_level_kernel(const int32_t* __restrict__ rows, int64_t count,
                                     const int64_t* __restrict__ rowptr,
                                     const int32_t* __restrict__ col,
+                                    const int64_t* __restrict__ diag,
                                     const uint64_t* __restrict__ lu, int64_t nnz,
                                     const uint64_t* __restrict__ r, int64_t ldr, uint64_t* w,
                                     int64_t ldw, const int* __restrict__ gate) {
@@ -116,14 +155,7 @@ __global__ void lsolve_level_kernel(const int32_t* __restrict__ rows, int64_t co
   const int32_t i = rows[t];
   Num<W> acc;
   load<W>(acc, r, ldr, i);
-  for (int64_t k = rowptr[i]; k < rowptr[i + 1] && col[k] < i; ++k) {
-    Num<W> l, y, p, s;
-    load<W>(l, lu, nnz, k);
-    load<W>(y, w, ldw, col[k]);
-    mul_rn<W>(l, y, p);
-    sub_rn<W>(acc, p, s);
-    acc = s;
-  }
+  sub_products<W, false>(acc, lu, nnz, col, w, ldw, rowptr[i], diag[i]);  // k < i: left of (i, i)
   store<W>(acc, w, ldw, i);
 }
 
@@ -140,14 +172,7 @@ __global__ void usolve_level_kernel(const int32_t* __restrict__ rows, int64_t co
   const int32_t i = rows[t];
   Num<W> acc, d, q;
   load<W>(acc, w, ldw, i);
-  for (int64_t k = diag[i] + 1; k < rowptr[i + 1]; ++k) {
-    Num<W> u, z, p, s;
-    load<W>(u, lu, nnz, k);
-    load<W>(z, w, ldw, col[k]);
-    mul_rn<W>(u, z, p);
-    sub_rn<W>(acc, p, s);
-    acc = s;
-  }
+  sub_products<W, false>(acc, lu, nnz, col, w, ldw, diag[i] + 1, rowptr[i + 1]);
   load<W>(d, lu, nnz, diag[i]);  // nonzero: checked when the factor was built
   div_rn<W>(acc, d, q);
   store<W>(q, w, ldw, i);
@@ -173,28 +198,14 @@ __global__ void __launch_bounds__(256) trsv_block_kernel(
       Num<W> acc;
       if (UPPER) {
         load_w<W>(acc, w, ldw, i);
-        for (int64_t k = diag[i] + 1; k < rowptr[i + 1]; ++k) {
-          Num<W> u, z, pr, s;
-          load<W>(u, lu, nnz, k);
-          load_w<W>(z, w, ldw, col[k]);
-          mul_rn<W>(u, z, pr);
-          sub_rn<W>(acc, pr, s);
-          acc = s;
-        }
+        sub_products<W, true>(acc, lu, nnz, col, w, ldw, diag[i] + 1, rowptr[i + 1]);
         Num<W> d, q;
         load<W>(d, lu, nnz, diag[i]);
         div_rn<W>(acc, d, q);
         store<W>(q, w, ldw, i);
       } else {
         load<W>(acc, r, ldr, i);
-        for (int64_t k = rowptr[i]; k < rowptr[i + 1] && col[k] < i; ++k) {
-          Num<W> lv, y, pr, s;
-          load<W>(lv, lu, nnz, k);
-          load_w<W>(y, w, ldw, col[k]);
-          mul_rn<W>(lv, y, pr);
-          sub_rn<W>(acc, pr, s);
-          acc = s;
-        }
+        sub_products<W, true>(acc, lu, nnz, col, w, ldw, rowptr[i], diag[i]);
         store<W>(acc, w, ldw, i);
       }
     }
@@ -228,7 +239,8 @@ mp_status launch_ilu0_apply(const mp_ilu_s* M, const uint64_t* r, int64_t ldr, u
     for (int64_t l = 0; l < M->nl; ++l) {
       const int64_t cnt = M->lvl_l[l + 1] - M->lvl_l[l];
       lsolve_level_kernel<W><<<blocks_for(cnt, tpb), tpb, 0, st>>>(
-          M->rows_l + M->lvl_l[l], cnt, M->rowptr, M->col, M->lu, M->nnz, r, ldr, w, ldw, gate);
+          M->rows_l + M->lvl_l[l], cnt, M->rowptr, M->col, M->diag, M->lu, M->nnz, r, ldr, w,
+          ldw, gate);
     }
     for (int64_t l = 0; l < M->nu; ++l) {
       const int64_t cnt = M->lvl_u[l + 1] - M->lvl_u[l];
