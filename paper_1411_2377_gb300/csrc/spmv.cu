@@ -23,7 +23,7 @@ namespace mpk {
 namespace {
 
 constexpr int kThreads = 128;   // 4 chunks per block
-constexpr int kFastSpan = 512;  // bits of exponent span handled per thread
+constexpr int kFastSpan = 384;  // bits of exponent span handled per thread
 
 // Bits of a row sum kept below the top p bits of its largest term by the
 // windowed EXACT form (the rest is checked, not computed; see below).
