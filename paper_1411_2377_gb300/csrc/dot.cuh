@@ -199,19 +199,45 @@ __device__ void dot_block_partial(const DotDev& a, const DotScratch& s, int j, i
     return;
   }
   for (int d = 0; d < nd; ++d) c[d * kDotThreads] = 0;
-  for (int64_t t = r.base + threadIdx.x; t < r.end; t += r.stride) {
-    const int64_t i = index(t);
-    if (i < 0) continue;
-    Num<W> x, y;
-    load<W>(x, a.x[j], a.ldx[j], i);
-    load<W>(y, a.y[j], a.ldy[j], i);
-    if (zero_e(x.e) || zero_e(y.e)) continue;
+  auto accumulate = [&](const Num<W>& x, const Num<W>& y) {
+    if (zero_e(x.e) || zero_e(y.e)) return;
     uint32_t P[2 * W];
     if (W >= 16)
       mul_full_ilp<W>(x.m, y.m, P);
     else
       mul_full<W>(x.m, y.m, P);
     add_term<W>(c, kDotThreads, P, x.e + y.e - anchor, x.s ^ y.s);
+  };
+  if constexpr (W <= 16) {
+    // the next element's operands are loaded before the current one is
+    // multiplied and added (its load latency overlaps that work)
+    int64_t t = r.base + threadIdx.x;
+    int64_t in = t < r.end ? index(t) : -1;
+    Num<W> xn, yn;
+    if (in >= 0) {
+      load<W>(xn, a.x[j], a.ldx[j], in);
+      load<W>(yn, a.y[j], a.ldy[j], in);
+    }
+    while (t < r.end) {
+      const int64_t i = in;
+      const Num<W> x = xn, y = yn;
+      t += r.stride;
+      in = t < r.end ? index(t) : -1;
+      if (in >= 0) {
+        load<W>(xn, a.x[j], a.ldx[j], in);
+        load<W>(yn, a.y[j], a.ldy[j], in);
+      }
+      if (i >= 0) accumulate(x, y);
+    }
+  } else {
+    for (int64_t t = r.base + threadIdx.x; t < r.end; t += r.stride) {
+      const int64_t i = index(t);
+      if (i < 0) continue;
+      Num<W> x, y;
+      load<W>(x, a.x[j], a.ldx[j], i);
+      load<W>(y, a.y[j], a.ldy[j], i);
+      accumulate(x, y);
+    }
   }
   __syncthreads();
   for (int d = warp; d < nd; d += kDotWarps) {
