@@ -20,6 +20,7 @@
 #include <cstring>
 #include <vector>
 
+#include "gpbicg.cuh"
 #include "internal.h"
 #include "mpdev.cuh"
 
@@ -474,25 +475,16 @@ struct BV {
 
 enum { VR, VRT, VP, VQ, VT, VV, VW, VY, VU, VZ, VS };
 
+// The element steps are gpbicg.cuh's (the single solver's), per instance:
+// its scalars are the K-vector entries of the element's instance.
 template <int W>
 __global__ void b_wp(const int* done, const int32_t* inst, const uint64_t* S, int K, const BV V) {
   ELEM_LOOP(i, V.N) {
     const int k = inst[i];
     if (done[k]) continue;
-    Num<W> beta, a, b, c;
+    Num<W> beta;
     lds<W>(beta, S, K, BETA, k);
-    load<W>(a, V.v[VQ], V.ld, i);
-    mul_rn<W>(beta, a, b);
-    load<W>(a, V.v[VV], V.ld, i);
-    add_rn<W>(a, b, c);
-    store<W>(c, V.v[VW], V.ld, i);
-    load<W>(a, V.v[VP], V.ld, i);
-    load<W>(b, V.v[VU], V.ld, i);
-    sub_rn<W>(a, b, c);
-    mul_rn<W>(beta, c, a);
-    load<W>(b, V.v[VR], V.ld, i);
-    add_rn<W>(b, a, c);
-    store<W>(c, V.v[VP], V.ld, i);
+    gp_wp_elem<W>(i, beta, V.v[VV], V.v[VQ], V.v[VR], V.v[VP], V.v[VU], V.v[VW], V.ld);
   }
 }
 
@@ -502,9 +494,10 @@ __global__ void b_sty(const int* done, const int32_t* inst, const uint64_t* S, i
   ELEM_LOOP(i, V.N) {
     const int k = inst[i];
     if (done[k]) continue;
-    Num<W> alpha, a, b, c, sv, aq;
+    Num<W> alpha;
     lds<W>(alpha, S, K, ALPHA, k);
-    if (first) {
+    if (first) {  // t = r - alpha q;  y = alpha q - r
+      Num<W> a, c, aq;
       load<W>(a, V.v[VQ], V.ld, i);
       mul_rn<W>(alpha, a, aq);
       load<W>(a, V.v[VR], V.ld, i);
@@ -514,69 +507,27 @@ __global__ void b_sty(const int* done, const int32_t* inst, const uint64_t* S, i
       store<W>(c, V.v[VY], V.ld, i);
       continue;
     }
-    load<W>(a, V.v[VT], V.ld, i);
-    load<W>(b, V.v[VR], V.ld, i);
-    sub_rn<W>(a, b, sv);
-    store<W>(sv, V.v[VS], V.ld, i);
-    load<W>(a, V.v[VQ], V.ld, i);
-    mul_rn<W>(alpha, a, c);
-    sub_rn<W>(b, c, a);
-    store<W>(a, V.v[VT], V.ld, i);
-    load<W>(a, V.v[VW], V.ld, i);
-    load<W>(b, V.v[VQ], V.ld, i);
-    sub_rn<W>(a, b, c);
-    mul_rn<W>(alpha, c, a);
-    sub_rn<W>(sv, a, c);
-    store<W>(c, V.v[VY], V.ld, i);
+    gp_sty_elem<W>(i, alpha, V.v[VR], V.v[VQ], V.v[VW], V.v[VS], V.v[VT], V.v[VY], V.ld);
   }
 }
 
 template <int W>
 __global__ void b_uzxr(const int* done, const int32_t* inst, const uint64_t* S, int K, const BV V,
                        uint64_t* x, int64_t ldx) {
+  Vecs U{};
+  U.v[0] = V.v[VQ]; U.v[1] = V.v[VS]; U.v[2] = V.v[VU]; U.v[3] = V.v[VR]; U.v[4] = V.v[VZ];
+  U.v[5] = V.v[VP]; U.v[6] = V.v[VT]; U.v[7] = V.v[VY]; U.v[8] = V.v[VV];
+  U.ld = V.ld;
+  U.n = V.N;
   ELEM_LOOP(i, V.N) {
     const int k = inst[i];
     if (done[k]) continue;
-    const int64_t ld = V.ld;
-    Num<W> sc, a, b, c, un, zn;
-    lds<W>(sc, S, K, BETA, k);
-    load<W>(a, V.v[VU], ld, i);
-    mul_rn<W>(sc, a, b);
-    load<W>(a, V.v[VS], ld, i);
-    add_rn<W>(a, b, c);
-    lds<W>(sc, S, K, ETA, k);
-    mul_rn<W>(sc, c, b);
-    lds<W>(sc, S, K, ZETA, k);
-    load<W>(a, V.v[VQ], ld, i);
-    mul_rn<W>(sc, a, c);
-    add_rn<W>(c, b, un);
-    store<W>(un, V.v[VU], ld, i);
-    load<W>(a, V.v[VR], ld, i);
-    mul_rn<W>(sc, a, b);
-    lds<W>(sc, S, K, ETA, k);
-    load<W>(a, V.v[VZ], ld, i);
-    mul_rn<W>(sc, a, c);
-    add_rn<W>(b, c, a);
-    lds<W>(sc, S, K, ALPHA, k);
-    mul_rn<W>(sc, un, b);
-    sub_rn<W>(a, b, zn);
-    store<W>(zn, V.v[VZ], ld, i);
-    load<W>(a, V.v[VP], ld, i);
-    mul_rn<W>(sc, a, b);
-    load<W>(a, x, ldx, i);
-    add_rn<W>(a, b, c);
-    add_rn<W>(c, zn, a);
-    store<W>(a, x, ldx, i);
-    lds<W>(sc, S, K, ETA, k);
-    load<W>(a, V.v[VY], ld, i);
-    mul_rn<W>(sc, a, b);
-    load<W>(a, V.v[VT], ld, i);
-    sub_rn<W>(a, b, c);
-    lds<W>(sc, S, K, ZETA, k);
-    load<W>(a, V.v[VV], ld, i);
-    mul_rn<W>(sc, a, b);
-    sub_rn<W>(c, b, a);
-    store<W>(a, V.v[VR], ld, i);
+    Num<W> beta, eta, zeta, alpha;
+    lds<W>(beta, S, K, BETA, k);
+    lds<W>(eta, S, K, ETA, k);
+    lds<W>(zeta, S, K, ZETA, k);
+    lds<W>(alpha, S, K, ALPHA, k);
+    gp_uzxr_elem<W>(i, beta, eta, zeta, alpha, U, x, ldx);
   }
 }
 
