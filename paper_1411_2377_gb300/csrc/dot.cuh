@@ -268,10 +268,16 @@ struct NoPost {
   __device__ void operator()(int) const {}
 };
 
-// Shared memory of one block's finalize of a dot.
+// Shared memory of one block's finalize of a dot.  The partials are summed
+// into kFinGroups windows (the warps of a block split into groups) and the
+// windows then into sum: many blocks' digits landing on the same few global
+// digits would otherwise serialise on those addresses' shared atomics.
+constexpr int kFinGroups = 4;
+
 template <int W>
 struct DotFinSmem {
   int64_t sum[DotWin<W>::cap];
+  int64_t part[kFinGroups * DotWin<W>::cap];  // group g's window: part[g * nd ...]
   long long red[64];
   int off_of[kDotMaxBlocks];  // block b's digit offset (its nd_of[b] = 0: no partial)
   int nd_of[kDotMaxBlocks];
@@ -299,7 +305,7 @@ __device__ void dot_finalize_one(const DotDev& a, const DotScratch& s, int j,
     const long long A = (lo >> 5) * 32;
     const int nd = dot_digits(hi - A, W);
     if (threadIdx.x == 0) f.ndmax = 0;
-    for (int d = threadIdx.x; d < nd; d += blockDim.x) f.sum[d] = 0;
+    for (int d = threadIdx.x; d < kFinGroups * nd; d += blockDim.x) f.part[d] = 0;
     __syncthreads();
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
       const long long l = __ldcg(blo + b), h = __ldcg(bhi + b);
@@ -319,11 +325,20 @@ __device__ void dot_finalize_one(const DotDev& a, const DotScratch& s, int j,
     // consecutive items are consecutive digits of one block (coalesced)
     const int m = f.ndmax;
     const int64_t* part = s.partials + (size_t)j * nb * DotWin<W>::cap;
+    const int grp = (int)((threadIdx.x >> 5) % kFinGroups);
+    int64_t* win = f.part + (size_t)grp * nd;
     for (int q = threadIdx.x; q < nb * m; q += blockDim.x) {
       const int b = q / m, d = q - b * m;
       if (d < f.nd_of[b])
-        atomicAdd(reinterpret_cast<unsigned long long*>(&f.sum[f.off_of[b] + d]),
+        atomicAdd(reinterpret_cast<unsigned long long*>(&win[f.off_of[b] + d]),
                   (unsigned long long)__ldcg(part + (size_t)b * DotWin<W>::cap + d));
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < nd; d += blockDim.x) {
+      int64_t t = 0;
+#pragma unroll
+      for (int g = 0; g < kFinGroups; ++g) t += f.part[(size_t)g * nd + d];
+      f.sum[d] = t;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
