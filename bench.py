@@ -112,11 +112,16 @@ def profiled_traffic(kernel_key):
     return None
 
 
+# Bits the windowed EXACT kernel keeps below the top p bits of a row's
+# largest term (its kTopGuard); windowed_issued follows the same rule.
+TOP_GUARD = 80
+
+
 def windowed_issued(p, rowptr, colidx, vplanes, xplanes, products):
     """32x32->64 multiplies the windowed EXACT kernel issues per nonzero
     product on this workload, from its window rule: with the row's nonzero
     terms at exponents E in [emin, emax] (span = emax - emin), the counters
-    start at radix-2^29 digit wb = (span + p - 128) // 29, a term sits at digit
+    start at radix-2^29 digit wb = (span + p - TOP_GUARD) // 29, a term sits at digit
     q = (E - emin) // 29, and of its NA x NX column product (NA = ceil(p/29)
     limbs of a, NX = ceil((p + 28)/29) of the shifted x) only the columns
     k >= max(0, wb - q) are computed.  (The rare rows whose rounding the
@@ -141,7 +146,7 @@ def windowed_issued(p, rowptr, colidx, vplanes, xplanes, products):
     np.minimum.at(emin, row[live], E[live])
     np.maximum.at(emax, row[live], E[live])
     span = emax - emin
-    wb = (span + 32 * W - 128) // R
+    wb = (span + 32 * W - TOP_GUARD) // R
     q = (E - emin[row]) // R
     kmin = np.clip(wb[row] - q, 0, nc)
     issued = int(suffix[kmin][live].sum())

@@ -26,8 +26,12 @@ constexpr int kThreads = 128;   // 4 chunks per block
 constexpr int kFastSpan = 384;  // bits of exponent span handled per thread
 
 // Bits of a row sum kept below the top p bits of its largest term by the
-// windowed EXACT form (the rest is checked, not computed; see below).
-constexpr int kTopGuard = 128;
+// windowed EXACT form (the rest is checked, not computed; see below).  A row
+// whose sum falls more than about kTopGuard - 48 bits below its largest term
+// (the skipped columns' error bound is 42 + log2(len) bits, and 8 decisive
+// bits are asked for) goes to the exact kernel; fewer guard bits skip more
+// columns of every product.
+constexpr int kTopGuard = 80;
 
 template <int W>
 struct Win {
