@@ -151,22 +151,34 @@ __device__ __forceinline__ uint64_t gather_head(const SellView& S, const uint64_
   return S.xrec ? __ldg(S.xrec + (int64_t)c * S.xrs) : __ldg(x + c);
 }
 
-// Record copy of x for the gathers (one thread per element).
+// Record copy of x for the gathers.  A warp takes 32 consecutive elements:
+// it loads their planes (consecutive lanes, consecutive addresses), lays the
+// 32 records out in shared memory and writes them as one contiguous run of
+// 32 records, so that its stores are coalesced too (a thread writing its own
+// record would leave a warp's stores a record apart).  256 threads a block.
 template <int W>
-__global__ void to_records_kernel(const uint64_t* __restrict__ x, int64_t ldx, int64_t n,
-                                  uint64_t* __restrict__ xr, int rs) {
+__global__ void __launch_bounds__(256) to_records_kernel(const uint64_t* __restrict__ x,
+                                                         int64_t ldx, int64_t n,
+                                                         uint64_t* __restrict__ xr) {
   constexpr int L = W / 2;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    uint64_t w[(L + 2) / 2 * 2];
+  constexpr int RS = (L + 2) & ~1;  // words per record: L + 1 rounded up to even
+  constexpr int SP = RS + 1;        // odd stride in shared memory: no bank conflicts
+  __shared__ uint64_t tile[8][32 * SP];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint64_t* t = tile[warp];
+  const int64_t ntiles = (n + 31) / 32;
+  for (int64_t tl = blockIdx.x * 8LL + warp; tl < ntiles; tl += (int64_t)gridDim.x * 8) {
+    const int64_t i0 = tl * 32;
+    const int cnt = (int)(n - i0 < 32 ? n - i0 : 32);
+    if (lane < cnt) {
 #pragma unroll
-    for (int k = 0; k <= L; ++k) w[k] = __ldg(x + (int64_t)k * ldx + i);
-    if ((L + 1) & 1) w[L + 1] = 0u;
-    uint4* r = reinterpret_cast<uint4*>(xr + i * rs);
-#pragma unroll
-    for (int k = 0; k < (L + 2) / 2; ++k)
-      r[k] = make_uint4((uint32_t)w[2 * k], (uint32_t)(w[2 * k] >> 32), (uint32_t)w[2 * k + 1],
-                        (uint32_t)(w[2 * k + 1] >> 32));
+      for (int k = 0; k <= L; ++k) t[lane * SP + k] = __ldg(x + (int64_t)k * ldx + i0 + lane);
+      if (RS > L + 1) t[lane * SP + L + 1] = 0u;
+    }
+    __syncwarp();
+    uint64_t* dst = xr + i0 * RS;
+    for (int w = lane; w < cnt * RS; w += 32) dst[w] = t[(w / RS) * SP + (w % RS)];
+    __syncwarp();
   }
 }
 
@@ -843,7 +855,7 @@ mp_status spmv_w(const mp_csr_s* M, const Sell& S, int mode, const uint64_t* x, 
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t nb = std::min<int64_t>((M->n + 255) / 256, (int64_t)sms * 8);
-    to_records_kernel<W><<<(int)std::max<int64_t>(nb, 1), 256, 0, st>>>(x, ldx, M->n, Mw->xrec, rs);
+    to_records_kernel<W><<<(int)std::max<int64_t>(nb, 1), 256, 0, st>>>(x, ldx, M->n, Mw->xrec);
     count_launch();
     V.xrec = Mw->xrec;
     V.xrs = rs;
