@@ -365,7 +365,7 @@ mp_status launch_spmv_big(const mp_csr_s* M, const Sell& S, int mode, const uint
   if (S.nchunks == 0) return MP_OK;
   BigSell B{S.nslots, S.nchunks, S.chunk_off, S.row_of, S.row_len, S.col, S.val};
   // the matrix's overflow-list word (unused at these precisions) is the row counter
-  unsigned* next = reinterpret_cast<unsigned*>(M->ovf);
+  unsigned* next = reinterpret_cast<unsigned*>(ovf_of(M, S));
   MPK_CUDA(cudaMemsetAsync(next, 0, sizeof(unsigned), st));
   return dispatch_big(M->prec, [&](auto w) -> mp_status {
     constexpr int W = decltype(w)::value;

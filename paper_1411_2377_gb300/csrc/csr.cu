@@ -431,6 +431,7 @@ mp_status create_impl(int64_t n, const int64_t* rowptr, const int32_t* colidx,
     free_sell(M->A);
     free_sell(M->AT);
     cudaFree(M->ovf);
+    cudaFree(M->ovf_t);
     delete M;
     return s;
   };
@@ -635,8 +636,10 @@ mp_status create_impl(int64_t n, const int64_t* rowptr, const int32_t* colidx,
     M->has_t = true;
   }
   if ((r = dalloc(&M->ovf, (size_t)n + 1, M->bytes)) != MP_OK) return fail(r);
+  if (M->has_t && (r = dalloc(&M->ovf_t, (size_t)n + 1, M->bytes)) != MP_OK) return fail(r);
   {
     cudaError_t e = cudaMemsetAsync(M->ovf, 0, sizeof(int32_t), st);
+    if (e == cudaSuccess && M->ovf_t) e = cudaMemsetAsync(M->ovf_t, 0, sizeof(int32_t), st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail(cuda_error(e, "finishing create"));
   }
@@ -677,8 +680,10 @@ mp_status mp_csr_destroy(mp_csr A) {
   free_sell(A->A);
   free_sell(A->AT);
   cudaFree(A->ovf);
+  cudaFree(A->ovf_t);
   cudaFree(A->a64);
   cudaFree(A->xrec);
+  cudaFree(A->xrec_t);
   cudaFree(A->rowscale);
   delete A;
   cudaSetDevice(cur);

@@ -37,7 +37,11 @@ struct mp_csr_s {
   int device = 0;
   bool has_t = false;
   mpk::Sell A, AT;
-  int32_t* ovf = nullptr;  // [n + 1]: overflow-row count then rows (EXACT wide path)
+  // [n + 1]: overflow-row count then rows (EXACT wide path); ovf_t for
+  // products with A^T, so that a product with A and one with A^T can run at
+  // the same time (BiCG's two products)
+  int32_t* ovf = nullptr;
+  int32_t* ovf_t = nullptr;
   int64_t bytes = 0;
   // SpMV launch configuration per mode (ORDERED [0], EXACT [1]), set by
   // mp_csr_tune / mp_csr_set_config: threads per block, variant bits and
@@ -46,8 +50,10 @@ struct mp_csr_s {
   int32_t cfg_tpb[2] = {-1, -1};
   int32_t cfg_var[2] = {-1, -1};
   int32_t cfg_carve[2] = {-1, -1};
-  // record copy of x for the gathers (variant bit 3), allocated on first use
+  // record copy of x for the gathers (variant bit 3), allocated on first use;
+  // xrec_t for products with A^T
   uint64_t* xrec = nullptr;
+  uint64_t* xrec_t = nullptr;
   // mean distinct 32-byte groups a warp's gather of one x plane touches (8..32)
   double gather_sectors = 0.0;
   // FP64 copy for mixed-precision refinement (built on first use): the
@@ -77,6 +83,13 @@ struct mp_ilu_s {
 };
 
 namespace mpk {
+
+// The scratch of a product with layout S of M (A or A^T): its overflow list
+// and its record copy of x.
+inline bool is_transposed(const mp_csr_s* M, const Sell& S) { return &S == &M->AT; }
+inline int32_t* ovf_of(const mp_csr_s* M, const Sell& S) {
+  return is_transposed(M, S) && M->ovf_t ? M->ovf_t : M->ovf;
+}
 
 // w = (LU)^{-1} r with an ILU(0) factor, one launch per level; gate as for
 // the SpMV (a nonzero flag makes every launch return at once).

@@ -51,6 +51,9 @@ struct SolveCall {
   cudaStream_t st;
   const mp_ilu_s* pre;  // ILU(0) preconditioner K (BiCGSTAB), or null
   int pre_left;         // 1: K applied on the left (Section 4.2), 0: on the right
+  // BiCG: a second stream and two events, for A^T p~ beside A p
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 template <int W>
@@ -771,13 +774,23 @@ mp_status bi_iteration(const Work& w, const SolveCall& c, bool first) {
     launch_pdl(bi_p<W>, g, 128, 0, st, w.st, w.S, w.vec(R), w.vec(RT), w.vec(P), w.vec(PT), ld, n);
     count_launch();
   }
-  if ((r = launch_spmv(c.A, op_a(c),c.o.mode, w.vec(P), ld, w.vec(Z), ld, nullptr, 0, gate, st)) != MP_OK)
+  // z~ = A^T p~ does not depend on z = A p: it runs on the second stream
+  // (forked after the p update, joined before the x, r updates that use it),
+  // beside z = A p and the (p~, z) dot and alpha on the first
+  cudaError_t ce = cudaEventRecord(c.ev_fork, st);
+  if (ce == cudaSuccess) ce = cudaStreamWaitEvent(c.st2, c.ev_fork, 0);
+  if (ce != cudaSuccess) return cuda_error(ce, "forking A^T p~");
+  if ((r = launch_spmv(c.A, op_at(c), c.o.mode, w.vec(PT), ld, w.vec(ZT), ld, nullptr, 0, gate,
+                       c.st2)) != MP_OK)
     return r;
-  if ((r = launch_spmv(c.A, op_at(c),c.o.mode, w.vec(PT), ld, w.vec(ZT), ld, nullptr, 0, gate, st)) != MP_OK)
+  if ((ce = cudaEventRecord(c.ev_join, c.st2)) != cudaSuccess) return cuda_error(ce, "joining A^T p~");
+  if ((r = launch_spmv(c.A, op_a(c), c.o.mode, w.vec(P), ld, w.vec(Z), ld, nullptr, 0, gate, st)) != MP_OK)
     return r;
   if ((r = dot2<W>(w, w.vec(PT), w.vec(Z), DEN, nullptr, nullptr, 0, st, gate,
                    PostAlpha<W>{w.st, w.S})) != MP_OK)
     return r;
+  if ((ce = cudaStreamWaitEvent(st, c.ev_join, 0)) != cudaSuccess)
+    return cuda_error(ce, "joining A^T p~");
   launch_pdl(bi_xr<W>, g, 128, 0, st, w.st, w.S, w.vec(P), w.vec(Z), w.vec(ZT), w.vec(R), w.vec(RT),
                               c.x.data, c.x.ld, ld, n);
   count_launch();
@@ -889,6 +902,18 @@ mp_status solve_w(const SolveCall& cu, mp_solve_info* info) {
   SolveCall c = cu;
   c.st = st;
   const int64_t n = c.A->n;
+  if (M == kBiCG) {
+    ces = cudaStreamCreateWithFlags(&c.st2, cudaStreamNonBlocking);
+    if (ces == cudaSuccess) ces = cudaEventCreateWithFlags(&c.ev_fork, cudaEventDisableTiming);
+    if (ces == cudaSuccess) ces = cudaEventCreateWithFlags(&c.ev_join, cudaEventDisableTiming);
+    if (ces != cudaSuccess) {
+      if (c.ev_fork) cudaEventDestroy(c.ev_fork);
+      if (c.st2) cudaStreamDestroy(c.st2);
+      cudaEventDestroy(fence);
+      cudaStreamDestroy(st);
+      return cuda_error(ces, "solver stream set-up");
+    }
+  }
   Work w;
   const int kVecs = M == kGPBiCG ? 11 : (M == kCGS || c.pre ? 8 : 6);
   mp_status r = alloc_work(w, c.A->prec, n, kVecs, st);
@@ -1028,6 +1053,12 @@ mp_status solve_w(const SolveCall& cu, mp_solve_info* info) {
   cudaEventRecord(fence, st);
   cudaStreamWaitEvent(cu.st, fence, 0);
   cudaStreamSynchronize(st);
+  if (c.st2) {
+    cudaStreamSynchronize(c.st2);
+    cudaEventDestroy(c.ev_fork);
+    cudaEventDestroy(c.ev_join);
+    cudaStreamDestroy(c.st2);
+  }
   cudaEventDestroy(fence);
   cudaStreamDestroy(st);
   if (r != MP_OK) return r;

@@ -849,15 +849,16 @@ mp_status spmv_w(const mp_csr_s* M, const Sell& S, int mode, const uint64_t* x, 
   if (cf.rec) {  // gathers from a record copy of x (one pass over x first)
     mp_csr_s* Mw = const_cast<mp_csr_s*>(M);
     const int rs = record_words(W);
-    if (!Mw->xrec)
-      MPK_CUDA(cudaMalloc((void**)&Mw->xrec, sizeof(uint64_t) * rs * (size_t)(M->n > 0 ? M->n : 1)));
+    uint64_t*& xrec = is_transposed(M, S) ? Mw->xrec_t : Mw->xrec;
+    if (!xrec)
+      MPK_CUDA(cudaMalloc((void**)&xrec, sizeof(uint64_t) * rs * (size_t)(M->n > 0 ? M->n : 1)));
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t nb = std::min<int64_t>((M->n + 255) / 256, (int64_t)sms * 8);
-    to_records_kernel<W><<<(int)std::max<int64_t>(nb, 1), 256, 0, st>>>(x, ldx, M->n, Mw->xrec);
+    to_records_kernel<W><<<(int)std::max<int64_t>(nb, 1), 256, 0, st>>>(x, ldx, M->n, xrec);
     count_launch();
-    V.xrec = Mw->xrec;
+    V.xrec = xrec;
     V.xrs = rs;
   }
   const int blocks = (int)((S.nchunks * 32 + tpb - 1) / tpb);
@@ -894,7 +895,8 @@ mp_status spmv_w(const mp_csr_s* M, const Sell& S, int mode, const uint64_t* x, 
   }
   int* status = status_word();
   if (!status) return set_error(MP_ERR_CUDA, "status word unavailable");
-  MPK_CUDA(cudaMemsetAsync(M->ovf, 0, sizeof(int32_t), st));
+  int32_t* const ovf = ovf_of(M, S);
+  MPK_CUDA(cudaMemsetAsync(ovf, 0, sizeof(int32_t), st));
   const bool cols = cf.cols;
   // the windowed form serves y = A x only; the residual keeps the full window
   const bool top = cf.top && !b;
@@ -909,14 +911,14 @@ mp_status spmv_w(const mp_csr_s* M, const Sell& S, int mode, const uint64_t* x, 
     // the gathers of x
     MPK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                   cf.carve < 0 ? (int)cudaSharedmemCarveoutDefault : cf.carve));
-    kern<<<blocks, tpb, smem, st>>>(V, x, ldx, y, ldy, bb, ldb, M->ovf, status, gate);
+    kern<<<blocks, tpb, smem, st>>>(V, x, ldx, y, ldy, bb, ldb, ovf, status, gate);
     return MP_OK;
   };
   mp_status r;
   if (b) {
     r = cols ? exact(spmv_exact_kernel<W, true, true>, b) : exact(spmv_exact_kernel<W, true, false>, b);
     if (r != MP_OK) return r;
-    spmv_exact_wide_kernel<W, true><<<sms * 4, 32, 0, st>>>(V, x, ldx, y, ldy, b, ldb, M->ovf,
+    spmv_exact_wide_kernel<W, true><<<sms * 4, 32, 0, st>>>(V, x, ldx, y, ldy, b, ldb, ovf,
                                                             status, gate);
   } else {
     const bool stage = cf.stage, wide = cf.wide;
@@ -924,7 +926,7 @@ mp_status spmv_w(const mp_csr_s* M, const Sell& S, int mode, const uint64_t* x, 
       MPK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       MPK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                     cf.carve < 0 ? (int)cudaSharedmemCarveoutDefault : cf.carve));
-      kern<<<blocks, tpb, smem, st>>>(V, x, ldx, y, ldy, M->ovf, status, gate);
+      kern<<<blocks, tpb, smem, st>>>(V, x, ldx, y, ldy, ovf, status, gate);
       return MP_OK;
     };
     bool launched = false;
@@ -953,7 +955,7 @@ mp_status spmv_w(const mp_csr_s* M, const Sell& S, int mode, const uint64_t* x, 
       r = exact(spmv_exact_kernel<W, false, true, false, 8>, nullptr);
     if (r != MP_OK) return r;
     spmv_exact_wide_kernel<W, false><<<sms * 4, 32, 0, st>>>(V, x, ldx, y, ldy, nullptr, 0,
-                                                             M->ovf, status, gate);
+                                                             ovf, status, gate);
   }
   count_launch(2);
   return launch_check("spmv_exact_kernel");
