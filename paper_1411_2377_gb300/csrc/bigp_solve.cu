@@ -416,6 +416,9 @@ mp_status solve_big_w(int method, mp_csr A, mp_vec b, mp_vec x, const mp_solve_o
   const size_t vbytes = sizeof(uint64_t) * (L + 1) * (size_t)s.ld;
   uint64_t* V = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
+  // BiCG: a second stream and two events, for A^T p~ beside A p
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   BState hs{0, MP_ERR_NOCONV, 0};
   mp_status r = MP_OK;
   // a failing CUDA call ends the solve through the cleanup below
@@ -423,6 +426,12 @@ mp_status solve_big_w(int method, mp_csr A, mp_vec b, mp_vec x, const mp_solve_o
     return e == cudaSuccess ? MP_OK : cuda_error(e, what);
   };
   do {
+    if (method == 0) {
+      r = ok(cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking), "cudaStreamCreate");
+      if (r == MP_OK) r = ok(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming), "cudaEventCreate");
+      if (r == MP_OK) r = ok(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming), "cudaEventCreate");
+      if (r != MP_OK) break;
+    }
     if ((r = ok(cudaMalloc((void**)&V, vbytes * nvec), "cudaMalloc")) != MP_OK) break;
     r = ok(cudaMalloc((void**)&s.S, sizeof(uint64_t) * (L + 1) * NSLOT),
            "cudaMalloc");
@@ -485,14 +494,22 @@ mp_status solve_big_w(int method, mp_csr A, mp_vec b, mp_vec x, const mp_solve_o
           if ((r = s.lin(pv, rv, pv, BETA, 0)) != MP_OK) break;  // p = r + beta p
           if ((r = s.lin(pt, rt, pt, BETA, 0)) != MP_OK) break;  // p~ = r~ + beta p~
         }
+        // z~ = A^T p~ on the second stream, beside z = A p, the (p~, z) dot
+        // and alpha; joined before r~ takes it
+        if ((r = ok(cudaEventRecord(ev_fork, st), "cudaEventRecord")) != MP_OK) break;
+        if ((r = ok(cudaStreamWaitEvent(st2, ev_fork, 0), "cudaStreamWaitEvent")) != MP_OK) break;
+        if ((r = launch_spmv_big(A, *s.SAT, s.mode, pt, s.ld, zt, s.ld, nullptr, 0, s.gate(),
+                                 st2)) != MP_OK)
+          break;  // z~ = A^T p~
+        if ((r = ok(cudaEventRecord(ev_join, st2), "cudaEventRecord")) != MP_OK) break;
         if ((r = s.spmv(*s.SA, pv, z)) != MP_OK) break;    // z = A p
-        if ((r = s.spmv(*s.SAT, pt, zt)) != MP_OK) break;  // z~ = A^T p~
         if ((r = s.dot(pt, z, DEN)) != MP_OK) break;
         Prog p1;
         p1.add(kBrkZ, 0, DEN).add(kDiv, ALPHA, RHO, DEN);
         if ((r = s.run(p1)) != MP_OK) break;
         if ((r = s.lin(xw, xw, pv, ALPHA, 0)) != MP_OK) break;      // x = x + alpha p
         if ((r = s.lin(rv, rv, z, ALPHA, kNegB)) != MP_OK) break;   // r = r - alpha z
+        if ((r = ok(cudaStreamWaitEvent(st, ev_join, 0), "cudaStreamWaitEvent")) != MP_OK) break;
         if ((r = s.lin(rt, rt, zt, ALPHA, kNegB)) != MP_OK) break;  // r~ = r~ - alpha z~
       } else if (method == 2) {  // CGS (textbook form, the oracle's reading)
         uint64_t *u = vec(3), *q = vec(4), *v = vec(5), *w = vec(6), *aw = vec(7), *tmp = vec(8);
@@ -670,6 +687,12 @@ mp_status solve_big_w(int method, mp_csr A, mp_vec b, mp_vec x, const mp_solve_o
     }
   } while (false);
   cudaStreamSynchronize(st);
+  if (st2) {
+    cudaStreamSynchronize(st2);
+    cudaStreamDestroy(st2);
+  }
+  if (ev_fork) cudaEventDestroy(ev_fork);
+  if (ev_join) cudaEventDestroy(ev_join);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   cudaFree(V);
