@@ -137,3 +137,32 @@ def test_dot_at_the_benchmark_size(p):
     assert lib.mp_dot_noalloc(x.c(), y.c(), out.c(), mpk._stream(None)) == 0
     mpk.check()
     assert_bitwise(out.planes(), want[None], f"dot_noalloc p={p} n=1e6")
+
+
+@pytest.mark.parametrize("p", (128, 1024))
+def test_dot_right_after_a_kernel_that_writes_its_operand(p):
+    """The dot kernels are launched programmatically (they may start while
+    the previous kernel in the stream finishes and wait on the device for
+    it): a dot issued right after a kernel that writes x, on the same stream
+    and without a host sync, sees the written x.  Eight rounds, each writing
+    a different x, every result against the oracle."""
+    mpk = need_gpu()
+    import torch
+
+    n = 200_000
+    Y = rand_planes(n, p, 91, zero_frac=0.01, emin=-30, emax=30)
+    y = mpk.Vec.from_planes(Y, p)
+    src = [mpk.Vec.from_planes(rand_planes(n, p, 92 + k, zero_frac=0.01, emin=-30, emax=30), p)
+           for k in range(8)]
+    x = mpk.Vec.empty(n, p)
+    zero = torch.zeros_like(x.t)
+    outs = []
+    torch.cuda.synchronize()
+    for k in range(8):
+        torch.bitwise_xor(src[k].t, zero, out=x.t)  # an elementwise kernel writes x
+        outs.append(mpk.dot(x, y, sync=False))
+    torch.cuda.synchronize()
+    for k in range(8):
+        want, st = oracle.dot(p, recs(src[k].planes()), recs(Y))
+        assert st == oracle.OK
+        assert_bitwise(outs[k].planes(), want[None], f"dot after a producer, round {k}")
