@@ -127,6 +127,46 @@ __device__ __forceinline__ void block_minmax(long long& lo, long long& hi, long 
   }
 }
 
+// P[0..2W) = a b exactly from radix-2^29 column sums (p >= 512): NA limbs
+// of each operand, column sums C_k < 2^64 (at most NA products of < 2^58,
+// plus a carry < 2^35), one carry pass into 29-bit digits, and the digits
+// packed into 32-bit words as they are produced (the word count and bit
+// position are compile-time constants of the unrolled loop).  One 32x32->64
+// multiply-add per limb pair and no carry instructions, against three
+// instructions per word product for the schoolbook rows.
+template <int W>
+__device__ __forceinline__ void mul_full_cols(const uint32_t (&a)[W], const uint32_t (&b)[W],
+                                              uint32_t (&P)[2 * W]) {
+  constexpr int NA = Cols<W>::NA;
+  static_assert(2 * NA * kR >= 64 * W, "the digits cover the product");
+  uint32_t al[NA], bl[NA];
+  cut_limbs<W, NA>(a, al);
+  cut_limbs<W, NA>(b, bl);
+  uint64_t carry = 0u, buf = 0u;
+  int nb = 0, w = 0;
+#pragma unroll
+  for (int k = 0; k < 2 * NA; ++k) {
+    uint64_t acc = carry;
+#pragma unroll
+    for (int i = (k - NA + 1 > 0 ? k - NA + 1 : 0); i <= (k < NA - 1 ? k : NA - 1); ++i)
+      acc += (uint64_t)al[i] * bl[k - i];
+    carry = acc >> kR;
+    buf |= (acc & kRMask) << nb;  // nb <= 31: at most 60 bits
+    nb += kR;
+    if (nb >= 32 && w < 2 * W) {
+      P[w++] = (uint32_t)buf;
+      buf >>= 32;
+      nb -= 32;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 2 * W; ++j)
+    if (j >= w) {  // the product's top words not yet emitted (the loop ran out of digits)
+      P[j] = (uint32_t)buf;
+      buf >>= 32;
+    }
+}
+
 // The elements one block takes for a dot: i = base + threadIdx.x + m stride
 // (m >= 0) while i < end, read through map[i] when map is not null (a
 // negative entry: no element).  The accumulate kernel's grid-stride share is
@@ -202,8 +242,8 @@ __device__ void dot_block_partial(const DotDev& a, const DotScratch& s, int j, i
   auto accumulate = [&](const Num<W>& x, const Num<W>& y) {
     if (zero_e(x.e) || zero_e(y.e)) return;
     uint32_t P[2 * W];
-    if (W >= 16)
-      mul_full_ilp<W>(x.m, y.m, P);
+    if constexpr (W >= 16)
+      mul_full_cols<W>(x.m, y.m, P);
     else
       mul_full<W>(x.m, y.m, P);
     add_term<W>(c, kDotThreads, P, x.e + y.e - anchor, x.s ^ y.s);
