@@ -52,7 +52,7 @@ __global__ void axpy_kernel(const uint64_t* __restrict__ al, int64_t n,
     Num<W> xv, yv, t, r;
     load<W>(xv, x, ldx, i);
     load<W>(yv, y, ldy, i);
-    mul_rn<W>(alpha, xv, t);
+    mul_rn_fast<W>(alpha, xv, t);
     add_rn<W>(yv, t, r);
     store<W>(r, y, ldy, i);
   }

@@ -28,11 +28,11 @@ __device__ __forceinline__ void gp_wp_elem(int64_t i, const Num<W>& beta, const 
   load<W>(pi, p, ld, i);
   load<W>(ui, u, ld, i);
   load<W>(ri, r, ld, i);
-  mul_rn<W>(beta, qi, b);
+  mul_rn_fast<W>(beta, qi, b);
   add_rn<W>(vi, b, c);
   store<W>(c, w, ld, i);
   sub_rn<W>(pi, ui, c);
-  mul_rn<W>(beta, c, a);
+  mul_rn_fast<W>(beta, c, a);
   add_rn<W>(ri, a, c);
   store<W>(c, p, ld, i);
 }
@@ -49,11 +49,11 @@ __device__ __forceinline__ void gp_sty_elem(int64_t i, const Num<W>& alpha, cons
   load<W>(wi, w, ld, i);
   sub_rn<W>(ti, ri, sv);
   store<W>(sv, s, ld, i);
-  mul_rn<W>(alpha, qi, c);
+  mul_rn_fast<W>(alpha, qi, c);
   sub_rn<W>(ri, c, a);
   store<W>(a, t, ld, i);
   sub_rn<W>(wi, qi, c);
-  mul_rn<W>(alpha, c, a);
+  mul_rn_fast<W>(alpha, c, a);
   sub_rn<W>(sv, a, c);
   store<W>(c, y, ld, i);
 }
@@ -77,25 +77,25 @@ __device__ __forceinline__ void gp_uzxr_elem(int64_t i, const Num<W>& beta, cons
   load<W>(yi, V.v[7], ld, i);
   load<W>(ti, V.v[6], ld, i);
   load<W>(vi, V.v[8], ld, i);
-  mul_rn<W>(beta, ui, b);
+  mul_rn_fast<W>(beta, ui, b);
   add_rn<W>(si, b, c);
-  mul_rn<W>(eta, c, b);
-  mul_rn<W>(zeta, qi, c);
+  mul_rn_fast<W>(eta, c, b);
+  mul_rn_fast<W>(zeta, qi, c);
   add_rn<W>(c, b, un);
   store<W>(un, V.v[2], ld, i);
-  mul_rn<W>(zeta, ri, b);  // zeta r
-  mul_rn<W>(eta, zi, c);   // eta z
+  mul_rn_fast<W>(zeta, ri, b);  // zeta r
+  mul_rn_fast<W>(eta, zi, c);   // eta z
   add_rn<W>(b, c, a);
-  mul_rn<W>(alpha, un, b);
+  mul_rn_fast<W>(alpha, un, b);
   sub_rn<W>(a, b, zn);
   store<W>(zn, V.v[4], ld, i);
-  mul_rn<W>(alpha, pi, b);  // alpha p
+  mul_rn_fast<W>(alpha, pi, b);  // alpha p
   add_rn<W>(xi, b, c);
   add_rn<W>(c, zn, a);
   store<W>(a, x, ldx, i);
-  mul_rn<W>(eta, yi, b);  // eta y
+  mul_rn_fast<W>(eta, yi, b);  // eta y
   sub_rn<W>(ti, b, c);
-  mul_rn<W>(zeta, vi, b);  // zeta v
+  mul_rn_fast<W>(zeta, vi, b);  // zeta v
   sub_rn<W>(c, b, a);
   store<W>(a, V.v[3], ld, i);
 }

@@ -63,7 +63,7 @@ __device__ __forceinline__ void sub_products(Num<W>& acc, const uint64_t* __rest
           load_w<W>(z, w, ldw, col[k + u]);
         else
           load<W>(z, w, ldw, col[k + u]);
-        mul_rn<W>(f, z, pr[u]);
+        mul_rn_fast<W>(f, z, pr[u]);
       }
     }
 #pragma unroll
@@ -131,7 +131,7 @@ __global__ void ilu_level_kernel(const int32_t* __restrict__ rows, int64_t count
       Num<W> ukj, aij, t1, t2;
       load_w<W>(ukj, lu, nnz, q);
       load_w<W>(aij, lu, nnz, ij);
-      mul_rn<W>(l, ukj, t1);
+      mul_rn_fast<W>(l, ukj, t1);
       sub_rn<W>(aij, t1, t2);
       store<W>(t2, lu, nnz, ij);
     }

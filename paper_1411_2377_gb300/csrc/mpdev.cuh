@@ -878,6 +878,17 @@ __device__ __forceinline__ void mul_rn_short(const Num<W>& a, const Num<W>& b, N
   round_increment<W>(r.m, r.e, rb & ((any != 0u) | (r.m[0] & 1u)));
 }
 
+// r = RN(a*b) in the cheaper form for the precision: the short column
+// product from p = 512, the word product below.  Both are correctly
+// rounded, so the result is the same.
+template <int W>
+__device__ __forceinline__ void mul_rn_fast(const Num<W>& a, const Num<W>& b, Num<W>& r) {
+  if constexpr (W >= 16)
+    mul_rn_short<W>(a, b, r);
+  else
+    mul_rn<W>(a, b, r);
+}
+
 // As add_product_cols for a window of counters that starts qrel digits above
 // the term's own digit 0 (qrel = q - window base, may be negative): columns
 // below the window (k < -qrel) are skipped, and errp is set when a skipped

@@ -125,10 +125,10 @@ __device__ void s_setup(SState* st, uint64_t* S, double rtol, double atol) {
   Num<W> rt, at, T, A, t, thr, rr0, rho, z;
   from_f64<W>(rtol, rt);
   from_f64<W>(atol, at);
-  mul_rn<W>(rt, rt, T);
-  mul_rn<W>(at, at, A);
+  mul_rn_fast<W>(rt, rt, T);
+  mul_rn_fast<W>(at, at, A);
   ld_s<W>(rr0, S, RR0);
-  mul_rn<W>(T, rr0, t);
+  mul_rn_fast<W>(T, rr0, t);
   add_rn<W>(t, A, thr);
   st_s<W>(thr, S, THR);
   set_zero(z, 0u);
@@ -199,8 +199,8 @@ __device__ void s_zeta(SState* st, uint64_t* S, int lane) {
     ld_s<W>(y1, S, j1);
     ld_s<W>(x2, S, i2);
     ld_s<W>(y2, S, j2);
-    mul_rn<W>(x1, y1, a);
-    mul_rn<W>(x2, y2, b);
+    mul_rn_fast<W>(x1, y1, a);
+    mul_rn_fast<W>(x2, y2, b);
     sub_rn<W>(a, b, c);
     part[lane] = c;
   }
@@ -287,7 +287,7 @@ __device__ void s_check(SState* st, uint64_t* S, uint64_t* hist, int64_t hist_ld
     finish(st, MP_ERR_TIMEOUT);
   } else if (BDIV >= 0) {
     Num<W> b;
-    mul_rn<W>(q[0], q[1], b);
+    mul_rn_fast<W>(q[0], q[1], b);
     st_s<W>(b, S, BETA);
   } else {
     st_s<W>(q[0], S, BETA);
@@ -393,7 +393,7 @@ __global__ void gp_ty1(const SState* st, const uint64_t* __restrict__ S, const u
   GRID_LOOP(i, n) {
     Num<W> a, aq, c;
     load<W>(a, q, ld, i);
-    mul_rn<W>(alpha, a, aq);
+    mul_rn_fast<W>(alpha, a, aq);
     load<W>(a, r, ld, i);
     sub_rn<W>(a, aq, c);
     store<W>(c, t, ld, i);
@@ -439,10 +439,10 @@ __global__ void bi_p(const SState* st, const uint64_t* __restrict__ S, const uin
     load<W>(ri, r, ld, i);
     load<W>(pti, pt, ld, i);
     load<W>(rti, rt, ld, i);
-    mul_rn<W>(beta, pi, b);
+    mul_rn_fast<W>(beta, pi, b);
     add_rn<W>(ri, b, c);
     store<W>(c, p, ld, i);
-    mul_rn<W>(beta, pti, b);
+    mul_rn_fast<W>(beta, pti, b);
     add_rn<W>(rti, b, c);
     store<W>(c, pt, ld, i);
   }
@@ -464,13 +464,13 @@ __global__ void bi_xr(const SState* st, const uint64_t* __restrict__ S, const ui
     load<W>(ri, r, ld, i);
     load<W>(zti, zt, ld, i);
     load<W>(rti, rt, ld, i);
-    mul_rn<W>(alpha, pi, b);
+    mul_rn_fast<W>(alpha, pi, b);
     add_rn<W>(xi, b, c);
     store<W>(c, x, ldx, i);
-    mul_rn<W>(alpha, zi, b);
+    mul_rn_fast<W>(alpha, zi, b);
     sub_rn<W>(ri, b, c);
     store<W>(c, r, ld, i);
-    mul_rn<W>(alpha, zti, b);
+    mul_rn_fast<W>(alpha, zti, b);
     sub_rn<W>(rti, b, c);
     store<W>(c, rt, ld, i);
   }
@@ -488,12 +488,12 @@ __global__ void cgs_up(const SState* st, const uint64_t* __restrict__ S, const u
     load<W>(qv, q, ld, i);
     load<W>(ri, r, ld, i);
     load<W>(pi, p, ld, i);
-    mul_rn<W>(beta, qv, a);
+    mul_rn_fast<W>(beta, qv, a);
     add_rn<W>(ri, a, un);
     store<W>(un, u, ld, i);
-    mul_rn<W>(beta, pi, b);
+    mul_rn_fast<W>(beta, pi, b);
     add_rn<W>(qv, b, a);
-    mul_rn<W>(beta, a, b);
+    mul_rn_fast<W>(beta, a, b);
     add_rn<W>(un, b, a);
     store<W>(a, p, ld, i);
   }
@@ -512,12 +512,12 @@ __global__ void cgs_qwx(const SState* st, const uint64_t* __restrict__ S, const 
     load<W>(uv, u, ld, i);
     load<W>(vi, v, ld, i);
     load<W>(xi, x, ldx, i);
-    mul_rn<W>(alpha, vi, b);
+    mul_rn_fast<W>(alpha, vi, b);
     sub_rn<W>(uv, b, qv);
     store<W>(qv, q, ld, i);
     add_rn<W>(uv, qv, wv);
     store<W>(wv, w, ld, i);
-    mul_rn<W>(alpha, wv, b);
+    mul_rn_fast<W>(alpha, wv, b);
     add_rn<W>(xi, b, uv);
     store<W>(uv, x, ldx, i);
   }
@@ -533,7 +533,7 @@ __global__ void r_minus(const SState* st, const uint64_t* __restrict__ S, const 
     Num<W> sc, av, b, rv, c;
     ld_s<W>(sc, S, SCAL);
     load<W>(av, a, ld, i);
-    mul_rn<W>(sc, av, b);
+    mul_rn_fast<W>(sc, av, b);
     load<W>(rv, r, ld, i);
     sub_rn<W>(rv, b, c);
     store<W>(c, r, ld, i);
@@ -551,10 +551,10 @@ __global__ void bs_p(const SState* st, const uint64_t* __restrict__ S, const uin
     ld_s<W>(beta, S, BETA);
     ld_s<W>(omega, S, OMEGA);
     load<W>(a, v, ld, i);
-    mul_rn<W>(omega, a, b);
+    mul_rn_fast<W>(omega, a, b);
     load<W>(a, p, ld, i);
     sub_rn<W>(a, b, c);
-    mul_rn<W>(beta, c, a);
+    mul_rn_fast<W>(beta, c, a);
     load<W>(b, r, ld, i);
     add_rn<W>(b, a, c);
     store<W>(c, p, ld, i);
@@ -571,7 +571,7 @@ __global__ void bs_s(const SState* st, const uint64_t* __restrict__ S, const uin
     Num<W> alpha, a, b, c;
     ld_s<W>(alpha, S, ALPHA);
     load<W>(a, v, ld, i);
-    mul_rn<W>(alpha, a, b);
+    mul_rn_fast<W>(alpha, a, b);
     load<W>(a, r, ld, i);
     sub_rn<W>(a, b, c);
     store<W>(c, s, ld, i);
@@ -595,12 +595,12 @@ __global__ void bs_xr(const SState* st, const uint64_t* __restrict__ S, const ui
     load<W>(sxi, sx, ld, i);
     load<W>(si, s, ld, i);
     load<W>(ti, t, ld, i);
-    mul_rn<W>(alpha, pxi, b);
+    mul_rn_fast<W>(alpha, pxi, b);
     add_rn<W>(xi, b, c);
-    mul_rn<W>(omega, sxi, b);
+    mul_rn_fast<W>(omega, sxi, b);
     add_rn<W>(c, b, a);
     store<W>(a, x, ldx, i);
-    mul_rn<W>(omega, ti, b);
+    mul_rn_fast<W>(omega, ti, b);
     sub_rn<W>(si, b, c);
     store<W>(c, r, ld, i);
   }
