@@ -41,7 +41,11 @@ __global__ void __launch_bounds__(128) gemv_ordered_kernel(int64_t m, int64_t n,
     }
     if (zero_e(a.e) || zero_e(xv.e)) continue;
     Num<W> t, s;
-    if (W >= 8)
+    // the product forms of the sparse ORDERED kernel, so that the two compare
+    // like with like: short column product from p = 512, columns at 256
+    if constexpr (W >= 16)
+      mul_rn_short<W>(a, xv, t);
+    else if constexpr (W >= 8)
       mul_rn_cols<W>(a, xv, t);
     else
       mul_rn<W>(a, xv, t);
