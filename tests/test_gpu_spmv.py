@@ -217,3 +217,36 @@ def test_device_transpose_with_a_long_column_and_unsorted_rows(p):
         want_t, _ = oracle.spmv_t(p, m, rowptr, colidx, recs(V), recs(X))
         assert_bitwise(mpk.spmv(A, x, mode=name).planes(), want, f"{name} p={p}")
         assert_bitwise(mpk.spmv_t(A, x, mode=name).planes(), want_t, f"T {name} p={p}")
+
+
+def test_products_with_a_and_its_transpose_at_the_same_time():
+    """y = A x and z = A^T w on two streams at once (as BiCG runs them), EXACT
+    at p = 256 on a scattered pattern with n >= 65536, so that both products
+    gather x from a record copy, and with exponents spread over +-300, so that
+    rows overflow to the exact warp-per-row kernel: the two layouts have their
+    own record buffers and overflow lists, and both results equal the
+    oracle's, in three rounds with different vectors."""
+    mpk = need_gpu()
+    import torch
+
+    p, n = 256, 70_000
+    rowptr, colidx = random_csr(n, seed=71, mean_len=4, max_len=40)
+    V = rand_planes(len(colidx), p, 72, zero_frac=0.02, emin=-300, emax=300)
+    A = mpk.CSR(rowptr, colidx, V, p, transpose=True)
+    Vr = recs(V)
+    rt, ct, vt = oracle.transpose(p, rowptr, colidx, Vr)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    for k in range(3):
+        X = rand_planes(n, p, 73 + 2 * k, zero_frac=0.02, emin=-40, emax=40)
+        Wv = rand_planes(n, p, 74 + 2 * k, zero_frac=0.02, emin=-40, emax=40)
+        x, w = mpk.Vec.from_planes(X, p), mpk.Vec.from_planes(Wv, p)
+        y, z = mpk.Vec.empty(n, p), mpk.Vec.empty(n, p)
+        torch.cuda.synchronize()
+        mpk.spmv(A, x, y, mode="exact", stream=s1, sync=False)
+        mpk.spmv_t(A, w, z, mode="exact", stream=s2, sync=False)
+        torch.cuda.synchronize()
+        want_y = oracle_spmv_threads(oracle, p, oracle.EXACT, rowptr, colidx, Vr, recs(X))
+        want_z = oracle_spmv_threads(oracle, p, oracle.EXACT, rt, ct, vt, recs(Wv))
+        assert_bitwise(y.planes(), want_y, f"A x beside A^T w, round {k}")
+        assert_bitwise(z.planes(), want_z, f"A^T w beside A x, round {k}")
+    A.close()
