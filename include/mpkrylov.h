@@ -178,7 +178,12 @@ mp_status mp_spmv(mp_csr A, mp_vec x, mp_vec y, mp_mode mode, void* stream);
 
 /* y = A^T x (BiCG's shadow product, Fig. 5); row j of A^T lists the rows i
  * of A with a stored a_ij in ascending i, which is the ORDERED order.
- * Requires MP_CSR_TRANSPOSE at creation. */
+ * Requires MP_CSR_TRANSPOSE at creation.
+ * Streams: each of A's two layouts (A, A^T) keeps its own working storage
+ * (the record copy of x, the EXACT overflow list), so a product with A
+ * (mp_spmv, mp_residual) and one with A^T may run at the same time on
+ * different streams; two products with the same layout that overlap on the
+ * GPU race on it. */
 mp_status mp_spmv_t(mp_csr A, mp_vec x, mp_vec y, mp_mode mode, void* stream);
 
 /* r_i = RN(b_i - sum_k a_ik x_k), summed exactly and rounded once (the
