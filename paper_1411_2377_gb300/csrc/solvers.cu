@@ -917,8 +917,16 @@ mp_status solve_w(const SolveCall& cu, mp_solve_info* info) {
   Work w;
   const int kVecs = M == kGPBiCG ? 11 : (M == kCGS || c.pre ? 8 : 6);
   mp_status r = alloc_work(w, c.A->prec, n, kVecs, st);
-  if (r != MP_OK) {
+  if (r != MP_OK) {  // the work space, the streams and events go before returning
     free_work(w, st);
+    cudaStreamSynchronize(st);
+    if (c.st2) {
+      cudaEventDestroy(c.ev_fork);
+      cudaEventDestroy(c.ev_join);
+      cudaStreamDestroy(c.st2);
+    }
+    cudaEventDestroy(fence);
+    cudaStreamDestroy(st);
     return r;
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
