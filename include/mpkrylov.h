@@ -450,7 +450,9 @@ int64_t mp_launch_count(int32_t reset);
  * CUDA call there is reported as failed once (cudaErrorUnknown) without
  * being made; the library must then return MP_ERR_CUDA and release what the
  * call had allocated.  Sites: "solver poll" (the host's read of a p <= 1024
- * solver's device state).  site = NULL or "" disarms.  Nothing reaches the
+ * solver's device state) and "work memory" (each stream-ordered allocation
+ * of the work space of a p <= 1024 solver or of mp_refine; a failure there
+ * returns MP_ERR_CUDA before any iteration).  site = NULL or "" disarms.  Nothing reaches the
  * GPU: the fault is a fake status on the host.  mp_debug_pool_used returns
  * the bytes in use in the current device's default stream-ordered memory
  * pool (where the solvers take their work memory), to check that a failed

@@ -936,19 +936,12 @@ mp_status mp_batch_gpbicg(mp_batch B, mp_vec b, mp_vec x, const mp_solve_opts* o
   cudaStream_t cu = static_cast<cudaStream_t>(stream);
   cudaStream_t st = nullptr;
   cudaEvent_t fence = nullptr;
-  MPK_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-  MPK_CUDA(cudaEventCreateWithFlags(&fence, cudaEventDisableTiming));
-  MPK_CUDA(cudaEventRecord(fence, cu));
-  MPK_CUDA(cudaStreamWaitEvent(st, fence, 0));
+  if ((r = private_stream_open(cu, &st, &fence)) != MP_OK) return r;
   r = dispatch_w(B->prec, [&](auto w) {
     constexpr int W = decltype(w)::value;
     return batch_entry<W>(B, b, x, *opts, infos, st);
   });
-  cudaEventRecord(fence, st);
-  cudaStreamWaitEvent(cu, fence, 0);
-  cudaStreamSynchronize(st);
-  cudaEventDestroy(fence);
-  cudaStreamDestroy(st);
+  private_stream_close(cu, st, fence);
   return r;
 }
 

@@ -120,6 +120,17 @@ int* status_word();  // device address of the current device's status word
 void count_launch(int k = 1);
 mp_status launch_check(const char* what);  // cudaGetLastError after a launch
 
+// A private non-blocking stream whose work starts after what the caller's
+// stream holds now (the solvers capture graphs, which the legacy default
+// stream does not allow).  On failure nothing is left created.
+mp_status private_stream_open(cudaStream_t caller, cudaStream_t* ps, cudaEvent_t* fence);
+// Makes the caller's stream wait for the private stream's work, waits for it
+// on the host and destroys the stream and the event.
+void private_stream_close(cudaStream_t caller, cudaStream_t ps, cudaEvent_t fence);
+// cudaMallocAsync of a solver's work space, behind the "work memory"
+// fault-injection site.
+cudaError_t work_malloc(void** p, size_t bytes, cudaStream_t st);
+
 // ---- precision ------------------------------------------------------------
 inline bool prec_ok(int p) { return p == 128 || p == 256 || p == 512 || p == 1024; }
 // 2048, 4096, 8192: one value per warp (bigp.cu); SpMV, dot and axpy only.

@@ -484,8 +484,17 @@ mp_status inner_solve(Inner& w, const mp_csr_s* M, double rtol, int64_t maxit, i
 
 mp_status build_f64(mp_csr_s* M, int equilibrate, cudaStream_t st) {
   if (M->a64) return MP_OK;
-  MPK_CUDA(cudaMalloc((void**)&M->a64, sizeof(double) * (size_t)(M->A.nslots > 0 ? M->A.nslots : 1)));
-  MPK_CUDA(cudaMalloc((void**)&M->rowscale, sizeof(double) * (size_t)(M->n > 0 ? M->n : 1)));
+  // both buffers or neither: a64 set marks the copy as built
+  double *a64 = nullptr, *rowscale = nullptr;
+  cudaError_t e = cudaMalloc((void**)&a64, sizeof(double) * (size_t)(M->A.nslots > 0 ? M->A.nslots : 1));
+  if (e == cudaSuccess)
+    e = cudaMalloc((void**)&rowscale, sizeof(double) * (size_t)(M->n > 0 ? M->n : 1));
+  if (e != cudaSuccess) {
+    cudaFree(a64);
+    return cuda_error(e, "FP64 copy of the matrix");
+  }
+  M->a64 = a64;
+  M->rowscale = rowscale;
   M->bytes += 8 * (M->A.nslots + M->n);
   if (M->A.nchunks == 0) return MP_OK;
   const int rb = (int)((M->A.nchunks * 32 + kT - 1) / kT);
@@ -511,17 +520,18 @@ mp_status refine_w(mp_csr_s* M, const mp_vec& b, const mp_vec& x, const mp_refin
   uint64_t* sc = nullptr;     // p-bit scalars: (r,r), (b,b)
   long long* words = nullptr; // emax, dmax bits, xmax bits
   void* dscr = nullptr;
-  MPK_CUDA(cudaMallocAsync((void**)&w.v, sizeof(double) * 12 * (size_t)w.n, st));
-  MPK_CUDA(cudaMallocAsync((void**)&w.S, sizeof(double) * NS64, st));
-  MPK_CUDA(cudaMallocAsync((void**)&w.partial, sizeof(double) * 5 * kDotBlocks, st));
-  MPK_CUDA(cudaMallocAsync((void**)&w.st, sizeof(St64), st));
-  MPK_CUDA(cudaMallocAsync((void**)&rbuf, sizeof(uint64_t) * (L + 1) * (size_t)w.n, st));
-  MPK_CUDA(cudaMallocAsync((void**)&sc, sizeof(uint64_t) * 2 * (L + 1), st));
-  MPK_CUDA(cudaMallocAsync((void**)&words, sizeof(long long) * 3, st));
+  // a failed allocation skips the solve; the cleanup below frees what was taken
   const size_t db = dot_scratch_bytes(M->prec, 2);
-  MPK_CUDA(cudaMallocAsync(&dscr, db, st));
-  if ((r = init_dot_scratch(dscr, st)) != MP_OK) return r;
-  cudaEvent_t e0, e1;
+  cudaError_t ca = work_malloc((void**)&w.v, sizeof(double) * 12 * (size_t)w.n, st);
+  if (ca == cudaSuccess) ca = work_malloc((void**)&w.S, sizeof(double) * NS64, st);
+  if (ca == cudaSuccess) ca = work_malloc((void**)&w.partial, sizeof(double) * 5 * kDotBlocks, st);
+  if (ca == cudaSuccess) ca = work_malloc((void**)&w.st, sizeof(St64), st);
+  if (ca == cudaSuccess) ca = work_malloc((void**)&rbuf, sizeof(uint64_t) * (L + 1) * (size_t)w.n, st);
+  if (ca == cudaSuccess) ca = work_malloc((void**)&sc, sizeof(uint64_t) * 2 * (L + 1), st);
+  if (ca == cudaSuccess) ca = work_malloc((void**)&words, sizeof(long long) * 3, st);
+  if (ca == cudaSuccess) ca = work_malloc(&dscr, db, st);
+  r = ca != cudaSuccess ? cuda_error(ca, "refinement work memory") : init_dot_scratch(dscr, st);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   cudaEventRecord(e0, st);
@@ -529,7 +539,7 @@ mp_status refine_w(mp_csr_s* M, const mp_vec& b, const mp_vec& x, const mp_refin
   mp_refine_info out{};
   out.status = MP_ERR_NOCONV;
   double bb = 0.0;
-  for (int64_t it = 0; it <= o.max_outer; ++it) {
+  for (int64_t it = 0; r == MP_OK && it <= o.max_outer; ++it) {
     // r = RN_row(b - A x) (exact rows), (r,r) and (b,b) at p bits
     if ((r = launch_spmv(M, M->A, MP_EXACT, x.data, x.ld, rbuf, w.n, b.data, b.ld, nullptr, st)) != MP_OK)
       break;
@@ -598,8 +608,8 @@ mp_status refine_w(mp_csr_s* M, const mp_vec& b, const mp_vec& x, const mp_refin
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
   out.ms = ms;
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
   cudaFreeAsync(w.v, st);
   cudaFreeAsync(w.S, st);
   cudaFreeAsync(w.partial, st);
@@ -637,19 +647,12 @@ mp_status mp_refine(mp_csr A, mp_vec b, mp_vec x, const mp_refine_opts* opts, mp
   // private stream fenced to the caller's (the inner solve captures graphs)
   cudaStream_t ps = nullptr;
   cudaEvent_t fence = nullptr;
-  MPK_CUDA(cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking));
-  MPK_CUDA(cudaEventCreateWithFlags(&fence, cudaEventDisableTiming));
-  MPK_CUDA(cudaEventRecord(fence, st));
-  MPK_CUDA(cudaStreamWaitEvent(ps, fence, 0));
+  if ((r = private_stream_open(st, &ps, &fence)) != MP_OK) return r;
   r = dispatch_w(A->prec, [&](auto w) {
     constexpr int W = decltype(w)::value;
     return refine_w<W>(A, b, x, *opts, info, ps);
   });
-  cudaEventRecord(fence, ps);
-  cudaStreamWaitEvent(st, fence, 0);
-  cudaStreamSynchronize(ps);
-  cudaEventDestroy(fence);
-  cudaStreamDestroy(ps);
+  private_stream_close(st, ps, fence);
   return r;
 }
 

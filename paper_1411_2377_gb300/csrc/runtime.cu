@@ -75,6 +75,34 @@ mp_status launch_check(const char* what) {
   return MP_OK;
 }
 
+mp_status private_stream_open(cudaStream_t caller, cudaStream_t* ps, cudaEvent_t* fence) {
+  *ps = nullptr;
+  *fence = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(ps, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(fence, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(*fence, caller);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(*ps, *fence, 0);
+  if (e == cudaSuccess) return MP_OK;
+  if (*fence) cudaEventDestroy(*fence);
+  if (*ps) cudaStreamDestroy(*ps);
+  *ps = nullptr;
+  *fence = nullptr;
+  return cuda_error(e, "private stream set-up");
+}
+
+void private_stream_close(cudaStream_t caller, cudaStream_t ps, cudaEvent_t fence) {
+  cudaEventRecord(fence, ps);
+  cudaStreamWaitEvent(caller, fence, 0);
+  cudaStreamSynchronize(ps);
+  cudaEventDestroy(fence);
+  cudaStreamDestroy(ps);
+}
+
+cudaError_t work_malloc(void** p, size_t bytes, cudaStream_t st) {
+  const cudaError_t e = injected_fault("work memory");
+  return e != cudaSuccess ? e : cudaMallocAsync(p, bytes, st);
+}
+
 mp_status check_vec(const mp_vec& v, int64_t n, int prec, const char* name) {
   if (v.prec_bits != prec)
     return set_error(MP_ERR_ARG, "%s: precision %d, expected %d", name, v.prec_bits, prec);

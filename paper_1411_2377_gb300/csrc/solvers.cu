@@ -644,10 +644,12 @@ mp_status alloc_work(Work& w, int prec, int64_t n, int nvec, cudaStream_t st) {
   const size_t db = dot_scratch_bytes(prec, 5);
   w.status = status_word();
   if (!w.status) return set_error(MP_ERR_CUDA, "status word unavailable");
-  MPK_CUDA(cudaMallocAsync((void**)&w.vecs, vb, st));
-  MPK_CUDA(cudaMallocAsync((void**)&w.S, sb, st));
-  MPK_CUDA(cudaMallocAsync((void**)&w.st, sizeof(SState), st));
-  MPK_CUDA(cudaMallocAsync(&w.dscratch, db, st));
+  // what was allocated before a failure is released by free_work
+  cudaError_t e = work_malloc((void**)&w.vecs, vb, st);
+  if (e == cudaSuccess) e = work_malloc((void**)&w.S, sb, st);
+  if (e == cudaSuccess) e = work_malloc((void**)&w.st, sizeof(SState), st);
+  if (e == cudaSuccess) e = work_malloc(&w.dscratch, db, st);
+  if (e != cudaSuccess) return cuda_error(e, "solver work memory");
   return init_dot_scratch(w.dscratch, st);
 }
 
@@ -890,43 +892,33 @@ mp_status solve_w(const SolveCall& cu, mp_solve_info* info) {
   // stream by events (the legacy default stream cannot be captured).
   cudaStream_t st = nullptr;
   cudaEvent_t fence = nullptr;
-  cudaError_t ces = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-  if (ces == cudaSuccess) ces = cudaEventCreateWithFlags(&fence, cudaEventDisableTiming);
-  if (ces == cudaSuccess) ces = cudaEventRecord(fence, cu.st);
-  if (ces == cudaSuccess) ces = cudaStreamWaitEvent(st, fence, 0);
-  if (ces != cudaSuccess) {
-    if (fence) cudaEventDestroy(fence);
-    if (st) cudaStreamDestroy(st);
-    return cuda_error(ces, "solver stream set-up");
-  }
+  mp_status r = private_stream_open(cu.st, &st, &fence);
+  if (r != MP_OK) return r;
   SolveCall c = cu;
   c.st = st;
   const int64_t n = c.A->n;
   if (M == kBiCG) {
-    ces = cudaStreamCreateWithFlags(&c.st2, cudaStreamNonBlocking);
+    cudaError_t ces = cudaStreamCreateWithFlags(&c.st2, cudaStreamNonBlocking);
     if (ces == cudaSuccess) ces = cudaEventCreateWithFlags(&c.ev_fork, cudaEventDisableTiming);
     if (ces == cudaSuccess) ces = cudaEventCreateWithFlags(&c.ev_join, cudaEventDisableTiming);
     if (ces != cudaSuccess) {
       if (c.ev_fork) cudaEventDestroy(c.ev_fork);
       if (c.st2) cudaStreamDestroy(c.st2);
-      cudaEventDestroy(fence);
-      cudaStreamDestroy(st);
+      private_stream_close(cu.st, st, fence);
       return cuda_error(ces, "solver stream set-up");
     }
   }
   Work w;
   const int kVecs = M == kGPBiCG ? 11 : (M == kCGS || c.pre ? 8 : 6);
-  mp_status r = alloc_work(w, c.A->prec, n, kVecs, st);
+  r = alloc_work(w, c.A->prec, n, kVecs, st);
   if (r != MP_OK) {  // the work space, the streams and events go before returning
     free_work(w, st);
-    cudaStreamSynchronize(st);
     if (c.st2) {
       cudaEventDestroy(c.ev_fork);
       cudaEventDestroy(c.ev_join);
       cudaStreamDestroy(c.st2);
     }
-    cudaEventDestroy(fence);
-    cudaStreamDestroy(st);
+    private_stream_close(cu.st, st, fence);
     return r;
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1058,17 +1050,13 @@ mp_status solve_w(const SolveCall& cu, mp_solve_info* info) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   free_work(w, st);
-  cudaEventRecord(fence, st);
-  cudaStreamWaitEvent(cu.st, fence, 0);
-  cudaStreamSynchronize(st);
   if (c.st2) {
     cudaStreamSynchronize(c.st2);
     cudaEventDestroy(c.ev_fork);
     cudaEventDestroy(c.ev_join);
     cudaStreamDestroy(c.st2);
   }
-  cudaEventDestroy(fence);
-  cudaStreamDestroy(st);
+  private_stream_close(cu.st, st, fence);
   if (r != MP_OK) return r;
   return static_cast<mp_status>(hs.status);
 }

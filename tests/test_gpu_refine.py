@@ -80,3 +80,44 @@ def test_refinement_status_and_options():
     assert info2["status"] == 0
     with pytest.raises(mpk.MPError):
         mpk.refine(A, b, inner_rtol=0.0)
+
+
+@pytest.mark.parametrize("after", (0, 4, 7))
+def test_failed_work_allocation_returns_cuda_status_and_releases_what_it_took(after):
+    """A failed stream-ordered allocation of the refinement's work space
+    (the first, the fifth or the last of its eight; a fake status from the
+    library's host-side fault hook, nothing faults on the GPU) returns
+    MP_ERR_CUDA, leaves x as it was and gives back the allocations already
+    made; the next refinement is unaffected."""
+    import ctypes
+    import torch
+
+    mpk = need_gpu()
+    lib = mpk._lib.load()
+    p = 256
+    rowptr, colidx, v64 = synth.stencil3d(4, seed=3)
+    n = len(rowptr) - 1
+    A = mpk.CSR(rowptr, colidx, v64, p)
+    b = mpk.spmv(A, mpk.Vec.from_f64(np.ones(n), p), mode="exact")
+    _, info0 = mpk.refine(A, b, rtol=2.0 ** -240, max_outer=30)  # builds the FP64 copy
+    assert info0["status"] == 0
+    x0 = mpk.Vec.from_f64(np.full(n, 0.5), p)
+    torch.cuda.synchronize()
+    used = ctypes.c_int64()
+    assert lib.mp_debug_pool_used(ctypes.byref(used)) == 0
+    before = used.value
+    opts = mpk._lib.MpRefineOpts(2.0 ** -240, 30, 1e-10, 20_000, 1, 16)
+    info = mpk._lib.MpRefineInfo()
+    assert lib.mp_debug_fail(b"work memory", after) == 0
+    try:
+        st = lib.mp_refine(A.h, b.c(), x0.c(), ctypes.byref(opts), ctypes.byref(info), None)
+    finally:
+        lib.mp_debug_fail(None, 0)
+    assert st == 4  # MP_ERR_CUDA
+    assert b"refinement work memory" in lib.mp_last_error()
+    torch.cuda.synchronize()
+    assert lib.mp_debug_pool_used(ctypes.byref(used)) == 0
+    assert used.value == before
+    assert np.array_equal(x0.planes(), mpk.Vec.from_f64(np.full(n, 0.5), p).planes())
+    _, info1 = mpk.refine(A, b, rtol=2.0 ** -240, max_outer=30)
+    assert (info1["status"], info1["outer"]) == (0, info0["outer"])

@@ -185,6 +185,48 @@ def test_failed_state_read_returns_cuda_status_and_releases_work_memory(after):
     assert_bitwise(x.planes(), xo, "x after the failed solve")
 
 
+@pytest.mark.parametrize("name,after", [("gpbicg", 0), ("gpbicg", 3), ("bicg", 2)])
+def test_failed_work_allocation_returns_cuda_status_and_releases_what_it_took(name, after):
+    """A failed stream-ordered allocation of the solver's work space (the
+    first one, after = 0, or one after others were made; the failure is a
+    fake status from the library's host-side fault hook, nothing faults on
+    the GPU) returns MP_ERR_CUDA before any iteration and gives back the
+    allocations already made; the next solve still matches the oracle."""
+    import ctypes
+    import torch
+
+    mpk = need_gpu()
+    lib = mpk._lib.load()
+    p = 256
+    rowptr, colidx, v64 = synth.stencil2d(16, seed=1)
+    n = len(rowptr) - 1
+    vals = oracle.from_f64(p, v64)
+    b, _ = oracle.spmv(p, oracle.EXACT, rowptr, colidx, vals, oracle.from_f64(p, np.ones(n)))
+    A = mpk.CSR(rowptr, colidx, v64, p, transpose=True)
+    bv = mpk.Vec.from_planes(synth.records_to_planes(b), p)
+    fn = getattr(mpk, name)
+    torch.cuda.synchronize()
+    used = ctypes.c_int64()
+    assert lib.mp_debug_pool_used(ctypes.byref(used)) == 0
+    before = used.value
+    assert lib.mp_debug_fail(b"work memory", after) == 0
+    try:
+        with pytest.raises(mpk.MPError) as e:
+            fn(A, bv, rtol=1e-40, maxit=200)
+    finally:
+        lib.mp_debug_fail(None, 0)
+    assert e.value.status == 4  # MP_ERR_CUDA
+    assert b"solver work memory" in lib.mp_last_error()
+    torch.cuda.synchronize()
+    assert lib.mp_debug_pool_used(ctypes.byref(used)) == 0
+    assert used.value == before
+    x, info = fn(A, bv, rtol=1e-40, maxit=200)
+    xo, it, st, _ = SOLVERS[name](p, oracle.ORDERED, rowptr, colidx, vals, b,
+                                  oracle.empty(p, n), 1e-40, 0.0, 200)
+    assert (info["iters"], info["status"]) == (it, st)
+    assert_bitwise(x.planes(), xo, f"{name} x after the failed allocation")
+
+
 @pytest.mark.parametrize("name", ("gpbicg", "bicg"))
 def test_time_limit_ends_the_device_loop(name):
     """time_limit_ms: the device-side loop ends with MP_ERR_TIMEOUT once an
