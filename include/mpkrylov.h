@@ -195,7 +195,11 @@ mp_status mp_residual(mp_csr A, mp_vec b, mp_vec x, mp_vec r, void* stream);
 /* out = RN(sum_i x_i y_i) formed exactly and rounded once (the inner
  * products of Fig. 5); zero pairs are skipped, an exact zero is +0.  out is
  * a device scalar (n = 1).  Uses a per-device scratch buffer allocated on
- * first use. */
+ * first use and grown (cudaFree, then cudaMalloc) when a later call needs
+ * more.  Every call on a device shares that buffer, so calls that overlap on
+ * the GPU (on two streams with no ordering between them) race and produce
+ * wrong results: order them on one stream.  The solvers do not use it (each
+ * solve has its own scratch). */
 mp_status mp_dot(mp_vec x, mp_vec y, mp_vec out, void* stream);
 
 /* y_i = RN(y_i + RN(alpha * x_i)); alpha a device scalar. */

@@ -521,7 +521,11 @@ mp_status create_impl(int64_t n, const int64_t* rowptr, const int32_t* colidx,
     } else {
       double* d64 = nullptr;
       if ((r = dalloc(&d64, nnz, tmp)) != MP_OK) return fail(r);
-      cudaMemcpyAsync(d64, values64, (size_t)nnz * 8, cudaMemcpyHostToDevice, st);
+      const cudaError_t e = cudaMemcpyAsync(d64, values64, (size_t)nnz * 8, cudaMemcpyHostToDevice, st);
+      if (e != cudaSuccess) {
+        cudaFree(d64);
+        return cuda_fail(e, "cudaMemcpyAsync(values)");
+      }
       if (prec_big(prec)) {
         f64_to_planes_wide<<<grid_for(nnz, 256), 256, 0, st>>>(d64, nnz, L, d_raw, d_bad);
         count_launch();
