@@ -84,8 +84,11 @@ class Vec:
     def __init__(self, tensor, prec: int):
         torch = _torch()
         L = prec // 64
-        assert tensor.dtype == torch.int64 and tensor.dim() == 2 and tensor.shape[0] == L + 1
-        assert tensor.is_cuda and tensor.stride(1) == 1
+        if tensor.dtype != torch.int64 or tensor.dim() != 2 or tensor.shape[0] != L + 1:
+            raise ValueError(f"a {prec}-bit vector is an int64 tensor of shape ({L + 1}, n); got "
+                             f"{tuple(tensor.shape)} {tensor.dtype}")
+        if not tensor.is_cuda or tensor.stride(1) != 1:
+            raise ValueError("a vector's planes are a CUDA tensor with unit stride along n")
         self.t = tensor
         self.prec = prec
 
@@ -154,18 +157,29 @@ class CSR:
         lib = _lib.load()
         rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
         colidx = np.ascontiguousarray(colidx, dtype=np.int32)
+        # lengths the library reads from these host arrays (it checks the contents)
+        if rowptr.ndim != 1 or rowptr.shape[0] < 1:
+            raise ValueError("rowptr holds n + 1 >= 1 offsets")
+        nnz = int(rowptr[-1])
+        if colidx.ndim != 1 or colidx.shape[0] != max(nnz, 0):
+            raise ValueError(f"colidx holds rowptr[-1] = {nnz} column indices; got "
+                             f"shape {colidx.shape}")
         n = rowptr.shape[0] - 1
         handle = ctypes.c_void_p()
         flags = _lib.MP_CSR_TRANSPOSE if transpose else 0
         values = np.asarray(values)
         if values.dtype == np.float64:
             vals = np.ascontiguousarray(values)
+            if vals.shape != colidx.shape:
+                raise ValueError(f"{colidx.shape[0]} double values expected; got shape {vals.shape}")
             st = lib.mp_csr_create_f64(n, rowptr.ctypes.data, colidx.ctypes.data,
                                        vals.ctypes.data, prec, flags, _stream(stream),
                                        ctypes.byref(handle))
         else:
             vals = np.ascontiguousarray(values, dtype=np.uint64)
-            assert vals.shape == (prec // 64 + 1, colidx.shape[0]), vals.shape
+            if vals.shape != (prec // 64 + 1, colidx.shape[0]):
+                raise ValueError(f"values are ({prec // 64 + 1}, {colidx.shape[0]}) planes; got "
+                                 f"shape {vals.shape}")
             st = lib.mp_csr_create(n, rowptr.ctypes.data, colidx.ctypes.data, vals.ctypes.data,
                                    prec, flags, _stream(stream), ctypes.byref(handle))
         _ok(st, "mp_csr_create")

@@ -160,3 +160,31 @@ def test_fault_hook_arguments_without_gpu(lib):
     assert lib.mp_debug_fail(b"x" * 80, 0) == _lib.MP_ERR_ARG
     assert lib.mp_debug_fail(b"solver poll", -1) == _lib.MP_ERR_ARG
     assert lib.mp_debug_fail(None, 0) == _lib.MP_OK
+
+
+def test_binding_checks_array_lengths_without_gpu(lib):
+    """The binding refuses host arrays shorter or longer than the lengths the
+    library reads from them (rowptr[-1] column indices and values) and
+    tensors that are not a vector's planes, before any library call."""
+    import numpy as np
+    import torch
+
+    import paper_1411_2377_gb300 as mpk
+
+    p = 128
+    rowptr = np.array([0, 2, 3], np.int64)
+    planes = np.zeros((p // 64 + 1, 3), np.uint64)
+    with pytest.raises(ValueError, match="column indices"):
+        mpk.CSR(rowptr, np.array([0, 1], np.int32), planes[:, :2], p)
+    with pytest.raises(ValueError, match="column indices"):
+        mpk.CSR(rowptr, np.array([0, 1, 1, 0], np.int32), planes, p)
+    with pytest.raises(ValueError, match="double values"):
+        mpk.CSR(rowptr, np.array([0, 1, 1], np.int32), np.array([1.0, 2.0]), p)
+    with pytest.raises(ValueError, match="planes"):
+        mpk.CSR(rowptr, np.array([0, 1, 1], np.int32), planes[:2], p)
+    with pytest.raises(ValueError, match="offsets"):
+        mpk.CSR(np.zeros(0, np.int64), np.zeros(0, np.int32), np.zeros(0), p)
+    with pytest.raises(ValueError, match="shape"):
+        mpk.Vec(torch.zeros((p // 64, 4), dtype=torch.int64), p)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        mpk.Vec(torch.zeros((p // 64 + 1, 4), dtype=torch.int64), p)
