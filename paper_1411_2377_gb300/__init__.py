@@ -78,6 +78,21 @@ def imad_probe(stream=None) -> float:
     return rate.value
 
 
+def _csr_arrays(rowptr, colidx):
+    """rowptr and colidx as the library reads them, contiguous int64 and
+    int32; raises ValueError unless colidx holds rowptr[-1] entries (the
+    library reads that many host words and checks their contents)."""
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    colidx = np.ascontiguousarray(colidx, dtype=np.int32)
+    if rowptr.ndim != 1 or rowptr.shape[0] < 1:
+        raise ValueError("rowptr holds n + 1 >= 1 offsets")
+    nnz = int(rowptr[-1])
+    if colidx.ndim != 1 or colidx.shape[0] != max(nnz, 0):
+        raise ValueError(f"colidx holds rowptr[-1] = {nnz} column indices; got "
+                         f"shape {colidx.shape}")
+    return rowptr, colidx
+
+
 class Vec:
     """n p-bit values on the GPU (planes of a (L+1, n) int64 tensor)."""
 
@@ -155,15 +170,7 @@ class CSR:
         """values: (L+1, nnz) uint64 planes, or float64 values (converted
         exactly to p bits)."""
         lib = _lib.load()
-        rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
-        colidx = np.ascontiguousarray(colidx, dtype=np.int32)
-        # lengths the library reads from these host arrays (it checks the contents)
-        if rowptr.ndim != 1 or rowptr.shape[0] < 1:
-            raise ValueError("rowptr holds n + 1 >= 1 offsets")
-        nnz = int(rowptr[-1])
-        if colidx.ndim != 1 or colidx.shape[0] != max(nnz, 0):
-            raise ValueError(f"colidx holds rowptr[-1] = {nnz} column indices; got "
-                             f"shape {colidx.shape}")
+        rowptr, colidx = _csr_arrays(rowptr, colidx)
         n = rowptr.shape[0] - 1
         handle = ctypes.c_void_p()
         flags = _lib.MP_CSR_TRANSPOSE if transpose else 0
@@ -438,9 +445,10 @@ class Batch:
         self._keep = []
         ns, rps, cis, vas = [], [], [], []
         for rowptr, colidx, values in systems:
-            rp = np.ascontiguousarray(rowptr, dtype=np.int64)
-            ci = np.ascontiguousarray(colidx, dtype=np.int32)
+            rp, ci = _csr_arrays(rowptr, colidx)
             va = np.ascontiguousarray(values, dtype=np.float64)
+            if va.shape != ci.shape:
+                raise ValueError(f"{ci.shape[0]} double values expected; got shape {va.shape}")
             self._keep += [rp, ci, va]
             ns.append(rp.shape[0] - 1)
             rps.append(rp.ctypes.data)

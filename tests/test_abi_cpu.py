@@ -184,6 +184,11 @@ def test_binding_checks_array_lengths_without_gpu(lib):
         mpk.CSR(rowptr, np.array([0, 1, 1], np.int32), planes[:2], p)
     with pytest.raises(ValueError, match="offsets"):
         mpk.CSR(np.zeros(0, np.int64), np.zeros(0, np.int32), np.zeros(0), p)
+    with pytest.raises(ValueError, match="column indices"):
+        mpk.Batch([(rowptr, np.array([0, 1, 1], np.int32), np.ones(3)),
+                   (rowptr, np.array([0, 1], np.int32), np.ones(2))], p)
+    with pytest.raises(ValueError, match="double values"):
+        mpk.Batch([(rowptr, np.array([0, 1, 1], np.int32), np.ones(4))], p)
     with pytest.raises(ValueError, match="shape"):
         mpk.Vec(torch.zeros((p // 64, 4), dtype=torch.int64), p)
     with pytest.raises(ValueError, match="CUDA tensor"):
