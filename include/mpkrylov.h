@@ -36,9 +36,12 @@
  * argument errors are returned immediately, while data-dependent errors found
  * by kernels (an exact sum whose exponent span exceeds MP_SPAN_CAP, a zero
  * divisor) are recorded in a per-device status word read by mp_check().
- * Calls that share an mp_csr handle or the per-device status word must be
- * ordered on one stream.  There is no CPU fallback: without a usable GPU
- * every compute call returns MP_ERR_CUDA.
+ * Kernels record there with an atomic compare-and-swap from MP_OK, so the
+ * first error recorded since the last mp_check stays, whichever stream's
+ * call recorded it.  Calls that share an mp_csr handle must be ordered on
+ * one stream, except a product with A beside one with A^T (mp_spmv_t).
+ * There is no CPU fallback: without a usable GPU every compute call returns
+ * MP_ERR_CUDA.
  */
 #ifndef MPKRYLOV_H
 #define MPKRYLOV_H
