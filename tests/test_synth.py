@@ -55,3 +55,51 @@ def test_batch_systems_generator():
     assert all(1 <= x["nrhs"] <= 4 for x in d)
     ns = [x["m"] ** (2 if x["kind"] == "2d" else 3) for x in d]
     assert min(ns) >= 1000 and max(ns) <= 70000
+
+
+def test_stencil_value_recipes():
+    """The 5-point matrix: diagonal 4 + U(0, 0.1), neighbours -1 + 0.3 U(-1, 1)
+    at the grid neighbours only; the 7-point convection-diffusion matrix:
+    per row, diagonal 6 s and neighbours (-1 -/+ gamma) s with one scale s,
+    gamma = Pe h / 2, the upwind side (-1 - gamma) towards lower indices."""
+    m = 16
+    rp, ci, v = synth.stencil2d(m, seed=0)
+    rows = np.repeat(np.arange(m * m), np.diff(rp))
+    diag = rows == ci
+    assert np.all((v[diag] >= 4.0) & (v[diag] < 4.1))
+    off = ~diag
+    assert np.all((v[off] > -1.3) & (v[off] < -0.7))
+    d = np.abs(ci[off].astype(np.int64) - rows[off])
+    assert set(np.unique(d)) == {1, m}
+    assert np.all((rows[off] // m == ci[off] // m) | (d == m))  # no wrap-around
+    m, pe = 6, 50.0
+    rp, ci, v = synth.stencil3d(m, seed=2, pe=pe)
+    g = pe / (m + 1) / 2.0
+    for i in range(m ** 3):
+        s, e = rp[i], rp[i + 1]
+        cols, vals = ci[s:e], v[s:e]
+        scale = vals[cols == i][0] / 6.0
+        assert 1.0 <= scale <= 1e20
+        for c, a in zip(cols, vals):
+            if c != i:
+                want = (-1.0 - g) if c < i else (-1.0 + g)
+                assert abs(a / scale - want) < 1e-12
+
+
+def test_lotkin_pattern():
+    """Section 3's workload: first row ones, a_ij = 1/(i+j-1) (1-based)
+    below it, about s % of the entries dropped, the same draw for every
+    precision (the pattern does not depend on p)."""
+    n, s = 40, 30.0
+    rp, ci, num, den = synth.lotkin_pattern(n, s, seed=7)
+    assert np.all(num == 1.0)
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    want = np.where(rows == 0, 1.0, rows + ci + 1.0)
+    assert np.array_equal(den, want)
+    kept = len(ci) / (n * n)
+    assert 0.62 < kept < 0.78
+    assert np.all(np.diff(ci.astype(np.int64))[np.diff(rows) == 0] > 0)
+    full = synth.lotkin_pattern(n, 0.0, seed=7)
+    assert full[0][-1] == n * n
+    again = synth.lotkin_pattern(n, s, seed=7)
+    assert all(np.array_equal(a, b) for a, b in zip(again, (rp, ci, num, den)))
