@@ -195,9 +195,14 @@ mp_status mp_residual(mp_csr A, mp_vec b, mp_vec x, mp_vec r, void* stream);
 
 /* ---- vectors ------------------------------------------------------------- */
 
+/* Longest vectors mp_dot accepts: its 64-bit digit counters, which add the
+ * products' 32-bit digits of every element, stay exact for up to 2^31 - 1
+ * products.  Longer vectors give MP_ERR_ARG before any CUDA call. */
+#define MP_DOT_MAX_N INT64_C(2147483647)
+
 /* out = RN(sum_i x_i y_i) formed exactly and rounded once (the inner
  * products of Fig. 5); zero pairs are skipped, an exact zero is +0.  out is
- * a device scalar (n = 1).  Uses a per-device scratch buffer allocated on
+ * a device scalar (n = 1); n <= MP_DOT_MAX_N.  Uses a per-device scratch buffer allocated on
  * first use and grown (cudaFree, then cudaMalloc) when a later call needs
  * more.  Every call on a device shares that buffer, so calls that overlap on
  * the GPU (on two streams with no ordering between them) race and produce
@@ -220,9 +225,8 @@ mp_status mp_vec_to_f64(mp_vec a, double* d, void* stream);
 
 /* ---- allocation-free dot product (the paper has no counterpart) ---------- */
 
-/* Longest vectors mp_dot_noalloc accepts (its 64-bit digit counters stay
- * exact for up to 2^31 - 1 products). */
-#define MP_DOT_NOALLOC_MAX_N INT64_C(2147483647)
+/* Longest vectors mp_dot_noalloc accepts (the bound of mp_dot). */
+#define MP_DOT_NOALLOC_MAX_N MP_DOT_MAX_N
 /* Size of the device array that holds mp_dot_noalloc's scratch. */
 #define MP_DOT_NOALLOC_SCRATCH_BYTES 298112
 

@@ -203,6 +203,9 @@ mp_status mp_dot(mp_vec x, mp_vec y, mp_vec out, void* stream) {
   if ((r = check_vec(x, x.n, x.prec_bits, "x")) != MP_OK) return r;
   if ((r = check_vec(y, x.n, x.prec_bits, "y")) != MP_OK) return r;
   if ((r = check_vec(out, 1, x.prec_bits, "out")) != MP_OK) return r;
+  if (x.n > MP_DOT_MAX_N)
+    return set_error(MP_ERR_ARG, "mp_dot: length %lld exceeds the maximum %lld", (long long)x.n,
+                     (long long)MP_DOT_MAX_N);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t bytes = big ? dot_big_scratch_bytes(x.prec_bits) : dot_scratch_bytes(x.prec_bits, 1);
   int dev = 0;

@@ -133,10 +133,10 @@ def test_autotune_leaves_the_wide_precisions_alone():
 
 
 def test_noalloc_dot_refusals_without_gpu(lib):
-    """mp_dot_noalloc refuses, on the host and before any CUDA call, vectors
-    longer than MP_DOT_NOALLOC_MAX_N (a length-2^31 view of a 4-element host
-    buffer: nothing reads it) and the wide precisions, which only mp_dot
-    takes."""
+    """mp_dot_noalloc and mp_dot refuse, on the host and before any CUDA
+    call, vectors longer than MP_DOT_MAX_N (a length-2^31 view of a
+    4-element host buffer: nothing reads it); mp_dot_noalloc also refuses
+    the wide precisions, which only mp_dot takes."""
     import numpy as np
 
     from paper_1411_2377_gb300 import _lib
@@ -147,6 +147,11 @@ def test_noalloc_dot_refusals_without_gpu(lib):
     out = _lib.MpVec(1, 128, 1, buf.ctypes.data)
     assert lib.mp_dot_noalloc(big, big, out, None) == _lib.MP_ERR_ARG
     assert b"maximum" in lib.mp_last_error()
+    assert lib.mp_dot(big, big, out, None) == _lib.MP_ERR_ARG  # the same bound
+    assert b"maximum" in lib.mp_last_error()
+    wbig = _lib.MpVec(n, 2048, n, buf.ctypes.data)
+    wout = _lib.MpVec(1, 2048, 1, buf.ctypes.data)
+    assert lib.mp_dot(wbig, wbig, wout, None) == _lib.MP_ERR_ARG
     wide = np.zeros(33 * 4, np.uint64)
     x = _lib.MpVec(4, 2048, 4, wide.ctypes.data)
     o = _lib.MpVec(1, 2048, 1, wide.ctypes.data)
