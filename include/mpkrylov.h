@@ -134,7 +134,10 @@ mp_status mp_csr_info(mp_csr A, int64_t* n, int64_t* nnz, int32_t* prec_bits,
  *     bit 1: products formed from radix-2^29 column sums (one multiply-add
  *            per pair of 29-bit limbs, no carries inside the product; EXACT
  *            then keeps 29-bit digit counters), else from 32-bit words with
- *            carry chains;
+ *            carry chains.  EXACT column-form counters add parts below 2^35
+ *            per term into 64-bit integers, so a row sum is exact for rows of
+ *            up to 2^27 stored entries; the word form (bit 1 clear) adds
+ *            32-bit digits and is exact for any row;
  *     bit 2: MP_EXACT column form: 16 columns computed at a time, not 8
  *            (with bit 4: registers capped for four blocks of at most 128
  *            threads per SM);
