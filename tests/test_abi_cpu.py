@@ -198,3 +198,64 @@ def test_binding_checks_array_lengths_without_gpu(lib):
         mpk.Vec(torch.zeros((p // 64, 4), dtype=torch.int64), p)
     with pytest.raises(ValueError, match="CUDA tensor"):
         mpk.Vec(torch.zeros((p // 64 + 1, 4), dtype=torch.int64), p)
+
+
+def test_host_argument_checks_without_gpu(lib):
+    """Argument errors are found on the host and returned before any CUDA
+    call (MP_ERR_ARG, with the offending item in mp_last_error), so they
+    behave the same on a machine without a GPU: matrix creation, products,
+    solvers, refinement, batches, ILU(0) and the vector calls."""
+    import numpy as np
+
+    from paper_1411_2377_gb300 import _lib
+
+    ARG = _lib.MP_ERR_ARG
+    out = ctypes.c_void_p()
+    col = np.array([0, 1, 1], np.int32)
+    v = np.ones(3)
+
+    def create(n, rowptr, colidx=col, values=v, flags=0, p=128, dst=ctypes.byref(out)):
+        rp = rowptr.ctypes.data if rowptr is not None else None
+        ci = colidx.ctypes.data if colidx is not None else None
+        va = values.ctypes.data if values is not None else None
+        return lib.mp_csr_create_f64(n, rp, ci, va, p, flags, None, dst)
+
+    good = np.array([0, 2, 3], np.int64)
+    assert create(2, good, dst=None) == ARG
+    assert create(-1, good) == ARG
+    assert create(1 << 31, good) == ARG and b"out of range" in lib.mp_last_error()
+    assert create(2, None) == ARG
+    assert create(2, np.array([1, 2, 3], np.int64)) == ARG and b"rowptr[0]" in lib.mp_last_error()
+    assert create(2, np.array([0, 2, 1], np.int64)) == ARG
+    assert b"row 1: rowptr decreases" in lib.mp_last_error()
+    assert create(2, good, colidx=None) == ARG
+    assert create(2, good, values=None) == ARG
+    assert create(2, good, flags=4) == ARG and b"flags" in lib.mp_last_error()
+    assert out.value is None  # nothing was created
+
+    buf = np.zeros(3 * 8, np.uint64)
+    vec = lambda n, p=128: _lib.MpVec(n, p, max(n, 1), buf.ctypes.data)  # noqa: E731
+    opts = _lib.MpSolveOpts(1e-30, 0.0, 100, 0, 8, _lib.MpVec(0, 128, 1, None), 0, 0)
+    info = _lib.MpSolveInfo()
+    for f in (lib.mp_spmv, lib.mp_spmv_t):
+        assert f(None, vec(2), vec(2), 0, None) == ARG
+    assert lib.mp_residual(None, vec(2), vec(2), vec(2), None) == ARG
+    for f in (lib.mp_bicg, lib.mp_gpbicg, lib.mp_cgs, lib.mp_bicgstab):
+        assert f(None, vec(2), vec(2), ctypes.byref(opts), ctypes.byref(info), None) == ARG
+    ropts = _lib.MpRefineOpts(1e-30, 10, 1e-10, 1000, 1, 8)
+    assert lib.mp_refine(None, vec(2), vec(2), ctypes.byref(ropts), None, None) == ARG
+    assert lib.mp_batch_gpbicg(None, vec(2), vec(2), ctypes.byref(opts), None, None) == ARG
+    assert lib.mp_ilu0_create(None, None, ctypes.byref(out)) == ARG
+    assert lib.mp_ilu0_factor(None, vec(2), None) == ARG
+    assert lib.mp_ilu0_apply(None, vec(2), vec(2), None) == ARG
+    assert lib.mp_csr_grad(None, vec(2), vec(2), vec(2), None) == ARG
+    # vector calls: lengths, precisions and the op code
+    assert lib.mp_axpy(vec(1), vec(3), vec(2), None) == ARG
+    assert lib.mp_axpy(vec(1), vec(2), vec(2, 256), None) == ARG
+    assert lib.mp_dot(vec(2), vec(3), vec(1), None) == ARG
+    assert lib.mp_dot(vec(2), vec(2), vec(2), None) == ARG  # out is a scalar
+    assert lib.mp_ewise(9, vec(2), vec(2), vec(2), None) == ARG
+    assert lib.mp_gemv(-1, 2, vec(0), vec(2), vec(0), None) == ARG
+    assert lib.mp_gemv(2, 2, vec(3), vec(2), vec(2), None) == ARG  # A holds m*n values
+    short_ld = _lib.MpVec(4, 128, 2, buf.ctypes.data)
+    assert lib.mp_dot(short_ld, short_ld, vec(1), None) == ARG and b"ld" in lib.mp_last_error()
