@@ -20,7 +20,14 @@ roofline   = the dominant product (largest share of the step): algorithmic
              integer-multiply peak; the slower of the two is the bound.
 cpu_baseline = the oracle (plain C) on bounded row samples, on all host cores
                (rows split over threads) with the one-thread figure beside
-               it, plus the oracle's GPBiCG per iteration on the 64x64 system.
+               it, plus the oracle's GPBiCG on the 64x64 system and set-up
+               plus one iteration of its GPBiCG and BiCG on the 100^3
+               row-scaled system.
+solver     = untimed by `value`: BiCG, GPBiCG, CGS and BiCGSTAB to 1e-30 on
+             the 64x64 system; refinement against the plain solvers on the
+             100^3 system; the batched solves against sequential ones; the
+             differentiable solve; BiCGSTAB with and without ILU(0) (Table 3
+             stand-in); the dense/sparse ratio of Section 3; p = 2048-8192.
 
 --impl reference times the oracle alone on all host cores (the CPU
 reference arm).
