@@ -56,7 +56,7 @@ def tridiag(n, p):
     return np.cumsum(rowptr), np.array(cols, np.int32), oracle.from_f64(p, np.array(vals))
 
 
-@pytest.mark.parametrize("p", (128, 512))
+@pytest.mark.parametrize("p", (128, 512, 2048, 8192))
 def test_ilu0_and_apply_replay_bitwise(p):
     rowptr, colidx, vals, b = rand_system(7, p, 4, density=0.5)
     lu, st = oracle.ilu0(p, rowptr, colidx, vals)
@@ -143,6 +143,25 @@ def test_bicgstab_ilu0_replay_bitwise(mode, side):
                                                side=side)
         xr, itr, str_, hr = replay.bicgstab_ilu0(rows, exact.vec_decode(b, p), X0, p, mode,
                                                  1e-300, maxit, side=side)
+        assert it == itr
+        assert [v.key() for v in xr] == [exact.decode(r, p).key() for r in x]
+        assert [v.key() for v in hr] == [exact.decode(r, p).key() for r in hist]
+
+
+@pytest.mark.parametrize("side", ("left", "right"))
+def test_wide_build_bicgstab_ilu0_replay_bitwise(side):
+    """The wide build (p = 2048) runs the same steps: every iterate of both
+    forms equals the exact-arithmetic replay."""
+    p, n = 2048, 5
+    rowptr, colidx, vals, b = rand_system(n, p, 9, density=0.5)
+    rows = rows_of(rowptr, colidx, vals, p)
+    X0 = exact.vec_decode(oracle.empty(p, n), p)
+    for maxit in (1, 3):
+        x, it, st, hist = oracle.bicgstab_ilu0(p, oracle.ORDERED, rowptr, colidx, vals, b,
+                                               oracle.empty(p, n), 1e-300, 0.0, maxit,
+                                               side=side)
+        xr, itr, str_, hr = replay.bicgstab_ilu0(rows, exact.vec_decode(b, p), X0, p,
+                                                 oracle.ORDERED, 1e-300, maxit, side=side)
         assert it == itr
         assert [v.key() for v in xr] == [exact.decode(r, p).key() for r in x]
         assert [v.key() for v in hr] == [exact.decode(r, p).key() for r in hist]
