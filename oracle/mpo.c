@@ -1,5 +1,5 @@
 /* mpo.c -- CPU oracle for p-bit CSR SpMV, exact dot products, BiCG, GPBiCG,
- * CGS and BiCGSTAB.
+ * CGS, BiCGSTAB, ILU(0) and BiCGSTAB preconditioned with ILU(0).
  *
  * TEST INFRASTRUCTURE ONLY (see mpo.h).  Deliberately plain and slow: natural
  * numbers are little-endian arrays of 32-bit words handled by schoolbook
